@@ -1,0 +1,705 @@
+/* FP64 CPU oracle for the syGlass direct-volume-rendering hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the bench's
+ * CPU-baseline leg may load this library. It shares no code with the CUDA
+ * path (no headers, helpers or tables), and nothing in it is blocked, fused
+ * or reordered beyond what the definitions below state.
+ *
+ * What it computes, following the paper's "Volume Rendering" section:
+ *  - the multi-resolution block pyramid ("Octree Representation"): level L+1
+ *    is the 2x box filter of level L, floor((sum of 8 + 4) / 8), with the
+ *    edge replicated for odd sizes;
+ *  - per-block value ranges (block plus its one-voxel apron) and the
+ *    transfer-function emptiness test derived from them;
+ *  - the octree traversal that picks blocks whose resolution matches the
+ *    pixel resolution ("Octree Representation", last paragraph): top-down
+ *    from the roots, frustum culling, accept a block when one of its voxels
+ *    subtends at most tau pixels at the block's closest point to the nearer
+ *    eye, render one level coarser and request the children when any needed
+ *    child is not resident;
+ *  - per-pixel ray casting under the emission-absorption model ("DVR
+ *    Techniques", second integral), discretised front to back with
+ *    associated colours, early termination, trilinear sampling of the global
+ *    level-L voxel arrays (never bricks or aprons) and a 1D transfer function.
+ *
+ * Readings of points the paper leaves open (opacity correction, the sample
+ * lattice, voxel centres, the integer form of the LOD test, the culling
+ * planes, the channel blend) are stated at each function.
+ *
+ * Parity pins: every function here is checked by the CPU tests against
+ * closed forms (Beer-Lambert, linear fields, hand-computed 4^3 cases),
+ * brute force (pyramid, selection) and invariants (coverage, monotonicity,
+ * stereo mirror, opacity-correction step invariance).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <omp.h>
+
+#define OR_MAX_LEVELS 16
+#define OR_MAX_CH 4
+
+typedef struct {
+  int32_t dtype;  /* 1 = uint8, 2 = uint16 */
+  int32_t levels; /* pyramid levels, 0 = finest */
+  int32_t brick;  /* block edge B in voxels of the block's own level */
+  int32_t nch;    /* channels, blended additively */
+  int64_t dims[OR_MAX_LEVELS][3];
+  const void* data[OR_MAX_LEVELS][OR_MAX_CH]; /* global level-L arrays, x fastest */
+  double model[16]; /* voxel space [0,N]^3 -> world, column major */
+} or_volume;
+
+typedef struct {
+  int32_t n;        /* table entries */
+  float lo, hi;     /* intensity window mapped onto [0, n-1] */
+  float ref_step;   /* step, in level-0 voxels, at which the table's alphas hold */
+  const float* rgba; /* 4n, straight (not premultiplied) colour + opacity */
+} or_tf;
+
+/* ------------------------------------------------------------------------ */
+/* small linear algebra (column-major 4x4, FP64)                             */
+
+static void mat_mul(const double* a, const double* b, double* o) {
+  double t[16];
+  for (int c = 0; c < 4; ++c)
+    for (int r = 0; r < 4; ++r) {
+      double s = 0.0;
+      for (int k = 0; k < 4; ++k) s += a[k * 4 + r] * b[c * 4 + k];
+      t[c * 4 + r] = s;
+    }
+  memcpy(o, t, sizeof t);
+}
+
+/* Gauss-Jordan with partial pivoting; returns 0 if singular */
+static int mat_inv(const double* m, double* inv) {
+  double a[4][8];
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) {
+      a[r][c] = m[c * 4 + r];
+      a[r][c + 4] = (r == c) ? 1.0 : 0.0;
+    }
+  for (int c = 0; c < 4; ++c) {
+    int p = c;
+    for (int r = c + 1; r < 4; ++r)
+      if (fabs(a[r][c]) > fabs(a[p][c])) p = r;
+    if (fabs(a[p][c]) < 1e-300) return 0;
+    if (p != c)
+      for (int k = 0; k < 8; ++k) { double t = a[p][k]; a[p][k] = a[c][k]; a[c][k] = t; }
+    double d = a[c][c];
+    for (int k = 0; k < 8; ++k) a[c][k] /= d;
+    for (int r = 0; r < 4; ++r)
+      if (r != c) {
+        double f = a[r][c];
+        if (f != 0.0)
+          for (int k = 0; k < 8; ++k) a[r][k] -= f * a[c][k];
+      }
+  }
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) inv[c * 4 + r] = a[r][c + 4];
+  return 1;
+}
+
+static void mat_apply(const double* m, const double* v, double* o) {
+  for (int r = 0; r < 4; ++r)
+    o[r] = m[r] * v[0] + m[4 + r] * v[1] + m[8 + r] * v[2] + m[12 + r] * v[3];
+}
+
+/* ------------------------------------------------------------------------ */
+/* pyramid                                                                   */
+
+static inline uint32_t vox_get(const void* p, int dtype, int64_t idx) {
+  return dtype == 1 ? ((const uint8_t*)p)[idx] : ((const uint16_t*)p)[idx];
+}
+
+/* One 2x box-filter step: dst[j] = floor((sum over the 2x2x2 children of src,
+ * child indices clamped into src, + 4) / 8). dst dims are ceil(src/2). */
+void or_pyramid_level(const void* src, int dtype, const int64_t* sdims, void* dst) {
+  int64_t nx = sdims[0], ny = sdims[1], nz = sdims[2];
+  int64_t mx = (nx + 1) / 2, my = (ny + 1) / 2, mz = (nz + 1) / 2;
+#pragma omp parallel for schedule(static)
+  for (int64_t z = 0; z < mz; ++z)
+    for (int64_t y = 0; y < my; ++y)
+      for (int64_t x = 0; x < mx; ++x) {
+        uint64_t s = 0;
+        for (int dz = 0; dz < 2; ++dz)
+          for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+              int64_t X = 2 * x + dx, Y = 2 * y + dy, Z = 2 * z + dz;
+              if (X > nx - 1) X = nx - 1;
+              if (Y > ny - 1) Y = ny - 1;
+              if (Z > nz - 1) Z = nz - 1;
+              s += vox_get(src, dtype, (Z * ny + Y) * nx + X);
+            }
+        uint32_t v = (uint32_t)((s + 4) / 8);
+        int64_t o = (z * my + y) * mx + x;
+        if (dtype == 1) ((uint8_t*)dst)[o] = (uint8_t)v;
+        else ((uint16_t*)dst)[o] = (uint16_t)v;
+      }
+}
+
+/* ------------------------------------------------------------------------ */
+/* blocks (octree nodes)                                                     */
+
+static void level_blocks(const or_volume* v, int L, int64_t nb[3]) {
+  for (int a = 0; a < 3; ++a) nb[a] = (v->dims[L][a] + v->brick - 1) / v->brick;
+}
+
+/* Node ids: levels in order 0..levels-1, within a level x fastest. */
+int64_t or_node_count(const or_volume* v, int64_t* level_offsets /* levels+1, may be NULL */) {
+  int64_t off = 0;
+  for (int L = 0; L < v->levels; ++L) {
+    if (level_offsets) level_offsets[L] = off;
+    int64_t nb[3];
+    level_blocks(v, L, nb);
+    off += nb[0] * nb[1] * nb[2];
+  }
+  if (level_offsets) level_offsets[v->levels] = off;
+  return off;
+}
+
+/* Value range of every block of every level and channel: min and max over
+ * the block's voxels plus a one-voxel apron on every side, with indices
+ * clamped into the level (the voxels a trilinear sample anywhere inside the
+ * block can touch). out: [node][channel][2]. */
+void or_block_ranges(const or_volume* v, uint32_t* out) {
+  int64_t off[OR_MAX_LEVELS + 1];
+  or_node_count(v, off);
+  const int64_t B = v->brick;
+  for (int L = 0; L < v->levels; ++L) {
+    int64_t nb[3];
+    level_blocks(v, L, nb);
+    const int64_t* D = v->dims[L];
+    int64_t nblk = nb[0] * nb[1] * nb[2];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t b = 0; b < nblk; ++b) {
+      int64_t bx = b % nb[0], by = (b / nb[0]) % nb[1], bz = b / (nb[0] * nb[1]);
+      int64_t lo[3] = {bx * B - 1, by * B - 1, bz * B - 1};
+      int64_t hi[3] = {bx * B + B, by * B + B, bz * B + B}; /* inclusive */
+      for (int a = 0; a < 3; ++a) {
+        if (lo[a] < 0) lo[a] = 0;
+        if (hi[a] > D[a] - 1) hi[a] = D[a] - 1;
+      }
+      for (int c = 0; c < v->nch; ++c) {
+        uint32_t mn = 0xffffffffu, mx = 0;
+        for (int64_t z = lo[2]; z <= hi[2]; ++z)
+          for (int64_t y = lo[1]; y <= hi[1]; ++y)
+            for (int64_t x = lo[0]; x <= hi[0]; ++x) {
+              uint32_t q = vox_get(v->data[L][c], v->dtype, (z * D[1] + y) * D[0] + x);
+              if (q < mn) mn = q;
+              if (q > mx) mx = q;
+            }
+        out[((off[L] + b) * v->nch + c) * 2 + 0] = mn;
+        out[((off[L] + b) * v->nch + c) * 2 + 1] = mx;
+      }
+    }
+  }
+}
+
+/* Transfer-function emptiness of a value range [vmin, vmax] for one channel.
+ * Decided in FP32, in this exact sequence, because it turns floating point
+ * into a table index: x = (v - lo) / (hi - lo) clamped to [0,1], q = x (n-1);
+ * the range is empty iff every entry from floor(q(vmin)) - 1 to
+ * floor(q(vmax)) + 2 (clamped to the table) has alpha exactly 0. The one-entry
+ * margins make the test conservative against a one-ulp difference in q. */
+static int tf_range_empty(const or_tf* tf, uint32_t vmin, uint32_t vmax) {
+  volatile float width = tf->hi - tf->lo;
+  volatile float x0 = ((float)vmin - tf->lo) / width;
+  volatile float x1 = ((float)vmax - tf->lo) / width;
+  float a = x0 < 0.0f ? 0.0f : (x0 > 1.0f ? 1.0f : x0);
+  float b = x1 < 0.0f ? 0.0f : (x1 > 1.0f ? 1.0f : x1);
+  volatile float q0 = a * (float)(tf->n - 1);
+  volatile float q1 = b * (float)(tf->n - 1);
+  int ilo = (int)floorf(q0) - 1, ihi = (int)floorf(q1) + 2;
+  if (ilo < 0) ilo = 0;
+  if (ihi > tf->n - 1) ihi = tf->n - 1;
+  for (int i = ilo; i <= ihi; ++i)
+    if (tf->rgba[4 * i + 3] != 0.0f) return 0;
+  return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* LOD + residency selection                                                 */
+
+typedef struct {
+  const or_volume* v;
+  const or_tf* tf;
+  const uint32_t* ranges; /* [node][ch][2] */
+  const uint8_t* resident;
+  int64_t off[OR_MAX_LEVELS + 1];
+  int64_t nb[OR_MAX_LEVELS][3];
+  int64_t eye[2][3];       /* 1/64 level-0 voxel */
+  int64_t plane[2][4][4];  /* A,B,C (x 2^16) and D (x 2^16 x 64), pushed out 1 voxel */
+  uint64_t K;              /* floor(tau^2 theta^2 2^40) */
+  uint8_t* own_empty;
+  uint8_t* sub_empty;
+  uint8_t* state;
+  int32_t* leaf;
+  int32_t* req;
+  int req_cap, nreq;
+} sel_t;
+
+enum { ST_UNSEEN = 0, ST_CULLED = 1, ST_EMPTY = 2, ST_SELECTED = 3, ST_FALLBACK = 4, ST_REFINED = 5 };
+
+static void node_box(const sel_t* s, int L, const int64_t* b, int64_t* lo, int64_t* hi) {
+  int64_t span = (int64_t)s->v->brick << L;
+  for (int a = 0; a < 3; ++a) {
+    int64_t l = b[a] * span, h = (b[a] + 1) * span;
+    if (h > s->v->dims[0][a]) h = s->v->dims[0][a];
+    lo[a] = l * 64;
+    hi[a] = h * 64;
+  }
+}
+
+/* Culled iff the block lies entirely outside one of the four side planes of
+ * the view pyramid of each eye (the near and far planes are not used: rays
+ * start at the eye and run to the volume's exit). */
+static int node_culled(const sel_t* s, int L, const int64_t* b) {
+  int64_t lo[3], hi[3];
+  node_box(s, L, b, lo, hi);
+  for (int e = 0; e < 2; ++e) {
+    int outside = 0;
+    for (int p = 0; p < 4 && !outside; ++p) {
+      const int64_t* P = s->plane[e][p];
+      int64_t val = P[3];
+      for (int a = 0; a < 3; ++a) val += P[a] * (P[a] >= 0 ? hi[a] : lo[a]);
+      if (val < 0) outside = 1;
+    }
+    if (!outside) return 0;
+  }
+  return 1;
+}
+
+/* Accept level L iff L == 0 or a level-L voxel (2^L level-0 voxels wide)
+ * subtends at most tau pixels at distance d, d the distance from the block's
+ * box to the nearer eye: 2^L <= tau theta d. In integers, with d in 1/64
+ * voxel: 4^L 64^2 2^40 <= K d^2, evaluated exactly in 128 bits. */
+static int node_accept(const sel_t* s, int L, const int64_t* b) {
+  if (L == 0) return 1;
+  int64_t lo[3], hi[3];
+  node_box(s, L, b, lo, hi);
+  unsigned __int128 best = 0;
+  for (int e = 0; e < 2; ++e) {
+    unsigned __int128 d2 = 0;
+    for (int a = 0; a < 3; ++a) {
+      int64_t q = s->eye[e][a], dd = 0;
+      if (q < lo[a]) dd = lo[a] - q;
+      else if (q > hi[a]) dd = q - hi[a];
+      d2 += (unsigned __int128)((uint64_t)dd) * (uint64_t)dd;
+    }
+    if (e == 0 || d2 < best) best = d2;
+  }
+  unsigned __int128 lhs = (unsigned __int128)1 << (52 + 2 * L);
+  return lhs <= (unsigned __int128)s->K * best;
+}
+
+static int64_t node_id(const sel_t* s, int L, const int64_t* b) {
+  return s->off[L] + (b[2] * s->nb[L][1] + b[1]) * s->nb[L][0] + b[0];
+}
+
+static void fill_leaf(sel_t* s, int L, const int64_t* b, int32_t id) {
+  int64_t n = (int64_t)1 << L;
+  for (int64_t z = b[2] * n; z < (b[2] + 1) * n && z < s->nb[0][2]; ++z)
+    for (int64_t y = b[1] * n; y < (b[1] + 1) * n && y < s->nb[0][1]; ++y)
+      for (int64_t x = b[0] * n; x < (b[0] + 1) * n && x < s->nb[0][0]; ++x)
+        s->leaf[(z * s->nb[0][1] + y) * s->nb[0][0] + x] = id;
+}
+
+static void visit(sel_t* s, int L, const int64_t* b) {
+  int64_t id = node_id(s, L, b);
+  if (node_culled(s, L, b)) { s->state[id] = ST_CULLED; return; }
+  if (s->sub_empty[id]) { s->state[id] = ST_EMPTY; return; }
+  if (node_accept(s, L, b)) { s->state[id] = ST_SELECTED; fill_leaf(s, L, b, (int32_t)id); return; }
+  int64_t need[8][3];
+  int nneed = 0, nmiss = 0;
+  for (int c = 0; c < 8; ++c) {
+    int64_t cb[3] = {2 * b[0] + (c & 1), 2 * b[1] + ((c >> 1) & 1), 2 * b[2] + ((c >> 2) & 1)};
+    if (cb[0] >= s->nb[L - 1][0] || cb[1] >= s->nb[L - 1][1] || cb[2] >= s->nb[L - 1][2]) continue;
+    int64_t cid = node_id(s, L - 1, cb);
+    if (node_culled(s, L - 1, cb)) { s->state[cid] = ST_CULLED; continue; }
+    if (s->sub_empty[cid]) { s->state[cid] = ST_EMPTY; continue; }
+    memcpy(need[nneed++], cb, sizeof cb);
+    if (s->resident && !s->resident[cid]) ++nmiss;
+  }
+  if (nmiss > 0) {
+    for (int i = 0; i < nneed; ++i) {
+      int64_t cid = node_id(s, L - 1, need[i]);
+      if (!s->resident[cid] && s->nreq < s->req_cap) s->req[s->nreq++] = (int32_t)cid;
+    }
+    s->state[id] = ST_FALLBACK;
+    fill_leaf(s, L, b, (int32_t)id);
+    return;
+  }
+  s->state[id] = ST_REFINED;
+  for (int i = 0; i < nneed; ++i) visit(s, L - 1, need[i]);
+}
+
+static int cmp_i32(const void* a, const void* b) {
+  int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+  return (x > y) - (x < y);
+}
+
+/* Quantised selection inputs for one eye, from FP64 copies of the FP32
+ * matrices: the eye in voxel space rounded to 1/64 voxel, and the four side
+ * planes of clip = P V M, normalised to unit normals in voxel space,
+ * A,B,C = round(n 2^16), D = round(d 2^16 64) + 2^16 64 (one voxel outward). */
+static void eye_inputs(const double* model, const double* view, const double* proj, int64_t* eye,
+                       int64_t planes[4][4]) {
+  double vm[16], vminv[16], clip[16];
+  mat_mul(view, model, vm);
+  mat_inv(vm, vminv);
+  double o[4] = {0, 0, 0, 1}, e[4];
+  mat_apply(vminv, o, e);
+  for (int a = 0; a < 3; ++a) {
+    double q = e[a] / e[3] * 64.0;
+    if (q > 68719476736.0) q = 68719476736.0;
+    if (q < -68719476736.0) q = -68719476736.0;
+    eye[a] = llround(q);
+  }
+  mat_mul(proj, vm, clip);
+  for (int p = 0; p < 4; ++p) {
+    int row = p >> 1;
+    double sg = (p & 1) ? -1.0 : 1.0;
+    double pl[4];
+    for (int k = 0; k < 4; ++k) pl[k] = clip[k * 4 + 3] + sg * clip[k * 4 + row];
+    double n = sqrt(pl[0] * pl[0] + pl[1] * pl[1] + pl[2] * pl[2]);
+    if (n < 1e-300) { planes[p][0] = planes[p][1] = planes[p][2] = 0; planes[p][3] = 1; continue; }
+    for (int k = 0; k < 3; ++k) planes[p][k] = llround(pl[k] / n * 65536.0);
+    double d = pl[3] / n;
+    if (d > 1048576.0) d = 1048576.0;
+    if (d < -1048576.0) d = -1048576.0;
+    planes[p][3] = llround(d * 65536.0 * 64.0) + 65536LL * 64LL;
+  }
+}
+
+/* view/proj: [2][16] column major (FP64 copies of FP32 inputs).
+ * leaf: one int32 per level-0 block cell, -1 where nothing is rendered.
+ * state: one byte per node (see ST_*). req: requested node ids, ascending.
+ * Returns the number of selected nodes. */
+int or_select(const or_volume* v, const or_tf* tfs, const uint32_t* ranges, const double* view,
+              const double* proj, int height, double tau, const uint8_t* resident, int32_t* leaf,
+              uint8_t* state, int32_t* req, int req_cap, int* nreq) {
+  sel_t s;
+  memset(&s, 0, sizeof s);
+  s.v = v; s.tf = tfs; s.ranges = ranges; s.resident = resident;
+  int64_t nn = or_node_count(v, s.off);
+  for (int L = 0; L < v->levels; ++L) level_blocks(v, L, s.nb[L]);
+  for (int e = 0; e < 2; ++e) eye_inputs(v->model, view + 16 * e, proj + 16 * e, s.eye[e], s.plane[e]);
+  /* pixel angle at the image centre: theta = 2 tan(fovy/2) / H = 2 / (P11 H) */
+  double theta = 2.0 / (proj[5] * (double)height);
+  double tt = tau * theta;
+  double kf = floor(tt * tt * 1099511627776.0);
+  if (!(kf >= 0.0)) kf = 0.0;
+  if (kf > 1099511627776.0) kf = 1099511627776.0;
+  s.K = (uint64_t)kf;
+
+  s.own_empty = (uint8_t*)calloc(nn, 1);
+  s.sub_empty = (uint8_t*)calloc(nn, 1);
+  s.state = state;
+  memset(state, 0, nn);
+  for (int64_t id = 0; id < nn; ++id) {
+    int e = 1;
+    for (int c = 0; c < v->nch && e; ++c)
+      e = tf_range_empty(&tfs[c], ranges[(id * v->nch + c) * 2], ranges[(id * v->nch + c) * 2 + 1]);
+    s.own_empty[id] = (uint8_t)e;
+  }
+  /* subtree emptiness: the block and all its descendants are empty */
+  for (int L = 0; L < v->levels; ++L)
+    for (int64_t bz = 0; bz < s.nb[L][2]; ++bz)
+      for (int64_t by = 0; by < s.nb[L][1]; ++by)
+        for (int64_t bx = 0; bx < s.nb[L][0]; ++bx) {
+          int64_t b[3] = {bx, by, bz};
+          int64_t id = node_id(&s, L, b);
+          int e = s.own_empty[id];
+          if (L > 0)
+            for (int c = 0; c < 8 && e; ++c) {
+              int64_t cb[3] = {2 * bx + (c & 1), 2 * by + ((c >> 1) & 1), 2 * bz + ((c >> 2) & 1)};
+              if (cb[0] >= s.nb[L - 1][0] || cb[1] >= s.nb[L - 1][1] || cb[2] >= s.nb[L - 1][2]) continue;
+              e = s.sub_empty[node_id(&s, L - 1, cb)];
+            }
+          s.sub_empty[id] = (uint8_t)e;
+        }
+  int64_t ncell = s.nb[0][0] * s.nb[0][1] * s.nb[0][2];
+  for (int64_t i = 0; i < ncell; ++i) leaf[i] = -1;
+  s.leaf = leaf; s.req = req; s.req_cap = req_cap; s.nreq = 0;
+  int top = v->levels - 1;
+  for (int64_t bz = 0; bz < s.nb[top][2]; ++bz)
+    for (int64_t by = 0; by < s.nb[top][1]; ++by)
+      for (int64_t bx = 0; bx < s.nb[top][0]; ++bx) {
+        int64_t b[3] = {bx, by, bz};
+        visit(&s, top, b);
+      }
+  qsort(req, s.nreq, sizeof(int32_t), cmp_i32);
+  *nreq = s.nreq;
+  int nsel = 0;
+  for (int64_t id = 0; id < nn; ++id) nsel += (state[id] == ST_SELECTED || state[id] == ST_FALLBACK);
+  free(s.own_empty);
+  free(s.sub_empty);
+  return nsel;
+}
+
+/* The integers the selection decides with, exposed for pins. */
+void or_select_inputs(const or_volume* v, const double* view, const double* proj, int height, double tau,
+                      int64_t* eyes /*2x3*/, int64_t* planes /*2x4x4*/, uint64_t* K) {
+  for (int e = 0; e < 2; ++e)
+    eye_inputs(v->model, view + 16 * e, proj + 16 * e, eyes + 3 * e, (int64_t(*)[4])(planes + 16 * e));
+  double theta = 2.0 / (proj[5] * (double)height);
+  double tt = tau * theta;
+  double kf = floor(tt * tt * 1099511627776.0);
+  if (!(kf >= 0.0)) kf = 0.0;
+  if (kf > 1099511627776.0) kf = 1099511627776.0;
+  *K = (uint64_t)kf;
+}
+
+/* ------------------------------------------------------------------------ */
+/* sampling and classification                                               */
+
+static inline double fetch(const or_volume* v, int L, int c, int64_t x, int64_t y, int64_t z) {
+  const int64_t* D = v->dims[L];
+  if (x < 0) x = 0; if (x > D[0] - 1) x = D[0] - 1;
+  if (y < 0) y = 0; if (y > D[1] - 1) y = D[1] - 1;
+  if (z < 0) z = 0; if (z > D[2] - 1) z = D[2] - 1;
+  return (double)vox_get(v->data[L][c], v->dtype, (z * D[1] + y) * D[0] + x);
+}
+
+/* Trilinear value of level L, channel c at p (level-0 voxel units). Voxel j
+ * of level L has its centre at (j + 0.5) 2^L; indices are clamped to the
+ * level (clamp-to-edge). The blend is the exact trilinear weighting. */
+double or_sample(const or_volume* v, int L, int c, const double* p) {
+  double s = 1.0 / (double)((int64_t)1 << L);
+  double u[3], f[3];
+  int64_t i[3];
+  for (int a = 0; a < 3; ++a) {
+    u[a] = p[a] * s - 0.5;
+    i[a] = (int64_t)floor(u[a]);
+    f[a] = u[a] - (double)i[a];
+  }
+  double acc = 0.0;
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        double w = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+        acc += w * fetch(v, L, c, i[0] + dx, i[1] + dy, i[2] + dz);
+      }
+  return acc;
+}
+
+/* Opacity-corrected table for a sample spacing of `spacing` level-0 voxels:
+ * alpha' = 1 - (1 - alpha)^(spacing / ref_step), colour unchanged. */
+void or_tf_table(const or_tf* tf, double spacing, double* out /*4n*/) {
+  double e = spacing / (double)tf->ref_step;
+  for (int i = 0; i < tf->n; ++i) {
+    for (int k = 0; k < 3; ++k) out[4 * i + k] = tf->rgba[4 * i + k];
+    out[4 * i + 3] = 1.0 - pow(1.0 - (double)tf->rgba[4 * i + 3], e);
+  }
+}
+
+/* Classification: x = clamp((v - lo)/(hi - lo), 0, 1), q = x (n-1), linear
+ * interpolation between entries floor(q) and floor(q)+1 (clamped). */
+void or_classify(const or_tf* tf, const double* table, double value, double* rgba) {
+  double x = (value - (double)tf->lo) / ((double)tf->hi - (double)tf->lo);
+  if (x < 0.0) x = 0.0;
+  if (x > 1.0) x = 1.0;
+  double q = x * (double)(tf->n - 1);
+  int i = (int)floor(q);
+  if (i > tf->n - 1) i = tf->n - 1;
+  int i1 = i + 1 > tf->n - 1 ? tf->n - 1 : i + 1;
+  double f = q - (double)i;
+  for (int k = 0; k < 4; ++k) rgba[k] = table[4 * i + k] * (1.0 - f) + table[4 * i1 + k] * f;
+}
+
+/* ------------------------------------------------------------------------ */
+/* ray casting                                                               */
+
+enum { FL_FACE = 1, FL_TEDGE = 2, FL_TERM = 4 };
+
+typedef struct {
+  const or_volume* v;
+  const or_tf* tf;
+  const int32_t* leaf;
+  int64_t nb0[3];
+  int64_t off[OR_MAX_LEVELS + 1];
+  double* table[OR_MAX_LEVELS][OR_MAX_CH];
+  double inv[16]; /* (P V M)^-1 */
+  double eye[3];
+  int W, H;
+  double step, term, term_tol, eps;
+} ray_t;
+
+static int node_level(const ray_t* r, int32_t id) {
+  if (id < 0) return -1;
+  int L = 0;
+  while (L + 1 < r->v->levels && id >= r->off[L + 1]) ++L;
+  return L;
+}
+
+static int32_t cell_at(const ray_t* r, const int64_t* c) {
+  return r->leaf[(c[2] * r->nb0[1] + c[1]) * r->nb0[0] + c[0]];
+}
+
+static void cell_of(const ray_t* r, const double* p, double shift, const int* dirs, int64_t* c) {
+  for (int a = 0; a < 3; ++a) {
+    int64_t q = (int64_t)floor((p[a] + shift * dirs[a]) / (double)r->v->brick);
+    if (q < 0) q = 0;
+    if (q > r->nb0[a] - 1) q = r->nb0[a] - 1;
+    c[a] = q;
+  }
+}
+
+/* One ray, FP64. Two compositing results bracket the termination decision:
+ * "early" stops after the first sample with A >= term - term_tol, "late"
+ * after the first with A >= term + term_tol (they differ only when a sample
+ * lands within term_tol of the threshold). Flags mark pixels where an FP32
+ * implementation may legitimately assign a sample differently: a sample
+ * within eps of a face between cells rendered at different levels (FL_FACE),
+ * a sample within eps of the volume exit (FL_TEDGE), or a differing
+ * termination (FL_TERM). */
+static void cast(const ray_t* r, int64_t pix, double* early, double* late, uint32_t* ne, uint32_t* nl,
+                 uint8_t* flag) {
+  int i = (int)(pix % r->W), j = (int)(pix / r->W);
+  double x = 2.0 * (i + 0.5) / r->W - 1.0, y = 1.0 - 2.0 * (j + 0.5) / r->H;
+  double pn[4] = {x, y, -1.0, 1.0}, pf[4] = {x, y, 1.0, 1.0}, a[4], b[4];
+  mat_apply(r->inv, pn, a);
+  mat_apply(r->inv, pf, b);
+  double d[3], dn = 0.0;
+  for (int k = 0; k < 3; ++k) { d[k] = b[k] / b[3] - a[k] / a[3]; dn += d[k] * d[k]; }
+  dn = sqrt(dn);
+  for (int k = 0; k < 3; ++k) d[k] /= dn;
+  const double* o = r->eye;
+  double tn = -INFINITY, tf = INFINITY;
+  uint8_t fl = 0;
+  for (int k = 0; k < 3; ++k) {
+    double N = (double)r->v->dims[0][k];
+    if (d[k] == 0.0) {
+      if (o[k] < 0.0 || o[k] > N) { tf = -INFINITY; break; }
+      continue;
+    }
+    double t1 = (0.0 - o[k]) / d[k], t2 = (N - o[k]) / d[k];
+    if (t1 > t2) { double t = t1; t1 = t2; t2 = t; }
+    if (t1 > tn) tn = t1;
+    if (t2 < tf) tf = t2;
+  }
+  double t0 = tn > 0.0 ? tn : 0.0, t1 = tf;
+  double C[3] = {0, 0, 0}, A = 0.0, Ce[3] = {0, 0, 0}, Ae = 0.0;
+  uint32_t cnt = 0, cnte = 0;
+  int early_done = 0;
+  if (t1 > t0) {
+    if (fabs(tn) < r->eps) fl |= FL_TEDGE;
+    int nch = r->v->nch;
+    for (int64_t k = 0;; ++k) {
+      double t = t0 + (double)k * r->step;
+      if (t >= t1) {
+        if (t - t1 < r->eps) fl |= FL_TEDGE;
+        break;
+      }
+      if (t1 - t < r->eps) fl |= FL_TEDGE;
+      double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
+      int zero[3] = {0, 0, 0};
+      int64_t cell[3];
+      cell_of(r, p, 0.0, zero, cell);
+      int32_t id = cell_at(r, cell);
+      int L = node_level(r, id);
+      /* face proximity: the cells within eps of p, all sign combinations */
+      if (!(fl & FL_FACE)) {
+        int near_ax[3], nnear = 0;
+        for (int ax = 0; ax < 3; ++ax) {
+          double fr = p[ax] / (double)r->v->brick;
+          double dist = fabs(fr - floor(fr + 0.5)) * (double)r->v->brick;
+          near_ax[ax] = dist < r->eps;
+          nnear += near_ax[ax];
+        }
+        if (nnear) {
+          int used = (L >= 0 && (k & (((int64_t)1 << L) - 1)) == 0);
+          int differs = 0;
+          for (int m = 0; m < 8; ++m) {
+            int dirs[3];
+            int skip = 0;
+            for (int ax = 0; ax < 3; ++ax) {
+              dirs[ax] = (m >> ax) & 1 ? 1 : -1;
+              if (!near_ax[ax] && ((m >> ax) & 1)) skip = 1;
+              if (!near_ax[ax]) dirs[ax] = 0;
+            }
+            if (skip) continue;
+            int64_t c2[3];
+            cell_of(r, p, r->eps, dirs, c2);
+            int32_t id2 = cell_at(r, c2);
+            int L2 = node_level(r, id2);
+            if (L2 != L) differs = 1;
+            if (L2 >= 0 && (k & (((int64_t)1 << L2) - 1)) == 0) used = 1;
+          }
+          if (differs && used) fl |= FL_FACE;
+        }
+      }
+      if (L < 0 || (k & (((int64_t)1 << L) - 1)) != 0) continue;
+      /* classify every channel, blend additively (alpha capped at 1) */
+      double sa = 0.0, sc[3] = {0, 0, 0};
+      for (int c = 0; c < nch; ++c) {
+        double val = or_sample(r->v, L, c, p), rgba[4];
+        or_classify(&r->tf[c], r->table[L][c], val, rgba);
+        sa += rgba[3];
+        for (int q = 0; q < 3; ++q) sc[q] += rgba[3] * rgba[q];
+      }
+      double as = sa < 1.0 ? sa : 1.0;
+      double scale = sa > 0.0 ? as / (sa > as ? sa : as) : 0.0;
+      for (int q = 0; q < 3; ++q) C[q] += (1.0 - A) * sc[q] * scale;
+      A += (1.0 - A) * as;
+      ++cnt;
+      if (!early_done && A >= r->term - r->term_tol) {
+        early_done = 1;
+        memcpy(Ce, C, sizeof C);
+        Ae = A;
+        cnte = cnt;
+      }
+      if (A >= r->term + r->term_tol) break;
+    }
+  }
+  if (!early_done) { memcpy(Ce, C, sizeof C); Ae = A; cnte = cnt; }
+  if (cnte != cnt) fl |= FL_TERM;
+  for (int q = 0; q < 3; ++q) { early[q] = Ce[q]; late[q] = C[q]; }
+  early[3] = Ae;
+  late[3] = A;
+  *ne = cnte;
+  *nl = cnt;
+  *flag = fl;
+}
+
+/* Render the pixels pix[0..npix) (row-major ids j*W+i, row 0 = top; NULL
+ * means every pixel) of one eye. leaf comes from or_select. step is the
+ * level-0 sample spacing; level L samples every 2^L-th lattice point
+ * t0 + k step, k >= 0, anchored at the volume entry t0. Returns 0 on a
+ * singular matrix. nthreads <= 0 uses every core. */
+int or_render(const or_volume* v, const or_tf* tfs, const int32_t* leaf, const double* view,
+              const double* proj, int W, int H, double step, double term, double term_tol, double eps,
+              const int64_t* pix, int64_t npix, double* rgba_early, double* rgba_late, uint32_t* cnt_early,
+              uint32_t* cnt_late, uint8_t* flags, int nthreads) {
+  ray_t r;
+  memset(&r, 0, sizeof r);
+  r.v = v; r.tf = tfs; r.leaf = leaf; r.W = W; r.H = H;
+  r.step = step; r.term = term; r.term_tol = term_tol; r.eps = eps;
+  or_node_count(v, r.off);
+  level_blocks(v, 0, r.nb0);
+  double vm[16], pvm[16], vminv[16];
+  mat_mul(view, v->model, vm);
+  mat_mul(proj, vm, pvm);
+  if (!mat_inv(pvm, r.inv) || !mat_inv(vm, vminv)) return 0;
+  double o[4] = {0, 0, 0, 1}, e[4];
+  mat_apply(vminv, o, e);
+  for (int k = 0; k < 3; ++k) r.eye[k] = e[k] / e[3];
+  for (int L = 0; L < v->levels; ++L)
+    for (int c = 0; c < v->nch; ++c) {
+      r.table[L][c] = (double*)malloc(sizeof(double) * 4 * tfs[c].n);
+      or_tf_table(&tfs[c], step * (double)((int64_t)1 << L), r.table[L][c]);
+    }
+  int64_t n = pix ? npix : (int64_t)W * H;
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t q = 0; q < n; ++q) {
+    int64_t id = pix ? pix[q] : q;
+    cast(&r, id, rgba_early + 4 * q, rgba_late + 4 * q, cnt_early + q, cnt_late + q, flags + q);
+  }
+  for (int L = 0; L < v->levels; ++L)
+    for (int c = 0; c < v->nch; ++c) free(r.table[L][c]);
+  return 1;
+}
+
+int or_max_threads(void) { return omp_get_max_threads(); }

@@ -1,0 +1,201 @@
+"""Pins of the FP64 oracle against closed forms, brute force and hand-derived
+values (CPU only). Each test names the property of the paper's method it
+fixes; none re-types the oracle's own code."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _axial_camera(eye_z, cx=2.0, cy=2.0, fovy=90.0, size=9):
+    view = synth.colmajor(synth.look_at([cx, cy, eye_z], [cx, cy, 0.0], [0.0, 1.0, 0.0]))
+    proj = synth.colmajor(synth.perspective(fovy, 1.0, 0.1, 1000.0))
+    return view, proj
+
+
+def _const_tf(rgb, a, n=256, lo=0.0, hi=255.0, ref=0.5):
+    tab = np.tile(np.array([*rgb, a], np.float32), (n, 1))
+    return oracle.make_tf(tab, lo, hi, ref)
+
+
+def _render_centre(vol, tfs, view, proj, size=9, step=0.5, brick=None):
+    sel = vol.select(tfs, [view, view], [proj, proj], size, tau=1.0)
+    c = (size // 2) * size + size // 2
+    return vol.render(tfs, sel["leaf"], view, proj, size, size, step=step, pixels=[c])
+
+
+# ---------------------------------------------------------------- pyramid (Octree Representation)
+
+@pytest.mark.parametrize("shape,dtype", [((7, 13, 10), np.uint16), ((5, 4, 9), np.uint8), ((1, 3, 2), np.uint16)])
+def test_pyramid_matches_brute_force_box_filter(shape, dtype):
+    rng = np.random.default_rng(7)
+    hi = 65535 if dtype == np.uint16 else 255
+    a = rng.integers(0, hi + 1, shape).astype(dtype)
+    levels = oracle.pyramid(a, 3)
+    ref = a.astype(np.int64)
+    for L in range(1, 3):
+        # brute force: replicate the last plane along odd axes, then average 2x2x2 blocks
+        pad = [(0, s % 2) for s in ref.shape]
+        e = np.pad(ref, pad, mode="edge")
+        z, y, x = (s // 2 for s in e.shape)
+        s = e.reshape(z, 2, y, 2, x, 2).sum(axis=(1, 3, 5))
+        ref = (s + 4) // 8
+        assert levels[L].shape == ref.shape
+        assert np.array_equal(levels[L].astype(np.int64), ref)
+
+
+def test_block_ranges_cover_the_apron():
+    rng = np.random.default_rng(3)
+    a = rng.integers(0, 60000, (20, 17, 33)).astype(np.uint16)
+    B = 8
+    vol = oracle.Volume([oracle.pyramid(a, 2)], B)
+    r = vol.block_ranges()
+    for L in range(2):
+        g = vol.channels[0][L]
+        nbx, nby, nbz = vol.blocks_per_axis(L)
+        for bz in range(nbz):
+            for by in range(nby):
+                for bx in range(nbx):
+                    sl = tuple(slice(max(b * B - 1, 0), min(b * B + B + 1, n))
+                               for b, n in zip((bz, by, bx), g.shape))
+                    node = vol.level_offsets[L] + (bz * nby + by) * nbx + bx
+                    assert r[node, 0, 0] == g[sl].min() and r[node, 0, 1] == g[sl].max()
+
+
+# ---------------------------------------------------------------- trilinear sampling (DVR Techniques)
+
+def test_trilinear_reproduces_linear_fields_at_two_levels():
+    nz, ny, nx = 10, 12, 16
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    lvl0 = (3 * i + 5 * j + 7 * k + 11).astype(np.uint16)
+    k1, j1, i1 = np.meshgrid(np.arange(5), np.arange(6), np.arange(8), indexing="ij")
+    lvl1 = (13 * i1 + 2 * j1 + 29 * k1 + 100).astype(np.uint16)
+    vol = oracle.Volume([[lvl0, lvl1]], 8)
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        p = rng.uniform(-1.0, [nx + 1.0, ny + 1.0, nz + 1.0])
+        u = np.clip(p - 0.5, 0.0, [nx - 1, ny - 1, nz - 1])  # clamp-to-edge beyond the last centres
+        assert vol.sample(0, 0, p) == pytest.approx(3 * u[0] + 5 * u[1] + 7 * u[2] + 11, abs=1e-9)
+        u1 = np.clip(p / 2.0 - 0.5, 0.0, [7, 5, 4])  # level-1 voxel j is centred at (j+0.5)*2
+        assert vol.sample(1, 0, p) == pytest.approx(13 * u1[0] + 2 * u1[1] + 29 * u1[2] + 100, abs=1e-9)
+
+
+# ---------------------------------------------------------------- transfer function
+
+def test_classification_of_a_linear_ramp_is_the_window_position():
+    n = 256
+    ramp = np.stack([np.linspace(0, 1, n)] * 4, 1).astype(np.float32)
+    tf = oracle.make_tf(ramp, 1000.0, 3000.0)
+    tab = oracle.tf_table(tf, 0.5)
+    for v, x in [(0.0, 0.0), (1000.0, 0.0), (2000.0, 0.5), (2500.0, 0.75), (3000.0, 1.0), (65535.0, 1.0)]:
+        assert oracle.classify(tf, tab, v) == pytest.approx([x] * 4, abs=1e-6)
+
+
+def test_opacity_correction_composes_like_repeated_samples():
+    a = np.linspace(0, 0.9, 256).astype(np.float32)
+    tab = np.stack([a, a, a, a], 1)
+    tf = oracle.make_tf(tab, 0.0, 255.0, ref_step=0.5)
+    t1 = oracle.tf_table(tf, 0.5)
+    t4 = oracle.tf_table(tf, 2.0)
+    # one sample over 4 reference steps transmits what 4 samples transmit
+    assert np.allclose(1.0 - t4[:, 3], (1.0 - t1[:, 3]) ** 4, atol=1e-12)
+    assert np.allclose(t1[:, :3], tab[:, :3])
+
+
+# ---------------------------------------------------------------- compositing: closed forms
+
+def test_constant_volume_is_beer_lambert_with_opacity_correction():
+    n = 16
+    vol = oracle.Volume([[np.full((n, n, n), 100, np.uint8)]], n)
+    a = float(np.float32(0.05))  # the table holds FP32 values
+    rgb = tuple(float(np.float32(c)) for c in (0.2, 0.5, 0.8))
+    tf = _const_tf(rgb, a)
+    view, proj = _axial_camera(40.0, cx=8.0, cy=8.0)
+    # step 0.3: samples t0 + 0.3k < t0 + 16 -> k = 0..53 (54 samples), each
+    # with alpha' = 1 - (1-a)^(0.3/0.5)
+    r = _render_centre(vol, [tf], view, proj, step=0.3)
+    A = 1.0 - (1.0 - a) ** (0.6 * 54)
+    assert r["count_late"][0] == 54 and r["flags"][0] == 0
+    assert r["late"][0] == pytest.approx([rgb[0] * A, rgb[1] * A, rgb[2] * A, A], abs=1e-12)
+
+
+def test_constant_volume_terminates_at_0_99():
+    n = 16
+    vol = oracle.Volume([[np.full((n, n, n), 100, np.uint8)]], n)
+    tf = _const_tf((1.0, 1.0, 1.0), 0.2)
+    view, proj = _axial_camera(40.0, cx=8.0, cy=8.0)
+    r = _render_centre(vol, [tf], view, proj, step=0.5)
+    # 1 - 0.8^20 = 0.98847 < 0.99 <= 1 - 0.8^21 = 0.99078
+    a = float(np.float32(0.2))
+    assert r["count_late"][0] == 21
+    assert r["late"][0][3] == pytest.approx(1.0 - (1.0 - a) ** 21, abs=1e-12)
+
+
+def test_step_refinement_with_correction_keeps_opacity():
+    n = 16
+    vol = oracle.Volume([[np.full((n, n, n), 100, np.uint8)]], n)
+    tf = _const_tf((0.3, 0.3, 0.3), 0.03)
+    view, proj = _axial_camera(40.3, cx=8.0, cy=8.0)  # entry at t0 = 24.3, exit 40.3 (no lattice point on it)
+    r1 = _render_centre(vol, [tf], view, proj, step=0.4)   # 40 samples
+    r2 = _render_centre(vol, [tf], view, proj, step=0.2)   # 80 samples
+    assert r1["count_late"][0] * 2 == r2["count_late"][0] == 80
+    assert r1["late"][0] == pytest.approx(r2["late"][0], abs=1e-12)
+
+
+def test_empty_volume_and_transparent_tf_give_background():
+    n = 16
+    vol = oracle.Volume([[np.zeros((n, n, n), np.uint8)]], 8)
+    tf = _const_tf((1, 1, 1), 0.0)
+    view, proj = synth.orbit_camera(n=n, seed=5, width=17, height=17)
+    sel = vol.select([tf], [view, view], [proj, proj], 17)
+    assert (sel["leaf"] == -1).all() and sel["selected"] == 0
+    r = vol.render([tf], sel["leaf"], view, proj, 17, 17)
+    assert not r["late"].any() and not r["count_late"].any()
+
+
+@pytest.mark.parametrize("case", json.load(open(os.path.join(GOLDEN, "hand_4cubed.json")))["cases"],
+                         ids=lambda c: c["name"])
+def test_hand_computed_4cubed_cases(case):
+    chans = []
+    tfs = []
+    for planes, e1 in zip(case["planes"], case["tf_entry1"]):
+        v = np.zeros((4, 4, 4), np.uint8)
+        for k in planes:
+            v[k] = 255
+        chans.append([v])
+        tfs.append(oracle.make_tf(np.array([[0, 0, 0, 0], e1], np.float32), 0.0, 255.0))
+    vol = oracle.Volume(chans, 4)
+    view, proj = _axial_camera(10.0)
+    r = _render_centre(vol, tfs, view, proj)
+    assert r["count_late"][0] == case["samples"]
+    # the hand values use exact decimals; the table stores them as FP32 (relative error <= 6e-8)
+    assert r["late"][0] == pytest.approx(case["rgba"], abs=1e-7)
+
+
+# ---------------------------------------------------------------- symmetry
+
+def test_stereo_mirror_symmetry():
+    n = 32
+    rng = np.random.default_rng(11)
+    half = rng.integers(0, 255, (n, n, n // 2)).astype(np.uint8)
+    v = np.concatenate([half, half[:, :, ::-1]], axis=2)  # v[z,y,x] = v[z,y,n-1-x]
+    vol = oracle.Volume([oracle.pyramid(v, 2)], 8)
+    tf = oracle.make_tf(synth.tf_piecewise(4), 0.0, 255.0)
+    W = H = 24
+    proj = synth.colmajor(synth.perspective(60.0, 1.0, 0.1, 500.0))
+    views = [synth.colmajor(synth.look_at([n / 2 + s * 6.0, n / 2 + 3.0, 70.0], [n / 2 + s * 6.0, n / 2 + 3.0, 0.0],
+                                          [0, 1, 0])) for s in (-1.0, 1.0)]
+    sel = vol.select([tf], views, [proj, proj], H, tau=8.0)
+    assert sel["selected"] > 1
+    left = vol.render([tf], sel["leaf"], views[0], proj, W, H)
+    right = vol.render([tf], sel["leaf"], views[1], proj, W, H)
+    L = left["late"].reshape(H, W, 4)
+    R = right["late"].reshape(H, W, 4)[:, ::-1]
+    assert np.abs(L - R).max() < 1e-9
+    assert np.array_equal(left["count_late"].reshape(H, W), right["count_late"].reshape(H, W)[:, ::-1])
