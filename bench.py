@@ -1,0 +1,326 @@
+"""Stereo DVR throughput of the B300 library on the bricked multi-LOD workload.
+
+Workload (one "step" = one stereo frame: LOD/residency selection + ray casting
+of both eyes for one head pose): a 1024^3 uint16 volume of 200 seeded
+Catmull-Rom filaments (radius 2-6, intensity 2000-60000) over a Poisson(300)
+background, 64^3 bricks with a one-voxel apron, 4 pyramid levels; 64 seeded
+head poses (0.3-1.0 m from a 0.5 m volume, 64 mm IPD, 100 deg fovy), two
+1440x1600 eyes, step 0.5 voxel, tau 1 pixel, early termination at 0.99.
+Synthetic data; the brick pool (2.7 GB) is far larger than L2, and every step
+renders a different pose.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun each rank renders its own poses
+(replicas, weak scaling); timing is the max over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "stereo fps @2x1440x1600 + Gsamples/s; learned vs plain fps at >=40 dB PSNR"
+W_EYE, H_EYE = 1440, 1600
+N_VOX, BRICK, LEVELS, NPOSES = 1024, 64, 4, 64
+SEEDS = dict(volume=1002, tf=2002, poses=3002)
+WINDOW = (300.0, 60000.0)
+STEP, TAU, TERM = 0.5, 1.0, 0.99
+WORKLOAD = ("bricked multi-LOD stereo: 1024^3 u16 filaments, 64^3 bricks + apron, 4 levels, "
+            "64 head poses, 2x1440x1600, step 0.5, tau 1 px")
+
+
+def workload_config(extra=None):
+    c = {"workload": WORKLOAD, "volume": [N_VOX] * 3, "dtype_voxels": "u16", "brick": BRICK, "apron": 1,
+         "lod_levels": LEVELS, "poses": NPOSES, "eye": [W_EYE, H_EYE], "step_voxels": STEP, "tau_px": TAU,
+         "term_alpha": TERM, "l2": "inputs larger than L2 (2.7 GB brick pool, a different pose every step)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def make_inputs():
+    import synth
+    vol = synth.filaments_u16((N_VOX,) * 3, seed=SEEDS["volume"])
+    tf = synth.tf_piecewise(SEEDS["tf"], zero_alpha_points=2)
+    poses = synth.head_poses(NPOSES, seed=SEEDS["poses"], width=W_EYE, height=H_EYE)
+    model = synth.volume_model(N_VOX, 0.5)
+    return vol, tf, poses, model
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def cpu_baseline(vol, tf_table, poses, model, frac_target_s=15.0):
+    """The FP64 oracle, as it stands, on a bounded pixel sample of pose 0."""
+    import oracle
+    t_setup = time.perf_counter()
+    ovol = oracle.Volume([oracle.pyramid(vol, LEVELS)], BRICK, model=model)
+    otf = oracle.make_tf(tf_table, *WINDOW)
+    views, projs = poses[0]
+    setup_s = time.perf_counter() - t_setup
+    npix = W_EYE * H_EYE
+    stride = 256
+    t0 = time.perf_counter()
+    sel = ovol.select([otf], views, projs, H_EYE, tau=TAU)
+    samples = 0
+    for e in range(2):
+        pix = np.arange(e * 7, npix, stride)
+        r = ovol.render([otf], sel["leaf"], views[e], projs[e], W_EYE, H_EYE, step=STEP, pixels=pix)
+        samples += int(r["count_late"].sum())
+    dt = time.perf_counter() - t0
+    frac = 1.0 / stride
+    return {"value": round(frac / dt, 6), "unit": "stereo frames/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"pose 0, every {stride}th pixel of both eyes ({2 * npix // stride} rays) + selection; "
+                      f"{samples} samples in {dt:.2f} s = {samples / dt / 1e6:.1f} Msamples/s; "
+                      f"fps extrapolated from the pixel fraction",
+            "msamples_per_s": round(samples / dt / 1e6, 3), "setup_s": round(setup_s, 2)}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle on the host cores, bounded sample per step."""
+    if rank != 0:
+        return
+    import oracle
+    vol, tf_table, poses, model = make_inputs()
+    ovol = oracle.Volume([oracle.pyramid(vol, LEVELS)], BRICK, model=model)
+    otf = oracle.make_tf(tf_table, *WINDOW)
+    stride = 1024
+    npix = W_EYE * H_EYE
+
+    def step(i):
+        views, projs = poses[i % NPOSES]
+        sel = ovol.select([otf], views, projs, H_EYE, tau=TAU)
+        s = 0
+        for e in range(2):
+            r = ovol.render([otf], sel["leaf"], views[e], projs[e], W_EYE, H_EYE, step=STEP,
+                            pixels=np.arange((i * 13 + e * 7) % stride, npix, stride))
+            s += int(r["count_late"].sum())
+        return s
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    samples = 0
+    for i in range(args.steps):
+        samples += step(args.warmup + i)
+    dt = time.perf_counter() - t0
+    frames = args.steps / stride
+    fps = frames / dt
+    line = {"metric": METRIC, "value": round(fps, 6), "unit": "stereo frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": workload_config({"sample": f"every {stride}th pixel of both eyes per step"}),
+            "gsamples_per_s": round(samples / dt / 1e9, 6),
+            "cpu_baseline": {"value": round(fps, 6), "unit": "stereo frames/s", "cores": oracle.max_threads(),
+                             "kind": "oracle",
+                             "sample": f"each step: pose i, every {stride}th pixel of both eyes + selection; "
+                                       "fps extrapolated from the pixel fraction"},
+            "e2e": {"value": round(fps, 6), "unit": "stereo frames/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1804_08197_b300 import sg
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    vol_host, tf_table, poses, model = make_inputs()
+    vol = sg.sg_volume_create((N_VOX,) * 3, sg.SG_U16, BRICK, LEVELS, model=model)
+    d0 = torch.from_numpy(vol_host.view(np.int16)).to(dev)
+    sg.sg_upload_volume_device(vol, 0, 0, d0.data_ptr())
+    torch.cuda.synchronize()
+    del d0
+    sg.sg_set_transfer_function(vol, 0, tf_table, *WINDOW)
+    stream = torch.cuda.current_stream()
+    outs = [torch.empty((H_EYE, W_EYE, 4), dtype=torch.float32, device=dev) for _ in range(2)]
+    total = torch.zeros(1, dtype=torch.int64, device=dev)
+    pose_objs = [sg.make_pose(v, p, W_EYE, H_EYE, pixel_error=TAU, slot=0) for v, p in poses]
+    mine = [pose_objs[(rank + world * i) % NPOSES] for i in range(NPOSES)]
+    prm = sg.render_params(step=STEP, term_alpha=TERM, empty_skip=1, sample_total=total)
+
+    def step(i, ev=None):
+        p = mine[i % NPOSES]
+        sg.sg_select_lod(vol, p, stream=stream)
+        if ev is not None:
+            ev[0].record(stream)
+        sg.sg_render(vol, p, prm, outs, stream=stream)
+        if ev is not None:
+            ev[1].record(stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    total.zero_()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    rev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i, rev[i])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    render_ms = [a.elapsed_time(b) for a, b in rev]
+    samples = int(total.item())
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+
+    # algorithmic bytes of the render launches (outside the timed region):
+    # distinct non-transparent selected bricks + the two output images
+    brick_bytes = (BRICK + 2) ** 3 * 2
+    out_bytes = 2 * W_EYE * H_EYE * 16
+    alg = []
+    for i in range(args.steps):
+        st = sg.sg_select_lod(vol, mine[(args.warmup + i) % NPOSES], stats=True, stream=stream)
+        alg.append(st["nonempty"] * brick_bytes + out_bytes)
+    sel_stats = st
+    peak, peak_kind = measured_peak_hbm()
+    avg_render_s = sum(render_ms) / len(render_ms) / 1e3
+    achieved = (sum(alg) / len(alg)) / avg_render_s / 1e9
+
+    # end to end through the public C ABI with host buffers: pose in, both images out
+    host = [torch.empty((H_EYE, W_EYE, 4), dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    e2e_steps = max(4, min(args.steps, 16))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        p = mine[i % NPOSES]
+        sg.sg_select_lod(vol, p, stream=stream)
+        sg.sg_render_host(vol, p, prm, host, stream=stream)
+    e2e_s = time.perf_counter() - t0
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(vol_host, tf_table, poses, model)
+
+    if rank == 0:
+        fps = args.steps * world / (ms_max / 1e3)
+        line = {"metric": METRIC, "value": round(fps, 3), "unit": "stereo frames/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": workload_config({"parallelism": f"replicas x{world}"}),
+                "gsamples_per_s": round(samples * world / (ms_max / 1e3) / 1e9, 3),
+                "samples_per_step": samples // args.steps,
+                "render_ms_mean": round(sum(render_ms) / len(render_ms), 4),
+                "gpu_launches": 2 * args.steps,
+                "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                             "frac": round(achieved / peak, 5), "traffic": None,
+                             "kernel": "k_render", "peak_source": peak_kind,
+                             "algorithmic_bytes_per_launch": int(sum(alg) / len(alg))},
+                "clocks": clk,
+                "e2e": {"value": round(e2e_s and e2e_steps / e2e_s, 3), "unit": "stereo frames/s",
+                        "h2d_bytes_per_step": int(np.dtype(np.uint8).itemsize * len(bytes(mine[0]))),
+                        "d2h_bytes_per_step": out_bytes},
+                "select_stats_last": sel_stats}
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    sg.sg_volume_destroy(vol)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=64)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

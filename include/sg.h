@@ -1,0 +1,231 @@
+/* sg.h: C ABI of the B300 direct-volume-rendering library.
+ *
+ * The library renders bricked, multi-resolution 8/16-bit volumes by per-pixel
+ * ray casting under the emission-absorption optical model, as a stereo pair
+ * per head pose. It follows the "Volume Rendering" section of syGlass
+ * (arXiv:1804.08197):
+ *   - "DVR Techniques": one ray per pixel, sampled at a fixed step, trilinear
+ *     interpolation, transfer function, emission-absorption compositing with
+ *     early ray termination;
+ *   - "Octree Representation": blocks in a multi-resolution pyramid, chosen
+ *     top-down by comparing the block's angular voxel size with the pixel
+ *     angle, front to back, with frustum culling and a one-level-coarser
+ *     fallback while children are not cached;
+ *   - "Volumetric Data Cashing": a GPU brick cache with least-recently-used
+ *     eviction by timestamp.
+ *
+ * Conventions shared by every call
+ *  - Every call returns sg_status; no exception crosses the ABI. On failure,
+ *    sg_last_error() returns a thread-local message naming the cause.
+ *  - "stream" is a cudaStream_t (NULL = the legacy default stream). Calls that
+ *    take a stream enqueue their GPU work on it and return without waiting,
+ *    unless stated otherwise.
+ *  - Matrices are 4x4 float, column major, OpenGL conventions (clip z in
+ *    [-1, 1]). Voxel space is [0, N]^3 in level-0 voxels, voxel i has its
+ *    centre at i + 0.5; the model matrix maps voxel space to world space.
+ *  - Images are row-major RGBA float32, row 0 = top, colour premultiplied by
+ *    alpha (associated colour), background (0, 0, 0, 0).
+ *  - Host arrays are owned by the caller and only read during the call
+ *    (asynchronous uploads read them until the stream reaches the copy:
+ *    keep them alive and unchanged until then; pinned memory makes the copy
+ *    asynchronous). Device output buffers are owned by the caller. All other
+ *    device memory (brick pool, page tables, transfer functions, selections)
+ *    is owned by the volume and released by sg_volume_destroy.
+ */
+#ifndef SG_H
+#define SG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SG_OK = 0,
+  SG_ERR_INVALID_ARG = 1, /* a pointer, size, index or enum is out of range */
+  SG_ERR_OOM = 2,         /* a device or pinned-host allocation failed; no state was changed */
+  SG_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error string) */
+  SG_ERR_NOT_RESIDENT = 4,/* a brick the call needs is not in the device cache */
+  SG_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  SG_ERR_STATE = 6        /* calls out of order (e.g. render before select, TF missing) */
+} sg_status;
+
+typedef enum { SG_U8 = 1, SG_U16 = 2 } sg_dtype;
+
+typedef struct sg_volume sg_volume; /* opaque, owned by the library */
+
+/* Volume description ("Octree Representation": blocks of a multi-resolution
+ * pyramid). Level 0 has dims; level L+1 has ceil(N_L / 2) voxels per axis and
+ * is the 2x box filter of level L: floor((sum of the 8 children + 4) / 8),
+ * children beyond the edge replicated. A block (brick) of level L covers
+ * level-L voxels [b B, (b+1) B) per axis and is stored with a one-voxel apron
+ * on every side ((B+2)^3 voxels, x fastest), apron voxels taken from the
+ * neighbours or replicated at the volume edge. Node ids number the blocks
+ * level by level from 0, x fastest within a level. */
+typedef struct {
+  int32_t dims[3];            /* level-0 voxels x, y, z (>= 1) */
+  int32_t dtype;              /* SG_U8 or SG_U16 */
+  int32_t channels;           /* 1..4, blended additively */
+  int32_t timepoints;         /* >= 1 (3D movies) */
+  int32_t brick_size;         /* B: multiple of 8, 8..256 */
+  int32_t apron;              /* must be 1 */
+  int32_t lod_levels;         /* 1..16 */
+  int32_t reserved;
+  uint64_t device_pool_bytes; /* 0: every brick of every level resident; else the
+                                 brick cache budget (bricks stream in by LRU) */
+  float model[16];            /* voxel space -> world, column major; uniform scale */
+} sg_volume_desc;
+
+/* Creates a volume and allocates its page tables. With device_pool_bytes == 0
+ * the brick pool holds every brick; otherwise it holds as many brick groups
+ * (all channels of one brick) as fit the budget, and the coarsest level of
+ * every time point must fit. Errors: INVALID_ARG (bad desc), OOM. */
+sg_status sg_volume_create(const sg_volume_desc* desc, sg_volume** out);
+
+/* Waits for the volume's work and frees everything it owns. NULL is a no-op. */
+sg_status sg_volume_destroy(sg_volume* vol);
+
+/* Ingest from a device array: dev_level0 holds the whole level-0 volume of
+ * time point t, channel c (dims[0]*dims[1]*dims[2] voxels of dtype, x
+ * fastest, caller-owned device memory). The library builds levels
+ * 1..lod_levels-1 with the box filter, packs every brick with its apron into
+ * the pool and records each brick's value range (min/max over the brick and
+ * its apron) and the ranges of its 8^3-voxel sub-blocks. Only valid when
+ * every brick is resident (device_pool_bytes == 0). Temporary device memory:
+ * about 1/7 of the level-0 bytes, released before return. Errors:
+ * INVALID_ARG, STATE (pooled volume), OOM, CUDA. */
+sg_status sg_upload_volume_device(sg_volume* vol, int t, int c, const void* dev_level0, void* stream);
+
+/* Ingest of ready bricks from host memory (the container's "already memory
+ * aligned" chunks, "Volumetric Data Storage"): n bricks of one (t, c, level),
+ * brick i at block coordinates brick_xyz[3i..3i+2], each (B+2)^3 voxels with
+ * its apron, x fastest, stored back to back in host. Bricks not yet cached
+ * get a pool slot (evicting the least recently used unpinned brick groups
+ * when the pool is full). The brick's value ranges are recomputed on the GPU.
+ * Errors: INVALID_ARG, OOM (pool full of bricks in use this frame), CUDA. */
+sg_status sg_upload_bricks(sg_volume* vol, int t, int c, int level, int n, const int32_t* brick_xyz,
+                           const void* host, void* stream);
+
+/* Transfer function of channel c ("DVR Techniques": tau for colour, T for
+ * opacity; "Visualization Enhancements": one per channel). rgba holds n >= 2
+ * entries of straight colour and opacity in [0, 1]; the opacities are those of
+ * one sample every ref_step level-0 voxels. A voxel value v maps to
+ * x = clamp((v - lo) / (hi - lo), 0, 1), table position q = x (n - 1), with
+ * linear interpolation between entries floor(q) and floor(q) + 1. A sample
+ * spaced s apart uses opacity 1 - (1 - alpha)^(s / ref_step). Also derives
+ * which blocks and 8^3 sub-blocks are transparent under the table and marks
+ * earlier selections stale. Errors: INVALID_ARG (n < 2 or > 4096, hi <= lo,
+ * ref_step <= 0), OOM, CUDA. */
+sg_status sg_set_transfer_function(sg_volume* vol, int c, const float* rgba, int n, float lo, float hi,
+                                   float ref_step, void* stream);
+
+/* One head pose: the two eyes' view and projection matrices, the per-eye image
+ * size, the LOD tolerance in pixels (tau, 1.0 = a voxel may cover one pixel),
+ * the time point, and the selection slot that sg_select_lod fills and
+ * sg_render reads (0 .. 255; independent poses in flight use different slots). */
+typedef struct {
+  float view[2][16];
+  float proj[2][16];
+  int32_t width, height;
+  float pixel_error;
+  int32_t t;
+  int32_t slot;
+  int32_t reserved;
+} sg_pose;
+
+typedef struct {
+  uint32_t selected;  /* blocks rendered (including fallbacks) */
+  uint32_t culled;    /* blocks outside both view pyramids */
+  uint32_t empty;     /* blocks dropped because they and all descendants are transparent */
+  uint32_t requested; /* non-resident children requested */
+  uint32_t fallback;  /* blocks rendered one level coarser than wanted */
+  uint32_t nonempty;  /* selected blocks that are not transparent themselves (their bricks get sampled) */
+  uint32_t reserved[2];
+} sg_select_stats;
+
+/* LOD and residency selection for one pose ("Octree Representation", last
+ * paragraph). Top-down from the roots (every block of the coarsest level):
+ * a block outside one side plane of the view pyramid of both eyes (planes
+ * pushed one voxel outward) is culled; a block that is transparent together
+ * with all its descendants is dropped; a block of level L is accepted when
+ * L == 0 or 2^L <= tau theta d, with theta = 2 / (P11 height) the pixel angle
+ * at the image centre and d the distance from the block to the nearer eye
+ * (0 inside). The test runs in exact integers: eyes rounded to 1/64 voxel,
+ * K = floor((tau theta)^2 2^40), accept iff 4^L 64^2 2^40 <= K d^2 (128-bit).
+ * Otherwise, if a needed (not culled, not dropped) child is not resident,
+ * those children are requested and the block itself is rendered; else the
+ * needed children are visited. The result (which block renders each level-0
+ * block cell, requests, counters) is kept in pose->slot. If stats is not NULL
+ * the call waits for the stream and fills it. Errors: INVALID_ARG, STATE (no
+ * transfer function or no data for t), CUDA. */
+sg_status sg_select_lod(sg_volume* vol, const sg_pose* pose, sg_select_stats* stats, void* stream);
+
+/* Selection for n poses in one launch (batched frames); no stats. */
+sg_status sg_select_lod_batch(sg_volume* vol, const sg_pose* poses, int n, void* stream);
+
+/* Copies a selection to host memory (waits for the stream): per level-0 block
+ * cell the rendering node id or -1 (ncell = product of ceil(dims/B)); per node
+ * the traversal state (0 unseen, 1 culled, 2 dropped-empty, 3 selected,
+ * 4 selected as fallback, 5 refined); the requested node ids in ascending
+ * order (at most req_cap, *nreq gets the full count). Any output may be NULL.
+ * Errors: INVALID_ARG, STATE (slot never selected), CUDA. */
+sg_status sg_read_selection(sg_volume* vol, int slot, int32_t* cell_node, int64_t ncell, uint8_t* node_state,
+                            int64_t nnode, int32_t* req, int32_t req_cap, int32_t* nreq, void* stream);
+
+/* Copies the stored brick of (t, c, level, bx, by, bz) to host: (B+2)^3
+ * voxels of dtype, x fastest, apron included (waits for the stream). For
+ * inspection and tests of the ingest path. Errors: INVALID_ARG,
+ * NOT_RESIDENT (brick not in the cache), CUDA. */
+sg_status sg_read_brick(sg_volume* vol, int t, int c, int level, int bx, int by, int bz, void* host_out,
+                        void* stream);
+
+enum { SG_MODE_EMISSION_ABSORPTION = 0 };
+
+typedef struct {
+  float step;             /* level-0 sample spacing in voxels (> 0); level L samples every 2^L-th point */
+  float term_alpha;       /* early ray termination threshold, e.g. 0.99 (<= 0: 0.99) */
+  int32_t mode;           /* SG_MODE_EMISSION_ABSORPTION */
+  int32_t empty_skip;     /* 1: skip transparent blocks and 8^3 sub-blocks (output unchanged) */
+  uint32_t* sample_count[2]; /* optional device buffers (W*H per eye): samples composited per pixel */
+  unsigned long long* sample_total; /* optional device counter: incremented by the samples composited */
+} sg_render_params;
+
+/* Ray casts both eyes of a selected pose ("DVR Techniques"). For pixel (i,j)
+ * the ray leaves the eye towards the unprojection of NDC
+ * (2(i+0.5)/W - 1, 1 - 2(j+0.5)/H); t is in level-0 voxels; the ray is
+ * clipped to [0,N]^3: t0 = max(t_near, 0), t1 = t_far. Samples lie on the
+ * lattice t0 + k step (k >= 0), every 2^L-th point inside a block of level L.
+ * Each sample: trilinear value from the block's brick (exact trilinear
+ * weights in FP32), table lookup per channel, channels blended additively
+ * (alpha_s = min(1, sum alpha_c), colour scaled by alpha_s / max(alpha_s,
+ * sum alpha_c)), then C += (1 - A) colour_s, A += (1 - A) alpha_s; the ray
+ * stops after the sample that makes A >= term_alpha. out_rgba[e]: caller-owned
+ * device buffers of W*H*4 floats, 16-byte aligned. Errors: INVALID_ARG,
+ * STATE (slot not selected for this pose's t, or selection stale), CUDA. */
+sg_status sg_render(sg_volume* vol, const sg_pose* pose, const sg_render_params* params, float* out_rgba[2],
+                    void* stream);
+
+/* As sg_render, but the images land in caller-owned HOST buffers (W*H*4
+ * floats per eye; pinned memory gives full copy bandwidth). Renders into
+ * library-owned device staging, copies back and waits for the stream. */
+sg_status sg_render_host(sg_volume* vol, const sg_pose* pose, const sg_render_params* params,
+                         float* host_rgba[2], void* stream);
+
+/* Renders n selected poses (2n images of possibly different sizes) in one
+ * persistent launch over a queue of ray tiles ("3D Movies": time points;
+ * several viewers). outs[2i + e] is pose i's eye e (device, W*H*4 floats). */
+sg_status sg_render_batch(sg_volume* vol, const sg_pose* poses, int n, const sg_render_params* params,
+                          float** outs, void* stream);
+
+/* Thread-local message of the last failure on this thread ("" if none). */
+const char* sg_last_error(void);
+
+/* Library version string. */
+const char* sg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SG_H */

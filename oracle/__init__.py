@@ -28,7 +28,7 @@ MAX_LEVELS = 16
 MAX_CH = 4
 
 ST_UNSEEN, ST_CULLED, ST_EMPTY, ST_SELECTED, ST_FALLBACK, ST_REFINED = range(6)
-FL_FACE, FL_TEDGE, FL_TERM = 1, 2, 4
+FL_FACE, FL_TEDGE, FL_TERM, FL_COUNT = 1, 2, 4, 8
 
 
 def build(force=False):

@@ -511,7 +511,7 @@ void or_classify(const or_tf* tf, const double* table, double value, double* rgb
 /* ------------------------------------------------------------------------ */
 /* ray casting                                                               */
 
-enum { FL_FACE = 1, FL_TEDGE = 2, FL_TERM = 4 };
+enum { FL_FACE = 1, FL_TEDGE = 2, FL_TERM = 4, FL_COUNT = 8 };
 
 typedef struct {
   const or_volume* v;
@@ -599,7 +599,13 @@ static void cast(const ray_t* r, int64_t pix, double* early, double* late, uint3
       cell_of(r, p, 0.0, zero, cell);
       int32_t id = cell_at(r, cell);
       int L = node_level(r, id);
-      /* face proximity: the cells within eps of p, all sign combinations */
+      /* face proximity: the cells within eps of p, all sign combinations.
+       * Two rendered levels that differ, or a dropped (transparent) cell next
+       * to a block of level > 0, can change the value (FL_FACE). A dropped
+       * cell next to a level-0 block cannot: the dropped subtree's level-0
+       * ranges include the one-voxel apron, so the sample's alpha is exactly
+       * 0 wherever it is assigned; only the sample count may differ
+       * (FL_COUNT). */
       if (!(fl & FL_FACE)) {
         int near_ax[3], nnear = 0;
         for (int ax = 0; ax < 3; ++ax) {
@@ -610,7 +616,7 @@ static void cast(const ray_t* r, int64_t pix, double* early, double* late, uint3
         }
         if (nnear) {
           int used = (L >= 0 && (k & (((int64_t)1 << L) - 1)) == 0);
-          int differs = 0;
+          int value = 0, count = 0;
           for (int m = 0; m < 8; ++m) {
             int dirs[3];
             int skip = 0;
@@ -624,10 +630,14 @@ static void cast(const ray_t* r, int64_t pix, double* early, double* late, uint3
             cell_of(r, p, r->eps, dirs, c2);
             int32_t id2 = cell_at(r, c2);
             int L2 = node_level(r, id2);
-            if (L2 != L) differs = 1;
+            if (L2 != L) {
+              if ((L >= 0 && L2 >= 0) || L > 0 || L2 > 0) value = 1;
+              else count = 1;
+            }
             if (L2 >= 0 && (k & (((int64_t)1 << L2) - 1)) == 0) used = 1;
           }
-          if (differs && used) fl |= FL_FACE;
+          if (used && value) fl |= FL_FACE;
+          if (used && count) fl |= FL_COUNT;
         }
       }
       if (L < 0 || (k & (((int64_t)1 << L) - 1)) != 0) continue;

@@ -1,0 +1,621 @@
+// C ABI of the B300 DVR library: argument checks, ownership, the brick pool
+// and its LRU ("Volumetric Data Cashing": a GPU cache of chunks with
+// timestamps, evicting the oldest when full), and the launches.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <set>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+namespace sg {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+sg_status cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return SG_ERR_CUDA;
+}
+
+}  // namespace sg
+
+using namespace sg;
+
+#define SG_CHECK_ARG(cond, msg)      \
+  do {                               \
+    if (!(cond)) {                   \
+      set_error(msg);                \
+      return SG_ERR_INVALID_ARG;     \
+    }                                \
+  } while (0)
+
+#define SG_CUDA(call, what)                          \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+namespace {
+
+struct VolumeExtra {
+  std::set<std::pair<uint64_t, int64_t>> lru;  // (stamp, slot) of occupied, unpinned slots
+  std::vector<int64_t> free_slots;
+  int32_t* d_scratch = nullptr;                // upload bookkeeping
+  size_t scratch_n = 0;
+};
+
+std::vector<std::pair<sg_volume*, VolumeExtra*>>& extras() {
+  static std::vector<std::pair<sg_volume*, VolumeExtra*>> x;
+  return x;
+}
+
+VolumeExtra* extra_of(sg_volume* v) {
+  for (auto& p : extras())
+    if (p.first == v) return p.second;
+  return nullptr;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+void free_volume(sg_volume* v) {
+  if (!v) return;
+  cudaFree(v->d_pool);
+  cudaFree(v->d_slot);
+  cudaFree(v->d_range);
+  cudaFree(v->d_subrange);
+  cudaFree(v->d_subempty);
+  cudaFree(v->d_nodeflags);
+  cudaFree(v->d_tf_raw);
+  cudaFree(v->d_lut);
+  cudaFree(v->d_stage);
+  cudaFree(v->d_err);
+  cudaFree(v->d_stamp);
+  for (auto& s : v->sel) {
+    cudaFree(s.d_leaf);
+    cudaFree(s.d_cell_node);
+    cudaFree(s.d_state);
+    cudaFree(s.d_req);
+    cudaFree(s.d_counters);
+    cudaFree(s.d_frontier);
+  }
+  auto& xs = extras();
+  for (size_t i = 0; i < xs.size(); ++i)
+    if (xs[i].first == v) {
+      cudaFree(xs[i].second->d_scratch);
+      delete xs[i].second;
+      xs.erase(xs.begin() + i);
+      break;
+    }
+  delete v;
+}
+
+bool tfs_ready(const sg_volume* v) {
+  for (int c = 0; c < v->nch; ++c)
+    if (!v->tf[c].set) return false;
+  return true;
+}
+
+sg_status refresh_flags(sg_volume* v, cudaStream_t s) {
+  if (!tfs_ready(v)) return SG_OK;
+  SG_CUDA(launch_tf_flags(v, s), "transfer-function flags");
+  return SG_OK;
+}
+
+sg_status ensure_selection(sg_volume* v, int slot) {
+  SelSlot& s = v->sel[slot];
+  if (s.d_leaf) return SG_OK;
+  cudaError_t e;
+  if ((e = dalloc(&s.d_leaf, v->ncell)) != cudaSuccess || (e = dalloc(&s.d_cell_node, v->ncell)) != cudaSuccess ||
+      (e = dalloc(&s.d_state, v->nodes)) != cudaSuccess || (e = dalloc(&s.d_req, v->nodes)) != cudaSuccess ||
+      (e = dalloc(&s.d_counters, 8)) != cudaSuccess ||
+      (e = dalloc(&s.d_frontier, 2 * v->max_level_nodes)) != cudaSuccess) {
+    set_error(std::string("selection buffers: ") + cudaGetErrorString(e));
+    return SG_ERR_OOM;
+  }
+  return SG_OK;
+}
+
+sg_status check_pose(const sg_volume* v, const sg_pose* p) {
+  SG_CHECK_ARG(p, "pose is NULL");
+  SG_CHECK_ARG(p->slot >= 0 && p->slot < kMaxSlots, "pose.slot out of range [0, 255]");
+  SG_CHECK_ARG(p->t >= 0 && p->t < v->T, "pose.t out of range");
+  SG_CHECK_ARG(p->width > 0 && p->height > 0 && p->width <= 32768 && p->height <= 32768, "pose image size");
+  SG_CHECK_ARG(p->pixel_error > 0.0f, "pose.pixel_error must be > 0");
+  SG_CHECK_ARG(p->proj[0][5] != 0.0f, "projection has P11 == 0");
+  return SG_OK;
+}
+
+sg_status check_render_params(const sg_render_params* r) {
+  SG_CHECK_ARG(r, "render params are NULL");
+  SG_CHECK_ARG(r->step > 0.0f && r->step < 1e6f, "render step must be > 0");
+  SG_CHECK_ARG(r->term_alpha <= 1.0f, "term_alpha must be <= 1");
+  SG_CHECK_ARG(r->mode == SG_MODE_EMISSION_ABSORPTION, "unknown render mode");
+  return SG_OK;
+}
+
+sg_status check_ready_for_render(sg_volume* v, const sg_pose* p) {
+  const SelSlot& s = v->sel[p->slot];
+  if (!s.valid || s.t != p->t) {
+    set_error("sg_render: the pose's selection slot was not selected for this time point");
+    return SG_ERR_STATE;
+  }
+  if (s.tf_version != v->tf_version) {
+    set_error("sg_render: selection is stale (transfer function or data changed); call sg_select_lod again");
+    return SG_ERR_STATE;
+  }
+  return SG_OK;
+}
+
+sg_status prepare_lut(sg_volume* v, float step, cudaStream_t s) {
+  if (v->lut_step != step) {
+    SG_CUDA(launch_lut(v, step, s), "opacity-corrected tables");
+    v->lut_step = step;
+  }
+  return SG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sg_last_error(void) { return g_err.c_str(); }
+
+const char* sg_version(void) { return "sg-b300 0.1 (sm_103a)"; }
+
+sg_status sg_volume_create(const sg_volume_desc* d, sg_volume** out) {
+  SG_CHECK_ARG(d && out, "desc and out must not be NULL");
+  *out = nullptr;
+  SG_CHECK_ARG(d->dims[0] >= 1 && d->dims[1] >= 1 && d->dims[2] >= 1, "dims must be >= 1");
+  SG_CHECK_ARG(d->dtype == SG_U8 || d->dtype == SG_U16, "dtype must be SG_U8 or SG_U16");
+  SG_CHECK_ARG(d->channels >= 1 && d->channels <= kMaxCh, "channels must be 1..4");
+  SG_CHECK_ARG(d->timepoints >= 1 && d->timepoints <= 4096, "timepoints must be 1..4096");
+  SG_CHECK_ARG(d->brick_size >= 8 && d->brick_size <= 256 && d->brick_size % 8 == 0,
+               "brick_size must be a multiple of 8 in [8, 256]");
+  SG_CHECK_ARG(d->apron == 1, "apron must be 1");
+  SG_CHECK_ARG(d->lod_levels >= 1 && d->lod_levels <= kMaxLevels, "lod_levels must be 1..16");
+
+  sg_volume* v = new (std::nothrow) sg_volume();
+  if (!v) {
+    set_error("host allocation failed");
+    return SG_ERR_OOM;
+  }
+  v->desc = *d;
+  v->levels = d->lod_levels;
+  v->B = d->brick_size;
+  v->nch = d->channels;
+  v->T = d->timepoints;
+  v->esize = d->dtype == SG_U8 ? 1 : 2;
+  int64_t off = 0;
+  int64_t dims[3] = {d->dims[0], d->dims[1], d->dims[2]};
+  for (int L = 0; L < v->levels; ++L) {
+    LevelGeom& g = v->geom[L];
+    for (int a = 0; a < 3; ++a) {
+      g.dims[a] = dims[a];
+      g.nb[a] = (int32_t)((dims[a] + v->B - 1) / v->B);
+      dims[a] = (dims[a] + 1) / 2;
+    }
+    g.off = off;
+    int64_t n = (int64_t)g.nb[0] * g.nb[1] * g.nb[2];
+    off += n;
+    v->max_level_nodes = std::max(v->max_level_nodes, n);
+  }
+  v->nodes = off;
+  v->ncell = (int64_t)v->geom[0].nb[0] * v->geom[0].nb[1] * v->geom[0].nb[2];
+  if (v->ncell > (1 << 24) || v->nodes * v->T > ((int64_t)1 << 30)) {
+    delete v;
+    set_error("volume has too many blocks (use a larger brick_size)");
+    return SG_ERR_INVALID_ARG;
+  }
+  const int R = v->B + 2;
+  v->brick_bytes = ((size_t)R * R * R * v->esize + 255) / 256 * 256;
+  v->nsub = v->B / kSub;
+  const int ns3 = v->nsub * v->nsub * v->nsub;
+  v->sub_words = (ns3 + 63) / 64;
+  const int top = v->levels - 1;
+  const int64_t top_nodes = (int64_t)v->geom[top].nb[0] * v->geom[top].nb[1] * v->geom[top].nb[2];
+  if (d->device_pool_bytes == 0) {
+    v->pool_slots = v->nodes * v->T;
+  } else {
+    v->pooled = true;
+    v->pool_slots = (int64_t)(d->device_pool_bytes / (v->brick_bytes * v->nch));
+    if (v->pool_slots < top_nodes * v->T) {
+      delete v;
+      set_error("device_pool_bytes cannot hold the coarsest level of every time point");
+      return SG_ERR_INVALID_ARG;
+    }
+    v->pool_slots = std::min(v->pool_slots, v->nodes * v->T);
+  }
+  if (v->pool_slots >= (1 << 26)) {
+    delete v;
+    set_error("brick pool has too many slots");
+    return SG_ERR_INVALID_ARG;
+  }
+
+  cudaError_t e = cudaSuccess;
+  const int64_t tn = v->nodes * v->T;
+  if ((e = dalloc(&v->d_pool, (size_t)v->pool_slots * v->nch * v->brick_bytes)) != cudaSuccess ||
+      (e = dalloc(&v->d_slot, tn)) != cudaSuccess || (e = dalloc(&v->d_range, tn * v->nch * 2)) != cudaSuccess ||
+      (e = dalloc(&v->d_subrange, (size_t)v->pool_slots * ns3 * v->nch * 2)) != cudaSuccess ||
+      (e = dalloc(&v->d_subempty, (size_t)v->pool_slots * v->sub_words)) != cudaSuccess ||
+      (e = dalloc(&v->d_nodeflags, tn)) != cudaSuccess ||
+      (e = dalloc(&v->d_tf_raw, (size_t)v->nch * kMaxTF * 4)) != cudaSuccess ||
+      (e = dalloc(&v->d_lut, (size_t)v->nch * v->levels * kMaxTF)) != cudaSuccess ||
+      (e = dalloc(&v->d_err, 4)) != cudaSuccess) {
+    free_volume(v);
+    set_error(std::string("device allocation: ") + cudaGetErrorString(e));
+    return SG_ERR_OOM;
+  }
+  // page table: resident volumes map (t, node) -> t * nodes + node
+  v->h_slot.assign(tn, -1);
+  if (!v->pooled)
+    for (int64_t i = 0; i < tn; ++i) v->h_slot[i] = (int32_t)i;
+  // value ranges start unknown (min > max), which is never transparent
+  if ((e = cudaMemcpy(v->d_slot, v->h_slot.data(), tn * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(v->d_range, 0, tn * v->nch * 2 * sizeof(uint32_t))) != cudaSuccess ||
+      (e = cudaMemset2D(v->d_range, 8, 0xff, 4, tn * v->nch)) != cudaSuccess ||
+      (e = cudaMemset(v->d_subempty, 0, (size_t)v->pool_slots * v->sub_words * 8)) != cudaSuccess ||
+      (e = cudaMemset(v->d_nodeflags, 0, tn)) != cudaSuccess ||
+      (e = cudaMemset(v->d_tf_raw, 0, (size_t)v->nch * kMaxTF * 16)) != cudaSuccess) {
+    free_volume(v);
+    return cuda_fail(e, "volume initialisation");
+  }
+  v->has_data.assign((size_t)v->T * v->nch, 0);
+  VolumeExtra* x = new VolumeExtra();
+  extras().push_back({v, x});
+  if (v->pooled) {
+    v->slot_owner.assign(v->pool_slots, -1);
+    v->slot_stamp.assign(v->pool_slots, 0);
+    v->slot_pinned.assign(v->pool_slots, 0);
+    for (int64_t s = v->pool_slots - 1; s >= 0; --s) x->free_slots.push_back(s);
+    if ((e = dalloc(&v->d_stamp, v->pool_slots)) != cudaSuccess ||
+        (e = cudaMemset(v->d_stamp, 0, v->pool_slots * sizeof(uint64_t))) != cudaSuccess) {
+      free_volume(v);
+      set_error(std::string("stamp table: ") + cudaGetErrorString(e));
+      return SG_ERR_OOM;
+    }
+  }
+  *out = v;
+  return SG_OK;
+}
+
+sg_status sg_volume_destroy(sg_volume* v) {
+  if (!v) return SG_OK;
+  cudaDeviceSynchronize();
+  free_volume(v);
+  return SG_OK;
+}
+
+sg_status sg_upload_volume_device(sg_volume* v, int t, int c, const void* dev_level0, void* stream) {
+  SG_CHECK_ARG(v && dev_level0, "volume and dev_level0 must not be NULL");
+  SG_CHECK_ARG(t >= 0 && t < v->T && c >= 0 && c < v->nch, "t or c out of range");
+  if (v->pooled) {
+    set_error("sg_upload_volume_device needs a fully resident volume (device_pool_bytes == 0)");
+    return SG_ERR_STATE;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<void*> lv(v->levels, nullptr);
+  lv[0] = const_cast<void*>(dev_level0);
+  for (int L = 1; L < v->levels; ++L) {
+    const LevelGeom& g = v->geom[L];
+    size_t bytes = (size_t)g.dims[0] * g.dims[1] * g.dims[2] * v->esize;
+    cudaError_t e = cudaMallocAsync(&lv[L], bytes, s);
+    if (e != cudaSuccess) {
+      for (int k = 1; k < L; ++k) cudaFreeAsync(lv[k], s);
+      set_error(std::string("pyramid scratch: ") + cudaGetErrorString(e));
+      return SG_ERR_OOM;
+    }
+    SG_CUDA(launch_pyramid(lv[L - 1], v->geom[L - 1].dims, lv[L], g.dims, v->esize, s), "pyramid");
+  }
+  for (int L = 0; L < v->levels; ++L) SG_CUDA(launch_pack_level(v, t, c, L, lv[L], s), "brick packing");
+  for (int L = 1; L < v->levels; ++L) cudaFreeAsync(lv[L], s);
+  v->has_data[(size_t)t * v->nch + c] = 1;
+  ++v->tf_version;  // block ranges changed: earlier selections are stale
+  return refresh_flags(v, s);
+}
+
+sg_status sg_set_transfer_function(sg_volume* v, int c, const float* rgba, int n, float lo, float hi, float ref_step,
+                                   void* stream) {
+  SG_CHECK_ARG(v && rgba, "volume and rgba must not be NULL");
+  SG_CHECK_ARG(c >= 0 && c < v->nch, "channel out of range");
+  SG_CHECK_ARG(n >= 2 && n <= kMaxTF, "table size must be 2..4096");
+  SG_CHECK_ARG(hi > lo, "window needs hi > lo");
+  SG_CHECK_ARG(ref_step > 0.0f, "ref_step must be > 0");
+  for (int i = 0; i < 4 * n; ++i)
+    SG_CHECK_ARG(rgba[i] >= 0.0f && rgba[i] <= 1.0f, "table entries must be in [0, 1]");
+  cudaStream_t s = (cudaStream_t)stream;
+  TFHost& t = v->tf[c];
+  t.set = true;
+  t.n = n;
+  t.lo = lo;
+  t.hi = hi;
+  t.ref_step = ref_step;
+  t.rgba.assign(rgba, rgba + 4 * n);
+  SG_CUDA(cudaMemcpyAsync(v->d_tf_raw + (size_t)c * kMaxTF * 4, t.rgba.data(), sizeof(float) * 4 * n,
+                          cudaMemcpyHostToDevice, s),
+          "transfer-function upload");
+  // the host vector stays alive in the volume until the next call for c; a
+  // stream sync keeps it valid for an asynchronous copy from pageable memory
+  SG_CUDA(cudaStreamSynchronize(s), "transfer-function upload");
+  v->lut_step = -1.0f;
+  ++v->tf_version;
+  return refresh_flags(v, s);
+}
+
+sg_status sg_select_lod(sg_volume* v, const sg_pose* p, sg_select_stats* stats, void* stream) {
+  SG_CHECK_ARG(v, "volume is NULL");
+  sg_status st = check_pose(v, p);
+  if (st != SG_OK) return st;
+  st = sg_select_lod_batch(v, p, 1, stream);
+  if (st != SG_OK || !stats) return st;
+  uint32_t c[8];
+  cudaStream_t s = (cudaStream_t)stream;
+  SG_CUDA(cudaMemcpyAsync(c, v->sel[p->slot].d_counters, sizeof c, cudaMemcpyDeviceToHost, s), "select stats");
+  SG_CUDA(cudaStreamSynchronize(s), "select stats");
+  memset(stats, 0, sizeof *stats);
+  stats->requested = c[0];
+  stats->selected = c[1];
+  stats->culled = c[2];
+  stats->empty = c[3];
+  stats->fallback = c[4];
+  stats->nonempty = c[5];
+  return SG_OK;
+}
+
+sg_status sg_select_lod_batch(sg_volume* v, const sg_pose* poses, int n, void* stream) {
+  SG_CHECK_ARG(v && poses && n >= 1, "volume/poses NULL or n < 1");
+  if (!tfs_ready(v)) {
+    set_error("sg_select_lod: set a transfer function for every channel first");
+    return SG_ERR_STATE;
+  }
+  for (int i = 0; i < n; ++i) {
+    sg_status st = check_pose(v, &poses[i]);
+    if (st != SG_OK) return st;
+    for (int c = 0; c < v->nch; ++c)
+      if (!v->has_data[(size_t)poses[i].t * v->nch + c]) {
+        set_error("sg_select_lod: no data uploaded for this time point / channel");
+        return SG_ERR_STATE;
+      }
+    if (v->pooled) {
+      const LevelGeom& g = v->geom[v->levels - 1];
+      int64_t nt = (int64_t)g.nb[0] * g.nb[1] * g.nb[2];
+      for (int64_t b = 0; b < nt; ++b)
+        if (v->h_slot[(int64_t)poses[i].t * v->nodes + g.off + b] < 0) {
+          set_error("sg_select_lod: the coarsest level must be resident (upload it first)");
+          return SG_ERR_STATE;
+        }
+    }
+    for (int j = 0; j < i; ++j)
+      SG_CHECK_ARG(poses[j].slot != poses[i].slot, "poses of one batch must use different selection slots");
+    st = ensure_selection(v, poses[i].slot);
+    if (st != SG_OK) return st;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  ++v->frame;
+  SG_CUDA(launch_select(v, poses, n, s), "selection");
+  for (int i = 0; i < n; ++i) {
+    SelSlot& sl = v->sel[poses[i].slot];
+    sl.valid = true;
+    sl.t = poses[i].t;
+    sl.tf_version = v->tf_version;
+  }
+  return SG_OK;
+}
+
+sg_status sg_read_selection(sg_volume* v, int slot, int32_t* cell_node, int64_t ncell, uint8_t* node_state,
+                            int64_t nnode, int32_t* req, int32_t req_cap, int32_t* nreq, void* stream) {
+  SG_CHECK_ARG(v && slot >= 0 && slot < kMaxSlots, "volume NULL or slot out of range");
+  const SelSlot& sl = v->sel[slot];
+  if (!sl.valid) {
+    set_error("sg_read_selection: slot was never selected");
+    return SG_ERR_STATE;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  SG_CHECK_ARG(!cell_node || ncell >= v->ncell, "cell_node buffer too small");
+  SG_CHECK_ARG(!node_state || nnode >= v->nodes, "node_state buffer too small");
+  uint32_t c[8];
+  SG_CUDA(cudaMemcpyAsync(c, sl.d_counters, sizeof c, cudaMemcpyDeviceToHost, s), "read selection");
+  if (cell_node)
+    SG_CUDA(cudaMemcpyAsync(cell_node, sl.d_cell_node, v->ncell * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+            "read selection");
+  if (node_state)
+    SG_CUDA(cudaMemcpyAsync(node_state, sl.d_state, v->nodes, cudaMemcpyDeviceToHost, s), "read selection");
+  SG_CUDA(cudaStreamSynchronize(s), "read selection");
+  if (nreq) *nreq = (int32_t)c[0];
+  if (req && req_cap > 0) {
+    std::vector<int32_t> r(c[0]);
+    if (c[0]) {
+      SG_CUDA(cudaMemcpy(r.data(), sl.d_req, c[0] * sizeof(int32_t), cudaMemcpyDeviceToHost), "read requests");
+    }
+    std::sort(r.begin(), r.end());
+    for (int32_t i = 0; i < req_cap && i < (int32_t)r.size(); ++i) req[i] = r[i];
+  }
+  return SG_OK;
+}
+
+sg_status sg_read_brick(sg_volume* v, int t, int c, int level, int bx, int by, int bz, void* host_out,
+                        void* stream) {
+  SG_CHECK_ARG(v && host_out, "volume or host_out NULL");
+  SG_CHECK_ARG(t >= 0 && t < v->T && c >= 0 && c < v->nch && level >= 0 && level < v->levels,
+               "t, c or level out of range");
+  const LevelGeom& g = v->geom[level];
+  SG_CHECK_ARG(bx >= 0 && bx < g.nb[0] && by >= 0 && by < g.nb[1] && bz >= 0 && bz < g.nb[2],
+               "brick coordinates out of range");
+  int64_t node = g.off + ((int64_t)bz * g.nb[1] + by) * g.nb[0] + bx;
+  int32_t slot = v->h_slot[(int64_t)t * v->nodes + node];
+  if (slot < 0) {
+    set_error("sg_read_brick: brick not resident");
+    return SG_ERR_NOT_RESIDENT;
+  }
+  const int R = v->B + 2;
+  cudaStream_t s = (cudaStream_t)stream;
+  SG_CUDA(cudaMemcpyAsync(host_out, v->d_pool + ((size_t)slot * v->nch + c) * v->brick_bytes,
+                          (size_t)R * R * R * v->esize, cudaMemcpyDeviceToHost, s),
+          "brick download");
+  SG_CUDA(cudaStreamSynchronize(s), "brick download");
+  return SG_OK;
+}
+
+sg_status sg_render(sg_volume* v, const sg_pose* p, const sg_render_params* prm, float* out_rgba[2], void* stream) {
+  SG_CHECK_ARG(v && out_rgba && out_rgba[0] && out_rgba[1], "volume or outputs NULL");
+  SG_CHECK_ARG(((uintptr_t)out_rgba[0] % 16) == 0 && ((uintptr_t)out_rgba[1] % 16) == 0,
+               "output buffers must be 16-byte aligned");
+  sg_status st = check_pose(v, p);
+  if (st != SG_OK) return st;
+  if ((st = check_render_params(prm)) != SG_OK) return st;
+  if ((st = check_ready_for_render(v, p)) != SG_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = prepare_lut(v, prm->step, s)) != SG_OK) return st;
+  SG_CUDA(launch_render(v, p, 1, prm, out_rgba, s), "render");
+  return SG_OK;
+}
+
+sg_status sg_render_host(sg_volume* v, const sg_pose* p, const sg_render_params* prm, float* host_rgba[2],
+                         void* stream) {
+  SG_CHECK_ARG(v && host_rgba && host_rgba[0] && host_rgba[1], "volume or outputs NULL");
+  sg_status st = check_pose(v, p);
+  if (st != SG_OK) return st;
+  const size_t per = (size_t)p->width * p->height * 4 * sizeof(float);
+  if (v->stage_bytes < 2 * per) {
+    cudaFree(v->d_stage);
+    v->d_stage = nullptr;
+    v->stage_bytes = 0;
+    cudaError_t e = cudaMalloc(&v->d_stage, 2 * per);
+    if (e != cudaSuccess) {
+      set_error(std::string("staging allocation: ") + cudaGetErrorString(e));
+      return SG_ERR_OOM;
+    }
+    v->stage_bytes = 2 * per;
+  }
+  float* dev[2] = {v->d_stage, v->d_stage + per / sizeof(float)};
+  st = sg_render(v, p, prm, dev, stream);
+  if (st != SG_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  SG_CUDA(cudaMemcpyAsync(host_rgba[0], dev[0], per, cudaMemcpyDeviceToHost, s), "image download");
+  SG_CUDA(cudaMemcpyAsync(host_rgba[1], dev[1], per, cudaMemcpyDeviceToHost, s), "image download");
+  SG_CUDA(cudaStreamSynchronize(s), "image download");
+  return SG_OK;
+}
+
+sg_status sg_render_batch(sg_volume* v, const sg_pose* poses, int n, const sg_render_params* prm, float** outs,
+                          void* stream) {
+  SG_CHECK_ARG(v && poses && outs && n >= 1 && n <= 64, "volume/poses/outs NULL or n not in 1..64");
+  sg_status st = check_render_params(prm);
+  if (st != SG_OK) return st;
+  for (int i = 0; i < n; ++i) {
+    if ((st = check_pose(v, &poses[i])) != SG_OK) return st;
+    if ((st = check_ready_for_render(v, &poses[i])) != SG_OK) return st;
+    SG_CHECK_ARG(outs[2 * i] && outs[2 * i + 1], "batch output NULL");
+    SG_CHECK_ARG(((uintptr_t)outs[2 * i] % 16) == 0 && ((uintptr_t)outs[2 * i + 1] % 16) == 0,
+                 "output buffers must be 16-byte aligned");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = prepare_lut(v, prm->step, s)) != SG_OK) return st;
+  SG_CUDA(launch_render(v, poses, n, prm, outs, s), "batched render");
+  return SG_OK;
+}
+
+sg_status sg_upload_bricks(sg_volume* v, int t, int c, int level, int n, const int32_t* xyz, const void* host,
+                           void* stream) {
+  SG_CHECK_ARG(v && xyz && host && n >= 1, "volume/brick_xyz/host NULL or n < 1");
+  SG_CHECK_ARG(t >= 0 && t < v->T && c >= 0 && c < v->nch, "t or c out of range");
+  SG_CHECK_ARG(level >= 0 && level < v->levels, "level out of range");
+  const LevelGeom& g = v->geom[level];
+  for (int i = 0; i < n; ++i)
+    SG_CHECK_ARG(xyz[3 * i] >= 0 && xyz[3 * i] < g.nb[0] && xyz[3 * i + 1] >= 0 && xyz[3 * i + 1] < g.nb[1] &&
+                     xyz[3 * i + 2] >= 0 && xyz[3 * i + 2] < g.nb[2],
+                 "brick coordinates out of range");
+  cudaStream_t s = (cudaStream_t)stream;
+  VolumeExtra* x = extra_of(v);
+  const int R = v->B + 2;
+  const size_t raw = (size_t)R * R * R * v->esize;
+  std::vector<int32_t> nodes(n), slots(n);
+  if (v->pooled) {
+    // stamps of slots used by recent selections
+    std::vector<uint64_t> st(v->pool_slots);
+    SG_CUDA(cudaStreamSynchronize(s), "upload");
+    SG_CUDA(cudaMemcpy(st.data(), v->d_stamp, v->pool_slots * sizeof(uint64_t), cudaMemcpyDeviceToHost), "stamps");
+    for (int64_t sl = 0; sl < v->pool_slots; ++sl)
+      if (v->slot_owner[sl] >= 0 && !v->slot_pinned[sl] && st[sl] != v->slot_stamp[sl]) {
+        x->lru.erase({v->slot_stamp[sl], sl});
+        v->slot_stamp[sl] = st[sl];
+        x->lru.insert({st[sl], sl});
+      }
+  }
+  std::vector<std::pair<int64_t, int32_t>> table_updates;  // (t*nodes+node, slot)
+  for (int i = 0; i < n; ++i) {
+    int64_t node = g.off + ((int64_t)xyz[3 * i + 2] * g.nb[1] + xyz[3 * i + 1]) * g.nb[0] + xyz[3 * i];
+    int64_t key = (int64_t)t * v->nodes + node;
+    nodes[i] = (int32_t)node;
+    int32_t slot = v->h_slot[key];
+    if (slot < 0) {
+      int64_t sl;
+      if (!x->free_slots.empty()) {
+        sl = x->free_slots.back();
+        x->free_slots.pop_back();
+      } else {
+        // least recently used slot not used by the current frame
+        auto it = x->lru.begin();
+        if (it == x->lru.end() || it->first >= v->frame) {
+          set_error("sg_upload_bricks: brick cache full of bricks used by the current frame");
+          return SG_ERR_OOM;
+        }
+        sl = it->second;
+        x->lru.erase(it);
+        int64_t old = v->slot_owner[sl];
+        v->h_slot[old] = -1;
+        table_updates.push_back({old, -1});
+      }
+      slot = (int32_t)sl;
+      v->slot_owner[sl] = key;
+      v->h_slot[key] = slot;
+      table_updates.push_back({key, slot});
+      if (level == v->levels - 1) {
+        v->slot_pinned[sl] = 1;
+      } else {
+        v->slot_stamp[sl] = v->frame;
+        x->lru.insert({v->frame, sl});
+      }
+    }
+    slots[i] = slot;
+    SG_CUDA(cudaMemcpyAsync(v->d_pool + ((size_t)slot * v->nch + c) * v->brick_bytes,
+                            static_cast<const uint8_t*>(host) + raw * i, raw, cudaMemcpyHostToDevice, s),
+            "brick upload");
+  }
+  for (auto& u : table_updates)
+    SG_CUDA(cudaMemcpyAsync(v->d_slot + u.first, &u.second, sizeof(int32_t), cudaMemcpyHostToDevice, s),
+            "page table update");
+  // device copies of the node and slot lists for the range kernels
+  if (x->scratch_n < (size_t)2 * n) {
+    cudaFree(x->d_scratch);
+    x->d_scratch = nullptr;
+    x->scratch_n = 0;
+    cudaError_t e = dalloc(&x->d_scratch, (size_t)2 * n);
+    if (e != cudaSuccess) {
+      set_error(std::string("upload scratch: ") + cudaGetErrorString(e));
+      return SG_ERR_OOM;
+    }
+    x->scratch_n = 2 * n;
+  }
+  SG_CUDA(cudaMemcpyAsync(x->d_scratch, nodes.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s), "upload");
+  SG_CUDA(cudaMemcpyAsync(x->d_scratch + n, slots.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s), "upload");
+  SG_CUDA(launch_brick_ranges(v, t, c, level, x->d_scratch, n, s), "brick ranges");
+  SG_CUDA(launch_subranges(v, x->d_scratch + n, n, c, s), "sub-block ranges");
+  // the host vectors above are consumed by the copies before they are reused
+  SG_CUDA(cudaStreamSynchronize(s), "upload");
+  v->has_data[(size_t)t * v->nch + c] = 1;
+  return refresh_flags(v, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+// Internal declarations of the B300 DVR library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sg.h"
+
+namespace sg {
+
+constexpr int kMaxLevels = 16;
+constexpr int kMaxCh = 4;
+constexpr int kMaxSlots = 256;   // selection slots per volume
+constexpr int kSub = 8;          // sub-block edge (level-L voxels) for empty skipping
+constexpr int kMaxTF = 4096;
+
+// A leaf-map entry tells the ray caster what renders one level-0 block cell.
+//   bit 31      : nothing renders here (culled or transparent); bits 0..3 give
+//                 the level of the dropped block so a ray can jump all of it
+//   bits 0..3   : level L of the rendering block
+//   bit 4       : the block itself is transparent under the current tables
+//   bits 5..30  : pool slot of the block's brick group
+constexpr uint32_t kLeafNone = 0x80000000u;
+__host__ __device__ inline uint32_t leaf_pack(uint32_t slot, int level, bool own_empty) {
+  return (slot << 5) | (own_empty ? 16u : 0u) | (uint32_t)level;
+}
+
+// Node traversal states (match the C ABI's sg_read_selection documentation).
+enum : uint8_t { kUnseen = 0, kCulled = 1, kEmpty = 2, kSelected = 3, kFallback = 4, kRefined = 5 };
+
+// Node flags derived from the transfer functions.
+enum : uint8_t { kOwnEmpty = 1, kSubtreeEmpty = 2 };
+
+struct LevelGeom {
+  int64_t dims[3];  // voxels of this level
+  int32_t nb[3];    // blocks per axis
+  int64_t off;      // first node id of this level
+};
+
+// Quantised inputs of the integer selection test for one pose.
+struct SelectInputs {
+  int64_t eye[2][3];      // 1/64 level-0 voxel
+  int64_t plane[2][4][4]; // A, B, C (x 2^16), D (x 2^16 x 64, one voxel outward)
+  uint64_t K;             // floor((tau theta)^2 2^40)
+};
+
+struct SelSlot {
+  bool valid = false;
+  int t = -1;
+  uint64_t tf_version = 0;
+  uint32_t* d_leaf = nullptr;      // [ncell]
+  int32_t* d_cell_node = nullptr;  // [ncell]
+  uint8_t* d_state = nullptr;      // [nodes]
+  int32_t* d_req = nullptr;        // [nodes]
+  uint32_t* d_counters = nullptr;  // [8]: nreq, selected, culled, empty, fallback
+  int32_t* d_frontier = nullptr;   // [2][max level count]
+};
+
+struct TFHost {
+  bool set = false;
+  int n = 0;
+  float lo = 0, hi = 1, ref_step = 0.5f;
+  std::vector<float> rgba;
+};
+
+}  // namespace sg
+
+struct sg_volume {
+  sg_volume_desc desc;
+  int levels = 0, B = 0, nch = 0, T = 0, esize = 0;
+  sg::LevelGeom geom[sg::kMaxLevels];
+  int64_t nodes = 0;        // per time point
+  int64_t ncell = 0;        // level-0 block cells
+  int64_t max_level_nodes = 0;
+  int nsub = 0;             // sub-blocks per axis in a brick
+  int sub_words = 0;        // 64-bit words of sub-block empty bits per slot
+
+  // brick pool: slot s, channel c at d_pool + (s * nch + c) * brick_bytes
+  uint8_t* d_pool = nullptr;
+  int64_t pool_slots = 0;
+  size_t brick_bytes = 0;   // (B+2)^3 * esize, padded to 256
+  bool pooled = false;      // LRU cache instead of everything resident
+
+  int32_t* d_slot = nullptr;       // [T][nodes] slot or -1
+  std::vector<int32_t> h_slot;     // host mirror
+  uint32_t* d_range = nullptr;     // [T][nodes][nch][2]
+  uint16_t* d_subrange = nullptr;  // [slots][nsub^3][nch][2]
+  uint64_t* d_subempty = nullptr;  // [slots][sub_words]
+  uint8_t* d_nodeflags = nullptr;  // [T][nodes]
+  std::vector<uint8_t> has_data;   // [T][nch]
+
+  // transfer functions
+  sg::TFHost tf[sg::kMaxCh];
+  float* d_tf_raw = nullptr;       // [nch][kMaxTF][4]
+  float4* d_lut = nullptr;         // [nch][levels][kMaxTF] opacity-corrected
+  float lut_step = -1.0f;
+  uint64_t tf_version = 0;
+
+  // LRU state (pooled volumes)
+  std::vector<int64_t> slot_owner;    // slot -> t*nodes+node or -1
+  std::vector<uint64_t> slot_stamp;   // last frame the slot was used
+  std::vector<uint8_t> slot_pinned;   // coarsest level: never evicted
+  uint64_t frame = 0;
+  uint64_t* d_stamp = nullptr;        // [slots] frame of last use, written by the selection kernel
+
+  sg::SelSlot sel[sg::kMaxSlots];
+
+  float* d_stage = nullptr;  // sg_render_host staging
+  size_t stage_bytes = 0;
+  uint32_t* d_err = nullptr; // device error word (bounded waits)
+};
+
+namespace sg {
+
+void set_error(const std::string& msg);
+sg_status cuda_fail(cudaError_t e, const char* what);
+
+// ingest.cu
+cudaError_t launch_pyramid(const void* src, const int64_t* sdims, void* dst, const int64_t* ddims, int esize,
+                           cudaStream_t s);
+cudaError_t launch_pack_level(sg_volume* v, int t, int c, int L, const void* level_data, cudaStream_t s);
+cudaError_t launch_subranges(sg_volume* v, const int32_t* d_slots, int nslots, int c, cudaStream_t s);
+cudaError_t launch_brick_ranges(sg_volume* v, int t, int c, int L, const int32_t* d_nodes, int n,
+                                cudaStream_t s);
+
+// tf.cu
+cudaError_t launch_tf_flags(sg_volume* v, cudaStream_t s);
+cudaError_t launch_lut(sg_volume* v, float step, cudaStream_t s);
+
+// select.cu
+void compute_select_inputs(const sg_volume* v, const sg_pose* p, SelectInputs* out);
+cudaError_t launch_select(sg_volume* v, const sg_pose* poses, int n, cudaStream_t s);
+
+// render.cu
+cudaError_t launch_render(sg_volume* v, const sg_pose* poses, int n, const sg_render_params* prm,
+                          float* const* outs, cudaStream_t s);
+
+}  // namespace sg

@@ -1,0 +1,168 @@
+// Transfer-function preparation ("DVR Techniques": transfer functions tau
+// and T; "Visualization Enhancements": one table per channel).
+//  - which blocks / 8^3 sub-blocks are transparent under the tables
+//    (alpha exactly 0 over their whole value range), used to drop subtrees
+//    during selection and to skip work while ray casting;
+//  - per-level opacity-corrected tables for the current sample spacing.
+#include "internal.h"
+
+namespace sg {
+namespace {
+
+struct TFParams {
+  int nch;
+  int n[kMaxCh];
+  float lo[kMaxCh], hi[kMaxCh];
+  const float* raw;  // [nch][kMaxTF][4]
+};
+
+// A value range is transparent when every table entry a value in it can
+// touch has alpha 0. The index is decided in FP32, in this exact order:
+// x = (v - lo) / (hi - lo) clamped to [0,1], q = x (n-1), entries
+// floor(q(vmin)) - 1 .. floor(q(vmax)) + 2 (the one-entry margins absorb a
+// one-ulp difference in how a sampler computes q). Unknown ranges
+// (vmin > vmax) are never transparent.
+__device__ bool range_empty(const TFParams& p, int c, uint32_t vmin, uint32_t vmax) {
+  if (vmin > vmax) return false;
+  const int n = p.n[c];
+  const float width = __fsub_rn(p.hi[c], p.lo[c]);
+  float x0 = __fdiv_rn(__fsub_rn(__uint2float_rn(vmin), p.lo[c]), width);
+  float x1 = __fdiv_rn(__fsub_rn(__uint2float_rn(vmax), p.lo[c]), width);
+  x0 = fminf(fmaxf(x0, 0.0f), 1.0f);
+  x1 = fminf(fmaxf(x1, 0.0f), 1.0f);
+  int ilo = (int)floorf(__fmul_rn(x0, (float)(n - 1))) - 1;
+  int ihi = (int)floorf(__fmul_rn(x1, (float)(n - 1))) + 2;
+  ilo = max(ilo, 0);
+  ihi = min(ihi, n - 1);
+  const float* a = p.raw + (size_t)c * kMaxTF * 4;
+  for (int i = ilo; i <= ihi; ++i)
+    if (a[4 * i + 3] != 0.0f) return false;
+  return true;
+}
+
+__global__ void k_own_empty(TFParams p, const uint32_t* __restrict__ range, int64_t total, uint8_t* __restrict__ flags) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    bool e = true;
+    for (int c = 0; c < p.nch && e; ++c) e = range_empty(p, c, range[(i * p.nch + c) * 2], range[(i * p.nch + c) * 2 + 1]);
+    flags[i] = e ? kOwnEmpty : 0;
+  }
+}
+
+// subtree-transparent = transparent itself and every existing child subtree-transparent
+__global__ void k_subtree(uint8_t* __restrict__ flags, int64_t nodes, int T, int64_t off, int nbx, int nby, int nbz,
+                          int64_t coff, int cbx, int cby, int cbz, int leaf_level) {
+  const int64_t per = (int64_t)nbx * nby * nbz;
+  const int64_t total = per * T;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t t = i / per, b = i % per;
+    int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((int64_t)nbx * nby));
+    uint8_t* f = flags + t * nodes + off + b;
+    bool e = (*f & kOwnEmpty) != 0;
+    if (!leaf_level)
+      for (int k = 0; k < 8 && e; ++k) {
+        int cx = 2 * bx + (k & 1), cy = 2 * by + ((k >> 1) & 1), cz = 2 * bz + ((k >> 2) & 1);
+        if (cx >= cbx || cy >= cby || cz >= cbz) continue;
+        e = (flags[t * nodes + coff + ((int64_t)cz * cby + cy) * cbx + cx] & kSubtreeEmpty) != 0;
+      }
+    if (e) *f |= kSubtreeEmpty;
+  }
+}
+
+// one thread per 64-bit word of sub-block transparency bits of a slot
+__global__ void k_sub_empty(TFParams p, const uint16_t* __restrict__ subrange, int64_t slots, int ns3, int words,
+                            uint64_t* __restrict__ out) {
+  const int64_t total = slots * words;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t slot = i / words;
+    int w = (int)(i % words);
+    uint64_t bits = 0;
+    for (int k = 0; k < 64; ++k) {
+      int s = w * 64 + k;
+      if (s >= ns3) break;
+      bool e = true;
+      for (int c = 0; c < p.nch && e; ++c) {
+        const uint16_t* r = subrange + ((slot * ns3 + s) * p.nch + c) * 2;
+        e = range_empty(p, c, r[0], r[1]);
+      }
+      if (e) bits |= 1ull << k;
+    }
+    out[i] = bits;
+  }
+}
+
+// Opacity correction per level: a level-L sample stands for step 2^L
+// level-0 voxels: alpha' = 1 - (1 - alpha)^(step 2^L / ref_step).
+struct LutParams {
+  int nch, levels;
+  int n[kMaxCh];
+  float ref[kMaxCh];
+};
+
+__global__ void k_lut(const float* __restrict__ raw, LutParams p, float step, float4* __restrict__ lut) {
+  const int total = p.nch * p.levels * kMaxTF;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    int e = i % kMaxTF, L = (i / kMaxTF) % p.levels, c = i / (kMaxTF * p.levels);
+    if (e >= p.n[c]) continue;
+    const float* r = raw + ((size_t)c * kMaxTF + e) * 4;
+    float ex = step * (float)(1 << L) / p.ref[c];
+    float a = r[3];
+    float ac = (a >= 1.0f) ? 1.0f : 1.0f - powf(1.0f - a, ex);
+    lut[i] = make_float4(r[0], r[1], r[2], ac);
+  }
+}
+
+TFParams make_params(const sg_volume* v) {
+  TFParams p;
+  p.nch = v->nch;
+  for (int c = 0; c < kMaxCh; ++c) {
+    p.n[c] = c < v->nch ? v->tf[c].n : 2;
+    p.lo[c] = c < v->nch ? v->tf[c].lo : 0.0f;
+    p.hi[c] = c < v->nch ? v->tf[c].hi : 1.0f;
+  }
+  p.raw = v->d_tf_raw;
+  return p;
+}
+
+unsigned grid_for(int64_t total, int threads) {
+  int64_t b = (total + threads - 1) / threads;
+  if (b > 148 * 32) b = 148 * 32;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+cudaError_t launch_tf_flags(sg_volume* v, cudaStream_t s) {
+  TFParams p = make_params(v);
+  int64_t total = v->nodes * v->T;
+  k_own_empty<<<grid_for(total, 256), 256, 0, s>>>(p, v->d_range, total, v->d_nodeflags);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  for (int L = 0; L < v->levels; ++L) {
+    const LevelGeom& g = v->geom[L];
+    const LevelGeom& cg = v->geom[L > 0 ? L - 1 : 0];
+    int64_t n = (int64_t)g.nb[0] * g.nb[1] * g.nb[2] * v->T;
+    k_subtree<<<grid_for(n, 256), 256, 0, s>>>(v->d_nodeflags, v->nodes, v->T, g.off, g.nb[0], g.nb[1], g.nb[2],
+                                               cg.off, cg.nb[0], cg.nb[1], cg.nb[2], L == 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  int ns3 = v->nsub * v->nsub * v->nsub;
+  int64_t words = (int64_t)v->pool_slots * v->sub_words;
+  k_sub_empty<<<grid_for(words, 128), 128, 0, s>>>(p, v->d_subrange, v->pool_slots, ns3, v->sub_words, v->d_subempty);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lut(sg_volume* v, float step, cudaStream_t s) {
+  LutParams p;
+  p.nch = v->nch;
+  p.levels = v->levels;
+  for (int c = 0; c < kMaxCh; ++c) {
+    p.n[c] = c < v->nch ? v->tf[c].n : 2;
+    p.ref[c] = c < v->nch ? v->tf[c].ref_step : 1.0f;
+  }
+  int total = v->nch * v->levels * kMaxTF;
+  k_lut<<<grid_for(total, 256), 256, 0, s>>>(v->d_tf_raw, p, step, v->d_lut);
+  return cudaGetLastError();
+}
+
+}  // namespace sg

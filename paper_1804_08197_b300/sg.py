@@ -1,0 +1,222 @@
+"""ctypes binding of libsg.so (include/sg.h). Argument marshalling only.
+
+Every function here forwards to the C entry point of the same name; device
+buffers are passed as raw pointers (e.g. torch tensors' data_ptr()) and
+streams as cudaStream_t handles (torch.cuda.Stream.cuda_stream). There is no
+fallback: if libsg.so is missing or fails to load, importing this module
+raises.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsg.so")
+
+SG_OK, SG_ERR_INVALID_ARG, SG_ERR_OOM, SG_ERR_CUDA, SG_ERR_NOT_RESIDENT, SG_ERR_TIMEOUT, SG_ERR_STATE = range(7)
+SG_U8, SG_U16 = 1, 2
+SG_MODE_EMISSION_ABSORPTION = 0
+STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_OOM", 3: "SG_ERR_CUDA", 4: "SG_ERR_NOT_RESIDENT",
+                5: "SG_ERR_TIMEOUT", 6: "SG_ERR_STATE"}
+
+EXPORTS = ["sg_volume_create", "sg_volume_destroy", "sg_upload_volume_device", "sg_upload_bricks",
+           "sg_set_transfer_function", "sg_select_lod", "sg_select_lod_batch", "sg_read_selection", "sg_read_brick",
+           "sg_render", "sg_render_host", "sg_render_batch", "sg_last_error", "sg_version"]
+
+
+class SGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class sg_volume_desc(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32 * 3), ("dtype", ctypes.c_int32), ("channels", ctypes.c_int32),
+                ("timepoints", ctypes.c_int32), ("brick_size", ctypes.c_int32), ("apron", ctypes.c_int32),
+                ("lod_levels", ctypes.c_int32), ("reserved", ctypes.c_int32), ("device_pool_bytes", ctypes.c_uint64),
+                ("model", ctypes.c_float * 16)]
+
+
+class sg_pose(ctypes.Structure):
+    _fields_ = [("view", (ctypes.c_float * 16) * 2), ("proj", (ctypes.c_float * 16) * 2), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("pixel_error", ctypes.c_float), ("t", ctypes.c_int32),
+                ("slot", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class sg_select_stats(ctypes.Structure):
+    _fields_ = [("selected", ctypes.c_uint32), ("culled", ctypes.c_uint32), ("empty", ctypes.c_uint32),
+                ("requested", ctypes.c_uint32), ("fallback", ctypes.c_uint32), ("nonempty", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
+
+
+class sg_render_params(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_float), ("term_alpha", ctypes.c_float), ("mode", ctypes.c_int32),
+                ("empty_skip", ctypes.c_int32), ("sample_count", ctypes.c_void_p * 2),
+                ("sample_total", ctypes.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libsg.so not built at {LIB_PATH}: run python -m paper_1804_08197_b300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_float
+    P = ctypes.POINTER
+    sig = {
+        "sg_volume_create": [P(sg_volume_desc), P(vp)],
+        "sg_volume_destroy": [vp],
+        "sg_upload_volume_device": [vp, i32, i32, vp, vp],
+        "sg_upload_bricks": [vp, i32, i32, i32, i32, vp, vp, vp],
+        "sg_set_transfer_function": [vp, i32, vp, i32, f32, f32, f32, vp],
+        "sg_select_lod": [vp, P(sg_pose), P(sg_select_stats), vp],
+        "sg_select_lod_batch": [vp, P(sg_pose), i32, vp],
+        "sg_read_selection": [vp, i32, vp, i64, vp, i64, vp, i32, vp, vp],
+        "sg_read_brick": [vp, i32, i32, i32, i32, i32, i32, vp, vp],
+        "sg_render": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
+        "sg_render_host": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
+        "sg_render_batch": [vp, P(sg_pose), i32, P(sg_render_params), P(vp), vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.sg_last_error.restype = ctypes.c_char_p
+    L.sg_last_error.argtypes = []
+    L.sg_version.restype = ctypes.c_char_p
+    L.sg_version.argtypes = []
+    return L
+
+
+lib = _load()
+
+
+def _check(status):
+    if status != SG_OK:
+        raise SGError(status, lib.sg_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(x.ctypes.data)  # numpy
+
+
+# --------------------------------------------------------------------------- entry points
+
+def sg_version():
+    return lib.sg_version().decode()
+
+
+def sg_volume_create(dims, dtype, brick_size, lod_levels, channels=1, timepoints=1, apron=1,
+                     device_pool_bytes=0, model=None):
+    d = sg_volume_desc()
+    d.dims[:] = [int(x) for x in dims]
+    d.dtype = dtype
+    d.channels = channels
+    d.timepoints = timepoints
+    d.brick_size = brick_size
+    d.apron = apron
+    d.lod_levels = lod_levels
+    d.device_pool_bytes = device_pool_bytes
+    m = [1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1] if model is None else [float(x) for x in model]
+    d.model[:] = m
+    h = ctypes.c_void_p()
+    _check(lib.sg_volume_create(ctypes.byref(d), ctypes.byref(h)))
+    return h
+
+
+def sg_volume_destroy(vol):
+    _check(lib.sg_volume_destroy(vol))
+
+
+def sg_upload_volume_device(vol, t, c, dev_level0, stream=None):
+    _check(lib.sg_upload_volume_device(vol, t, c, _ptr(dev_level0), _stream(stream)))
+
+
+def sg_upload_bricks(vol, t, c, level, brick_xyz, host, stream=None):
+    import numpy as np
+    xyz = np.ascontiguousarray(brick_xyz, np.int32).reshape(-1, 3)
+    _check(lib.sg_upload_bricks(vol, t, c, level, len(xyz), _ptr(xyz), _ptr(host), _stream(stream)))
+
+
+def sg_set_transfer_function(vol, c, rgba, lo, hi, ref_step=0.5, stream=None):
+    import numpy as np
+    tab = np.ascontiguousarray(rgba, np.float32).reshape(-1, 4)
+    _check(lib.sg_set_transfer_function(vol, c, _ptr(tab), len(tab), lo, hi, ref_step, _stream(stream)))
+
+
+def make_pose(views, projs, width, height, pixel_error=1.0, t=0, slot=0):
+    p = sg_pose()
+    for e in range(2):
+        p.view[e][:] = [float(x) for x in views[e]]
+        p.proj[e][:] = [float(x) for x in projs[e]]
+    p.width, p.height = int(width), int(height)
+    p.pixel_error = pixel_error
+    p.t, p.slot = t, slot
+    return p
+
+
+def sg_select_lod(vol, pose, stats=False, stream=None):
+    st = sg_select_stats() if stats else None
+    _check(lib.sg_select_lod(vol, ctypes.byref(pose), ctypes.byref(st) if st is not None else None, _stream(stream)))
+    if st is not None:
+        return dict(selected=st.selected, culled=st.culled, empty=st.empty, requested=st.requested,
+                    fallback=st.fallback, nonempty=st.nonempty)
+    return None
+
+
+def sg_select_lod_batch(vol, poses, stream=None):
+    arr = (sg_pose * len(poses))(*poses)
+    _check(lib.sg_select_lod_batch(vol, arr, len(poses), _stream(stream)))
+
+
+def sg_read_selection(vol, slot, ncell, nnode, req_cap=1 << 16, stream=None):
+    import numpy as np
+    cells = np.empty(ncell, np.int32)
+    state = np.empty(nnode, np.uint8)
+    req = np.empty(req_cap, np.int32)
+    nreq = ctypes.c_int32(0)
+    _check(lib.sg_read_selection(vol, slot, _ptr(cells), ncell, _ptr(state), nnode, _ptr(req), req_cap,
+                                 ctypes.byref(nreq), _stream(stream)))
+    return cells, state, req[: min(nreq.value, req_cap)].copy()
+
+
+def sg_read_brick(vol, t, c, level, bx, by, bz, host_out, stream=None):
+    _check(lib.sg_read_brick(vol, t, c, level, bx, by, bz, _ptr(host_out), _stream(stream)))
+
+
+def render_params(step=0.5, term_alpha=0.99, empty_skip=1, sample_count=None, sample_total=None):
+    r = sg_render_params()
+    if sample_total is not None:
+        r.sample_total = _ptr(sample_total).value
+    r.step, r.term_alpha, r.mode, r.empty_skip = step, term_alpha, SG_MODE_EMISSION_ABSORPTION, empty_skip
+    if sample_count is not None:
+        r.sample_count[0] = _ptr(sample_count[0]).value
+        r.sample_count[1] = _ptr(sample_count[1]).value
+    return r
+
+
+def sg_render(vol, pose, params, outs, stream=None):
+    arr = (ctypes.c_void_p * 2)(_ptr(outs[0]).value, _ptr(outs[1]).value)
+    _check(lib.sg_render(vol, ctypes.byref(pose), ctypes.byref(params), arr, _stream(stream)))
+
+
+def sg_render_host(vol, pose, params, host_outs, stream=None):
+    arr = (ctypes.c_void_p * 2)(_ptr(host_outs[0]).value, _ptr(host_outs[1]).value)
+    _check(lib.sg_render_host(vol, ctypes.byref(pose), ctypes.byref(params), arr, _stream(stream)))
+
+
+def sg_render_batch(vol, poses, params, outs, stream=None):
+    parr = (sg_pose * len(poses))(*poses)
+    oarr = (ctypes.c_void_p * len(outs))(*[_ptr(o).value for o in outs])
+    _check(lib.sg_render_batch(vol, parr, len(poses), ctypes.byref(params), oarr, _stream(stream)))

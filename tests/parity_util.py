@@ -1,0 +1,114 @@
+"""Shared helpers of the GPU parity tests: run one case through the C ABI
+(libsg.so) and through the FP64 oracle on the same seeded inputs, then compare.
+
+Image bar (tolerance 1e-3 per RGBA channel): for every pixel the oracle does
+not flag, the GPU value must lie within [min(early, late) - 1e-3,
+max(early, late) + 1e-3] per channel, where early/late are the oracle's
+results with the termination threshold moved by -/+1e-4 (equal unless a
+sample lands within 1e-4 of the threshold). Pixels with a sample within
+1e-3 voxel of a face between blocks of different levels, or of the volume
+exit, may legitimately differ by one sample's assignment; they are counted
+and must stay rare. Where a transparent (dropped) cell meets a level-0 block
+only the sample count can differ (the sample's alpha is exactly 0 either
+way), so those pixels keep the value check and skip the count check.
+Selections must match bit for bit."""
+import numpy as np
+
+import oracle
+
+TOL = 1e-3
+
+
+def gpu_available():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+class GpuCase:
+    """A volume on the GPU through the C ABI plus its oracle twin."""
+
+    def __init__(self, level0_channels, brick, levels, model=None, timepoints_data=None):
+        import torch
+        from paper_1804_08197_b300 import sg
+        self.sg = sg
+        self.torch = torch
+        a0 = level0_channels[0]
+        self.dtype = sg.SG_U8 if a0.dtype == np.uint8 else sg.SG_U16
+        dims = (a0.shape[2], a0.shape[1], a0.shape[0])
+        self.dims = dims
+        self.brick = brick
+        self.levels = levels
+        self.model = model
+        self.vol = sg.sg_volume_create(dims, self.dtype, brick, levels, channels=len(level0_channels), model=model)
+        for c, a in enumerate(level0_channels):
+            d = torch.from_numpy(np.ascontiguousarray(a).view(np.int16 if a.dtype == np.uint16 else np.uint8)).cuda()
+            sg.sg_upload_volume_device(self.vol, 0, c, d.data_ptr())
+            torch.cuda.synchronize()
+            del d
+        self.ovol = oracle.Volume([oracle.pyramid(a, levels) for a in level0_channels], brick, model=model)
+        self.ranges = self.ovol.block_ranges()
+        nb0 = self.ovol.blocks_per_axis(0)
+        self.ncell = nb0[0] * nb0[1] * nb0[2]
+
+    def set_tfs(self, tables, windows, ref_step=0.5):
+        self.tables = tables
+        self.windows = windows
+        for c, (t, (lo, hi)) in enumerate(zip(tables, windows)):
+            self.sg.sg_set_transfer_function(self.vol, c, t, lo, hi, ref_step)
+        self.otfs = [oracle.make_tf(t, lo, hi, ref_step) for t, (lo, hi) in zip(tables, windows)]
+
+    def select(self, views, projs, W, H, tau=1.0, slot=0):
+        sg = self.sg
+        pose = sg.make_pose(views, projs, W, H, pixel_error=tau, slot=slot)
+        stats = sg.sg_select_lod(self.vol, pose, stats=True)
+        cells, state, req = sg.sg_read_selection(self.vol, slot, self.ncell, self.ovol.node_count)
+        ref = self.ovol.select(self.otfs, views, projs, H, tau=tau, ranges=self.ranges)
+        return pose, stats, (cells, state, req), ref
+
+    def render(self, pose, step=0.5, empty_skip=1, counts=True, term=0.99):
+        torch, sg = self.torch, self.sg
+        W, H = pose.width, pose.height
+        outs = [torch.empty((H, W, 4), dtype=torch.float32, device="cuda") for _ in range(2)]
+        cnt = [torch.zeros((H, W), dtype=torch.int32, device="cuda") for _ in range(2)] if counts else None
+        prm = sg.render_params(step=step, term_alpha=term, empty_skip=empty_skip, sample_count=cnt)
+        sg.sg_render(self.vol, pose, prm, outs)
+        torch.cuda.synchronize()
+        imgs = [o.cpu().numpy().reshape(-1, 4) for o in outs]
+        cs = [c.cpu().numpy().reshape(-1).astype(np.int64) for c in cnt] if counts else None
+        return imgs, cs
+
+    def oracle_render(self, leaf, view, proj, W, H, step=0.5, pixels=None):
+        return self.ovol.render(self.otfs, leaf, view, proj, W, H, step=step, pixels=pixels)
+
+    def close(self):
+        self.sg.sg_volume_destroy(self.vol)
+
+
+def compare_selection(gpu, ref):
+    cells, state, req = gpu
+    assert np.array_equal(cells, ref["leaf"]), f"leaf map differs in {np.count_nonzero(cells != ref['leaf'])} cells"
+    assert np.array_equal(state, ref["state"]), f"node states differ in {np.count_nonzero(state != ref['state'])}"
+    assert np.array_equal(np.sort(req), ref["requests"])
+
+
+def compare_image(img, ref, counts=None, max_flagged=0.01, tol=TOL):
+    """img: (n,4) GPU pixels matching ref's pixel order. Returns stats."""
+    fl = ref["flags"]
+    strict = (fl & (oracle.FL_FACE | oracle.FL_TEDGE)) == 0
+    lo = np.minimum(ref["early"], ref["late"]) - tol
+    hi = np.maximum(ref["early"], ref["late"]) + tol
+    bad = strict[:, None] & ((img < lo) | (img > hi))
+    err = np.where(strict[:, None], np.abs(img - ref["late"]), 0.0)
+    worst = np.unravel_index(np.argmax(err), err.shape)
+    assert not bad.any(), (f"{np.count_nonzero(bad.any(1))} pixels outside tolerance; worst {err.max():.3g} at "
+                           f"{worst}: gpu {img[worst[0]]} oracle {ref['late'][worst[0]]} flags {fl[worst[0]]}")
+    frac = 1.0 - strict.mean()
+    assert frac <= max_flagged, f"{frac:.4f} of pixels flagged"
+    if counts is not None:
+        cstrict = strict & ((fl & oracle.FL_COUNT) == 0)
+        ok = (counts >= ref["count_early"]) & (counts <= ref["count_late"])
+        assert ok[cstrict].all(), f"{np.count_nonzero(~ok[cstrict])} sample-count mismatches"
+    return dict(max_err=float(err.max()), flagged=float(frac), n=len(img))

@@ -1,0 +1,190 @@
+"""GPU parity through the C ABI against the FP64 oracle on seeded inputs:
+bit-exact bricks and selections, images within 1e-3, sample counts, empty
+skipping that changes nothing, ragged and degenerate sizes."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity_util import GpuCase, compare_image, compare_selection
+
+pytestmark = pytest.mark.gpu
+
+
+def _c1_case():
+    v = synth.gaussians_u8(128, seed=1001)
+    case = GpuCase([v], 128, 1)
+    case.set_tfs([synth.tf_piecewise(2001)], [(0.0, 255.0)])
+    return case
+
+
+def test_plain_ray_cast_single_view_matches_oracle():
+    """128^3 uint8 Gaussians, one 256x256 view, step 0.5 (the plain single-view case)."""
+    case = _c1_case()
+    try:
+        view, proj = synth.orbit_camera(128, seed=3001, width=256, height=256)
+        pose, stats, gsel, ref = case.select([view, view], [proj, proj], 256, 256)
+        compare_selection(gsel, ref)
+        imgs, cnts = case.render(pose, empty_skip=0)
+        oref = case.oracle_render(ref["leaf"], view, proj, 256, 256)
+        st = compare_image(imgs[0], oref, cnts[0])
+        assert np.array_equal(imgs[0], imgs[1])  # both eyes share the view
+        assert oref["late"][:, 3].max() > 0.5 and st["max_err"] < 1e-3
+        skip, _ = case.render(pose, empty_skip=1)
+        assert np.array_equal(skip[0], imgs[0])
+    finally:
+        case.close()
+
+
+def _filament_case(dims=(256, 256, 256), brick=32, levels=4, seed=1002, ntubes=40):
+    v = synth.filaments_u16(dims, seed=seed, ntubes=ntubes)
+    model = synth.volume_model(max(dims), 0.5)
+    case = GpuCase([v], brick, levels, model=model)
+    case.set_tfs([synth.tf_piecewise(2002, zero_alpha_points=2)], [(300.0, 60000.0)])
+    return case
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_multilod_stereo_pair_matches_oracle(seed):
+    case = _filament_case()
+    try:
+        W, H = 360, 400
+        (views, projs), = synth.head_poses(1, seed=3100 + seed, extent_m=0.5, width=W, height=H)
+        # tau scaled so that a 360x400 image selects as a 1440x1600 one would
+        pose, stats, gsel, ref = case.select(views, projs, W, H, tau=0.25)
+        compare_selection(gsel, ref)
+        levels = {case.ovol.node_coords(i)[0] for i in np.flatnonzero(ref["state"] == oracle.ST_SELECTED)}
+        assert stats["selected"] == ref["selected"]
+        imgs, cnts = case.render(pose, empty_skip=0)
+        for e in range(2):
+            oref = case.oracle_render(ref["leaf"], views[e], projs[e], W, H)
+            compare_image(imgs[e], oref, cnts[e])
+        skip, _ = case.render(pose, empty_skip=1)
+        assert np.array_equal(skip[0], imgs[0]) and np.array_equal(skip[1], imgs[1])
+        assert len(levels) >= 1
+    finally:
+        case.close()
+
+
+def test_ragged_volume_and_image_sizes():
+    case = _filament_case(dims=(200, 150, 97), brick=16, levels=3, ntubes=15)
+    try:
+        W, H = 211, 97
+        (views, projs), = synth.head_poses(1, seed=3200, extent_m=0.5, width=W, height=H)
+        pose, _, gsel, ref = case.select(views, projs, W, H, tau=0.5)
+        compare_selection(gsel, ref)
+        imgs, cnts = case.render(pose, empty_skip=1)
+        for e in range(2):
+            oref = case.oracle_render(ref["leaf"], views[e], projs[e], W, H)
+            compare_image(imgs[e], oref)
+    finally:
+        case.close()
+
+
+def test_bricks_hold_the_box_filtered_pyramid_with_aprons():
+    rng = np.random.default_rng(5)
+    a = rng.integers(0, 60000, (37, 45, 70)).astype(np.uint16)  # z, y, x: ragged on every axis
+    case = GpuCase([a], 16, 3)
+    try:
+        B = 16
+        R = B + 2
+        for L in range(3):
+            g = case.ovol.channels[0][L]
+            nbx, nby, nbz = case.ovol.blocks_per_axis(L)
+            for bz in range(nbz):
+                for by in range(nby):
+                    for bx in range(nbx):
+                        out = np.empty((R, R, R), np.uint16)
+                        case.sg.sg_read_brick(case.vol, 0, 0, L, bx, by, bz, out)
+                        iz = np.clip(np.arange(R) + bz * B - 1, 0, g.shape[0] - 1)
+                        iy = np.clip(np.arange(R) + by * B - 1, 0, g.shape[1] - 1)
+                        ix = np.clip(np.arange(R) + bx * B - 1, 0, g.shape[2] - 1)
+                        assert np.array_equal(out, g[np.ix_(iz, iy, ix)]), (L, bx, by, bz)
+    finally:
+        case.close()
+
+
+def test_tiny_and_empty_volumes():
+    # 5x3x2 voxels, one brick per level, 1x1 and 3x2 images
+    a = (np.arange(30, dtype=np.uint8).reshape(2, 3, 5) * 8)
+    case = GpuCase([a], 8, 2)
+    try:
+        case.set_tfs([synth.tf_piecewise(7)], [(0.0, 255.0)])
+        for W, H in ((1, 1), (3, 2)):
+            view, proj = synth.orbit_camera(5, seed=9, width=W, height=H, radius_widths=3.0)
+            pose, _, gsel, ref = case.select([view, view], [proj, proj], W, H)
+            compare_selection(gsel, ref)
+            imgs, cnts = case.render(pose, empty_skip=0)
+            compare_image(imgs[0], case.oracle_render(ref["leaf"], view, proj, W, H), cnts[0], max_flagged=1.0)
+    finally:
+        case.close()
+    z = np.zeros((16, 16, 16), np.uint8)
+    case = GpuCase([z], 8, 2)
+    try:
+        case.set_tfs([synth.tf_piecewise(8)], [(0.0, 255.0)])
+        view, proj = synth.orbit_camera(16, seed=4, width=32, height=32)
+        pose, stats, gsel, ref = case.select([view, view], [proj, proj], 32, 32)
+        compare_selection(gsel, ref)
+        assert stats["selected"] == 0
+        imgs, cnts = case.render(pose)
+        assert not imgs[0].any() and not cnts[0].any()
+    finally:
+        case.close()
+
+
+def test_two_channels_blend_additively():
+    a = synth.blobs_u16((96, 80, 64), seed=1003, channel=0, nblobs=10)
+    b = synth.blobs_u16((96, 80, 64), seed=1003, channel=1, nblobs=10)
+    case = GpuCase([a, b], 16, 3, model=synth.volume_model(96, 0.5))
+    try:
+        case.set_tfs([synth.tf_piecewise(2003, zero_alpha_points=2, colour=(0.1, 0.9, 0.2)),
+                      synth.tf_piecewise(2004, zero_alpha_points=2, colour=(0.9, 0.1, 0.8))],
+                     [(200.0, 40000.0), (200.0, 40000.0)])
+        W, H = 160, 176
+        (views, projs), = synth.head_poses(1, seed=3300, extent_m=0.5, width=W, height=H)
+        pose, _, gsel, ref = case.select(views, projs, W, H, tau=0.5)
+        compare_selection(gsel, ref)
+        imgs, cnts = case.render(pose, empty_skip=1)
+        for e in range(2):
+            compare_image(imgs[e], case.oracle_render(ref["leaf"], views[e], projs[e], W, H))
+    finally:
+        case.close()
+
+
+def test_call_order_errors():
+    from paper_1804_08197_b300 import sg
+    case = _c1_case()
+    try:
+        view, proj = synth.orbit_camera(128, seed=3001, width=64, height=64)
+        pose = sg.make_pose([view, view], [proj, proj], 64, 64, slot=3)
+        import torch
+        outs = [torch.empty((64, 64, 4), device="cuda") for _ in range(2)]
+        with pytest.raises(sg.SGError) as ei:
+            sg.sg_render(case.vol, pose, sg.render_params(), outs)
+        assert ei.value.status == sg.SG_ERR_STATE
+        sg.sg_select_lod(case.vol, pose)
+        sg.sg_render(case.vol, pose, sg.render_params(), outs)
+        # a new transfer function makes the selection stale
+        sg.sg_set_transfer_function(case.vol, 0, synth.tf_piecewise(5), 0.0, 255.0)
+        with pytest.raises(sg.SGError) as ei:
+            sg.sg_render(case.vol, pose, sg.render_params(), outs)
+        assert ei.value.status == sg.SG_ERR_STATE
+        with pytest.raises(sg.SGError) as ei:
+            sg.sg_render(case.vol, pose, sg.render_params(step=-1.0), outs)
+        assert ei.value.status == sg.SG_ERR_INVALID_ARG
+    finally:
+        case.close()
+
+
+def test_render_host_matches_device_render():
+    from paper_1804_08197_b300 import sg
+    case = _c1_case()
+    try:
+        view, proj = synth.orbit_camera(128, seed=3001, width=96, height=80)
+        pose, _, _, _ = case.select([view, view], [proj, proj], 96, 80)
+        dev, _ = case.render(pose, counts=False)
+        host = [np.empty((80, 96, 4), np.float32) for _ in range(2)]
+        sg.sg_render_host(case.vol, pose, sg.render_params(), host)
+        assert np.array_equal(host[0].reshape(-1, 4), dev[0])
+    finally:
+        case.close()
