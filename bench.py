@@ -47,12 +47,12 @@ def workload_config(extra=None):
     return c
 
 
-def make_inputs():
+def make_inputs(n_vox=N_VOX):
     import synth
-    vol = synth.filaments_u16((N_VOX,) * 3, seed=SEEDS["volume"])
+    vol = synth.filaments_u16((n_vox,) * 3, seed=SEEDS["volume"], ntubes=max(1, 200 * n_vox // N_VOX))
     tf = synth.tf_piecewise(SEEDS["tf"], zero_alpha_points=2)
     poses = synth.head_poses(NPOSES, seed=SEEDS["poses"], width=W_EYE, height=H_EYE)
-    model = synth.volume_model(N_VOX, 0.5)
+    model = synth.volume_model(n_vox, 0.5)
     return vol, tf, poses, model
 
 
@@ -191,8 +191,9 @@ def run_ours(args, rank, world, local_rank):
     from paper_1804_08197_b300 import sg
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    vol_host, tf_table, poses, model = make_inputs()
-    vol = sg.sg_volume_create((N_VOX,) * 3, sg.SG_U16, BRICK, LEVELS, model=model)
+    n_vox = args.volume
+    vol_host, tf_table, poses, model = make_inputs(n_vox)
+    vol = sg.sg_volume_create((n_vox,) * 3, sg.SG_U16, BRICK, LEVELS, model=model)
     d0 = torch.from_numpy(vol_host.view(np.int16)).to(dev)
     sg.sg_upload_volume_device(vol, 0, 0, d0.data_ptr())
     torch.cuda.synchronize()
@@ -265,7 +266,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_s = time.perf_counter() - t0
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and n_vox == N_VOX:
         cpu = cpu_baseline(vol_host, tf_table, poses, model)
 
     if rank == 0:
@@ -273,7 +274,8 @@ def run_ours(args, rank, world, local_rank):
         line = {"metric": METRIC, "value": round(fps, 3), "unit": "stereo frames/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "data": "synthetic", "config": workload_config({"parallelism": f"replicas x{world}"}),
+                "data": "synthetic", "config": workload_config({"parallelism": f"replicas x{world}",
+                                                                "volume": [n_vox] * 3}),
                 "gsamples_per_s": round(samples * world / (ms_max / 1e3) / 1e9, 3),
                 "samples_per_step": samples // args.steps,
                 "render_ms_mean": round(sum(render_ms) / len(render_ms), 4),
@@ -300,6 +302,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--volume", type=int, default=N_VOX, help="volume edge (default 1024; smaller for profiling)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -29,17 +29,20 @@ def _stale():
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force=False, verbose=False):
-    if not force and not _stale():
+def build(force=False, verbose=False, out=None, defines=()):
+    """Compiles csrc/*.cu into `out` (default: the in-tree libsg.so)."""
+    out = out or LIB
+    if out == LIB and not defines and not force and not _stale():
         return LIB
     cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", "-o", LIB + ".tmp"]
+           "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", "-o", out + ".tmp"]
+    cmd += [f"-D{d}" for d in defines]
     if verbose:
         cmd += ["-Xptxas", "-v"]
     cmd += [os.path.join(CSRC, f) for f in SOURCES]
     subprocess.check_call(cmd)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(out + ".tmp", out)
+    return out
 
 
 if __name__ == "__main__":

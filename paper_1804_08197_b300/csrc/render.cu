@@ -19,9 +19,16 @@ namespace sg {
 namespace {
 
 constexpr int kTileW = 16, kTileH = 8, kThreads = kTileW * kTileH;
+// minimum resident CTAs per SM requested from the register allocator
+#ifndef SG_RENDER_MINB
+#define SG_RENDER_MINB 1
+#endif
 
 struct ImageJob {
-  float inv[16];   // (P V M)^-1, column major
+  // ray direction (unnormalised) = dx * x_ndc + dy * y_ndc + d0, voxel space:
+  // the homogeneous unprojection of NDC (x, y, 1) minus w times the eye,
+  // folded on the host in FP64 so the kernel has no near/far cancellation
+  float dx[3], dy[3], d0[3];
   float eye[3];    // voxel space
   int32_t W, H;
   int32_t tile_begin;  // first flat tile index of this image
@@ -52,15 +59,6 @@ struct Args {
   int empty_skip;
   unsigned long long* total_samples;
 };
-
-__device__ inline float4 unproject(const float* m, float x, float y, float z) {
-  float4 r;
-  r.x = m[0] * x + m[4] * y + m[8] * z + m[12];
-  r.y = m[1] * x + m[5] * y + m[9] * z + m[13];
-  r.z = m[2] * x + m[6] * y + m[10] * z + m[14];
-  r.w = m[3] * x + m[7] * y + m[11] * z + m[15];
-  return r;
-}
 
 // first lattice index k >= kmin with t0 + k step >= t (same FP32 expression
 // as the sampling loop, so the split is consistent)
@@ -139,8 +137,17 @@ __device__ inline bool sample_run(const Args& a, const T* __restrict__ brick0, i
   return false;
 }
 
+// exit distance of a ray from the slab [lo, hi] along one axis
+__device__ inline float axis_exit(float o, float d, float inv, float lo, float hi) {
+  return d > 0.0f ? (hi - o) * inv : (d < 0.0f ? (lo - o) * inv : INFINITY);
+}
+
+__device__ inline int cell_of(float p, float Bf, int lo, int hi) {
+  return min(max((int)floorf(p / Bf), lo), hi);
+}
+
 template <typename T, int MAXI>
-__global__ void __launch_bounds__(kThreads) k_render(Args a, Jobs<MAXI> jobs) {
+__global__ void __launch_bounds__(kThreads, SG_RENDER_MINB) k_render(Args a, Jobs<MAXI> jobs) {
   const int tile = blockIdx.x;
   int im = 0;
   while (im + 1 < jobs.n && tile >= jobs.img[im + 1].tile_begin) ++im;
@@ -154,26 +161,27 @@ __global__ void __launch_bounds__(kThreads) k_render(Args a, Jobs<MAXI> jobs) {
 
   const float x = 2.0f * ((float)px + 0.5f) / (float)J.W - 1.0f;
   const float y = 1.0f - 2.0f * ((float)py + 0.5f) / (float)J.H;
-  const float4 pn = unproject(J.inv, x, y, -1.0f), pf = unproject(J.inv, x, y, 1.0f);
-  float3 d = make_float3(pf.x / pf.w - pn.x / pn.w, pf.y / pf.w - pn.y / pn.w, pf.z / pf.w - pn.z / pn.w);
+  float3 d = make_float3(fmaf(J.dx[0], x, fmaf(J.dy[0], y, J.d0[0])), fmaf(J.dx[1], x, fmaf(J.dy[1], y, J.d0[1])),
+                         fmaf(J.dx[2], x, fmaf(J.dy[2], y, J.d0[2])));
   const float dn = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
   d.x *= dn; d.y *= dn; d.z *= dn;
   const float3 o = make_float3(J.eye[0], J.eye[1], J.eye[2]);
+  const float3 inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
 
-  // clip to [0,N]^3
+  // clip to [0,N]^3 (slab method); an axis-parallel ray outside a slab misses
   float tn = -INFINITY, tf = INFINITY;
-  const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
-  float inv[3];
+  {
+    const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z}, ii[3] = {inv.x, inv.y, inv.z};
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    inv[k] = 1.0f / dd[k];
-    if (dd[k] == 0.0f) {
-      if (oo[k] < 0.0f || oo[k] > a.dims0[k]) tf = -INFINITY;
-      continue;
+    for (int k = 0; k < 3; ++k) {
+      if (dd[k] == 0.0f) {
+        if (oo[k] < 0.0f || oo[k] > a.dims0[k]) tf = -INFINITY;
+        continue;
+      }
+      const float t1 = (0.0f - oo[k]) * ii[k], t2 = (a.dims0[k] - oo[k]) * ii[k];
+      tn = fmaxf(tn, fminf(t1, t2));
+      tf = fminf(tf, fmaxf(t1, t2));
     }
-    float t1 = (0.0f - oo[k]) * inv[k], t2 = (a.dims0[k] - oo[k]) * inv[k];
-    tn = fmaxf(tn, fminf(t1, t2));
-    tf = fminf(tf, fmaxf(t1, t2));
   }
   const float t0 = fmaxf(tn, 0.0f), t1 = tf;
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -184,66 +192,61 @@ __global__ void __launch_bounds__(kThreads) k_render(Args a, Jobs<MAXI> jobs) {
 
   if (hit) {
     const float Bf = (float)a.B;
-    int cell[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      float p = fmaf(t0, dd[k], oo[k]);
-      cell[k] = min(max((int)floorf(p / Bf), 0), a.nb0[k] - 1);
-    }
+    int cx = cell_of(fmaf(t0, d.x, o.x), Bf, 0, a.nb0[0] - 1);
+    int cy = cell_of(fmaf(t0, d.y, o.y), Bf, 0, a.nb0[1] - 1);
+    int cz = cell_of(fmaf(t0, d.z, o.z), Bf, 0, a.nb0[2] - 1);
     int knext = 0;
     float tcur = t0;
     bool done = false;
     for (int guard = 0; guard < 4096 && !done; ++guard) {
-      const uint32_t e = __ldg(J.leaf + ((size_t)cell[2] * a.nb0[1] + cell[1]) * a.nb0[0] + cell[0]);
+      const uint32_t e = __ldg(J.leaf + ((size_t)cz * a.nb0[1] + cy) * a.nb0[0] + cx);
       const int L = e & 15;
-      int nlo_c[3], nhi_c[3];
-      float lo[3], hi[3], texit[3];
+      // the block of level L holding this cell: cells [nl, nh), level-0 box [lo, hi]
+      const int nlx = (cx >> L) << L, nly = (cy >> L) << L, nlz = (cz >> L) << L;
+      const int nhx = min(nlx + (1 << L), a.nb0[0]), nhy = min(nly + (1 << L), a.nb0[1]),
+                nhz = min(nlz + (1 << L), a.nb0[2]);
+      const float lox = (float)nlx * Bf, loy = (float)nly * Bf, loz = (float)nlz * Bf;
       const float span = (float)(a.B << L);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        nlo_c[k] = (cell[k] >> L) << L;
-        nhi_c[k] = min(nlo_c[k] + (1 << L), a.nb0[k]);
-        lo[k] = (float)(cell[k] >> L) * span;
-        hi[k] = fminf(lo[k] + span, a.dims0[k]);
-        texit[k] = dd[k] > 0.0f ? (hi[k] - oo[k]) * inv[k] : (dd[k] < 0.0f ? (lo[k] - oo[k]) * inv[k] : INFINITY);
-      }
+      const float hix = fminf(lox + span, a.dims0[0]), hiy = fminf(loy + span, a.dims0[1]),
+                  hiz = fminf(loz + span, a.dims0[2]);
+      const float ex = axis_exit(o.x, d.x, inv.x, lox, hix), ey = axis_exit(o.y, d.y, inv.y, loy, hiy),
+                  ez = axis_exit(o.z, d.z, inv.z, loz, hiz);
       int ax = 0;
-      float tx = texit[0];
-      if (texit[1] < tx) { tx = texit[1]; ax = 1; }
-      if (texit[2] < tx) { tx = texit[2]; ax = 2; }
+      float tx = ex;
+      if (ey < tx) { tx = ey; ax = 1; }
+      if (ez < tx) { tx = ez; ax = 2; }
       const float tend = fminf(tx, t1);
       const bool none = (e & kLeafNone) != 0;
       const bool own_empty = (e & 16u) != 0;
       if (!none && !(a.empty_skip && own_empty) && tend > tcur) {
         const uint32_t slot = (e & ~kLeafNone) >> 5;
         const T* brick0 = reinterpret_cast<const T*>(a.pool + (size_t)slot * a.nch * a.brick_bytes);
-        const float s = __int_as_float((127 - L) << 23);
-        // brick-local origin: level-L block origin (b B) minus the apron minus the half-voxel
-        const float3 nlo = make_float3(lo[0] * s - 0.5f, lo[1] * s - 0.5f, lo[2] * s - 0.5f);
+        const float s = __int_as_float((127 - L) << 23);  // 2^-L
+        // brick-local coordinate = level-L position - block origin + 1 (apron) - 0.5 (voxel centre)
+        const float3 nlo = make_float3(lox * s - 0.5f, loy * s - 0.5f, loz * s - 0.5f);
         if (!a.empty_skip) {
           done = sample_run<T>(a, brick0, L, o, d, t0, tend, knext, nlo, acc, cnt);
         } else {
           // walk the 8^3 sub-blocks of this block between tcur and tend
           const float S = (float)(kSub << L);
           const uint64_t* bits = a.subempty + (size_t)slot * a.sub_words;
-          int si[3];
-          float tmax[3], tdel[3];
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            float p = fmaf(tcur, dd[k], oo[k]);
-            si[k] = min(max((int)floorf((p - lo[k]) / S), 0), a.nsub - 1);
-            if (dd[k] > 0.0f) { tmax[k] = (lo[k] + (si[k] + 1) * S - oo[k]) * inv[k]; tdel[k] = S * inv[k]; }
-            else if (dd[k] < 0.0f) { tmax[k] = (lo[k] + si[k] * S - oo[k]) * inv[k]; tdel[k] = -S * inv[k]; }
-            else { tmax[k] = INFINITY; tdel[k] = INFINITY; }
-          }
+          const int nsm = a.nsub - 1;
+          int sx = min(max((int)floorf((fmaf(tcur, d.x, o.x) - lox) / S), 0), nsm);
+          int sy = min(max((int)floorf((fmaf(tcur, d.y, o.y) - loy) / S), 0), nsm);
+          int sz = min(max((int)floorf((fmaf(tcur, d.z, o.z) - loz) / S), 0), nsm);
+          const int stx = d.x > 0.0f ? 1 : -1, sty = d.y > 0.0f ? 1 : -1, stz = d.z > 0.0f ? 1 : -1;
+          float tmx = d.x != 0.0f ? (lox + (sx + (d.x > 0.0f)) * S - o.x) * inv.x : INFINITY;
+          float tmy = d.y != 0.0f ? (loy + (sy + (d.y > 0.0f)) * S - o.y) * inv.y : INFINITY;
+          float tmz = d.z != 0.0f ? (loz + (sz + (d.z > 0.0f)) * S - o.z) * inv.z : INFINITY;
+          const float tdx = fabsf(S * inv.x), tdy = fabsf(S * inv.y), tdz = fabsf(S * inv.z);
           int kk = knext;
           for (int g2 = 0; g2 < 1024; ++g2) {
             int sa = 0;
-            float ts = tmax[0];
-            if (tmax[1] < ts) { ts = tmax[1]; sa = 1; }
-            if (tmax[2] < ts) { ts = tmax[2]; sa = 2; }
+            float ts = tmx;
+            if (tmy < ts) { ts = tmy; sa = 1; }
+            if (tmz < ts) { ts = tmz; sa = 2; }
             const float tsb = fminf(ts, tend);
-            const int sid = (si[2] * a.nsub + si[1]) * a.nsub + si[0];
+            const int sid = (sz * a.nsub + sy) * a.nsub + sx;
             const bool sub_empty = (__ldg(bits + (sid >> 6)) >> (sid & 63)) & 1ull;
             if (!sub_empty) {
               done = sample_run<T>(a, brick0, L, o, d, t0, tsb, kk, nlo, acc, cnt);
@@ -251,25 +254,46 @@ __global__ void __launch_bounds__(kThreads) k_render(Args a, Jobs<MAXI> jobs) {
             }
             kk = first_k_at(tsb, t0, a, kk);
             if (tsb >= tend) break;
-            si[sa] += dd[sa] > 0.0f ? 1 : -1;
-            if (si[sa] < 0 || si[sa] >= a.nsub) break;
-            tmax[sa] += tdel[sa];
+            if (sa == 0) {
+              sx += stx;
+              if (sx < 0 || sx > nsm) break;
+              tmx += tdx;
+            } else if (sa == 1) {
+              sy += sty;
+              if (sy < 0 || sy > nsm) break;
+              tmy += tdy;
+            } else {
+              sz += stz;
+              if (sz < 0 || sz > nsm) break;
+              tmz += tdz;
+            }
           }
         }
       }
       if (done) break;
       knext = first_k_at(tend, t0, a, knext);
       if (tx >= t1) break;
-      // step into the neighbour across the exit face
-      const int step_c = dd[ax] > 0.0f ? nhi_c[ax] : nlo_c[ax] - 1;
-      if (step_c < 0 || step_c >= a.nb0[ax]) break;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        if (k == ax) continue;
-        float p = fmaf(tx, dd[k], oo[k]);
-        cell[k] = min(max((int)floorf(p / Bf), nlo_c[k]), nhi_c[k] - 1);
+      // step into the neighbour across the exit face; the other coordinates
+      // stay inside this block's cell range
+      if (ax == 0) {
+        const int c = d.x > 0.0f ? nhx : nlx - 1;
+        if (c < 0 || c >= a.nb0[0]) break;
+        cx = c;
+        cy = cell_of(fmaf(tx, d.y, o.y), Bf, nly, nhy - 1);
+        cz = cell_of(fmaf(tx, d.z, o.z), Bf, nlz, nhz - 1);
+      } else if (ax == 1) {
+        const int c = d.y > 0.0f ? nhy : nly - 1;
+        if (c < 0 || c >= a.nb0[1]) break;
+        cy = c;
+        cx = cell_of(fmaf(tx, d.x, o.x), Bf, nlx, nhx - 1);
+        cz = cell_of(fmaf(tx, d.z, o.z), Bf, nlz, nhz - 1);
+      } else {
+        const int c = d.z > 0.0f ? nhz : nlz - 1;
+        if (c < 0 || c >= a.nb0[2]) break;
+        cz = c;
+        cx = cell_of(fmaf(tx, d.x, o.x), Bf, nlx, nhx - 1);
+        cy = cell_of(fmaf(tx, d.y, o.y), Bf, nly, nhy - 1);
       }
-      cell[ax] = step_c;
       tcur = tend;
     }
   }
@@ -333,8 +357,18 @@ bool setup_image(const sg_volume* v, const sg_pose* p, int e, ImageJob* J) {
   mul4(V, M, VM);
   mul4(P, VM, PVM);
   if (!inv4(PVM, inv) || !inv4(VM, vminv)) return false;
-  for (int i = 0; i < 16; ++i) J->inv[i] = (float)inv[i];
-  for (int k = 0; k < 3; ++k) J->eye[k] = (float)(vminv[12 + k] / vminv[15]);
+  double eye[3];
+  for (int k = 0; k < 3; ++k) eye[k] = vminv[12 + k] / vminv[15];
+  // h(x, y) = inv (x, y, 1, 1); direction = h.xyz - h.w eye (the far point
+  // seen from the eye, times h.w); oriented so that it points forward
+  const double hw = inv[11] + inv[15];
+  const double sgn = hw < 0.0 ? -1.0 : 1.0;
+  for (int r = 0; r < 3; ++r) {
+    J->dx[r] = (float)(sgn * (inv[0 + r] - eye[r] * inv[3]));
+    J->dy[r] = (float)(sgn * (inv[4 + r] - eye[r] * inv[7]));
+    J->d0[r] = (float)(sgn * ((inv[8 + r] + inv[12 + r]) - eye[r] * (inv[11] + inv[15])));
+    J->eye[r] = (float)eye[r];
+  }
   J->W = p->width;
   J->H = p->height;
   J->leaf = v->sel[p->slot].d_leaf;

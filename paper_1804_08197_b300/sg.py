@@ -10,7 +10,8 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libsg.so")
+# SG_LIBRARY may point at another build of the same library (e.g. a tuning variant)
+LIB_PATH = os.environ.get("SG_LIBRARY") or os.path.join(HERE, "libsg.so")
 
 SG_OK, SG_ERR_INVALID_ARG, SG_ERR_OOM, SG_ERR_CUDA, SG_ERR_NOT_RESIDENT, SG_ERR_TIMEOUT, SG_ERR_STATE = range(7)
 SG_U8, SG_U16 = 1, 2
