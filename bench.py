@@ -124,7 +124,7 @@ def cpu_baseline(vol, tf_table, poses, model, frac_target_s=15.0):
     views, projs = poses[0]
     setup_s = time.perf_counter() - t_setup
     npix = W_EYE * H_EYE
-    stride = 256
+    stride = 8  # about 10-20 s of oracle work on a 16-core host
     t0 = time.perf_counter()
     sel = ovol.select([otf], views, projs, H_EYE, tau=TAU)
     samples = 0
@@ -149,7 +149,7 @@ def run_reference(args, rank, world):
     vol, tf_table, poses, model = make_inputs()
     ovol = oracle.Volume([oracle.pyramid(vol, LEVELS)], BRICK, model=model)
     otf = oracle.make_tf(tf_table, *WINDOW)
-    stride = 1024
+    stride = 128
     npix = W_EYE * H_EYE
 
     def step(i):
