@@ -219,6 +219,32 @@ sg_status sg_render_host(sg_volume* vol, const sg_pose* pose, const sg_render_pa
 sg_status sg_render_batch(sg_volume* vol, const sg_pose* poses, int n, const sg_render_params* params,
                           float** outs, void* stream);
 
+/* How sg_render / sg_render_batch map rays onto the GPU. tile_w x tile_h
+ * pixel tiles (warps cover 8 x 4 pixels), rays_per_thread rays per thread;
+ * persistent != 0: a grid sized to the GPU pulls tiles from a queue shared by
+ * all images of the launch (balances uneven image sizes), else one CTA per
+ * tile. Supported shapes (w, h, rays): (16,8,1) (8,16,1) (32,4,1) (8,8,1)
+ * (16,16,2) (32,8,2); all zero = the default one-CTA-per-16x8-tile kernel.
+ * Launches of one volume must not overlap on the GPU when persistent. */
+typedef struct {
+  int32_t persistent;
+  int32_t tile_w, tile_h;
+  int32_t rays_per_thread;
+  int32_t reserved[4];
+} sg_render_config;
+
+/* Sets / reads the volume's render configuration. Errors: INVALID_ARG. */
+sg_status sg_set_render_config(sg_volume* vol, const sg_render_config* cfg);
+sg_status sg_get_render_config(sg_volume* vol, sg_render_config* cfg);
+
+/* Autotuner: renders the n selected poses with every supported configuration
+ * (one warm-up launch, then reps timed launches each, CUDA events on the
+ * stream), keeps the fastest as the volume's configuration and returns it
+ * with its mean launch time. Outputs are overwritten. Waits for the stream.
+ * Errors: as sg_render_batch, CUDA. */
+sg_status sg_autotune_render(sg_volume* vol, const sg_pose* poses, int n, const sg_render_params* params,
+                             float** outs, int reps, sg_render_config* best, float* best_ms, void* stream);
+
 /* Thread-local message of the last failure on this thread ("" if none). */
 const char* sg_last_error(void);
 

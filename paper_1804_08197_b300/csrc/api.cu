@@ -526,6 +526,61 @@ sg_status sg_render_batch(sg_volume* v, const sg_pose* poses, int n, const sg_re
   return SG_OK;
 }
 
+sg_status sg_set_render_config(sg_volume* v, const sg_render_config* cfg) {
+  SG_CHECK_ARG(v && cfg, "volume or config NULL");
+  SG_CHECK_ARG(render_config_supported(cfg), "unsupported tile shape / rays per thread");
+  v->render_cfg = *cfg;
+  return SG_OK;
+}
+
+sg_status sg_get_render_config(sg_volume* v, sg_render_config* cfg) {
+  SG_CHECK_ARG(v && cfg, "volume or config NULL");
+  *cfg = v->render_cfg;
+  return SG_OK;
+}
+
+sg_status sg_autotune_render(sg_volume* v, const sg_pose* poses, int n, const sg_render_params* prm, float** outs,
+                             int reps, sg_render_config* best, float* best_ms, void* stream) {
+  SG_CHECK_ARG(v && reps >= 1 && reps <= 1000, "volume NULL or reps not in 1..1000");
+  cudaStream_t s = (cudaStream_t)stream;
+  sg_render_config cand[32];
+  int nc = render_config_candidates(cand, 32);
+  cudaEvent_t e0, e1;
+  SG_CUDA(cudaEventCreate(&e0), "autotune events");
+  SG_CUDA(cudaEventCreate(&e1), "autotune events");
+  const sg_render_config keep = v->render_cfg;
+  float best_t = 1e30f;
+  sg_render_config best_c = keep;
+  sg_status st = SG_OK;
+  for (int i = 0; i < nc && st == SG_OK; ++i) {
+    v->render_cfg = cand[i];
+    st = sg_render_batch(v, poses, n, prm, outs, stream);  // warm-up, also validates the arguments
+    if (st != SG_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && st == SG_OK; ++r) st = sg_render_batch(v, poses, n, prm, outs, stream);
+    cudaEventRecord(e1, s);
+    cudaError_t ce = cudaEventSynchronize(e1);
+    if (ce != cudaSuccess) {
+      st = cuda_fail(ce, "autotune");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (ms < best_t) {
+      best_t = ms;
+      best_c = cand[i];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  v->render_cfg = st == SG_OK ? best_c : keep;
+  if (st != SG_OK) return st;
+  if (best) *best = best_c;
+  if (best_ms) *best_ms = best_t;
+  return SG_OK;
+}
+
 sg_status sg_upload_bricks(sg_volume* v, int t, int c, int level, int n, const int32_t* xyz, const void* host,
                            void* stream) {
   SG_CHECK_ARG(v && xyz && host && n >= 1, "volume/brick_xyz/host NULL or n < 1");

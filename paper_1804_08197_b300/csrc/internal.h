@@ -107,9 +107,10 @@ struct sg_volume {
 
   sg::SelSlot sel[sg::kMaxSlots];
 
+  sg_render_config render_cfg = {};  // tile shape / persistence; zero = default
   float* d_stage = nullptr;  // sg_render_host staging
   size_t stage_bytes = 0;
-  uint32_t* d_err = nullptr; // device error word (bounded waits)
+  uint32_t* d_err = nullptr; // device control block: [0] tile queue head of the persistent render
 };
 
 namespace sg {
@@ -136,5 +137,7 @@ cudaError_t launch_select(sg_volume* v, const sg_pose* poses, int n, cudaStream_
 // render.cu
 cudaError_t launch_render(sg_volume* v, const sg_pose* poses, int n, const sg_render_params* prm,
                           float* const* outs, cudaStream_t s);
+bool render_config_supported(const sg_render_config* c);
+int render_config_candidates(sg_render_config* out, int cap);
 
 }  // namespace sg

@@ -23,6 +23,11 @@ constexpr int kTileW = 16, kTileH = 8, kThreads = kTileW * kTileH;
 #ifndef SG_RENDER_MINB
 #define SG_RENDER_MINB 1
 #endif
+// 1: a sample landing in a transparent 8^3 sub-block jumps to the sub-block's
+// exit; 0: it steps to the next lattice point (cheaper step, more steps)
+#ifndef SG_SUBBLOCK_JUMP
+#define SG_SUBBLOCK_JUMP 1
+#endif
 
 struct ImageJob {
   // ray direction (unnormalised) = dx * x_ndc + dy * y_ndc + d0, voxel space:
@@ -96,45 +101,34 @@ __device__ inline float4 classify(const Args& a, int c, int L, float v) {
                      fmaf(f, e1.w - e0.w, e0.w));
 }
 
-// Samples lattice points k (multiples of 2^L, k >= kfirst) with t_k < t_end
-// inside one block; returns true when the ray terminated.
+// Trilinear value + classification + front-to-back compositing of one sample
+// at brick-local coordinate l (all channels, additive blend). Returns true
+// when the ray is opaque enough to stop.
 template <typename T>
-__device__ inline bool sample_run(const Args& a, const T* __restrict__ brick0, int L, float3 o, float3 d,
-                                  float t0, float t_end, int kfirst, float3 nlo, float4& acc, uint32_t& cnt) {
-  const int kstep = 1 << L;
-  const float s = __int_as_float((127 - L) << 23);  // 2^-L
+__device__ __forceinline__ bool composite_sample(const Args& a, const T* __restrict__ brick0, int L, float lx, float ly,
+                                                 float lz, float4& acc) {
   const int R = a.B + 2;
-  for (int k = (kfirst + kstep - 1) & ~(kstep - 1);; k += kstep) {
-    const float t = fmaf((float)k, a.step, t0);
-    if (!(t < t_end)) break;
-    // brick-local coordinate: level-L position + 0.5 (apron) - 0.5 (voxel centre) - block origin
-    const float lx = fmaf(fmaf(t, d.x, o.x), s, -nlo.x);
-    const float ly = fmaf(fmaf(t, d.y, o.y), s, -nlo.y);
-    const float lz = fmaf(fmaf(t, d.z, o.z), s, -nlo.z);
-    float sa = 0.0f, sr = 0.0f, sg = 0.0f, sb = 0.0f;
-    for (int c = 0; c < a.nch; ++c) {
-      const T* br = reinterpret_cast<const T*>(reinterpret_cast<const uint8_t*>(brick0) + (size_t)c * a.brick_bytes);
-      float v = tri<T>(br, R, lx, ly, lz, a.B);
-      float4 e = classify(a, c, L, v);
-      sa += e.w;
-      sr = fmaf(e.w, e.x, sr);
-      sg = fmaf(e.w, e.y, sg);
-      sb = fmaf(e.w, e.z, sb);
-    }
-    if (sa > 1.0f) {  // additive blend saturates: alpha 1, colour renormalised
-      float r = 1.0f / sa;
-      sr *= r; sg *= r; sb *= r;
-      sa = 1.0f;
-    }
-    const float w = 1.0f - acc.w;
-    acc.x = fmaf(w, sr, acc.x);
-    acc.y = fmaf(w, sg, acc.y);
-    acc.z = fmaf(w, sb, acc.z);
-    acc.w = fmaf(w, sa, acc.w);
-    ++cnt;
-    if (acc.w >= a.term) return true;
+  float sa = 0.0f, sr = 0.0f, sg = 0.0f, sb = 0.0f;
+  for (int c = 0; c < a.nch; ++c) {
+    const T* br = reinterpret_cast<const T*>(reinterpret_cast<const uint8_t*>(brick0) + (size_t)c * a.brick_bytes);
+    const float v = tri<T>(br, R, lx, ly, lz, a.B);
+    const float4 e = classify(a, c, L, v);
+    sa += e.w;
+    sr = fmaf(e.w, e.x, sr);
+    sg = fmaf(e.w, e.y, sg);
+    sb = fmaf(e.w, e.z, sb);
   }
-  return false;
+  if (sa > 1.0f) {  // additive blend saturates: alpha 1, colour renormalised
+    const float r = 1.0f / sa;
+    sr *= r; sg *= r; sb *= r;
+    sa = 1.0f;
+  }
+  const float w = 1.0f - acc.w;
+  acc.x = fmaf(w, sr, acc.x);
+  acc.y = fmaf(w, sg, acc.y);
+  acc.z = fmaf(w, sb, acc.z);
+  acc.w = fmaf(w, sa, acc.w);
+  return acc.w >= a.term;
 }
 
 // exit distance of a ray from the slab [lo, hi] along one axis
@@ -146,19 +140,16 @@ __device__ inline int cell_of(float p, float Bf, int lo, int hi) {
   return min(max((int)floorf(p / Bf), lo), hi);
 }
 
-template <typename T, int MAXI>
-__global__ void __launch_bounds__(kThreads, SG_RENDER_MINB) k_render(Args a, Jobs<MAXI> jobs) {
-  const int tile = blockIdx.x;
-  int im = 0;
-  while (im + 1 < jobs.n && tile >= jobs.img[im + 1].tile_begin) ++im;
-  const ImageJob& J = jobs.img[im];
-  const int lt = tile - J.tile_begin;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // warp = 8 x 4 pixels, CTA = 2 x 2 warps
-  const int px = (lt % J.tiles_x) * kTileW + (warp & 1) * 8 + (lane & 7);
-  const int py = (lt / J.tiles_x) * kTileH + (warp >> 1) * 4 + (lane >> 3);
-  const bool active = px < J.W && py < J.H;
-
+// One ray: pixel (px, py) of image J; acc = premultiplied RGBA, cnt = samples
+// composited. A single flat loop advances the ray by one event per
+// iteration (take a sample, jump over a transparent 8^3 sub-block, or move to
+// the next block), so the lanes of a warp stay in one loop instead of
+// diverging across nested ones.
+template <typename T>
+__device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int px, int py, bool active, float4& acc,
+                                          uint32_t& cnt) {
+  acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  cnt = 0;
   const float x = 2.0f * ((float)px + 0.5f) / (float)J.W - 1.0f;
   const float y = 1.0f - 2.0f * ((float)py + 0.5f) / (float)J.H;
   float3 d = make_float3(fmaf(J.dx[0], x, fmaf(J.dy[0], y, J.d0[0])), fmaf(J.dx[1], x, fmaf(J.dy[1], y, J.d0[1])),
@@ -184,119 +175,127 @@ __global__ void __launch_bounds__(kThreads, SG_RENDER_MINB) k_render(Args a, Job
     }
   }
   const float t0 = fmaxf(tn, 0.0f), t1 = tf;
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  uint32_t cnt = 0;
   // a degenerate matrix gives a NaN direction and an unbounded segment: no hit
   const bool hit = active && isfinite(t0) && isfinite(t1) && t1 > t0 && (t1 - t0) * a.inv_step < 16.0e6f &&
                    isfinite(d.x + d.y + d.z);
+  if (!hit) return;
 
-  if (hit) {
-    const float Bf = (float)a.B;
-    int cx = cell_of(fmaf(t0, d.x, o.x), Bf, 0, a.nb0[0] - 1);
-    int cy = cell_of(fmaf(t0, d.y, o.y), Bf, 0, a.nb0[1] - 1);
-    int cz = cell_of(fmaf(t0, d.z, o.z), Bf, 0, a.nb0[2] - 1);
-    int knext = 0;
-    float tcur = t0;
-    bool done = false;
-    for (int guard = 0; guard < 4096 && !done; ++guard) {
-      const uint32_t e = __ldg(J.leaf + ((size_t)cz * a.nb0[1] + cy) * a.nb0[0] + cx);
-      const int L = e & 15;
-      // the block of level L holding this cell: cells [nl, nh), level-0 box [lo, hi]
-      const int nlx = (cx >> L) << L, nly = (cy >> L) << L, nlz = (cz >> L) << L;
-      const int nhx = min(nlx + (1 << L), a.nb0[0]), nhy = min(nly + (1 << L), a.nb0[1]),
-                nhz = min(nlz + (1 << L), a.nb0[2]);
-      const float lox = (float)nlx * Bf, loy = (float)nly * Bf, loz = (float)nlz * Bf;
-      const float span = (float)(a.B << L);
-      const float hix = fminf(lox + span, a.dims0[0]), hiy = fminf(loy + span, a.dims0[1]),
-                  hiz = fminf(loz + span, a.dims0[2]);
-      const float ex = axis_exit(o.x, d.x, inv.x, lox, hix), ey = axis_exit(o.y, d.y, inv.y, loy, hiy),
-                  ez = axis_exit(o.z, d.z, inv.z, loz, hiz);
-      int ax = 0;
-      float tx = ex;
-      if (ey < tx) { tx = ey; ax = 1; }
-      if (ez < tx) { tx = ez; ax = 2; }
-      const float tend = fminf(tx, t1);
-      const bool none = (e & kLeafNone) != 0;
-      const bool own_empty = (e & 16u) != 0;
-      if (!none && !(a.empty_skip && own_empty) && tend > tcur) {
-        const uint32_t slot = (e & ~kLeafNone) >> 5;
-        const T* brick0 = reinterpret_cast<const T*>(a.pool + (size_t)slot * a.nch * a.brick_bytes);
-        const float s = __int_as_float((127 - L) << 23);  // 2^-L
-        // brick-local coordinate = level-L position - block origin + 1 (apron) - 0.5 (voxel centre)
-        const float3 nlo = make_float3(lox * s - 0.5f, loy * s - 0.5f, loz * s - 0.5f);
-        if (!a.empty_skip) {
-          done = sample_run<T>(a, brick0, L, o, d, t0, tend, knext, nlo, acc, cnt);
+  const float Bf = (float)a.B;
+  int cx = cell_of(fmaf(t0, d.x, o.x), Bf, 0, a.nb0[0] - 1);
+  int cy = cell_of(fmaf(t0, d.y, o.y), Bf, 0, a.nb0[1] - 1);
+  int cz = cell_of(fmaf(t0, d.z, o.z), Bf, 0, a.nb0[2] - 1);
+  int k = 0;            // next lattice point
+  int kb = 0;           // first lattice point owned by the current block
+  int L = 0, kstep = 1; // current block's level and lattice stride
+  int ax = -1;          // axis through which the current block is left (-1: no block yet)
+  float tend = -1.0f;   // exit of the current block (clipped to t1)
+  float texit = -1.0f;  // unclipped exit
+  uint32_t slot = 0;
+  float3 lo = make_float3(0.f, 0.f, 0.f);  // block origin, level-0 voxels
+  float sL = 1.0f;                         // 2^-L
+  bool render = false;
+  const int nsm = a.nsub - 1;
+
+  for (int guard = 0; guard < (1 << 25); ++guard) {
+    const float t = fmaf((float)k, a.step, t0);
+    if (!render || !(t < tend)) {
+      // ---- leave the current block and enter the next one
+      if (ax >= 0) {
+        if (texit >= t1) break;
+        const int nl_x = (cx >> L) << L, nl_y = (cy >> L) << L, nl_z = (cz >> L) << L;
+        const int nh_x = min(nl_x + (1 << L), a.nb0[0]), nh_y = min(nl_y + (1 << L), a.nb0[1]),
+                  nh_z = min(nl_z + (1 << L), a.nb0[2]);
+        if (ax == 0) {
+          const int c = d.x > 0.0f ? nh_x : nl_x - 1;
+          if (c < 0 || c >= a.nb0[0]) break;
+          cy = cell_of(fmaf(texit, d.y, o.y), Bf, nl_y, nh_y - 1);
+          cz = cell_of(fmaf(texit, d.z, o.z), Bf, nl_z, nh_z - 1);
+          cx = c;
+        } else if (ax == 1) {
+          const int c = d.y > 0.0f ? nh_y : nl_y - 1;
+          if (c < 0 || c >= a.nb0[1]) break;
+          cx = cell_of(fmaf(texit, d.x, o.x), Bf, nl_x, nh_x - 1);
+          cz = cell_of(fmaf(texit, d.z, o.z), Bf, nl_z, nh_z - 1);
+          cy = c;
         } else {
-          // walk the 8^3 sub-blocks of this block between tcur and tend
-          const float S = (float)(kSub << L);
-          const uint64_t* bits = a.subempty + (size_t)slot * a.sub_words;
-          const int nsm = a.nsub - 1;
-          int sx = min(max((int)floorf((fmaf(tcur, d.x, o.x) - lox) / S), 0), nsm);
-          int sy = min(max((int)floorf((fmaf(tcur, d.y, o.y) - loy) / S), 0), nsm);
-          int sz = min(max((int)floorf((fmaf(tcur, d.z, o.z) - loz) / S), 0), nsm);
-          const int stx = d.x > 0.0f ? 1 : -1, sty = d.y > 0.0f ? 1 : -1, stz = d.z > 0.0f ? 1 : -1;
-          float tmx = d.x != 0.0f ? (lox + (sx + (d.x > 0.0f)) * S - o.x) * inv.x : INFINITY;
-          float tmy = d.y != 0.0f ? (loy + (sy + (d.y > 0.0f)) * S - o.y) * inv.y : INFINITY;
-          float tmz = d.z != 0.0f ? (loz + (sz + (d.z > 0.0f)) * S - o.z) * inv.z : INFINITY;
-          const float tdx = fabsf(S * inv.x), tdy = fabsf(S * inv.y), tdz = fabsf(S * inv.z);
-          int kk = knext;
-          for (int g2 = 0; g2 < 1024; ++g2) {
-            int sa = 0;
-            float ts = tmx;
-            if (tmy < ts) { ts = tmy; sa = 1; }
-            if (tmz < ts) { ts = tmz; sa = 2; }
-            const float tsb = fminf(ts, tend);
-            const int sid = (sz * a.nsub + sy) * a.nsub + sx;
-            const bool sub_empty = (__ldg(bits + (sid >> 6)) >> (sid & 63)) & 1ull;
-            if (!sub_empty) {
-              done = sample_run<T>(a, brick0, L, o, d, t0, tsb, kk, nlo, acc, cnt);
-              if (done) break;
-            }
-            kk = first_k_at(tsb, t0, a, kk);
-            if (tsb >= tend) break;
-            if (sa == 0) {
-              sx += stx;
-              if (sx < 0 || sx > nsm) break;
-              tmx += tdx;
-            } else if (sa == 1) {
-              sy += sty;
-              if (sy < 0 || sy > nsm) break;
-              tmy += tdy;
-            } else {
-              sz += stz;
-              if (sz < 0 || sz > nsm) break;
-              tmz += tdz;
-            }
-          }
+          const int c = d.z > 0.0f ? nh_z : nl_z - 1;
+          if (c < 0 || c >= a.nb0[2]) break;
+          cx = cell_of(fmaf(texit, d.x, o.x), Bf, nl_x, nh_x - 1);
+          cy = cell_of(fmaf(texit, d.y, o.y), Bf, nl_y, nh_y - 1);
+          cz = c;
         }
+        // lattice points before the exit belong to the block just left
+        k = first_k_at(tend, t0, a, kb);
       }
-      if (done) break;
-      knext = first_k_at(tend, t0, a, knext);
-      if (tx >= t1) break;
-      // step into the neighbour across the exit face; the other coordinates
-      // stay inside this block's cell range
-      if (ax == 0) {
-        const int c = d.x > 0.0f ? nhx : nlx - 1;
-        if (c < 0 || c >= a.nb0[0]) break;
-        cx = c;
-        cy = cell_of(fmaf(tx, d.y, o.y), Bf, nly, nhy - 1);
-        cz = cell_of(fmaf(tx, d.z, o.z), Bf, nlz, nhz - 1);
-      } else if (ax == 1) {
-        const int c = d.y > 0.0f ? nhy : nly - 1;
-        if (c < 0 || c >= a.nb0[1]) break;
-        cy = c;
-        cx = cell_of(fmaf(tx, d.x, o.x), Bf, nlx, nhx - 1);
-        cz = cell_of(fmaf(tx, d.z, o.z), Bf, nlz, nhz - 1);
-      } else {
-        const int c = d.z > 0.0f ? nhz : nlz - 1;
-        if (c < 0 || c >= a.nb0[2]) break;
-        cz = c;
-        cx = cell_of(fmaf(tx, d.x, o.x), Bf, nlx, nhx - 1);
-        cy = cell_of(fmaf(tx, d.y, o.y), Bf, nly, nhy - 1);
-      }
-      tcur = tend;
+      const uint32_t e = __ldg(J.leaf + ((size_t)cz * a.nb0[1] + cy) * a.nb0[0] + cx);
+      L = e & 15;
+      const int nl_x = (cx >> L) << L, nl_y = (cy >> L) << L, nl_z = (cz >> L) << L;
+      lo = make_float3((float)nl_x * Bf, (float)nl_y * Bf, (float)nl_z * Bf);
+      const float span = (float)(a.B << L);
+      const float ex = axis_exit(o.x, d.x, inv.x, lo.x, fminf(lo.x + span, a.dims0[0]));
+      const float ey = axis_exit(o.y, d.y, inv.y, lo.y, fminf(lo.y + span, a.dims0[1]));
+      const float ez = axis_exit(o.z, d.z, inv.z, lo.z, fminf(lo.z + span, a.dims0[2]));
+      ax = 0;
+      texit = ex;
+      if (ey < texit) { texit = ey; ax = 1; }
+      if (ez < texit) { texit = ez; ax = 2; }
+      tend = fminf(texit, t1);
+      kb = k;
+      render = !(e & kLeafNone) && !(a.empty_skip && (e & 16u));
+      if (!render) continue;  // owns its lattice points without sampling them: leave at once
+      kstep = 1 << L;
+      k = (k + kstep - 1) & ~(kstep - 1);
+      slot = (e & ~kLeafNone) >> 5;
+      sL = __int_as_float((127 - L) << 23);
+      continue;
     }
+    // ---- lattice point k lies in a rendered block of level L
+    const float px0 = fmaf(t, d.x, o.x), py0 = fmaf(t, d.y, o.y), pz0 = fmaf(t, d.z, o.z);
+    // brick-local coordinate: level-L position - block origin + 1 (apron) - 0.5 (voxel centre)
+    const float lx = fmaf(px0 - lo.x, sL, 0.5f), ly = fmaf(py0 - lo.y, sL, 0.5f), lz = fmaf(pz0 - lo.z, sL, 0.5f);
+    if (a.empty_skip) {
+      const int sx = min(max((int)floorf((lx - 0.5f) * 0.125f), 0), nsm);
+      const int sy = min(max((int)floorf((ly - 0.5f) * 0.125f), 0), nsm);
+      const int sz = min(max((int)floorf((lz - 0.5f) * 0.125f), 0), nsm);
+      const int sid = (sz * a.nsub + sy) * a.nsub + sx;
+      if ((__ldg(a.subempty + (size_t)slot * a.sub_words + (sid >> 6)) >> (sid & 63)) & 1ull) {
+#if SG_SUBBLOCK_JUMP
+        // transparent sub-block: jump to its exit (lattice points before it are skipped)
+        const float S = (float)(kSub << L);
+        const float bx = fmaf((float)sx, S, lo.x), by = fmaf((float)sy, S, lo.y), bz = fmaf((float)sz, S, lo.z);
+        const float ts = fminf(fminf(axis_exit(o.x, d.x, inv.x, bx, bx + S), axis_exit(o.y, d.y, inv.y, by, by + S)),
+                               fminf(axis_exit(o.z, d.z, inv.z, bz, bz + S), tend));
+        k = max(first_k_at(ts, t0, a, k), k + 1);
+        k = (k + kstep - 1) & ~(kstep - 1);
+#else
+        k += kstep;
+#endif
+        continue;
+      }
+    }
+    const T* brick0 = reinterpret_cast<const T*>(a.pool + (size_t)slot * a.nch * a.brick_bytes);
+    ++cnt;
+    if (composite_sample<T>(a, brick0, L, lx, ly, lz, acc)) break;
+    k += kstep;
   }
+}
+
+template <typename T, int MAXI>
+__global__ void __launch_bounds__(kThreads, SG_RENDER_MINB) k_render(Args a, Jobs<MAXI> jobs) {
+  const int tile = blockIdx.x;
+  int im = 0;
+  while (im + 1 < jobs.n && tile >= jobs.img[im + 1].tile_begin) ++im;
+  const ImageJob& J = jobs.img[im];
+  const int lt = tile - J.tile_begin;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // warp = 8 x 4 pixels, CTA = 2 x 2 warps
+  const int px = (lt % J.tiles_x) * kTileW + (warp & 1) * 8 + (lane & 7);
+  const int py = (lt / J.tiles_x) * kTileH + (warp >> 1) * 4 + (lane >> 3);
+  const bool active = px < J.W && py < J.H;
+
+  float4 acc;
+  uint32_t cnt;
+  trace_ray<T>(a, J, px, py, active, acc, cnt);
   if (active) {
     const size_t pix = (size_t)py * J.W + px;
     J.out[pix] = acc;
@@ -306,6 +305,58 @@ __global__ void __launch_bounds__(kThreads, SG_RENDER_MINB) k_render(Args a, Job
     __syncwarp();
     const unsigned c = __reduce_add_sync(0xffffffffu, cnt);
     if (lane == 0) atomicAdd(a.total_samples, (unsigned long long)c);
+  }
+}
+
+// Tiles of TW x TH pixels (warps cover 8 x 4 sub-tiles), RPT rays per thread.
+// PERSIST: a grid sized to the machine pulls tiles from a global counter
+// (work queue over all images of the batch, whatever their sizes); else one
+// CTA per tile.
+template <typename T, int TW, int TH, int RPT, bool PERSIST>
+__global__ void __launch_bounds__(TW * TH / RPT) k_render_tiles(Args a, Jobs<128> jobs, int* __restrict__ counter) {
+  constexpr int kN = TW * TH / RPT;
+  constexpr int kSubX = TW / 8;
+  __shared__ int s_tile;
+  uint32_t total = 0;
+  for (int it = 0;; ++it) {
+    int tile;
+    if (PERSIST) {
+      if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
+      __syncthreads();
+      tile = s_tile;
+      __syncthreads();
+    } else {
+      if (it > 0) break;
+      tile = blockIdx.x;
+    }
+    if (tile >= jobs.total_tiles) break;
+    int im = 0;
+    while (im + 1 < jobs.n && tile >= jobs.img[im + 1].tile_begin) ++im;
+    const ImageJob& J = jobs.img[im];
+    const int lt = tile - J.tile_begin;
+    const int tx = lt % J.tiles_x, ty = lt / J.tiles_x;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int idx = threadIdx.x + r * kN;
+      const int sub = idx >> 5, lane = idx & 31;
+      const int px = tx * TW + (sub % kSubX) * 8 + (lane & 7);
+      const int py = ty * TH + (sub / kSubX) * 4 + (lane >> 3);
+      const bool active = px < J.W && py < J.H;
+      float4 acc;
+      uint32_t cnt;
+      trace_ray<T>(a, J, px, py, active, acc, cnt);
+      if (active) {
+        const size_t pix = (size_t)py * J.W + px;
+        J.out[pix] = acc;
+        if (J.cnt) J.cnt[pix] = cnt;
+      }
+      total += cnt;
+    }
+  }
+  if (a.total_samples) {
+    __syncwarp();
+    const unsigned c = __reduce_add_sync(0xffffffffu, total);
+    if ((threadIdx.x & 31) == 0) atomicAdd(a.total_samples, (unsigned long long)c);
   }
 }
 
@@ -375,9 +426,7 @@ bool setup_image(const sg_volume* v, const sg_pose* p, int e, ImageJob* J) {
   return true;
 }
 
-template <int MAXI>
-cudaError_t launch_impl(sg_volume* v, const sg_pose* poses, int n, const sg_render_params* prm, float* const* outs,
-                        cudaStream_t s) {
+Args make_args(const sg_volume* v, const sg_render_params* prm) {
   Args a;
   a.pool = v->d_pool;
   a.brick_bytes = v->brick_bytes;
@@ -402,26 +451,80 @@ cudaError_t launch_impl(sg_volume* v, const sg_pose* poses, int n, const sg_rend
   a.term = prm->term_alpha > 0.0f ? prm->term_alpha : 0.99f;
   a.empty_skip = prm->empty_skip;
   a.total_samples = prm->sample_total;
+  return a;
+}
 
-  Jobs<MAXI> jobs;
+template <int MAXI>
+bool make_jobs(const sg_volume* v, const sg_pose* poses, int n, const sg_render_params* prm, float* const* outs,
+               int TW, int TH, Jobs<MAXI>* jobs) {
   int ni = 0, tiles = 0;
   for (int i = 0; i < n; ++i)
     for (int e = 0; e < 2; ++e) {
-      ImageJob& J = jobs.img[ni];
-      if (!setup_image(v, &poses[i], e, &J)) return cudaErrorInvalidValue;
+      ImageJob& J = jobs->img[ni];
+      if (!setup_image(v, &poses[i], e, &J)) return false;
       J.out = reinterpret_cast<float4*>(outs[2 * i + e]);
-      J.cnt = (n == 1 && prm->sample_count[e]) ? prm->sample_count[e] : nullptr;
-      J.tiles_x = (J.W + kTileW - 1) / kTileW;
+      J.cnt = prm->sample_count[e] && n == 1 ? prm->sample_count[e] : nullptr;
+      J.tiles_x = (J.W + TW - 1) / TW;
       J.tile_begin = tiles;
-      tiles += J.tiles_x * ((J.H + kTileH - 1) / kTileH);
+      tiles += J.tiles_x * ((J.H + TH - 1) / TH);
       ++ni;
     }
-  jobs.n = ni;
-  jobs.total_tiles = tiles;
+  jobs->n = ni;
+  jobs->total_tiles = tiles;
+  return true;
+}
+
+template <typename T, int TW, int TH, int RPT>
+cudaError_t launch_tiles(sg_volume* v, const Args& a, const Jobs<128>& jobs, bool persist, cudaStream_t s) {
+  constexpr int kN = TW * TH / RPT;
+  if (!persist) {
+    k_render_tiles<T, TW, TH, RPT, false><<<jobs.total_tiles, kN, 0, s>>>(a, jobs, nullptr);
+    return cudaGetLastError();
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_tiles<T, TW, TH, RPT, true>, kN, 0);
+  if (per_sm < 1) per_sm = 1;
+  int grid = sms * per_sm;
+  if (grid > jobs.total_tiles) grid = jobs.total_tiles;
+  // word 0 of the volume's device control block is the tile queue head
+  cudaError_t e = cudaMemsetAsync(v->d_err, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  k_render_tiles<T, TW, TH, RPT, true><<<grid, kN, 0, s>>>(a, jobs, reinterpret_cast<int*>(v->d_err));
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t dispatch_tiles(sg_volume* v, const Args& a, const sg_pose* poses, int n, const sg_render_params* prm,
+                           float* const* outs, const sg_render_config& c, cudaStream_t s) {
+  Jobs<128> jobs;  // by-value kernel parameter block (about 13 KB)
+  const bool p = c.persistent != 0;
+#define SG_TILE(TW, TH, RPT)                                                              \
+  if (c.tile_w == TW && c.tile_h == TH && c.rays_per_thread == RPT) {                     \
+    if (!make_jobs<128>(v, poses, n, prm, outs, TW, TH, &jobs)) return cudaErrorInvalidValue; \
+    return launch_tiles<T, TW, TH, RPT>(v, a, jobs, p, s);                                \
+  }
+  SG_TILE(16, 8, 1)
+  SG_TILE(8, 16, 1)
+  SG_TILE(32, 4, 1)
+  SG_TILE(8, 8, 1)
+  SG_TILE(16, 16, 2)
+  SG_TILE(32, 8, 2)
+#undef SG_TILE
+  return cudaErrorInvalidValue;
+}
+
+template <int MAXI>
+cudaError_t launch_impl(sg_volume* v, const sg_pose* poses, int n, const sg_render_params* prm, float* const* outs,
+                        cudaStream_t s) {
+  Args a = make_args(v, prm);
+  Jobs<MAXI> jobs;
+  if (!make_jobs<MAXI>(v, poses, n, prm, outs, kTileW, kTileH, &jobs)) return cudaErrorInvalidValue;
   if (v->esize == 1)
-    k_render<uint8_t, MAXI><<<tiles, kThreads, 0, s>>>(a, jobs);
+    k_render<uint8_t, MAXI><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
   else
-    k_render<uint16_t, MAXI><<<tiles, kThreads, 0, s>>>(a, jobs);
+    k_render<uint16_t, MAXI><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
   return cudaGetLastError();
 }
 
@@ -429,9 +532,39 @@ cudaError_t launch_impl(sg_volume* v, const sg_pose* poses, int n, const sg_rend
 
 cudaError_t launch_render(sg_volume* v, const sg_pose* poses, int n, const sg_render_params* prm, float* const* outs,
                           cudaStream_t s) {
-  if (n <= 1) return launch_impl<2>(v, poses, n, prm, outs, s);
-  if (n <= 64) return launch_impl<128>(v, poses, n, prm, outs, s);
-  return cudaErrorInvalidValue;
+  if (n < 1 || n > 64) return cudaErrorInvalidValue;
+  const sg_render_config& c = v->render_cfg;
+  if (c.tile_w == 0) {  // default: one 16 x 8 CTA per tile
+    if (n == 1) return launch_impl<2>(v, poses, n, prm, outs, s);
+    return launch_impl<128>(v, poses, n, prm, outs, s);
+  }
+  Args a = make_args(v, prm);
+  if (v->esize == 1) return dispatch_tiles<uint8_t>(v, a, poses, n, prm, outs, c, s);
+  return dispatch_tiles<uint16_t>(v, a, poses, n, prm, outs, c, s);
+}
+
+bool render_config_supported(const sg_render_config* c) {
+  const int shapes[][3] = {{16, 8, 1}, {8, 16, 1}, {32, 4, 1}, {8, 8, 1}, {16, 16, 2}, {32, 8, 2}};
+  if (c->tile_w == 0 && c->tile_h == 0) return true;
+  for (auto& sh : shapes)
+    if (c->tile_w == sh[0] && c->tile_h == sh[1] && c->rays_per_thread == sh[2]) return true;
+  return false;
+}
+
+int render_config_candidates(sg_render_config* out, int cap) {
+  const int shapes[][3] = {{16, 8, 1}, {8, 16, 1}, {32, 4, 1}, {8, 8, 1}, {16, 16, 2}, {32, 8, 2}};
+  int k = 0;
+  for (int p = 0; p < 2; ++p)
+    for (auto& sh : shapes) {
+      if (k >= cap) return k;
+      sg_render_config c = {};
+      c.persistent = p;
+      c.tile_w = sh[0];
+      c.tile_h = sh[1];
+      c.rays_per_thread = sh[2];
+      out[k++] = c;
+    }
+  return k;
 }
 
 }  // namespace sg

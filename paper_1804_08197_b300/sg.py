@@ -21,7 +21,8 @@ STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_OOM", 3: "SG_ERR
 
 EXPORTS = ["sg_volume_create", "sg_volume_destroy", "sg_upload_volume_device", "sg_upload_bricks",
            "sg_set_transfer_function", "sg_select_lod", "sg_select_lod_batch", "sg_read_selection", "sg_read_brick",
-           "sg_render", "sg_render_host", "sg_render_batch", "sg_last_error", "sg_version"]
+           "sg_render", "sg_render_host", "sg_render_batch", "sg_set_render_config", "sg_get_render_config",
+           "sg_autotune_render", "sg_last_error", "sg_version"]
 
 
 class SGError(RuntimeError):
@@ -55,6 +56,15 @@ class sg_render_params(ctypes.Structure):
                 ("sample_total", ctypes.c_void_p)]
 
 
+class sg_render_config(ctypes.Structure):
+    _fields_ = [("persistent", ctypes.c_int32), ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
+                ("rays_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+    def as_dict(self):
+        return dict(persistent=self.persistent, tile_w=self.tile_w, tile_h=self.tile_h,
+                    rays_per_thread=self.rays_per_thread)
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libsg.so not built at {LIB_PATH}: run python -m paper_1804_08197_b300.build")
@@ -74,6 +84,10 @@ def _load():
         "sg_render": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
         "sg_render_host": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
         "sg_render_batch": [vp, P(sg_pose), i32, P(sg_render_params), P(vp), vp],
+        "sg_set_render_config": [vp, P(sg_render_config)],
+        "sg_get_render_config": [vp, P(sg_render_config)],
+        "sg_autotune_render": [vp, P(sg_pose), i32, P(sg_render_params), P(vp), i32, P(sg_render_config),
+                               P(ctypes.c_float), vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -221,3 +235,26 @@ def sg_render_batch(vol, poses, params, outs, stream=None):
     parr = (sg_pose * len(poses))(*poses)
     oarr = (ctypes.c_void_p * len(outs))(*[_ptr(o).value for o in outs])
     _check(lib.sg_render_batch(vol, parr, len(poses), ctypes.byref(params), oarr, _stream(stream)))
+
+
+def sg_set_render_config(vol, persistent=0, tile_w=0, tile_h=0, rays_per_thread=1):
+    c = sg_render_config()
+    c.persistent, c.tile_w, c.tile_h, c.rays_per_thread = persistent, tile_w, tile_h, rays_per_thread
+    _check(lib.sg_set_render_config(vol, ctypes.byref(c)))
+
+
+def sg_get_render_config(vol):
+    c = sg_render_config()
+    _check(lib.sg_get_render_config(vol, ctypes.byref(c)))
+    return c.as_dict()
+
+
+def sg_autotune_render(vol, poses, params, outs, reps=3, stream=None):
+    """Returns (best config dict, mean ms per launch); the volume keeps the best."""
+    parr = (sg_pose * len(poses))(*poses)
+    oarr = (ctypes.c_void_p * len(outs))(*[_ptr(o).value for o in outs])
+    best = sg_render_config()
+    ms = ctypes.c_float(0.0)
+    _check(lib.sg_autotune_render(vol, parr, len(poses), ctypes.byref(params), oarr, reps, ctypes.byref(best),
+                                  ctypes.byref(ms), _stream(stream)))
+    return best.as_dict(), ms.value
