@@ -65,38 +65,53 @@ struct Args {
   unsigned long long* total_samples;
 };
 
-// first lattice index k >= kmin with t0 + k step >= t (same FP32 expression
-// as the sampling loop, so the split is consistent)
+// Exact integer <-> float conversions on the FMA/ALU pipes (the conversion
+// unit runs at a fraction of the FMA rate, and the loop below needs several
+// per sample): an integer 0 <= v < 2^23 is OR-ed into the mantissa of 2^23
+// and 2^23 subtracted; floor/ceil of |x| < 2^22 is read from the mantissa of
+// x + 1.5 * 2^23 added with round-down / round-up.
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+constexpr int kMagicBits = 0x4B400000;
+__device__ __forceinline__ float u2f(uint32_t v) { return __int_as_float(0x4B000000 | v) - 8388608.0f; }
+__device__ __forceinline__ int floor_i(float x) { return __float_as_int(__fadd_rd(x, kMagic)) - kMagicBits; }
+__device__ __forceinline__ int ceil_i(float x) { return __float_as_int(__fadd_ru(x, kMagic)) - kMagicBits; }
+__device__ __forceinline__ float floor_f(float x) { return __fadd_rd(x, kMagic) - kMagic; }
+
+// lattice point k: t0 + k step, the one FP32 expression every owner test uses
+__device__ __forceinline__ float lattice_t(int k, float t0, const Args& a) { return fmaf(u2f((uint32_t)k), a.step, t0); }
+
+// first lattice index k >= kmin with t_k >= t (exact: the ownership split
+// between blocks uses it)
 __device__ inline int first_k_at(float t, float t0, const Args& a, int kmin) {
-  float kf = ceilf((t - t0) * a.inv_step);
-  int k = kf > (float)kmin ? (int)fminf(kf, 1.0e9f) : kmin;
-  while (k > kmin && fmaf((float)(k - 1), a.step, t0) >= t) --k;
-  while (fmaf((float)k, a.step, t0) < t) ++k;
+  int k = max(ceil_i((t - t0) * a.inv_step), kmin);
+  while (k > kmin && lattice_t(k - 1, t0, a) >= t) --k;
+  while (lattice_t(k, t0, a) < t) ++k;
   return k;
 }
 
 template <typename T>
-__device__ inline float tri(const T* __restrict__ b, int R, float lx, float ly, float lz, int B) {
-  float fx = floorf(lx), fy = floorf(ly), fz = floorf(lz);
-  int ix = min(max((int)fx, 0), B), iy = min(max((int)fy, 0), B), iz = min(max((int)fz, 0), B);
-  float wx = lx - fx, wy = ly - fy, wz = lz - fz;
+__device__ __forceinline__ float tri(const T* __restrict__ b, int R, float lx, float ly, float lz, int B) {
+  const float fx = floor_f(lx), fy = floor_f(ly), fz = floor_f(lz);
+  const int ix = min(max(floor_i(lx), 0), B), iy = min(max(floor_i(ly), 0), B), iz = min(max(floor_i(lz), 0), B);
+  const float wx = lx - fx, wy = ly - fy, wz = lz - fz;
   const T* p = b + ((size_t)iz * R + iy) * R + ix;
   const size_t RR = (size_t)R * R;
-  float v000 = p[0], v100 = p[1], v010 = p[R], v110 = p[R + 1];
-  float v001 = p[RR], v101 = p[RR + 1], v011 = p[RR + R], v111 = p[RR + R + 1];
-  float c00 = fmaf(wx, v100 - v000, v000), c10 = fmaf(wx, v110 - v010, v010);
-  float c01 = fmaf(wx, v101 - v001, v001), c11 = fmaf(wx, v111 - v011, v011);
-  float c0 = fmaf(wy, c10 - c00, c00), c1 = fmaf(wy, c11 - c01, c01);
+  const float v000 = u2f(p[0]), v100 = u2f(p[1]), v010 = u2f(p[R]), v110 = u2f(p[R + 1]);
+  const float v001 = u2f(p[RR]), v101 = u2f(p[RR + 1]), v011 = u2f(p[RR + R]), v111 = u2f(p[RR + R + 1]);
+  const float c00 = fmaf(wx, v100 - v000, v000), c10 = fmaf(wx, v110 - v010, v010);
+  const float c01 = fmaf(wx, v101 - v001, v001), c11 = fmaf(wx, v111 - v011, v011);
+  const float c0 = fmaf(wy, c10 - c00, c00), c1 = fmaf(wy, c11 - c01, c01);
   return fmaf(wz, c1 - c0, c0);
 }
 
-__device__ inline float4 classify(const Args& a, int c, int L, float v) {
-  float x = fminf(fmaxf((v - a.lo[c]) * a.inv_w[c], 0.0f), 1.0f);
-  float q = x * (float)(a.n[c] - 1);
-  int i = min((int)q, a.n[c] - 2);
-  float f = q - (float)i;
+__device__ __forceinline__ float4 classify(const Args& a, int c, int L, float v) {
+  const float x = fminf(fmaxf((v - a.lo[c]) * a.inv_w[c], 0.0f), 1.0f);
+  const float q = x * (float)(a.n[c] - 1);
+  const float fl = fminf(floor_f(q), (float)(a.n[c] - 2));  // entry index as an exact float
+  const int i = __float_as_int(fl + kMagic) - kMagicBits;
+  const float f = q - fl;
   const float4* t = a.lut + ((size_t)c * a.levels + L) * kMaxTF + i;
-  float4 e0 = __ldg(t), e1 = __ldg(t + 1);
+  const float4 e0 = __ldg(t), e1 = __ldg(t + 1);
   return make_float4(fmaf(f, e1.x - e0.x, e0.x), fmaf(f, e1.y - e0.y, e0.y), fmaf(f, e1.z - e0.z, e0.z),
                      fmaf(f, e1.w - e0.w, e0.w));
 }
@@ -136,8 +151,8 @@ __device__ inline float axis_exit(float o, float d, float inv, float lo, float h
   return d > 0.0f ? (hi - o) * inv : (d < 0.0f ? (lo - o) * inv : INFINITY);
 }
 
-__device__ inline int cell_of(float p, float Bf, int lo, int hi) {
-  return min(max((int)floorf(p / Bf), lo), hi);
+__device__ inline int cell_of(float p, float invB, int lo, int hi) {
+  return min(max(floor_i(p * invB), lo), hi);
 }
 
 // One ray: pixel (px, py) of image J; acc = premultiplied RGBA, cnt = samples
@@ -176,14 +191,14 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
   }
   const float t0 = fmaxf(tn, 0.0f), t1 = tf;
   // a degenerate matrix gives a NaN direction and an unbounded segment: no hit
-  const bool hit = active && isfinite(t0) && isfinite(t1) && t1 > t0 && (t1 - t0) * a.inv_step < 16.0e6f &&
+  const bool hit = active && isfinite(t0) && isfinite(t1) && t1 > t0 && (t1 - t0) * a.inv_step < 4.0e6f &&
                    isfinite(d.x + d.y + d.z);
   if (!hit) return;
 
-  const float Bf = (float)a.B;
-  int cx = cell_of(fmaf(t0, d.x, o.x), Bf, 0, a.nb0[0] - 1);
-  int cy = cell_of(fmaf(t0, d.y, o.y), Bf, 0, a.nb0[1] - 1);
-  int cz = cell_of(fmaf(t0, d.z, o.z), Bf, 0, a.nb0[2] - 1);
+  const float Bf = (float)a.B, invB = 1.0f / Bf;
+  int cx = cell_of(fmaf(t0, d.x, o.x), invB, 0, a.nb0[0] - 1);
+  int cy = cell_of(fmaf(t0, d.y, o.y), invB, 0, a.nb0[1] - 1);
+  int cz = cell_of(fmaf(t0, d.z, o.z), invB, 0, a.nb0[2] - 1);
   int k = 0;            // next lattice point
   int kb = 0;           // first lattice point owned by the current block
   int L = 0, kstep = 1; // current block's level and lattice stride
@@ -197,7 +212,7 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
   const int nsm = a.nsub - 1;
 
   for (int guard = 0; guard < (1 << 25); ++guard) {
-    const float t = fmaf((float)k, a.step, t0);
+    const float t = lattice_t(k, t0, a);
     if (!render || !(t < tend)) {
       // ---- leave the current block and enter the next one
       if (ax >= 0) {
@@ -208,20 +223,20 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
         if (ax == 0) {
           const int c = d.x > 0.0f ? nh_x : nl_x - 1;
           if (c < 0 || c >= a.nb0[0]) break;
-          cy = cell_of(fmaf(texit, d.y, o.y), Bf, nl_y, nh_y - 1);
-          cz = cell_of(fmaf(texit, d.z, o.z), Bf, nl_z, nh_z - 1);
+          cy = cell_of(fmaf(texit, d.y, o.y), invB, nl_y, nh_y - 1);
+          cz = cell_of(fmaf(texit, d.z, o.z), invB, nl_z, nh_z - 1);
           cx = c;
         } else if (ax == 1) {
           const int c = d.y > 0.0f ? nh_y : nl_y - 1;
           if (c < 0 || c >= a.nb0[1]) break;
-          cx = cell_of(fmaf(texit, d.x, o.x), Bf, nl_x, nh_x - 1);
-          cz = cell_of(fmaf(texit, d.z, o.z), Bf, nl_z, nh_z - 1);
+          cx = cell_of(fmaf(texit, d.x, o.x), invB, nl_x, nh_x - 1);
+          cz = cell_of(fmaf(texit, d.z, o.z), invB, nl_z, nh_z - 1);
           cy = c;
         } else {
           const int c = d.z > 0.0f ? nh_z : nl_z - 1;
           if (c < 0 || c >= a.nb0[2]) break;
-          cx = cell_of(fmaf(texit, d.x, o.x), Bf, nl_x, nh_x - 1);
-          cy = cell_of(fmaf(texit, d.y, o.y), Bf, nl_y, nh_y - 1);
+          cx = cell_of(fmaf(texit, d.x, o.x), invB, nl_x, nh_x - 1);
+          cy = cell_of(fmaf(texit, d.y, o.y), invB, nl_y, nh_y - 1);
           cz = c;
         }
         // lattice points before the exit belong to the block just left
@@ -254,18 +269,22 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
     // brick-local coordinate: level-L position - block origin + 1 (apron) - 0.5 (voxel centre)
     const float lx = fmaf(px0 - lo.x, sL, 0.5f), ly = fmaf(py0 - lo.y, sL, 0.5f), lz = fmaf(pz0 - lo.z, sL, 0.5f);
     if (a.empty_skip) {
-      const int sx = min(max((int)floorf((lx - 0.5f) * 0.125f), 0), nsm);
-      const int sy = min(max((int)floorf((ly - 0.5f) * 0.125f), 0), nsm);
-      const int sz = min(max((int)floorf((lz - 0.5f) * 0.125f), 0), nsm);
+      const int sx = min(max(floor_i(lx - 0.5f) >> 3, 0), nsm);
+      const int sy = min(max(floor_i(ly - 0.5f) >> 3, 0), nsm);
+      const int sz = min(max(floor_i(lz - 0.5f) >> 3, 0), nsm);
       const int sid = (sz * a.nsub + sy) * a.nsub + sx;
-      if ((__ldg(a.subempty + (size_t)slot * a.sub_words + (sid >> 6)) >> (sid & 63)) & 1ull) {
+      // 64-bit words read as little-endian 32-bit halves
+      const uint32_t* w32 = reinterpret_cast<const uint32_t*>(a.subempty) + (size_t)slot * a.sub_words * 2;
+      if ((__ldg(w32 + (sid >> 5)) >> (sid & 31)) & 1u) {
 #if SG_SUBBLOCK_JUMP
         // transparent sub-block: jump to its exit (lattice points before it are skipped)
         const float S = (float)(kSub << L);
         const float bx = fmaf((float)sx, S, lo.x), by = fmaf((float)sy, S, lo.y), bz = fmaf((float)sz, S, lo.z);
         const float ts = fminf(fminf(axis_exit(o.x, d.x, inv.x, bx, bx + S), axis_exit(o.y, d.y, inv.y, by, by + S)),
                                fminf(axis_exit(o.z, d.z, inv.z, bz, bz + S), tend));
-        k = max(first_k_at(ts, t0, a, k), k + 1);
+        // a rounded-up target may skip a point lying within rounding of the
+        // exit: it is inside this sub-block's footprint margin, alpha 0, exact
+        k = max(ceil_i((ts - t0) * a.inv_step), k + 1);
         k = (k + kstep - 1) & ~(kstep - 1);
 #else
         k += kstep;
