@@ -76,6 +76,7 @@ void free_volume(sg_volume* v) {
   cudaFree(v->d_range);
   cudaFree(v->d_subrange);
   cudaFree(v->d_subempty);
+  cudaFree(v->d_subdist);
   cudaFree(v->d_nodeflags);
   cudaFree(v->d_tf_raw);
   cudaFree(v->d_lut);
@@ -249,6 +250,7 @@ sg_status sg_volume_create(const sg_volume_desc* d, sg_volume** out) {
       (e = dalloc(&v->d_slot, tn)) != cudaSuccess || (e = dalloc(&v->d_range, tn * v->nch * 2)) != cudaSuccess ||
       (e = dalloc(&v->d_subrange, (size_t)v->pool_slots * ns3 * v->nch * 2)) != cudaSuccess ||
       (e = dalloc(&v->d_subempty, (size_t)v->pool_slots * v->sub_words)) != cudaSuccess ||
+      (e = dalloc(&v->d_subdist, (size_t)v->pool_slots * ns3)) != cudaSuccess ||
       (e = dalloc(&v->d_nodeflags, tn)) != cudaSuccess ||
       (e = dalloc(&v->d_tf_raw, (size_t)v->nch * kMaxTF * 4)) != cudaSuccess ||
       (e = dalloc(&v->d_lut, (size_t)v->nch * v->levels * kMaxTF)) != cudaSuccess ||
@@ -266,6 +268,7 @@ sg_status sg_volume_create(const sg_volume_desc* d, sg_volume** out) {
       (e = cudaMemset(v->d_range, 0, tn * v->nch * 2 * sizeof(uint32_t))) != cudaSuccess ||
       (e = cudaMemset2D(v->d_range, 8, 0xff, 4, tn * v->nch)) != cudaSuccess ||
       (e = cudaMemset(v->d_subempty, 0, (size_t)v->pool_slots * v->sub_words * 8)) != cudaSuccess ||
+      (e = cudaMemset(v->d_subdist, 0, (size_t)v->pool_slots * ns3)) != cudaSuccess ||
       (e = cudaMemset(v->d_nodeflags, 0, tn)) != cudaSuccess ||
       (e = cudaMemset(v->d_tf_raw, 0, (size_t)v->nch * kMaxTF * 16)) != cudaSuccess) {
     free_volume(v);

@@ -23,11 +23,7 @@ constexpr int kTileW = 16, kTileH = 8, kThreads = kTileW * kTileH;
 #ifndef SG_RENDER_MINB
 #define SG_RENDER_MINB 1
 #endif
-// 1: a sample landing in a transparent 8^3 sub-block jumps to the sub-block's
-// exit; 0: it steps to the next lattice point (cheaper step, more steps)
-#ifndef SG_SUBBLOCK_JUMP
-#define SG_SUBBLOCK_JUMP 1
-#endif
+
 
 struct ImageJob {
   // ray direction (unnormalised) = dx * x_ndc + dy * y_ndc + d0, voxel space:
@@ -53,7 +49,7 @@ struct Jobs {
 struct Args {
   const uint8_t* pool;
   size_t brick_bytes;
-  const uint64_t* subempty;
+  const uint8_t* subdist;   // [slot][nsub^3] distance to a non-transparent sub-block
   const float4* lut;   // [nch][levels][kMaxTF]
   int nch, levels, B, nsub, sub_words;
   int nb0[3];
@@ -273,22 +269,21 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
       const int sy = min(max(floor_i(ly - 0.5f) >> 3, 0), nsm);
       const int sz = min(max(floor_i(lz - 0.5f) >> 3, 0), nsm);
       const int sid = (sz * a.nsub + sy) * a.nsub + sx;
-      // 64-bit words read as little-endian 32-bit halves
-      const uint32_t* w32 = reinterpret_cast<const uint32_t*>(a.subempty) + (size_t)slot * a.sub_words * 2;
-      if ((__ldg(w32 + (sid >> 5)) >> (sid & 31)) & 1u) {
-#if SG_SUBBLOCK_JUMP
-        // transparent sub-block: jump to its exit (lattice points before it are skipped)
+      const int D = __ldg(a.subdist + (size_t)slot * a.nsub * a.nsub * a.nsub + sid);
+      if (D > 0) {
+        // every sub-block within D - 1 steps is transparent: jump to the exit
+        // of that cube (clipped to the brick); the lattice points skipped
+        // have alpha exactly 0
         const float S = (float)(kSub << L);
-        const float bx = fmaf((float)sx, S, lo.x), by = fmaf((float)sy, S, lo.y), bz = fmaf((float)sz, S, lo.z);
-        const float ts = fminf(fminf(axis_exit(o.x, d.x, inv.x, bx, bx + S), axis_exit(o.y, d.y, inv.y, by, by + S)),
-                               fminf(axis_exit(o.z, d.z, inv.z, bz, bz + S), tend));
+        const float bx0 = fmaf((float)max(sx - D + 1, 0), S, lo.x), bx1 = fmaf((float)min(sx + D, a.nsub), S, lo.x);
+        const float by0 = fmaf((float)max(sy - D + 1, 0), S, lo.y), by1 = fmaf((float)min(sy + D, a.nsub), S, lo.y);
+        const float bz0 = fmaf((float)max(sz - D + 1, 0), S, lo.z), bz1 = fmaf((float)min(sz + D, a.nsub), S, lo.z);
+        const float ts = fminf(fminf(axis_exit(o.x, d.x, inv.x, bx0, bx1), axis_exit(o.y, d.y, inv.y, by0, by1)),
+                               fminf(axis_exit(o.z, d.z, inv.z, bz0, bz1), tend));
         // a rounded-up target may skip a point lying within rounding of the
-        // exit: it is inside this sub-block's footprint margin, alpha 0, exact
+        // exit: it is inside the cube's footprint margin, alpha 0, exact
         k = max(ceil_i((ts - t0) * a.inv_step), k + 1);
         k = (k + kstep - 1) & ~(kstep - 1);
-#else
-        k += kstep;
-#endif
         continue;
       }
     }
@@ -449,7 +444,7 @@ Args make_args(const sg_volume* v, const sg_render_params* prm) {
   Args a;
   a.pool = v->d_pool;
   a.brick_bytes = v->brick_bytes;
-  a.subempty = v->d_subempty;
+  a.subdist = v->d_subdist;
   a.lut = v->d_lut;
   a.nch = v->nch;
   a.levels = v->levels;

@@ -90,6 +90,43 @@ __global__ void k_sub_empty(TFParams p, const uint16_t* __restrict__ subrange, i
   }
 }
 
+// Chebyshev distance, in sub-blocks, from every 8^3 sub-block of a brick to
+// the nearest non-transparent one of the same brick: 0 = not transparent,
+// D > 0 = every sub-block within D - 1 steps (26-neighbourhood) is
+// transparent, so a ray may cross that whole cube without a sample. Computed
+// by breadth-first dilation rounds up to kMaxDist; farther cells keep
+// kMaxDist + 1 (capped by the brick edge where the ray's jump is clipped).
+constexpr int kMaxDist = 7;
+__global__ void k_sub_dist(const uint64_t* __restrict__ bits, int nsub, int words, uint8_t* __restrict__ dist) {
+  extern __shared__ uint8_t sd[];
+  const int64_t slot = blockIdx.x;
+  const int ns3 = nsub * nsub * nsub;
+  const uint64_t* w = bits + slot * words;
+  for (int i = threadIdx.x; i < ns3; i += blockDim.x) sd[i] = ((w[i >> 6] >> (i & 63)) & 1ull) ? 255 : 0;
+  __syncthreads();
+  for (int r = 1; r <= kMaxDist; ++r) {
+    for (int i = threadIdx.x; i < ns3; i += blockDim.x) {
+      if (sd[i] != 255) continue;
+      const int x = i % nsub, y = (i / nsub) % nsub, z = i / (nsub * nsub);
+      bool near = false;
+      for (int dz = -1; dz <= 1 && !near; ++dz)
+        for (int dy = -1; dy <= 1 && !near; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int X = x + dx, Y = y + dy, Z = z + dz;
+            if (X < 0 || Y < 0 || Z < 0 || X >= nsub || Y >= nsub || Z >= nsub) continue;
+            if (sd[(Z * nsub + Y) * nsub + X] == r - 1) { near = true; break; }
+          }
+      if (near) sd[i] = 254;  // mark; becomes r after the round
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ns3; i += blockDim.x)
+      if (sd[i] == 254) sd[i] = (uint8_t)r;
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < ns3; i += blockDim.x)
+    dist[slot * ns3 + i] = sd[i] == 255 ? (uint8_t)(kMaxDist + 1) : sd[i];
+}
+
 // Opacity correction per level: a level-L sample stands for step 2^L
 // level-0 voxels: alpha' = 1 - (1 - alpha)^(step 2^L / ref_step).
 struct LutParams {
@@ -149,6 +186,8 @@ cudaError_t launch_tf_flags(sg_volume* v, cudaStream_t s) {
   int ns3 = v->nsub * v->nsub * v->nsub;
   int64_t words = (int64_t)v->pool_slots * v->sub_words;
   k_sub_empty<<<grid_for(words, 128), 128, 0, s>>>(p, v->d_subrange, v->pool_slots, ns3, v->sub_words, v->d_subempty);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_sub_dist<<<(unsigned)v->pool_slots, 256, ns3, s>>>(v->d_subempty, v->nsub, v->sub_words, v->d_subdist);
   return cudaGetLastError();
 }
 
