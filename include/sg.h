@@ -165,6 +165,30 @@ sg_status sg_select_lod(sg_volume* vol, const sg_pose* pose, sg_select_stats* st
 /* Selection for n poses in one launch (batched frames); no stats. */
 sg_status sg_select_lod_batch(sg_volume* vol, const sg_pose* poses, int n, void* stream);
 
+/* Allocation-free selection. The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory while they render,
+ * such as a thread under a hard frame budget or one recording a CUDA graph
+ * (cudaMalloc may synchronise the device and cannot be captured). It
+ * computes what sg_select_lod computes for the pose, but writes into the
+ * caller's device buffers and takes its breadth-first scratch from a fixed
+ * array inside the library: 2 x 65536 int32 (512 KiB) that every GPU which
+ * loads the library keeps until the process exits. Volumes with more than
+ * 65536 blocks on one level are rejected (SG_ERR_INVALID_ARG); sg_select_lod
+ * has no such limit. Outputs (device, caller-owned): leaf[ncell] render
+ * entries, cell_node[ncell] node id or -1, node_state[nodes] as in
+ * sg_read_selection, req[nodes] requested node ids in no particular order,
+ * counters[8] = requested, selected, culled, empty, fallback, nonempty.
+ * The first call on a device looks up the fixed array's device address (no
+ * allocation); make that first call before any stream capture. Every call
+ * shares the array and it keeps the last call's contents (each call writes
+ * before it reads, nothing needs clearing): calls whose work overlaps on the
+ * GPU race, so order them (one stream, or events). pose.slot is ignored and
+ * LRU timestamps are not updated. The call allocates nothing and does not
+ * wait for the stream. Errors: INVALID_ARG, STATE (no transfer function or
+ * data), CUDA. */
+sg_status sg_select_lod_noalloc(sg_volume* vol, const sg_pose* pose, uint32_t* leaf, int32_t* cell_node,
+                                uint8_t* node_state, int32_t* req, uint32_t* counters, void* stream);
+
 /* Copies a selection to host memory (waits for the stream): per level-0 block
  * cell the rendering node id or -1 (ncell = product of ceil(dims/B)); per node
  * the traversal state (0 unseen, 1 culled, 2 dropped-empty, 3 selected,

@@ -11,6 +11,8 @@
 // level (frontier in global scratch), then fills the per-cell leaf map.
 #include <math.h>
 
+#include <mutex>
+
 #include "internal.h"
 
 namespace sg {
@@ -365,3 +367,103 @@ cudaError_t launch_select(sg_volume* v, const sg_pose* poses, int n, cudaStream_
 }
 
 }  // namespace sg
+
+// ---------------------------------------------------------------- selection without allocation
+//
+// For callers that must not allocate device memory while they render (a
+// thread under a hard frame budget, or one recording a CUDA graph, cannot
+// call cudaMalloc: it may synchronise the device and cannot be captured).
+// The breadth-first frontier that the selection kernel needs comes from this
+// fixed array instead of the volume's per-slot buffers.
+
+namespace {
+constexpr int64_t kStaticFrontierNodes = 65536;  // blocks per level; 2 x 256 KiB
+}  // namespace
+
+static __device__ __align__(256) int32_t g_static_frontier[2 * kStaticFrontierNodes];
+
+namespace {
+std::mutex g_static_mu;
+int32_t* g_static_ptr[256] = {};  // device address of g_static_frontier, per device ordinal
+}  // namespace
+
+extern "C" sg_status sg_select_lod_noalloc(sg_volume* v, const sg_pose* p, uint32_t* leaf, int32_t* cell_node,
+                                           uint8_t* node_state, int32_t* req, uint32_t* counters, void* stream) {
+  using namespace sg;
+  if (!v || !p || !leaf || !cell_node || !node_state || !req || !counters) {
+    set_error("sg_select_lod_noalloc: volume, pose and every output must be non-NULL");
+    return SG_ERR_INVALID_ARG;
+  }
+  if (p->t < 0 || p->t >= v->T || p->width <= 0 || p->height <= 0 || !(p->pixel_error > 0.0f) ||
+      p->proj[0][5] == 0.0f) {
+    set_error("sg_select_lod_noalloc: pose out of range (t, image size, pixel_error or P11)");
+    return SG_ERR_INVALID_ARG;
+  }
+  if (v->max_level_nodes > kStaticFrontierNodes) {
+    set_error("sg_select_lod_noalloc: the volume has more than 65536 blocks on one level; its fixed scratch "
+              "holds at most 65536 (use sg_select_lod)");
+    return SG_ERR_INVALID_ARG;
+  }
+  for (int c = 0; c < v->nch; ++c)
+    if (!v->tf[c].set || !v->has_data[(size_t)p->t * v->nch + c]) {
+      set_error("sg_select_lod_noalloc: set a transfer function and upload data for every channel first");
+      return SG_ERR_STATE;
+    }
+  if (v->pooled) {
+    const LevelGeom& g = v->geom[v->levels - 1];
+    const int64_t nt = (int64_t)g.nb[0] * g.nb[1] * g.nb[2];
+    for (int64_t b = 0; b < nt; ++b)
+      if (v->h_slot[(int64_t)p->t * v->nodes + g.off + b] < 0) {
+        set_error("sg_select_lod_noalloc: the coarsest level must be resident");
+        return SG_ERR_STATE;
+      }
+  }
+  // set-up, once per device with that device current: the array's device
+  // address (host code cannot use the symbol itself as a pointer)
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "sg_select_lod_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= 256) {
+    set_error("sg_select_lod_noalloc: device ordinal out of range");
+    return SG_ERR_INVALID_ARG;
+  }
+  int32_t* frontier = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_static_frontier);
+      if (e != cudaSuccess) return cuda_fail(e, "sg_select_lod_noalloc: cudaGetSymbolAddress");
+      g_static_ptr[dev] = static_cast<int32_t*>(ptr);
+    }
+    frontier = g_static_ptr[dev];
+  }
+  SelGeom g;
+  g.levels = v->levels;
+  g.B = v->B;
+  for (int a = 0; a < 3; ++a) g.dims0[a] = v->geom[0].dims[a];
+  for (int L = 0; L < kMaxLevels; ++L) {
+    for (int a = 0; a < 3; ++a) g.nb[L][a] = L < v->levels ? v->geom[L].nb[a] : 0;
+    g.off[L] = L < v->levels ? v->geom[L].off : 0;
+  }
+  g.nodes = v->nodes;
+  g.max_level_nodes = kStaticFrontierNodes;  // the two halves of the fixed array
+  g.slot = v->d_slot;
+  g.flags = v->d_nodeflags;
+  g.stamp = nullptr;  // a pure function of its inputs: LRU stamps are left alone
+  g.frame = 0;
+  SelJobs jobs;
+  SelJob& J = jobs.j[0];
+  compute_select_inputs(v, p, &J.in);
+  J.t = p->t;
+  J.leaf = leaf;
+  J.cell_node = cell_node;
+  J.state = node_state;
+  J.req = req;
+  J.counters = counters;
+  J.frontier = frontier;
+  k_select<<<1, kSelThreads, 0, (cudaStream_t)stream>>>(jobs, g);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "sg_select_lod_noalloc: launch");
+  return SG_OK;
+}
