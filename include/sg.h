@@ -198,6 +198,11 @@ sg_status sg_select_lod_noalloc(sg_volume* vol, const sg_pose* pose, uint32_t* l
 sg_status sg_read_selection(sg_volume* vol, int slot, int32_t* cell_node, int64_t ncell, uint8_t* node_state,
                             int64_t nnode, int32_t* req, int32_t req_cap, int32_t* nreq, void* stream);
 
+/* Copies the page table of time point t to host: per node the pool slot of
+ * its brick group, or -1 when it is not cached ("Volumetric Data Cashing").
+ * slot_of_node holds nnode >= nodes entries. Errors: INVALID_ARG. */
+sg_status sg_read_residency(sg_volume* vol, int t, int32_t* slot_of_node, int64_t nnode);
+
 /* Copies the stored brick of (t, c, level, bx, by, bz) to host: (B+2)^3
  * voxels of dtype, x fastest, apron included (waits for the stream). For
  * inspection and tests of the ingest path. Errors: INVALID_ARG,

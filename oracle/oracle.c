@@ -203,6 +203,9 @@ void or_block_ranges(const or_volume* v, uint32_t* out) {
  * floor(q(vmax)) + 2 (clamped to the table) has alpha exactly 0. The one-entry
  * margins make the test conservative against a one-ulp difference in q. */
 static int tf_range_empty(const or_tf* tf, uint32_t vmin, uint32_t vmax) {
+  /* an unknown range (vmin > vmax: a block whose data was never seen) is
+   * never transparent */
+  if (vmin > vmax) return 0;
   volatile float width = tf->hi - tf->lo;
   volatile float x0 = ((float)vmin - tf->lo) / width;
   volatile float x1 = ((float)vmax - tf->lo) / width;

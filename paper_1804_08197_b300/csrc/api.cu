@@ -447,6 +447,14 @@ sg_status sg_read_selection(sg_volume* v, int slot, int32_t* cell_node, int64_t 
   return SG_OK;
 }
 
+sg_status sg_read_residency(sg_volume* v, int t, int32_t* slot_of_node, int64_t nnode) {
+  SG_CHECK_ARG(v && slot_of_node, "volume or output NULL");
+  SG_CHECK_ARG(t >= 0 && t < v->T, "t out of range");
+  SG_CHECK_ARG(nnode >= v->nodes, "output too small");
+  memcpy(slot_of_node, v->h_slot.data() + (size_t)t * v->nodes, v->nodes * sizeof(int32_t));
+  return SG_OK;
+}
+
 sg_status sg_read_brick(sg_volume* v, int t, int c, int level, int bx, int by, int bz, void* host_out,
                         void* stream) {
   SG_CHECK_ARG(v && host_out, "volume or host_out NULL");

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_OOM", 3: "SG_ERR
 EXPORTS = ["sg_volume_create", "sg_volume_destroy", "sg_upload_volume_device", "sg_upload_bricks",
            "sg_set_transfer_function", "sg_select_lod", "sg_select_lod_batch", "sg_read_selection", "sg_read_brick",
            "sg_render", "sg_render_host", "sg_render_batch", "sg_set_render_config", "sg_get_render_config",
-           "sg_autotune_render", "sg_select_lod_noalloc", "sg_last_error", "sg_version"]
+           "sg_autotune_render", "sg_select_lod_noalloc", "sg_read_residency", "sg_last_error", "sg_version"]
 
 
 class SGError(RuntimeError):
@@ -81,6 +81,7 @@ def _load():
         "sg_select_lod_batch": [vp, P(sg_pose), i32, vp],
         "sg_read_selection": [vp, i32, vp, i64, vp, i64, vp, i32, vp, vp],
         "sg_read_brick": [vp, i32, i32, i32, i32, i32, i32, vp, vp],
+        "sg_read_residency": [vp, i32, vp, i64],
         "sg_render": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
         "sg_render_host": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
         "sg_render_batch": [vp, P(sg_pose), i32, P(sg_render_params), P(vp), vp],
@@ -265,3 +266,10 @@ def sg_select_lod_noalloc(vol, pose, leaf, cell_node, node_state, req, counters,
     """Allocation-free selection into caller-owned device buffers (see include/sg.h)."""
     _check(lib.sg_select_lod_noalloc(vol, ctypes.byref(pose), _ptr(leaf), _ptr(cell_node), _ptr(node_state),
                                      _ptr(req), _ptr(counters), _stream(stream)))
+
+
+def sg_read_residency(vol, t, nnode):
+    import numpy as np
+    out = np.empty(nnode, np.int32)
+    _check(lib.sg_read_residency(vol, t, _ptr(out), nnode))
+    return out

@@ -203,20 +203,34 @@ void sy_blobs_u16(uint16_t* out, int nx, int ny, int nz, uint64_t seed, int chan
     a[b] = urange(sd, 5, base + 9, 5000.0, 40000.0);
   }
   const uint64_t plane = (uint64_t)nx * ny;
-#pragma omp parallel for schedule(static)
-  for (int z = 0; z < nz; ++z)
-    for (int y = 0; y < ny; ++y)
-      for (int x = 0; x < nx; ++x) {
-        uint64_t idx = plane * z + (uint64_t)y * nx + x;
-        double v = noise_max * u01(sd, 6 + (uint64_t)t * 131, idx);
-        for (int b = 0; b < nblobs; ++b) {
-          double dx = x + 0.5 - c[b][0], dy = y + 0.5 - c[b][1], dz = z + 0.5 - c[b][2];
-          double r2 = dx * dx + dy * dy + dz * dz, lim = 3.5 * s[b];
-          if (r2 < lim * lim) v += a[b] * exp(-r2 / (2.0 * s[b] * s[b]));
-        }
-        double r = floor(v + 0.5);
-        out[idx] = (uint16_t)(r > 65535.0 ? 65535.0 : r);
+  /* per z-slice: noise, then every blob whose 3.5 sigma ball reaches the slice */
+#pragma omp parallel
+  {
+    double* acc = (double*)malloc(sizeof(double) * plane);
+#pragma omp for schedule(dynamic, 4)
+    for (int z = 0; z < nz; ++z) {
+      for (uint64_t i = 0; i < plane; ++i) acc[i] = noise_max * u01(sd, 6 + (uint64_t)t * 131, plane * z + i);
+      for (int b = 0; b < nblobs; ++b) {
+        double lim = 3.5 * s[b], dz = z + 0.5 - c[b][2];
+        if (fabs(dz) >= lim) continue;
+        int x0 = (int)floor(c[b][0] - lim), x1 = (int)ceil(c[b][0] + lim);
+        int y0 = (int)floor(c[b][1] - lim), y1 = (int)ceil(c[b][1] + lim);
+        if (x0 < 0) x0 = 0; if (y0 < 0) y0 = 0;
+        if (x1 > nx - 1) x1 = nx - 1; if (y1 > ny - 1) y1 = ny - 1;
+        for (int y = y0; y <= y1; ++y)
+          for (int x = x0; x <= x1; ++x) {
+            double dx = x + 0.5 - c[b][0], dy = y + 0.5 - c[b][1];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < lim * lim) acc[(uint64_t)y * nx + x] += a[b] * exp(-r2 / (2.0 * s[b] * s[b]));
+          }
       }
+      for (uint64_t i = 0; i < plane; ++i) {
+        double r = floor(acc[i] + 0.5);
+        out[plane * z + i] = (uint16_t)(r > 65535.0 ? 65535.0 : r);
+      }
+    }
+    free(acc);
+  }
 }
 
 /* --- configuration "large volume": jittered cell bodies with membrane shells, u8 ---

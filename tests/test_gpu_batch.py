@@ -120,3 +120,38 @@ def test_select_and_batched_render_replay_in_a_cuda_graph():
             assert np.array_equal(o.cpu().numpy(), r)
     finally:
         case.close()
+
+
+def test_time_points_are_independent_volumes():
+    """3D movies: pose.t picks the time point; each matches the oracle of its own data."""
+    import torch
+    import oracle
+    from paper_1804_08197_b300 import sg
+    dims = (80, 64, 48)
+    model = synth.volume_model(80, 0.5)
+    vol = sg.sg_volume_create(dims, sg.SG_U16, 16, 3, timepoints=3, model=model)
+    try:
+        data = [synth.blobs_u16(dims, seed=1003, channel=0, t=t, nblobs=10) for t in range(3)]
+        for t, a in enumerate(data):
+            d = torch.from_numpy(a.view(np.int16)).cuda()
+            sg.sg_upload_volume_device(vol, t, 0, d.data_ptr())
+        table = synth.tf_piecewise(2003, zero_alpha_points=2)
+        sg.sg_set_transfer_function(vol, 0, table, 200.0, 40000.0)
+        W, H = 120, 128
+        (views, projs), = synth.head_poses(1, seed=3700, extent_m=0.5, width=W, height=H)
+        poses = [sg.make_pose(views, projs, W, H, pixel_error=0.5, t=t, slot=t) for t in range(3)]
+        sg.sg_select_lod_batch(vol, poses)
+        outs = [torch.empty((H, W, 4), device="cuda") for _ in range(6)]
+        sg.sg_render_batch(vol, poses, sg.render_params(), outs)
+        torch.cuda.synchronize()
+        otf = oracle.make_tf(table, 200.0, 40000.0)
+        for t in (0, 2):
+            ov = oracle.Volume([oracle.pyramid(data[t], 3)], 16, model=model)
+            ref = ov.select([otf], views, projs, H, tau=0.5)
+            cells, _, _ = sg.sg_read_selection(vol, t, len(ref["leaf"]), ov.node_count)
+            assert np.array_equal(cells, ref["leaf"])
+            compare_image(outs[2 * t].cpu().numpy().reshape(-1, 4),
+                          ov.render([otf], ref["leaf"], views[0], projs[0], W, H))
+        assert not np.array_equal(outs[0].cpu().numpy(), outs[4].cpu().numpy())
+    finally:
+        sg.sg_volume_destroy(vol)

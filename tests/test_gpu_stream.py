@@ -1,0 +1,109 @@
+"""Streaming through the brick cache ("Volumetric Data Cashing"): a pooled
+volume starts with only its coarsest level; each frame selects (falling back
+one level and requesting missing children, "Octree Representation"), then
+uploads the requested bricks, evicting the least recently used ones when the
+cache is full. Every frame's selection must equal the oracle's for the same
+residency and the same known value ranges, bit for bit; the converged frame
+must render like the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity_util import compare_image, compare_selection
+
+pytestmark = pytest.mark.gpu
+
+B, LEVELS, DIMS = 16, 4, (128, 128, 128)
+
+
+def _brick(ovol, L, bx, by, bz):
+    g = ovol.channels[0][L]
+    R = B + 2
+    iz = np.clip(np.arange(R) + bz * B - 1, 0, g.shape[0] - 1)
+    iy = np.clip(np.arange(R) + by * B - 1, 0, g.shape[1] - 1)
+    ix = np.clip(np.arange(R) + bx * B - 1, 0, g.shape[2] - 1)
+    return np.ascontiguousarray(g[np.ix_(iz, iy, ix)])
+
+
+def _stereo(head, target, W, H, fovy=40.0, ipd=0.064):
+    """Two eyes -/+ ipd/2 along the head's x axis, parallel, looking at target."""
+    head, target = np.asarray(head, float), np.asarray(target, float)
+    f = (target - head) / np.linalg.norm(target - head)
+    s = np.cross(f, [0.0, 0.0, 1.0])
+    s /= np.linalg.norm(s)
+    proj = synth.colmajor(synth.perspective(fovy, W / H, 0.01, 10.0))
+    views = [synth.colmajor(synth.look_at(head + k * ipd / 2 * s, head + k * ipd / 2 * s + f, [0, 0, 1]))
+             for k in (-1.0, 1.0)]
+    return views, [proj, proj]
+
+
+def test_streaming_frames_match_the_oracle_and_evict_lru():
+    import torch
+    from paper_1804_08197_b300 import sg
+    a = synth.filaments_u16(DIMS, seed=31, ntubes=18)
+    model = synth.volume_model(128, 0.5)
+    ovol = oracle.Volume([oracle.pyramid(a, LEVELS)], B, model=model)
+    full = ovol.block_ranges()
+    table = synth.tf_piecewise(2002, zero_alpha_points=2)
+    otf = oracle.make_tf(table, 300.0, 60000.0)
+    W, H, tau = 192, 208, 0.3
+    poses = [_stereo((-0.32, 0.05, 0.22), (-0.14, 0.0, 0.0), W, H), _stereo((0.32, -0.05, 0.22), (0.14, 0.0, 0.0), W, H)]
+    # working sets of the converged (fully resident) selections size the cache
+    need = []
+    for views, projs in poses:
+        st = ovol.select([otf], views, projs, H, tau=tau)["state"]
+        need.append(set(np.flatnonzero(np.isin(st, [oracle.ST_SELECTED, oracle.ST_FALLBACK, oracle.ST_REFINED]))))
+    cap = max(len(n) for n in need) + 8
+    assert len(need[0] | need[1]) > cap, "the two views must not fit the cache together"
+    brick_bytes = ((B + 2) ** 3 * 2 + 255) // 256 * 256
+    vol = sg.sg_volume_create(DIMS, sg.SG_U16, B, LEVELS, device_pool_bytes=cap * brick_bytes, model=model)
+    try:
+        sg.sg_set_transfer_function(vol, 0, table, 300.0, 60000.0)
+        known = np.zeros(ovol.node_count, bool)
+
+        def upload(ids):
+            by_level = {}
+            for i in ids:
+                L, b = ovol.node_coords(int(i))
+                by_level.setdefault(L, []).append(b)
+            for L, bs in by_level.items():
+                host = np.stack([_brick(ovol, L, *b) for b in bs])
+                sg.sg_upload_bricks(vol, 0, 0, L, np.array(bs), host)
+            known[np.array(list(ids), dtype=np.int64)] = True
+
+        upload([ovol.level_offsets[LEVELS - 1]])  # the root
+        ever_resident = set()
+        evicted = False
+        for views, projs in poses:
+            pose = sg.make_pose(views, projs, W, H, pixel_error=tau)
+            for frame in range(LEVELS + 2):
+                stats = sg.sg_select_lod(vol, pose, stats=True)
+                gsel = sg.sg_read_selection(vol, 0, len(ovol.select([otf], views, projs, H)["leaf"]), ovol.node_count)
+                res = sg.sg_read_residency(vol, 0, ovol.node_count) >= 0
+                now = set(np.flatnonzero(res))
+                evicted |= bool(ever_resident - now)
+                ever_resident |= now
+                ranges = full.copy()
+                ranges[~known, 0, 0] = 0xFFFFFFFF
+                ranges[~known, 0, 1] = 0
+                ref = ovol.select([otf], views, projs, H, tau=tau, resident=res.astype(np.uint8), ranges=ranges)
+                compare_selection(gsel, ref)
+                if stats["requested"] == 0:
+                    break
+                upload(gsel[2])
+            assert stats["requested"] == 0 and stats["fallback"] == 0
+        assert evicted, "the second view should have evicted bricks of the first"
+        # the converged second view renders like the oracle
+        views, projs = poses[1]
+        pose = sg.make_pose(views, projs, W, H, pixel_error=tau)
+        sg.sg_select_lod(vol, pose)
+        outs = [torch.empty((H, W, 4), device="cuda") for _ in range(2)]
+        sg.sg_render(vol, pose, sg.render_params(), outs)
+        torch.cuda.synchronize()
+        ref = ovol.select([otf], views, projs, H, tau=tau)
+        for e in range(2):
+            compare_image(outs[e].cpu().numpy().reshape(-1, 4),
+                          ovol.render([otf], ref["leaf"], views[e], projs[e], W, H))
+    finally:
+        sg.sg_volume_destroy(vol)

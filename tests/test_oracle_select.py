@@ -187,3 +187,19 @@ def test_everything_behind_the_camera_is_culled():
     assert sel["selected"] == 0 and (sel["leaf"] == -1).all()
     top = vol.level_offsets[2]
     assert (sel["state"][top:] == oracle.ST_CULLED).all()
+
+
+def test_unknown_ranges_are_never_transparent():
+    # every voxel 0 and alpha 0 over the low end: every block is transparent...
+    a = np.zeros((64, 64, 64), np.uint8)
+    vol = oracle.Volume([oracle.pyramid(a, 3)], 16)
+    tf = oracle.make_tf(synth.tf_piecewise(8, zero_alpha_points=2), 0.0, 255.0)
+    v, p = _cam([32, 32, 300], [32, 32, 32], fovy=60.0)
+    r = vol.block_ranges()
+    assert vol.select([tf], [v, v], [p, p], 512, ranges=r)["selected"] == 0
+    # ...unless its data was never seen (min > max): then it must be rendered
+    unk = r.copy()
+    unk[: vol.level_offsets[1], 0, 0] = 0xFFFFFFFF
+    unk[: vol.level_offsets[1], 0, 1] = 0
+    sel = vol.select([tf], [v, v], [p, p], 512, ranges=unk, tau=1e-9)
+    assert sel["selected"] == vol.level_offsets[1]  # all level-0 blocks
