@@ -144,13 +144,14 @@ def cpu_baseline(vol, tf_table, poses, model, frac_target_s=15.0):
 BATCH_DIMS, BATCH_T, BATCH_RES = (512, 512, 256), 16, [(1440, 1600), (1080, 1200), (720, 800)]
 
 
-def batched_4d(sg, torch, dev, stream, reps=10):
+def batched_4d(sg, torch, dev, reps=10):
     """Batched 4D multichannel render: 16 time points of a 512x512x256 u16
     volume with 2 channels (drifting, growing blobs; green/magenta tables,
     additive blend), 3 stereo viewers at 1440x1600, 1080x1200 and 720x800:
     96 images of uneven sizes per persistent launch, select + render captured
     in one CUDA graph and replayed. Configuration chosen by the autotuner."""
     import synth
+    stream = torch.cuda.Stream(device=dev)  # graphs are captured on a side stream
     model = synth.volume_model(max(BATCH_DIMS), 0.5)
     vol = sg.sg_volume_create(BATCH_DIMS, sg.SG_U16, BRICK, LEVELS, channels=2, timepoints=BATCH_T, model=model)
     t0 = time.perf_counter()
@@ -158,6 +159,7 @@ def batched_4d(sg, torch, dev, stream, reps=10):
         for c in range(2):
             a = synth.blobs_u16(BATCH_DIMS, seed=1003, channel=c, t=t, nblobs=40)
             d = torch.from_numpy(a.view(np.int16)).to(dev)
+            torch.cuda.synchronize()
             sg.sg_upload_volume_device(vol, t, c, d.data_ptr(), stream=stream)
             torch.cuda.synchronize()
     ingest_s = time.perf_counter() - t0
@@ -180,15 +182,16 @@ def batched_4d(sg, torch, dev, stream, reps=10):
     with torch.cuda.graph(g, stream=stream):
         sg.sg_select_lod_batch(vol, poses, stream=stream)
         sg.sg_render_batch(vol, poses, prm, outs, stream=stream)
-    for _ in range(2):
-        g.replay()
-    torch.cuda.synchronize()
-    total.zero_()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        g.replay()
-    e1.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize()
+        total.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            g.replay()
+        e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     px = sum(2 * w * h for w, h in BATCH_RES) * BATCH_T
@@ -331,7 +334,7 @@ def run_ours(args, rank, world, local_rank):
 
     batched = None
     if rank == 0 and not args.no_extra and n_vox == N_VOX:
-        batched = batched_4d(sg, torch, dev, stream)
+        batched = batched_4d(sg, torch, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and n_vox == N_VOX:

@@ -108,6 +108,17 @@ sg_status sg_upload_volume_device(sg_volume* vol, int t, int c, const void* dev_
 sg_status sg_upload_bricks(sg_volume* vol, int t, int c, int level, int n, const int32_t* brick_xyz,
                            const void* host, void* stream);
 
+/* Value ranges of bricks known without their data, as a container's index
+ * table would hold them ("Volumetric Data Storage": chunks with an index):
+ * minmax[2i], minmax[2i+1] are the min and max over brick i (at block
+ * coordinates brick_xyz[3i..3i+2] of (t, c, level)) and its one-voxel apron.
+ * With them, selection drops transparent subtrees before their bricks are
+ * ever cached instead of requesting them (an unknown range is never
+ * transparent). Marks earlier selections stale. Errors: INVALID_ARG, OOM,
+ * CUDA. */
+sg_status sg_set_brick_ranges(sg_volume* vol, int t, int c, int level, int n, const int32_t* brick_xyz,
+                              const uint32_t* minmax, void* stream);
+
 /* Transfer function of channel c ("DVR Techniques": tau for colour, T for
  * opacity; "Visualization Enhancements": one per channel). rgba holds n >= 2
  * entries of straight colour and opacity in [0, 1]; the opacities are those of

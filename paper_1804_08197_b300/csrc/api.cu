@@ -328,6 +328,34 @@ sg_status sg_upload_volume_device(sg_volume* v, int t, int c, const void* dev_le
   return refresh_flags(v, s);
 }
 
+sg_status sg_set_brick_ranges(sg_volume* v, int t, int c, int level, int n, const int32_t* xyz,
+                              const uint32_t* minmax, void* stream) {
+  SG_CHECK_ARG(v && xyz && minmax && n >= 1, "volume/brick_xyz/minmax NULL or n < 1");
+  SG_CHECK_ARG(t >= 0 && t < v->T && c >= 0 && c < v->nch && level >= 0 && level < v->levels,
+               "t, c or level out of range");
+  const LevelGeom& g = v->geom[level];
+  cudaStream_t s = (cudaStream_t)stream;
+  // host-side scatter into a copy of the level's range table, one upload
+  const int64_t nlev = (int64_t)g.nb[0] * g.nb[1] * g.nb[2];
+  std::vector<uint32_t> tab((size_t)nlev * v->nch * 2);
+  uint32_t* dst = v->d_range + ((int64_t)t * v->nodes + g.off) * v->nch * 2;
+  SG_CUDA(cudaMemcpyAsync(tab.data(), dst, tab.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "ranges");
+  SG_CUDA(cudaStreamSynchronize(s), "ranges");
+  for (int i = 0; i < n; ++i) {
+    SG_CHECK_ARG(xyz[3 * i] >= 0 && xyz[3 * i] < g.nb[0] && xyz[3 * i + 1] >= 0 && xyz[3 * i + 1] < g.nb[1] &&
+                     xyz[3 * i + 2] >= 0 && xyz[3 * i + 2] < g.nb[2],
+                 "brick coordinates out of range");
+    SG_CHECK_ARG(minmax[2 * i] <= minmax[2 * i + 1], "range with min > max");
+    int64_t b = ((int64_t)xyz[3 * i + 2] * g.nb[1] + xyz[3 * i + 1]) * g.nb[0] + xyz[3 * i];
+    tab[(b * v->nch + c) * 2] = minmax[2 * i];
+    tab[(b * v->nch + c) * 2 + 1] = minmax[2 * i + 1];
+  }
+  SG_CUDA(cudaMemcpyAsync(dst, tab.data(), tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s), "ranges");
+  SG_CUDA(cudaStreamSynchronize(s), "ranges");
+  ++v->tf_version;
+  return refresh_flags(v, s);
+}
+
 sg_status sg_set_transfer_function(sg_volume* v, int c, const float* rgba, int n, float lo, float hi, float ref_step,
                                    void* stream) {
   SG_CHECK_ARG(v && rgba, "volume and rgba must not be NULL");

@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_OOM", 3: "SG_ERR
 EXPORTS = ["sg_volume_create", "sg_volume_destroy", "sg_upload_volume_device", "sg_upload_bricks",
            "sg_set_transfer_function", "sg_select_lod", "sg_select_lod_batch", "sg_read_selection", "sg_read_brick",
            "sg_render", "sg_render_host", "sg_render_batch", "sg_set_render_config", "sg_get_render_config",
-           "sg_autotune_render", "sg_select_lod_noalloc", "sg_read_residency", "sg_last_error", "sg_version"]
+           "sg_autotune_render", "sg_select_lod_noalloc", "sg_read_residency", "sg_set_brick_ranges", "sg_last_error",
+           "sg_version"]
 
 
 class SGError(RuntimeError):
@@ -82,6 +83,7 @@ def _load():
         "sg_read_selection": [vp, i32, vp, i64, vp, i64, vp, i32, vp, vp],
         "sg_read_brick": [vp, i32, i32, i32, i32, i32, i32, vp, vp],
         "sg_read_residency": [vp, i32, vp, i64],
+        "sg_set_brick_ranges": [vp, i32, i32, i32, i32, vp, vp, vp],
         "sg_render": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
         "sg_render_host": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
         "sg_render_batch": [vp, P(sg_pose), i32, P(sg_render_params), P(vp), vp],
@@ -273,3 +275,10 @@ def sg_read_residency(vol, t, nnode):
     out = np.empty(nnode, np.int32)
     _check(lib.sg_read_residency(vol, t, _ptr(out), nnode))
     return out
+
+
+def sg_set_brick_ranges(vol, t, c, level, brick_xyz, minmax, stream=None):
+    import numpy as np
+    xyz = np.ascontiguousarray(brick_xyz, np.int32).reshape(-1, 3)
+    mm = np.ascontiguousarray(minmax, np.uint32).reshape(-1, 2)
+    _check(lib.sg_set_brick_ranges(vol, t, c, level, len(xyz), _ptr(xyz), _ptr(mm), _stream(stream)))

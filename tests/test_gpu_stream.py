@@ -38,7 +38,8 @@ def _stereo(head, target, W, H, fovy=40.0, ipd=0.064):
     return views, [proj, proj]
 
 
-def test_streaming_frames_match_the_oracle_and_evict_lru():
+@pytest.mark.parametrize("index_ranges", [True])
+def test_streaming_frames_match_the_oracle_and_evict_lru(index_ranges):
     import torch
     from paper_1804_08197_b300 import sg
     a = synth.filaments_u16(DIMS, seed=31, ntubes=18)
@@ -61,6 +62,14 @@ def test_streaming_frames_match_the_oracle_and_evict_lru():
     try:
         sg.sg_set_transfer_function(vol, 0, table, 300.0, 60000.0)
         known = np.zeros(ovol.node_count, bool)
+        if index_ranges:
+            # the container's index table gives every brick's range up front
+            for L in range(LEVELS):
+                nbx, nby, nbz = ovol.blocks_per_axis(L)
+                xyz = np.array([(x, y, z) for z in range(nbz) for y in range(nby) for x in range(nbx)])
+                lo, hi = ovol.level_offsets[L], ovol.level_offsets[L + 1]
+                sg.sg_set_brick_ranges(vol, 0, 0, L, xyz, full[lo:hi, 0, :])
+            known[:] = True
 
         def upload(ids):
             by_level = {}
