@@ -86,7 +86,7 @@ def test_streaming_frames_match_the_oracle_and_evict_lru(index_ranges):
         evicted = False
         for views, projs in poses:
             pose = sg.make_pose(views, projs, W, H, pixel_error=tau)
-            for frame in range(LEVELS + 2):
+            for frame in range(24):  # overlap bricks evicted early come back a few frames later
                 stats = sg.sg_select_lod(vol, pose, stats=True)
                 gsel = sg.sg_read_selection(vol, 0, len(ovol.select([otf], views, projs, H)["leaf"]), ovol.node_count)
                 res = sg.sg_read_residency(vol, 0, ovol.node_count) >= 0
