@@ -285,6 +285,55 @@ sg_status sg_get_render_config(sg_volume* vol, sg_render_config* cfg);
 sg_status sg_autotune_render(sg_volume* vol, const sg_pose* poses, int n, const sg_render_params* params,
                              float** outs, int reps, sg_render_config* best, float* best_ms, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned reconstruction (not in the paper): a residual U-Net that turns a
+ * half-resolution render (h x w, rendered at twice the step) into the
+ * full-resolution image (2h x 2w): out = bilinear_2x(in) +
+ * pixel_shuffle_2x(head(unet(in))). Three levels of 3x3 convolutions with
+ * 32 / 64 / 128 channels, ReLU, 2x2 average pooling, nearest upsampling and
+ * skip concatenation; BF16 weights and activations, FP32 accumulation on the
+ * tensor cores. Parameters (FP32 master copy), in order, per layer
+ * c1a c1b c2a c2b c3a c3b d2a d2b d1a d1b head: W[Cout][9][Cin] (tap =
+ * 3 (dy+1) + (dx+1)) then b[Cout], with (Cin, Cout) = (16,32) (32,32) (32,64)
+ * (64,64) (64,128) (128,128) (192,64) (64,64) (96,32) (32,32) (32,16); input
+ * channels 4..15 of c1a are zero padding. The head starts at zero, so an
+ * untrained network is exactly the bilinear upsampling. */
+typedef struct sg_unet sg_unet;
+
+/* Allocates weights, optimizer state and activations for batches of up to
+ * max_batch (<= 64) images of up to max_h x max_w half-resolution pixels
+ * (multiples of 4); He-normal weights from seed. Errors: INVALID_ARG, OOM. */
+sg_status sg_unet_create(int max_batch, int max_h, int max_w, uint64_t seed, sg_unet** out);
+sg_status sg_unet_destroy(sg_unet* net);
+sg_status sg_unet_param_count(sg_unet* net, int64_t* n);
+/* Copies the FP32 parameters (which = 0) or their last gradients (which = 1)
+ * to host (synchronous). */
+sg_status sg_unet_get_params(sg_unet* net, float* host, int64_t n, int which);
+/* Replaces the parameters from host (synchronous). */
+sg_status sg_unet_set_params(sg_unet* net, const float* host, int64_t n);
+
+/* Inference on n images: in[i] and out[i] are device pointers (host array of
+ * n pointers) to RGBA FP32 rows, in_pitch / out_pitch floats apart (so crops
+ * of larger images work in place); in is h x w, out is 2h x 2w. Keeps the
+ * activations for sg_unet_backward. Errors: INVALID_ARG, CUDA. */
+sg_status sg_unet_forward(sg_unet* net, const float* const* in, int64_t in_pitch, int n, int h, int w,
+                          float* const* out, int64_t out_pitch, void* stream);
+
+/* Gradients of the MSE between the last forward's outputs (out, as passed to
+ * it) and target (n images, 2h x 2w RGBA rows target_pitch floats apart),
+ * averaged over every output value; loss (device float, may be NULL) gets the
+ * MSE. Overwrites the previous gradients. Errors: INVALID_ARG, CUDA. */
+sg_status sg_unet_backward(sg_unet* net, const float* const* target, int64_t target_pitch, const float* const* out,
+                           int64_t out_pitch, float* loss, void* stream);
+
+/* One Adam step on the FP32 master parameters with the last gradients
+ * (bias-corrected moments), then refreshes the BF16 copies. */
+sg_status sg_unet_adam_step(sg_unet* net, float lr, float beta1, float beta2, float eps, void* stream);
+
+/* PSNR of a against b over count floats in [0, 1]: 10 log10(1 / MSE), into
+ * the device float out_db (1000 when identical). */
+sg_status sg_psnr(const float* a, const float* b, int64_t count, float* out_db, void* stream);
+
 /* Thread-local message of the last failure on this thread ("" if none). */
 const char* sg_last_error(void);
 

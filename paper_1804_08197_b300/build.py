@@ -9,7 +9,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsg.so")
-SOURCES = ["api.cu", "ingest.cu", "tf.cu", "select.cu", "render.cu"]
+SOURCES = ["api.cu", "ingest.cu", "tf.cu", "select.cu", "render.cu", "unet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -35,7 +35,7 @@ def build(force=False, verbose=False, out=None, defines=()):
     if out == LIB and not defines and not force and not _stale():
         return LIB
     cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", "-o", out + ".tmp"]
+           "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", "--extended-lambda", "-o", out + ".tmp"]
     cmd += [f"-D{d}" for d in defines]
     if verbose:
         cmd += ["-Xptxas", "-v"]

@@ -1,0 +1,748 @@
+// Learned reconstruction: a 3-level residual U-Net (32 / 64 / 128 channels,
+// 3x3 convolutions, BF16 weights and activations, FP32 accumulation) that
+// turns a half-resolution, coarser-step render into a full-resolution image:
+// out = bilinear_2x(in) + pixel_shuffle_2x(head(unet(in))). Trained on the
+// GPU with the project's own forward and backward kernels (Adam, MSE), used
+// with the plain full-rate render as fallback and judge (PSNR).
+//
+// Layers (h x w = half-resolution size, multiple of 4):
+//   c1a 16->32, c1b 32->32 (= e1)               at h x w      (input: RGBA + 12 zero channels)
+//   pool, c2a 32->64, c2b 64->64 (= e2)          at h/2 x w/2
+//   pool, c3a 64->128, c3b 128->128              at h/4 x w/4
+//   up, concat [up 128 | e2 64], d2a 192->64, d2b 64->64   at h/2 x w/2
+//   up, concat [up 64 | e1 32],  d1a 96->32,  d1b 32->32   at h x w
+//   head 32->16 (no ReLU, FP32) -> pixel shuffle -> 4 channels at 2h x 2w
+#include <math.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "unet_gemm.cuh"
+
+using namespace sg;
+using namespace sg::nn;
+
+namespace {
+
+constexpr int kLayers = 11;
+enum { C1A, C1B, C2A, C2B, C3A, C3B, D2A, D2B, D1A, D1B, HEAD };
+const int kCin[kLayers] = {16, 32, 32, 64, 64, 128, 192, 64, 96, 32, 32};
+const int kCout[kLayers] = {32, 32, 64, 64, 128, 128, 64, 64, 32, 32, 16};
+constexpr int kWgradSplits = 32;
+
+// ------------------------------------------------------------------ elementwise kernels
+
+template <typename F>
+__global__ void k_each(int64_t n, F f) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) f(i);
+}
+
+unsigned blocks_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 148 * 64) b = 148 * 64;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+template <typename F>
+cudaError_t each(int64_t n, cudaStream_t s, F f) {
+  if (n <= 0) return cudaSuccess;
+  k_each<<<blocks_for(n), 256, 0, s>>>(n, f);
+  return cudaGetLastError();
+}
+
+// sum over i < n of f(i) into *out (+=): grid-stride with whole warps, then
+// one atomic per warp
+template <typename F>
+__global__ void k_sum(int64_t n, F f, float* out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n_round = (n + 31) / 32 * 32;
+  float v = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_round; i += stride)
+    if (i < n) v += f(i);
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, v);
+}
+
+template <typename F>
+cudaError_t sum(int64_t n, float* out, cudaStream_t s, F f) {
+  if (n <= 0) return cudaSuccess;
+  k_sum<<<blocks_for(n), 256, 0, s>>>(n, f, out);
+  return cudaGetLastError();
+}
+
+struct Crops {
+  const float* ptr[64];  // per batch element, FP32 RGBA rows
+  int64_t pitch;         // floats between rows
+};
+
+struct OutPtrs {
+  float* p[64];
+};
+struct ConstOutPtrs {
+  const float* p[64];
+};
+
+}  // namespace
+
+struct sg_unet {
+  int max_n = 0, max_h = 0, max_w = 0;
+  int n = 0, h = 0, w = 0;  // shape of the last forward
+  int64_t nparam = 0;
+  int64_t woff[kLayers], boff[kLayers];
+  float* d_param = nullptr;   // FP32 master weights + biases
+  float* d_grad = nullptr;
+  float* d_m = nullptr;
+  float* d_v = nullptr;
+  bf16* d_w = nullptr;        // BF16 copy of the weights [Cout][9][Cin]
+  bf16* d_wt = nullptr;       // flipped / transposed for the input gradient [Cin][9][Cout]
+  int64_t step = 0;
+  // activations (BF16) and their gradients (FP32), NHWC
+  bf16 *in16 = nullptr, *a1 = nullptr, *cat1 = nullptr, *p1 = nullptr, *a2 = nullptr, *cat2 = nullptr,
+       *p2 = nullptr, *a3 = nullptr, *b3 = nullptr, *a4 = nullptr, *d2 = nullptr, *a5 = nullptr, *d1 = nullptr;
+  float* head = nullptr;      // [N][h][w][16] FP32
+  float *g_a1 = nullptr, *g_cat1 = nullptr, *g_p1 = nullptr, *g_a2 = nullptr, *g_cat2 = nullptr, *g_p2 = nullptr,
+        *g_a3 = nullptr, *g_b3 = nullptr, *g_a4 = nullptr, *g_d2 = nullptr, *g_a5 = nullptr, *g_d1 = nullptr,
+        *g_head = nullptr;
+  bf16* dz = nullptr;         // masked gradient staging (largest layer)
+  float* dw_part = nullptr;   // [S][9][128][192]
+  float* db_part = nullptr;   // [S][128]
+  float* d_loss = nullptr;    // [2]
+  Crops in_crops;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+cudaError_t alloc(sg_unet* u, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
+  if (e == cudaSuccess) u->allocs.push_back(*p);
+  return e;
+}
+
+void free_unet(sg_unet* u) {
+  for (void* p : u->allocs) cudaFree(p);
+  delete u;
+}
+
+// ---- conv launch helpers
+
+template <int BN>
+cudaError_t conv_bn(const ConvArgs& a, cudaStream_t s) {
+  const int64_t M = (int64_t)a.N * a.H * a.W;
+  dim3 grid((unsigned)((M + kConvBM - 1) / kConvBM), a.Cout / BN);
+  if (a.Cin % 32 == 0)
+    k_conv3x3<BN, 2><<<grid, 128, 0, s>>>(a);
+  else
+    k_conv3x3<BN, 1><<<grid, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t conv(const ConvArgs& a, cudaStream_t s) {
+  if (a.Cout % 128 == 0) return conv_bn<128>(a, s);
+  if (a.Cout % 64 == 0) return conv_bn<64>(a, s);
+  if (a.Cout % 32 == 0) return conv_bn<32>(a, s);
+  return conv_bn<16>(a, s);
+}
+
+cudaError_t wgrad(sg_unet* u, int L, const bf16* dz, int dz_stride, const bf16* in, int in_stride, int in_off,
+                  int N, int H, int W, cudaStream_t s) {
+  WgradArgs a;
+  a.dz = dz;
+  a.dz_stride = dz_stride;
+  a.dz_off = 0;
+  a.in = in;
+  a.in_stride = in_stride;
+  a.in_off = in_off;
+  a.dw_part = u->dw_part;
+  a.db_part = u->db_part;
+  a.N = N;
+  a.H = H;
+  a.W = W;
+  a.Cin = kCin[L];
+  a.Cout = kCout[L];
+  a.S = kWgradSplits;
+  const int TM = a.Cout % 32 == 0 ? 32 : 16, TN = a.Cin % 32 == 0 ? 32 : 16;
+  dim3 grid(a.Cout / TM, a.Cin / TN, 9 * a.S);
+  if (TM == 32 && TN == 32) k_wgrad<32, 32><<<grid, 128, 0, s>>>(a);
+  else if (TM == 32) k_wgrad<32, 16><<<grid, 128, 0, s>>>(a);
+  else if (TN == 32) k_wgrad<16, 32><<<grid, 128, 0, s>>>(a);
+  else k_wgrad<16, 16><<<grid, 128, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // sum the splits into the gradient: dW[co][tap][ci] (+=), db[co] (+=)
+  const int Cin = a.Cin, Cout = a.Cout;
+  float* gw = u->d_grad + u->woff[L];
+  float* gb = u->d_grad + u->boff[L];
+  const float* part = u->dw_part;
+  const float* bpart = u->db_part;
+  e = each((int64_t)Cout * 9 * Cin, s, [=] __device__(int64_t i) {
+    const int ci = (int)(i % Cin), tap = (int)((i / Cin) % 9), co = (int)(i / (9 * Cin));
+    float acc = 0.f;
+    for (int k = 0; k < kWgradSplits; ++k) acc += part[(((size_t)k * 9 + tap) * Cout + co) * Cin + ci];
+    gw[i] += acc;
+  });
+  if (e != cudaSuccess) return e;
+  return each(Cout, s, [=] __device__(int64_t co) {
+    float acc = 0.f;
+    for (int k = 0; k < kWgradSplits; ++k) acc += bpart[(size_t)k * Cout + co];
+    gb[co] += acc;
+  });
+}
+
+ConvArgs conv_args(sg_unet* u, int L, const bf16* in, int in_stride, int in_off, int N, int H, int W) {
+  ConvArgs a;
+  memset(&a, 0, sizeof a);
+  a.in = in;
+  a.in_stride = in_stride;
+  a.in_off = in_off;
+  a.wt = u->d_w + u->woff[L];
+  a.bias = u->d_param + u->boff[L];
+  a.N = N;
+  a.H = H;
+  a.W = W;
+  a.Cin = kCin[L];
+  a.Cout = kCout[L];
+  a.relu = L != HEAD;
+  return a;
+}
+
+// masked gradient: dz = bf16(dy * (y > 0)) (no mask for the head)
+cudaError_t relu_bwd(const float* dy, int dy_stride, int dy_off, const bf16* y, int y_stride, int y_off, int C,
+                     int64_t P, bf16* dz, cudaStream_t s) {
+  return each(P * C, s, [=] __device__(int64_t i) {
+    const int64_t p = i / C;
+    const int c = (int)(i % C);
+    float g = dy[p * dy_stride + dy_off + c];
+    if (y && !(__bfloat162float(y[p * y_stride + y_off + c]) > 0.f)) g = 0.f;
+    dz[i] = __float2bfloat16_rn(g);
+  });
+}
+
+// input gradient of a conv: dx[:, off..off+Cin) += conv(dz, flipped weights)
+cudaError_t dgrad(sg_unet* u, int L, const bf16* dz, float* dx, int dx_stride, int dx_off, int N, int H, int W,
+                  cudaStream_t s) {
+  ConvArgs a;
+  memset(&a, 0, sizeof a);
+  a.in = dz;
+  a.in_stride = kCout[L];
+  a.in_off = 0;
+  a.wt = u->d_wt + u->woff[L];
+  a.N = N;
+  a.H = H;
+  a.W = W;
+  a.Cin = kCout[L];
+  a.Cout = kCin[L];
+  a.out_f32 = dx;
+  a.f32_stride = dx_stride;
+  a.f32_off = dx_off;
+  a.f32_accumulate = 1;
+  return conv(a, s);
+}
+
+// He-normal initial weights (counter-based Box-Muller), zero biases, zero head
+__global__ void k_init(float* p, int64_t n, float stdv, uint64_t seed, int64_t base) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed * 0x9E3779B97F4A7C15ull + (uint64_t)(base + i) * 0xD1B54A32D192ED03ull;
+    z ^= z >> 31; z *= 0xBF58476D1CE4E5B9ull; z ^= z >> 29; z *= 0x94D049BB133111EBull; z ^= z >> 32;
+    const float u1 = ((z >> 40) + 1) * (1.0f / 16777217.0f), u2 = ((z & 0xFFFFFF)) * (1.0f / 16777216.0f);
+    p[i] = stdv * sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+  }
+}
+
+cudaError_t refresh_bf16(sg_unet* u, cudaStream_t s) {
+  // BF16 weights and the flipped/transposed copy used by the input gradient
+  for (int L = 0; L < kLayers; ++L) {
+    const int Cin = kCin[L], Cout = kCout[L];
+    const float* w = u->d_param + u->woff[L];
+    bf16* wb = u->d_w + u->woff[L];
+    bf16* wt = u->d_wt + u->woff[L];
+    cudaError_t e = each((int64_t)Cout * 9 * Cin, s, [=] __device__(int64_t i) {
+      const int ci = (int)(i % Cin), tap = (int)((i / Cin) % 9), co = (int)(i / (9 * Cin));
+      const bf16 v = __float2bfloat16_rn(w[i]);
+      wb[i] = v;
+      wt[((size_t)ci * 9 + (8 - tap)) * Cout + co] = v;
+    });
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// ---- forward / backward schedule
+
+cudaError_t forward(sg_unet* u, const Crops& c, int N, int h, int w, float* out, int64_t out_pitch,
+                    float* const* out_ptrs, cudaStream_t s) {
+  cudaError_t e;
+  const int h2 = h / 2, w2 = w / 2, h4 = h / 4, w4 = w / 4;
+  const int64_t P1 = (int64_t)N * h * w, P2 = P1 / 4, P3 = P1 / 16;
+  // input: RGBA -> 16 BF16 channels
+  bf16* in16 = u->in16;
+  const Crops cc = c;
+  e = each(P1 * 16, s, [=] __device__(int64_t i) {
+    const int ch = (int)(i % 16);
+    const int64_t p = i / 16;
+    const int x = (int)(p % w), y = (int)((p / w) % h), n = (int)(p / ((int64_t)w * h));
+    float v = ch < 4 ? cc.ptr[n][y * cc.pitch + x * 4 + ch] : 0.f;
+    in16[i] = __float2bfloat16_rn(v);
+  });
+  if (e) return e;
+  ConvArgs a;
+  a = conv_args(u, C1A, u->in16, 16, 0, N, h, w); a.out = u->a1; a.out_stride = 32; a.out_off = 0;
+  if ((e = conv(a, s))) return e;
+  // e1 lives in cat1 at channel offset 64 (after the 64 upsampled channels)
+  a = conv_args(u, C1B, u->a1, 32, 0, N, h, w); a.out = u->cat1; a.out_stride = 96; a.out_off = 64;
+  if ((e = conv(a, s))) return e;
+  // pool e1 -> p1
+  {
+    const bf16* src = u->cat1;
+    bf16* dst = u->p1;
+    e = each(P2 * 32, s, [=] __device__(int64_t i) {
+      const int ch = (int)(i % 32);
+      const int64_t q = i / 32;
+      const int x = (int)(q % w2), y = (int)((q / w2) % h2), n = (int)(q / ((int64_t)w2 * h2));
+      float acc = 0.f;
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx)
+          acc += __bfloat162float(src[(((int64_t)n * h + 2 * y + dy) * w + 2 * x + dx) * 96 + 64 + ch]);
+      dst[i] = __float2bfloat16_rn(0.25f * acc);
+    });
+    if (e) return e;
+  }
+  a = conv_args(u, C2A, u->p1, 32, 0, N, h2, w2); a.out = u->a2; a.out_stride = 64; a.out_off = 0;
+  if ((e = conv(a, s))) return e;
+  a = conv_args(u, C2B, u->a2, 64, 0, N, h2, w2); a.out = u->cat2; a.out_stride = 192; a.out_off = 128;
+  if ((e = conv(a, s))) return e;
+  {
+    const bf16* src = u->cat2;
+    bf16* dst = u->p2;
+    e = each(P3 * 64, s, [=] __device__(int64_t i) {
+      const int ch = (int)(i % 64);
+      const int64_t q = i / 64;
+      const int x = (int)(q % w4), y = (int)((q / w4) % h4), n = (int)(q / ((int64_t)w4 * h4));
+      float acc = 0.f;
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx)
+          acc += __bfloat162float(src[(((int64_t)n * h2 + 2 * y + dy) * w2 + 2 * x + dx) * 192 + 128 + ch]);
+      dst[i] = __float2bfloat16_rn(0.25f * acc);
+    });
+    if (e) return e;
+  }
+  a = conv_args(u, C3A, u->p2, 64, 0, N, h4, w4); a.out = u->a3; a.out_stride = 128; a.out_off = 0;
+  if ((e = conv(a, s))) return e;
+  a = conv_args(u, C3B, u->a3, 128, 0, N, h4, w4); a.out = u->b3; a.out_stride = 128; a.out_off = 0;
+  if ((e = conv(a, s))) return e;
+  // nearest up b3 -> cat2[:, 0..128)
+  {
+    const bf16* src = u->b3;
+    bf16* dst = u->cat2;
+    e = each(P2 * 128, s, [=] __device__(int64_t i) {
+      const int ch = (int)(i % 128);
+      const int64_t q = i / 128;
+      const int x = (int)(q % w2), y = (int)((q / w2) % h2), n = (int)(q / ((int64_t)w2 * h2));
+      dst[q * 192 + ch] = src[(((int64_t)n * h4 + y / 2) * w4 + x / 2) * 128 + ch];
+    });
+    if (e) return e;
+  }
+  a = conv_args(u, D2A, u->cat2, 192, 0, N, h2, w2); a.out = u->a4; a.out_stride = 64; a.out_off = 0;
+  if ((e = conv(a, s))) return e;
+  a = conv_args(u, D2B, u->a4, 64, 0, N, h2, w2); a.out = u->d2; a.out_stride = 64; a.out_off = 0;
+  if ((e = conv(a, s))) return e;
+  {
+    const bf16* src = u->d2;
+    bf16* dst = u->cat1;
+    e = each(P1 * 64, s, [=] __device__(int64_t i) {
+      const int ch = (int)(i % 64);
+      const int64_t q = i / 64;
+      const int x = (int)(q % w), y = (int)((q / w) % h), n = (int)(q / ((int64_t)w * h));
+      dst[q * 96 + ch] = src[(((int64_t)n * h2 + y / 2) * w2 + x / 2) * 64 + ch];
+    });
+    if (e) return e;
+  }
+  a = conv_args(u, D1A, u->cat1, 96, 0, N, h, w); a.out = u->a5; a.out_stride = 32; a.out_off = 0;
+  if ((e = conv(a, s))) return e;
+  a = conv_args(u, D1B, u->a5, 32, 0, N, h, w); a.out = u->d1; a.out_stride = 32; a.out_off = 0;
+  if ((e = conv(a, s))) return e;
+  a = conv_args(u, HEAD, u->d1, 32, 0, N, h, w); a.out_f32 = u->head; a.f32_stride = 16; a.f32_off = 0;
+  if ((e = conv(a, s))) return e;
+  // out = bilinear 2x (half-pixel centres, clamp) of the input + pixel shuffle of the head
+  {
+    const float* head = u->head;
+    const int H2 = 2 * h, W2 = 2 * w;
+    OutPtrs op;
+    for (int n = 0; n < N; ++n) op.p[n] = out_ptrs ? out_ptrs[n] : out + (size_t)n * H2 * out_pitch;
+    const int64_t opitch = out_pitch;
+    e = each((int64_t)N * H2 * W2 * 4, s, [=] __device__(int64_t i) {
+      const int ch = (int)(i % 4);
+      const int64_t q = i / 4;
+      const int X = (int)(q % W2), Y = (int)((q / W2) % H2), n = (int)(q / ((int64_t)W2 * H2));
+      const float ux = 0.5f * X - 0.25f, uy = 0.5f * Y - 0.25f;
+      const float fx0 = floorf(ux), fy0 = floorf(uy);
+      const float fx = ux - fx0, fy = uy - fy0;
+      const int x0 = min(max((int)fx0, 0), w - 1), x1 = min(max((int)fx0 + 1, 0), w - 1);
+      const int y0 = min(max((int)fy0, 0), h - 1), y1 = min(max((int)fy0 + 1, 0), h - 1);
+      const float* src = cc.ptr[n];
+      const float v00 = src[y0 * cc.pitch + x0 * 4 + ch], v01 = src[y0 * cc.pitch + x1 * 4 + ch];
+      const float v10 = src[y1 * cc.pitch + x0 * 4 + ch], v11 = src[y1 * cc.pitch + x1 * 4 + ch];
+      const float b = (1.f - fy) * ((1.f - fx) * v00 + fx * v01) + fy * ((1.f - fx) * v10 + fx * v11);
+      const int k = ch * 4 + (Y & 1) * 2 + (X & 1);  // head channel of this sub-pixel
+      const float r = head[(((int64_t)n * h + Y / 2) * w + X / 2) * 16 + k];
+      op.p[n][(int64_t)Y * opitch + X * 4 + ch] = b + r;
+    });
+    if (e) return e;
+  }
+  u->n = N;
+  u->h = h;
+  u->w = w;
+  u->in_crops = c;
+  return cudaSuccess;
+}
+
+cudaError_t backward(sg_unet* u, const Crops& tgt, const float* out, int64_t out_pitch, float* const* out_ptrs,
+                     cudaStream_t s) {
+  cudaError_t e;
+  const int N = u->n, h = u->h, w = u->w, h2 = h / 2, w2 = w / 2, h4 = h / 4, w4 = w / 4;
+  const int64_t P1 = (int64_t)N * h * w, P2 = P1 / 4, P3 = P1 / 16;
+  const int H2 = 2 * h, W2 = 2 * w;
+  const int64_t count = (int64_t)N * H2 * W2 * 4;
+  // zero gradients of parameters and activations
+  if ((e = cudaMemsetAsync(u->d_grad, 0, u->nparam * sizeof(float), s))) return e;
+  const size_t f = sizeof(float);
+  if ((e = cudaMemsetAsync(u->g_cat1, 0, P1 * 96 * f, s)) || (e = cudaMemsetAsync(u->g_a1, 0, P1 * 32 * f, s)) ||
+      (e = cudaMemsetAsync(u->g_p1, 0, P2 * 32 * f, s)) || (e = cudaMemsetAsync(u->g_a2, 0, P2 * 64 * f, s)) ||
+      (e = cudaMemsetAsync(u->g_cat2, 0, P2 * 192 * f, s)) || (e = cudaMemsetAsync(u->g_p2, 0, P3 * 64 * f, s)) ||
+      (e = cudaMemsetAsync(u->g_a3, 0, P3 * 128 * f, s)) || (e = cudaMemsetAsync(u->g_b3, 0, P3 * 128 * f, s)) ||
+      (e = cudaMemsetAsync(u->g_a4, 0, P2 * 64 * f, s)) || (e = cudaMemsetAsync(u->g_d2, 0, P2 * 64 * f, s)) ||
+      (e = cudaMemsetAsync(u->g_a5, 0, P1 * 32 * f, s)) || (e = cudaMemsetAsync(u->g_d1, 0, P1 * 32 * f, s)) ||
+      (e = cudaMemsetAsync(u->d_loss, 0, 2 * f, s)))
+    return e;
+  // MSE over all outputs; d out = 2 (out - target) / count, routed to the head by the pixel shuffle
+  {
+    ConstOutPtrs op;
+    for (int n = 0; n < N; ++n) op.p[n] = out_ptrs ? out_ptrs[n] : out + (size_t)n * H2 * out_pitch;
+    float* gh = u->g_head;
+    float* loss = u->d_loss;
+    const Crops t = tgt;
+    const int64_t opitch = out_pitch;
+    const float scale = 1.0f / (float)count;
+    e = each(count, s, [=] __device__(int64_t i) {
+      const int ch = (int)(i % 4);
+      const int64_t q = i / 4;
+      const int X = (int)(q % W2), Y = (int)((q / W2) % H2), n = (int)(q / ((int64_t)W2 * H2));
+      const float d = op.p[n][(int64_t)Y * opitch + X * 4 + ch] - t.ptr[n][Y * t.pitch + X * 4 + ch];
+      const int k = ch * 4 + (Y & 1) * 2 + (X & 1);
+      gh[(((int64_t)n * h + Y / 2) * w + X / 2) * 16 + k] = 2.0f * d * scale;
+    });
+    if (e) return e;
+    e = sum(count, loss, s, [=] __device__(int64_t i) {
+      const int ch = (int)(i % 4);
+      const int64_t q = i / 4;
+      const int X = (int)(q % W2), Y = (int)((q / W2) % H2), n = (int)(q / ((int64_t)W2 * H2));
+      const float d = op.p[n][(int64_t)Y * opitch + X * 4 + ch] - t.ptr[n][Y * t.pitch + X * 4 + ch];
+      return d * d * scale;
+    });
+    if (e) return e;
+  }
+  bf16* dz = u->dz;
+  // head (no ReLU)
+  if ((e = relu_bwd(u->g_head, 16, 0, nullptr, 0, 0, 16, P1, dz, s))) return e;
+  if ((e = wgrad(u, HEAD, dz, 16, u->d1, 32, 0, N, h, w, s))) return e;
+  if ((e = dgrad(u, HEAD, dz, u->g_d1, 32, 0, N, h, w, s))) return e;
+  // d1b: y = d1, x = a5
+  if ((e = relu_bwd(u->g_d1, 32, 0, u->d1, 32, 0, 32, P1, dz, s))) return e;
+  if ((e = wgrad(u, D1B, dz, 32, u->a5, 32, 0, N, h, w, s))) return e;
+  if ((e = dgrad(u, D1B, dz, u->g_a5, 32, 0, N, h, w, s))) return e;
+  // d1a: y = a5, x = cat1 (96)
+  if ((e = relu_bwd(u->g_a5, 32, 0, u->a5, 32, 0, 32, P1, dz, s))) return e;
+  if ((e = wgrad(u, D1A, dz, 32, u->cat1, 96, 0, N, h, w, s))) return e;
+  if ((e = dgrad(u, D1A, dz, u->g_cat1, 96, 0, N, h, w, s))) return e;
+  // up: g_d2 += sum of the 4 children of g_cat1[:, 0..64)
+  {
+    const float* gc = u->g_cat1;
+    float* gd = u->g_d2;
+    e = each(P2 * 64, s, [=] __device__(int64_t i) {
+      const int ch = (int)(i % 64);
+      const int64_t q = i / 64;
+      const int x = (int)(q % w2), y = (int)((q / w2) % h2), n = (int)(q / ((int64_t)w2 * h2));
+      float acc = 0.f;
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) acc += gc[(((int64_t)n * h + 2 * y + dy) * w + 2 * x + dx) * 96 + ch];
+      gd[i] += acc;
+    });
+    if (e) return e;
+  }
+  // d2b: y = d2, x = a4
+  if ((e = relu_bwd(u->g_d2, 64, 0, u->d2, 64, 0, 64, P2, dz, s))) return e;
+  if ((e = wgrad(u, D2B, dz, 64, u->a4, 64, 0, N, h2, w2, s))) return e;
+  if ((e = dgrad(u, D2B, dz, u->g_a4, 64, 0, N, h2, w2, s))) return e;
+  // d2a: y = a4, x = cat2 (192)
+  if ((e = relu_bwd(u->g_a4, 64, 0, u->a4, 64, 0, 64, P2, dz, s))) return e;
+  if ((e = wgrad(u, D2A, dz, 64, u->cat2, 192, 0, N, h2, w2, s))) return e;
+  if ((e = dgrad(u, D2A, dz, u->g_cat2, 192, 0, N, h2, w2, s))) return e;
+  // up: g_b3 += children of g_cat2[:, 0..128)
+  {
+    const float* gc = u->g_cat2;
+    float* gb = u->g_b3;
+    e = each(P3 * 128, s, [=] __device__(int64_t i) {
+      const int ch = (int)(i % 128);
+      const int64_t q = i / 128;
+      const int x = (int)(q % w4), y = (int)((q / w4) % h4), n = (int)(q / ((int64_t)w4 * h4));
+      float acc = 0.f;
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) acc += gc[(((int64_t)n * h2 + 2 * y + dy) * w2 + 2 * x + dx) * 192 + ch];
+      gb[i] += acc;
+    });
+    if (e) return e;
+  }
+  // c3b: y = b3, x = a3
+  if ((e = relu_bwd(u->g_b3, 128, 0, u->b3, 128, 0, 128, P3, dz, s))) return e;
+  if ((e = wgrad(u, C3B, dz, 128, u->a3, 128, 0, N, h4, w4, s))) return e;
+  if ((e = dgrad(u, C3B, dz, u->g_a3, 128, 0, N, h4, w4, s))) return e;
+  // c3a: y = a3, x = p2
+  if ((e = relu_bwd(u->g_a3, 128, 0, u->a3, 128, 0, 128, P3, dz, s))) return e;
+  if ((e = wgrad(u, C3A, dz, 128, u->p2, 64, 0, N, h4, w4, s))) return e;
+  if ((e = dgrad(u, C3A, dz, u->g_p2, 64, 0, N, h4, w4, s))) return e;
+  // pool: g_cat2[:, 128..192) += g_p2 / 4 (e2's gradient lives at its place in cat2)
+  {
+    const float* gp = u->g_p2;
+    float* gc = u->g_cat2;
+    e = each(P2 * 64, s, [=] __device__(int64_t i) {
+      const int ch = (int)(i % 64);
+      const int64_t q = i / 64;
+      const int x = (int)(q % w2), y = (int)((q / w2) % h2), n = (int)(q / ((int64_t)w2 * h2));
+      gc[q * 192 + 128 + ch] += 0.25f * gp[(((int64_t)n * h4 + y / 2) * w4 + x / 2) * 64 + ch];
+    });
+    if (e) return e;
+  }
+  // c2b: y = e2 = cat2[:, 128..), x = a2
+  if ((e = relu_bwd(u->g_cat2, 192, 128, u->cat2, 192, 128, 64, P2, dz, s))) return e;
+  if ((e = wgrad(u, C2B, dz, 64, u->a2, 64, 0, N, h2, w2, s))) return e;
+  if ((e = dgrad(u, C2B, dz, u->g_a2, 64, 0, N, h2, w2, s))) return e;
+  // c2a: y = a2, x = p1
+  if ((e = relu_bwd(u->g_a2, 64, 0, u->a2, 64, 0, 64, P2, dz, s))) return e;
+  if ((e = wgrad(u, C2A, dz, 64, u->p1, 32, 0, N, h2, w2, s))) return e;
+  if ((e = dgrad(u, C2A, dz, u->g_p1, 32, 0, N, h2, w2, s))) return e;
+  {
+    const float* gp = u->g_p1;
+    float* gc = u->g_cat1;
+    e = each(P1 * 32, s, [=] __device__(int64_t i) {
+      const int ch = (int)(i % 32);
+      const int64_t q = i / 32;
+      const int x = (int)(q % w), y = (int)((q / w) % h), n = (int)(q / ((int64_t)w * h));
+      gc[q * 96 + 64 + ch] += 0.25f * gp[(((int64_t)n * h2 + y / 2) * w2 + x / 2) * 32 + ch];
+    });
+    if (e) return e;
+  }
+  // c1b: y = e1 = cat1[:, 64..), x = a1
+  if ((e = relu_bwd(u->g_cat1, 96, 64, u->cat1, 96, 64, 32, P1, dz, s))) return e;
+  if ((e = wgrad(u, C1B, dz, 32, u->a1, 32, 0, N, h, w, s))) return e;
+  if ((e = dgrad(u, C1B, dz, u->g_a1, 32, 0, N, h, w, s))) return e;
+  // c1a: y = a1, x = in16 (no input gradient)
+  if ((e = relu_bwd(u->g_a1, 32, 0, u->a1, 32, 0, 32, P1, dz, s))) return e;
+  if ((e = wgrad(u, C1A, dz, 32, u->in16, 16, 0, N, h, w, s))) return e;
+  return cudaSuccess;
+}
+
+sg_status check_shape(const sg_unet* u, int n, int h, int w) {
+  if (n < 1 || n > u->max_n || n > 64 || h < 4 || w < 4 || h % 4 || w % 4 || (int64_t)h * w > (int64_t)u->max_h * u->max_w) {
+    set_error("unet: batch 1..max_batch (<= 64), h and w multiples of 4 with h*w <= max_h*max_w");
+    return SG_ERR_INVALID_ARG;
+  }
+  return SG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sg_status sg_unet_create(int max_batch, int max_h, int max_w, uint64_t seed, sg_unet** out) {
+  if (!out || max_batch < 1 || max_batch > 64 || max_h < 4 || max_w < 4 || max_h % 4 || max_w % 4) {
+    set_error("sg_unet_create: max_batch 1..64, max_h and max_w multiples of 4");
+    return SG_ERR_INVALID_ARG;
+  }
+  sg_unet* u = new sg_unet();
+  u->max_n = max_batch;
+  u->max_h = max_h;
+  u->max_w = max_w;
+  int64_t off = 0;
+  for (int L = 0; L < kLayers; ++L) {
+    u->woff[L] = off;
+    off += (int64_t)kCout[L] * 9 * kCin[L];
+    u->boff[L] = off;
+    off += kCout[L];
+  }
+  u->nparam = off;
+  const int64_t P1 = (int64_t)max_batch * max_h * max_w, P2 = P1 / 4, P3 = P1 / 16;
+  const size_t b = sizeof(bf16), f = sizeof(float);
+  cudaError_t e = cudaSuccess;
+  void** p;
+#define A_(ptr, bytes) \
+  if (e == cudaSuccess) { p = reinterpret_cast<void**>(&(ptr)); e = alloc(u, p, (bytes)); }
+  A_(u->d_param, off * f) A_(u->d_grad, off * f) A_(u->d_m, off * f) A_(u->d_v, off * f)
+  A_(u->d_w, off * b) A_(u->d_wt, off * b)
+  A_(u->in16, P1 * 16 * b) A_(u->a1, P1 * 32 * b) A_(u->cat1, P1 * 96 * b) A_(u->p1, P2 * 32 * b)
+  A_(u->a2, P2 * 64 * b) A_(u->cat2, P2 * 192 * b) A_(u->p2, P3 * 64 * b) A_(u->a3, P3 * 128 * b)
+  A_(u->b3, P3 * 128 * b) A_(u->a4, P2 * 64 * b) A_(u->d2, P2 * 64 * b) A_(u->a5, P1 * 32 * b) A_(u->d1, P1 * 32 * b)
+  A_(u->head, P1 * 16 * f)
+  A_(u->g_a1, P1 * 32 * f) A_(u->g_cat1, P1 * 96 * f) A_(u->g_p1, P2 * 32 * f) A_(u->g_a2, P2 * 64 * f)
+  A_(u->g_cat2, P2 * 192 * f) A_(u->g_p2, P3 * 64 * f) A_(u->g_a3, P3 * 128 * f) A_(u->g_b3, P3 * 128 * f)
+  A_(u->g_a4, P2 * 64 * f) A_(u->g_d2, P2 * 64 * f) A_(u->g_a5, P1 * 32 * f) A_(u->g_d1, P1 * 32 * f)
+  A_(u->g_head, P1 * 16 * f) A_(u->dz, P1 * 32 * b)
+  A_(u->dw_part, (size_t)kWgradSplits * 9 * 128 * 192 * f) A_(u->db_part, (size_t)kWgradSplits * 128 * f)
+  A_(u->d_loss, 2 * f)
+#undef A_
+  if (e != cudaSuccess) {
+    free_unet(u);
+    set_error(std::string("sg_unet_create: ") + cudaGetErrorString(e));
+    return SG_ERR_OOM;
+  }
+  // He-normal weights, zero biases; the head starts at zero so the untrained
+  // network is exactly the bilinear upsampling of its input
+  cudaMemset(u->d_param, 0, off * f);
+  cudaMemset(u->d_m, 0, off * f);
+  cudaMemset(u->d_v, 0, off * f);
+  for (int L = 0; L < HEAD; ++L) {
+    const int64_t n = (int64_t)kCout[L] * 9 * kCin[L];
+    const int fan_in = 9 * (L == C1A ? 4 : kCin[L]);
+    k_init<<<blocks_for(n), 256>>>(u->d_param + u->woff[L], n, sqrtf(2.0f / fan_in), seed, u->woff[L]);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    // input channels 4..15 of c1a are padding: their weights stay zero
+    float* w = u->d_param + u->woff[C1A];
+    e = each((int64_t)kCout[C1A] * 9 * 16, 0, [=] __device__(int64_t i) {
+      if (i % 16 >= 4) w[i] = 0.f;
+    });
+  }
+  if (e == cudaSuccess) e = refresh_bf16(u, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_unet(u);
+    return cuda_fail(e, "sg_unet_create");
+  }
+  *out = u;
+  return SG_OK;
+}
+
+sg_status sg_unet_destroy(sg_unet* u) {
+  if (!u) return SG_OK;
+  cudaDeviceSynchronize();
+  free_unet(u);
+  return SG_OK;
+}
+
+sg_status sg_unet_param_count(sg_unet* u, int64_t* n) {
+  if (!u || !n) {
+    set_error("sg_unet_param_count: NULL argument");
+    return SG_ERR_INVALID_ARG;
+  }
+  *n = u->nparam;
+  return SG_OK;
+}
+
+sg_status sg_unet_get_params(sg_unet* u, float* host, int64_t n, int which) {
+  if (!u || !host || n < u->nparam || which < 0 || which > 1) {
+    set_error("sg_unet_get_params: NULL, too small, or which not 0/1");
+    return SG_ERR_INVALID_ARG;
+  }
+  cudaError_t e = cudaMemcpy(host, which ? u->d_grad : u->d_param, u->nparam * sizeof(float), cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? SG_OK : cuda_fail(e, "sg_unet_get_params");
+}
+
+sg_status sg_unet_set_params(sg_unet* u, const float* host, int64_t n) {
+  if (!u || !host || n != u->nparam) {
+    set_error("sg_unet_set_params: NULL or wrong count");
+    return SG_ERR_INVALID_ARG;
+  }
+  cudaError_t e = cudaMemcpy(u->d_param, host, n * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = refresh_bf16(u, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? SG_OK : cuda_fail(e, "sg_unet_set_params");
+}
+
+sg_status sg_unet_forward(sg_unet* u, const float* const* in, int64_t in_pitch, int n, int h, int w, float* const* out,
+                          int64_t out_pitch, void* stream) {
+  if (!u || !in || !out) {
+    set_error("sg_unet_forward: NULL argument");
+    return SG_ERR_INVALID_ARG;
+  }
+  sg_status st = check_shape(u, n, h, w);
+  if (st != SG_OK) return st;
+  if (in_pitch < 4 * w || out_pitch < 8 * w) {
+    set_error("sg_unet_forward: pitch smaller than a row");
+    return SG_ERR_INVALID_ARG;
+  }
+  Crops c;
+  for (int i = 0; i < n; ++i) {
+    if (!in[i] || !out[i]) {
+      set_error("sg_unet_forward: NULL image pointer");
+      return SG_ERR_INVALID_ARG;
+    }
+    c.ptr[i] = in[i];
+  }
+  c.pitch = in_pitch;
+  cudaError_t e = forward(u, c, n, h, w, nullptr, out_pitch, out, (cudaStream_t)stream);
+  return e == cudaSuccess ? SG_OK : cuda_fail(e, "sg_unet_forward");
+}
+
+sg_status sg_unet_backward(sg_unet* u, const float* const* target, int64_t target_pitch, const float* const* out,
+                           int64_t out_pitch, float* loss, void* stream) {
+  if (!u || !target || !out || u->n == 0) {
+    set_error("sg_unet_backward: NULL argument or no forward pass before");
+    return SG_ERR_INVALID_ARG;
+  }
+  Crops t;
+  for (int i = 0; i < u->n; ++i) t.ptr[i] = target[i];
+  t.pitch = target_pitch;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = backward(u, t, nullptr, out_pitch, const_cast<float* const*>(out), s);
+  if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, u->d_loss, sizeof(float), cudaMemcpyDeviceToDevice, s);
+  return e == cudaSuccess ? SG_OK : cuda_fail(e, "sg_unet_backward");
+}
+
+sg_status sg_unet_adam_step(sg_unet* u, float lr, float beta1, float beta2, float eps, void* stream) {
+  if (!u || !(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f)) {
+    set_error("sg_unet_adam_step: bad hyper-parameters");
+    return SG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  ++u->step;
+  const float c1 = 1.0f - powf(beta1, (float)u->step), c2 = 1.0f - powf(beta2, (float)u->step);
+  float *p = u->d_param, *g = u->d_grad, *m = u->d_m, *v = u->d_v;
+  const int64_t pad_lo = u->woff[C1A], pad_n = (int64_t)kCout[C1A] * 9 * 16;
+  cudaError_t e = each(u->nparam, s, [=] __device__(int64_t i) {
+    // the padding input channels of the first layer stay zero
+    if (i >= pad_lo && i < pad_lo + pad_n && (i - pad_lo) % 16 >= 4) return;
+    const float gi = g[i];
+    const float mi = beta1 * m[i] + (1.f - beta1) * gi, vi = beta2 * v[i] + (1.f - beta2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  });
+  if (e == cudaSuccess) e = refresh_bf16(u, s);
+  return e == cudaSuccess ? SG_OK : cuda_fail(e, "sg_unet_adam_step");
+}
+
+// PSNR of a against b over count floats (values in [0, 1]): 10 log10(1 / MSE)
+sg_status sg_psnr(const float* a, const float* b, int64_t count, float* out_db, void* stream) {
+  if (!a || !b || !out_db || count <= 0) {
+    set_error("sg_psnr: NULL argument or empty");
+    return SG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  float* acc = out_db;  // accumulate the squared error sum in the output, then convert
+  cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(float), s);
+  if (e == cudaSuccess)
+    e = sum(count, acc, s, [=] __device__(int64_t i) {
+      const float d = a[i] - b[i];
+      return d * d;
+    });
+  if (e == cudaSuccess)
+    e = each(1, s, [=] __device__(int64_t) {
+      const float mse = acc[0] / (float)count;
+      acc[0] = mse > 0.f ? 10.0f * log10f(1.0f / mse) : 1000.0f;
+    });
+  return e == cudaSuccess ? SG_OK : cuda_fail(e, "sg_psnr");
+}
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+"""Learned reconstruction driver: training pairs from the renderer, training
+and fallback-guarded inference of the residual U-Net.
+
+Every step runs in libsg.so kernels; this module only sequences C-ABI calls
+and passes device pointers (crops are pointer offsets into full images, no
+copies). A pair is the plain full-rate render of a pose (W x H per eye,
+step s) and the reduced render of the same pose at half resolution and twice
+the step (W/2 x H/2, step 2s, LOD chosen for the half-resolution image); the
+network maps the reduced render to the full-rate one. The full-rate render
+is also the fallback and the judge: a frame whose PSNR against it falls below
+the threshold is replaced by it.
+"""
+import numpy as np
+
+from . import sg
+
+
+class Learned:
+    def __init__(self, vol, width, height, step=0.5, tau=1.0, max_batch=16, crop=64, seed=1, device="cuda",
+                 slot_full=200, slot_half=201):
+        import torch
+        self.torch = torch
+        self.vol = vol
+        self.W, self.H = width, height
+        self.w, self.h = width // 2, height // 2
+        assert self.h % 4 == 0 and self.w % 4 == 0
+        self.step, self.tau = step, tau
+        self.crop = crop
+        self.slot_full, self.slot_half = slot_full, slot_half
+        self.net = sg.sg_unet_create(max(max_batch, 2), max(self.h, crop), max(self.w, crop), seed)
+        dev = torch.device(device)
+        f32 = torch.float32
+        self.full = [torch.empty((self.H, self.W, 4), dtype=f32, device=dev) for _ in range(2)]
+        self.half = [torch.empty((self.h, self.w, 4), dtype=f32, device=dev) for _ in range(2)]
+        self.recon = [torch.empty((self.H, self.W, 4), dtype=f32, device=dev) for _ in range(2)]
+        self.crop_out = torch.empty((max_batch, 2 * crop, 2 * crop, 4), dtype=f32, device=dev)
+        self.loss = torch.zeros(1, dtype=f32, device=dev)
+        self.psnr_buf = torch.zeros(2, dtype=f32, device=dev)
+        self.rng = np.random.default_rng(seed)
+
+    def close(self):
+        sg.sg_unet_destroy(self.net)
+
+    # ------------------------------------------------------------------ rendering
+    def pose_full(self, views, projs, t=0):
+        return sg.make_pose(views, projs, self.W, self.H, pixel_error=self.tau, t=t, slot=self.slot_full)
+
+    def pose_half(self, views, projs, t=0):
+        return sg.make_pose(views, projs, self.w, self.h, pixel_error=self.tau, t=t, slot=self.slot_half)
+
+    def render_full(self, views, projs, outs=None, stream=None):
+        p = self.pose_full(views, projs)
+        sg.sg_select_lod(self.vol, p, stream=stream)
+        sg.sg_render(self.vol, p, sg.render_params(step=self.step), outs or self.full, stream=stream)
+
+    def render_half(self, views, projs, stream=None):
+        p = self.pose_half(views, projs)
+        sg.sg_select_lod(self.vol, p, stream=stream)
+        sg.sg_render(self.vol, p, sg.render_params(step=2 * self.step), self.half, stream=stream)
+
+    # ------------------------------------------------------------------ training
+    def _crops(self, n):
+        """n random crops over the two eyes of the current pair: (in_ptrs, target_ptrs)."""
+        c, f = self.crop, 4  # 4 floats per pixel
+        ins, tgts = [], []
+        for _ in range(n):
+            e = int(self.rng.integers(0, 2))
+            y = int(self.rng.integers(0, self.h - c + 1)) // 2 * 2
+            x = int(self.rng.integers(0, self.w - c + 1)) // 2 * 2
+            ins.append(self.half[e].data_ptr() + (y * self.w + x) * f * 4)
+            tgts.append(self.full[e].data_ptr() + (2 * y * self.W + 2 * x) * f * 4)
+        return ins, tgts
+
+    def train_on_pair(self, views, projs, steps=1, batch=16, lr=5e-4, stream=None):
+        """Renders one pair, then takes `steps` Adam steps on random crops of it.
+        Returns the last loss (device scalar tensor)."""
+        self.render_full(views, projs, stream=stream)
+        self.render_half(views, projs, stream=stream)
+        c = self.crop
+        outs = [self.crop_out[i].data_ptr() for i in range(batch)]
+        for _ in range(steps):
+            ins, tgts = self._crops(batch)
+            sg.sg_unet_forward(self.net, ins, self.w * 4, c, c, outs, 2 * c * 4, stream=stream)
+            sg.sg_unet_backward(self.net, tgts, self.W * 4, outs, 2 * c * 4, loss=self.loss, stream=stream)
+            sg.sg_unet_adam_step(self.net, lr, stream=stream)
+        return self.loss
+
+    # ------------------------------------------------------------------ inference
+    def reconstruct(self, stream=None):
+        """Both eyes of the current half-resolution render -> self.recon."""
+        sg.sg_unet_forward(self.net, self.half, self.w * 4, self.h, self.w, self.recon, self.W * 4, stream=stream)
+
+    def psnr(self, a, b, out_index=0, stream=None):
+        sg.sg_psnr(a, b, a.numel(), self.psnr_buf[out_index:out_index + 1], stream=stream)
+        return self.psnr_buf[out_index:out_index + 1]
+
+    def frame_psnr(self, stream=None):
+        """PSNR (dB) of the current reconstruction against the current full-rate
+        render over both eyes: 10 log10(1 / mean of the two eyes' MSE)."""
+        for e in range(2):
+            self.psnr(self.recon[e], self.full[e], out_index=e, stream=stream)
+        db = self.psnr_buf.cpu().numpy().astype(np.float64)
+        mse = np.mean([10.0 ** (-d / 10.0) for d in db])
+        return 10.0 * np.log10(1.0 / mse) if mse > 0 else 1000.0
+
+    def evaluate(self, views, projs, stream=None):
+        """Renders one pose both ways, reconstructs, returns the PSNR (dB)."""
+        self.render_full(views, projs, stream=stream)
+        self.render_half(views, projs, stream=stream)
+        self.reconstruct(stream=stream)
+        return self.frame_psnr(stream=stream)

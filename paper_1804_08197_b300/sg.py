@@ -22,8 +22,9 @@ STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_OOM", 3: "SG_ERR
 EXPORTS = ["sg_volume_create", "sg_volume_destroy", "sg_upload_volume_device", "sg_upload_bricks",
            "sg_set_transfer_function", "sg_select_lod", "sg_select_lod_batch", "sg_read_selection", "sg_read_brick",
            "sg_render", "sg_render_host", "sg_render_batch", "sg_set_render_config", "sg_get_render_config",
-           "sg_autotune_render", "sg_select_lod_noalloc", "sg_read_residency", "sg_set_brick_ranges", "sg_last_error",
-           "sg_version"]
+           "sg_autotune_render", "sg_select_lod_noalloc", "sg_read_residency", "sg_set_brick_ranges", "sg_unet_create", "sg_unet_destroy",
+           "sg_unet_param_count", "sg_unet_get_params", "sg_unet_set_params", "sg_unet_forward", "sg_unet_backward",
+           "sg_unet_adam_step", "sg_psnr", "sg_last_error", "sg_version"]
 
 
 class SGError(RuntimeError):
@@ -84,6 +85,15 @@ def _load():
         "sg_read_brick": [vp, i32, i32, i32, i32, i32, i32, vp, vp],
         "sg_read_residency": [vp, i32, vp, i64],
         "sg_set_brick_ranges": [vp, i32, i32, i32, i32, vp, vp, vp],
+        "sg_unet_create": [i32, i32, i32, ctypes.c_uint64, P(vp)],
+        "sg_unet_destroy": [vp],
+        "sg_unet_param_count": [vp, P(i64)],
+        "sg_unet_get_params": [vp, vp, i64, i32],
+        "sg_unet_set_params": [vp, vp, i64],
+        "sg_unet_forward": [vp, vp, i64, i32, i32, i32, vp, i64, vp],
+        "sg_unet_backward": [vp, vp, i64, vp, i64, vp, vp],
+        "sg_unet_adam_step": [vp, f32, f32, f32, f32, vp],
+        "sg_psnr": [vp, vp, i64, vp, vp],
         "sg_render": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
         "sg_render_host": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
         "sg_render_batch": [vp, P(sg_pose), i32, P(sg_render_params), P(vp), vp],
@@ -282,3 +292,58 @@ def sg_set_brick_ranges(vol, t, c, level, brick_xyz, minmax, stream=None):
     xyz = np.ascontiguousarray(brick_xyz, np.int32).reshape(-1, 3)
     mm = np.ascontiguousarray(minmax, np.uint32).reshape(-1, 2)
     _check(lib.sg_set_brick_ranges(vol, t, c, level, len(xyz), _ptr(xyz), _ptr(mm), _stream(stream)))
+
+
+# --------------------------------------------------------------------------- learned reconstruction
+
+def _ptr_array(xs):
+    return (ctypes.c_void_p * len(xs))(*[_ptr(x).value for x in xs])
+
+
+def sg_unet_create(max_batch, max_h, max_w, seed=1):
+    h = ctypes.c_void_p()
+    _check(lib.sg_unet_create(max_batch, max_h, max_w, seed, ctypes.byref(h)))
+    return h
+
+
+def sg_unet_destroy(net):
+    _check(lib.sg_unet_destroy(net))
+
+
+def sg_unet_param_count(net):
+    n = ctypes.c_int64(0)
+    _check(lib.sg_unet_param_count(net, ctypes.byref(n)))
+    return n.value
+
+
+def sg_unet_get_params(net, which=0):
+    import numpy as np
+    n = sg_unet_param_count(net)
+    out = np.empty(n, np.float32)
+    _check(lib.sg_unet_get_params(net, _ptr(out), n, which))
+    return out
+
+
+def sg_unet_set_params(net, params):
+    import numpy as np
+    p = np.ascontiguousarray(params, np.float32)
+    _check(lib.sg_unet_set_params(net, _ptr(p), len(p)))
+
+
+def sg_unet_forward(net, ins, in_pitch, h, w, outs, out_pitch, stream=None):
+    """ins/outs: lists of device buffers (or int pointers); pitches in floats."""
+    _check(lib.sg_unet_forward(net, _ptr_array(ins), in_pitch, len(ins), h, w, _ptr_array(outs), out_pitch,
+                               _stream(stream)))
+
+
+def sg_unet_backward(net, targets, target_pitch, outs, out_pitch, loss=None, stream=None):
+    _check(lib.sg_unet_backward(net, _ptr_array(targets), target_pitch, _ptr_array(outs), out_pitch, _ptr(loss),
+                                _stream(stream)))
+
+
+def sg_unet_adam_step(net, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib.sg_unet_adam_step(net, lr, beta1, beta2, eps, _stream(stream)))
+
+
+def sg_psnr(a, b, count, out_db, stream=None):
+    _check(lib.sg_psnr(_ptr(a), _ptr(b), count, _ptr(out_db), _stream(stream)))

@@ -1,0 +1,129 @@
+"""Learned reconstruction on the GPU against the FP64 network oracle:
+forward outputs and gradients at BF16 tolerance, the untrained (zero-head)
+network as exact bilinear upsampling, the PSNR kernel's closed form, and a
+short training run that must beat the method without the network."""
+import numpy as np
+import pytest
+
+import oracle.unet as ou
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16(x):
+    import torch
+    return torch.from_numpy(np.asarray(x, np.float32)).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+
+
+def _random_params(seed, n):
+    rng = np.random.default_rng(seed)
+    p = np.zeros(n, np.float32)
+    for (ws, bs), ci in zip(ou.layer_slices(), ou.CIN):
+        p[ws] = rng.normal(0, np.sqrt(2.0 / (9 * ci)), ws.stop - ws.start)
+        p[bs] = rng.normal(0, 0.05, bs.stop - bs.start)
+    ws, _ = ou.layer_slices()[0]
+    w0 = p[ws].reshape(32, 9, 16)
+    w0[:, :, 4:] = 0  # padding input channels
+    return p
+
+
+def _run(net, x, t=None):
+    import torch
+    from paper_1804_08197_b300 import sg
+    N, h, w, _ = x.shape
+    xin = [torch.from_numpy(np.ascontiguousarray(x[i], np.float32)).cuda() for i in range(N)]
+    out = [torch.zeros((2 * h, 2 * w, 4), device="cuda") for _ in range(N)]
+    sg.sg_unet_forward(net, xin, w * 4, h, w, out, 2 * w * 4)
+    loss = None
+    if t is not None:
+        tt = [torch.from_numpy(np.ascontiguousarray(t[i], np.float32)).cuda() for i in range(N)]
+        lb = torch.zeros(1, device="cuda")
+        sg.sg_unet_backward(net, tt, 2 * w * 4, out, 2 * w * 4, loss=lb)
+        torch.cuda.synchronize()
+        loss = float(lb.item())
+    torch.cuda.synchronize()
+    return np.stack([o.cpu().numpy() for o in out]).astype(np.float64), loss
+
+
+def test_forward_and_gradients_match_the_oracle_at_bf16_tolerance():
+    from paper_1804_08197_b300 import sg
+    net = sg.sg_unet_create(2, 16, 24, seed=3)
+    try:
+        n = sg.sg_unet_param_count(net)
+        assert n == ou.param_count()
+        p = _random_params(5, n)
+        sg.sg_unet_set_params(net, p)
+        rng = np.random.default_rng(7)
+        x = rng.uniform(0, 1, (2, 16, 24, 4))
+        t = rng.uniform(0, 1, (2, 32, 48, 4))
+        gpu_out, gpu_loss = _run(net, x, t)
+        g_gpu = sg.sg_unet_get_params(net, which=1).astype(np.float64)
+        # the oracle sees the BF16-rounded weights the tensor cores use (biases stay FP32)
+        q = p.astype(np.float64).copy()
+        for ws, _ in ou.layer_slices():
+            q[ws] = _bf16(p[ws])
+        loss, g_ref, out_ref = ou.loss_grad(q, x, t)
+        base = ou.bilinear2x(x)
+        r_gpu, r_ref = gpu_out - base, out_ref - base
+        assert np.linalg.norm(r_gpu - r_ref) <= 2e-2 * np.linalg.norm(r_ref)
+        assert gpu_loss == pytest.approx(loss, rel=1e-2)
+        for L, (ws, bs) in enumerate(ou.layer_slices()):
+            for sl in (ws, bs):
+                ref = g_ref[sl]
+                err = np.linalg.norm(g_gpu[sl] - ref)
+                assert err <= 5e-2 * np.linalg.norm(ref) + 1e-12, (ou.NAMES[L], err / np.linalg.norm(ref))
+    finally:
+        sg.sg_unet_destroy(net)
+
+
+def test_untrained_network_is_exactly_bilinear_upsampling():
+    from paper_1804_08197_b300 import sg
+    net = sg.sg_unet_create(3, 12, 20, seed=9)
+    try:
+        x = np.random.default_rng(2).uniform(0, 1, (3, 12, 20, 4))
+        out, _ = _run(net, x)
+        assert np.abs(out - ou.bilinear2x(x)).max() < 1e-6
+    finally:
+        sg.sg_unet_destroy(net)
+
+
+def test_psnr_closed_form():
+    import torch
+    from paper_1804_08197_b300 import sg
+    a = torch.zeros(1000, device="cuda")
+    b = torch.full((1000,), 0.1, device="cuda")
+    db = torch.zeros(1, device="cuda")
+    sg.sg_psnr(a, b, 1000, db)
+    assert float(db.item()) == pytest.approx(20.0, abs=1e-4)  # MSE 0.01
+    b[:500] = 0.0
+    sg.sg_psnr(a, b, 1000, db)
+    assert float(db.item()) == pytest.approx(10 * np.log10(1 / 0.005), abs=1e-4)
+
+
+def test_training_beats_the_method_without_the_network():
+    import torch
+    from paper_1804_08197_b300 import sg
+    from paper_1804_08197_b300.learned import Learned
+    dims = (192, 192, 192)
+    a = synth.filaments_u16(dims, seed=41, ntubes=30)
+    vol = sg.sg_volume_create(dims, sg.SG_U16, 32, 3, model=synth.volume_model(192, 0.5))
+    try:
+        d = torch.from_numpy(a.view(np.int16)).cuda()
+        sg.sg_upload_volume_device(vol, 0, 0, d.data_ptr())
+        sg.sg_set_transfer_function(vol, 0, synth.tf_piecewise(2002, zero_alpha_points=2), 300.0, 60000.0)
+        W, H = 256, 288
+        rec = Learned(vol, W, H, max_batch=8, crop=32, seed=5)
+        try:
+            train = synth.head_poses(40, seed=9100, width=W, height=H, dist=(0.35, 0.8))
+            held = synth.head_poses(4, seed=9200, width=W, height=H, dist=(0.35, 0.8))
+            before = [rec.evaluate(v, p) for v, p in held]
+            for i in range(160):
+                v, p = train[i % len(train)]
+                rec.train_on_pair(v, p, steps=2, batch=8, lr=1e-3)
+            after = [rec.evaluate(v, p) for v, p in held]
+            assert np.mean(after) > np.mean(before) + 0.5, (before, after)
+        finally:
+            rec.close()
+    finally:
+        sg.sg_volume_destroy(vol)
