@@ -256,12 +256,19 @@ __global__ void __launch_bounds__(kSelThreads) k_select(SelJobs jobs, SelGeom g)
         if (slot[cid] < 0) miss |= 1 << k;
       }
       if (miss) {
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < 8; ++k) {
+          if (!(need & (1 << k))) continue;
+          int cx = 2 * bx + (k & 1), cy = 2 * by + ((k >> 1) & 1), cz = 2 * bz + ((k >> 2) & 1);
+          const int64_t cid = g.off[L - 1] + (cz * cny + cy) * cnx + cx;
           if (miss & (1 << k)) {
-            int cx = 2 * bx + (k & 1), cy = 2 * by + ((k >> 1) & 1), cz = 2 * bz + ((k >> 2) & 1);
             int r = atomicAdd(&s_nreq, 1);
-            J.req[r] = (int32_t)(g.off[L - 1] + (cz * cny + cy) * cnx + cx);
+            J.req[r] = (int32_t)cid;
+          } else if (g.stamp) {
+            // the resident siblings of the missing children are in use too:
+            // evicting them would keep this block from ever refining
+            g.stamp[slot[cid]] = g.frame;
           }
+        }
         J.state[id] = kFallback;
         atomicAdd(&s_sel, 1);
         atomicAdd(&s_fb, 1);
