@@ -205,6 +205,78 @@ def batched_4d(sg, torch, dev, reps=10):
     return res
 
 
+def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=1000, steps_per_pair=3, eval_poses=16,
+                  threshold_db=40.0):
+    """Learned reconstruction vs the plain path on the same GPU: training on
+    `pairs` seeded (pose, full-rate render, half-res render) pairs of the
+    bench volume, evaluation on a held-out volume seed and held-out poses.
+    Learned frame = select + render both eyes at 720x800, step 1.0, + the
+    U-Net to 2x1440x1600; a frame under the PSNR threshold falls back to (and
+    also pays for) the plain full-rate render."""
+    import synth
+    from paper_1804_08197_b300.learned import Learned
+    stream = torch.cuda.current_stream()
+    rec = Learned(vol, W_EYE, H_EYE, step=STEP, tau=TAU, max_batch=16, crop=64, seed=7)
+    t0 = time.perf_counter()
+    train = synth.head_poses(512, seed=9100, width=W_EYE, height=H_EYE)
+    for i in range(pairs):
+        v, p = train[i % len(train)]
+        rec.train_on_pair(v, p, steps=steps_per_pair, batch=16, lr=5e-4 if i < pairs * 3 // 4 else 1.5e-4)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # held-out volume (different seed) and poses
+    ev = synth.filaments_u16((N_VOX,) * 3, seed=9001)
+    vol2 = sg.sg_volume_create((N_VOX,) * 3, sg.SG_U16, BRICK, LEVELS, model=model)
+    d = torch.from_numpy(ev.view(np.int16)).to(dev)
+    sg.sg_upload_volume_device(vol2, 0, 0, d.data_ptr())
+    torch.cuda.synchronize()
+    del d, ev
+    sg.sg_set_transfer_function(vol2, 0, tf_table, *WINDOW)
+    rec.vol = vol2
+    held = synth.head_poses(eval_poses, seed=9300, width=W_EYE, height=H_EYE)
+    for v, p in held[:2]:  # warm-up
+        rec.evaluate(v, p)
+    ev_ = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    psnrs, t_learned, t_plain, t_net = [], [], [], []
+    for v, p in held:
+        a, b = ev_()
+        a.record(stream)
+        rec.render_half(v, p, stream=stream)
+        c, dd = ev_()
+        c.record(stream)
+        rec.reconstruct(stream=stream)
+        dd.record(stream)
+        b.record(stream)
+        e, f = ev_()
+        e.record(stream)
+        rec.render_full(v, p, stream=stream)
+        f.record(stream)
+        torch.cuda.synchronize()
+        psnrs.append(rec.frame_psnr(stream=stream))
+        t_learned.append(a.elapsed_time(b))
+        t_net.append(c.elapsed_time(dd))
+        t_plain.append(e.elapsed_time(f))
+    sg.sg_volume_destroy(vol2)
+    rec.close()
+    psnrs = np.array(psnrs)
+    fall = psnrs < threshold_db
+    learned_ms = float(np.mean(np.array(t_learned) + np.where(fall, t_plain, 0.0)))
+    plain_ms = float(np.mean(t_plain))
+    net_flop = 2 * 268.0e9 / 2  # ~134 GFLOP per eye (3x3 convs), both eyes
+    return {"workload": "learned reconstruction: 2x720x800 at step 1.0 -> U-Net (32/64/128, BF16) -> 2x1440x1600; "
+                        f"trained on {pairs} seeded pairs of the bench volume, evaluated on a held-out volume "
+                        f"seed and {eval_poses} held-out poses",
+            "learned_fps": round(1e3 / learned_ms, 2), "plain_fps": round(1e3 / plain_ms, 2),
+            "learned_over_plain": round(plain_ms / learned_ms, 3),
+            "psnr_db": {"mean": round(float(psnrs.mean()), 2), "min": round(float(psnrs.min()), 2),
+                        "median": round(float(np.median(psnrs)), 2)},
+            "fallback_rate": round(float(fall.mean()), 3), "threshold_db": threshold_db,
+            "net_ms": round(float(np.mean(t_net)), 3),
+            "net_tflops": round(net_flop / (float(np.mean(t_net)) / 1e3) / 1e12, 1),
+            "half_render_ms": round(float(np.mean(np.array(t_learned) - np.array(t_net))), 3),
+            "train_s": round(train_s, 1), "train_pairs": pairs, "steps_per_pair": steps_per_pair}
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle on the host cores, bounded sample per step."""
     if rank != 0:
@@ -332,9 +404,10 @@ def run_ours(args, rank, world, local_rank):
         sg.sg_render_host(vol, p, prm, host, stream=stream)
     e2e_s = time.perf_counter() - t0
 
-    batched = None
+    batched = learned = None
     if rank == 0 and not args.no_extra and n_vox == N_VOX:
         batched = batched_4d(sg, torch, dev)
+        learned = learned_recon(sg, torch, dev, vol, tf_table, model, pairs=args.learned_pairs)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and n_vox == N_VOX:
@@ -364,6 +437,8 @@ def run_ours(args, rank, world, local_rank):
             line["cpu_baseline"] = cpu
         if batched:
             line["batched_4d"] = batched
+        if learned:
+            line["learned"] = learned
         print(json.dumps(line), flush=True)
     sg.sg_volume_destroy(vol)
 
@@ -375,7 +450,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the batched 4D multichannel measurement")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched 4D and learned measurements")
+    ap.add_argument("--learned-pairs", type=int, default=1000, help="training pairs for the learned path")
     ap.add_argument("--volume", type=int, default=N_VOX, help="volume edge (default 1024; smaller for profiling)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
