@@ -326,6 +326,16 @@ sg_status sg_unet_forward(sg_unet* net, const float* const* in, int64_t in_pitch
 sg_status sg_unet_backward(sg_unet* net, const float* const* target, int64_t target_pitch, const float* const* out,
                            int64_t out_pitch, float* loss, void* stream);
 
+/* Selects the tensor-core path of the convolutions: 1 (default) = tcgen05
+ * with tensor-memory accumulators, 0 = mma.sync (the portable path; same
+ * arithmetic: BF16 products, FP32 sums). */
+sg_status sg_unet_set_tensor_path(sg_unet* net, int tcgen05);
+
+/* Reports (and clears) a timed-out bounded wait in a tcgen05 convolution since
+ * the last check: SG_ERR_TIMEOUT means the affected outputs are invalid.
+ * Synchronous. */
+sg_status sg_unet_check(sg_unet* net);
+
 /* One Adam step on the FP32 master parameters with the last gradients
  * (bias-corrected moments), then refreshes the BF16 copies. */
 sg_status sg_unet_adam_step(sg_unet* net, float lr, float beta1, float beta2, float eps, void* stream);

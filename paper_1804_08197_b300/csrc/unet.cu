@@ -20,6 +20,7 @@
 
 #include "internal.h"
 #include "unet_gemm.cuh"
+#include "unet_tc.cuh"
 
 using namespace sg;
 using namespace sg::nn;
@@ -88,6 +89,8 @@ struct ConstOutPtrs {
 
 struct sg_unet {
   int max_n = 0, max_h = 0, max_w = 0;
+  int tc = 1;                 // convolutions on tcgen05 (1) or mma.sync (0)
+  uint32_t* d_err = nullptr;  // set by a tcgen05 kernel whose bounded wait gave up
   int n = 0, h = 0, w = 0;  // shape of the last forward
   int64_t nparam = 0;
   int64_t woff[kLayers], boff[kLayers];
@@ -139,7 +142,28 @@ cudaError_t conv_bn(const ConvArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t conv(const ConvArgs& a, cudaStream_t s) {
+template <int BN>
+cudaError_t conv_tc(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
+  const int64_t M = (int64_t)a.N * a.H * a.W;
+  const int smem = kTcStages * (kTcBM + BN) * kTcBK * 2;
+  static bool configured = false;  // per template instance, set once on first use
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  dim3 grid((unsigned)((M + kTcBM - 1) / kTcBM), a.Cout / BN);
+  k_conv3x3_tc<BN><<<grid, 128, smem, s>>>(a, err);
+  return cudaGetLastError();
+}
+
+cudaError_t conv(const ConvArgs& a, cudaStream_t s, uint32_t* tc_err = nullptr) {
+  if (tc_err) {
+    if (a.Cout % 128 == 0) return conv_tc<128>(a, tc_err, s);
+    if (a.Cout % 64 == 0) return conv_tc<64>(a, tc_err, s);
+    if (a.Cout % 32 == 0) return conv_tc<32>(a, tc_err, s);
+    return conv_tc<16>(a, tc_err, s);
+  }
   if (a.Cout % 128 == 0) return conv_bn<128>(a, s);
   if (a.Cout % 64 == 0) return conv_bn<64>(a, s);
   if (a.Cout % 32 == 0) return conv_bn<32>(a, s);
@@ -238,7 +262,7 @@ cudaError_t dgrad(sg_unet* u, int L, const bf16* dz, float* dx, int dx_stride, i
   a.f32_stride = dx_stride;
   a.f32_off = dx_off;
   a.f32_accumulate = 1;
-  return conv(a, s);
+  return conv(a, s, u->tc ? u->d_err : nullptr);
 }
 
 // He-normal initial weights (counter-based Box-Muller), zero biases, zero head
@@ -289,10 +313,10 @@ cudaError_t forward(sg_unet* u, const Crops& c, int N, int h, int w, float* out,
   if (e) return e;
   ConvArgs a;
   a = conv_args(u, C1A, u->in16, 16, 0, N, h, w); a.out = u->a1; a.out_stride = 32; a.out_off = 0;
-  if ((e = conv(a, s))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
   // e1 lives in cat1 at channel offset 64 (after the 64 upsampled channels)
   a = conv_args(u, C1B, u->a1, 32, 0, N, h, w); a.out = u->cat1; a.out_stride = 96; a.out_off = 64;
-  if ((e = conv(a, s))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
   // pool e1 -> p1
   {
     const bf16* src = u->cat1;
@@ -310,9 +334,9 @@ cudaError_t forward(sg_unet* u, const Crops& c, int N, int h, int w, float* out,
     if (e) return e;
   }
   a = conv_args(u, C2A, u->p1, 32, 0, N, h2, w2); a.out = u->a2; a.out_stride = 64; a.out_off = 0;
-  if ((e = conv(a, s))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
   a = conv_args(u, C2B, u->a2, 64, 0, N, h2, w2); a.out = u->cat2; a.out_stride = 192; a.out_off = 128;
-  if ((e = conv(a, s))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
   {
     const bf16* src = u->cat2;
     bf16* dst = u->p2;
@@ -329,9 +353,9 @@ cudaError_t forward(sg_unet* u, const Crops& c, int N, int h, int w, float* out,
     if (e) return e;
   }
   a = conv_args(u, C3A, u->p2, 64, 0, N, h4, w4); a.out = u->a3; a.out_stride = 128; a.out_off = 0;
-  if ((e = conv(a, s))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
   a = conv_args(u, C3B, u->a3, 128, 0, N, h4, w4); a.out = u->b3; a.out_stride = 128; a.out_off = 0;
-  if ((e = conv(a, s))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
   // nearest up b3 -> cat2[:, 0..128)
   {
     const bf16* src = u->b3;
@@ -345,9 +369,9 @@ cudaError_t forward(sg_unet* u, const Crops& c, int N, int h, int w, float* out,
     if (e) return e;
   }
   a = conv_args(u, D2A, u->cat2, 192, 0, N, h2, w2); a.out = u->a4; a.out_stride = 64; a.out_off = 0;
-  if ((e = conv(a, s))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
   a = conv_args(u, D2B, u->a4, 64, 0, N, h2, w2); a.out = u->d2; a.out_stride = 64; a.out_off = 0;
-  if ((e = conv(a, s))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
   {
     const bf16* src = u->d2;
     bf16* dst = u->cat1;
@@ -360,11 +384,11 @@ cudaError_t forward(sg_unet* u, const Crops& c, int N, int h, int w, float* out,
     if (e) return e;
   }
   a = conv_args(u, D1A, u->cat1, 96, 0, N, h, w); a.out = u->a5; a.out_stride = 32; a.out_off = 0;
-  if ((e = conv(a, s))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
   a = conv_args(u, D1B, u->a5, 32, 0, N, h, w); a.out = u->d1; a.out_stride = 32; a.out_off = 0;
-  if ((e = conv(a, s))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
   a = conv_args(u, HEAD, u->d1, 32, 0, N, h, w); a.out_f32 = u->head; a.f32_stride = 16; a.f32_off = 0;
-  if ((e = conv(a, s))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
   // out = bilinear 2x (half-pixel centres, clamp) of the input + pixel shuffle of the head
   {
     const float* head = u->head;
@@ -590,6 +614,7 @@ sg_status sg_unet_create(int max_batch, int max_h, int max_w, uint64_t seed, sg_
   A_(u->g_head, P1 * 16 * f) A_(u->dz, P1 * 32 * b)
   A_(u->dw_part, (size_t)kWgradSplits * 9 * 128 * 192 * f) A_(u->db_part, (size_t)kWgradSplits * 128 * f)
   A_(u->d_loss, 2 * f)
+  A_(u->d_err, 16)
 #undef A_
   if (e != cudaSuccess) {
     free_unet(u);
@@ -599,6 +624,7 @@ sg_status sg_unet_create(int max_batch, int max_h, int max_w, uint64_t seed, sg_
   // He-normal weights, zero biases; the head starts at zero so the untrained
   // network is exactly the bilinear upsampling of its input
   cudaMemset(u->d_param, 0, off * f);
+  cudaMemset(u->d_err, 0, 16);
   cudaMemset(u->d_m, 0, off * f);
   cudaMemset(u->d_v, 0, off * f);
   for (int L = 0; L < HEAD; ++L) {
@@ -621,6 +647,31 @@ sg_status sg_unet_create(int max_batch, int max_h, int max_w, uint64_t seed, sg_
     return cuda_fail(e, "sg_unet_create");
   }
   *out = u;
+  return SG_OK;
+}
+
+sg_status sg_unet_set_tensor_path(sg_unet* u, int tcgen05) {
+  if (!u || (tcgen05 != 0 && tcgen05 != 1)) {
+    set_error("sg_unet_set_tensor_path: NULL or mode not 0/1");
+    return SG_ERR_INVALID_ARG;
+  }
+  u->tc = tcgen05;
+  return SG_OK;
+}
+
+sg_status sg_unet_check(sg_unet* u) {
+  if (!u) {
+    set_error("sg_unet_check: NULL");
+    return SG_ERR_INVALID_ARG;
+  }
+  uint32_t e = 0;
+  cudaError_t ce = cudaMemcpy(&e, u->d_err, sizeof e, cudaMemcpyDeviceToHost);
+  if (ce != cudaSuccess) return cuda_fail(ce, "sg_unet_check");
+  if (e) {
+    cudaMemset(u->d_err, 0, sizeof e);
+    set_error("sg_unet: a tensor-core wait timed out (results of the affected launches are invalid)");
+    return SG_ERR_TIMEOUT;
+  }
   return SG_OK;
 }
 

@@ -1,0 +1,244 @@
+// 3x3 convolution as an implicit GEMM on the 5th-generation tensor cores
+// (tcgen05, sm_100 family): BF16 operands in shared memory, FP32
+// accumulator in tensor memory (TMEM), one thread issuing the MMAs.
+//
+// Tile: 128 output pixels (M) x BN output channels (N) per CTA; K = 9 Cin
+// (tap-major, then channel) in blocks of 64, zero-padded to a multiple of 64.
+// Operands are gathered with cp.async into the canonical K-major layout
+// without swizzle: 8-row x 16-byte core matrices, 128 bytes each; along K
+// core matrices are 128 B apart (leading byte offset), along M/N 8-row groups
+// are 1024 B apart (stride byte offset). A 3-stage ring overlaps the gather
+// of block k+2 with the MMAs of block k; tcgen05.commit arrives on the
+// stage's mbarrier when its MMAs are done. Every wait is bounded: on timeout
+// the CTA raises an error word and leaves (after freeing its TMEM).
+#pragma once
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "unet_gemm.cuh"
+
+namespace sg {
+namespace nn {
+
+constexpr int kTcBM = 128, kTcBK = 64, kTcStages = 3;
+constexpr uint32_t kTcSpinLimit = 1u << 26;
+
+__device__ __forceinline__ uint64_t tc_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  // start address, leading / stride byte offsets (all >> 4), descriptor
+  // version 1, no swizzle, base offset 0
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major, M x N
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kTcSpinLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(128) k_conv3x3_tc(ConvArgs a, uint32_t* err) {
+  constexpr int kTmemCols = BN < 32 ? 32 : BN;
+  constexpr int kAStage = kTcBM * kTcBK * 2;  // bytes
+  constexpr int kBStage = BN * kTcBK * 2;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint64_t bars[kTcStages];
+  __shared__ uint32_t tmem_base_s;
+  __shared__ volatile int abort_s;
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + kTcStages * kAStage;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t M = (int64_t)a.N * a.H * a.W;
+  const int64_t m0 = (int64_t)blockIdx.x * kTcBM;
+  const int n0 = blockIdx.y * BN;
+  const int K = 9 * a.Cin;
+  const int nkb = (K + kTcBK - 1) / kTcBK;
+
+  if (tid == 0) {
+    for (int s = 0; s < kTcStages; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[s])));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    abort_s = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base_s)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_base_s;
+
+  // this thread gathers row `tid` of A (pixel m0 + tid) and row `tid` of B (channel n0 + tid)
+  const int64_t p = m0 + tid;
+  const bool prow = p < M;
+  int px = 0, py = 0;
+  int64_t pn = 0;
+  if (prow) {
+    px = (int)(p % a.W);
+    py = (int)((p / a.W) % a.H);
+    pn = p / ((int64_t)a.W * a.H);
+  }
+  auto gather = [&](int kb, int st) {
+    const uint32_t arow = smem_u32(sA + st * kAStage) + (tid >> 3) * 1024 + (tid & 7) * 16;
+#pragma unroll
+    for (int j = 0; j < kTcBK / 8; ++j) {
+      const int k = kb * kTcBK + j * 8;
+      const void* src = a.in;
+      int bytes = 0;
+      if (prow && k < K) {
+        const int tap = k / a.Cin, c = k % a.Cin;
+        const int yy = py + tap / 3 - 1, xx = px + tap % 3 - 1;
+        if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) {
+          src = a.in + (((pn * a.H + yy) * a.W + xx) * a.in_stride + a.in_off + c);
+          bytes = 16;
+        }
+      }
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(arow + j * 128), "l"(src), "r"(bytes));
+    }
+    if (tid < BN) {
+      const uint32_t brow = smem_u32(sB + st * kBStage) + (tid >> 3) * 1024 + (tid & 7) * 16;
+#pragma unroll
+      for (int j = 0; j < kTcBK / 8; ++j) {
+        const int k = kb * kTcBK + j * 8;
+        const void* src = a.wt;
+        int bytes = 0;
+        if (k < K) {
+          src = a.wt + (size_t)(n0 + tid) * K + k;
+          bytes = 16;
+        }
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(brow + j * 128), "l"(src), "r"(bytes));
+      }
+    }
+  };
+
+  // prologue: blocks 0 .. stages-2
+#pragma unroll
+  for (int s = 0; s < kTcStages - 1; ++s) {
+    if (s < nkb) gather(s, s);
+    cp_async_commit();
+  }
+  constexpr uint32_t idesc = tc_idesc(kTcBM, BN);
+  // no thread ever leaves the loop early (every __syncthreads is reached by
+  // all); after a timed-out wait the CTA only skips work and reports
+  for (int kb = 0; kb < nkb; ++kb) {
+    const int st = kb % kTcStages;
+    cp_async_wait<kTcStages - 2>();
+    // this thread's copies into stage st are complete; make them visible to the tensor core
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    const bool aborted = abort_s != 0;
+    if (tid == 0 && !aborted) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t a_base = smem_u32(sA + st * kAStage), b_base = smem_u32(sB + st * kBStage);
+#pragma unroll
+      for (int kk = 0; kk < kTcBK / 16; ++kk) {
+        const uint64_t da = tc_smem_desc(a_base + kk * 256, 128, 1024);
+        const uint64_t db = tc_smem_desc(b_base + kk * 256, 128, 1024);
+        const uint32_t accum = (kb > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(accum));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       smem_u32(&bars[st]))
+                   : "memory");
+    }
+    // refill the stage used by block kb-1 with block kb+stages-1 once its MMAs are done
+    const int nxt = kb + kTcStages - 1;
+    if (nxt < nkb && !aborted) {
+      const int sn = nxt % kTcStages;
+      bool ready = true;
+      if (nxt >= kTcStages) {
+        const int use = (nxt - kTcStages) / kTcStages;  // completed use of stage sn
+        ready = mbar_wait(smem_u32(&bars[sn]), use & 1);
+        if (!ready) abort_s = 1;
+      }
+      if (ready) gather(nxt, sn);
+    }
+    cp_async_commit();
+  }
+  __syncthreads();
+  // wait for the last block's MMAs
+  if (abort_s == 0) {
+    const int last = nkb - 1, st = last % kTcStages, use = last / kTcStages;
+    if (!mbar_wait(smem_u32(&bars[st]), use & 1)) abort_s = 1;
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  if (abort_s) {
+    if (tid == 0) atomicExch(err, 1u);
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    // epilogue: warp w reads TMEM lanes 32w .. 32w+31 (pixel rows), 16 columns at a time
+    const int64_t pr = m0 + warp * 32 + lane;
+#pragma unroll
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t r[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (pr < M) {
+        float v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          v[i] = __uint_as_float(r[i]);
+          if (a.bias) v[i] += a.bias[n0 + c0 + i];
+          if (a.relu) v[i] = fmaxf(v[i], 0.f);
+        }
+        if (a.out) {
+          uint32_t packed[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+            packed[i] = *reinterpret_cast<uint32_t*>(&h2);
+          }
+          uint4* o = reinterpret_cast<uint4*>(a.out + pr * a.out_stride + a.out_off + n0 + c0);
+          o[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+          o[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+        }
+        if (a.out_f32) {
+          float4* o = reinterpret_cast<float4*>(a.out_f32 + pr * a.f32_stride + a.f32_off + n0 + c0);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            float4 q = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            if (a.f32_accumulate) {
+              const float4 o0 = o[i];
+              q.x += o0.x; q.y += o0.y; q.z += o0.z; q.w += o0.w;
+            }
+            o[i] = q;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
+}
+
+}  // namespace nn
+}  // namespace sg

@@ -24,7 +24,8 @@ EXPORTS = ["sg_volume_create", "sg_volume_destroy", "sg_upload_volume_device", "
            "sg_render", "sg_render_host", "sg_render_batch", "sg_set_render_config", "sg_get_render_config",
            "sg_autotune_render", "sg_select_lod_noalloc", "sg_read_residency", "sg_set_brick_ranges", "sg_unet_create", "sg_unet_destroy",
            "sg_unet_param_count", "sg_unet_get_params", "sg_unet_set_params", "sg_unet_forward", "sg_unet_backward",
-           "sg_unet_adam_step", "sg_psnr", "sg_last_error", "sg_version"]
+           "sg_unet_adam_step", "sg_unet_set_tensor_path", "sg_unet_check", "sg_psnr", "sg_last_error",
+           "sg_version"]
 
 
 class SGError(RuntimeError):
@@ -94,6 +95,8 @@ def _load():
         "sg_unet_backward": [vp, vp, i64, vp, i64, vp, vp],
         "sg_unet_adam_step": [vp, f32, f32, f32, f32, vp],
         "sg_psnr": [vp, vp, i64, vp, vp],
+        "sg_unet_set_tensor_path": [vp, i32],
+        "sg_unet_check": [vp],
         "sg_render": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
         "sg_render_host": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
         "sg_render_batch": [vp, P(sg_pose), i32, P(sg_render_params), P(vp), vp],
@@ -347,3 +350,11 @@ def sg_unet_adam_step(net, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
 
 def sg_psnr(a, b, count, out_db, stream=None):
     _check(lib.sg_psnr(_ptr(a), _ptr(b), count, _ptr(out_db), _stream(stream)))
+
+
+def sg_unet_set_tensor_path(net, tcgen05=1):
+    _check(lib.sg_unet_set_tensor_path(net, tcgen05))
+
+
+def sg_unet_check(net):
+    _check(lib.sg_unet_check(net))

@@ -77,6 +77,35 @@ def test_forward_and_gradients_match_the_oracle_at_bf16_tolerance():
         sg.sg_unet_destroy(net)
 
 
+def test_tcgen05_and_mma_sync_paths_agree():
+    """The tcgen05 (TMEM) and mma.sync convolutions compute the same BF16
+    products with FP32 sums: outputs and gradients agree to summation order."""
+    from paper_1804_08197_b300 import sg
+    net = sg.sg_unet_create(2, 24, 40, seed=11)
+    try:
+        p = _random_params(12, sg.sg_unet_param_count(net))
+        sg.sg_unet_set_params(net, p)
+        rng = np.random.default_rng(13)
+        x = rng.uniform(0, 1, (2, 24, 40, 4))
+        t = rng.uniform(0, 1, (2, 48, 80, 4))
+        res = {}
+        for path in (0, 1):
+            sg.sg_unet_set_tensor_path(net, path)
+            out, loss = _run(net, x, t)
+            sg.sg_unet_check(net)
+            res[path] = (out, loss, sg.sg_unet_get_params(net, which=1).astype(np.float64))
+        base = ou.bilinear2x(x)
+        r0, r1 = res[0][0] - base, res[1][0] - base
+        assert np.linalg.norm(r1 - r0) <= 1e-3 * np.linalg.norm(r0)
+        assert res[1][1] == pytest.approx(res[0][1], rel=1e-4)
+        for ws, bs in ou.layer_slices():
+            for sl in (ws, bs):
+                g0, g1 = res[0][2][sl], res[1][2][sl]
+                assert np.linalg.norm(g1 - g0) <= 2e-2 * np.linalg.norm(g0) + 1e-12
+    finally:
+        sg.sg_unet_destroy(net)
+
+
 def test_untrained_network_is_exactly_bilinear_upsampling():
     from paper_1804_08197_b300 import sg
     net = sg.sg_unet_create(3, 12, 20, seed=9)
