@@ -205,7 +205,7 @@ def batched_4d(sg, torch, dev, reps=10):
     return res
 
 
-def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=1000, steps_per_pair=3, eval_poses=16,
+def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=2000, steps_per_pair=4, eval_poses=16,
                   threshold_db=40.0):
     """Learned reconstruction vs the plain path on the same GPU: training on
     `pairs` seeded (pose, full-rate render, half-res render) pairs of the
@@ -217,13 +217,6 @@ def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=1000, steps_per_pa
     from paper_1804_08197_b300.learned import Learned
     stream = torch.cuda.current_stream()
     rec = Learned(vol, W_EYE, H_EYE, step=STEP, tau=TAU, max_batch=16, crop=64, seed=7)
-    t0 = time.perf_counter()
-    train = synth.head_poses(512, seed=9100, width=W_EYE, height=H_EYE)
-    for i in range(pairs):
-        v, p = train[i % len(train)]
-        rec.train_on_pair(v, p, steps=steps_per_pair, batch=16, lr=5e-4 if i < pairs * 3 // 4 else 1.5e-4)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
     # held-out volume (different seed) and poses
     ev = synth.filaments_u16((N_VOX,) * 3, seed=9001)
     vol2 = sg.sg_volume_create((N_VOX,) * 3, sg.SG_U16, BRICK, LEVELS, model=model)
@@ -232,8 +225,20 @@ def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=1000, steps_per_pa
     torch.cuda.synchronize()
     del d, ev
     sg.sg_set_transfer_function(vol2, 0, tf_table, *WINDOW)
-    rec.vol = vol2
     held = synth.head_poses(eval_poses, seed=9300, width=W_EYE, height=H_EYE)
+    # the untrained network is exactly the bilinear upsampling: the method without it
+    rec.vol = vol2
+    bilinear = np.array([rec.evaluate(v, p) for v, p in held])
+    rec.vol = vol
+    t0 = time.perf_counter()
+    train = synth.head_poses(512, seed=9100, width=W_EYE, height=H_EYE)
+    for i in range(pairs):
+        v, p = train[i % len(train)]
+        rec.train_on_pair(v, p, steps=steps_per_pair, batch=16, lr=5e-4 if i < pairs * 3 // 4 else 1.5e-4)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    sg.sg_unet_check(rec.net)
+    rec.vol = vol2
     for v, p in held[:2]:  # warm-up
         rec.evaluate(v, p)
     ev_ = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -270,6 +275,7 @@ def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=1000, steps_per_pa
             "learned_over_plain": round(plain_ms / learned_ms, 3),
             "psnr_db": {"mean": round(float(psnrs.mean()), 2), "min": round(float(psnrs.min()), 2),
                         "median": round(float(np.median(psnrs)), 2)},
+            "bilinear_psnr_db": {"mean": round(float(bilinear.mean()), 2), "min": round(float(bilinear.min()), 2)},
             "fallback_rate": round(float(fall.mean()), 3), "threshold_db": threshold_db,
             "net_ms": round(float(np.mean(t_net)), 3),
             "net_tflops": round(net_flop / (float(np.mean(t_net)) / 1e3) / 1e12, 1),
@@ -451,7 +457,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched 4D and learned measurements")
-    ap.add_argument("--learned-pairs", type=int, default=1000, help="training pairs for the learned path")
+    ap.add_argument("--learned-pairs", type=int, default=2000, help="training pairs for the learned path")
     ap.add_argument("--volume", type=int, default=N_VOX, help="volume edge (default 1024; smaller for profiling)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -5,8 +5,8 @@ Every step runs in libsg.so kernels; this module only sequences C-ABI calls
 and passes device pointers (crops are pointer offsets into full images, no
 copies). A pair is the plain full-rate render of a pose (W x H per eye,
 step s) and the reduced render of the same pose at half resolution and twice
-the step (W/2 x H/2, step 2s, LOD chosen for the half-resolution image); the
-network maps the reduced render to the full-rate one. The full-rate render
+the step (W/2 x H/2, step 2s, at the level of detail of the full-resolution
+image); the network maps the reduced render to the full-rate one. The full-rate render
 is also the fallback and the judge: a frame whose PSNR against it falls below
 the threshold is replaced by it.
 """
@@ -46,7 +46,9 @@ class Learned:
         return sg.make_pose(views, projs, self.W, self.H, pixel_error=self.tau, t=t, slot=self.slot_full)
 
     def pose_half(self, views, projs, t=0):
-        return sg.make_pose(views, projs, self.w, self.h, pixel_error=self.tau, t=t, slot=self.slot_half)
+        # the reduced render keeps the level of detail of the full-resolution
+        # image: tau is halved because its pixels are twice as large
+        return sg.make_pose(views, projs, self.w, self.h, pixel_error=0.5 * self.tau, t=t, slot=self.slot_half)
 
     def render_full(self, views, projs, outs=None, stream=None):
         p = self.pose_full(views, projs)
