@@ -85,6 +85,121 @@ struct ConstOutPtrs {
   const float* p[64];
 };
 
+// per-item kernels with 32-bit indices (every count here is < 2^31), one
+// item = one pixel or one pixel x 8-channel chunk, 16-byte accesses
+template <typename F>
+__global__ void k_each32(int n, F f) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) f(i);
+}
+template <typename F>
+cudaError_t each32(int64_t n, cudaStream_t s, F f) {
+  if (n <= 0) return cudaSuccess;
+  k_each32<<<blocks_for(n), 256, 0, s>>>((int)n, f);
+  return cudaGetLastError();
+}
+
+struct Pix {  // pixel index -> (n, y, x) of an N x H x W grid
+  int n, y, x;
+  __device__ Pix(int i, int H, int W) {
+    const int hw = H * W;
+    n = i / hw;
+    const int r = i - n * hw;
+    y = r / W;
+    x = r - y * W;
+  }
+};
+
+__device__ __forceinline__ void bf8_to_f(const uint4& v, float* f) {
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 t = __bfloat1622float2(h[i]);
+    f[2 * i] = t.x;
+    f[2 * i + 1] = t.y;
+  }
+}
+__device__ __forceinline__ uint4 f_to_bf8(const float* f) {
+  uint4 v;
+  __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&v);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+  return v;
+}
+
+// dst[q, doff + c] = mean of the 2x2 children of src (BF16, channels in chunks of 8)
+cudaError_t pool_fwd(const bf16* src, int sstride, int soff, bf16* dst, int dstride, int doff, int C, int N, int h,
+                     int w, cudaStream_t s) {
+  const int h2 = h / 2, w2 = w / 2, nc = C / 8;
+  return each32((int64_t)N * h2 * w2 * nc, s, [=] __device__(int i) {
+    const int q = i / nc, c = (i - q * nc) * 8;
+    const Pix P(q, h2, w2);
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0}, f[8];
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        bf8_to_f(*reinterpret_cast<const uint4*>(src + ((size_t)(P.n * h + 2 * P.y + dy) * w + 2 * P.x + dx) * sstride +
+                                                 soff + c),
+                 f);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] += f[k];
+      }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] *= 0.25f;
+    *reinterpret_cast<uint4*>(dst + (size_t)q * dstride + doff + c) = f_to_bf8(acc);
+  });
+}
+
+// dst (2h x 2w) [q, doff + c] = src (h x w) nearest
+cudaError_t up_fwd(const bf16* src, int sstride, bf16* dst, int dstride, int doff, int C, int N, int h, int w,
+                   cudaStream_t s) {
+  const int H = 2 * h, W = 2 * w, nc = C / 8;
+  return each32((int64_t)N * H * W * nc, s, [=] __device__(int i) {
+    const int q = i / nc, c = (i - q * nc) * 8;
+    const Pix P(q, H, W);
+    *reinterpret_cast<uint4*>(dst + (size_t)q * dstride + doff + c) =
+        *reinterpret_cast<const uint4*>(src + ((size_t)(P.n * h + P.y / 2) * w + P.x / 2) * sstride + c);
+  });
+}
+
+// gradient of nearest upsampling: dst (h x w) += sum of the 4 children in src (2h x 2w, FP32)
+cudaError_t up_bwd(const float* src, int sstride, float* dst, int dstride, int C, int N, int h, int w,
+                   cudaStream_t s) {
+  const int nc = C / 4;
+  return each32((int64_t)N * h * w * nc, s, [=] __device__(int i) {
+    const int q = i / nc, c = (i - q * nc) * 4;
+    const Pix P(q, h, w);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        const float4 v = *reinterpret_cast<const float4*>(
+            src + ((size_t)(P.n * 2 * h + 2 * P.y + dy) * (2 * w) + 2 * P.x + dx) * sstride + c);
+        acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+      }
+    float4* o = reinterpret_cast<float4*>(dst + (size_t)q * dstride + c);
+    float4 t = *o;
+    t.x += acc.x; t.y += acc.y; t.z += acc.z; t.w += acc.w;
+    *o = t;
+  });
+}
+
+// gradient of 2x2 average pooling: dst (2h x 2w)[., doff + c] += src (h x w) / 4 (FP32)
+cudaError_t pool_bwd(const float* src, int sstride, float* dst, int dstride, int doff, int C, int N, int h, int w,
+                     cudaStream_t s) {
+  const int H = 2 * h, W = 2 * w, nc = C / 4;
+  return each32((int64_t)N * H * W * nc, s, [=] __device__(int i) {
+    const int q = i / nc, c = (i - q * nc) * 4;
+    const Pix P(q, H, W);
+    const float4 v = *reinterpret_cast<const float4*>(src + ((size_t)(P.n * h + P.y / 2) * w + P.x / 2) * sstride + c);
+    float4* o = reinterpret_cast<float4*>(dst + (size_t)q * dstride + doff + c);
+    float4 t = *o;
+    t.x += 0.25f * v.x; t.y += 0.25f * v.y; t.z += 0.25f * v.z; t.w += 0.25f * v.w;
+    *o = t;
+  });
+}
+
 }  // namespace
 
 struct sg_unet {
@@ -232,15 +347,23 @@ ConvArgs conv_args(sg_unet* u, int L, const bf16* in, int in_stride, int in_off,
   return a;
 }
 
-// masked gradient: dz = bf16(dy * (y > 0)) (no mask for the head)
+// masked gradient: dz = bf16(dy * (y > 0)) (no mask for the head), 8 channels per item
 cudaError_t relu_bwd(const float* dy, int dy_stride, int dy_off, const bf16* y, int y_stride, int y_off, int C,
                      int64_t P, bf16* dz, cudaStream_t s) {
-  return each(P * C, s, [=] __device__(int64_t i) {
-    const int64_t p = i / C;
-    const int c = (int)(i % C);
-    float g = dy[p * dy_stride + dy_off + c];
-    if (y && !(__bfloat162float(y[p * y_stride + y_off + c]) > 0.f)) g = 0.f;
-    dz[i] = __float2bfloat16_rn(g);
+  const int nc = C / 8;
+  return each32(P * nc, s, [=] __device__(int i) {
+    const int p = i / nc, c = (i - p * nc) * 8;
+    const float4* g = reinterpret_cast<const float4*>(dy + (size_t)p * dy_stride + dy_off + c);
+    const float4 g0 = g[0], g1 = g[1];
+    float f[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+    if (y) {
+      float yv[8];
+      bf8_to_f(*reinterpret_cast<const uint4*>(y + (size_t)p * y_stride + y_off + c), yv);
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (!(yv[k] > 0.f)) f[k] = 0.f;
+    }
+    *reinterpret_cast<uint4*>(dz + (size_t)p * C + c) = f_to_bf8(f);
   });
 }
 
@@ -299,16 +422,17 @@ cudaError_t forward(sg_unet* u, const Crops& c, int N, int h, int w, float* out,
                     float* const* out_ptrs, cudaStream_t s) {
   cudaError_t e;
   const int h2 = h / 2, w2 = w / 2, h4 = h / 4, w4 = w / 4;
-  const int64_t P1 = (int64_t)N * h * w, P2 = P1 / 4, P3 = P1 / 16;
-  // input: RGBA -> 16 BF16 channels
+  const int64_t P1 = (int64_t)N * h * w;
+  // input: RGBA -> 16 BF16 channels (4 + 12 zero), one pixel per item
   bf16* in16 = u->in16;
   const Crops cc = c;
-  e = each(P1 * 16, s, [=] __device__(int64_t i) {
-    const int ch = (int)(i % 16);
-    const int64_t p = i / 16;
-    const int x = (int)(p % w), y = (int)((p / w) % h), n = (int)(p / ((int64_t)w * h));
-    float v = ch < 4 ? cc.ptr[n][y * cc.pitch + x * 4 + ch] : 0.f;
-    in16[i] = __float2bfloat16_rn(v);
+  e = each32(P1, s, [=] __device__(int i) {
+    const Pix P(i, h, w);
+    const float4 v = *reinterpret_cast<const float4*>(cc.ptr[P.n] + (int64_t)P.y * cc.pitch + P.x * 4);
+    const float f[8] = {v.x, v.y, v.z, v.w, 0.f, 0.f, 0.f, 0.f}, zero[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint4* o = reinterpret_cast<uint4*>(in16 + (size_t)i * 16);
+    o[0] = f_to_bf8(f);
+    o[1] = f_to_bf8(zero);
   });
   if (e) return e;
   ConvArgs a;
@@ -317,72 +441,22 @@ cudaError_t forward(sg_unet* u, const Crops& c, int N, int h, int w, float* out,
   // e1 lives in cat1 at channel offset 64 (after the 64 upsampled channels)
   a = conv_args(u, C1B, u->a1, 32, 0, N, h, w); a.out = u->cat1; a.out_stride = 96; a.out_off = 64;
   if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
-  // pool e1 -> p1
-  {
-    const bf16* src = u->cat1;
-    bf16* dst = u->p1;
-    e = each(P2 * 32, s, [=] __device__(int64_t i) {
-      const int ch = (int)(i % 32);
-      const int64_t q = i / 32;
-      const int x = (int)(q % w2), y = (int)((q / w2) % h2), n = (int)(q / ((int64_t)w2 * h2));
-      float acc = 0.f;
-      for (int dy = 0; dy < 2; ++dy)
-        for (int dx = 0; dx < 2; ++dx)
-          acc += __bfloat162float(src[(((int64_t)n * h + 2 * y + dy) * w + 2 * x + dx) * 96 + 64 + ch]);
-      dst[i] = __float2bfloat16_rn(0.25f * acc);
-    });
-    if (e) return e;
-  }
+  if ((e = pool_fwd(u->cat1, 96, 64, u->p1, 32, 0, 32, N, h, w, s))) return e;  // pool e1 -> p1
   a = conv_args(u, C2A, u->p1, 32, 0, N, h2, w2); a.out = u->a2; a.out_stride = 64; a.out_off = 0;
   if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
   a = conv_args(u, C2B, u->a2, 64, 0, N, h2, w2); a.out = u->cat2; a.out_stride = 192; a.out_off = 128;
   if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
-  {
-    const bf16* src = u->cat2;
-    bf16* dst = u->p2;
-    e = each(P3 * 64, s, [=] __device__(int64_t i) {
-      const int ch = (int)(i % 64);
-      const int64_t q = i / 64;
-      const int x = (int)(q % w4), y = (int)((q / w4) % h4), n = (int)(q / ((int64_t)w4 * h4));
-      float acc = 0.f;
-      for (int dy = 0; dy < 2; ++dy)
-        for (int dx = 0; dx < 2; ++dx)
-          acc += __bfloat162float(src[(((int64_t)n * h2 + 2 * y + dy) * w2 + 2 * x + dx) * 192 + 128 + ch]);
-      dst[i] = __float2bfloat16_rn(0.25f * acc);
-    });
-    if (e) return e;
-  }
+  if ((e = pool_fwd(u->cat2, 192, 128, u->p2, 64, 0, 64, N, h2, w2, s))) return e;  // pool e2 -> p2
   a = conv_args(u, C3A, u->p2, 64, 0, N, h4, w4); a.out = u->a3; a.out_stride = 128; a.out_off = 0;
   if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
   a = conv_args(u, C3B, u->a3, 128, 0, N, h4, w4); a.out = u->b3; a.out_stride = 128; a.out_off = 0;
   if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
-  // nearest up b3 -> cat2[:, 0..128)
-  {
-    const bf16* src = u->b3;
-    bf16* dst = u->cat2;
-    e = each(P2 * 128, s, [=] __device__(int64_t i) {
-      const int ch = (int)(i % 128);
-      const int64_t q = i / 128;
-      const int x = (int)(q % w2), y = (int)((q / w2) % h2), n = (int)(q / ((int64_t)w2 * h2));
-      dst[q * 192 + ch] = src[(((int64_t)n * h4 + y / 2) * w4 + x / 2) * 128 + ch];
-    });
-    if (e) return e;
-  }
+  if ((e = up_fwd(u->b3, 128, u->cat2, 192, 0, 128, N, h4, w4, s))) return e;  // up b3 -> cat2[:, 0..128)
   a = conv_args(u, D2A, u->cat2, 192, 0, N, h2, w2); a.out = u->a4; a.out_stride = 64; a.out_off = 0;
   if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
   a = conv_args(u, D2B, u->a4, 64, 0, N, h2, w2); a.out = u->d2; a.out_stride = 64; a.out_off = 0;
   if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
-  {
-    const bf16* src = u->d2;
-    bf16* dst = u->cat1;
-    e = each(P1 * 64, s, [=] __device__(int64_t i) {
-      const int ch = (int)(i % 64);
-      const int64_t q = i / 64;
-      const int x = (int)(q % w), y = (int)((q / w) % h), n = (int)(q / ((int64_t)w * h));
-      dst[q * 96 + ch] = src[(((int64_t)n * h2 + y / 2) * w2 + x / 2) * 64 + ch];
-    });
-    if (e) return e;
-  }
+  if ((e = up_fwd(u->d2, 64, u->cat1, 96, 0, 64, N, h2, w2, s))) return e;  // up d2 -> cat1[:, 0..64)
   a = conv_args(u, D1A, u->cat1, 96, 0, N, h, w); a.out = u->a5; a.out_stride = 32; a.out_off = 0;
   if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
   a = conv_args(u, D1B, u->a5, 32, 0, N, h, w); a.out = u->d1; a.out_stride = 32; a.out_off = 0;
@@ -396,22 +470,26 @@ cudaError_t forward(sg_unet* u, const Crops& c, int N, int h, int w, float* out,
     OutPtrs op;
     for (int n = 0; n < N; ++n) op.p[n] = out_ptrs ? out_ptrs[n] : out + (size_t)n * H2 * out_pitch;
     const int64_t opitch = out_pitch;
-    e = each((int64_t)N * H2 * W2 * 4, s, [=] __device__(int64_t i) {
-      const int ch = (int)(i % 4);
-      const int64_t q = i / 4;
-      const int X = (int)(q % W2), Y = (int)((q / W2) % H2), n = (int)(q / ((int64_t)W2 * H2));
-      const float ux = 0.5f * X - 0.25f, uy = 0.5f * Y - 0.25f;
+    e = each32((int64_t)N * H2 * W2, s, [=] __device__(int i) {
+      const Pix P(i, H2, W2);
+      const float ux = 0.5f * P.x - 0.25f, uy = 0.5f * P.y - 0.25f;
       const float fx0 = floorf(ux), fy0 = floorf(uy);
       const float fx = ux - fx0, fy = uy - fy0;
       const int x0 = min(max((int)fx0, 0), w - 1), x1 = min(max((int)fx0 + 1, 0), w - 1);
       const int y0 = min(max((int)fy0, 0), h - 1), y1 = min(max((int)fy0 + 1, 0), h - 1);
-      const float* src = cc.ptr[n];
-      const float v00 = src[y0 * cc.pitch + x0 * 4 + ch], v01 = src[y0 * cc.pitch + x1 * 4 + ch];
-      const float v10 = src[y1 * cc.pitch + x0 * 4 + ch], v11 = src[y1 * cc.pitch + x1 * 4 + ch];
-      const float b = (1.f - fy) * ((1.f - fx) * v00 + fx * v01) + fy * ((1.f - fx) * v10 + fx * v11);
-      const int k = ch * 4 + (Y & 1) * 2 + (X & 1);  // head channel of this sub-pixel
-      const float r = head[(((int64_t)n * h + Y / 2) * w + X / 2) * 16 + k];
-      op.p[n][(int64_t)Y * opitch + X * 4 + ch] = b + r;
+      const float* src = cc.ptr[P.n];
+      const float4 v00 = *reinterpret_cast<const float4*>(src + y0 * cc.pitch + x0 * 4);
+      const float4 v01 = *reinterpret_cast<const float4*>(src + y0 * cc.pitch + x1 * 4);
+      const float4 v10 = *reinterpret_cast<const float4*>(src + y1 * cc.pitch + x0 * 4);
+      const float4 v11 = *reinterpret_cast<const float4*>(src + y1 * cc.pitch + x1 * 4);
+      const float a00 = (1.f - fy) * (1.f - fx), a01 = (1.f - fy) * fx, a10 = fy * (1.f - fx), a11 = fy * fx;
+      const float* hp = head + ((size_t)(P.n * h + P.y / 2) * w + P.x / 2) * 16 + (P.y & 1) * 2 + (P.x & 1);
+      float4 o;
+      o.x = a00 * v00.x + a01 * v01.x + a10 * v10.x + a11 * v11.x + hp[0];
+      o.y = a00 * v00.y + a01 * v01.y + a10 * v10.y + a11 * v11.y + hp[4];
+      o.z = a00 * v00.z + a01 * v01.z + a10 * v10.z + a11 * v11.z + hp[8];
+      o.w = a00 * v00.w + a01 * v01.w + a10 * v10.w + a11 * v11.w + hp[12];
+      *reinterpret_cast<float4*>(op.p[P.n] + (int64_t)P.y * opitch + P.x * 4) = o;
     });
     if (e) return e;
   }
@@ -449,21 +527,24 @@ cudaError_t backward(sg_unet* u, const Crops& tgt, const float* out, int64_t out
     const Crops t = tgt;
     const int64_t opitch = out_pitch;
     const float scale = 1.0f / (float)count;
-    e = each(count, s, [=] __device__(int64_t i) {
-      const int ch = (int)(i % 4);
-      const int64_t q = i / 4;
-      const int X = (int)(q % W2), Y = (int)((q / W2) % H2), n = (int)(q / ((int64_t)W2 * H2));
-      const float d = op.p[n][(int64_t)Y * opitch + X * 4 + ch] - t.ptr[n][Y * t.pitch + X * 4 + ch];
-      const int k = ch * 4 + (Y & 1) * 2 + (X & 1);
-      gh[(((int64_t)n * h + Y / 2) * w + X / 2) * 16 + k] = 2.0f * d * scale;
+    const int64_t npix = (int64_t)N * H2 * W2;
+    e = each32(npix, s, [=] __device__(int i) {
+      const Pix P(i, H2, W2);
+      const float4 o = *reinterpret_cast<const float4*>(op.p[P.n] + (int64_t)P.y * opitch + P.x * 4);
+      const float4 g = *reinterpret_cast<const float4*>(t.ptr[P.n] + (int64_t)P.y * t.pitch + P.x * 4);
+      float* hp = gh + ((size_t)(P.n * h + P.y / 2) * w + P.x / 2) * 16 + (P.y & 1) * 2 + (P.x & 1);
+      hp[0] = 2.0f * (o.x - g.x) * scale;
+      hp[4] = 2.0f * (o.y - g.y) * scale;
+      hp[8] = 2.0f * (o.z - g.z) * scale;
+      hp[12] = 2.0f * (o.w - g.w) * scale;
     });
     if (e) return e;
-    e = sum(count, loss, s, [=] __device__(int64_t i) {
-      const int ch = (int)(i % 4);
-      const int64_t q = i / 4;
-      const int X = (int)(q % W2), Y = (int)((q / W2) % H2), n = (int)(q / ((int64_t)W2 * H2));
-      const float d = op.p[n][(int64_t)Y * opitch + X * 4 + ch] - t.ptr[n][Y * t.pitch + X * 4 + ch];
-      return d * d * scale;
+    e = sum(npix, loss, s, [=] __device__(int64_t i) {
+      const Pix P((int)i, H2, W2);
+      const float4 o = *reinterpret_cast<const float4*>(op.p[P.n] + (int64_t)P.y * opitch + P.x * 4);
+      const float4 g = *reinterpret_cast<const float4*>(t.ptr[P.n] + (int64_t)P.y * t.pitch + P.x * 4);
+      const float dx = o.x - g.x, dy = o.y - g.y, dz = o.z - g.z, dw = o.w - g.w;
+      return (dx * dx + dy * dy + dz * dz + dw * dw) * scale;
     });
     if (e) return e;
   }
@@ -480,21 +561,7 @@ cudaError_t backward(sg_unet* u, const Crops& tgt, const float* out, int64_t out
   if ((e = relu_bwd(u->g_a5, 32, 0, u->a5, 32, 0, 32, P1, dz, s))) return e;
   if ((e = wgrad(u, D1A, dz, 32, u->cat1, 96, 0, N, h, w, s))) return e;
   if ((e = dgrad(u, D1A, dz, u->g_cat1, 96, 0, N, h, w, s))) return e;
-  // up: g_d2 += sum of the 4 children of g_cat1[:, 0..64)
-  {
-    const float* gc = u->g_cat1;
-    float* gd = u->g_d2;
-    e = each(P2 * 64, s, [=] __device__(int64_t i) {
-      const int ch = (int)(i % 64);
-      const int64_t q = i / 64;
-      const int x = (int)(q % w2), y = (int)((q / w2) % h2), n = (int)(q / ((int64_t)w2 * h2));
-      float acc = 0.f;
-      for (int dy = 0; dy < 2; ++dy)
-        for (int dx = 0; dx < 2; ++dx) acc += gc[(((int64_t)n * h + 2 * y + dy) * w + 2 * x + dx) * 96 + ch];
-      gd[i] += acc;
-    });
-    if (e) return e;
-  }
+  if ((e = up_bwd(u->g_cat1, 96, u->g_d2, 64, 64, N, h2, w2, s))) return e;  // up: g_d2 += children
   // d2b: y = d2, x = a4
   if ((e = relu_bwd(u->g_d2, 64, 0, u->d2, 64, 0, 64, P2, dz, s))) return e;
   if ((e = wgrad(u, D2B, dz, 64, u->a4, 64, 0, N, h2, w2, s))) return e;
@@ -503,21 +570,7 @@ cudaError_t backward(sg_unet* u, const Crops& tgt, const float* out, int64_t out
   if ((e = relu_bwd(u->g_a4, 64, 0, u->a4, 64, 0, 64, P2, dz, s))) return e;
   if ((e = wgrad(u, D2A, dz, 64, u->cat2, 192, 0, N, h2, w2, s))) return e;
   if ((e = dgrad(u, D2A, dz, u->g_cat2, 192, 0, N, h2, w2, s))) return e;
-  // up: g_b3 += children of g_cat2[:, 0..128)
-  {
-    const float* gc = u->g_cat2;
-    float* gb = u->g_b3;
-    e = each(P3 * 128, s, [=] __device__(int64_t i) {
-      const int ch = (int)(i % 128);
-      const int64_t q = i / 128;
-      const int x = (int)(q % w4), y = (int)((q / w4) % h4), n = (int)(q / ((int64_t)w4 * h4));
-      float acc = 0.f;
-      for (int dy = 0; dy < 2; ++dy)
-        for (int dx = 0; dx < 2; ++dx) acc += gc[(((int64_t)n * h2 + 2 * y + dy) * w2 + 2 * x + dx) * 192 + ch];
-      gb[i] += acc;
-    });
-    if (e) return e;
-  }
+  if ((e = up_bwd(u->g_cat2, 192, u->g_b3, 128, 128, N, h4, w4, s))) return e;  // up: g_b3 += children
   // c3b: y = b3, x = a3
   if ((e = relu_bwd(u->g_b3, 128, 0, u->b3, 128, 0, 128, P3, dz, s))) return e;
   if ((e = wgrad(u, C3B, dz, 128, u->a3, 128, 0, N, h4, w4, s))) return e;
@@ -527,17 +580,7 @@ cudaError_t backward(sg_unet* u, const Crops& tgt, const float* out, int64_t out
   if ((e = wgrad(u, C3A, dz, 128, u->p2, 64, 0, N, h4, w4, s))) return e;
   if ((e = dgrad(u, C3A, dz, u->g_p2, 64, 0, N, h4, w4, s))) return e;
   // pool: g_cat2[:, 128..192) += g_p2 / 4 (e2's gradient lives at its place in cat2)
-  {
-    const float* gp = u->g_p2;
-    float* gc = u->g_cat2;
-    e = each(P2 * 64, s, [=] __device__(int64_t i) {
-      const int ch = (int)(i % 64);
-      const int64_t q = i / 64;
-      const int x = (int)(q % w2), y = (int)((q / w2) % h2), n = (int)(q / ((int64_t)w2 * h2));
-      gc[q * 192 + 128 + ch] += 0.25f * gp[(((int64_t)n * h4 + y / 2) * w4 + x / 2) * 64 + ch];
-    });
-    if (e) return e;
-  }
+  if ((e = pool_bwd(u->g_p2, 64, u->g_cat2, 192, 128, 64, N, h4, w4, s))) return e;
   // c2b: y = e2 = cat2[:, 128..), x = a2
   if ((e = relu_bwd(u->g_cat2, 192, 128, u->cat2, 192, 128, 64, P2, dz, s))) return e;
   if ((e = wgrad(u, C2B, dz, 64, u->a2, 64, 0, N, h2, w2, s))) return e;
@@ -546,17 +589,7 @@ cudaError_t backward(sg_unet* u, const Crops& tgt, const float* out, int64_t out
   if ((e = relu_bwd(u->g_a2, 64, 0, u->a2, 64, 0, 64, P2, dz, s))) return e;
   if ((e = wgrad(u, C2A, dz, 64, u->p1, 32, 0, N, h2, w2, s))) return e;
   if ((e = dgrad(u, C2A, dz, u->g_p1, 32, 0, N, h2, w2, s))) return e;
-  {
-    const float* gp = u->g_p1;
-    float* gc = u->g_cat1;
-    e = each(P1 * 32, s, [=] __device__(int64_t i) {
-      const int ch = (int)(i % 32);
-      const int64_t q = i / 32;
-      const int x = (int)(q % w), y = (int)((q / w) % h), n = (int)(q / ((int64_t)w * h));
-      gc[q * 96 + 64 + ch] += 0.25f * gp[(((int64_t)n * h2 + y / 2) * w2 + x / 2) * 32 + ch];
-    });
-    if (e) return e;
-  }
+  if ((e = pool_bwd(u->g_p1, 32, u->g_cat1, 96, 64, 32, N, h2, w2, s))) return e;  // pool: e1's gradient
   // c1b: y = e1 = cat1[:, 64..), x = a1
   if ((e = relu_bwd(u->g_cat1, 96, 64, u->cat1, 96, 64, 32, P1, dz, s))) return e;
   if ((e = wgrad(u, C1B, dz, 32, u->a1, 32, 0, N, h, w, s))) return e;
