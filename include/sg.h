@@ -326,9 +326,10 @@ sg_status sg_unet_forward(sg_unet* net, const float* const* in, int64_t in_pitch
 sg_status sg_unet_backward(sg_unet* net, const float* const* target, int64_t target_pitch, const float* const* out,
                            int64_t out_pitch, float* loss, void* stream);
 
-/* Selects the tensor-core path of the convolutions: 1 (default) = tcgen05
- * with tensor-memory accumulators, 0 = mma.sync (the portable path; same
- * arithmetic: BF16 products, FP32 sums). */
+/* Selects the tensor-core path of the convolutions (all: BF16 products, FP32
+ * sums): 2 (default) = tcgen05 with TMEM accumulators, each CTA computing two
+ * output rows from input row segments loaded once per 32 channels (halo
+ * reuse); 1 = tcgen05 implicit GEMM gathering every tap; 0 = mma.sync. */
 sg_status sg_unet_set_tensor_path(sg_unet* net, int tcgen05);
 
 /* Reports (and clears) a timed-out bounded wait in a tcgen05 convolution since

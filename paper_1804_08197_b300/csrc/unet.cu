@@ -204,7 +204,7 @@ cudaError_t pool_bwd(const float* src, int sstride, float* dst, int dstride, int
 
 struct sg_unet {
   int max_n = 0, max_h = 0, max_w = 0;
-  int tc = 1;                 // convolutions on tcgen05 (1) or mma.sync (0)
+  int tc = 2;                 // convolutions: 2 tcgen05 halo reuse, 1 tcgen05 implicit GEMM, 0 mma.sync
   uint32_t* d_err = nullptr;  // set by a tcgen05 kernel whose bounded wait gave up
   int n = 0, h = 0, w = 0;  // shape of the last forward
   int64_t nparam = 0;
@@ -272,7 +272,34 @@ cudaError_t conv_tc(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t conv(const ConvArgs& a, cudaStream_t s, uint32_t* tc_err = nullptr) {
+#ifndef SG_HALO_ROWS
+#define SG_HALO_ROWS 2
+#endif
+
+template <int BN, int R>
+cudaError_t conv_halo(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
+  const int stages = a.Cin / 32 > 1 ? 2 : 1;
+  const int smem = stages * halo_stage_bytes<BN, R>();
+  static int configured = 0;  // largest dynamic shared memory set so far for this instance
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_halo<BN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         2 * halo_stage_bytes<BN, R>());
+    if (e != cudaSuccess) return e;
+    configured = 2 * halo_stage_bytes<BN, R>();
+  }
+  dim3 grid((a.W + 127) / 128, a.N * ((a.H + R - 1) / R), a.Cout / BN);
+  k_conv3x3_halo<BN, R><<<grid, 128, smem, s>>>(a, stages, err);
+  return cudaGetLastError();
+}
+
+// mode: 0 mma.sync, 1 tcgen05 implicit GEMM, 2 tcgen05 with halo reuse
+// (Cin a multiple of 32; otherwise the implicit GEMM)
+cudaError_t conv(const ConvArgs& a, cudaStream_t s, uint32_t* tc_err = nullptr, int mode = 2) {
+  if (tc_err && mode == 2 && a.Cin % 32 == 0) {
+    if (a.Cout % 64 == 0) return conv_halo<64, SG_HALO_ROWS>(a, tc_err, s);
+    if (a.Cout % 32 == 0) return conv_halo<32, SG_HALO_ROWS>(a, tc_err, s);
+    return conv_halo<16, SG_HALO_ROWS>(a, tc_err, s);
+  }
   if (tc_err) {
     if (a.Cout % 128 == 0) return conv_tc<128>(a, tc_err, s);
     if (a.Cout % 64 == 0) return conv_tc<64>(a, tc_err, s);
@@ -385,7 +412,7 @@ cudaError_t dgrad(sg_unet* u, int L, const bf16* dz, float* dx, int dx_stride, i
   a.f32_stride = dx_stride;
   a.f32_off = dx_off;
   a.f32_accumulate = 1;
-  return conv(a, s, u->tc ? u->d_err : nullptr);
+  return conv(a, s, u->tc ? u->d_err : nullptr, u->tc);
 }
 
 // He-normal initial weights (counter-based Box-Muller), zero biases, zero head
@@ -437,32 +464,32 @@ cudaError_t forward(sg_unet* u, const Crops& c, int N, int h, int w, float* out,
   if (e) return e;
   ConvArgs a;
   a = conv_args(u, C1A, u->in16, 16, 0, N, h, w); a.out = u->a1; a.out_stride = 32; a.out_off = 0;
-  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
   // e1 lives in cat1 at channel offset 64 (after the 64 upsampled channels)
   a = conv_args(u, C1B, u->a1, 32, 0, N, h, w); a.out = u->cat1; a.out_stride = 96; a.out_off = 64;
-  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
   if ((e = pool_fwd(u->cat1, 96, 64, u->p1, 32, 0, 32, N, h, w, s))) return e;  // pool e1 -> p1
   a = conv_args(u, C2A, u->p1, 32, 0, N, h2, w2); a.out = u->a2; a.out_stride = 64; a.out_off = 0;
-  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
   a = conv_args(u, C2B, u->a2, 64, 0, N, h2, w2); a.out = u->cat2; a.out_stride = 192; a.out_off = 128;
-  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
   if ((e = pool_fwd(u->cat2, 192, 128, u->p2, 64, 0, 64, N, h2, w2, s))) return e;  // pool e2 -> p2
   a = conv_args(u, C3A, u->p2, 64, 0, N, h4, w4); a.out = u->a3; a.out_stride = 128; a.out_off = 0;
-  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
   a = conv_args(u, C3B, u->a3, 128, 0, N, h4, w4); a.out = u->b3; a.out_stride = 128; a.out_off = 0;
-  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
   if ((e = up_fwd(u->b3, 128, u->cat2, 192, 0, 128, N, h4, w4, s))) return e;  // up b3 -> cat2[:, 0..128)
   a = conv_args(u, D2A, u->cat2, 192, 0, N, h2, w2); a.out = u->a4; a.out_stride = 64; a.out_off = 0;
-  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
   a = conv_args(u, D2B, u->a4, 64, 0, N, h2, w2); a.out = u->d2; a.out_stride = 64; a.out_off = 0;
-  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
   if ((e = up_fwd(u->d2, 64, u->cat1, 96, 0, 64, N, h2, w2, s))) return e;  // up d2 -> cat1[:, 0..64)
   a = conv_args(u, D1A, u->cat1, 96, 0, N, h, w); a.out = u->a5; a.out_stride = 32; a.out_off = 0;
-  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
   a = conv_args(u, D1B, u->a5, 32, 0, N, h, w); a.out = u->d1; a.out_stride = 32; a.out_off = 0;
-  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
   a = conv_args(u, HEAD, u->d1, 32, 0, N, h, w); a.out_f32 = u->head; a.f32_stride = 16; a.f32_off = 0;
-  if ((e = conv(a, s, u->tc ? u->d_err : nullptr))) return e;
+  if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
   // out = bilinear 2x (half-pixel centres, clamp) of the input + pixel shuffle of the head
   {
     const float* head = u->head;
@@ -684,8 +711,8 @@ sg_status sg_unet_create(int max_batch, int max_h, int max_w, uint64_t seed, sg_
 }
 
 sg_status sg_unet_set_tensor_path(sg_unet* u, int tcgen05) {
-  if (!u || (tcgen05 != 0 && tcgen05 != 1)) {
-    set_error("sg_unet_set_tensor_path: NULL or mode not 0/1");
+  if (!u || tcgen05 < 0 || tcgen05 > 2) {
+    set_error("sg_unet_set_tensor_path: NULL or mode not 0/1/2");
     return SG_ERR_INVALID_ARG;
   }
   u->tc = tcgen05;

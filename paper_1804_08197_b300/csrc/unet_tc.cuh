@@ -242,3 +242,202 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(ConvArgs a, uint32_t* err) {
 
 }  // namespace nn
 }  // namespace sg
+
+namespace sg {
+namespace nn {
+
+// Halo-reuse variant for Cin a multiple of 32 and BN <= 64: a CTA computes R
+// consecutive output rows x 128 pixels of one image row band and loads, per
+// 32-channel chunk, the R + 2 input row segments it needs (130 pixels with
+// the left/right halo, zero outside the image) once. Each segment is stored
+// K-major with a 16-byte row pitch ([4 k-chunks][136 pixels][8 channels]),
+// so tap (dy, dx) of output row r is a descriptor starting dx + 1 pixel rows
+// into segment r + dy + 1: leading byte offset 2176 (next 8 channels), stride
+// byte offset 128 (next 8 pixels). Weights of the chunk for all 9 taps sit in
+// the canonical layout ([tap][BN/8][4][8 rows][16 B]). R accumulators of BN
+// columns each live side by side in TMEM.
+constexpr int kHaloPx = 136;                 // 130 used + padding
+constexpr int kHaloSeg = 4 * kHaloPx * 16;   // one row segment, 32 channels: 8704 B
+
+template <int BN, int R>
+__host__ __device__ constexpr int halo_stage_bytes() {
+  return (R + 2) * kHaloSeg + 9 * BN * 64;
+}
+
+template <int BN, int R>
+__global__ void __launch_bounds__(128) k_conv3x3_halo(ConvArgs a, int stages, uint32_t* err) {
+  constexpr int kCols = R * BN < 32 ? 32 : (R * BN <= 64 ? 64 : (R * BN <= 128 ? 128 : 256));
+  constexpr int kA = (R + 2) * kHaloSeg, kStage = halo_stage_bytes<BN, R>();
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint64_t bars[2];
+  __shared__ uint32_t tmem_base_s;
+  __shared__ volatile int abort_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int x0 = blockIdx.x * 128;
+  const int bands = (a.H + R - 1) / R;
+  const int n = blockIdx.y / bands, y0 = (blockIdx.y % bands) * R;
+  const int n0 = blockIdx.z * BN;
+  const int K = 9 * a.Cin, nch = a.Cin / 32;
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    abort_s = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base_s)),
+                 "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_base_s;
+
+  auto gather = [&](int ch, int st) {
+    const uint32_t base = smem_u32(smem + st * kStage);
+    // input segments: (R + 2) rows x 130 pixels x 4 chunks of 8 channels
+    constexpr int kItemsA = (R + 2) * 130 * 4;
+    for (int it = tid; it < kItemsA; it += 128) {
+      const int seg = it / 520, rem = it - seg * 520, px = rem >> 2, kc = rem & 3;
+      const int yy = y0 + seg - 1, xx = x0 + px - 1;
+      const void* src = a.in;
+      int bytes = 0;
+      if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) {
+        src = a.in + ((((int64_t)n * a.H + yy) * a.W + xx) * a.in_stride + a.in_off + ch * 32 + kc * 8);
+        bytes = 16;
+      }
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(base + seg * kHaloSeg + kc * (kHaloPx * 16) +
+                                                                               px * 16),
+                   "l"(src), "r"(bytes));
+    }
+    // weights of this chunk, all taps
+    constexpr int kItemsB = 9 * BN * 4;
+    for (int it = tid; it < kItemsB; it += 128) {
+      const int tap = it / (BN * 4), rem = it - tap * (BN * 4), r = rem >> 2, kc = rem & 3;
+      const bf16* src = a.wt + (size_t)(n0 + r) * K + tap * a.Cin + ch * 32 + kc * 8;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + kA + tap * (BN * 64) + (r >> 3) * 512 +
+                                                                          kc * 128 + (r & 7) * 16),
+                   "l"(src));
+    }
+  };
+
+  constexpr uint32_t idesc = tc_idesc(128, BN);
+  gather(0, 0);
+  cp_async_commit();
+  for (int ch = 0; ch < nch; ++ch) {
+    const int st = stages > 1 ? (ch & 1) : 0;
+    cp_async_wait<0>();
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    const bool aborted = abort_s != 0;
+    if (tid == 0 && !aborted) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t base = smem_u32(smem + st * kStage);
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+            const uint64_t da =
+                tc_smem_desc(base + (r + dy + 1) * kHaloSeg + (dx + 1) * 16 + 2 * kk * (kHaloPx * 16), kHaloPx * 16, 128);
+            const uint64_t db = tc_smem_desc(base + kA + tap * (BN * 64) + 2 * kk * 128, 128, 512);
+            const uint32_t accum = (ch > 0 || tap > 0 || kk > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "setp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + r * BN),
+                "l"(da), "l"(db), "r"(idesc), "r"(accum));
+          }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       smem_u32(&bars[st]))
+                   : "memory");
+    }
+    if (ch + 1 < nch && !aborted) {
+      // the next chunk's buffer: with two stages it was used by chunk ch - 1,
+      // with one stage by chunk ch (just issued); wait for those MMAs first
+      const int sn = stages > 1 ? ((ch + 1) & 1) : 0;
+      const int prev = stages > 1 ? ch - 1 : ch;
+      bool ready = true;
+      if (prev >= 0) {
+        const int use = stages > 1 ? prev >> 1 : prev;
+        ready = mbar_wait(smem_u32(&bars[sn]), use & 1);
+        if (!ready) abort_s = 1;
+      }
+      if (ready) gather(ch + 1, sn);
+    }
+    cp_async_commit();
+  }
+  __syncthreads();
+  if (abort_s == 0) {
+    const int last = nch - 1;
+    const int st = stages > 1 ? (last & 1) : 0, use = stages > 1 ? last >> 1 : last;
+    if (!mbar_wait(smem_u32(&bars[st]), use & 1)) abort_s = 1;
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  if (abort_s) {
+    if (tid == 0) atomicExch(err, 1u);
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const int x = x0 + warp * 32 + lane;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int y = y0 + r;
+#pragma unroll
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t v32[16];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + r * BN + c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(v32[0]), "=r"(v32[1]), "=r"(v32[2]), "=r"(v32[3]), "=r"(v32[4]), "=r"(v32[5]), "=r"(v32[6]),
+              "=r"(v32[7]), "=r"(v32[8]), "=r"(v32[9]), "=r"(v32[10]), "=r"(v32[11]), "=r"(v32[12]), "=r"(v32[13]),
+              "=r"(v32[14]), "=r"(v32[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (x < a.W && y < a.H) {
+          const int64_t pr = ((int64_t)n * a.H + y) * a.W + x;
+          float v[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            v[i] = __uint_as_float(v32[i]);
+            if (a.bias) v[i] += a.bias[n0 + c0 + i];
+            if (a.relu) v[i] = fmaxf(v[i], 0.f);
+          }
+          if (a.out) {
+            uint32_t packed[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+              packed[i] = *reinterpret_cast<uint32_t*>(&h2);
+            }
+            uint4* o = reinterpret_cast<uint4*>(a.out + pr * a.out_stride + a.out_off + n0 + c0);
+            o[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            o[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+          }
+          if (a.out_f32) {
+            float4* o = reinterpret_cast<float4*>(a.out_f32 + pr * a.f32_stride + a.f32_off + n0 + c0);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              float4 q = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+              if (a.f32_accumulate) {
+                const float4 o0 = o[i];
+                q.x += o0.x; q.y += o0.y; q.z += o0.z; q.w += o0.w;
+              }
+              o[i] = q;
+            }
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols));
+}
+
+}  // namespace nn
+}  // namespace sg

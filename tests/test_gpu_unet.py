@@ -78,30 +78,32 @@ def test_forward_and_gradients_match_the_oracle_at_bf16_tolerance():
 
 
 def test_tcgen05_and_mma_sync_paths_agree():
-    """The tcgen05 (TMEM) and mma.sync convolutions compute the same BF16
-    products with FP32 sums: outputs and gradients agree to summation order."""
+    """The tcgen05 (TMEM; implicit GEMM and halo reuse) and mma.sync
+    convolutions compute the same BF16 products with FP32 sums: outputs and
+    gradients agree to summation order."""
     from paper_1804_08197_b300 import sg
-    net = sg.sg_unet_create(2, 24, 40, seed=11)
+    net = sg.sg_unet_create(2, 24, 140, seed=11)  # 140 columns: two 128-pixel segments per row
     try:
         p = _random_params(12, sg.sg_unet_param_count(net))
         sg.sg_unet_set_params(net, p)
         rng = np.random.default_rng(13)
-        x = rng.uniform(0, 1, (2, 24, 40, 4))
-        t = rng.uniform(0, 1, (2, 48, 80, 4))
+        x = rng.uniform(0, 1, (2, 24, 140, 4))
+        t = rng.uniform(0, 1, (2, 48, 280, 4))
         res = {}
-        for path in (0, 1):
+        for path in (0, 1, 2):
             sg.sg_unet_set_tensor_path(net, path)
             out, loss = _run(net, x, t)
             sg.sg_unet_check(net)
             res[path] = (out, loss, sg.sg_unet_get_params(net, which=1).astype(np.float64))
         base = ou.bilinear2x(x)
-        r0, r1 = res[0][0] - base, res[1][0] - base
-        assert np.linalg.norm(r1 - r0) <= 1e-3 * np.linalg.norm(r0)
-        assert res[1][1] == pytest.approx(res[0][1], rel=1e-4)
-        for ws, bs in ou.layer_slices():
-            for sl in (ws, bs):
-                g0, g1 = res[0][2][sl], res[1][2][sl]
-                assert np.linalg.norm(g1 - g0) <= 2e-2 * np.linalg.norm(g0) + 1e-12
+        for path in (1, 2):
+            r0, r1 = res[0][0] - base, res[path][0] - base
+            assert np.linalg.norm(r1 - r0) <= 1e-3 * np.linalg.norm(r0), path
+            assert res[path][1] == pytest.approx(res[0][1], rel=1e-4)
+            for ws, bs in ou.layer_slices():
+                for sl in (ws, bs):
+                    g0, g1 = res[0][2][sl], res[path][2][sl]
+                    assert np.linalg.norm(g1 - g0) <= 2e-2 * np.linalg.norm(g0) + 1e-12, path
     finally:
         sg.sg_unet_destroy(net)
 
