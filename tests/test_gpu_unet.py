@@ -98,7 +98,8 @@ def test_tcgen05_and_mma_sync_paths_agree():
         base = ou.bilinear2x(x)
         for path in (1, 2):
             r0, r1 = res[0][0] - base, res[path][0] - base
-            assert np.linalg.norm(r1 - r0) <= 1e-3 * np.linalg.norm(r0), path
+            # shared BF16 rounding points, different FP32 summation order
+            assert np.linalg.norm(r1 - r0) <= 5e-3 * np.linalg.norm(r0), path
             assert res[path][1] == pytest.approx(res[0][1], rel=1e-4)
             for ws, bs in ou.layer_slices():
                 for sl in (ws, bs):
