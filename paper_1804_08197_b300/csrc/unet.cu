@@ -273,7 +273,7 @@ cudaError_t conv_tc(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
 }
 
 #ifndef SG_HALO_ROWS
-#define SG_HALO_ROWS 2
+#define SG_HALO_ROWS 4
 #endif
 
 template <int BN, int R>
