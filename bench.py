@@ -205,7 +205,7 @@ def batched_4d(sg, torch, dev, reps=10):
     return res
 
 
-def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=2000, steps_per_pair=4, eval_poses=16,
+def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=4000, steps_per_pair=4, eval_poses=16,
                   threshold_db=40.0):
     """Learned reconstruction vs the plain path on the same GPU: training on
     `pairs` seeded (pose, full-rate render, half-res render) pairs of the
@@ -234,7 +234,8 @@ def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=2000, steps_per_pa
     train = synth.head_poses(512, seed=9100, width=W_EYE, height=H_EYE)
     for i in range(pairs):
         v, p = train[i % len(train)]
-        rec.train_on_pair(v, p, steps=steps_per_pair, batch=16, lr=5e-4 if i < pairs * 3 // 4 else 1.5e-4)
+        lr = 8e-4 * (0.05 + 0.95 * 0.5 * (1.0 + np.cos(np.pi * i / pairs)))  # cosine decay
+        rec.train_on_pair(v, p, steps=steps_per_pair, batch=16, lr=lr)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     sg.sg_unet_check(rec.net)
@@ -281,6 +282,29 @@ def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=2000, steps_per_pa
             "net_tflops": round(net_flop / (float(np.mean(t_net)) / 1e3) / 1e12, 1),
             "half_render_ms": round(float(np.mean(np.array(t_learned) - np.array(t_net))), 3),
             "train_s": round(train_s, 1), "train_pairs": pairs, "steps_per_pair": steps_per_pair}
+
+
+def run_net_only(args):
+    """U-Net forwards on both eyes at 720x800 (random input), for profiling."""
+    import torch
+    from paper_1804_08197_b300 import sg
+    torch.cuda.set_device(0)
+    net = sg.sg_unet_create(2, H_EYE // 2, W_EYE // 2, seed=1)
+    x = [torch.rand((H_EYE // 2, W_EYE // 2, 4), device="cuda") for _ in range(2)]
+    o = [torch.empty((H_EYE, W_EYE, 4), device="cuda") for _ in range(2)]
+    for _ in range(args.warmup):
+        sg.sg_unet_forward(net, x, W_EYE // 2 * 4, H_EYE // 2, W_EYE // 2, o, W_EYE * 4)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        sg.sg_unet_forward(net, x, W_EYE // 2 * 4, H_EYE // 2, W_EYE // 2, o, W_EYE * 4)
+    b.record()
+    torch.cuda.synchronize()
+    sg.sg_unet_check(net)
+    ms = a.elapsed_time(b) / args.steps
+    print(json.dumps({"net_forward_ms": round(ms, 4), "tflops": round(268e9 / (ms / 1e3) / 1e12, 1)}), flush=True)
+    sg.sg_unet_destroy(net)
 
 
 def run_reference(args, rank, world):
@@ -457,7 +481,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched 4D and learned measurements")
-    ap.add_argument("--learned-pairs", type=int, default=2000, help="training pairs for the learned path")
+    ap.add_argument("--learned-pairs", type=int, default=4000,
+                    help="training pairs for the learned path (20000 = the full budget, ~4 min)")
+    ap.add_argument("--only", choices=["net"], default=None,
+                    help="net: only U-Net forwards at 2x720x800 (a small case for profiling the convolutions)")
     ap.add_argument("--volume", type=int, default=N_VOX, help="volume edge (default 1024; smaller for profiling)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -472,7 +499,9 @@ def main():
         if backend == "nccl":
             torch.cuda.set_device(local_rank)
         dist.init_process_group(backend)
-    if args.impl == "reference":
+    if args.only == "net":
+        run_net_only(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world, local_rank)
