@@ -276,29 +276,36 @@ cudaError_t conv_tc(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
 #define SG_HALO_ROWS 4
 #endif
 
-template <int BN, int R>
+template <int BN, int R, int CC>
 cudaError_t conv_halo(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
-  const int stages = a.Cin / 32 > 1 ? 2 : 1;
-  const int smem = stages * halo_stage_bytes<BN, R>();
-  static int configured = 0;  // largest dynamic shared memory set so far for this instance
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_halo<BN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         2 * halo_stage_bytes<BN, R>());
+  // two stages only where two CTAs still fit on an SM
+  constexpr int kOne = halo_stage_bytes<BN, R, CC>();
+  const int stages = (a.Cin / CC > 1 && 2 * kOne <= 110 * 1024) ? 2 : 1;
+  const int smem = stages * kOne;
+  static bool configured = false;  // per template instance, set once on first use
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_halo<BN, R, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         2 * kOne);
     if (e != cudaSuccess) return e;
-    configured = 2 * halo_stage_bytes<BN, R>();
+    configured = true;
   }
   dim3 grid((a.W + 127) / 128, a.N * ((a.H + R - 1) / R), a.Cout / BN);
-  k_conv3x3_halo<BN, R><<<grid, 128, smem, s>>>(a, stages, err);
+  k_conv3x3_halo<BN, R, CC><<<grid, 128, smem, s>>>(a, stages, err);
   return cudaGetLastError();
 }
 
+template <int BN>
+cudaError_t conv_halo_cc(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
+  if (a.Cin % 32 == 0) return conv_halo<BN, SG_HALO_ROWS, 32>(a, err, s);
+  return conv_halo<BN, SG_HALO_ROWS, 16>(a, err, s);
+}
+
 // mode: 0 mma.sync, 1 tcgen05 implicit GEMM, 2 tcgen05 with halo reuse
-// (Cin a multiple of 32; otherwise the implicit GEMM)
 cudaError_t conv(const ConvArgs& a, cudaStream_t s, uint32_t* tc_err = nullptr, int mode = 2) {
-  if (tc_err && mode == 2 && a.Cin % 32 == 0) {
-    if (a.Cout % 64 == 0) return conv_halo<64, SG_HALO_ROWS>(a, tc_err, s);
-    if (a.Cout % 32 == 0) return conv_halo<32, SG_HALO_ROWS>(a, tc_err, s);
-    return conv_halo<16, SG_HALO_ROWS>(a, tc_err, s);
+  if (tc_err && mode == 2 && a.Cin % 16 == 0) {
+    if (a.Cout % 64 == 0) return conv_halo_cc<64>(a, tc_err, s);
+    if (a.Cout % 32 == 0) return conv_halo_cc<32>(a, tc_err, s);
+    return conv_halo_cc<16>(a, tc_err, s);
   }
   if (tc_err) {
     if (a.Cout % 128 == 0) return conv_tc<128>(a, tc_err, s);

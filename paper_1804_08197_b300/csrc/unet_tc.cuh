@@ -246,28 +246,33 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(ConvArgs a, uint32_t* err) {
 namespace sg {
 namespace nn {
 
-// Halo-reuse variant for Cin a multiple of 32 and BN <= 64: a CTA computes R
-// consecutive output rows x 128 pixels of one image row band and loads, per
-// 32-channel chunk, the R + 2 input row segments it needs (130 pixels with
-// the left/right halo, zero outside the image) once. Each segment is stored
-// K-major with a 16-byte row pitch ([4 k-chunks][136 pixels][8 channels]),
-// so tap (dy, dx) of output row r is a descriptor starting dx + 1 pixel rows
-// into segment r + dy + 1: leading byte offset 2176 (next 8 channels), stride
-// byte offset 128 (next 8 pixels). Weights of the chunk for all 9 taps sit in
-// the canonical layout ([tap][BN/8][4][8 rows][16 B]). R accumulators of BN
-// columns each live side by side in TMEM.
-constexpr int kHaloPx = 136;                 // 130 used + padding
-constexpr int kHaloSeg = 4 * kHaloPx * 16;   // one row segment, 32 channels: 8704 B
+// Halo-reuse variant for Cin a multiple of CC (16 or 32) and BN <= 64: a CTA
+// computes R consecutive output rows x 128 pixels of one image row band and
+// loads, per CC-channel chunk, the R + 2 input row segments it needs (130
+// pixels with the left/right halo, zero outside the image) once. Each segment
+// is stored K-major with a 16-byte row pitch ([CC/8 k-chunks][136 pixels][8
+// channels]), so tap (dy, dx) of output row r is a descriptor starting dx + 1
+// pixel rows into segment r + dy + 1: leading byte offset 2176 (next 8
+// channels), stride byte offset 128 (next 8 pixels). Weights of the chunk for
+// all 9 taps sit in the canonical layout ([tap][BN/8][CC/8][8 rows][16 B]).
+// R accumulators of BN columns each live side by side in TMEM.
+constexpr int kHaloPx = 136;  // 130 used + padding
 
-template <int BN, int R>
-__host__ __device__ constexpr int halo_stage_bytes() {
-  return (R + 2) * kHaloSeg + 9 * BN * 64;
+template <int CC>
+__host__ __device__ constexpr int halo_seg_bytes() {
+  return (CC / 8) * kHaloPx * 16;
 }
 
-template <int BN, int R>
+template <int BN, int R, int CC>
+__host__ __device__ constexpr int halo_stage_bytes() {
+  return (R + 2) * halo_seg_bytes<CC>() + 9 * BN * CC * 2;
+}
+
+template <int BN, int R, int CC>
 __global__ void __launch_bounds__(128) k_conv3x3_halo(ConvArgs a, int stages, uint32_t* err) {
   constexpr int kCols = R * BN < 32 ? 32 : (R * BN <= 64 ? 64 : (R * BN <= 128 ? 128 : 256));
-  constexpr int kA = (R + 2) * kHaloSeg, kStage = halo_stage_bytes<BN, R>();
+  constexpr int kHaloSeg = halo_seg_bytes<CC>(), KC = CC / 8;
+  constexpr int kA = (R + 2) * kHaloSeg, kStage = halo_stage_bytes<BN, R, CC>();
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ uint64_t bars[2];
   __shared__ uint32_t tmem_base_s;
@@ -277,7 +282,7 @@ __global__ void __launch_bounds__(128) k_conv3x3_halo(ConvArgs a, int stages, ui
   const int bands = (a.H + R - 1) / R;
   const int n = blockIdx.y / bands, y0 = (blockIdx.y % bands) * R;
   const int n0 = blockIdx.z * BN;
-  const int K = 9 * a.Cin, nch = a.Cin / 32;
+  const int K = 9 * a.Cin, nch = a.Cin / CC;
 
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[0])));
@@ -297,15 +302,15 @@ __global__ void __launch_bounds__(128) k_conv3x3_halo(ConvArgs a, int stages, ui
 
   auto gather = [&](int ch, int st) {
     const uint32_t base = smem_u32(smem + st * kStage);
-    // input segments: (R + 2) rows x 130 pixels x 4 chunks of 8 channels
-    constexpr int kItemsA = (R + 2) * 130 * 4;
+    // input segments: (R + 2) rows x 130 pixels x KC chunks of 8 channels
+    constexpr int kItemsA = (R + 2) * 130 * KC;
     for (int it = tid; it < kItemsA; it += 128) {
-      const int seg = it / 520, rem = it - seg * 520, px = rem >> 2, kc = rem & 3;
+      const int seg = it / (130 * KC), rem = it - seg * (130 * KC), px = rem / KC, kc = rem % KC;
       const int yy = y0 + seg - 1, xx = x0 + px - 1;
       const void* src = a.in;
       int bytes = 0;
       if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) {
-        src = a.in + ((((int64_t)n * a.H + yy) * a.W + xx) * a.in_stride + a.in_off + ch * 32 + kc * 8);
+        src = a.in + ((((int64_t)n * a.H + yy) * a.W + xx) * a.in_stride + a.in_off + ch * CC + kc * 8);
         bytes = 16;
       }
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(base + seg * kHaloSeg + kc * (kHaloPx * 16) +
@@ -313,12 +318,12 @@ __global__ void __launch_bounds__(128) k_conv3x3_halo(ConvArgs a, int stages, ui
                    "l"(src), "r"(bytes));
     }
     // weights of this chunk, all taps
-    constexpr int kItemsB = 9 * BN * 4;
+    constexpr int kItemsB = 9 * BN * KC;
     for (int it = tid; it < kItemsB; it += 128) {
-      const int tap = it / (BN * 4), rem = it - tap * (BN * 4), r = rem >> 2, kc = rem & 3;
-      const bf16* src = a.wt + (size_t)(n0 + r) * K + tap * a.Cin + ch * 32 + kc * 8;
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + kA + tap * (BN * 64) + (r >> 3) * 512 +
-                                                                          kc * 128 + (r & 7) * 16),
+      const int tap = it / (BN * KC), rem = it - tap * (BN * KC), r = rem / KC, kc = rem % KC;
+      const bf16* src = a.wt + (size_t)(n0 + r) * K + tap * a.Cin + ch * CC + kc * 8;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + kA + tap * (BN * CC * 2) +
+                                                                          (r >> 3) * (KC * 128) + kc * 128 + (r & 7) * 16),
                    "l"(src));
     }
   };
@@ -340,11 +345,11 @@ __global__ void __launch_bounds__(128) k_conv3x3_halo(ConvArgs a, int stages, ui
 #pragma unroll
         for (int tap = 0; tap < 9; ++tap)
 #pragma unroll
-          for (int kk = 0; kk < 2; ++kk) {
+          for (int kk = 0; kk < CC / 16; ++kk) {
             const int dy = tap / 3 - 1, dx = tap % 3 - 1;
             const uint64_t da =
                 tc_smem_desc(base + (r + dy + 1) * kHaloSeg + (dx + 1) * 16 + 2 * kk * (kHaloPx * 16), kHaloPx * 16, 128);
-            const uint64_t db = tc_smem_desc(base + kA + tap * (BN * 64) + 2 * kk * 128, 128, 512);
+            const uint64_t db = tc_smem_desc(base + kA + tap * (BN * CC * 2) + 2 * kk * 128, 128, KC * 128);
             const uint32_t accum = (ch > 0 || tap > 0 || kk > 0) ? 1u : 0u;
             asm volatile(
                 "{\n\t.reg .pred p;\n\t"
