@@ -115,6 +115,24 @@ def measured_peak_hbm():
         return 6400.0, "fallback"
 
 
+def profiled_traffic(alg_bytes):
+    """DRAM bytes per render launch from the committed ncu summary, scaled to
+    this run's algorithmic bytes; None if the kernel changed since."""
+    import hashlib
+    try:
+        rec = {}
+        for line in open(os.path.join(ROOT, "profiles", "render_traffic.txt")):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
+        sha = hashlib.sha256(open(os.path.join(ROOT, "paper_1804_08197_b300", "csrc", "render.cu"), "rb").read())
+        if sha.hexdigest()[:16] != rec["render_cu_sha256_16"]:
+            return None
+        return int(float(rec["traffic_bytes_per_launch"]) * alg_bytes / float(rec["algorithmic_bytes_per_launch"]))
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def cpu_baseline(vol, tf_table, poses, model, frac_target_s=15.0):
     """The FP64 oracle, as it stands, on a bounded pixel sample of pose 0."""
     import oracle
@@ -455,7 +473,7 @@ def run_ours(args, rank, world, local_rank):
                 "render_ms_mean": round(sum(render_ms) / len(render_ms), 4),
                 "gpu_launches": 2 * args.steps,
                 "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                             "frac": round(achieved / peak, 5), "traffic": None,
+                             "frac": round(achieved / peak, 5), "traffic": profiled_traffic(sum(alg) / len(alg)),
                              "kernel": "k_render", "peak_source": peak_kind,
                              "algorithmic_bytes_per_launch": int(sum(alg) / len(alg))},
                 "clocks": clk,
