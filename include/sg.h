@@ -104,9 +104,25 @@ sg_status sg_upload_volume_device(sg_volume* vol, int t, int c, const void* dev_
  * its apron, x fastest, stored back to back in host. Bricks not yet cached
  * get a pool slot (evicting the least recently used unpinned brick groups
  * when the pool is full). The brick's value ranges are recomputed on the GPU.
- * Errors: INVALID_ARG, OOM (pool full of bricks in use this frame), CUDA. */
+ * Errors: INVALID_ARG, OOM (pool full of bricks in use this frame: the
+ * bricks before the one that found no slot are cached and consistent),
+ * CUDA. */
 sg_status sg_upload_bricks(sg_volume* vol, int t, int c, int level, int n, const int32_t* brick_xyz,
                            const void* host, void* stream);
+
+/* Streaming ingest by node id: n bricks of (t, c), brick i the node nodes[i]
+ * (the ids sg_read_selection lists as requests; levels may be mixed), copied
+ * from host[i]: (B+2)^3 voxels of dtype with the apron, x fastest (pinned
+ * host memory makes the copies asynchronous; all are complete on return).
+ * Bricks are placed in list order, so a coarse-first list keeps the coarse
+ * ones when the cache runs short: placement stops, without an error, at the
+ * first brick that finds the cache full of bricks used by the current frame,
+ * and *n_done receives how many bricks (a prefix of the list) are cached.
+ * The page table, value ranges and transparency flags of every placed brick
+ * are updated before return. Errors: INVALID_ARG (node id out of range, NULL
+ * pointer), OOM (bookkeeping memory), CUDA. */
+sg_status sg_upload_brick_list(sg_volume* vol, int t, int c, int n, const int32_t* nodes, const void* const* host,
+                               int32_t* n_done, void* stream);
 
 /* Value ranges of bricks known without their data, as a container's index
  * table would hold them ("Volumetric Data Storage": chunks with an index):
@@ -213,6 +229,13 @@ sg_status sg_read_selection(sg_volume* vol, int slot, int32_t* cell_node, int64_
  * its brick group, or -1 when it is not cached ("Volumetric Data Cashing").
  * slot_of_node holds nnode >= nodes entries. Errors: INVALID_ARG. */
 sg_status sg_read_residency(sg_volume* vol, int t, int32_t* slot_of_node, int64_t nnode);
+
+/* Copies the value ranges of every brick of time point t to host:
+ * minmax[(node * channels + c) * 2 + {0, 1}] = min, max over the brick and
+ * its apron (min > max: never seen), nnode >= nodes. With
+ * sg_set_brick_ranges this moves a volume's index between volumes
+ * (synchronous). Errors: INVALID_ARG, CUDA. */
+sg_status sg_read_ranges(sg_volume* vol, int t, uint32_t* minmax, int64_t nnode);
 
 /* Copies the stored brick of (t, c, level, bx, by, bz) to host: (B+2)^3
  * voxels of dtype, x fastest, apron included (waits for the stream). For

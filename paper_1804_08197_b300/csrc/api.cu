@@ -108,10 +108,124 @@ bool tfs_ready(const sg_volume* v) {
   return true;
 }
 
-sg_status refresh_flags(sg_volume* v, cudaStream_t s) {
+sg_status refresh_flags(sg_volume* v, cudaStream_t s, const int32_t* d_slots = nullptr, int nslots = 0) {
   if (!tfs_ready(v)) return SG_OK;
-  SG_CUDA(launch_tf_flags(v, s), "transfer-function flags");
+  SG_CUDA(launch_tf_flags(v, s, d_slots, nslots), "transfer-function flags");
   return SG_OK;
+}
+
+__global__ void k_page_update(int32_t* __restrict__ slot_of_key, const int64_t* __restrict__ upd, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) slot_of_key[upd[2 * i]] = (int32_t)upd[2 * i + 1];
+}
+
+// Places bricks nodes[0..n) of (t, c) in the cache in list order, copying
+// brick i from host[i]; stops at the first brick that finds the cache full of
+// bricks used by the current frame (*done = bricks placed, a prefix of the
+// list). Page-table entries, value ranges and transparency flags of every
+// placed brick are consistent on return, whether or not the list was cut.
+sg_status upload_list(sg_volume* v, int t, int c, int n, const int32_t* nodes, const void* const* host, int* done,
+                      cudaStream_t s) {
+  VolumeExtra* x = extra_of(v);
+  const int R = v->B + 2;
+  const size_t raw = (size_t)R * R * R * v->esize;
+  *done = 0;
+  if (v->pooled) {
+    // stamps of slots used by recent selections
+    std::vector<uint64_t> st(v->pool_slots);
+    SG_CUDA(cudaStreamSynchronize(s), "upload");
+    SG_CUDA(cudaMemcpy(st.data(), v->d_stamp, v->pool_slots * sizeof(uint64_t), cudaMemcpyDeviceToHost), "stamps");
+    for (int64_t sl = 0; sl < v->pool_slots; ++sl)
+      if (v->slot_owner[sl] >= 0 && !v->slot_pinned[sl] && st[sl] != v->slot_stamp[sl]) {
+        x->lru.erase({v->slot_stamp[sl], sl});
+        v->slot_stamp[sl] = st[sl];
+        x->lru.insert({st[sl], sl});
+      }
+  }
+  std::vector<int32_t> lists(2 * (size_t)n);  // [nodes placed][their slots]
+  std::vector<int64_t> touched;               // page-table keys whose entry changed
+  int m = 0;
+  for (; m < n; ++m) {
+    const int32_t node = nodes[m];
+    const int64_t key = (int64_t)t * v->nodes + node;
+    int32_t slot = v->h_slot[key];
+    if (slot < 0) {
+      int64_t sl;
+      if (!x->free_slots.empty()) {
+        sl = x->free_slots.back();
+        x->free_slots.pop_back();
+      } else {
+        // least recently used slot not used by the current frame
+        auto it = x->lru.begin();
+        if (it == x->lru.end() || it->first >= v->frame) break;
+        sl = it->second;
+        x->lru.erase(it);
+        const int64_t old = v->slot_owner[sl];
+        v->h_slot[old] = -1;
+        touched.push_back(old);
+      }
+      slot = (int32_t)sl;
+      v->slot_owner[sl] = key;
+      v->h_slot[key] = slot;
+      touched.push_back(key);
+      int level = 0;
+      while (level + 1 < v->levels && node >= v->geom[level + 1].off) ++level;
+      if (level == v->levels - 1) {
+        v->slot_pinned[sl] = 1;
+      } else {
+        v->slot_stamp[sl] = v->frame;
+        x->lru.insert({v->frame, sl});
+      }
+    }
+    lists[m] = node;
+    lists[n + m] = slot;
+    SG_CUDA(cudaMemcpyAsync(v->d_pool + ((size_t)slot * v->nch + c) * v->brick_bytes, host[m], raw,
+                            cudaMemcpyHostToDevice, s),
+            "brick upload");
+  }
+  *done = m;
+  if (m == 0) return SG_OK;
+  // final page-table value of every touched key (a key evicted and placed
+  // again in the same list keeps its last value)
+  std::sort(touched.begin(), touched.end());
+  touched.erase(std::unique(touched.begin(), touched.end()), touched.end());
+  const size_t nupd = touched.size();
+  std::vector<int64_t> upd(2 * nupd);
+  for (size_t i = 0; i < nupd; ++i) {
+    upd[2 * i] = touched[i];
+    upd[2 * i + 1] = v->h_slot[touched[i]];
+  }
+  // device copies of the lists for the range kernels and the page update
+  const size_t need = 2 * (size_t)m + 4 * nupd;  // int32 words: lists + int64 pairs
+  if (x->scratch_n < need) {
+    cudaFree(x->d_scratch);
+    x->d_scratch = nullptr;
+    x->scratch_n = 0;
+    cudaError_t e = dalloc(&x->d_scratch, need + 2);
+    if (e != cudaSuccess) {
+      set_error(std::string("upload scratch: ") + cudaGetErrorString(e));
+      return SG_ERR_OOM;
+    }
+    x->scratch_n = need;
+  }
+  int32_t* d_nodes = x->d_scratch;
+  int32_t* d_slots = x->d_scratch + m;
+  int64_t* d_upd = reinterpret_cast<int64_t*>(x->d_scratch + ((2 * (size_t)m + 1) & ~(size_t)1));
+  SG_CUDA(cudaMemcpyAsync(d_nodes, lists.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, s), "upload");
+  SG_CUDA(cudaMemcpyAsync(d_slots, lists.data() + n, m * sizeof(int32_t), cudaMemcpyHostToDevice, s), "upload");
+  if (nupd) {
+    SG_CUDA(cudaMemcpyAsync(d_upd, upd.data(), upd.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s), "upload");
+    k_page_update<<<(unsigned)((nupd + 255) / 256), 256, 0, s>>>(v->d_slot, d_upd, (int)nupd);
+    SG_CUDA(cudaGetLastError(), "page table update");
+  }
+  SG_CUDA(launch_brick_ranges(v, t, c, 0, d_nodes, m, s), "brick ranges");
+  SG_CUDA(launch_subranges(v, d_slots, m, c, s), "sub-block ranges");
+  v->has_data[(size_t)t * v->nch + c] = 1;
+  // node flags everywhere, sub-block flags of the uploaded slots only
+  sg_status st = refresh_flags(v, s, d_slots, m);
+  // the host vectors above are consumed by the copies before they return
+  SG_CUDA(cudaStreamSynchronize(s), "upload");
+  return st;
 }
 
 sg_status ensure_selection(sg_volume* v, int slot) {
@@ -253,7 +367,7 @@ sg_status sg_volume_create(const sg_volume_desc* d, sg_volume** out) {
       (e = dalloc(&v->d_subdist, (size_t)v->pool_slots * ns3)) != cudaSuccess ||
       (e = dalloc(&v->d_nodeflags, tn)) != cudaSuccess ||
       (e = dalloc(&v->d_tf_raw, (size_t)v->nch * kMaxTF * 4)) != cudaSuccess ||
-      (e = dalloc(&v->d_lut, (size_t)v->nch * v->levels * kMaxTF)) != cudaSuccess ||
+      (e = dalloc(&v->d_lut, (size_t)2 * v->nch * v->levels * kMaxTF)) != cudaSuccess ||
       (e = dalloc(&v->d_err, 4)) != cudaSuccess) {
     free_volume(v);
     set_error(std::string("device allocation: ") + cudaGetErrorString(e));
@@ -475,6 +589,17 @@ sg_status sg_read_selection(sg_volume* v, int slot, int32_t* cell_node, int64_t 
   return SG_OK;
 }
 
+sg_status sg_read_ranges(sg_volume* v, int t, uint32_t* minmax, int64_t nnode) {
+  SG_CHECK_ARG(v && minmax, "volume or output NULL");
+  SG_CHECK_ARG(t >= 0 && t < v->T, "t out of range");
+  SG_CHECK_ARG(nnode >= v->nodes, "output too small");
+  SG_CUDA(cudaDeviceSynchronize(), "read ranges");
+  SG_CUDA(cudaMemcpy(minmax, v->d_range + (int64_t)t * v->nodes * v->nch * 2, v->nodes * v->nch * 2 * sizeof(uint32_t),
+                     cudaMemcpyDeviceToHost),
+          "read ranges");
+  return SG_OK;
+}
+
 sg_status sg_read_residency(sg_volume* v, int t, int32_t* slot_of_node, int64_t nnode) {
   SG_CHECK_ARG(v && slot_of_node, "volume or output NULL");
   SG_CHECK_ARG(t >= 0 && t < v->T, "t out of range");
@@ -630,86 +755,36 @@ sg_status sg_upload_bricks(sg_volume* v, int t, int c, int level, int n, const i
     SG_CHECK_ARG(xyz[3 * i] >= 0 && xyz[3 * i] < g.nb[0] && xyz[3 * i + 1] >= 0 && xyz[3 * i + 1] < g.nb[1] &&
                      xyz[3 * i + 2] >= 0 && xyz[3 * i + 2] < g.nb[2],
                  "brick coordinates out of range");
-  cudaStream_t s = (cudaStream_t)stream;
-  VolumeExtra* x = extra_of(v);
-  const int R = v->B + 2;
-  const size_t raw = (size_t)R * R * R * v->esize;
-  std::vector<int32_t> nodes(n), slots(n);
-  if (v->pooled) {
-    // stamps of slots used by recent selections
-    std::vector<uint64_t> st(v->pool_slots);
-    SG_CUDA(cudaStreamSynchronize(s), "upload");
-    SG_CUDA(cudaMemcpy(st.data(), v->d_stamp, v->pool_slots * sizeof(uint64_t), cudaMemcpyDeviceToHost), "stamps");
-    for (int64_t sl = 0; sl < v->pool_slots; ++sl)
-      if (v->slot_owner[sl] >= 0 && !v->slot_pinned[sl] && st[sl] != v->slot_stamp[sl]) {
-        x->lru.erase({v->slot_stamp[sl], sl});
-        v->slot_stamp[sl] = st[sl];
-        x->lru.insert({st[sl], sl});
-      }
-  }
-  std::vector<std::pair<int64_t, int32_t>> table_updates;  // (t*nodes+node, slot)
+  const size_t raw = (size_t)(v->B + 2) * (v->B + 2) * (v->B + 2) * v->esize;
+  std::vector<int32_t> nodes(n);
+  std::vector<const void*> ptrs(n);
   for (int i = 0; i < n; ++i) {
-    int64_t node = g.off + ((int64_t)xyz[3 * i + 2] * g.nb[1] + xyz[3 * i + 1]) * g.nb[0] + xyz[3 * i];
-    int64_t key = (int64_t)t * v->nodes + node;
-    nodes[i] = (int32_t)node;
-    int32_t slot = v->h_slot[key];
-    if (slot < 0) {
-      int64_t sl;
-      if (!x->free_slots.empty()) {
-        sl = x->free_slots.back();
-        x->free_slots.pop_back();
-      } else {
-        // least recently used slot not used by the current frame
-        auto it = x->lru.begin();
-        if (it == x->lru.end() || it->first >= v->frame) {
-          set_error("sg_upload_bricks: brick cache full of bricks used by the current frame");
-          return SG_ERR_OOM;
-        }
-        sl = it->second;
-        x->lru.erase(it);
-        int64_t old = v->slot_owner[sl];
-        v->h_slot[old] = -1;
-        table_updates.push_back({old, -1});
-      }
-      slot = (int32_t)sl;
-      v->slot_owner[sl] = key;
-      v->h_slot[key] = slot;
-      table_updates.push_back({key, slot});
-      if (level == v->levels - 1) {
-        v->slot_pinned[sl] = 1;
-      } else {
-        v->slot_stamp[sl] = v->frame;
-        x->lru.insert({v->frame, sl});
-      }
-    }
-    slots[i] = slot;
-    SG_CUDA(cudaMemcpyAsync(v->d_pool + ((size_t)slot * v->nch + c) * v->brick_bytes,
-                            static_cast<const uint8_t*>(host) + raw * i, raw, cudaMemcpyHostToDevice, s),
-            "brick upload");
+    nodes[i] = (int32_t)(g.off + ((int64_t)xyz[3 * i + 2] * g.nb[1] + xyz[3 * i + 1]) * g.nb[0] + xyz[3 * i]);
+    ptrs[i] = static_cast<const uint8_t*>(host) + raw * i;
   }
-  for (auto& u : table_updates)
-    SG_CUDA(cudaMemcpyAsync(v->d_slot + u.first, &u.second, sizeof(int32_t), cudaMemcpyHostToDevice, s),
-            "page table update");
-  // device copies of the node and slot lists for the range kernels
-  if (x->scratch_n < (size_t)2 * n) {
-    cudaFree(x->d_scratch);
-    x->d_scratch = nullptr;
-    x->scratch_n = 0;
-    cudaError_t e = dalloc(&x->d_scratch, (size_t)2 * n);
-    if (e != cudaSuccess) {
-      set_error(std::string("upload scratch: ") + cudaGetErrorString(e));
-      return SG_ERR_OOM;
-    }
-    x->scratch_n = 2 * n;
+  int done = 0;
+  sg_status st = upload_list(v, t, c, n, nodes.data(), ptrs.data(), &done, (cudaStream_t)stream);
+  if (st == SG_OK && done < n) {
+    set_error("sg_upload_bricks: brick cache full of bricks used by the current frame");
+    return SG_ERR_OOM;
   }
-  SG_CUDA(cudaMemcpyAsync(x->d_scratch, nodes.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s), "upload");
-  SG_CUDA(cudaMemcpyAsync(x->d_scratch + n, slots.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s), "upload");
-  SG_CUDA(launch_brick_ranges(v, t, c, level, x->d_scratch, n, s), "brick ranges");
-  SG_CUDA(launch_subranges(v, x->d_scratch + n, n, c, s), "sub-block ranges");
-  // the host vectors above are consumed by the copies before they are reused
-  SG_CUDA(cudaStreamSynchronize(s), "upload");
-  v->has_data[(size_t)t * v->nch + c] = 1;
-  return refresh_flags(v, s);
+  return st;
+}
+
+sg_status sg_upload_brick_list(sg_volume* v, int t, int c, int n, const int32_t* nodes, const void* const* host,
+                               int32_t* n_done, void* stream) {
+  SG_CHECK_ARG(v && n_done && n >= 0 && (n == 0 || (nodes && host)), "volume/nodes/host/n_done NULL or n < 0");
+  SG_CHECK_ARG(t >= 0 && t < v->T && c >= 0 && c < v->nch, "t or c out of range");
+  *n_done = 0;
+  for (int i = 0; i < n; ++i) {
+    SG_CHECK_ARG(nodes[i] >= 0 && nodes[i] < v->nodes, "node id out of range");
+    SG_CHECK_ARG(host[i], "host pointer NULL");
+  }
+  if (n == 0) return SG_OK;
+  int done = 0;
+  sg_status st = upload_list(v, t, c, n, nodes, host, &done, (cudaStream_t)stream);
+  *n_done = done;
+  return st;
 }
 
 }  // extern "C"

@@ -95,7 +95,7 @@ struct sg_volume {
   // transfer functions
   sg::TFHost tf[sg::kMaxCh];
   float* d_tf_raw = nullptr;       // [nch][kMaxTF][4]
-  float4* d_lut = nullptr;         // [nch][levels][kMaxTF] opacity-corrected
+  float4* d_lut = nullptr;         // [nch][levels][kMaxTF][2] opacity-corrected (entry, delta to next)
   float lut_step = -1.0f;
   uint64_t tf_version = 0;
 
@@ -128,7 +128,9 @@ cudaError_t launch_brick_ranges(sg_volume* v, int t, int c, int L, const int32_t
                                 cudaStream_t s);
 
 // tf.cu
-cudaError_t launch_tf_flags(sg_volume* v, cudaStream_t s);
+// node flags for every node; sub-block bits / distances for every slot, or
+// only the nslots slots listed in device array d_slots
+cudaError_t launch_tf_flags(sg_volume* v, cudaStream_t s, const int32_t* d_slots = nullptr, int nslots = 0);
 cudaError_t launch_lut(sg_volume* v, float step, cudaStream_t s);
 
 // select.cu

@@ -19,6 +19,17 @@ namespace sg {
 namespace {
 
 constexpr int kTileW = 16, kTileH = 8, kThreads = kTileW * kTileH;
+
+#ifdef SG_RENDER_EVENT_STATS
+// diagnostic build only: per-event counters of the ray loop
+// [0] samples [1] sub-block jumps [2] rendered block entries [3] skipped block
+// entries [4] warp loop trips [5] lane loop iterations [6] rays that hit
+// [7] sub-block lookups that found an opaque sub-block
+__device__ unsigned long long g_events[8];
+#define SG_EV(i, n) ev[i] += (n)
+#else
+#define SG_EV(i, n) ((void)0)
+#endif
 // minimum resident CTAs per SM requested from the register allocator
 #ifndef SG_RENDER_MINB
 #define SG_RENDER_MINB 1
@@ -85,17 +96,24 @@ __device__ inline int first_k_at(float t, float t0, const Args& a, int kmin) {
   return k;
 }
 
-template <typename T>
-__device__ __forceinline__ float tri(const T* __restrict__ b, int R, float lx, float ly, float lz, int B) {
-  const float fx = floor_f(lx), fy = floor_f(ly), fz = floor_f(lz);
-  const int ix = min(max(floor_i(lx), 0), B), iy = min(max(floor_i(ly), 0), B), iz = min(max(floor_i(lz), 0), B);
-  const float wx = lx - fx, wy = ly - fy, wz = lz - fz;
-  const T* p = b + ((size_t)iz * R + iy) * R + ix;
-  const size_t RR = (size_t)R * R;
-  const float v000 = u2f(p[0]), v100 = u2f(p[1]), v010 = u2f(p[R]), v110 = u2f(p[R + 1]);
-  const float v001 = u2f(p[RR]), v101 = u2f(p[RR + 1]), v011 = u2f(p[RR + R]), v111 = u2f(p[RR + R + 1]);
-  const float c00 = fmaf(wx, v100 - v000, v000), c10 = fmaf(wx, v110 - v010, v010);
-  const float c01 = fmaf(wx, v101 - v001, v001), c11 = fmaf(wx, v111 - v011, v011);
+// Trilinear interpolation at brick-local coordinate (lx, ly, lz) of a brick
+// of edge B (BK: B as a compile-time constant, 0 = runtime). Voxels are
+// turned into floats by OR-ing them into the mantissa of 2^23: differences of
+// two such biased values are exact, and one subtraction of 2^23 per pair
+// unbiases the base, so the result equals the plain FP32 formula.
+template <typename T, int BK>
+__device__ __forceinline__ float tri(const T* __restrict__ b, int Brt, float lx, float ly, float lz) {
+  const int B = BK ? BK : Brt, R = B + 2, RR = R * R;
+  const float rx = __fadd_rd(lx, kMagic), ry = __fadd_rd(ly, kMagic), rz = __fadd_rd(lz, kMagic);
+  const float wx = lx - (rx - kMagic), wy = ly - (ry - kMagic), wz = lz - (rz - kMagic);
+  const int ix = min(max(__float_as_int(rx) - kMagicBits, 0), B), iy = min(max(__float_as_int(ry) - kMagicBits, 0), B),
+            iz = min(max(__float_as_int(rz) - kMagicBits, 0), B);
+  const T* p = b + (iz * RR + iy * R + ix);
+  auto bias = [](uint32_t v) { return __int_as_float(0x4B000000 | v); };
+  const float b000 = bias(p[0]), b100 = bias(p[1]), b010 = bias(p[R]), b110 = bias(p[R + 1]);
+  const float b001 = bias(p[RR]), b101 = bias(p[RR + 1]), b011 = bias(p[RR + R]), b111 = bias(p[RR + R + 1]);
+  const float c00 = fmaf(wx, b100 - b000, b000 - 8388608.0f), c10 = fmaf(wx, b110 - b010, b010 - 8388608.0f);
+  const float c01 = fmaf(wx, b101 - b001, b001 - 8388608.0f), c11 = fmaf(wx, b111 - b011, b011 - 8388608.0f);
   const float c0 = fmaf(wy, c10 - c00, c00), c1 = fmaf(wy, c11 - c01, c01);
   return fmaf(wz, c1 - c0, c0);
 }
@@ -106,33 +124,41 @@ __device__ __forceinline__ float4 classify(const Args& a, int c, int L, float v)
   const float fl = fminf(floor_f(q), (float)(a.n[c] - 2));  // entry index as an exact float
   const int i = __float_as_int(fl + kMagic) - kMagicBits;
   const float f = q - fl;
-  const float4* t = a.lut + ((size_t)c * a.levels + L) * kMaxTF + i;
-  const float4 e0 = __ldg(t), e1 = __ldg(t + 1);
-  return make_float4(fmaf(f, e1.x - e0.x, e0.x), fmaf(f, e1.y - e0.y, e0.y), fmaf(f, e1.z - e0.z, e0.z),
-                     fmaf(f, e1.w - e0.w, e0.w));
+  const float4* t = a.lut + 2 * (((size_t)c * a.levels + L) * kMaxTF + i);
+  const float4 e0 = __ldg(t), de = __ldg(t + 1);
+  return make_float4(fmaf(f, de.x, e0.x), fmaf(f, de.y, e0.y), fmaf(f, de.z, e0.z), fmaf(f, de.w, e0.w));
 }
 
 // Trilinear value + classification + front-to-back compositing of one sample
 // at brick-local coordinate l (all channels, additive blend). Returns true
 // when the ray is opaque enough to stop.
-template <typename T>
+template <typename T, int BK>
 __device__ __forceinline__ bool composite_sample(const Args& a, const T* __restrict__ brick0, int L, float lx, float ly,
                                                  float lz, float4& acc) {
-  const int R = a.B + 2;
-  float sa = 0.0f, sr = 0.0f, sg = 0.0f, sb = 0.0f;
-  for (int c = 0; c < a.nch; ++c) {
-    const T* br = reinterpret_cast<const T*>(reinterpret_cast<const uint8_t*>(brick0) + (size_t)c * a.brick_bytes);
-    const float v = tri<T>(br, R, lx, ly, lz, a.B);
-    const float4 e = classify(a, c, L, v);
-    sa += e.w;
-    sr = fmaf(e.w, e.x, sr);
-    sg = fmaf(e.w, e.y, sg);
-    sb = fmaf(e.w, e.z, sb);
-  }
-  if (sa > 1.0f) {  // additive blend saturates: alpha 1, colour renormalised
-    const float r = 1.0f / sa;
-    sr *= r; sg *= r; sb *= r;
-    sa = 1.0f;
+  float sa, sr, sg, sb;
+  if (a.nch == 1) {
+    // one channel: alpha is an interpolation of table entries in [0, 1], so
+    // the additive blend below never saturates
+    const float4 e = classify(a, 0, L, tri<T, BK>(brick0, a.B, lx, ly, lz));
+    sa = e.w;
+    sr = e.w * e.x;
+    sg = e.w * e.y;
+    sb = e.w * e.z;
+  } else {
+    sa = 0.0f; sr = 0.0f; sg = 0.0f; sb = 0.0f;
+    for (int c = 0; c < a.nch; ++c) {
+      const T* br = reinterpret_cast<const T*>(reinterpret_cast<const uint8_t*>(brick0) + (size_t)c * a.brick_bytes);
+      const float4 e = classify(a, c, L, tri<T, BK>(br, a.B, lx, ly, lz));
+      sa += e.w;
+      sr = fmaf(e.w, e.x, sr);
+      sg = fmaf(e.w, e.y, sg);
+      sb = fmaf(e.w, e.z, sb);
+    }
+    if (sa > 1.0f) {  // additive blend saturates: alpha 1, colour renormalised
+      const float r = 1.0f / sa;
+      sr *= r; sg *= r; sb *= r;
+      sa = 1.0f;
+    }
   }
   const float w = 1.0f - acc.w;
   acc.x = fmaf(w, sr, acc.x);
@@ -156,7 +182,7 @@ __device__ inline int cell_of(float p, float invB, int lo, int hi) {
 // iteration (take a sample, jump over a transparent 8^3 sub-block, or move to
 // the next block), so the lanes of a warp stay in one loop instead of
 // diverging across nested ones.
-template <typename T>
+template <typename T, int BK>
 __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int px, int py, bool active, float4& acc,
                                           uint32_t& cnt) {
   acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -190,8 +216,12 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
   const bool hit = active && isfinite(t0) && isfinite(t1) && t1 > t0 && (t1 - t0) * a.inv_step < 4.0e6f &&
                    isfinite(d.x + d.y + d.z);
   if (!hit) return;
+#ifdef SG_RENDER_EVENT_STATS
+  unsigned long long ev[8] = {0, 0, 0, 0, 0, 0, 1, 0};
+#endif
 
-  const float Bf = (float)a.B, invB = 1.0f / Bf;
+  const int B = BK ? BK : a.B;
+  const float Bf = (float)B, invB = 1.0f / Bf;
   int cx = cell_of(fmaf(t0, d.x, o.x), invB, 0, a.nb0[0] - 1);
   int cy = cell_of(fmaf(t0, d.y, o.y), invB, 0, a.nb0[1] - 1);
   int cz = cell_of(fmaf(t0, d.z, o.z), invB, 0, a.nb0[2] - 1);
@@ -202,12 +232,20 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
   float tend = -1.0f;   // exit of the current block (clipped to t1)
   float texit = -1.0f;  // unclipped exit
   uint32_t slot = 0;
+  const T* brick0 = nullptr;               // the current block's brick (channel 0)
   float3 lo = make_float3(0.f, 0.f, 0.f);  // block origin, level-0 voxels
   float sL = 1.0f;                         // 2^-L
   bool render = false;
   const int nsm = a.nsub - 1;
 
   for (int guard = 0; guard < (1 << 25); ++guard) {
+#ifdef SG_RENDER_EVENT_STATS
+    {
+      const unsigned am = __activemask();
+      if ((am & ((1u << (threadIdx.x & 31)) - 1u)) == 0u) ++ev[4];
+      ++ev[5];
+    }
+#endif
     const float t = lattice_t(k, t0, a);
     if (!render || !(t < tend)) {
       // ---- leave the current block and enter the next one
@@ -242,7 +280,7 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
       L = e & 15;
       const int nl_x = (cx >> L) << L, nl_y = (cy >> L) << L, nl_z = (cz >> L) << L;
       lo = make_float3((float)nl_x * Bf, (float)nl_y * Bf, (float)nl_z * Bf);
-      const float span = (float)(a.B << L);
+      const float span = (float)(B << L);
       const float ex = axis_exit(o.x, d.x, inv.x, lo.x, fminf(lo.x + span, a.dims0[0]));
       const float ey = axis_exit(o.y, d.y, inv.y, lo.y, fminf(lo.y + span, a.dims0[1]));
       const float ez = axis_exit(o.z, d.z, inv.z, lo.z, fminf(lo.z + span, a.dims0[2]));
@@ -253,10 +291,12 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
       tend = fminf(texit, t1);
       kb = k;
       render = !(e & kLeafNone) && !(a.empty_skip && (e & 16u));
+      SG_EV(render ? 2 : 3, 1);
       if (!render) continue;  // owns its lattice points without sampling them: leave at once
       kstep = 1 << L;
       k = (k + kstep - 1) & ~(kstep - 1);
       slot = (e & ~kLeafNone) >> 5;
+      brick0 = reinterpret_cast<const T*>(a.pool + (size_t)slot * a.nch * a.brick_bytes);
       sL = __int_as_float((127 - L) << 23);
       continue;
     }
@@ -284,17 +324,23 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
         // exit: it is inside the cube's footprint margin, alpha 0, exact
         k = max(ceil_i((ts - t0) * a.inv_step), k + 1);
         k = (k + kstep - 1) & ~(kstep - 1);
+        SG_EV(1, 1);
         continue;
       }
+      SG_EV(7, 1);
     }
-    const T* brick0 = reinterpret_cast<const T*>(a.pool + (size_t)slot * a.nch * a.brick_bytes);
     ++cnt;
-    if (composite_sample<T>(a, brick0, L, lx, ly, lz, acc)) break;
+    SG_EV(0, 1);
+    if (composite_sample<T, BK>(a, brick0, L, lx, ly, lz, acc)) break;
     k += kstep;
   }
+#ifdef SG_RENDER_EVENT_STATS
+  for (int i = 0; i < 8; ++i)
+    if (ev[i]) atomicAdd(&g_events[i], ev[i]);
+#endif
 }
 
-template <typename T, int MAXI>
+template <typename T, int MAXI, int BK>
 __global__ void __launch_bounds__(kThreads, SG_RENDER_MINB) k_render(Args a, Jobs<MAXI> jobs) {
   const int tile = blockIdx.x;
   int im = 0;
@@ -309,7 +355,7 @@ __global__ void __launch_bounds__(kThreads, SG_RENDER_MINB) k_render(Args a, Job
 
   float4 acc;
   uint32_t cnt;
-  trace_ray<T>(a, J, px, py, active, acc, cnt);
+  trace_ray<T, BK>(a, J, px, py, active, acc, cnt);
   if (active) {
     const size_t pix = (size_t)py * J.W + px;
     J.out[pix] = acc;
@@ -326,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, SG_RENDER_MINB) k_render(Args a, Job
 // PERSIST: a grid sized to the machine pulls tiles from a global counter
 // (work queue over all images of the batch, whatever their sizes); else one
 // CTA per tile.
-template <typename T, int TW, int TH, int RPT, bool PERSIST>
+template <typename T, int TW, int TH, int RPT, bool PERSIST, int BK>
 __global__ void __launch_bounds__(TW * TH / RPT) k_render_tiles(Args a, Jobs<128> jobs, int* __restrict__ counter) {
   constexpr int kN = TW * TH / RPT;
   constexpr int kSubX = TW / 8;
@@ -358,7 +404,7 @@ __global__ void __launch_bounds__(TW * TH / RPT) k_render_tiles(Args a, Jobs<128
       const bool active = px < J.W && py < J.H;
       float4 acc;
       uint32_t cnt;
-      trace_ray<T>(a, J, px, py, active, acc, cnt);
+      trace_ray<T, BK>(a, J, px, py, active, acc, cnt);
       if (active) {
         const size_t pix = (size_t)py * J.W + px;
         J.out[pix] = acc;
@@ -488,28 +534,28 @@ bool make_jobs(const sg_volume* v, const sg_pose* poses, int n, const sg_render_
   return true;
 }
 
-template <typename T, int TW, int TH, int RPT>
+template <typename T, int TW, int TH, int RPT, int BK>
 cudaError_t launch_tiles(sg_volume* v, const Args& a, const Jobs<128>& jobs, bool persist, cudaStream_t s) {
   constexpr int kN = TW * TH / RPT;
   if (!persist) {
-    k_render_tiles<T, TW, TH, RPT, false><<<jobs.total_tiles, kN, 0, s>>>(a, jobs, nullptr);
+    k_render_tiles<T, TW, TH, RPT, false, BK><<<jobs.total_tiles, kN, 0, s>>>(a, jobs, nullptr);
     return cudaGetLastError();
   }
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_tiles<T, TW, TH, RPT, true>, kN, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_tiles<T, TW, TH, RPT, true, BK>, kN, 0);
   if (per_sm < 1) per_sm = 1;
   int grid = sms * per_sm;
   if (grid > jobs.total_tiles) grid = jobs.total_tiles;
   // word 0 of the volume's device control block is the tile queue head
   cudaError_t e = cudaMemsetAsync(v->d_err, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
-  k_render_tiles<T, TW, TH, RPT, true><<<grid, kN, 0, s>>>(a, jobs, reinterpret_cast<int*>(v->d_err));
+  k_render_tiles<T, TW, TH, RPT, true, BK><<<grid, kN, 0, s>>>(a, jobs, reinterpret_cast<int*>(v->d_err));
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, int BK>
 cudaError_t dispatch_tiles(sg_volume* v, const Args& a, const sg_pose* poses, int n, const sg_render_params* prm,
                            float* const* outs, const sg_render_config& c, cudaStream_t s) {
   Jobs<128> jobs;  // by-value kernel parameter block (about 13 KB)
@@ -517,7 +563,7 @@ cudaError_t dispatch_tiles(sg_volume* v, const Args& a, const sg_pose* poses, in
 #define SG_TILE(TW, TH, RPT)                                                              \
   if (c.tile_w == TW && c.tile_h == TH && c.rays_per_thread == RPT) {                     \
     if (!make_jobs<128>(v, poses, n, prm, outs, TW, TH, &jobs)) return cudaErrorInvalidValue; \
-    return launch_tiles<T, TW, TH, RPT>(v, a, jobs, p, s);                                \
+    return launch_tiles<T, TW, TH, RPT, BK>(v, a, jobs, p, s);                            \
   }
   SG_TILE(16, 8, 1)
   SG_TILE(8, 16, 1)
@@ -529,17 +575,32 @@ cudaError_t dispatch_tiles(sg_volume* v, const Args& a, const sg_pose* poses, in
   return cudaErrorInvalidValue;
 }
 
-template <int MAXI>
+template <int MAXI, int BK>
 cudaError_t launch_impl(sg_volume* v, const sg_pose* poses, int n, const sg_render_params* prm, float* const* outs,
                         cudaStream_t s) {
   Args a = make_args(v, prm);
   Jobs<MAXI> jobs;
   if (!make_jobs<MAXI>(v, poses, n, prm, outs, kTileW, kTileH, &jobs)) return cudaErrorInvalidValue;
   if (v->esize == 1)
-    k_render<uint8_t, MAXI><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
+    k_render<uint8_t, MAXI, BK><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
   else
-    k_render<uint16_t, MAXI><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
+    k_render<uint16_t, MAXI, BK><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
   return cudaGetLastError();
+}
+
+// Brick edges with a specialised kernel (voxel offsets become immediates);
+// any other edge runs the generic one.
+template <int BK>
+cudaError_t launch_b(sg_volume* v, const sg_pose* poses, int n, const sg_render_params* prm, float* const* outs,
+                     cudaStream_t s) {
+  const sg_render_config& c = v->render_cfg;
+  if (c.tile_w == 0) {  // default: one 16 x 8 CTA per tile
+    if (n == 1) return launch_impl<2, BK>(v, poses, n, prm, outs, s);
+    return launch_impl<128, BK>(v, poses, n, prm, outs, s);
+  }
+  Args a = make_args(v, prm);
+  if (v->esize == 1) return dispatch_tiles<uint8_t, BK>(v, a, poses, n, prm, outs, c, s);
+  return dispatch_tiles<uint16_t, BK>(v, a, poses, n, prm, outs, c, s);
 }
 
 }  // namespace
@@ -547,14 +608,12 @@ cudaError_t launch_impl(sg_volume* v, const sg_pose* poses, int n, const sg_rend
 cudaError_t launch_render(sg_volume* v, const sg_pose* poses, int n, const sg_render_params* prm, float* const* outs,
                           cudaStream_t s) {
   if (n < 1 || n > 64) return cudaErrorInvalidValue;
-  const sg_render_config& c = v->render_cfg;
-  if (c.tile_w == 0) {  // default: one 16 x 8 CTA per tile
-    if (n == 1) return launch_impl<2>(v, poses, n, prm, outs, s);
-    return launch_impl<128>(v, poses, n, prm, outs, s);
+  switch (v->B) {
+    case 32: return launch_b<32>(v, poses, n, prm, outs, s);
+    case 64: return launch_b<64>(v, poses, n, prm, outs, s);
+    case 128: return launch_b<128>(v, poses, n, prm, outs, s);
+    default: return launch_b<0>(v, poses, n, prm, outs, s);
   }
-  Args a = make_args(v, prm);
-  if (v->esize == 1) return dispatch_tiles<uint8_t>(v, a, poses, n, prm, outs, c, s);
-  return dispatch_tiles<uint16_t>(v, a, poses, n, prm, outs, c, s);
 }
 
 bool render_config_supported(const sg_render_config* c) {
@@ -582,3 +641,12 @@ int render_config_candidates(sg_render_config* out, int cap) {
 }
 
 }  // namespace sg
+
+#ifdef SG_RENDER_EVENT_STATS
+// diagnostic build only: reads and clears the ray-loop event counters
+extern "C" int sg_debug_render_events(unsigned long long* out8) {
+  if (cudaMemcpyFromSymbol(out8, sg::g_events, sizeof(sg::g_events)) != cudaSuccess) return 1;
+  static const unsigned long long zero[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  return cudaMemcpyToSymbol(sg::g_events, zero, sizeof(zero)) == cudaSuccess ? 0 : 1;
+}
+#endif

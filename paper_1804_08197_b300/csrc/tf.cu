@@ -70,10 +70,10 @@ __global__ void k_subtree(uint8_t* __restrict__ flags, int64_t nodes, int T, int
 
 // one thread per 64-bit word of sub-block transparency bits of a slot
 __global__ void k_sub_empty(TFParams p, const uint16_t* __restrict__ subrange, int64_t slots, int ns3, int words,
-                            uint64_t* __restrict__ out) {
+                            uint64_t* __restrict__ out, const int32_t* __restrict__ slot_list) {
   const int64_t total = slots * words;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t slot = i / words;
+    const int64_t slot = slot_list ? slot_list[i / words] : i / words;
     int w = (int)(i % words);
     uint64_t bits = 0;
     for (int k = 0; k < 64; ++k) {
@@ -86,7 +86,7 @@ __global__ void k_sub_empty(TFParams p, const uint16_t* __restrict__ subrange, i
       }
       if (e) bits |= 1ull << k;
     }
-    out[i] = bits;
+    out[slot * words + w] = bits;
   }
 }
 
@@ -97,9 +97,10 @@ __global__ void k_sub_empty(TFParams p, const uint16_t* __restrict__ subrange, i
 // by breadth-first dilation rounds up to kMaxDist; farther cells keep
 // kMaxDist + 1 (capped by the brick edge where the ray's jump is clipped).
 constexpr int kMaxDist = 7;
-__global__ void k_sub_dist(const uint64_t* __restrict__ bits, int nsub, int words, uint8_t* __restrict__ dist) {
+__global__ void k_sub_dist(const uint64_t* __restrict__ bits, int nsub, int words, uint8_t* __restrict__ dist,
+                           const int32_t* __restrict__ slot_list) {
   extern __shared__ uint8_t sd[];
-  const int64_t slot = blockIdx.x;
+  const int64_t slot = slot_list ? slot_list[blockIdx.x] : blockIdx.x;
   const int ns3 = nsub * nsub * nsub;
   const uint64_t* w = bits + slot * words;
   for (int i = threadIdx.x; i < ns3; i += blockDim.x) sd[i] = ((w[i >> 6] >> (i & 63)) & 1ull) ? 255 : 0;
@@ -135,16 +136,28 @@ struct LutParams {
   float ref[kMaxCh];
 };
 
+__device__ __forceinline__ float4 lut_entry(const float* __restrict__ raw, const LutParams& p, float step, int c,
+                                            int L, int e) {
+  const float* r = raw + ((size_t)c * kMaxTF + e) * 4;
+  const float ex = step * (float)(1 << L) / p.ref[c];
+  const float a = r[3];
+  const float ac = (a >= 1.0f) ? 1.0f : 1.0f - powf(1.0f - a, ex);
+  return make_float4(r[0], r[1], r[2], ac);
+}
+
+// Opacity-corrected tables, one per (channel, level): entry e holds the pair
+// (value_e, value_{e+1} - value_e), so that interpolation between entries e
+// and e+1 is one FMA per component (the difference is the FP32 one the
+// renderer would form itself; the last entry's difference is 0).
 __global__ void k_lut(const float* __restrict__ raw, LutParams p, float step, float4* __restrict__ lut) {
   const int total = p.nch * p.levels * kMaxTF;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     int e = i % kMaxTF, L = (i / kMaxTF) % p.levels, c = i / (kMaxTF * p.levels);
     if (e >= p.n[c]) continue;
-    const float* r = raw + ((size_t)c * kMaxTF + e) * 4;
-    float ex = step * (float)(1 << L) / p.ref[c];
-    float a = r[3];
-    float ac = (a >= 1.0f) ? 1.0f : 1.0f - powf(1.0f - a, ex);
-    lut[i] = make_float4(r[0], r[1], r[2], ac);
+    const float4 v0 = lut_entry(raw, p, step, c, L, e);
+    const float4 v1 = e + 1 < p.n[c] ? lut_entry(raw, p, step, c, L, e + 1) : v0;
+    lut[2 * (size_t)i] = v0;
+    lut[2 * (size_t)i + 1] = make_float4(v1.x - v0.x, v1.y - v0.y, v1.z - v0.z, v1.w - v0.w);
   }
 }
 
@@ -169,7 +182,7 @@ unsigned grid_for(int64_t total, int threads) {
 
 }  // namespace
 
-cudaError_t launch_tf_flags(sg_volume* v, cudaStream_t s) {
+cudaError_t launch_tf_flags(sg_volume* v, cudaStream_t s, const int32_t* d_slots, int nslots) {
   TFParams p = make_params(v);
   int64_t total = v->nodes * v->T;
   k_own_empty<<<grid_for(total, 256), 256, 0, s>>>(p, v->d_range, total, v->d_nodeflags);
@@ -183,11 +196,14 @@ cudaError_t launch_tf_flags(sg_volume* v, cudaStream_t s) {
                                                cg.off, cg.nb[0], cg.nb[1], cg.nb[2], L == 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  int ns3 = v->nsub * v->nsub * v->nsub;
-  int64_t words = (int64_t)v->pool_slots * v->sub_words;
-  k_sub_empty<<<grid_for(words, 128), 128, 0, s>>>(p, v->d_subrange, v->pool_slots, ns3, v->sub_words, v->d_subempty);
+  // sub-block bits and distances: every slot, or only the listed ones
+  const int ns3 = v->nsub * v->nsub * v->nsub;
+  const int64_t nsl = d_slots ? nslots : v->pool_slots;
+  if (nsl <= 0) return cudaSuccess;
+  const int64_t words = nsl * v->sub_words;
+  k_sub_empty<<<grid_for(words, 128), 128, 0, s>>>(p, v->d_subrange, nsl, ns3, v->sub_words, v->d_subempty, d_slots);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_sub_dist<<<(unsigned)v->pool_slots, 256, ns3, s>>>(v->d_subempty, v->nsub, v->sub_words, v->d_subdist);
+  k_sub_dist<<<(unsigned)nsl, 256, ns3, s>>>(v->d_subempty, v->nsub, v->sub_words, v->d_subdist, d_slots);
   return cudaGetLastError();
 }
 

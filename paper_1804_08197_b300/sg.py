@@ -24,7 +24,8 @@ EXPORTS = ["sg_volume_create", "sg_volume_destroy", "sg_upload_volume_device", "
            "sg_render", "sg_render_host", "sg_render_batch", "sg_set_render_config", "sg_get_render_config",
            "sg_autotune_render", "sg_select_lod_noalloc", "sg_read_residency", "sg_set_brick_ranges", "sg_unet_create", "sg_unet_destroy",
            "sg_unet_param_count", "sg_unet_get_params", "sg_unet_set_params", "sg_unet_forward", "sg_unet_backward",
-           "sg_unet_adam_step", "sg_unet_set_tensor_path", "sg_unet_check", "sg_psnr", "sg_last_error",
+           "sg_unet_adam_step", "sg_unet_set_tensor_path", "sg_unet_check", "sg_psnr", "sg_read_ranges", "sg_upload_brick_list",
+           "sg_last_error",
            "sg_version"]
 
 
@@ -79,12 +80,14 @@ def _load():
         "sg_volume_destroy": [vp],
         "sg_upload_volume_device": [vp, i32, i32, vp, vp],
         "sg_upload_bricks": [vp, i32, i32, i32, i32, vp, vp, vp],
+        "sg_upload_brick_list": [vp, i32, i32, i32, vp, vp, P(ctypes.c_int32), vp],
         "sg_set_transfer_function": [vp, i32, vp, i32, f32, f32, f32, vp],
         "sg_select_lod": [vp, P(sg_pose), P(sg_select_stats), vp],
         "sg_select_lod_batch": [vp, P(sg_pose), i32, vp],
         "sg_read_selection": [vp, i32, vp, i64, vp, i64, vp, i32, vp, vp],
         "sg_read_brick": [vp, i32, i32, i32, i32, i32, i32, vp, vp],
         "sg_read_residency": [vp, i32, vp, i64],
+        "sg_read_ranges": [vp, i32, vp, i64],
         "sg_set_brick_ranges": [vp, i32, i32, i32, i32, vp, vp, vp],
         "sg_unet_create": [i32, i32, i32, ctypes.c_uint64, P(vp)],
         "sg_unet_destroy": [vp],
@@ -179,6 +182,17 @@ def sg_upload_bricks(vol, t, c, level, brick_xyz, host, stream=None):
     import numpy as np
     xyz = np.ascontiguousarray(brick_xyz, np.int32).reshape(-1, 3)
     _check(lib.sg_upload_bricks(vol, t, c, level, len(xyz), _ptr(xyz), _ptr(host), _stream(stream)))
+
+
+def sg_upload_brick_list(vol, t, c, nodes, host_ptrs, stream=None):
+    """Uploads bricks by node id from per-brick host pointers (ints, numpy
+    arrays or tensors); returns how many (a prefix of the list) were cached."""
+    import numpy as np
+    ids = np.ascontiguousarray(nodes, np.int32).reshape(-1)
+    ptrs = _ptr_array(host_ptrs) if len(ids) else None
+    done = ctypes.c_int32(0)
+    _check(lib.sg_upload_brick_list(vol, t, c, len(ids), _ptr(ids), ptrs, ctypes.byref(done), _stream(stream)))
+    return done.value
 
 
 def sg_set_transfer_function(vol, c, rgba, lo, hi, ref_step=0.5, stream=None):
@@ -358,3 +372,19 @@ def sg_unet_set_tensor_path(net, tcgen05=1):
 
 def sg_unet_check(net):
     _check(lib.sg_unet_check(net))
+
+
+def sg_read_ranges(vol, t, nnode, channels=1):
+    import numpy as np
+    out = np.empty((nnode, channels, 2), np.uint32)
+    _check(lib.sg_read_ranges(vol, t, _ptr(out), nnode))
+    return out
+
+
+def sg_read_requests(vol, slot, cap=1 << 16):
+    """Requested node ids of a selection (ascending), without the other outputs."""
+    import numpy as np
+    req = np.empty(cap, np.int32)
+    nreq = ctypes.c_int32(0)
+    _check(lib.sg_read_selection(vol, slot, None, 0, None, 0, _ptr(req), cap, ctypes.byref(nreq), None))
+    return req[: min(nreq.value, cap)].copy()

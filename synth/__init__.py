@@ -202,3 +202,39 @@ def volume_model(n_vox, extent_m):
     extent_m centred at the origin (uniform scale)."""
     s = extent_m / float(n_vox)
     return colmajor(scale_translate(s, np.full(3, -extent_m / 2.0)))
+
+
+def flythrough_poses(count=256, seed=3004, extent_m=1.0, ipd=0.064, fovy=100.0, width=1440, height=1600):
+    """Seeded Catmull-Rom fly-through that starts outside a volume of world
+    extent `extent_m` (centred at the origin) and wanders through its central
+    part; each pose looks a little ahead along the path. Returns a list of
+    (views[2], projs[2]) column-major float32."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    e = extent_m
+    start = _unit(rng) * 1.2 * e
+    pts = [start * 1.3, start] + [rng.uniform(-0.3 * e, 0.3 * e, 3) for _ in range(5)] + [rng.uniform(-0.3 * e, 0.3 * e, 3)]
+
+    def cr(p0, p1, p2, p3, t):
+        return 0.5 * (2 * p1 + (-p0 + p2) * t + (2 * p0 - 5 * p1 + 4 * p2 - p3) * t * t +
+                      (-p0 + 3 * p1 - 3 * p2 + p3) * t ** 3)
+
+    nseg = len(pts) - 3
+    path = []
+    for i in range(count + 1):
+        u = i / count * nseg
+        k = min(int(u), nseg - 1)
+        path.append(cr(pts[k], pts[k + 1], pts[k + 2], pts[k + 3], u - k))
+    proj = colmajor(perspective(fovy, width / height, 0.005, 10.0))
+    poses = []
+    for i in range(count):
+        head, ahead = path[i], path[i + 1]
+        f = ahead - head
+        if np.linalg.norm(f) < 1e-9:
+            f = -head
+        f = f / np.linalg.norm(f)
+        up = np.array([0.0, 0.0, 1.0]) if abs(f[2]) < 0.95 else np.array([0.0, 1.0, 0.0])
+        s = np.cross(f, up)
+        s /= np.linalg.norm(s)
+        views = [colmajor(look_at(head + k * 0.5 * ipd * s, head + k * 0.5 * ipd * s + f, up)) for k in (-1.0, 1.0)]
+        poses.append((views, [proj, proj]))
+    return poses

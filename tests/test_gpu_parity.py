@@ -190,3 +190,37 @@ def test_render_host_matches_device_render():
         assert np.array_equal(host[0].reshape(-1, 4), dev[0])
     finally:
         case.close()
+
+
+@pytest.mark.parametrize("brick,levels,kind", [(64, 3, "u16"), (128, 2, "u8")])
+def test_specialised_brick_edges_match_oracle_in_every_launch_shape(brick, levels, kind):
+    """Brick edges 32, 64 and 128 run kernels specialised on the edge (the
+    other edges run the generic one, covered above): the bench's 64^3 u16
+    bricks and 128^3 u8 cell bodies, against the oracle and bit for bit across
+    every launch shape."""
+    if kind == "u16":
+        case = _filament_case(dims=(256, 256, 256), brick=brick, levels=levels)
+    else:
+        cells = synth.cells_u8_box(256, 0, 0, 0, 256, 256, 256, seed=1004, cell=64)
+        case = GpuCase([cells], brick, levels, model=synth.volume_model(256, 0.5))
+        case.set_tfs([synth.tf_piecewise(2004, zero_alpha_points=2, zero_span=(60, 80))], [(0.0, 255.0)])
+    try:
+        sg, torch = case.sg, case.torch
+        W, H = 288, 320
+        (views, projs), = synth.head_poses(1, seed=3150 + brick, extent_m=0.5, width=W, height=H)
+        pose, _, gsel, ref = case.select(views, projs, W, H, tau=0.25)
+        compare_selection(gsel, ref)
+        imgs, cnts = case.render(pose, empty_skip=0)
+        for e in range(2):
+            compare_image(imgs[e], case.oracle_render(ref["leaf"], views[e], projs[e], W, H), cnts[e])
+        assert max(float(i[:, 3].max()) for i in imgs) > 0.2
+        skip, _ = case.render(pose, empty_skip=1)
+        assert np.array_equal(skip[0], imgs[0]) and np.array_equal(skip[1], imgs[1])
+        for persistent in (0, 1):
+            for tw, th, rpt in [(16, 8, 1), (8, 16, 1), (32, 4, 1), (8, 8, 1), (16, 16, 2), (32, 8, 2)]:
+                sg.sg_set_render_config(case.vol, persistent, tw, th, rpt)
+                got, _ = case.render(pose, empty_skip=1, counts=False)
+                assert np.array_equal(got[0], imgs[0]) and np.array_equal(got[1], imgs[1]), (persistent, tw, th, rpt)
+        sg.sg_set_render_config(case.vol)
+    finally:
+        case.close()

@@ -38,8 +38,8 @@ def _stereo(head, target, W, H, fovy=40.0, ipd=0.064):
     return views, [proj, proj]
 
 
-@pytest.mark.parametrize("index_ranges", [True])
-def test_streaming_frames_match_the_oracle_and_evict_lru(index_ranges):
+@pytest.mark.parametrize("mode", ["bricks", "list"])
+def test_streaming_frames_match_the_oracle_and_evict_lru(mode, index_ranges=True):
     import torch
     from paper_1804_08197_b300 import sg
     a = synth.filaments_u16(DIMS, seed=31, ntubes=18)
@@ -72,6 +72,19 @@ def test_streaming_frames_match_the_oracle_and_evict_lru(index_ranges):
             known[:] = True
 
         def upload(ids):
+            if mode == "list":
+                # one call per frame, by node id, coarse levels first
+                ids = sorted((int(i) for i in ids), key=lambda n: (-ovol.node_coords(n)[0], n))
+                host = []
+                for n in ids:
+                    L, b = ovol.node_coords(n)
+                    host.append(_brick(ovol, L, *b))
+                done = sg.sg_upload_brick_list(vol, 0, 0, ids, host)
+                assert 0 < done <= len(ids)
+                res = sg.sg_read_residency(vol, 0, ovol.node_count)
+                assert (res[ids[:done]] >= 0).all()
+                known[np.array(ids[:done], dtype=np.int64)] = True
+                return
             by_level = {}
             for i in ids:
                 L, b = ovol.node_coords(int(i))
