@@ -223,43 +223,75 @@ def batched_4d(sg, torch, dev, reps=10):
     return res
 
 
-def streaming_flythrough(sg, torch, dev, n_vox=1024, brick=64, levels=4, cache_frac=0.25, count=256,
-                         budget_bytes=256 << 20):
-    """Large volume under a memory budget, scaled: cell bodies with membranes
-    (u8, 64^3 bricks + apron) at the voxel size of 4096 voxels over 1 m,
-    served from a pinned host brick store (every brick with its apron, in node
-    order, plus the index of brick value ranges) through a device cache that
-    holds `cache_frac` of the bricks. Per frame: select (missing children are
-    requested, the parent renders), upload the requests coarse-first under a
-    per-frame byte budget in one call, render both eyes. Reports frame time
-    p50/p99 (wall clock, synchronised per frame) and the cache hit rate."""
+def host_mem_available():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def streaming_flythrough(sg, torch, dev, full=None, count=256, budget_bytes=256 << 20):
+    """Large volume under a memory budget: cell bodies with membranes (u8,
+    seed 1004, 4096 voxels over 1 m) served from a pinned host brick store
+    (every brick with its apron, in node order, plus the index of brick value
+    ranges) through a device brick cache. Per frame: select (missing children
+    are requested, the parent renders), upload the requests coarse-first under
+    a per-frame byte budget in one call, render both eyes. Reports frame time
+    p50/p99 (wall clock, synchronised per frame) and the cache hit rate.
+
+    full: 4096^3 in 128^3 bricks, 6 levels, 40 GB cache (level 0 generated on
+    the GPU, 82 GB pinned host store); else the 1024^3 stand-in (64^3 bricks,
+    4 levels, cache of a quarter of the bricks). None picks full when the
+    device and the host have room for it."""
     import synth
+    free_dev, _ = torch.cuda.mem_get_info(dev)
+    if full is None:
+        full = free_dev > 190e9 and host_mem_available() > 130e9
+    if full:
+        n_vox, brick, levels, cache_bytes = 4096, 128, 6, 40_000_000_000
+    else:
+        n_vox, brick, levels, cache_bytes = 1024, 64, 4, None
     extent = n_vox / 4096.0
     model = synth.volume_model(n_vox, extent)
-    t0 = time.perf_counter()
-    a = synth.cells_u8_box(n_vox, 0, 0, 0, n_vox, n_vox, n_vox, seed=1004, cell=64)
-    gen_s = time.perf_counter() - t0
     # the container: built once by the library's own ingest into a resident
     # volume, then read back brick by brick into pinned host memory
+    t0 = time.perf_counter()
+    d = torch.empty((n_vox, n_vox, n_vox), dtype=torch.uint8, device=dev)
+    if full:
+        synth.cells_u8_device(n_vox, d.data_ptr(), seed=1004, cell=64)
+    else:
+        d.copy_(torch.from_numpy(synth.cells_u8_box(n_vox, 0, 0, 0, n_vox, n_vox, n_vox, seed=1004, cell=64)))
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
     src = sg.sg_volume_create((n_vox,) * 3, sg.SG_U8, brick, levels, model=model)
-    d = torch.from_numpy(a).to(dev)
     sg.sg_upload_volume_device(src, 0, 0, d.data_ptr())
     torch.cuda.synchronize()
-    del d, a
+    del d
+    torch.cuda.empty_cache()
     geo = []  # (level, bx, by, bz) by node id
     for L in range(levels):
         nb = -(-(-(-n_vox // (1 << L))) // brick)
         geo += [(L, x, y, z) for z in range(nb) for y in range(nb) for x in range(nb)]
     nodes = len(geo)
     R3 = (brick + 2) ** 3
-    store = torch.empty(nodes * R3, dtype=torch.uint8, pin_memory=True)
-    host = store.numpy()
+    # page-locked in place (exactly the bytes needed; a caching pinned
+    # allocator may round an 82 GB request up to the next power of two)
+    host = np.empty(nodes * R3, np.uint8)
+    cudart = torch.cuda.cudart()
+    rc = cudart.cudaHostRegister(host.ctypes.data, host.nbytes, 0)
+    if int(rc) != 0:
+        raise RuntimeError(f"cudaHostRegister of the brick store failed: {rc}")
     for i, (L, x, y, z) in enumerate(geo):
         sg.sg_read_brick(src, 0, 0, L, x, y, z, host[i * R3:(i + 1) * R3])
     ranges = sg.sg_read_ranges(src, 0, nodes)
     sg.sg_volume_destroy(src)
+    ingest_s = time.perf_counter() - t0
     slot_bytes = (R3 + 255) // 256 * 256
-    cache_bricks = int(cache_frac * nodes)
+    cache_bricks = cache_bytes // slot_bytes if cache_bytes else nodes // 4
     vol = sg.sg_volume_create((n_vox,) * 3, sg.SG_U8, brick, levels, model=model,
                               device_pool_bytes=cache_bricks * slot_bytes)
     tf = synth.tf_piecewise(2004, zero_alpha_points=2, zero_span=(60, 80))
@@ -269,7 +301,7 @@ def streaming_flythrough(sg, torch, dev, n_vox=1024, brick=64, levels=4, cache_f
         nl = sum(1 for g in geo if g[0] == L)
         sg.sg_set_brick_ranges(vol, 0, 0, L, np.array([g[1:] for g in geo[off:off + nl]]), ranges[off:off + nl, 0, :])
         off += nl
-    base = store.data_ptr()
+    base = host.ctypes.data
     top = [i for i, g in enumerate(geo) if g[0] == levels - 1]
     sg.sg_upload_brick_list(vol, 0, 0, top, [base + i * R3 for i in top])
     poses = synth.flythrough_poses(count, seed=3004, extent_m=extent, width=W_EYE, height=H_EYE)
@@ -294,17 +326,21 @@ def streaming_flythrough(sg, torch, dev, n_vox=1024, brick=64, levels=4, cache_f
         torch.cuda.synchronize()
         frame_ms.append((time.perf_counter() - t0) * 1e3)
     sg.sg_volume_destroy(vol)
+    cudart.cudaHostUnregister(host.ctypes.data)
+    del host
     fm, um = np.array(frame_ms), np.array(up_ms)
-    return {"workload": f"large volume under a memory budget, scaled: {n_vox}^3 u8 cell bodies + membranes "
-                        f"(voxel size of 4096 voxels per m), {brick}^3 bricks, {levels} levels, device cache "
-                        f"{cache_bricks} of {nodes} bricks, pinned host brick store, {count}-pose fly-through, "
-                        f"2x{W_EYE}x{H_EYE}, <= {budget_bytes >> 20} MiB uploaded per frame",
+    kind = "full size" if full else "scaled stand-in"
+    return {"workload": f"large volume under a memory budget ({kind}): {n_vox}^3 u8 cell bodies + membranes "
+                        f"(4096 voxels per m), {brick}^3 bricks, {levels} levels, device cache "
+                        f"{cache_bricks} of {nodes} bricks ({cache_bricks * slot_bytes / 1e9:.1f} GB), pinned host "
+                        f"brick store ({nodes * R3 / 1e9:.1f} GB), {count}-pose fly-through, 2x{W_EYE}x{H_EYE}, "
+                        f"<= {budget_bytes >> 20} MiB uploaded per frame",
             "frame_ms_p50": round(float(np.percentile(fm, 50)), 3),
             "frame_ms_p99": round(float(np.percentile(fm, 99)), 3),
             "upload_ms_p99": round(float(np.percentile(um, 99)), 3),
             "cache_hit_rate": round(float(np.mean(hits)), 4),
             "h2d_gbs": round(up_bricks * R3 / (um.sum() / 1e3) / 1e9, 2) if up_bricks else None,
-            "uploaded_bricks": int(up_bricks), "generate_s": round(gen_s, 1)}
+            "uploaded_bricks": int(up_bricks), "generate_s": round(gen_s, 1), "ingest_and_store_s": round(ingest_s, 1)}
 
 
 def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=4000, steps_per_pair=4, eval_poses=16,
@@ -461,7 +497,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     n_vox = args.volume
     vol_host, tf_table, poses, model = make_inputs(n_vox)
-    vol = sg.sg_volume_create((n_vox,) * 3, sg.SG_U16, BRICK, LEVELS, model=model)
+    vol = sg.sg_volume_create((n_vox,) * 3, sg.SG_U16, BRICK, LEVELS, model=model, skip_block=args.skip_block)
     d0 = torch.from_numpy(vol_host.view(np.int16)).to(dev)
     sg.sg_upload_volume_device(vol, 0, 0, d0.data_ptr())
     torch.cuda.synchronize()
@@ -588,6 +624,10 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the batched 4D and learned measurements")
     ap.add_argument("--learned-pairs", type=int, default=4000,
                     help="training pairs for the learned path (20000 = the full budget, ~4 min)")
+    ap.add_argument("--skip-block", type=int, default=0,
+                    help="empty-space skipping cell edge in voxels (0 = the library's default)")
+    ap.add_argument("--streaming-size", choices=["auto", "full", "scaled"], default="auto",
+                    help="large-volume fly-through at 4096^3 (full), at 1024^3 (scaled), or full when it fits")
     ap.add_argument("--only", choices=["net", "streaming"], default=None,
                     help="net: only U-Net forwards at 2x720x800 (a small case for profiling the convolutions); "
                          "streaming: only the large-volume fly-through")
@@ -611,7 +651,8 @@ def main():
         import torch
         from paper_1804_08197_b300 import sg
         torch.cuda.set_device(local_rank)
-        print(json.dumps(streaming_flythrough(sg, torch, torch.device("cuda"))), flush=True)
+        full = {"auto": None, "full": True, "scaled": False}[args.streaming_size]
+        print(json.dumps(streaming_flythrough(sg, torch, torch.device("cuda"), full=full)), flush=True)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -72,7 +72,9 @@ typedef struct {
   int32_t brick_size;         /* B: multiple of 8, 8..256 */
   int32_t apron;              /* must be 1 */
   int32_t lod_levels;         /* 1..16 */
-  int32_t reserved;
+  int32_t skip_block;         /* edge in voxels of the empty-space skipping cells within a brick:
+                                 2, 4, 8 or 16, dividing brick_size, at most 32 per brick edge;
+                                 0 = the finest of 2, 4, 8 with at most 32 cells per edge */
   uint64_t device_pool_bytes; /* 0: every brick of every level resident; else the
                                  brick cache budget (bricks stream in by LRU) */
   float model[16];            /* voxel space -> world, column major; uniform scale */
@@ -92,7 +94,7 @@ sg_status sg_volume_destroy(sg_volume* vol);
  * fastest, caller-owned device memory). The library builds levels
  * 1..lod_levels-1 with the box filter, packs every brick with its apron into
  * the pool and records each brick's value range (min/max over the brick and
- * its apron) and the ranges of its 8^3-voxel sub-blocks. Only valid when
+ * its apron) and the ranges of its skip_block^3-voxel sub-blocks. Only valid when
  * every brick is resident (device_pool_bytes == 0). Temporary device memory:
  * about 1/7 of the level-0 bytes, released before return. Errors:
  * INVALID_ARG, STATE (pooled volume), OOM, CUDA. */
@@ -142,7 +144,7 @@ sg_status sg_set_brick_ranges(sg_volume* vol, int t, int c, int level, int n, co
  * x = clamp((v - lo) / (hi - lo), 0, 1), table position q = x (n - 1), with
  * linear interpolation between entries floor(q) and floor(q) + 1. A sample
  * spaced s apart uses opacity 1 - (1 - alpha)^(s / ref_step). Also derives
- * which blocks and 8^3 sub-blocks are transparent under the table and marks
+ * which blocks and sub-blocks are transparent under the table and marks
  * earlier selections stale. Errors: INVALID_ARG (n < 2 or > 4096, hi <= lo,
  * ref_step <= 0), OOM, CUDA. */
 sg_status sg_set_transfer_function(sg_volume* vol, int c, const float* rgba, int n, float lo, float hi,
@@ -250,7 +252,7 @@ typedef struct {
   float step;             /* level-0 sample spacing in voxels (> 0); level L samples every 2^L-th point */
   float term_alpha;       /* early ray termination threshold, e.g. 0.99 (<= 0: 0.99) */
   int32_t mode;           /* SG_MODE_EMISSION_ABSORPTION */
-  int32_t empty_skip;     /* 1: skip transparent blocks and 8^3 sub-blocks (output unchanged) */
+  int32_t empty_skip;     /* 1: skip transparent blocks and sub-blocks (output unchanged) */
   uint32_t* sample_count[2]; /* optional device buffers (W*H per eye): samples composited per pixel */
   unsigned long long* sample_total; /* optional device counter: incremented by the samples composited */
 } sg_render_params;

@@ -300,6 +300,11 @@ sg_status sg_volume_create(const sg_volume_desc* d, sg_volume** out) {
                "brick_size must be a multiple of 8 in [8, 256]");
   SG_CHECK_ARG(d->apron == 1, "apron must be 1");
   SG_CHECK_ARG(d->lod_levels >= 1 && d->lod_levels <= kMaxLevels, "lod_levels must be 1..16");
+  // default: the finest cell that keeps at most kMaxSubPerEdge cells per brick edge
+  const int sub = d->skip_block ? d->skip_block : (d->brick_size <= 64 ? 2 : (d->brick_size <= 128 ? 4 : 8));
+  SG_CHECK_ARG((sub == 2 || sub == 4 || sub == 8 || sub == 16) && d->brick_size % sub == 0 &&
+                   d->brick_size / sub <= kMaxSubPerEdge,
+               "skip_block must be 0 or 2/4/8/16 dividing brick_size, at most 32 cells per brick edge");
 
   sg_volume* v = new (std::nothrow) sg_volume();
   if (!v) {
@@ -335,7 +340,9 @@ sg_status sg_volume_create(const sg_volume_desc* d, sg_volume** out) {
   }
   const int R = v->B + 2;
   v->brick_bytes = ((size_t)R * R * R * v->esize + 255) / 256 * 256;
-  v->nsub = v->B / kSub;
+  v->sub = sub;
+  v->sub_shift = sub == 2 ? 1 : (sub == 4 ? 2 : (sub == 8 ? 3 : 4));
+  v->nsub = v->B / sub;
   const int ns3 = v->nsub * v->nsub * v->nsub;
   v->sub_words = (ns3 + 63) / 64;
   const int top = v->levels - 1;

@@ -81,12 +81,13 @@ __global__ void k_pack(const T* __restrict__ lvl, int64_t nx, int64_t ny, int64_
   }
 }
 
-// Min/max of every 8^3 sub-block's trilinear footprint: sub-block s covers
-// level-L positions [bB + 8s, bB + 8s + 8] per axis, whose samples read
-// brick-local voxels 8s .. 8s + 9.
+// Min/max of every sub-block's trilinear footprint: with sub-block edge S,
+// sub-block s covers level-L positions [bB + Ss, bB + Ss + S] per axis, whose
+// samples read brick-local voxels Ss .. Ss + S + 1.
 template <typename T>
 __global__ void k_subranges(const uint8_t* __restrict__ pool, size_t brick_bytes, int nch, int c, int B, int nsub,
-                            const int32_t* __restrict__ slots, int32_t slot_base, uint16_t* __restrict__ subrange) {
+                            int S, const int32_t* __restrict__ slots, int32_t slot_base,
+                            uint16_t* __restrict__ subrange) {
   const int32_t slot = slots ? slots[blockIdx.x] : slot_base + (int32_t)blockIdx.x;
   if (slot < 0) return;
   const T* src = reinterpret_cast<const T*>(pool + ((size_t)slot * nch + c) * brick_bytes);
@@ -95,11 +96,10 @@ __global__ void k_subranges(const uint8_t* __restrict__ pool, size_t brick_bytes
   for (int s = threadIdx.x; s < ns3; s += blockDim.x) {
     int sx = s % nsub, sy = (s / nsub) % nsub, sz = s / (nsub * nsub);
     uint32_t mn = 0xffffffffu, mx = 0u;
-    for (int z = 0; z < kSub + 2; ++z)
-      for (int y = 0; y < kSub + 2; ++y) {
-        const T* row = src + ((size_t)(sz * kSub + z) * R + (sy * kSub + y)) * R + sx * kSub;
-#pragma unroll
-        for (int x = 0; x < kSub + 2; ++x) {
+    for (int z = 0; z < S + 2; ++z)
+      for (int y = 0; y < S + 2; ++y) {
+        const T* row = src + ((size_t)(sz * S + z) * R + (sy * S + y)) * R + sx * S;
+        for (int x = 0; x < S + 2; ++x) {
           uint32_t v = row[x];
           mn = min(mn, v);
           mx = max(mx, v);
@@ -171,10 +171,10 @@ cudaError_t launch_pack_level(sg_volume* v, int t, int c, int L, const void* dat
   if (!v->pooled) {
     int32_t base = (int32_t)((int64_t)t * v->nodes + g.off);
     if (v->esize == 1)
-      k_subranges<uint8_t><<<(unsigned)nblk, 256, 0, s>>>(v->d_pool, v->brick_bytes, v->nch, c, v->B, v->nsub,
+      k_subranges<uint8_t><<<(unsigned)nblk, 256, 0, s>>>(v->d_pool, v->brick_bytes, v->nch, c, v->B, v->nsub, v->sub,
                                                            nullptr, base, v->d_subrange);
     else
-      k_subranges<uint16_t><<<(unsigned)nblk, 256, 0, s>>>(v->d_pool, v->brick_bytes, v->nch, c, v->B, v->nsub,
+      k_subranges<uint16_t><<<(unsigned)nblk, 256, 0, s>>>(v->d_pool, v->brick_bytes, v->nch, c, v->B, v->nsub, v->sub,
                                                             nullptr, base, v->d_subrange);
     e = cudaGetLastError();
   }
@@ -184,10 +184,10 @@ cudaError_t launch_pack_level(sg_volume* v, int t, int c, int L, const void* dat
 cudaError_t launch_subranges(sg_volume* v, const int32_t* d_slots, int nslots, int c, cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;
   if (v->esize == 1)
-    k_subranges<uint8_t><<<nslots, 256, 0, s>>>(v->d_pool, v->brick_bytes, v->nch, c, v->B, v->nsub, d_slots, 0,
+    k_subranges<uint8_t><<<nslots, 256, 0, s>>>(v->d_pool, v->brick_bytes, v->nch, c, v->B, v->nsub, v->sub, d_slots, 0,
                                                 v->d_subrange);
   else
-    k_subranges<uint16_t><<<nslots, 256, 0, s>>>(v->d_pool, v->brick_bytes, v->nch, c, v->B, v->nsub, d_slots, 0,
+    k_subranges<uint16_t><<<nslots, 256, 0, s>>>(v->d_pool, v->brick_bytes, v->nch, c, v->B, v->nsub, v->sub, d_slots, 0,
                                                  v->d_subrange);
   return cudaGetLastError();
 }

@@ -13,7 +13,7 @@ namespace sg {
 constexpr int kMaxLevels = 16;
 constexpr int kMaxCh = 4;
 constexpr int kMaxSlots = 256;   // selection slots per volume
-constexpr int kSub = 8;          // sub-block edge (level-L voxels) for empty skipping
+constexpr int kMaxSubPerEdge = 32;  // empty-skipping cells per brick edge (distance map fits shared memory)
 constexpr int kMaxTF = 4096;
 
 // A leaf-map entry tells the ray caster what renders one level-0 block cell.
@@ -74,6 +74,7 @@ struct sg_volume {
   int64_t nodes = 0;        // per time point
   int64_t ncell = 0;        // level-0 block cells
   int64_t max_level_nodes = 0;
+  int sub = 0, sub_shift = 0;  // empty-skipping cell edge (level-L voxels) and its log2
   int nsub = 0;             // sub-blocks per axis in a brick
   int sub_words = 0;        // 64-bit words of sub-block empty bits per slot
 

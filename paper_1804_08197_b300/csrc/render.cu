@@ -3,7 +3,7 @@
 // compositing front to back with early termination. Blocks of the selected
 // octree cut ("Octree Representation") are visited front to back along each
 // ray in a single pass: the ray walks the level-0 block grid (leaf map), jumps
-// a whole block of level L at once, and inside a block walks 8^3-voxel
+// a whole block of level L at once, and inside a block walks small cubic
 // sub-blocks so that transparent ones cost no samples.
 //
 // Sample lattice: t0 + k step (k >= 0, t in level-0 voxels, t0 = volume
@@ -24,7 +24,7 @@ constexpr int kTileW = 16, kTileH = 8, kThreads = kTileW * kTileH;
 // diagnostic build only: per-event counters of the ray loop
 // [0] samples [1] sub-block jumps [2] rendered block entries [3] skipped block
 // entries [4] warp loop trips [5] lane loop iterations [6] rays that hit
-// [7] sub-block lookups that found an opaque sub-block
+// [7] samples that changed the accumulated opacity (alpha > 0)
 __device__ unsigned long long g_events[8];
 #define SG_EV(i, n) ev[i] += (n)
 #else
@@ -62,7 +62,7 @@ struct Args {
   size_t brick_bytes;
   const uint8_t* subdist;   // [slot][nsub^3] distance to a non-transparent sub-block
   const float4* lut;   // [nch][levels][kMaxTF]
-  int nch, levels, B, nsub, sub_words;
+  int nch, levels, B, nsub, sub_words, sub, sub_shift;
   int nb0[3];
   float dims0[3];
   int n[kMaxCh];
@@ -168,9 +168,10 @@ __device__ __forceinline__ bool composite_sample(const Args& a, const T* __restr
   return acc.w >= a.term;
 }
 
-// exit distance of a ray from the slab [lo, hi] along one axis
-__device__ inline float axis_exit(float o, float d, float inv, float lo, float hi) {
-  return d > 0.0f ? (hi - o) * inv : (d < 0.0f ? (lo - o) * inv : INFINITY);
+// exit distance of a ray from a slab along one axis, given the bound it
+// leaves through (the upper one for d > 0, the lower one for d < 0)
+__device__ __forceinline__ float exit_through(float o, float d, float inv, float bnd) {
+  return d != 0.0f ? (bnd - o) * inv : INFINITY;
 }
 
 __device__ inline int cell_of(float p, float invB, int lo, int hi) {
@@ -179,7 +180,7 @@ __device__ inline int cell_of(float p, float invB, int lo, int hi) {
 
 // One ray: pixel (px, py) of image J; acc = premultiplied RGBA, cnt = samples
 // composited. A single flat loop advances the ray by one event per
-// iteration (take a sample, jump over a transparent 8^3 sub-block, or move to
+// iteration (take a sample, jump over transparent sub-blocks, or move to
 // the next block), so the lanes of a warp stay in one loop instead of
 // diverging across nested ones.
 template <typename T, int BK>
@@ -233,6 +234,8 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
   float texit = -1.0f;  // unclipped exit
   uint32_t slot = 0;
   const T* brick0 = nullptr;               // the current block's brick (channel 0)
+  const uint8_t* subd = nullptr;           // its sub-block distance map
+  const int nsub3 = a.nsub * a.nsub * a.nsub;
   float3 lo = make_float3(0.f, 0.f, 0.f);  // block origin, level-0 voxels
   float sL = 1.0f;                         // 2^-L
   bool render = false;
@@ -254,36 +257,30 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
         const int nl_x = (cx >> L) << L, nl_y = (cy >> L) << L, nl_z = (cz >> L) << L;
         const int nh_x = min(nl_x + (1 << L), a.nb0[0]), nh_y = min(nl_y + (1 << L), a.nb0[1]),
                   nh_z = min(nl_z + (1 << L), a.nb0[2]);
-        if (ax == 0) {
-          const int c = d.x > 0.0f ? nh_x : nl_x - 1;
-          if (c < 0 || c >= a.nb0[0]) break;
-          cy = cell_of(fmaf(texit, d.y, o.y), invB, nl_y, nh_y - 1);
-          cz = cell_of(fmaf(texit, d.z, o.z), invB, nl_z, nh_z - 1);
-          cx = c;
-        } else if (ax == 1) {
-          const int c = d.y > 0.0f ? nh_y : nl_y - 1;
-          if (c < 0 || c >= a.nb0[1]) break;
-          cx = cell_of(fmaf(texit, d.x, o.x), invB, nl_x, nh_x - 1);
-          cz = cell_of(fmaf(texit, d.z, o.z), invB, nl_z, nh_z - 1);
-          cy = c;
-        } else {
-          const int c = d.z > 0.0f ? nh_z : nl_z - 1;
-          if (c < 0 || c >= a.nb0[2]) break;
-          cx = cell_of(fmaf(texit, d.x, o.x), invB, nl_x, nh_x - 1);
-          cy = cell_of(fmaf(texit, d.y, o.y), invB, nl_y, nh_y - 1);
-          cz = c;
-        }
+        // the neighbour across the exit face along axis ax; on the other two
+        // axes the cell of the exit point, clamped to the block just left
+        // (all three formed, the exit axis then replaced: no 3-way branch)
+        const int c_ax = ax == 0 ? (d.x > 0.0f ? nh_x : nl_x - 1)
+                                 : (ax == 1 ? (d.y > 0.0f ? nh_y : nl_y - 1) : (d.z > 0.0f ? nh_z : nl_z - 1));
+        const int n_ax = ax == 0 ? a.nb0[0] : (ax == 1 ? a.nb0[1] : a.nb0[2]);
+        if (c_ax < 0 || c_ax >= n_ax) break;
+        const int ncx = cell_of(fmaf(texit, d.x, o.x), invB, nl_x, nh_x - 1);
+        const int ncy = cell_of(fmaf(texit, d.y, o.y), invB, nl_y, nh_y - 1);
+        const int ncz = cell_of(fmaf(texit, d.z, o.z), invB, nl_z, nh_z - 1);
+        cx = ax == 0 ? c_ax : ncx;
+        cy = ax == 1 ? c_ax : ncy;
+        cz = ax == 2 ? c_ax : ncz;
         // lattice points before the exit belong to the block just left
         k = first_k_at(tend, t0, a, kb);
       }
       const uint32_t e = __ldg(J.leaf + ((size_t)cz * a.nb0[1] + cy) * a.nb0[0] + cx);
       L = e & 15;
       const int nl_x = (cx >> L) << L, nl_y = (cy >> L) << L, nl_z = (cz >> L) << L;
-      lo = make_float3((float)nl_x * Bf, (float)nl_y * Bf, (float)nl_z * Bf);
-      const float span = (float)(B << L);
-      const float ex = axis_exit(o.x, d.x, inv.x, lo.x, fminf(lo.x + span, a.dims0[0]));
-      const float ey = axis_exit(o.y, d.y, inv.y, lo.y, fminf(lo.y + span, a.dims0[1]));
-      const float ez = axis_exit(o.z, d.z, inv.z, lo.z, fminf(lo.z + span, a.dims0[2]));
+      lo = make_float3(u2f(nl_x) * Bf, u2f(nl_y) * Bf, u2f(nl_z) * Bf);
+      const float span = u2f(B << L);
+      const float ex = exit_through(o.x, d.x, inv.x, d.x > 0.0f ? fminf(lo.x + span, a.dims0[0]) : lo.x);
+      const float ey = exit_through(o.y, d.y, inv.y, d.y > 0.0f ? fminf(lo.y + span, a.dims0[1]) : lo.y);
+      const float ez = exit_through(o.z, d.z, inv.z, d.z > 0.0f ? fminf(lo.z + span, a.dims0[2]) : lo.z);
       ax = 0;
       texit = ex;
       if (ey < texit) { texit = ey; ax = 1; }
@@ -297,6 +294,7 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
       k = (k + kstep - 1) & ~(kstep - 1);
       slot = (e & ~kLeafNone) >> 5;
       brick0 = reinterpret_cast<const T*>(a.pool + (size_t)slot * a.nch * a.brick_bytes);
+      subd = a.subdist + (size_t)slot * nsub3;
       sL = __int_as_float((127 - L) << 23);
       continue;
     }
@@ -305,21 +303,22 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
     // brick-local coordinate: level-L position - block origin + 1 (apron) - 0.5 (voxel centre)
     const float lx = fmaf(px0 - lo.x, sL, 0.5f), ly = fmaf(py0 - lo.y, sL, 0.5f), lz = fmaf(pz0 - lo.z, sL, 0.5f);
     if (a.empty_skip) {
-      const int sx = min(max(floor_i(lx - 0.5f) >> 3, 0), nsm);
-      const int sy = min(max(floor_i(ly - 0.5f) >> 3, 0), nsm);
-      const int sz = min(max(floor_i(lz - 0.5f) >> 3, 0), nsm);
+      const int sx = min(max(floor_i(lx - 0.5f) >> a.sub_shift, 0), nsm);
+      const int sy = min(max(floor_i(ly - 0.5f) >> a.sub_shift, 0), nsm);
+      const int sz = min(max(floor_i(lz - 0.5f) >> a.sub_shift, 0), nsm);
       const int sid = (sz * a.nsub + sy) * a.nsub + sx;
-      const int D = __ldg(a.subdist + (size_t)slot * a.nsub * a.nsub * a.nsub + sid);
+      const int D = __ldg(subd + sid);
       if (D > 0) {
         // every sub-block within D - 1 steps is transparent: jump to the exit
         // of that cube (clipped to the brick); the lattice points skipped
         // have alpha exactly 0
-        const float S = (float)(kSub << L);
-        const float bx0 = fmaf((float)max(sx - D + 1, 0), S, lo.x), bx1 = fmaf((float)min(sx + D, a.nsub), S, lo.x);
-        const float by0 = fmaf((float)max(sy - D + 1, 0), S, lo.y), by1 = fmaf((float)min(sy + D, a.nsub), S, lo.y);
-        const float bz0 = fmaf((float)max(sz - D + 1, 0), S, lo.z), bz1 = fmaf((float)min(sz + D, a.nsub), S, lo.z);
-        const float ts = fminf(fminf(axis_exit(o.x, d.x, inv.x, bx0, bx1), axis_exit(o.y, d.y, inv.y, by0, by1)),
-                               fminf(axis_exit(o.z, d.z, inv.z, bz0, bz1), tend));
+        const float S = u2f(a.sub << L);
+        const int ex_i = d.x > 0.0f ? min(sx + D, a.nsub) : max(sx - D + 1, 0);
+        const int ey_i = d.y > 0.0f ? min(sy + D, a.nsub) : max(sy - D + 1, 0);
+        const int ez_i = d.z > 0.0f ? min(sz + D, a.nsub) : max(sz - D + 1, 0);
+        const float ts = fminf(fminf(exit_through(o.x, d.x, inv.x, fmaf(u2f(ex_i), S, lo.x)),
+                                     exit_through(o.y, d.y, inv.y, fmaf(u2f(ey_i), S, lo.y))),
+                               fminf(exit_through(o.z, d.z, inv.z, fmaf(u2f(ez_i), S, lo.z)), tend));
         // a rounded-up target may skip a point lying within rounding of the
         // exit: it is inside the cube's footprint margin, alpha 0, exact
         k = max(ceil_i((ts - t0) * a.inv_step), k + 1);
@@ -327,11 +326,17 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
         SG_EV(1, 1);
         continue;
       }
-      SG_EV(7, 1);
     }
     ++cnt;
     SG_EV(0, 1);
+#ifdef SG_RENDER_EVENT_STATS
+    const float w_before = acc.w;
+    const bool stop = composite_sample<T, BK>(a, brick0, L, lx, ly, lz, acc);
+    SG_EV(7, acc.w != w_before ? 1 : 0);
+    if (stop) break;
+#else
     if (composite_sample<T, BK>(a, brick0, L, lx, ly, lz, acc)) break;
+#endif
     k += kstep;
   }
 #ifdef SG_RENDER_EVENT_STATS
@@ -497,6 +502,8 @@ Args make_args(const sg_volume* v, const sg_render_params* prm) {
   a.B = v->B;
   a.nsub = v->nsub;
   a.sub_words = v->sub_words;
+  a.sub = v->sub;
+  a.sub_shift = v->sub_shift;
   for (int k = 0; k < 3; ++k) {
     a.nb0[k] = v->geom[0].nb[k];
     a.dims0[k] = (float)v->geom[0].dims[k];

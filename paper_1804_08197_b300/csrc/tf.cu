@@ -1,6 +1,6 @@
 // Transfer-function preparation ("DVR Techniques": transfer functions tau
 // and T; "Visualization Enhancements": one table per channel).
-//  - which blocks / 8^3 sub-blocks are transparent under the tables
+//  - which blocks and sub-blocks (skip_block^3 voxels) are transparent under the tables
 //    (alpha exactly 0 over their whole value range), used to drop subtrees
 //    during selection and to skip work while ray casting;
 //  - per-level opacity-corrected tables for the current sample spacing.
@@ -90,7 +90,7 @@ __global__ void k_sub_empty(TFParams p, const uint16_t* __restrict__ subrange, i
   }
 }
 
-// Chebyshev distance, in sub-blocks, from every 8^3 sub-block of a brick to
+// Chebyshev distance, in sub-blocks, from every sub-block of a brick to
 // the nearest non-transparent one of the same brick: 0 = not transparent,
 // D > 0 = every sub-block within D - 1 steps (26-neighbourhood) is
 // transparent, so a ray may cross that whole cube without a sample. Computed

@@ -38,7 +38,7 @@ class SGError(RuntimeError):
 class sg_volume_desc(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int32 * 3), ("dtype", ctypes.c_int32), ("channels", ctypes.c_int32),
                 ("timepoints", ctypes.c_int32), ("brick_size", ctypes.c_int32), ("apron", ctypes.c_int32),
-                ("lod_levels", ctypes.c_int32), ("reserved", ctypes.c_int32), ("device_pool_bytes", ctypes.c_uint64),
+                ("lod_levels", ctypes.c_int32), ("skip_block", ctypes.c_int32), ("device_pool_bytes", ctypes.c_uint64),
                 ("model", ctypes.c_float * 16)]
 
 
@@ -153,7 +153,7 @@ def sg_version():
 
 
 def sg_volume_create(dims, dtype, brick_size, lod_levels, channels=1, timepoints=1, apron=1,
-                     device_pool_bytes=0, model=None):
+                     device_pool_bytes=0, model=None, skip_block=0):
     d = sg_volume_desc()
     d.dims[:] = [int(x) for x in dims]
     d.dtype = dtype
@@ -163,6 +163,7 @@ def sg_volume_create(dims, dtype, brick_size, lod_levels, channels=1, timepoints
     d.apron = apron
     d.lod_levels = lod_levels
     d.device_pool_bytes = device_pool_bytes
+    d.skip_block = skip_block
     m = [1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1] if model is None else [float(x) for x in model]
     d.model[:] = m
     h = ctypes.c_void_p()

@@ -19,7 +19,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "synth.c")
 _LIB = os.path.join(_HERE, "libsynth.so")
+_GPU_SRC = os.path.join(_HERE, "synth_gpu.cu")
+_GPU_LIB = os.path.join(_HERE, "libsynth_gpu.so")
 _lib = None
+_gpu_lib = None
 
 
 def build(force=False):
@@ -27,6 +30,16 @@ def build(force=False):
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", _SRC, "-o", _LIB, "-lm"])
     return _LIB
+
+
+def build_gpu(force=False):
+    """Compile the GPU twin of the cell-body generator with nvcc (sm_103a)."""
+    if force or not os.path.exists(_GPU_LIB) or os.path.getmtime(_GPU_LIB) < os.path.getmtime(_GPU_SRC):
+        nvcc = "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc"
+        subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-shared",
+                               "-Xcompiler", "-fPIC", _GPU_SRC, "-o", _GPU_LIB + ".tmp"])
+        os.replace(_GPU_LIB + ".tmp", _GPU_LIB)
+    return _GPU_LIB
 
 
 def _load():
@@ -41,6 +54,7 @@ def _load():
         _lib.sy_blobs_u16.argtypes = [vp, i32, i32, i32, u64, i32, i32, i32, dbl]
         _lib.sy_cells_u8_box.argtypes = [vp, ctypes.c_long, u64, ctypes.c_long, ctypes.c_long,
                                          ctypes.c_long, i32, i32, i32, i32]
+        _lib.sy_cell_table.argtypes = [vp, ctypes.c_long, u64, i32]
     return _lib
 
 
@@ -88,6 +102,27 @@ def cells_u8_box(N, x0, y0, z0, sx, sy, sz, seed=1004, cell=64):
     out = np.empty((sz, sy, sx), np.uint8)
     _load().sy_cells_u8_box(_ptr(out), N, seed, x0, y0, z0, sx, sy, sz, cell)
     return out
+
+
+def cells_u8_device(N, dev_ptr, seed=1004, cell=64, z0=0, nz=None):
+    """Slices [z0, z0 + nz) of the same cell-body volume as cells_u8_box,
+    generated on the current GPU into device memory at dev_ptr (nz * N * N
+    bytes, x fastest). The cell parameters come from the CPU code; distances
+    and noise are FP32, so a small fraction of voxels (sphere boundaries,
+    rounding of the noisy value) may differ from cells_u8_box."""
+    global _gpu_lib
+    nz = N - z0 if nz is None else nz
+    if _gpu_lib is None:
+        build_gpu()
+        _gpu_lib = ctypes.CDLL(_GPU_LIB)
+        _gpu_lib.sy_cells_u8_gpu.argtypes = [ctypes.c_void_p, ctypes.c_long, ctypes.c_uint64, ctypes.c_long,
+                                             ctypes.c_long, ctypes.c_int, ctypes.c_void_p, ctypes.c_long]
+    ng = (N + cell - 1) // cell
+    table = np.empty(ng * ng * ng * 8, np.float32)
+    _load().sy_cell_table(_ptr(table), N, seed, cell)
+    err = _gpu_lib.sy_cells_u8_gpu(ctypes.c_void_p(dev_ptr), N, seed, z0, nz, cell, _ptr(table), ng)
+    if err != 0:
+        raise RuntimeError(f"sy_cells_u8_gpu failed with CUDA error {err}")
 
 
 # --------------------------------------------------------------------------- transfer functions

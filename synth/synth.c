@@ -295,3 +295,26 @@ void sy_cells_u8_box(uint8_t* out, long N, uint64_t seed, long x0, long y0, long
     }
   }
 }
+
+/* Parameters of every cell of the cell-body volume of edge N as float32, 8 per
+ * cell (present, centre x/y/z, radius, interior value, 0, 0), cells x fastest
+ * over a grid of ceil(N / cell)^3: the table the GPU generator reads. */
+void sy_cell_table(float* out, long N, uint64_t seed, int cell) {
+  long ng = (N + cell - 1) / cell;
+#pragma omp parallel for schedule(static)
+  for (long gz = 0; gz < ng; ++gz)
+    for (long gy = 0; gy < ng; ++gy)
+      for (long gx = 0; gx < ng; ++gx) {
+        cell_t o;
+        cell_params(seed, cell, gx, gy, gz, ng, &o);
+        float* p = out + (((size_t)gz * ng + gy) * ng + gx) * 8;
+        p[0] = (float)o.present;
+        p[1] = (float)o.c[0];
+        p[2] = (float)o.c[1];
+        p[3] = (float)o.c[2];
+        p[4] = (float)o.r;
+        p[5] = (float)o.inner;
+        p[6] = 0.0f;
+        p[7] = 0.0f;
+      }
+}

@@ -45,6 +45,11 @@ def test_invalid_arguments_are_rejected_on_the_host():
     assert lib.sg_volume_create(ctypes.byref(d), ctypes.byref(h)) == sg.SG_ERR_INVALID_ARG  # not a multiple of 8
     d.brick_size, d.apron = 32, 2
     assert lib.sg_volume_create(ctypes.byref(d), ctypes.byref(h)) == sg.SG_ERR_INVALID_ARG  # apron must be 1
+    d.apron = 1
+    for bad_skip, brick in [(3, 32), (64, 64), (16, 24), (4, 256)]:  # not 2/4/8/16, not dividing, > 32 cells
+        d.skip_block, d.brick_size = bad_skip, brick
+        assert lib.sg_volume_create(ctypes.byref(d), ctypes.byref(h)) == sg.SG_ERR_INVALID_ARG, (bad_skip, brick)
+        assert "skip_block" in lib.sg_last_error().decode()
     assert lib.sg_render(None, None, None, None, None) == sg.SG_ERR_INVALID_ARG
     assert lib.sg_select_lod(None, None, None, None) == sg.SG_ERR_INVALID_ARG
     assert lib.sg_volume_destroy(None) == sg.SG_OK

@@ -129,3 +129,73 @@ def test_streaming_frames_match_the_oracle_and_evict_lru(mode, index_ranges=True
                           ovol.render([otf], ref["leaf"], views[e], projs[e], W, H))
     finally:
         sg.sg_volume_destroy(vol)
+
+
+def test_upload_list_cut_short_leaves_a_consistent_cache():
+    """A request list longer than the cache: placement stops at the first
+    brick that finds every slot used by the current frame, the placed prefix
+    is resident and consistent (page table, ranges, flags), and the next
+    selection and render match the oracle for exactly that residency."""
+    import torch
+    from paper_1804_08197_b300 import sg
+    a = synth.filaments_u16(DIMS, seed=32, ntubes=24)
+    model = synth.volume_model(128, 0.5)
+    ovol = oracle.Volume([oracle.pyramid(a, LEVELS)], B, model=model)
+    full = ovol.block_ranges()
+    table = synth.tf_piecewise(2002, zero_alpha_points=2)
+    otf = oracle.make_tf(table, 300.0, 60000.0)
+    W, H, tau = 160, 176, 0.3
+    views, projs = _stereo((-0.3, 0.06, 0.2), (0.0, 0.0, 0.0), W, H)
+    cap = 14
+    brick_bytes = ((B + 2) ** 3 * 2 + 255) // 256 * 256
+    vol = sg.sg_volume_create(DIMS, sg.SG_U16, B, LEVELS, device_pool_bytes=cap * brick_bytes, model=model)
+    try:
+        sg.sg_set_transfer_function(vol, 0, table, 300.0, 60000.0)
+        for L in range(LEVELS):
+            nbx, nby, nbz = ovol.blocks_per_axis(L)
+            xyz = np.array([(x, y, z) for z in range(nbz) for y in range(nby) for x in range(nbx)])
+            lo, hi = ovol.level_offsets[L], ovol.level_offsets[L + 1]
+            sg.sg_set_brick_ranges(vol, 0, 0, L, xyz, full[lo:hi, 0, :])
+
+        def bricks(ids):
+            out = []
+            for n in ids:
+                L, b = ovol.node_coords(int(n))
+                out.append(_brick(ovol, L, *b))
+            return out
+
+        root = [int(ovol.level_offsets[LEVELS - 1])]
+        assert sg.sg_upload_brick_list(vol, 0, 0, root, bricks(root)) == 1
+        pose = sg.make_pose(views, projs, W, H, pixel_error=tau)
+        cut = False
+        for frame in range(6):
+            sg.sg_select_lod(vol, pose)
+            req = sg.sg_read_requests(vol, 0)
+            if len(req) == 0:
+                break
+            ids = sorted((int(n) for n in req), key=lambda n: (-ovol.node_coords(n)[0], n))
+            host = bricks(ids)
+            done = sg.sg_upload_brick_list(vol, 0, 0, ids, host)
+            cut |= done < len(ids)
+            res = sg.sg_read_residency(vol, 0, ovol.node_count)
+            assert (res[ids[:done]] >= 0).all()
+            assert len(set(res[res >= 0].tolist())) == np.count_nonzero(res >= 0) <= cap
+            # every resident brick holds its own data
+            for n in np.flatnonzero(res >= 0)[:6]:
+                L, b = ovol.node_coords(int(n))
+                got = np.empty((B + 2) ** 3, np.uint16)
+                sg.sg_read_brick(vol, 0, 0, L, *b, got)
+                assert np.array_equal(got, _brick(ovol, L, *b).reshape(-1))
+            # selection and image for exactly this residency
+            sg.sg_select_lod(vol, pose)
+            resident = (res >= 0).astype(np.uint8)
+            ref = ovol.select([otf], views, projs, H, tau=tau, resident=resident, ranges=full)
+            gsel = sg.sg_read_selection(vol, 0, len(ref["leaf"]), ovol.node_count)
+            compare_selection(gsel, ref)
+            outs = [torch.empty((H, W, 4), device="cuda") for _ in range(2)]
+            sg.sg_render(vol, pose, sg.render_params(), outs)
+            torch.cuda.synchronize()
+            compare_image(outs[0].cpu().numpy().reshape(-1, 4), ovol.render([otf], ref["leaf"], views[0], projs[0], W, H))
+        assert cut, "the cache should have been too small for one frame's requests"
+    finally:
+        sg.sg_volume_destroy(vol)
