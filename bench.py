@@ -309,21 +309,28 @@ def streaming_flythrough(sg, torch, dev, full=None, count=256, budget_bytes=256 
     prm = sg.render_params(step=STEP, term_alpha=TERM)
     per_frame = budget_bytes // R3
     frame_ms, up_ms, hits, up_bricks = [], [], [], 0
+    # pipelined frames: select and render on the compute stream; the bricks
+    # this frame requested upload on a copy stream while its render runs,
+    # and are in the cache for the next selection
+    comp, copy = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
     torch.cuda.synchronize()
     for views, projs in poses:
         t0 = time.perf_counter()
         pose = sg.make_pose(views, projs, W_EYE, H_EYE, pixel_error=TAU)
-        st = sg.sg_select_lod(vol, pose, stats=True)
+        st = sg.sg_select_lod(vol, pose, stats=True, stream=comp)
         # blocks drawn at the wanted detail / blocks wanted (drawn + missing)
         drawn = st["selected"] - st["fallback"]
         hits.append(drawn / (drawn + st["requested"]) if drawn + st["requested"] else 1.0)
-        tu = time.perf_counter()
+        req = []
         if st["requested"]:
-            req = sorted((int(n) for n in sg.sg_read_requests(vol, 0)), key=lambda n: (-geo[n][0], n))[:per_frame]
-            up_bricks += sg.sg_upload_brick_list(vol, 0, 0, req, [base + n * R3 for n in req])
+            req = sorted((int(n) for n in sg.sg_read_requests(vol, 0, stream=comp)),
+                         key=lambda n: (-geo[n][0], n))[:per_frame]
+        sg.sg_render(vol, pose, prm, outs, stream=comp)
+        tu = time.perf_counter()
+        if req:
+            up_bricks += sg.sg_upload_brick_list(vol, 0, 0, req, [base + n * R3 for n in req], stream=copy)
         up_ms.append((time.perf_counter() - tu) * 1e3)
-        sg.sg_render(vol, pose, prm, outs)
-        torch.cuda.synchronize()
+        comp.synchronize()
         frame_ms.append((time.perf_counter() - t0) * 1e3)
     sg.sg_volume_destroy(vol)
     cudart.cudaHostUnregister(host.ctypes.data)

@@ -121,8 +121,12 @@ sg_status sg_upload_bricks(sg_volume* vol, int t, int c, int level, int n, const
  * first brick that finds the cache full of bricks used by the current frame,
  * and *n_done receives how many bricks (a prefix of the list) are cached.
  * The page table, value ranges and transparency flags of every placed brick
- * are updated before return. Errors: INVALID_ARG (node id out of range, NULL
- * pointer), OOM (bookkeeping memory), CUDA. */
+ * are updated before return. Streams: the call first waits (on its stream)
+ * for the last selection launch, whose slot stamps decide what may be
+ * evicted; it never evicts a brick that selection used, so it may run on a
+ * copy stream while that selection's render runs on another.
+ * Errors: INVALID_ARG (node id out of range, NULL pointer), OOM (bookkeeping
+ * memory), CUDA. */
 sg_status sg_upload_brick_list(sg_volume* vol, int t, int c, int n, const int32_t* nodes, const void* const* host,
                                int32_t* n_done, void* stream);
 

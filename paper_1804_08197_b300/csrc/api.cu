@@ -83,6 +83,7 @@ void free_volume(sg_volume* v) {
   cudaFree(v->d_stage);
   cudaFree(v->d_err);
   cudaFree(v->d_stamp);
+  if (v->ev_select) cudaEventDestroy(v->ev_select);
   for (auto& s : v->sel) {
     cudaFree(s.d_leaf);
     cudaFree(s.d_cell_node);
@@ -131,10 +132,13 @@ sg_status upload_list(sg_volume* v, int t, int c, int n, const int32_t* nodes, c
   const size_t raw = (size_t)R * R * R * v->esize;
   *done = 0;
   if (v->pooled) {
-    // stamps of slots used by recent selections
+    // stamps of slots used by recent selections, read on this stream once
+    // the last selection launch (on whatever stream) has written them
     std::vector<uint64_t> st(v->pool_slots);
+    SG_CUDA(cudaStreamWaitEvent(s, v->ev_select, 0), "upload");
+    SG_CUDA(cudaMemcpyAsync(st.data(), v->d_stamp, v->pool_slots * sizeof(uint64_t), cudaMemcpyDeviceToHost, s),
+            "stamps");
     SG_CUDA(cudaStreamSynchronize(s), "upload");
-    SG_CUDA(cudaMemcpy(st.data(), v->d_stamp, v->pool_slots * sizeof(uint64_t), cudaMemcpyDeviceToHost), "stamps");
     for (int64_t sl = 0; sl < v->pool_slots; ++sl)
       if (v->slot_owner[sl] >= 0 && !v->slot_pinned[sl] && st[sl] != v->slot_stamp[sl]) {
         x->lru.erase({v->slot_stamp[sl], sl});
@@ -218,8 +222,8 @@ sg_status upload_list(sg_volume* v, int t, int c, int n, const int32_t* nodes, c
     k_page_update<<<(unsigned)((nupd + 255) / 256), 256, 0, s>>>(v->d_slot, d_upd, (int)nupd);
     SG_CUDA(cudaGetLastError(), "page table update");
   }
-  SG_CUDA(launch_brick_ranges(v, t, c, 0, d_nodes, m, s), "brick ranges");
   SG_CUDA(launch_subranges(v, d_slots, m, c, s), "sub-block ranges");
+  SG_CUDA(launch_brick_ranges(v, t, c, 0, d_nodes, m, s), "brick ranges");  // from the sub-block ranges
   v->has_data[(size_t)t * v->nch + c] = 1;
   // node flags everywhere, sub-block flags of the uploaded slots only
   sg_status st = refresh_flags(v, s, d_slots, m);
@@ -375,7 +379,8 @@ sg_status sg_volume_create(const sg_volume_desc* d, sg_volume** out) {
       (e = dalloc(&v->d_nodeflags, tn)) != cudaSuccess ||
       (e = dalloc(&v->d_tf_raw, (size_t)v->nch * kMaxTF * 4)) != cudaSuccess ||
       (e = dalloc(&v->d_lut, (size_t)2 * v->nch * v->levels * kMaxTF)) != cudaSuccess ||
-      (e = dalloc(&v->d_err, 4)) != cudaSuccess) {
+      (e = dalloc(&v->d_err, 4)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&v->ev_select, cudaEventDisableTiming)) != cudaSuccess) {
     free_volume(v);
     set_error(std::string("device allocation: ") + cudaGetErrorString(e));
     return SG_ERR_OOM;
@@ -556,6 +561,8 @@ sg_status sg_select_lod_batch(sg_volume* v, const sg_pose* poses, int n, void* s
   cudaStream_t s = (cudaStream_t)stream;
   ++v->frame;
   SG_CUDA(launch_select(v, poses, n, s), "selection");
+  // uploads on other streams read the stamps this launch writes
+  SG_CUDA(cudaEventRecord(v->ev_select, s), "selection");
   for (int i = 0; i < n; ++i) {
     SelSlot& sl = v->sel[poses[i].slot];
     sl.valid = true;
@@ -588,7 +595,9 @@ sg_status sg_read_selection(sg_volume* v, int slot, int32_t* cell_node, int64_t 
   if (req && req_cap > 0) {
     std::vector<int32_t> r(c[0]);
     if (c[0]) {
-      SG_CUDA(cudaMemcpy(r.data(), sl.d_req, c[0] * sizeof(int32_t), cudaMemcpyDeviceToHost), "read requests");
+      SG_CUDA(cudaMemcpyAsync(r.data(), sl.d_req, c[0] * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+              "read requests");
+      SG_CUDA(cudaStreamSynchronize(s), "read requests");
     }
     std::sort(r.begin(), r.end());
     for (int32_t i = 0; i < req_cap && i < (int32_t)r.size(); ++i) req[i] = r[i];

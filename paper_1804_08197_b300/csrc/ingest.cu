@@ -83,7 +83,9 @@ __global__ void k_pack(const T* __restrict__ lvl, int64_t nx, int64_t ny, int64_
 
 // Min/max of every sub-block's trilinear footprint: with sub-block edge S,
 // sub-block s covers level-L positions [bB + Ss, bB + Ss + S] per axis, whose
-// samples read brick-local voxels Ss .. Ss + S + 1.
+// samples read brick-local voxels Ss .. Ss + S + 1. Grid: (brick, layer sz);
+// a CTA covers one z-layer of nsub^2 sub-blocks of one brick, so a handful
+// of bricks still fills the machine.
 template <typename T>
 __global__ void k_subranges(const uint8_t* __restrict__ pool, size_t brick_bytes, int nch, int c, int B, int nsub,
                             int S, const int32_t* __restrict__ slots, int32_t slot_base,
@@ -92,40 +94,40 @@ __global__ void k_subranges(const uint8_t* __restrict__ pool, size_t brick_bytes
   if (slot < 0) return;
   const T* src = reinterpret_cast<const T*>(pool + ((size_t)slot * nch + c) * brick_bytes);
   const int R = B + 2;
-  const int ns3 = nsub * nsub * nsub;
-  for (int s = threadIdx.x; s < ns3; s += blockDim.x) {
-    int sx = s % nsub, sy = (s / nsub) % nsub, sz = s / (nsub * nsub);
+  const int n2 = nsub * nsub, ns3 = n2 * nsub;
+  const int sz = blockIdx.y;
+  for (int q = threadIdx.x; q < n2; q += blockDim.x) {
+    const int sx = q % nsub, sy = q / nsub;
     uint32_t mn = 0xffffffffu, mx = 0u;
     for (int z = 0; z < S + 2; ++z)
       for (int y = 0; y < S + 2; ++y) {
         const T* row = src + ((size_t)(sz * S + z) * R + (sy * S + y)) * R + sx * S;
         for (int x = 0; x < S + 2; ++x) {
-          uint32_t v = row[x];
+          const uint32_t v = __ldg(row + x);
           mn = min(mn, v);
           mx = max(mx, v);
         }
       }
-    uint16_t* o = subrange + (((size_t)slot * ns3 + s) * nch + c) * 2;
+    uint16_t* o = subrange + (((size_t)slot * ns3 + (size_t)sz * n2 + q) * nch + c) * 2;
     o[0] = (uint16_t)mn;
     o[1] = (uint16_t)mx;
   }
 }
 
-// Ranges of bricks uploaded ready-made (apron included): min/max over the
-// whole (B+2)^3 brick.
-template <typename T>
-__global__ void k_brick_range(const uint8_t* __restrict__ pool, size_t brick_bytes, int nch, int c, int B,
-                              const int32_t* __restrict__ slot_of_node, const int32_t* __restrict__ nodes,
-                              uint32_t* __restrict__ range) {
+// Range of a whole brick with its apron from its sub-block ranges: the
+// sub-block footprints cover the (B+2)^3 brick, so their min of mins and max
+// of maxes is the brick's range (one pass over the small table instead of
+// the brick).
+__global__ void k_brick_range_from_sub(const uint16_t* __restrict__ subrange, int ns3, int nch, int c,
+                                       const int32_t* __restrict__ slot_of_node, const int32_t* __restrict__ nodes,
+                                       uint32_t* __restrict__ range) {
   const int32_t node = nodes[blockIdx.x];
-  const int32_t slot = slot_of_node[node];
-  const T* src = reinterpret_cast<const T*>(pool + ((size_t)slot * nch + c) * brick_bytes);
-  const int64_t R3 = (int64_t)(B + 2) * (B + 2) * (B + 2);
+  const int64_t slot = slot_of_node[node];
   uint32_t mn = 0xffffffffu, mx = 0u;
-  for (int64_t i = threadIdx.x; i < R3; i += blockDim.x) {
-    uint32_t v = src[i];
-    mn = min(mn, v);
-    mx = max(mx, v);
+  for (int i = threadIdx.x; i < ns3; i += blockDim.x) {
+    const uint16_t* r = subrange + ((slot * ns3 + i) * nch + c) * 2;
+    mn = min(mn, (uint32_t)r[0]);
+    mx = max(mx, (uint32_t)r[1]);
   }
   block_minmax(mn, mx);
   if (threadIdx.x == 0) {
@@ -171,11 +173,12 @@ cudaError_t launch_pack_level(sg_volume* v, int t, int c, int L, const void* dat
   if (!v->pooled) {
     int32_t base = (int32_t)((int64_t)t * v->nodes + g.off);
     if (v->esize == 1)
-      k_subranges<uint8_t><<<(unsigned)nblk, 256, 0, s>>>(v->d_pool, v->brick_bytes, v->nch, c, v->B, v->nsub, v->sub,
-                                                           nullptr, base, v->d_subrange);
+      k_subranges<uint8_t><<<dim3((unsigned)nblk, v->nsub), 256, 0, s>>>(v->d_pool, v->brick_bytes, v->nch, c, v->B,
+                                                                          v->nsub, v->sub, nullptr, base, v->d_subrange);
     else
-      k_subranges<uint16_t><<<(unsigned)nblk, 256, 0, s>>>(v->d_pool, v->brick_bytes, v->nch, c, v->B, v->nsub, v->sub,
-                                                            nullptr, base, v->d_subrange);
+      k_subranges<uint16_t><<<dim3((unsigned)nblk, v->nsub), 256, 0, s>>>(v->d_pool, v->brick_bytes, v->nch, c, v->B,
+                                                                           v->nsub, v->sub, nullptr, base,
+                                                                           v->d_subrange);
     e = cudaGetLastError();
   }
   return e;
@@ -184,25 +187,22 @@ cudaError_t launch_pack_level(sg_volume* v, int t, int c, int L, const void* dat
 cudaError_t launch_subranges(sg_volume* v, const int32_t* d_slots, int nslots, int c, cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;
   if (v->esize == 1)
-    k_subranges<uint8_t><<<nslots, 256, 0, s>>>(v->d_pool, v->brick_bytes, v->nch, c, v->B, v->nsub, v->sub, d_slots, 0,
-                                                v->d_subrange);
+    k_subranges<uint8_t><<<dim3(nslots, v->nsub), 256, 0, s>>>(v->d_pool, v->brick_bytes, v->nch, c, v->B, v->nsub,
+                                                                v->sub, d_slots, 0, v->d_subrange);
   else
-    k_subranges<uint16_t><<<nslots, 256, 0, s>>>(v->d_pool, v->brick_bytes, v->nch, c, v->B, v->nsub, v->sub, d_slots, 0,
-                                                 v->d_subrange);
+    k_subranges<uint16_t><<<dim3(nslots, v->nsub), 256, 0, s>>>(v->d_pool, v->brick_bytes, v->nch, c, v->B, v->nsub,
+                                                                 v->sub, d_slots, 0, v->d_subrange);
   return cudaGetLastError();
 }
 
 cudaError_t launch_brick_ranges(sg_volume* v, int t, int c, int L, const int32_t* d_nodes, int n, cudaStream_t s) {
   (void)L;
   if (n <= 0) return cudaSuccess;
+  // needs the bricks' sub-block ranges (launch_subranges first, same stream)
   const int32_t* slot_of_node = v->d_slot + (int64_t)t * v->nodes;
   uint32_t* range = v->d_range + (int64_t)t * v->nodes * v->nch * 2;
-  if (v->esize == 1)
-    k_brick_range<uint8_t><<<n, 512, 0, s>>>(v->d_pool, v->brick_bytes, v->nch, c, v->B, slot_of_node, d_nodes,
-                                             range);
-  else
-    k_brick_range<uint16_t><<<n, 512, 0, s>>>(v->d_pool, v->brick_bytes, v->nch, c, v->B, slot_of_node, d_nodes,
-                                              range);
+  const int ns3 = v->nsub * v->nsub * v->nsub;
+  k_brick_range_from_sub<<<n, 256, 0, s>>>(v->d_subrange, ns3, v->nch, c, slot_of_node, d_nodes, range);
   return cudaGetLastError();
 }
 

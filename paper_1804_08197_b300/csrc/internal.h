@@ -106,6 +106,7 @@ struct sg_volume {
   std::vector<uint8_t> slot_pinned;   // coarsest level: never evicted
   uint64_t frame = 0;
   uint64_t* d_stamp = nullptr;        // [slots] frame of last use, written by the selection kernel
+  cudaEvent_t ev_select = nullptr;    // recorded after each stamping selection launch
 
   sg::SelSlot sel[sg::kMaxSlots];
 

@@ -30,10 +30,23 @@ __device__ unsigned long long g_events[8];
 #else
 #define SG_EV(i, n) ((void)0)
 #endif
-// minimum resident CTAs per SM requested from the register allocator
-#ifndef SG_RENDER_MINB
-#define SG_RENDER_MINB 1
+// Register budget of the brick-edge specialised one-ray-per-thread kernels:
+// 64 per thread, i.e. 32 resident warps per SM (on the 1024^3 bench 64
+// registers without spills beat 72 registers at 28 warps; 48 registers spill
+// and lose). The generic and two-rays-per-thread kernels would spill under
+// it and keep the compiler's choice.
+constexpr int kWarpsPerSM = 32;
+// Lattice points a sample iteration may take (the first after a sub-block
+// lookup, the others without one while they stay in the block): fewer loop
+// trips per sample and fewer iterations in which the warp also runs the jump
+// and block-step paths for its other lanes.
+#ifndef SG_SAMPLES_PER_ITER
+#define SG_SAMPLES_PER_ITER 2
 #endif
+constexpr int kSamplesPerIter = SG_SAMPLES_PER_ITER;
+__host__ __device__ constexpr int min_blocks(int threads, int rpt, int bk) {
+  return (rpt == 1 && bk != 0) ? kWarpsPerSM * 32 / threads : 1;
+}
 
 
 struct ImageJob {
@@ -331,13 +344,29 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
     SG_EV(0, 1);
 #ifdef SG_RENDER_EVENT_STATS
     const float w_before = acc.w;
-    const bool stop = composite_sample<T, BK>(a, brick0, L, lx, ly, lz, acc);
+    bool stop = composite_sample<T, BK>(a, brick0, L, lx, ly, lz, acc);
     SG_EV(7, acc.w != w_before ? 1 : 0);
-    if (stop) break;
 #else
-    if (composite_sample<T, BK>(a, brick0, L, lx, ly, lz, acc)) break;
+    bool stop = composite_sample<T, BK>(a, brick0, L, lx, ly, lz, acc);
 #endif
+    if (stop) break;
     k += kstep;
+    // the next lattice points of the same block, taken without a sub-block
+    // lookup: a sample in a transparent sub-block adds exactly nothing, so
+    // taking it is always exact
+#pragma unroll
+    for (int u = 1; u < kSamplesPerIter; ++u) {
+      const float t2 = lattice_t(k, t0, a);
+      if (!(t2 < tend)) break;
+      const float qx = fmaf(t2, d.x, o.x), qy = fmaf(t2, d.y, o.y), qz = fmaf(t2, d.z, o.z);
+      const float mx = fmaf(qx - lo.x, sL, 0.5f), my = fmaf(qy - lo.y, sL, 0.5f), mz = fmaf(qz - lo.z, sL, 0.5f);
+      ++cnt;
+      SG_EV(0, 1);
+      stop = composite_sample<T, BK>(a, brick0, L, mx, my, mz, acc);
+      if (stop) break;
+      k += kstep;
+    }
+    if (stop) break;
   }
 #ifdef SG_RENDER_EVENT_STATS
   for (int i = 0; i < 8; ++i)
@@ -346,7 +375,7 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
 }
 
 template <typename T, int MAXI, int BK>
-__global__ void __launch_bounds__(kThreads, SG_RENDER_MINB) k_render(Args a, Jobs<MAXI> jobs) {
+__global__ void __launch_bounds__(kThreads, min_blocks(kThreads, 1, BK)) k_render(Args a, Jobs<MAXI> jobs) {
   const int tile = blockIdx.x;
   int im = 0;
   while (im + 1 < jobs.n && tile >= jobs.img[im + 1].tile_begin) ++im;
@@ -378,7 +407,8 @@ __global__ void __launch_bounds__(kThreads, SG_RENDER_MINB) k_render(Args a, Job
 // (work queue over all images of the batch, whatever their sizes); else one
 // CTA per tile.
 template <typename T, int TW, int TH, int RPT, bool PERSIST, int BK>
-__global__ void __launch_bounds__(TW * TH / RPT) k_render_tiles(Args a, Jobs<128> jobs, int* __restrict__ counter) {
+__global__ void __launch_bounds__(TW * TH / RPT, min_blocks(TW * TH / RPT, RPT, BK))
+    k_render_tiles(Args a, Jobs<128> jobs, int* __restrict__ counter) {
   constexpr int kN = TW * TH / RPT;
   constexpr int kSubX = TW / 8;
   __shared__ int s_tile;

@@ -90,42 +90,58 @@ __global__ void k_sub_empty(TFParams p, const uint16_t* __restrict__ subrange, i
   }
 }
 
-// Chebyshev distance, in sub-blocks, from every sub-block of a brick to
-// the nearest non-transparent one of the same brick: 0 = not transparent,
-// D > 0 = every sub-block within D - 1 steps (26-neighbourhood) is
-// transparent, so a ray may cross that whole cube without a sample. Computed
-// by breadth-first dilation rounds up to kMaxDist; farther cells keep
-// kMaxDist + 1 (capped by the brick edge where the ray's jump is clipped).
-constexpr int kMaxDist = 7;
+// Chebyshev (L-infinity) distance, in sub-blocks, from every sub-block of a
+// brick to the nearest non-transparent one of the same brick: 0 = not
+// transparent, D > 0 = every sub-block within D - 1 steps (26-neighbourhood)
+// is transparent, so a ray may cross that whole cube without a sample; 255 =
+// no non-transparent sub-block in the brick (the ray's jump is clipped to the
+// brick). Exact, by the separable transform: a 1-D distance along x (two
+// scans per row), then along y and z the max-plus erosion
+// g'(i) = min_j max(|i - j|, g(j)), one column per thread in registers.
+constexpr int kDistInf = 255;
+__device__ __forceinline__ void erode_column(uint8_t* __restrict__ base, int stride, int n) {
+  uint8_t g[kMaxSubPerEdge];
+#pragma unroll
+  for (int j = 0; j < kMaxSubPerEdge; ++j)
+    if (j < n) g[j] = base[j * stride];
+  for (int i = 0; i < n; ++i) {
+    int best = kDistInf;
+#pragma unroll
+    for (int j = 0; j < kMaxSubPerEdge; ++j)
+      if (j < n) best = min(best, max(abs(i - j), (int)g[j]));
+    base[i * stride] = (uint8_t)best;
+  }
+}
+
 __global__ void k_sub_dist(const uint64_t* __restrict__ bits, int nsub, int words, uint8_t* __restrict__ dist,
                            const int32_t* __restrict__ slot_list) {
   extern __shared__ uint8_t sd[];
   const int64_t slot = slot_list ? slot_list[blockIdx.x] : blockIdx.x;
-  const int ns3 = nsub * nsub * nsub;
+  const int n = nsub, n2 = nsub * nsub, ns3 = n2 * nsub;
   const uint64_t* w = bits + slot * words;
-  for (int i = threadIdx.x; i < ns3; i += blockDim.x) sd[i] = ((w[i >> 6] >> (i & 63)) & 1ull) ? 255 : 0;
-  __syncthreads();
-  for (int r = 1; r <= kMaxDist; ++r) {
-    for (int i = threadIdx.x; i < ns3; i += blockDim.x) {
-      if (sd[i] != 255) continue;
-      const int x = i % nsub, y = (i / nsub) % nsub, z = i / (nsub * nsub);
-      bool near = false;
-      for (int dz = -1; dz <= 1 && !near; ++dz)
-        for (int dy = -1; dy <= 1 && !near; ++dy)
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int X = x + dx, Y = y + dy, Z = z + dz;
-            if (X < 0 || Y < 0 || Z < 0 || X >= nsub || Y >= nsub || Z >= nsub) continue;
-            if (sd[(Z * nsub + Y) * nsub + X] == r - 1) { near = true; break; }
-          }
-      if (near) sd[i] = 254;  // mark; becomes r after the round
+  // x: distance to the nearest non-transparent sub-block of the same row
+  for (int r = threadIdx.x; r < n2; r += blockDim.x) {
+    uint8_t* row = sd + r * n;
+    int last = -kDistInf;
+    for (int x = 0; x < n; ++x) {
+      const int i = r * n + x;
+      if (!((w[i >> 6] >> (i & 63)) & 1ull)) last = x;
+      row[x] = (uint8_t)min(x - last, kDistInf);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < ns3; i += blockDim.x)
-      if (sd[i] == 254) sd[i] = (uint8_t)r;
-    __syncthreads();
+    last = kDistInf * 2;
+    for (int x = n - 1; x >= 0; --x) {
+      if (row[x] == 0) last = x;
+      row[x] = (uint8_t)min((int)row[x], min(last - x, kDistInf));
+    }
   }
-  for (int i = threadIdx.x; i < ns3; i += blockDim.x)
-    dist[slot * ns3 + i] = sd[i] == 255 ? (uint8_t)(kMaxDist + 1) : sd[i];
+  __syncthreads();
+  for (int c = threadIdx.x; c < n2; c += blockDim.x)  // y columns: (x, z) = (c % n, c / n)
+    erode_column(sd + (c / n) * n2 + (c % n), n, n);
+  __syncthreads();
+  for (int c = threadIdx.x; c < n2; c += blockDim.x)  // z columns: (x, y) = (c % n, c / n)
+    erode_column(sd + c, n2, n);
+  __syncthreads();
+  for (int i = threadIdx.x; i < ns3; i += blockDim.x) dist[slot * ns3 + i] = sd[i];
 }
 
 // Opacity correction per level: a level-L sample stands for step 2^L

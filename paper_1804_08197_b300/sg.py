@@ -382,10 +382,10 @@ def sg_read_ranges(vol, t, nnode, channels=1):
     return out
 
 
-def sg_read_requests(vol, slot, cap=1 << 16):
+def sg_read_requests(vol, slot, cap=1 << 16, stream=None):
     """Requested node ids of a selection (ascending), without the other outputs."""
     import numpy as np
     req = np.empty(cap, np.int32)
     nreq = ctypes.c_int32(0)
-    _check(lib.sg_read_selection(vol, slot, None, 0, None, 0, _ptr(req), cap, ctypes.byref(nreq), None))
+    _check(lib.sg_read_selection(vol, slot, None, 0, None, 0, _ptr(req), cap, ctypes.byref(nreq), _stream(stream)))
     return req[: min(nreq.value, cap)].copy()

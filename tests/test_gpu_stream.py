@@ -38,7 +38,7 @@ def _stereo(head, target, W, H, fovy=40.0, ipd=0.064):
     return views, [proj, proj]
 
 
-@pytest.mark.parametrize("mode", ["bricks", "list"])
+@pytest.mark.parametrize("mode", ["bricks", "list", "pipelined"])
 def test_streaming_frames_match_the_oracle_and_evict_lru(mode, index_ranges=True):
     import torch
     from paper_1804_08197_b300 import sg
@@ -71,15 +71,18 @@ def test_streaming_frames_match_the_oracle_and_evict_lru(mode, index_ranges=True
                 sg.sg_set_brick_ranges(vol, 0, 0, L, xyz, full[lo:hi, 0, :])
             known[:] = True
 
+        comp = torch.cuda.Stream() if mode == "pipelined" else None
+        copy = torch.cuda.Stream() if mode == "pipelined" else None
+
         def upload(ids):
-            if mode == "list":
+            if mode in ("list", "pipelined"):
                 # one call per frame, by node id, coarse levels first
                 ids = sorted((int(i) for i in ids), key=lambda n: (-ovol.node_coords(n)[0], n))
                 host = []
                 for n in ids:
                     L, b = ovol.node_coords(n)
                     host.append(_brick(ovol, L, *b))
-                done = sg.sg_upload_brick_list(vol, 0, 0, ids, host)
+                done = sg.sg_upload_brick_list(vol, 0, 0, ids, host, stream=copy)
                 assert 0 < done <= len(ids)
                 res = sg.sg_read_residency(vol, 0, ovol.node_count)
                 assert (res[ids[:done]] >= 0).all()
@@ -113,6 +116,18 @@ def test_streaming_frames_match_the_oracle_and_evict_lru(mode, index_ranges=True
                 compare_selection(gsel, ref)
                 if stats["requested"] == 0:
                     break
+                if mode == "pipelined" and frame < 3:
+                    # this frame renders on one stream while its requests
+                    # upload on another (evicting only bricks it does not use)
+                    outs = [torch.empty((H, W, 4), device="cuda") for _ in range(2)]
+                    sg.sg_render(vol, pose, sg.render_params(), outs, stream=comp)
+                    upload(gsel[2])
+                    comp.synchronize()
+                    # early frames mix levels (fallbacks next to refined
+                    # blocks), so more pixels sit near a face between levels
+                    compare_image(outs[0].cpu().numpy().reshape(-1, 4),
+                                  ovol.render([otf], ref["leaf"], views[0], projs[0], W, H), max_flagged=0.05)
+                    continue
                 upload(gsel[2])
             assert stats["requested"] == 0 and stats["fallback"] == 0
         assert evicted, "the second view should have evicted bricks of the first"
