@@ -522,6 +522,8 @@ def run_ours(args, rank, world, local_rank):
 
     def step(i, ev=None):
         p = mine[i % NPOSES]
+        if ev is not None:
+            ev[2].record(stream)
         sg.sg_select_lod(vol, p, stream=stream)
         if ev is not None:
             ev[0].record(stream)
@@ -538,7 +540,7 @@ def run_ours(args, rank, world, local_rank):
     clocks = ClockSampler(local_rank)
     clocks.start()
     time.sleep(0.3)
-    rev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    rev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(args.steps)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -548,7 +550,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    render_ms = [a.elapsed_time(b) for a, b in rev]
+    render_ms = [a.elapsed_time(b) for a, b, _ in rev]
+    frame_ms = np.array([c.elapsed_time(b) for _, b, c in rev])  # select + render of one pose
     samples = int(total.item())
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
     if world > 1:
@@ -599,6 +602,9 @@ def run_ours(args, rank, world, local_rank):
                 "gsamples_per_s": round(samples * world / (ms_max / 1e3) / 1e9, 3),
                 "samples_per_step": samples // args.steps,
                 "render_ms_mean": round(sum(render_ms) / len(render_ms), 4),
+                "frame_ms": {"mean": round(float(frame_ms.mean()), 4),
+                             "p50": round(float(np.percentile(frame_ms, 50)), 4),
+                             "p99": round(float(np.percentile(frame_ms, 99)), 4)},
                 "gpu_launches": 2 * args.steps,
                 "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                              "frac": round(achieved / peak, 5), "traffic": profiled_traffic(sum(alg) / len(alg)),
