@@ -29,6 +29,7 @@ MAX_CH = 4
 
 ST_UNSEEN, ST_CULLED, ST_EMPTY, ST_SELECTED, ST_FALLBACK, ST_REFINED = range(6)
 FL_FACE, FL_TEDGE, FL_TERM, FL_COUNT = 1, 2, 4, 8
+MODE_EA, MODE_EMISSION, MODE_MIP = 0, 1, 2
 
 
 def build(force=False):
@@ -68,7 +69,7 @@ def _load():
         L.or_tf_table.argtypes = [vp, dbl, vp]
         L.or_classify.argtypes = [vp, vp, dbl, vp]
         L.or_render.argtypes = [vp, vp, vp, vp, vp, i32, i32, dbl, dbl, dbl, dbl, vp, i64,
-                                vp, vp, vp, vp, vp, i32]
+                                vp, vp, vp, vp, vp, i32, i32, vp]
         L.or_render.restype = i32
         L.or_max_threads.restype = i32
         _lib = L
@@ -140,6 +141,7 @@ class Volume:
             for c in range(self.nch):
                 s.data[L][c] = self.channels[c][L].ctypes.data
         m = np.eye(4).T.reshape(16) if model is None else np.asarray(model, np.float64)
+        self.model = np.asarray(m, np.float64).reshape(16).copy()
         for i in range(16):
             s.model[i] = float(m[i])
         self._s = s
@@ -195,10 +197,21 @@ class Volume:
         return _load().or_sample(ctypes.byref(self._s), int(L), int(c), _p(pp))
 
     def render(self, tfs, leaf, view, proj, W, H, step=0.5, term=0.99, term_tol=1e-4, eps=1e-3,
-               pixels=None, nthreads=0):
+               pixels=None, nthreads=0, mode=MODE_EA, depth=None):
         """Cast rays for `pixels` (flat ids j*W+i; None = all). Returns dict
-        with early/late RGBA (n,4) FP64, sample counts and flags."""
+        with early/late RGBA (n,4) FP64, sample counts and flags.
+
+        mode: MODE_EA (emission-absorption), MODE_EMISSION (emission only),
+        MODE_MIP (maximum intensity projection). depth: optional (H, W)
+        distances in world units from the eye along each pixel's ray to an
+        opaque surface that ends the ray (inf = none); converted to level-0
+        voxels with the model's uniform scale."""
         pix = None if pixels is None else np.ascontiguousarray(pixels, np.int64)
+        tmax = None
+        if depth is not None:
+            m = np.asarray(self.model, np.float64).reshape(4, 4).T  # column-major -> row-major
+            voxel = np.linalg.norm(m[:3, 0])
+            tmax = np.ascontiguousarray(np.asarray(depth, np.float64).reshape(-1) / voxel)
         n = W * H if pix is None else len(pix)
         e = np.zeros((n, 4)); l = np.zeros((n, 4))
         ce = np.zeros(n, np.uint32); cl = np.zeros(n, np.uint32); fl = np.zeros(n, np.uint8)
@@ -206,7 +219,7 @@ class Volume:
         p = np.ascontiguousarray(np.asarray(proj, np.float64).reshape(16))
         ok = _load().or_render(ctypes.byref(self._s), _tf_array(tfs), _p(np.ascontiguousarray(leaf, np.int32)),
                                _p(v), _p(p), W, H, step, term, term_tol, eps, _p(pix), n,
-                               _p(e), _p(l), _p(ce), _p(cl), _p(fl), int(nthreads))
+                               _p(e), _p(l), _p(ce), _p(cl), _p(fl), int(nthreads), int(mode), _p(tmax))
         if not ok:
             raise ValueError("singular view/projection/model matrix")
         return dict(early=e, late=l, count_early=ce, count_late=cl, flags=fl)

@@ -516,6 +516,12 @@ void or_classify(const or_tf* tf, const double* table, double value, double* rgb
 
 enum { FL_FACE = 1, FL_TEDGE = 2, FL_TERM = 4, FL_COUNT = 8 };
 
+/* Optical models ("DVR Techniques"): emission-absorption (front-to-back
+ * compositing with early termination), emission-only (the integral of the
+ * emitted intensity along the ray, no absorption, alpha output 0), and
+ * maximum intensity projection (the classified maximum along the ray). */
+enum { OR_MODE_EA = 0, OR_MODE_EMISSION = 1, OR_MODE_MIP = 2 };
+
 typedef struct {
   const or_volume* v;
   const or_tf* tf;
@@ -523,10 +529,13 @@ typedef struct {
   int64_t nb0[3];
   int64_t off[OR_MAX_LEVELS + 1];
   double* table[OR_MAX_LEVELS][OR_MAX_CH];
+  double* raw[OR_MAX_CH]; /* the tables as given (opacity for one reference step) */
   double inv[16]; /* (P V M)^-1 */
   double eye[3];
   int W, H;
   double step, term, term_tol, eps;
+  int mode;
+  const double* tmax; /* per image pixel: the ray ends there (level-0 voxels from the eye); NULL = none */
 } ray_t;
 
 static int node_level(const ray_t* r, int32_t id) {
@@ -583,6 +592,13 @@ static void cast(const ray_t* r, int64_t pix, double* early, double* late, uint3
     if (t2 < tf) tf = t2;
   }
   double t0 = tn > 0.0 ? tn : 0.0, t1 = tf;
+  /* depth-buffer termination: an opaque surface at tmax ends the ray
+   * ("Depth Buffer"-style compositing of volume and geometry) */
+  const double tsurf = r->tmax ? r->tmax[pix] : INFINITY;
+  if (tsurf < t1) t1 = tsurf;
+  double vmax[OR_MAX_CH];
+  int any = 0;
+  for (int c = 0; c < OR_MAX_CH; ++c) vmax[c] = -INFINITY;
   double C[3] = {0, 0, 0}, A = 0.0, Ce[3] = {0, 0, 0}, Ae = 0.0;
   uint32_t cnt = 0, cnte = 0;
   int early_done = 0;
@@ -644,6 +660,29 @@ static void cast(const ray_t* r, int64_t pix, double* early, double* late, uint3
         }
       }
       if (L < 0 || (k & (((int64_t)1 << L) - 1)) != 0) continue;
+      if (r->mode == OR_MODE_MIP) {
+        /* the maximum trilinear value per channel, classified after the loop */
+        for (int c = 0; c < nch; ++c) {
+          double val = or_sample(r->v, L, c, p);
+          if (val > vmax[c]) vmax[c] = val;
+        }
+        any = 1;
+        ++cnt;
+        continue;
+      }
+      if (r->mode == OR_MODE_EMISSION) {
+        /* emitted intensity per level-0 voxel of path: the table's colour
+         * times its opacity for one reference step, over that step; a
+         * level-L sample stands for step * 2^L of path */
+        for (int c = 0; c < nch; ++c) {
+          double val = or_sample(r->v, L, c, p), rgba[4];
+          or_classify(&r->tf[c], r->raw[c], val, rgba);
+          double w = rgba[3] * (r->step * (double)((int64_t)1 << L)) / (double)r->tf[c].ref_step;
+          for (int q = 0; q < 3; ++q) C[q] += w * rgba[q];
+        }
+        ++cnt;
+        continue;
+      }
       /* classify every channel, blend additively (alpha capped at 1) */
       double sa = 0.0, sc[3] = {0, 0, 0};
       for (int c = 0; c < nch; ++c) {
@@ -666,6 +705,21 @@ static void cast(const ray_t* r, int64_t pix, double* early, double* late, uint3
       if (A >= r->term + r->term_tol) break;
     }
   }
+  if (r->mode == OR_MODE_MIP && any) {
+    /* classify each channel's maximum with its table for one reference
+     * step, blend the channels additively (alpha capped at 1), premultiply */
+    double sa = 0.0, sc[3] = {0, 0, 0};
+    for (int c = 0; c < r->v->nch; ++c) {
+      double rgba[4];
+      or_classify(&r->tf[c], r->raw[c], vmax[c], rgba);
+      sa += rgba[3];
+      for (int q = 0; q < 3; ++q) sc[q] += rgba[3] * rgba[q];
+    }
+    double as = sa < 1.0 ? sa : 1.0;
+    double scale = sa > 0.0 ? as / (sa > as ? sa : as) : 0.0;
+    for (int q = 0; q < 3; ++q) C[q] = sc[q] * scale;
+    A = as;
+  }
   if (!early_done) { memcpy(Ce, C, sizeof C); Ae = A; cnte = cnt; }
   if (cnte != cnt) fl |= FL_TERM;
   for (int q = 0; q < 3; ++q) { early[q] = Ce[q]; late[q] = C[q]; }
@@ -684,11 +738,12 @@ static void cast(const ray_t* r, int64_t pix, double* early, double* late, uint3
 int or_render(const or_volume* v, const or_tf* tfs, const int32_t* leaf, const double* view,
               const double* proj, int W, int H, double step, double term, double term_tol, double eps,
               const int64_t* pix, int64_t npix, double* rgba_early, double* rgba_late, uint32_t* cnt_early,
-              uint32_t* cnt_late, uint8_t* flags, int nthreads) {
+              uint32_t* cnt_late, uint8_t* flags, int nthreads, int mode, const double* tmax) {
   ray_t r;
   memset(&r, 0, sizeof r);
   r.v = v; r.tf = tfs; r.leaf = leaf; r.W = W; r.H = H;
   r.step = step; r.term = term; r.term_tol = term_tol; r.eps = eps;
+  r.mode = mode; r.tmax = tmax;
   or_node_count(v, r.off);
   level_blocks(v, 0, r.nb0);
   double vm[16], pvm[16], vminv[16];
@@ -698,6 +753,10 @@ int or_render(const or_volume* v, const or_tf* tfs, const int32_t* leaf, const d
   double o[4] = {0, 0, 0, 1}, e[4];
   mat_apply(vminv, o, e);
   for (int k = 0; k < 3; ++k) r.eye[k] = e[k] / e[3];
+  for (int c = 0; c < v->nch; ++c) {
+    r.raw[c] = (double*)malloc(sizeof(double) * 4 * tfs[c].n);
+    for (int i = 0; i < 4 * tfs[c].n; ++i) r.raw[c][i] = (double)tfs[c].rgba[i];
+  }
   for (int L = 0; L < v->levels; ++L)
     for (int c = 0; c < v->nch; ++c) {
       r.table[L][c] = (double*)malloc(sizeof(double) * 4 * tfs[c].n);
@@ -712,6 +771,7 @@ int or_render(const or_volume* v, const or_tf* tfs, const int32_t* leaf, const d
   }
   for (int L = 0; L < v->levels; ++L)
     for (int c = 0; c < v->nch; ++c) free(r.table[L][c]);
+  for (int c = 0; c < v->nch; ++c) free(r.raw[c]);
   return 1;
 }
 

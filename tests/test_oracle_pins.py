@@ -199,3 +199,83 @@ def test_stereo_mirror_symmetry():
     R = right["late"].reshape(H, W, 4)[:, ::-1]
     assert np.abs(L - R).max() < 1e-9
     assert np.array_equal(left["count_late"].reshape(H, W), right["count_late"].reshape(H, W)[:, ::-1])
+
+
+# ---------------------------------------------------------------- optical models and depth termination
+
+def test_emission_only_is_the_rectangle_rule_of_the_emission_integral():
+    """Emission-only ("DVR Techniques"): I = integral of the emitted intensity
+    along the ray, no absorption, alpha 0. In a constant medium emitting
+    alpha * rgb per reference step, n samples of width step give
+    n * step / ref * alpha * rgb, whatever the step."""
+    n = 16
+    vol = oracle.Volume([[np.full((n, n, n), 100, np.uint8)]], n)
+    a = float(np.float32(0.05))
+    rgb = tuple(float(np.float32(c)) for c in (0.2, 0.5, 0.8))
+    tf = _const_tf(rgb, a)
+    view, proj = _axial_camera(40.0, cx=8.0, cy=8.0)
+    sel = vol.select([tf], [view, view], [proj, proj], 9, tau=1.0)
+    c = 4 * 9 + 4
+    # (at steps 0.5 and 0.25 a lattice point falls on the exit, which the
+    # oracle flags as a possible one-sample difference; the count is exact)
+    for step, count in [(0.3, 54), (0.5, 32), (0.25, 64)]:
+        r = vol.render([tf], sel["leaf"], view, proj, 9, 9, step=step, pixels=[c], mode=oracle.MODE_EMISSION)
+        assert r["count_late"][0] == count and (r["flags"][0] == 0) == (step == 0.3)
+        w = count * step / 0.5 * a
+        assert r["late"][0] == pytest.approx([w * rgb[0], w * rgb[1], w * rgb[2], 0.0], abs=1e-12)
+        assert np.array_equal(r["early"], r["late"])  # no termination
+
+
+def test_mip_classifies_the_largest_sample():
+    """Maximum intensity projection: the transfer function of the largest
+    sampled value along the ray, premultiplied. A ray along z through the
+    voxel centres of column (8, 8) samples voxel centres exactly at t0 + 0.5
+    + k (step 0.5), so the maximum is the largest voxel of the column."""
+    n = 16
+    a = np.full((n, n, n), 10, np.uint8)
+    a[5, 8, 8] = 180      # z = 5
+    a[11, 8, 8] = 140     # z = 11: smaller, nearer the eye
+    a[3, 2, 2] = 250      # off the ray
+    vol = oracle.Volume([[a]], n)
+    ramp = np.zeros((256, 4), np.float32)
+    ramp[:, 0] = np.linspace(0, 1, 256)
+    ramp[:, 1] = 0.5
+    ramp[:, 2] = np.linspace(1, 0, 256)
+    ramp[:, 3] = np.linspace(0, 1, 256) ** 2
+    tf = oracle.make_tf(ramp, 0.0, 255.0)
+    view, proj = _axial_camera(40.0, cx=8.5, cy=8.5)
+    sel = vol.select([tf], [view, view], [proj, proj], 9, tau=1.0)
+    r = vol.render([tf], sel["leaf"], view, proj, 9, 9, pixels=[4 * 9 + 4], mode=oracle.MODE_MIP)
+    e = ramp[180].astype(np.float64)  # q = 180 exactly: entry 180
+    assert r["late"][0] == pytest.approx([e[3] * e[0], e[3] * e[1], e[3] * e[2], e[3]], abs=1e-12)
+    assert r["count_late"][0] == 32
+
+
+def test_depth_buffer_ends_the_ray_like_an_opaque_surface():
+    """Depth-buffer termination: lattice points at or beyond the surface
+    distance are not sampled. Constant medium, step 0.5 = reference step:
+    a surface at t0 + 4.25 leaves k = 0..8 (9 samples), A = 1 - (1-a)^9; a
+    surface before the entry leaves nothing; inf leaves the full ray."""
+    n = 16
+    vol = oracle.Volume([[np.full((n, n, n), 100, np.uint8)]], n)
+    a = float(np.float32(0.05))
+    tf = _const_tf((1.0, 1.0, 1.0), a)
+    view, proj = _axial_camera(40.0, cx=8.0, cy=8.0)  # entry t0 = 24 along the centre ray
+    sel = vol.select([tf], [view, view], [proj, proj], 9, tau=1.0)
+    c = 4 * 9 + 4
+    for surf, count in [(24.0 + 4.25, 9), (10.0, 0), (np.inf, 32)]:
+        depth = np.full((9, 9), np.inf)
+        depth.reshape(-1)[c] = surf
+        r = vol.render([tf], sel["leaf"], view, proj, 9, 9, pixels=[c], depth=depth)
+        assert r["count_late"][0] == count
+        assert r["late"][0][3] == pytest.approx(1.0 - (1.0 - a) ** count, abs=1e-12)
+    # with a model that scales voxels to metres, depth is in metres
+    model = synth.colmajor(synth.scale_translate(0.01, np.zeros(3)))
+    volm = oracle.Volume([[np.full((n, n, n), 100, np.uint8)]], n, model=model)
+    viewm = synth.colmajor(synth.look_at([0.08, 0.08, 0.40], [0.08, 0.08, 0.0], [0.0, 1.0, 0.0]))
+    projm = synth.colmajor(synth.perspective(90.0, 1.0, 0.001, 10.0))
+    selm = volm.select([tf], [viewm, viewm], [projm, projm], 9, tau=1.0)
+    depth = np.full((9, 9), np.inf)
+    depth.reshape(-1)[c] = 0.2825  # 28.25 voxels of 0.01 m
+    r = volm.render([tf], selm["leaf"], viewm, projm, 9, 9, pixels=[c], depth=depth)
+    assert r["count_late"][0] == 9
