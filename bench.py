@@ -571,6 +571,25 @@ def run_ours(args, rank, world, local_rank):
     avg_render_s = sum(render_ms) / len(render_ms) / 1e3
     achieved = (sum(alg) / len(alg)) / avg_render_s / 1e9
 
+    # the other optical models on the same poses (select + render per step)
+    modes = {}
+    for name, mode in (("emission_only", sg.SG_MODE_EMISSION), ("mip", sg.SG_MODE_MIP)):
+        prm_m = sg.render_params(step=STEP, term_alpha=TERM, empty_skip=1, mode=mode)
+        for i in range(3):
+            sg.sg_select_lod(vol, mine[i], stream=stream)
+            sg.sg_render(vol, mine[i], prm_m, outs, stream=stream)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nm = min(args.steps, 32)
+        torch.cuda.synchronize()
+        a0.record(stream)
+        for i in range(nm):
+            p = mine[(args.warmup + i) % NPOSES]
+            sg.sg_select_lod(vol, p, stream=stream)
+            sg.sg_render(vol, p, prm_m, outs, stream=stream)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        modes[name] = {"fps": round(nm / (a0.elapsed_time(a1) / 1e3), 2), "steps": nm}
+
     # end to end through the public C ABI with host buffers: pose in, both images out
     host = [torch.empty((H_EYE, W_EYE, 4), dtype=torch.float32, pin_memory=True) for _ in range(2)]
     e2e_steps = max(4, min(args.steps, 16))
@@ -614,7 +633,8 @@ def run_ours(args, rank, world, local_rank):
                 "e2e": {"value": round(e2e_s and e2e_steps / e2e_s, 3), "unit": "stereo frames/s",
                         "h2d_bytes_per_step": int(np.dtype(np.uint8).itemsize * len(bytes(mine[0]))),
                         "d2h_bytes_per_step": out_bytes},
-                "select_stats_last": sel_stats}
+                "select_stats_last": sel_stats,
+                "optical_models": modes}
         if cpu:
             line["cpu_baseline"] = cpu
         if batched:

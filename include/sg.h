@@ -250,15 +250,35 @@ sg_status sg_read_ranges(sg_volume* vol, int t, uint32_t* minmax, int64_t nnode)
 sg_status sg_read_brick(sg_volume* vol, int t, int c, int level, int bx, int by, int bz, void* host_out,
                         void* stream);
 
-enum { SG_MODE_EMISSION_ABSORPTION = 0 };
+/* Optical models ("DVR Techniques"):
+ * - EMISSION_ABSORPTION: front-to-back compositing, C += (1 - A) colour_s,
+ *   A += (1 - A) alpha_s, early termination at term_alpha (below).
+ * - EMISSION: the emission-only integral, no absorption and no early
+ *   termination: C += sum_c alpha_c colour_c (step 2^L / ref_step), with the
+ *   table's alpha for one reference step; the output alpha is 0 (composite
+ *   additively over the scene behind).
+ * - MIP: maximum intensity projection: per channel the largest trilinear
+ *   value along the ray, classified with the table as given, channels
+ *   blended as above, output premultiplied. Empty-space skipping stays exact
+ *   only when every channel's transparent entries are the lowest ones (a
+ *   table whose alpha is 0 up to some entry and positive after it); other
+ *   tables render MIP without skipping. Blocks that selection dropped as
+ *   transparent are not sampled in any mode. */
+enum { SG_MODE_EMISSION_ABSORPTION = 0, SG_MODE_EMISSION = 1, SG_MODE_MIP = 2 };
 
 typedef struct {
   float step;             /* level-0 sample spacing in voxels (> 0); level L samples every 2^L-th point */
-  float term_alpha;       /* early ray termination threshold, e.g. 0.99 (<= 0: 0.99) */
-  int32_t mode;           /* SG_MODE_EMISSION_ABSORPTION */
+  float term_alpha;       /* early ray termination threshold, e.g. 0.99 (<= 0: 0.99); EMISSION_ABSORPTION only */
+  int32_t mode;           /* SG_MODE_* */
   int32_t empty_skip;     /* 1: skip transparent blocks and sub-blocks (output unchanged) */
   uint32_t* sample_count[2]; /* optional device buffers (W*H per eye): samples composited per pixel */
   unsigned long long* sample_total; /* optional device counter: incremented by the samples composited */
+  const float* depth[2];  /* optional device buffers (W*H per eye, row 0 = top, 4-byte aligned): the
+                             distance in world units from the eye along each pixel's ray to an opaque
+                             surface (a scene's depth buffer turned into distances, "Volumetric and
+                             Mesh Data Compositing"); the ray ends there, taking no sample at or beyond it, and
+                             the caller composites the premultiplied image over the scene; +inf = no
+                             surface. sg_render / sg_render_host only. */
 } sg_render_params;
 
 /* Ray casts both eyes of a selected pose ("DVR Techniques"). For pixel (i,j)

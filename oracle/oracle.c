@@ -593,7 +593,7 @@ static void cast(const ray_t* r, int64_t pix, double* early, double* late, uint3
   }
   double t0 = tn > 0.0 ? tn : 0.0, t1 = tf;
   /* depth-buffer termination: an opaque surface at tmax ends the ray
-   * ("Depth Buffer"-style compositing of volume and geometry) */
+   * ("Volumetric and Mesh Data Compositing") */
   const double tsurf = r->tmax ? r->tmax[pix] : INFINITY;
   if (tsurf < t1) t1 = tsurf;
   double vmax[OR_MAX_CH];

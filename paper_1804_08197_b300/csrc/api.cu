@@ -260,7 +260,10 @@ sg_status check_render_params(const sg_render_params* r) {
   SG_CHECK_ARG(r, "render params are NULL");
   SG_CHECK_ARG(r->step > 0.0f && r->step < 1e6f, "render step must be > 0");
   SG_CHECK_ARG(r->term_alpha <= 1.0f, "term_alpha must be <= 1");
-  SG_CHECK_ARG(r->mode == SG_MODE_EMISSION_ABSORPTION, "unknown render mode");
+  SG_CHECK_ARG(r->mode == SG_MODE_EMISSION_ABSORPTION || r->mode == SG_MODE_EMISSION || r->mode == SG_MODE_MIP,
+               "unknown render mode");
+  for (int e = 0; e < 2; ++e)
+    SG_CHECK_ARG(((uintptr_t)r->depth[e] % 4) == 0, "depth buffers must be 4-byte aligned");
   return SG_OK;
 }
 
@@ -277,10 +280,11 @@ sg_status check_ready_for_render(sg_volume* v, const sg_pose* p) {
   return SG_OK;
 }
 
-sg_status prepare_lut(sg_volume* v, float step, cudaStream_t s) {
-  if (v->lut_step != step) {
-    SG_CUDA(launch_lut(v, step, s), "opacity-corrected tables");
+sg_status prepare_lut(sg_volume* v, float step, int mode, cudaStream_t s) {
+  if (v->lut_step != step || v->lut_mode != mode) {
+    SG_CUDA(launch_lut(v, step, mode, s), "opacity-corrected tables");
     v->lut_step = step;
+    v->lut_mode = mode;
   }
   return SG_OK;
 }
@@ -499,6 +503,13 @@ sg_status sg_set_transfer_function(sg_volume* v, int c, const float* rgba, int n
   t.hi = hi;
   t.ref_step = ref_step;
   t.rgba.assign(rgba, rgba + 4 * n);
+  {
+    int e = 0;
+    while (e < n && rgba[4 * e + 3] == 0.0f) ++e;
+    bool positive_after = true;
+    for (int k = e; k < n; ++k) positive_after &= rgba[4 * k + 3] > 0.0f;
+    t.low_end_transparent = positive_after;
+  }
   SG_CUDA(cudaMemcpyAsync(v->d_tf_raw + (size_t)c * kMaxTF * 4, t.rgba.data(), sizeof(float) * 4 * n,
                           cudaMemcpyHostToDevice, s),
           "transfer-function upload");
@@ -506,6 +517,7 @@ sg_status sg_set_transfer_function(sg_volume* v, int c, const float* rgba, int n
   // stream sync keeps it valid for an asynchronous copy from pageable memory
   SG_CUDA(cudaStreamSynchronize(s), "transfer-function upload");
   v->lut_step = -1.0f;
+  v->lut_mode = -1;
   ++v->tf_version;
   return refresh_flags(v, s);
 }
@@ -656,7 +668,7 @@ sg_status sg_render(sg_volume* v, const sg_pose* p, const sg_render_params* prm,
   if ((st = check_render_params(prm)) != SG_OK) return st;
   if ((st = check_ready_for_render(v, p)) != SG_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  if ((st = prepare_lut(v, prm->step, s)) != SG_OK) return st;
+  if ((st = prepare_lut(v, prm->step, prm->mode, s)) != SG_OK) return st;
   SG_CUDA(launch_render(v, p, 1, prm, out_rgba, s), "render");
   return SG_OK;
 }
@@ -693,6 +705,7 @@ sg_status sg_render_batch(sg_volume* v, const sg_pose* poses, int n, const sg_re
   SG_CHECK_ARG(v && poses && outs && n >= 1 && n <= 64, "volume/poses/outs NULL or n not in 1..64");
   sg_status st = check_render_params(prm);
   if (st != SG_OK) return st;
+  SG_CHECK_ARG(!prm->depth[0] && !prm->depth[1], "depth buffers apply to sg_render only");
   for (int i = 0; i < n; ++i) {
     if ((st = check_pose(v, &poses[i])) != SG_OK) return st;
     if ((st = check_ready_for_render(v, &poses[i])) != SG_OK) return st;
@@ -701,7 +714,7 @@ sg_status sg_render_batch(sg_volume* v, const sg_pose* poses, int n, const sg_re
                  "output buffers must be 16-byte aligned");
   }
   cudaStream_t s = (cudaStream_t)stream;
-  if ((st = prepare_lut(v, prm->step, s)) != SG_OK) return st;
+  if ((st = prepare_lut(v, prm->step, prm->mode, s)) != SG_OK) return st;
   SG_CUDA(launch_render(v, poses, n, prm, outs, s), "batched render");
   return SG_OK;
 }

@@ -63,6 +63,9 @@ struct TFHost {
   int n = 0;
   float lo = 0, hi = 1, ref_step = 0.5f;
   std::vector<float> rgba;
+  // alpha is 0 exactly on a run of entries starting at entry 0 and positive
+  // after it (so every transparent value lies below every visible one)
+  bool low_end_transparent = false;
 };
 
 }  // namespace sg
@@ -98,6 +101,7 @@ struct sg_volume {
   float* d_tf_raw = nullptr;       // [nch][kMaxTF][4]
   float4* d_lut = nullptr;         // [nch][levels][kMaxTF][2] opacity-corrected (entry, delta to next)
   float lut_step = -1.0f;
+  int lut_mode = -1;
   uint64_t tf_version = 0;
 
   // LRU state (pooled volumes)
@@ -133,7 +137,7 @@ cudaError_t launch_brick_ranges(sg_volume* v, int t, int c, int L, const int32_t
 // node flags for every node; sub-block bits / distances for every slot, or
 // only the nslots slots listed in device array d_slots
 cudaError_t launch_tf_flags(sg_volume* v, cudaStream_t s, const int32_t* d_slots = nullptr, int nslots = 0);
-cudaError_t launch_lut(sg_volume* v, float step, cudaStream_t s);
+cudaError_t launch_lut(sg_volume* v, float step, int mode, cudaStream_t s);
 
 // select.cu
 void compute_select_inputs(const sg_volume* v, const sg_pose* p, SelectInputs* out);

@@ -61,6 +61,7 @@ struct ImageJob {
   float4* out;
   uint32_t* cnt;
   const uint32_t* leaf;
+  const float* depth;  // optional: world distance to an opaque surface per pixel
 };
 
 template <int MAXI>
@@ -82,6 +83,8 @@ struct Args {
   float lo[kMaxCh], inv_w[kMaxCh];
   float step, inv_step, term;
   int empty_skip;
+  int mip_skip;        // MIP may skip transparent space (every table transparent only at its low end)
+  float inv_voxel;     // level-0 voxels per world unit (the model's uniform scale, inverted)
   unsigned long long* total_samples;
 };
 
@@ -181,6 +184,34 @@ __device__ __forceinline__ bool composite_sample(const Args& a, const T* __restr
   return acc.w >= a.term;
 }
 
+// Emission-only sample: every channel adds its table colour times its
+// emission weight (the table's alpha for this level is alpha * step 2^L /
+// ref_step); no absorption, the ray never stops early.
+template <typename T, int BK>
+__device__ __forceinline__ void emission_sample(const Args& a, const T* __restrict__ brick0, int L, float lx, float ly,
+                                                float lz, float4& acc) {
+  for (int c = 0; c < a.nch; ++c) {
+    const T* br = reinterpret_cast<const T*>(reinterpret_cast<const uint8_t*>(brick0) + (size_t)c * a.brick_bytes);
+    const float4 e = classify(a, c, L, tri<T, BK>(br, a.B, lx, ly, lz));
+    acc.x = fmaf(e.w, e.x, acc.x);
+    acc.y = fmaf(e.w, e.y, acc.y);
+    acc.z = fmaf(e.w, e.z, acc.z);
+  }
+}
+
+// Maximum intensity projection sample: the running maximum of each
+// channel's trilinear value.
+template <typename T, int BK>
+__device__ __forceinline__ void mip_sample(const Args& a, const T* __restrict__ brick0, float lx, float ly, float lz,
+                                           float (&vmax)[kMaxCh]) {
+#pragma unroll
+  for (int c = 0; c < kMaxCh; ++c) {
+    if (c >= a.nch) break;
+    const T* br = reinterpret_cast<const T*>(reinterpret_cast<const uint8_t*>(brick0) + (size_t)c * a.brick_bytes);
+    vmax[c] = fmaxf(vmax[c], tri<T, BK>(br, a.B, lx, ly, lz));
+  }
+}
+
 // exit distance of a ray from a slab along one axis, given the bound it
 // leaves through (the upper one for d > 0, the lower one for d < 0)
 __device__ __forceinline__ float exit_through(float o, float d, float inv, float bnd) {
@@ -196,7 +227,7 @@ __device__ inline int cell_of(float p, float invB, int lo, int hi) {
 // iteration (take a sample, jump over transparent sub-blocks, or move to
 // the next block), so the lanes of a warp stay in one loop instead of
 // diverging across nested ones.
-template <typename T, int BK>
+template <typename T, int BK, int MODE>
 __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int px, int py, bool active, float4& acc,
                                           uint32_t& cnt) {
   acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -225,11 +256,19 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
       tf = fminf(tf, fmaxf(t1, t2));
     }
   }
-  const float t0 = fmaxf(tn, 0.0f), t1 = tf;
+  const float t0 = fmaxf(tn, 0.0f);
+  float t1 = tf;
+  // an opaque surface from the scene's depth buffer ends the ray
+  if (J.depth && active) t1 = fminf(t1, __ldg(J.depth + (size_t)py * J.W + px) * a.inv_voxel);
   // a degenerate matrix gives a NaN direction and an unbounded segment: no hit
   const bool hit = active && isfinite(t0) && isfinite(t1) && t1 > t0 && (t1 - t0) * a.inv_step < 4.0e6f &&
                    isfinite(d.x + d.y + d.z);
   if (!hit) return;
+  // transparent space may be skipped unless a MIP maximum could lie there
+  const bool skip = a.empty_skip && (MODE != SG_MODE_MIP || a.mip_skip);
+  float vmax[kMaxCh];
+#pragma unroll
+  for (int c = 0; c < kMaxCh; ++c) vmax[c] = -INFINITY;
 #ifdef SG_RENDER_EVENT_STATS
   unsigned long long ev[8] = {0, 0, 0, 0, 0, 0, 1, 0};
 #endif
@@ -300,7 +339,7 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
       if (ez < texit) { texit = ez; ax = 2; }
       tend = fminf(texit, t1);
       kb = k;
-      render = !(e & kLeafNone) && !(a.empty_skip && (e & 16u));
+      render = !(e & kLeafNone) && !(skip && (e & 16u));
       SG_EV(render ? 2 : 3, 1);
       if (!render) continue;  // owns its lattice points without sampling them: leave at once
       kstep = 1 << L;
@@ -315,7 +354,7 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
     const float px0 = fmaf(t, d.x, o.x), py0 = fmaf(t, d.y, o.y), pz0 = fmaf(t, d.z, o.z);
     // brick-local coordinate: level-L position - block origin + 1 (apron) - 0.5 (voxel centre)
     const float lx = fmaf(px0 - lo.x, sL, 0.5f), ly = fmaf(py0 - lo.y, sL, 0.5f), lz = fmaf(pz0 - lo.z, sL, 0.5f);
-    if (a.empty_skip) {
+    if (skip) {
       const int sx = min(max(floor_i(lx - 0.5f) >> a.sub_shift, 0), nsm);
       const int sy = min(max(floor_i(ly - 0.5f) >> a.sub_shift, 0), nsm);
       const int sz = min(max(floor_i(lz - 0.5f) >> a.sub_shift, 0), nsm);
@@ -342,18 +381,25 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
     }
     ++cnt;
     SG_EV(0, 1);
+    bool stop = false;
+    if (MODE == SG_MODE_EMISSION_ABSORPTION) {
 #ifdef SG_RENDER_EVENT_STATS
-    const float w_before = acc.w;
-    bool stop = composite_sample<T, BK>(a, brick0, L, lx, ly, lz, acc);
-    SG_EV(7, acc.w != w_before ? 1 : 0);
+      const float w_before = acc.w;
+      stop = composite_sample<T, BK>(a, brick0, L, lx, ly, lz, acc);
+      SG_EV(7, acc.w != w_before ? 1 : 0);
 #else
-    bool stop = composite_sample<T, BK>(a, brick0, L, lx, ly, lz, acc);
+      stop = composite_sample<T, BK>(a, brick0, L, lx, ly, lz, acc);
 #endif
+    } else if (MODE == SG_MODE_EMISSION) {
+      emission_sample<T, BK>(a, brick0, L, lx, ly, lz, acc);
+    } else {
+      mip_sample<T, BK>(a, brick0, lx, ly, lz, vmax);
+    }
     if (stop) break;
     k += kstep;
     // the next lattice points of the same block, taken without a sub-block
-    // lookup: a sample in a transparent sub-block adds exactly nothing, so
-    // taking it is always exact
+    // lookup: a sample in a transparent sub-block adds exactly nothing (and
+    // cannot raise a MIP maximum that matters), so taking it is always exact
 #pragma unroll
     for (int u = 1; u < kSamplesPerIter; ++u) {
       const float t2 = lattice_t(k, t0, a);
@@ -362,11 +408,37 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
       const float mx = fmaf(qx - lo.x, sL, 0.5f), my = fmaf(qy - lo.y, sL, 0.5f), mz = fmaf(qz - lo.z, sL, 0.5f);
       ++cnt;
       SG_EV(0, 1);
-      stop = composite_sample<T, BK>(a, brick0, L, mx, my, mz, acc);
+      if (MODE == SG_MODE_EMISSION_ABSORPTION)
+        stop = composite_sample<T, BK>(a, brick0, L, mx, my, mz, acc);
+      else if (MODE == SG_MODE_EMISSION)
+        emission_sample<T, BK>(a, brick0, L, mx, my, mz, acc);
+      else
+        mip_sample<T, BK>(a, brick0, mx, my, mz, vmax);
       if (stop) break;
       k += kstep;
     }
     if (stop) break;
+  }
+  if (MODE == SG_MODE_MIP && cnt > 0) {
+    // classify each channel's maximum (the MIP tables hold the transfer
+    // functions as given, the same for every level), blend the channels
+    // additively with alpha capped at 1, premultiply
+    float sa = 0.0f, sr = 0.0f, sg = 0.0f, sb = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kMaxCh; ++c) {
+      if (c >= a.nch) break;
+      const float4 e = classify(a, c, 0, vmax[c]);
+      sa += e.w;
+      sr = fmaf(e.w, e.x, sr);
+      sg = fmaf(e.w, e.y, sg);
+      sb = fmaf(e.w, e.z, sb);
+    }
+    if (sa > 1.0f) {
+      const float r = 1.0f / sa;
+      sr *= r; sg *= r; sb *= r;
+      sa = 1.0f;
+    }
+    acc = make_float4(sr, sg, sb, sa);
   }
 #ifdef SG_RENDER_EVENT_STATS
   for (int i = 0; i < 8; ++i)
@@ -374,7 +446,7 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
 #endif
 }
 
-template <typename T, int MAXI, int BK>
+template <typename T, int MAXI, int BK, int MODE>
 __global__ void __launch_bounds__(kThreads, min_blocks(kThreads, 1, BK)) k_render(Args a, Jobs<MAXI> jobs) {
   const int tile = blockIdx.x;
   int im = 0;
@@ -389,7 +461,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(kThreads, 1, BK)) k_rende
 
   float4 acc;
   uint32_t cnt;
-  trace_ray<T, BK>(a, J, px, py, active, acc, cnt);
+  trace_ray<T, BK, MODE>(a, J, px, py, active, acc, cnt);
   if (active) {
     const size_t pix = (size_t)py * J.W + px;
     J.out[pix] = acc;
@@ -439,7 +511,7 @@ __global__ void __launch_bounds__(TW * TH / RPT, min_blocks(TW * TH / RPT, RPT, 
       const bool active = px < J.W && py < J.H;
       float4 acc;
       uint32_t cnt;
-      trace_ray<T, BK>(a, J, px, py, active, acc, cnt);
+      trace_ray<T, BK, SG_MODE_EMISSION_ABSORPTION>(a, J, px, py, active, acc, cnt);
       if (active) {
         const size_t pix = (size_t)py * J.W + px;
         J.out[pix] = acc;
@@ -548,6 +620,12 @@ Args make_args(const sg_volume* v, const sg_render_params* prm) {
   a.term = prm->term_alpha > 0.0f ? prm->term_alpha : 0.99f;
   a.empty_skip = prm->empty_skip;
   a.total_samples = prm->sample_total;
+  // voxels per world unit: the model's scale is uniform, so the length of
+  // its first column is the voxel size
+  const float* m = v->desc.model;
+  a.inv_voxel = (float)(1.0 / sqrt((double)m[0] * m[0] + (double)m[1] * m[1] + (double)m[2] * m[2]));
+  a.mip_skip = 1;
+  for (int c = 0; c < v->nch; ++c) a.mip_skip &= v->tf[c].low_end_transparent ? 1 : 0;
   return a;
 }
 
@@ -561,6 +639,7 @@ bool make_jobs(const sg_volume* v, const sg_pose* poses, int n, const sg_render_
       if (!setup_image(v, &poses[i], e, &J)) return false;
       J.out = reinterpret_cast<float4*>(outs[2 * i + e]);
       J.cnt = prm->sample_count[e] && n == 1 ? prm->sample_count[e] : nullptr;
+      J.depth = n == 1 ? prm->depth[e] : nullptr;
       J.tiles_x = (J.W + TW - 1) / TW;
       J.tile_begin = tiles;
       tiles += J.tiles_x * ((J.H + TH - 1) / TH);
@@ -612,16 +691,16 @@ cudaError_t dispatch_tiles(sg_volume* v, const Args& a, const sg_pose* poses, in
   return cudaErrorInvalidValue;
 }
 
-template <int MAXI, int BK>
+template <int MAXI, int BK, int MODE>
 cudaError_t launch_impl(sg_volume* v, const sg_pose* poses, int n, const sg_render_params* prm, float* const* outs,
                         cudaStream_t s) {
   Args a = make_args(v, prm);
   Jobs<MAXI> jobs;
   if (!make_jobs<MAXI>(v, poses, n, prm, outs, kTileW, kTileH, &jobs)) return cudaErrorInvalidValue;
   if (v->esize == 1)
-    k_render<uint8_t, MAXI, BK><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
+    k_render<uint8_t, MAXI, BK, MODE><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
   else
-    k_render<uint16_t, MAXI, BK><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
+    k_render<uint16_t, MAXI, BK, MODE><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
   return cudaGetLastError();
 }
 
@@ -630,10 +709,14 @@ cudaError_t launch_impl(sg_volume* v, const sg_pose* poses, int n, const sg_rend
 template <int BK>
 cudaError_t launch_b(sg_volume* v, const sg_pose* poses, int n, const sg_render_params* prm, float* const* outs,
                      cudaStream_t s) {
+  // emission-only and MIP run the one-CTA-per-16x8-tile kernel (the launch
+  // shapes and the autotuner serve the emission-absorption model)
+  if (prm->mode == SG_MODE_EMISSION) return launch_impl<128, BK, SG_MODE_EMISSION>(v, poses, n, prm, outs, s);
+  if (prm->mode == SG_MODE_MIP) return launch_impl<128, BK, SG_MODE_MIP>(v, poses, n, prm, outs, s);
   const sg_render_config& c = v->render_cfg;
   if (c.tile_w == 0) {  // default: one 16 x 8 CTA per tile
-    if (n == 1) return launch_impl<2, BK>(v, poses, n, prm, outs, s);
-    return launch_impl<128, BK>(v, poses, n, prm, outs, s);
+    if (n == 1) return launch_impl<2, BK, SG_MODE_EMISSION_ABSORPTION>(v, poses, n, prm, outs, s);
+    return launch_impl<128, BK, SG_MODE_EMISSION_ABSORPTION>(v, poses, n, prm, outs, s);
   }
   Args a = make_args(v, prm);
   if (v->esize == 1) return dispatch_tiles<uint8_t, BK>(v, a, poses, n, prm, outs, c, s);

@@ -147,17 +147,28 @@ __global__ void k_sub_dist(const uint64_t* __restrict__ bits, int nsub, int word
 // Opacity correction per level: a level-L sample stands for step 2^L
 // level-0 voxels: alpha' = 1 - (1 - alpha)^(step 2^L / ref_step).
 struct LutParams {
-  int nch, levels;
+  int nch, levels, mode;
   int n[kMaxCh];
   float ref[kMaxCh];
 };
 
+// Table entry e of channel c for level L, per optical model: emission-
+// absorption stores the opacity of one level-L sample (step 2^L level-0
+// voxels), 1 - (1 - alpha)^(step 2^L / ref_step); emission-only stores the
+// emission weight of that sample, alpha * step 2^L / ref_step; maximum
+// intensity projection stores the table as given.
 __device__ __forceinline__ float4 lut_entry(const float* __restrict__ raw, const LutParams& p, float step, int c,
                                             int L, int e) {
   const float* r = raw + ((size_t)c * kMaxTF + e) * 4;
   const float ex = step * (float)(1 << L) / p.ref[c];
   const float a = r[3];
-  const float ac = (a >= 1.0f) ? 1.0f : 1.0f - powf(1.0f - a, ex);
+  float ac;
+  if (p.mode == SG_MODE_EMISSION)
+    ac = a * ex;
+  else if (p.mode == SG_MODE_MIP)
+    ac = a;
+  else
+    ac = (a >= 1.0f) ? 1.0f : 1.0f - powf(1.0f - a, ex);
   return make_float4(r[0], r[1], r[2], ac);
 }
 
@@ -223,10 +234,11 @@ cudaError_t launch_tf_flags(sg_volume* v, cudaStream_t s, const int32_t* d_slots
   return cudaGetLastError();
 }
 
-cudaError_t launch_lut(sg_volume* v, float step, cudaStream_t s) {
+cudaError_t launch_lut(sg_volume* v, float step, int mode, cudaStream_t s) {
   LutParams p;
   p.nch = v->nch;
   p.levels = v->levels;
+  p.mode = mode;
   for (int c = 0; c < kMaxCh; ++c) {
     p.n[c] = c < v->nch ? v->tf[c].n : 2;
     p.ref[c] = c < v->nch ? v->tf[c].ref_step : 1.0f;

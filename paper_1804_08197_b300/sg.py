@@ -15,7 +15,7 @@ LIB_PATH = os.environ.get("SG_LIBRARY") or os.path.join(HERE, "libsg.so")
 
 SG_OK, SG_ERR_INVALID_ARG, SG_ERR_OOM, SG_ERR_CUDA, SG_ERR_NOT_RESIDENT, SG_ERR_TIMEOUT, SG_ERR_STATE = range(7)
 SG_U8, SG_U16 = 1, 2
-SG_MODE_EMISSION_ABSORPTION = 0
+SG_MODE_EMISSION_ABSORPTION, SG_MODE_EMISSION, SG_MODE_MIP = 0, 1, 2
 STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_OOM", 3: "SG_ERR_CUDA", 4: "SG_ERR_NOT_RESIDENT",
                 5: "SG_ERR_TIMEOUT", 6: "SG_ERR_STATE"}
 
@@ -57,7 +57,7 @@ class sg_select_stats(ctypes.Structure):
 class sg_render_params(ctypes.Structure):
     _fields_ = [("step", ctypes.c_float), ("term_alpha", ctypes.c_float), ("mode", ctypes.c_int32),
                 ("empty_skip", ctypes.c_int32), ("sample_count", ctypes.c_void_p * 2),
-                ("sample_total", ctypes.c_void_p)]
+                ("sample_total", ctypes.c_void_p), ("depth", ctypes.c_void_p * 2)]
 
 
 class sg_render_config(ctypes.Structure):
@@ -242,14 +242,20 @@ def sg_read_brick(vol, t, c, level, bx, by, bz, host_out, stream=None):
     _check(lib.sg_read_brick(vol, t, c, level, bx, by, bz, _ptr(host_out), _stream(stream)))
 
 
-def render_params(step=0.5, term_alpha=0.99, empty_skip=1, sample_count=None, sample_total=None):
+def render_params(step=0.5, term_alpha=0.99, empty_skip=1, sample_count=None, sample_total=None,
+                  mode=SG_MODE_EMISSION_ABSORPTION, depth=None):
+    """depth: optional pair of device float buffers (H, W) per eye, the world
+    distance along each pixel's ray to an opaque surface (inf = none)."""
     r = sg_render_params()
     if sample_total is not None:
         r.sample_total = _ptr(sample_total).value
-    r.step, r.term_alpha, r.mode, r.empty_skip = step, term_alpha, SG_MODE_EMISSION_ABSORPTION, empty_skip
+    r.step, r.term_alpha, r.mode, r.empty_skip = step, term_alpha, mode, empty_skip
     if sample_count is not None:
         r.sample_count[0] = _ptr(sample_count[0]).value
         r.sample_count[1] = _ptr(sample_count[1]).value
+    if depth is not None:
+        r.depth[0] = _ptr(depth[0]).value
+        r.depth[1] = _ptr(depth[1]).value
     return r
 
 

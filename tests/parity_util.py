@@ -68,20 +68,24 @@ class GpuCase:
         ref = self.ovol.select(self.otfs, views, projs, H, tau=tau, ranges=self.ranges)
         return pose, stats, (cells, state, req), ref
 
-    def render(self, pose, step=0.5, empty_skip=1, counts=True, term=0.99):
+    def render(self, pose, step=0.5, empty_skip=1, counts=True, term=0.99, mode=0, depth=None):
+        """depth: optional pair of (H, W) float32 numpy arrays (world distances)."""
         torch, sg = self.torch, self.sg
         W, H = pose.width, pose.height
         outs = [torch.empty((H, W, 4), dtype=torch.float32, device="cuda") for _ in range(2)]
         cnt = [torch.zeros((H, W), dtype=torch.int32, device="cuda") for _ in range(2)] if counts else None
-        prm = sg.render_params(step=step, term_alpha=term, empty_skip=empty_skip, sample_count=cnt)
+        dd = None if depth is None else [torch.from_numpy(np.ascontiguousarray(d, np.float32)).cuda() for d in depth]
+        prm = sg.render_params(step=step, term_alpha=term, empty_skip=empty_skip, sample_count=cnt, mode=mode,
+                               depth=dd)
         sg.sg_render(self.vol, pose, prm, outs)
         torch.cuda.synchronize()
         imgs = [o.cpu().numpy().reshape(-1, 4) for o in outs]
         cs = [c.cpu().numpy().reshape(-1).astype(np.int64) for c in cnt] if counts else None
         return imgs, cs
 
-    def oracle_render(self, leaf, view, proj, W, H, step=0.5, pixels=None):
-        return self.ovol.render(self.otfs, leaf, view, proj, W, H, step=step, pixels=pixels)
+    def oracle_render(self, leaf, view, proj, W, H, step=0.5, pixels=None, mode=0, depth=None):
+        return self.ovol.render(self.otfs, leaf, view, proj, W, H, step=step, pixels=pixels, mode=mode,
+                                depth=depth)
 
     def close(self):
         self.sg.sg_volume_destroy(self.vol)
