@@ -69,7 +69,9 @@ def _load():
         L.or_tf_table.argtypes = [vp, dbl, vp]
         L.or_classify.argtypes = [vp, vp, dbl, vp]
         L.or_render.argtypes = [vp, vp, vp, vp, vp, i32, i32, dbl, dbl, dbl, dbl, vp, i64,
-                                vp, vp, vp, vp, vp, i32, i32, vp]
+                                vp, vp, vp, vp, vp, i32, i32, vp, vp]
+        L.or_lens_unwarp_point.argtypes = [vp, dbl, dbl, vp, vp]
+        L.or_unwarp.argtypes = [vp, vp, i32, i32, vp, i32, i32]
         L.or_render.restype = i32
         L.or_max_threads.restype = i32
         _lib = L
@@ -103,6 +105,32 @@ def pyramid(level0, levels):
         dst = np.empty(((src.shape[0] + 1) // 2, (src.shape[1] + 1) // 2, (src.shape[2] + 1) // 2), src.dtype)
         lib.or_pyramid_level(_p(src), dt, _p(sd), _p(dst))
         out.append(dst)
+    return out
+
+
+class Lens(ctypes.Structure):
+    """Radial lens model of one eye ("DVR for HMD"): warped NDC w looks
+    through undistorted NDC u = c + (w - c) (1 + k1 r^2 + k2 r^4) scale,
+    r^2 = ((w - c)_x aspect)^2 + (w - c)_y^2."""
+    _fields_ = [("k1", ctypes.c_double), ("k2", ctypes.c_double), ("scale", ctypes.c_double),
+                ("aspect", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double)]
+
+
+def lens(k1, k2, scale, aspect, cx=0.0, cy=0.0):
+    return Lens(float(k1), float(k2), float(scale), float(aspect), float(cx), float(cy))
+
+
+def unwarp_point(ln, ux, uy):
+    wx, wy = ctypes.c_double(), ctypes.c_double()
+    _load().or_lens_unwarp_point(ctypes.byref(ln), float(ux), float(uy), ctypes.byref(wx), ctypes.byref(wy))
+    return wx.value, wy.value
+
+
+def unwarp(ln, warped, W, H):
+    """warped: (Hw, Ww, 4) float32 RGBA -> (H, W, 4) FP64 in the undistorted space."""
+    w = np.ascontiguousarray(warped, np.float32)
+    out = np.zeros((H, W, 4))
+    _load().or_unwarp(ctypes.byref(ln), _p(w), w.shape[1], w.shape[0], _p(out), W, H)
     return out
 
 
@@ -197,7 +225,7 @@ class Volume:
         return _load().or_sample(ctypes.byref(self._s), int(L), int(c), _p(pp))
 
     def render(self, tfs, leaf, view, proj, W, H, step=0.5, term=0.99, term_tol=1e-4, eps=1e-3,
-               pixels=None, nthreads=0, mode=MODE_EA, depth=None):
+               pixels=None, nthreads=0, mode=MODE_EA, depth=None, lens=None):
         """Cast rays for `pixels` (flat ids j*W+i; None = all). Returns dict
         with early/late RGBA (n,4) FP64, sample counts and flags.
 
@@ -205,7 +233,8 @@ class Volume:
         MODE_MIP (maximum intensity projection). depth: optional (H, W)
         distances in world units from the eye along each pixel's ray to an
         opaque surface that ends the ray (inf = none); converted to level-0
-        voxels with the model's uniform scale."""
+        voxels with the model's uniform scale. lens: a Lens for rays through
+        the warped image (W x H is then the warped image's size)."""
         pix = None if pixels is None else np.ascontiguousarray(pixels, np.int64)
         tmax = None
         if depth is not None:
@@ -219,7 +248,8 @@ class Volume:
         p = np.ascontiguousarray(np.asarray(proj, np.float64).reshape(16))
         ok = _load().or_render(ctypes.byref(self._s), _tf_array(tfs), _p(np.ascontiguousarray(leaf, np.int32)),
                                _p(v), _p(p), W, H, step, term, term_tol, eps, _p(pix), n,
-                               _p(e), _p(l), _p(ce), _p(cl), _p(fl), int(nthreads), int(mode), _p(tmax))
+                               _p(e), _p(l), _p(ce), _p(cl), _p(fl), int(nthreads), int(mode), _p(tmax),
+                               ctypes.byref(lens) if lens is not None else None)
         if not ok:
             raise ValueError("singular view/projection/model matrix")
         return dict(early=e, late=l, count_early=ce, count_late=cl, flags=fl)

@@ -522,6 +522,77 @@ enum { FL_FACE = 1, FL_TEDGE = 2, FL_TERM = 4, FL_COUNT = 8 };
  * maximum intensity projection (the classified maximum along the ray). */
 enum { OR_MODE_EA = 0, OR_MODE_EMISSION = 1, OR_MODE_MIP = 2 };
 
+/* Radial lens model ("DVR for HMD"): the image is rendered in the lens's
+ * warped space with one ray per warped pixel. A warped NDC point w at offset
+ * d = w - c from the lens centre c looks through the undistorted NDC point
+ * u = c + d f(r) s, with f(r) = 1 + k1 r^2 + k2 r^4, r^2 = (d_x aspect)^2 +
+ * d_y^2 (aspect = width / height, so r is isotropic on the display) and s
+ * the scale. */
+typedef struct {
+  double k1, k2, scale, aspect, cx, cy;
+} or_lens;
+
+static void lens_warp_to_undistorted(const or_lens* L, double wx, double wy, double* ux, double* uy) {
+  double dx = wx - L->cx, dy = wy - L->cy;
+  double r2 = dx * L->aspect * dx * L->aspect + dy * dy;
+  double f = (1.0 + L->k1 * r2 + L->k2 * r2 * r2) * L->scale;
+  *ux = L->cx + dx * f;
+  *uy = L->cy + dy * f;
+}
+
+/* Inverse of the map above (k1, k2 >= 0, so r f(r) is increasing): given
+ * the undistorted u, the warped w. rho = |(u - c) / s| (aspect-weighted)
+ * equals r f(r); r is found by bisection on [0, rho] to full precision. */
+void or_lens_unwarp_point(const or_lens* L, double ux, double uy, double* wx, double* wy) {
+  double ex = (ux - L->cx) / L->scale, ey = (uy - L->cy) / L->scale;
+  double rho = sqrt(ex * L->aspect * ex * L->aspect + ey * ey);
+  if (rho == 0.0) { *wx = L->cx; *wy = L->cy; return; }
+  double lo = 0.0, hi = rho;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    double g = mid * (1.0 + L->k1 * mid * mid + L->k2 * mid * mid * mid * mid);
+    if (g < rho) lo = mid; else hi = mid;
+  }
+  double r = 0.5 * (lo + hi);
+  double f = 1.0 + L->k1 * r * r + L->k2 * r * r * r * r;
+  *wx = L->cx + ex / f;
+  *wy = L->cy + ey / f;
+}
+
+/* Resample a warped RGBA image (Ww x Hw, row 0 = top) to the undistorted
+ * image (W x H): output pixel centre u -> warped point w -> bilinear tap of
+ * the warped pixel centres (edge pixels replicated); points outside the
+ * warped image [-1, 1]^2 give (0,0,0,0). */
+void or_unwarp(const or_lens* L, const float* warped, int Ww, int Hw, double* out, int W, int H) {
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < H; ++j)
+    for (int i = 0; i < W; ++i) {
+      double ux = 2.0 * (i + 0.5) / W - 1.0, uy = 1.0 - 2.0 * (j + 0.5) / H, wx, wy;
+      or_lens_unwarp_point(L, ux, uy, &wx, &wy);
+      double* o = out + 4 * ((int64_t)j * W + i);
+      if (!(wx >= -1.0 && wx <= 1.0 && wy >= -1.0 && wy <= 1.0)) {
+        o[0] = o[1] = o[2] = o[3] = 0.0;
+        continue;
+      }
+      double px = (wx + 1.0) * 0.5 * Ww - 0.5, py = (1.0 - wy) * 0.5 * Hw - 0.5;
+      double fx = floor(px), fy = floor(py);
+      double ax = px - fx, ay = py - fy;
+      int x0 = (int)fx, y0 = (int)fy;
+      for (int k = 0; k < 4; ++k) {
+        double v = 0.0;
+        for (int b = 0; b < 2; ++b)
+          for (int a = 0; a < 2; ++a) {
+            int xx = x0 + a, yy = y0 + b;
+            xx = xx < 0 ? 0 : (xx > Ww - 1 ? Ww - 1 : xx);
+            yy = yy < 0 ? 0 : (yy > Hw - 1 ? Hw - 1 : yy);
+            double w = (a ? ax : 1.0 - ax) * (b ? ay : 1.0 - ay);
+            v += w * (double)warped[4 * ((int64_t)yy * Ww + xx) + k];
+          }
+        o[k] = v;
+      }
+    }
+}
+
 typedef struct {
   const or_volume* v;
   const or_tf* tf;
@@ -536,6 +607,7 @@ typedef struct {
   double step, term, term_tol, eps;
   int mode;
   const double* tmax; /* per image pixel: the ray ends there (level-0 voxels from the eye); NULL = none */
+  const or_lens* lens; /* rays through the warped image; NULL = none */
 } ray_t;
 
 static int node_level(const ray_t* r, int32_t id) {
@@ -570,6 +642,7 @@ static void cast(const ray_t* r, int64_t pix, double* early, double* late, uint3
                  uint8_t* flag) {
   int i = (int)(pix % r->W), j = (int)(pix / r->W);
   double x = 2.0 * (i + 0.5) / r->W - 1.0, y = 1.0 - 2.0 * (j + 0.5) / r->H;
+  if (r->lens) lens_warp_to_undistorted(r->lens, x, y, &x, &y);
   double pn[4] = {x, y, -1.0, 1.0}, pf[4] = {x, y, 1.0, 1.0}, a[4], b[4];
   mat_apply(r->inv, pn, a);
   mat_apply(r->inv, pf, b);
@@ -738,12 +811,13 @@ static void cast(const ray_t* r, int64_t pix, double* early, double* late, uint3
 int or_render(const or_volume* v, const or_tf* tfs, const int32_t* leaf, const double* view,
               const double* proj, int W, int H, double step, double term, double term_tol, double eps,
               const int64_t* pix, int64_t npix, double* rgba_early, double* rgba_late, uint32_t* cnt_early,
-              uint32_t* cnt_late, uint8_t* flags, int nthreads, int mode, const double* tmax) {
+              uint32_t* cnt_late, uint8_t* flags, int nthreads, int mode, const double* tmax,
+              const or_lens* lens) {
   ray_t r;
   memset(&r, 0, sizeof r);
   r.v = v; r.tf = tfs; r.leaf = leaf; r.W = W; r.H = H;
   r.step = step; r.term = term; r.term_tol = term_tol; r.eps = eps;
-  r.mode = mode; r.tmax = tmax;
+  r.mode = mode; r.tmax = tmax; r.lens = lens;
   or_node_count(v, r.off);
   level_blocks(v, 0, r.nb0);
   double vm[16], pvm[16], vminv[16];

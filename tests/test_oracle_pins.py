@@ -279,3 +279,58 @@ def test_depth_buffer_ends_the_ray_like_an_opaque_surface():
     depth.reshape(-1)[c] = 0.2825  # 28.25 voxels of 0.01 m
     r = volm.render([tf], selm["leaf"], viewm, projm, 9, 9, pixels=[c], depth=depth)
     assert r["count_late"][0] == 9
+
+
+# ---------------------------------------------------------------- warped-space rays (DVR for HMD)
+
+def test_identity_lens_casts_the_plain_rays():
+    """k1 = k2 = 0, scale 1: every warped pixel looks through its own centre,
+    so the warped render equals the plain one exactly."""
+    a = synth.gaussians_u8(32, seed=11, count=3)
+    vol = oracle.Volume([oracle.pyramid(a, 2)], 16)
+    tf = oracle.make_tf(synth.tf_piecewise(2001), 0.0, 255.0)
+    view, proj = synth.orbit_camera(32, seed=12, width=24, height=20)
+    sel = vol.select([tf], [view, view], [proj, proj], 20)
+    plain = vol.render([tf], sel["leaf"], view, proj, 24, 20)
+    warped = vol.render([tf], sel["leaf"], view, proj, 24, 20, lens=oracle.lens(0.0, 0.0, 1.0, 24 / 20))
+    assert np.array_equal(plain["late"], warped["late"]) and plain["late"][:, 3].max() > 0.05
+
+
+def test_lens_inverse_solves_the_radial_polynomial():
+    """The unwarp point is the preimage: warping it back gives u again, for a
+    barrel model with an off-centre lens (brute force round trip)."""
+    ln = oracle.lens(0.22, 0.24, 1.0 / 1.46, 0.9, cx=0.08, cy=-0.03)
+    rng = np.random.default_rng(4)
+    for ux, uy in rng.uniform(-1, 1, (200, 2)):
+        wx, wy = oracle.unwarp_point(ln, ux, uy)
+        dx, dy = wx - 0.08, wy + 0.03
+        r2 = (dx * 0.9) ** 2 + dy ** 2
+        f = (1 + 0.22 * r2 + 0.24 * r2 * r2) / 1.46
+        assert 0.08 + dx * f == pytest.approx(ux, abs=1e-13) and -0.03 + dy * f == pytest.approx(uy, abs=1e-13)
+
+
+def test_unwarp_reproduces_a_linear_warped_image():
+    """Bilinear taps reproduce an affine image exactly, so unwarping the
+    warped image g(w) = a w_x + b w_y + c gives g at the preimage of every
+    output pixel (inside the warped image, away from its edge pixels)."""
+    ln = oracle.lens(0.2, 0.1, 1.0 / 1.3, 1.0)
+    Ww, Hw, W, H = 40, 40, 56, 56
+    jj, ii = np.meshgrid(np.arange(Hw), np.arange(Ww), indexing="ij")
+    wx, wy = 2 * (ii + 0.5) / Ww - 1, 1 - 2 * (jj + 0.5) / Hw
+    g = np.zeros((Hw, Ww, 4), np.float32)
+    g[..., 0] = 0.3 * wx + 0.5
+    g[..., 1] = -0.2 * wy + 0.5
+    g[..., 3] = 1.0
+    out = oracle.unwarp(ln, g, W, H)
+    checked = 0
+    for j in range(H):
+        for i in range(W):
+            ux, uy = 2 * (i + 0.5) / W - 1, 1 - 2 * (j + 0.5) / H
+            px, py = oracle.unwarp_point(ln, ux, uy)
+            if abs(px) > 1 - 2.0 / Ww or abs(py) > 1 - 2.0 / Hw:
+                continue
+            assert out[j, i, 0] == pytest.approx(0.3 * px + 0.5, abs=2e-7)
+            assert out[j, i, 1] == pytest.approx(-0.2 * py + 0.5, abs=2e-7)
+            assert out[j, i, 3] == pytest.approx(1.0, abs=1e-12)
+            checked += 1
+    assert checked > W * H // 3
