@@ -250,6 +250,22 @@ sg_status sg_read_ranges(sg_volume* vol, int t, uint32_t* minmax, int64_t nnode)
 sg_status sg_read_brick(sg_volume* vol, int t, int c, int level, int bx, int by, int bz, void* host_out,
                         void* stream);
 
+/* Radial lens model of an HMD eye ("DVR for HMD"): the image is rendered in
+ * the lens's warped space, one ray per warped pixel, and unwarped afterwards
+ * (sg_unwarp), so no rays are spent on detail the lens would discard. A
+ * warped NDC point w (pixel (i,j) of a Ww x Hw image: (2(i+0.5)/Ww - 1,
+ * 1 - 2(j+0.5)/Hw)) at offset d = w - c from the lens centre c looks through
+ * the undistorted NDC point u = c + d (1 + k1 r^2 + k2 r^4) scale, with
+ * r^2 = (d_x aspect)^2 + d_y^2. k1, k2 >= 0; scale > 0 (0: 1 / (1 + k1 +
+ * k2), which maps the warped edge midpoints of a centred lens to the
+ * undistorted ones); aspect > 0 (0: the image's width / height). A warped
+ * image of scale * W x scale * H pixels has the undistorted W x H image's
+ * pixel density at the lens centre. */
+typedef struct {
+  float k1, k2, scale, aspect;
+  float centre[2][2]; /* lens centre per eye, NDC (x, y) */
+} sg_lens;
+
 /* Optical models ("DVR Techniques"):
  * - EMISSION_ABSORPTION: front-to-back compositing, C += (1 - A) colour_s,
  *   A += (1 - A) alpha_s, early termination at term_alpha (below).
@@ -279,6 +295,8 @@ typedef struct {
                              Mesh Data Compositing"); the ray ends there, taking no sample at or beyond it, and
                              the caller composites the premultiplied image over the scene; +inf = no
                              surface. sg_render / sg_render_host only. */
+  const sg_lens* lens;    /* optional: rays through the lens-warped image (the pose's width/height are the
+                             warped image's); sg_render / sg_render_host only */
 } sg_render_params;
 
 /* Ray casts both eyes of a selected pose ("DVR Techniques"). For pixel (i,j)
@@ -307,6 +325,16 @@ sg_status sg_render_host(sg_volume* vol, const sg_pose* pose, const sg_render_pa
  * several viewers). outs[2i + e] is pose i's eye e (device, W*H*4 floats). */
 sg_status sg_render_batch(sg_volume* vol, const sg_pose* poses, int n, const sg_render_params* params,
                           float** outs, void* stream);
+
+/* Unwarps both eyes of a warped render ("DVR for HMD"): output pixel (i,j)
+ * of the W x H undistorted image takes the preimage w of its NDC centre under
+ * the lens map (solved by Newton iterations on the radial polynomial) and a
+ * bilinear tap of the warped image's pixel centres, edge pixels replicated;
+ * preimages outside the warped image give (0,0,0,0). warped[e] / out[e]:
+ * device RGBA float buffers (Ww*Hw*4, W*H*4 floats, 16-byte aligned). Errors:
+ * INVALID_ARG, CUDA. */
+sg_status sg_unwarp(const sg_lens* lens, const float* warped[2], int Ww, int Hw, float* out[2], int W, int H,
+                    void* stream);
 
 /* How sg_render / sg_render_batch map rays onto the GPU. tile_w x tile_h
  * pixel tiles (warps cover 8 x 4 pixels), rays_per_thread rays per thread;

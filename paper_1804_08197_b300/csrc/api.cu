@@ -264,6 +264,10 @@ sg_status check_render_params(const sg_render_params* r) {
                "unknown render mode");
   for (int e = 0; e < 2; ++e)
     SG_CHECK_ARG(((uintptr_t)r->depth[e] % 4) == 0, "depth buffers must be 4-byte aligned");
+  if (r->lens)
+    SG_CHECK_ARG(r->lens->k1 >= 0.0f && r->lens->k2 >= 0.0f && r->lens->scale >= 0.0f && r->lens->aspect >= 0.0f &&
+                     r->lens->k1 < 100.0f && r->lens->k2 < 100.0f,
+                 "lens: k1, k2 in [0, 100), scale and aspect >= 0");
   return SG_OK;
 }
 
@@ -706,6 +710,7 @@ sg_status sg_render_batch(sg_volume* v, const sg_pose* poses, int n, const sg_re
   sg_status st = check_render_params(prm);
   if (st != SG_OK) return st;
   SG_CHECK_ARG(!prm->depth[0] && !prm->depth[1], "depth buffers apply to sg_render only");
+  SG_CHECK_ARG(!prm->lens, "lens-warped rendering applies to sg_render only");
   for (int i = 0; i < n; ++i) {
     if ((st = check_pose(v, &poses[i])) != SG_OK) return st;
     if ((st = check_ready_for_render(v, &poses[i])) != SG_OK) return st;
@@ -716,6 +721,21 @@ sg_status sg_render_batch(sg_volume* v, const sg_pose* poses, int n, const sg_re
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = prepare_lut(v, prm->step, prm->mode, s)) != SG_OK) return st;
   SG_CUDA(launch_render(v, poses, n, prm, outs, s), "batched render");
+  return SG_OK;
+}
+
+sg_status sg_unwarp(const sg_lens* lens, const float* warped[2], int Ww, int Hw, float* out[2], int W, int H,
+                    void* stream) {
+  SG_CHECK_ARG(lens && warped && out && warped[0] && warped[1] && out[0] && out[1], "lens or buffers NULL");
+  SG_CHECK_ARG(Ww > 0 && Hw > 0 && W > 0 && H > 0 && Ww <= 32768 && Hw <= 32768 && W <= 32768 && H <= 32768,
+               "image sizes must be in 1..32768");
+  SG_CHECK_ARG(lens->k1 >= 0.0f && lens->k2 >= 0.0f && lens->scale >= 0.0f && lens->aspect >= 0.0f &&
+                   lens->k1 < 100.0f && lens->k2 < 100.0f,
+               "lens: k1, k2 in [0, 100), scale and aspect >= 0");
+  for (int e = 0; e < 2; ++e)
+    SG_CHECK_ARG(((uintptr_t)warped[e] % 16) == 0 && ((uintptr_t)out[e] % 16) == 0, "buffers must be 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int e = 0; e < 2; ++e) SG_CUDA(launch_unwarp(lens, e, warped[e], Ww, Hw, out[e], W, H, s), "unwarp");
   return SG_OK;
 }
 

@@ -138,6 +138,8 @@ cudaError_t launch_brick_ranges(sg_volume* v, int t, int c, int L, const int32_t
 // only the nslots slots listed in device array d_slots
 cudaError_t launch_tf_flags(sg_volume* v, cudaStream_t s, const int32_t* d_slots = nullptr, int nslots = 0);
 cudaError_t launch_lut(sg_volume* v, float step, int mode, cudaStream_t s);
+cudaError_t launch_unwarp(const sg_lens* lens, int e, const float* warped, int Ww, int Hw, float* out, int W, int H,
+                          cudaStream_t s);
 
 // select.cu
 void compute_select_inputs(const sg_volume* v, const sg_pose* p, SelectInputs* out);

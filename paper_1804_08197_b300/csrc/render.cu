@@ -62,6 +62,9 @@ struct ImageJob {
   uint32_t* cnt;
   const uint32_t* leaf;
   const float* depth;  // optional: world distance to an opaque surface per pixel
+  // optional lens: NDC of a warped pixel -> the undistorted NDC it looks through
+  int lens;
+  float k1, k2, lscale, laspect, lcx, lcy;
 };
 
 template <int MAXI>
@@ -232,8 +235,15 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
                                           uint32_t& cnt) {
   acc = make_float4(0.f, 0.f, 0.f, 0.f);
   cnt = 0;
-  const float x = 2.0f * ((float)px + 0.5f) / (float)J.W - 1.0f;
-  const float y = 1.0f - 2.0f * ((float)py + 0.5f) / (float)J.H;
+  float x = 2.0f * ((float)px + 0.5f) / (float)J.W - 1.0f;
+  float y = 1.0f - 2.0f * ((float)py + 0.5f) / (float)J.H;
+  if (J.lens) {
+    const float ex = x - J.lcx, ey = y - J.lcy;
+    const float r2 = (ex * J.laspect) * (ex * J.laspect) + ey * ey;
+    const float f = (1.0f + r2 * (J.k1 + J.k2 * r2)) * J.lscale;
+    x = fmaf(ex, f, J.lcx);
+    y = fmaf(ey, f, J.lcy);
+  }
   float3 d = make_float3(fmaf(J.dx[0], x, fmaf(J.dy[0], y, J.d0[0])), fmaf(J.dx[1], x, fmaf(J.dy[1], y, J.d0[1])),
                          fmaf(J.dx[2], x, fmaf(J.dy[2], y, J.d0[2])));
   const float dn = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
@@ -640,6 +650,17 @@ bool make_jobs(const sg_volume* v, const sg_pose* poses, int n, const sg_render_
       J.out = reinterpret_cast<float4*>(outs[2 * i + e]);
       J.cnt = prm->sample_count[e] && n == 1 ? prm->sample_count[e] : nullptr;
       J.depth = n == 1 ? prm->depth[e] : nullptr;
+      J.lens = 0;
+      if (prm->lens && n == 1) {
+        const sg_lens& Ls = *prm->lens;
+        J.lens = 1;
+        J.k1 = Ls.k1;
+        J.k2 = Ls.k2;
+        J.lscale = Ls.scale > 0.0f ? Ls.scale : 1.0f / (1.0f + Ls.k1 + Ls.k2);
+        J.laspect = Ls.aspect > 0.0f ? Ls.aspect : (float)J.W / (float)J.H;
+        J.lcx = Ls.centre[e][0];
+        J.lcy = Ls.centre[e][1];
+      }
       J.tiles_x = (J.W + TW - 1) / TW;
       J.tile_begin = tiles;
       tiles += J.tiles_x * ((J.H + TH - 1) / TH);

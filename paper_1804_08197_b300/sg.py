@@ -24,7 +24,7 @@ EXPORTS = ["sg_volume_create", "sg_volume_destroy", "sg_upload_volume_device", "
            "sg_render", "sg_render_host", "sg_render_batch", "sg_set_render_config", "sg_get_render_config",
            "sg_autotune_render", "sg_select_lod_noalloc", "sg_read_residency", "sg_set_brick_ranges", "sg_unet_create", "sg_unet_destroy",
            "sg_unet_param_count", "sg_unet_get_params", "sg_unet_set_params", "sg_unet_forward", "sg_unet_backward",
-           "sg_unet_adam_step", "sg_unet_set_tensor_path", "sg_unet_check", "sg_psnr", "sg_read_ranges", "sg_upload_brick_list",
+           "sg_unet_adam_step", "sg_unet_set_tensor_path", "sg_unet_check", "sg_psnr", "sg_read_ranges", "sg_upload_brick_list", "sg_unwarp",
            "sg_last_error",
            "sg_version"]
 
@@ -54,10 +54,24 @@ class sg_select_stats(ctypes.Structure):
                 ("reserved", ctypes.c_uint32 * 2)]
 
 
+class sg_lens(ctypes.Structure):
+    _fields_ = [("k1", ctypes.c_float), ("k2", ctypes.c_float), ("scale", ctypes.c_float), ("aspect", ctypes.c_float),
+                ("centre", (ctypes.c_float * 2) * 2)]
+
+
+def make_lens(k1, k2, scale=0.0, aspect=0.0, centres=((0.0, 0.0), (0.0, 0.0))):
+    ln = sg_lens()
+    ln.k1, ln.k2, ln.scale, ln.aspect = k1, k2, scale, aspect
+    for e in range(2):
+        ln.centre[e][0], ln.centre[e][1] = centres[e]
+    return ln
+
+
 class sg_render_params(ctypes.Structure):
     _fields_ = [("step", ctypes.c_float), ("term_alpha", ctypes.c_float), ("mode", ctypes.c_int32),
                 ("empty_skip", ctypes.c_int32), ("sample_count", ctypes.c_void_p * 2),
-                ("sample_total", ctypes.c_void_p), ("depth", ctypes.c_void_p * 2)]
+                ("sample_total", ctypes.c_void_p), ("depth", ctypes.c_void_p * 2),
+                ("lens", ctypes.POINTER(sg_lens))]
 
 
 class sg_render_config(ctypes.Structure):
@@ -81,6 +95,7 @@ def _load():
         "sg_upload_volume_device": [vp, i32, i32, vp, vp],
         "sg_upload_bricks": [vp, i32, i32, i32, i32, vp, vp, vp],
         "sg_upload_brick_list": [vp, i32, i32, i32, vp, vp, P(ctypes.c_int32), vp],
+        "sg_unwarp": [P(sg_lens), P(vp), i32, i32, P(vp), i32, i32, vp],
         "sg_set_transfer_function": [vp, i32, vp, i32, f32, f32, f32, vp],
         "sg_select_lod": [vp, P(sg_pose), P(sg_select_stats), vp],
         "sg_select_lod_batch": [vp, P(sg_pose), i32, vp],
@@ -243,10 +258,14 @@ def sg_read_brick(vol, t, c, level, bx, by, bz, host_out, stream=None):
 
 
 def render_params(step=0.5, term_alpha=0.99, empty_skip=1, sample_count=None, sample_total=None,
-                  mode=SG_MODE_EMISSION_ABSORPTION, depth=None):
+                  mode=SG_MODE_EMISSION_ABSORPTION, depth=None, lens=None):
     """depth: optional pair of device float buffers (H, W) per eye, the world
-    distance along each pixel's ray to an opaque surface (inf = none)."""
+    distance along each pixel's ray to an opaque surface (inf = none).
+    lens: optional sg_lens (make_lens) for rays through the warped image; the
+    structure must stay alive while the parameters are used."""
     r = sg_render_params()
+    if lens is not None:
+        r.lens = ctypes.pointer(lens)
     if sample_total is not None:
         r.sample_total = _ptr(sample_total).value
     r.step, r.term_alpha, r.mode, r.empty_skip = step, term_alpha, mode, empty_skip
@@ -257,6 +276,13 @@ def render_params(step=0.5, term_alpha=0.99, empty_skip=1, sample_count=None, sa
         r.depth[0] = _ptr(depth[0]).value
         r.depth[1] = _ptr(depth[1]).value
     return r
+
+
+def sg_unwarp(lens, warped, Ww, Hw, outs, W, H, stream=None):
+    """Unwarps both eyes: warped/outs are pairs of device RGBA float buffers."""
+    wa = (ctypes.c_void_p * 2)(_ptr(warped[0]).value, _ptr(warped[1]).value)
+    oa = (ctypes.c_void_p * 2)(_ptr(outs[0]).value, _ptr(outs[1]).value)
+    _check(lib.sg_unwarp(ctypes.byref(lens), wa, Ww, Hw, oa, W, H, _stream(stream)))
 
 
 def sg_render(vol, pose, params, outs, stream=None):
