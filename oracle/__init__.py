@@ -48,7 +48,9 @@ class _Vol(ctypes.Structure):
 
 class _TF(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("lo", ctypes.c_float), ("hi", ctypes.c_float),
-                ("ref_step", ctypes.c_float), ("rgba", ctypes.c_void_p)]
+                ("ref_step", ctypes.c_float), ("rgba", ctypes.c_void_p), ("input", ctypes.c_int32),
+                ("m", ctypes.c_int32), ("pnear", ctypes.c_float), ("pfar", ctypes.c_float),
+                ("palette", ctypes.c_void_p)]
 
 
 def _load():
@@ -134,11 +136,23 @@ def unwarp(ln, warped, W, H):
     return out
 
 
-def make_tf(table, lo, hi, ref_step=0.5):
-    """Keeps the numpy table alive alongside the ctypes struct."""
+INPUT_VALUE, INPUT_GRADIENT = 0, 1
+
+
+def make_tf(table, lo, hi, ref_step=0.5, gradient=False, palette=None, near=0.0, far=1.0):
+    """Transfer function of one channel; keeps the numpy arrays alive
+    alongside the ctypes struct. gradient: the table reads the gradient
+    magnitude (value units per level-0 voxel) instead of the value; palette:
+    (m, 3) RGB replacing the table's colour, indexed by the sample's world
+    distance from the eye over [near, far]."""
     t = np.ascontiguousarray(table, np.float32)
     s = _TF(t.shape[0], lo, hi, ref_step, t.ctypes.data)
-    s._keep = t
+    s.input = INPUT_GRADIENT if gradient else INPUT_VALUE
+    s._keep = [t]
+    if palette is not None:
+        pal = np.ascontiguousarray(palette, np.float32).reshape(-1, 3)
+        s.m, s.pnear, s.pfar, s.palette = pal.shape[0], near, far, pal.ctypes.data
+        s._keep.append(pal)
     return s
 
 

@@ -55,7 +55,17 @@ typedef struct {
   float lo, hi;     /* intensity window mapped onto [0, n-1] */
   float ref_step;   /* step, in level-0 voxels, at which the table's alphas hold */
   const float* rgba; /* 4n, straight (not premultiplied) colour + opacity */
+  /* "Visualization Enhancements": the table reads the voxel value (input 0)
+   * or the gradient magnitude (input 1); with m > 0 the colour comes from a
+   * palette of m RGB entries indexed by the sample's world distance from the
+   * eye over [pnear, pfar] instead of the table's colour */
+  int32_t input;
+  int32_t m;
+  float pnear, pfar;
+  const float* palette; /* 3m */
 } or_tf;
+
+enum { OR_INPUT_VALUE = 0, OR_INPUT_GRADIENT = 1 };
 
 /* ------------------------------------------------------------------------ */
 /* small linear algebra (column-major 4x4, FP64)                             */
@@ -206,9 +216,18 @@ static int tf_range_empty(const or_tf* tf, uint32_t vmin, uint32_t vmax) {
   /* an unknown range (vmin > vmax: a block whose data was never seen) is
    * never transparent */
   if (vmin > vmax) return 0;
+  /* the table's input over the block: the value range, or for gradient
+   * input [0, sqrt(3) (vmax - vmin)]: each central difference of the
+   * trilinear field spans at most vmax - vmin (its taps lie in the block and
+   * its apron), and a level-L gradient is divided by 2^L >= 1 */
+  volatile float in0 = (float)vmin, in1 = (float)vmax;
+  if (tf->input == OR_INPUT_GRADIENT) {
+    in0 = 0.0f;
+    in1 = 1.7320508f * (float)(vmax - vmin);
+  }
   volatile float width = tf->hi - tf->lo;
-  volatile float x0 = ((float)vmin - tf->lo) / width;
-  volatile float x1 = ((float)vmax - tf->lo) / width;
+  volatile float x0 = (in0 - tf->lo) / width;
+  volatile float x1 = (in1 - tf->lo) / width;
   float a = x0 < 0.0f ? 0.0f : (x0 > 1.0f ? 1.0f : x0);
   float b = x1 < 0.0f ? 0.0f : (x1 > 1.0f ? 1.0f : x1);
   volatile float q0 = a * (float)(tf->n - 1);
@@ -511,6 +530,38 @@ void or_classify(const or_tf* tf, const double* table, double value, double* rgb
   for (int k = 0; k < 4; ++k) rgba[k] = table[4 * i + k] * (1.0 - f) + table[4 * i1 + k] * f;
 }
 
+/* Gradient magnitude of channel c's level-L field at level-0 position p, per
+ * level-0 voxel: central differences of the trilinear field at +-1/2 level-L
+ * voxel along each axis (the taps stay within a brick's one-voxel apron),
+ * divided by 2^L. */
+static double grad_mag(const or_volume* v, int L, int c, const double* p) {
+  double h = 0.5 * (double)((int64_t)1 << L), g2 = 0.0;
+  for (int ax = 0; ax < 3; ++ax) {
+    double a[3] = {p[0], p[1], p[2]}, b[3] = {p[0], p[1], p[2]};
+    a[ax] += h;
+    b[ax] -= h;
+    double d = or_sample(v, L, c, a) - or_sample(v, L, c, b);
+    g2 += d * d;
+  }
+  return sqrt(g2) / (double)((int64_t)1 << L);
+}
+
+/* Palette colour at world distance d from the eye: x = clamp((d - near) /
+ * (far - near), 0, 1), q = x (m - 1), linear between entries floor(q) and
+ * floor(q) + 1. */
+static void palette_rgb(const or_tf* tf, double d, double* rgb) {
+  double x = (d - (double)tf->pnear) / ((double)tf->pfar - (double)tf->pnear);
+  if (x < 0.0) x = 0.0;
+  if (x > 1.0) x = 1.0;
+  double q = x * (double)(tf->m - 1);
+  int i = (int)floor(q);
+  if (i > tf->m - 2) i = tf->m - 2;
+  if (i < 0) i = 0;
+  int i1 = i + 1 > tf->m - 1 ? tf->m - 1 : i + 1;
+  double f = q - (double)i;
+  for (int k = 0; k < 3; ++k) rgb[k] = tf->palette[3 * i + k] * (1.0 - f) + tf->palette[3 * i1 + k] * f;
+}
+
 /* ------------------------------------------------------------------------ */
 /* ray casting                                                               */
 
@@ -608,7 +659,13 @@ typedef struct {
   int mode;
   const double* tmax; /* per image pixel: the ray ends there (level-0 voxels from the eye); NULL = none */
   const or_lens* lens; /* rays through the warped image; NULL = none */
+  double voxel;        /* world units per level-0 voxel (the model's uniform scale) */
 } ray_t;
+
+/* the table's input for channel c at level-0 position p, sampled at level L */
+static double tf_input(const ray_t* r, int L, int c, const double* p) {
+  return r->tf[c].input == OR_INPUT_GRADIENT ? grad_mag(r->v, L, c, p) : or_sample(r->v, L, c, p);
+}
 
 static int node_level(const ray_t* r, int32_t id) {
   if (id < 0) return -1;
@@ -669,9 +726,9 @@ static void cast(const ray_t* r, int64_t pix, double* early, double* late, uint3
    * ("Volumetric and Mesh Data Compositing") */
   const double tsurf = r->tmax ? r->tmax[pix] : INFINITY;
   if (tsurf < t1) t1 = tsurf;
-  double vmax[OR_MAX_CH];
+  double vmax[OR_MAX_CH], tat[OR_MAX_CH];
   int any = 0;
-  for (int c = 0; c < OR_MAX_CH; ++c) vmax[c] = -INFINITY;
+  for (int c = 0; c < OR_MAX_CH; ++c) { vmax[c] = -INFINITY; tat[c] = 0.0; }
   double C[3] = {0, 0, 0}, A = 0.0, Ce[3] = {0, 0, 0}, Ae = 0.0;
   uint32_t cnt = 0, cnte = 0;
   int early_done = 0;
@@ -734,10 +791,11 @@ static void cast(const ray_t* r, int64_t pix, double* early, double* late, uint3
       }
       if (L < 0 || (k & (((int64_t)1 << L) - 1)) != 0) continue;
       if (r->mode == OR_MODE_MIP) {
-        /* the maximum trilinear value per channel, classified after the loop */
+        /* the maximum table input per channel (the first sample that
+         * reaches it keeps its distance), classified after the loop */
         for (int c = 0; c < nch; ++c) {
-          double val = or_sample(r->v, L, c, p);
-          if (val > vmax[c]) vmax[c] = val;
+          double val = tf_input(r, L, c, p);
+          if (val > vmax[c]) { vmax[c] = val; tat[c] = t; }
         }
         any = 1;
         ++cnt;
@@ -748,8 +806,9 @@ static void cast(const ray_t* r, int64_t pix, double* early, double* late, uint3
          * times its opacity for one reference step, over that step; a
          * level-L sample stands for step * 2^L of path */
         for (int c = 0; c < nch; ++c) {
-          double val = or_sample(r->v, L, c, p), rgba[4];
+          double val = tf_input(r, L, c, p), rgba[4];
           or_classify(&r->tf[c], r->raw[c], val, rgba);
+          if (r->tf[c].m > 0) palette_rgb(&r->tf[c], t * r->voxel, rgba);
           double w = rgba[3] * (r->step * (double)((int64_t)1 << L)) / (double)r->tf[c].ref_step;
           for (int q = 0; q < 3; ++q) C[q] += w * rgba[q];
         }
@@ -759,8 +818,9 @@ static void cast(const ray_t* r, int64_t pix, double* early, double* late, uint3
       /* classify every channel, blend additively (alpha capped at 1) */
       double sa = 0.0, sc[3] = {0, 0, 0};
       for (int c = 0; c < nch; ++c) {
-        double val = or_sample(r->v, L, c, p), rgba[4];
+        double val = tf_input(r, L, c, p), rgba[4];
         or_classify(&r->tf[c], r->table[L][c], val, rgba);
+        if (r->tf[c].m > 0) palette_rgb(&r->tf[c], t * r->voxel, rgba);
         sa += rgba[3];
         for (int q = 0; q < 3; ++q) sc[q] += rgba[3] * rgba[q];
       }
@@ -785,6 +845,7 @@ static void cast(const ray_t* r, int64_t pix, double* early, double* late, uint3
     for (int c = 0; c < r->v->nch; ++c) {
       double rgba[4];
       or_classify(&r->tf[c], r->raw[c], vmax[c], rgba);
+      if (r->tf[c].m > 0) palette_rgb(&r->tf[c], tat[c] * r->voxel, rgba);
       sa += rgba[3];
       for (int q = 0; q < 3; ++q) sc[q] += rgba[3] * rgba[q];
     }
@@ -818,6 +879,7 @@ int or_render(const or_volume* v, const or_tf* tfs, const int32_t* leaf, const d
   r.v = v; r.tf = tfs; r.leaf = leaf; r.W = W; r.H = H;
   r.step = step; r.term = term; r.term_tol = term_tol; r.eps = eps;
   r.mode = mode; r.tmax = tmax; r.lens = lens;
+  r.voxel = sqrt(v->model[0] * v->model[0] + v->model[1] * v->model[1] + v->model[2] * v->model[2]);
   or_node_count(v, r.off);
   level_blocks(v, 0, r.nb0);
   double vm[16], pvm[16], vminv[16];

@@ -334,3 +334,73 @@ def test_unwarp_reproduces_a_linear_warped_image():
             assert out[j, i, 3] == pytest.approx(1.0, abs=1e-12)
             checked += 1
     assert checked > W * H // 3
+
+
+# ---------------------------------------------------------------- gradient and depth-palette tables (Visualization Enhancements)
+
+def _ramp_table(n=256):
+    t = np.zeros((n, 4), np.float32)
+    t[:, 0] = np.linspace(0, 1, n)
+    t[:, 1] = np.linspace(1, 0, n)
+    t[:, 2] = 0.25
+    t[:, 3] = np.linspace(0, 0.5, n)
+    return t
+
+
+def test_gradient_input_of_a_linear_field_is_its_slope():
+    """Central differences of a trilinear linear field are exact: away from
+    the clamped border every sample's gradient magnitude is |(3, 5, 7)| =
+    sqrt(83) per voxel, so MIP of the gradient input classifies sqrt(83)."""
+    n = 16
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    a = (3 * i + 5 * j + 7 * k + 11).astype(np.uint16)
+    vol = oracle.Volume([[a]], n)
+    tab = _ramp_table()
+    tf = oracle.make_tf(tab, 0.0, 20.0, gradient=True)
+    view, proj = _axial_camera(40.0, cx=8.3, cy=7.6)
+    sel = vol.select([tf], [view, view], [proj, proj], 9, tau=1.0)
+    r = vol.render([tf], sel["leaf"], view, proj, 9, 9, pixels=[4 * 9 + 4], mode=oracle.MODE_MIP)
+    q = np.sqrt(83.0) / 20.0 * 255.0
+    f = q - np.floor(q)
+    e = tab[int(q)].astype(np.float64) * (1 - f) + tab[int(q) + 1].astype(np.float64) * f
+    assert r["late"][0] == pytest.approx([e[3] * e[0], e[3] * e[1], e[3] * e[2], e[3]], abs=1e-12)
+
+
+def test_gradient_input_drops_blocks_of_constant_value():
+    """With a table that is transparent at gradient 0, a block whose values
+    are all equal (gradient bound sqrt(3) (max - min) = 0) is transparent and
+    dropped; a block with varying values is not, even where a value table
+    would call it transparent."""
+    n = 32
+    a = np.full((n, n, n), 40, np.uint16)
+    rng = np.random.default_rng(9)
+    a[:, :, 18:] = rng.integers(30, 50, (n, n, 14))  # block x = 0 and its apron (x <= 16) stay constant
+    vol = oracle.Volume([[a]], 16)
+    tab = _ramp_table()
+    tab[:3, 3] = 0.0
+    view, proj = synth.orbit_camera(n, seed=21, width=32, height=32)
+    grad = vol.select([oracle.make_tf(tab, 0.0, 200.0, gradient=True)], [view, view], [proj, proj], 32)
+    value = vol.select([oracle.make_tf(tab, 1000.0, 2000.0)], [view, view], [proj, proj], 32)
+    assert value["selected"] == 0  # every value sits below the value window
+    lvl0 = [vol.node_coords(i)[1] for i in np.flatnonzero(grad["state"] == oracle.ST_SELECTED)]
+    assert lvl0 and all(b[0] == 1 for b in lvl0)  # only the varying half (x >= 16) survives
+
+
+def test_depth_palette_colours_by_distance():
+    """Constant medium, palette red at the entry distance to blue at the exit
+    distance: colour weights follow the arithmetico-geometric series of the
+    sample distances (t_k - t0) / 16 under opacity a' per sample."""
+    n = 16
+    vol = oracle.Volume([[np.full((n, n, n), 100, np.uint8)]], n)
+    a = float(np.float32(0.05))
+    tf = oracle.make_tf(np.tile(np.array([0.3, 0.3, 0.3, a], np.float32), (256, 1)), 0.0, 255.0,
+                        palette=[[1, 0, 0], [0, 0, 1]], near=24.0, far=40.0)
+    view, proj = _axial_camera(40.0, cx=8.0, cy=8.0)
+    sel = vol.select([tf], [view, view], [proj, proj], 9, tau=1.0)
+    r = vol.render([tf], sel["leaf"], view, proj, 9, 9, step=0.3, pixels=[4 * 9 + 4])
+    ap = 1.0 - (1.0 - a) ** 0.6
+    q, m = 1.0 - ap, 54
+    s0 = (1 - q ** m) / (1 - q)
+    s1 = q * (1 - m * q ** (m - 1) + (m - 1) * q ** m) / (1 - q) ** 2
+    d = 0.3 / 16.0
+    assert r["late"][0] == pytest.approx([ap * (s0 - d * s1), 0.0, ap * d * s1, 1 - q ** m], abs=1e-12)
