@@ -590,6 +590,55 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         modes[name] = {"fps": round(nm / (a0.elapsed_time(a1) / 1e3), 2), "steps": nm}
 
+    # lens-warped stereo ("DVR for HMD"): one ray per pixel of the warped
+    # image at the undistorted image's density at the lens centre, then the
+    # unwarp to 2x1440x1600; quality = PSNR against the plain render over the
+    # pixels the warped image covers
+    lens_k1, lens_k2 = 0.22, 0.24
+    lscale = 1.0 / (1.0 + lens_k1 + lens_k2)
+    Ww, Hw = int(round(W_EYE * lscale)), int(round(H_EYE * lscale))
+    ln = sg.make_lens(lens_k1, lens_k2, 0.0, W_EYE / H_EYE, ((0.05, 0.0), (-0.05, 0.0)))
+    warped = [torch.empty((Hw, Ww, 4), dtype=torch.float32, device=dev) for _ in range(2)]
+    unwarped = [torch.empty((H_EYE, W_EYE, 4), dtype=torch.float32, device=dev) for _ in range(2)]
+    prm_w = sg.render_params(step=STEP, term_alpha=TERM, empty_skip=1, lens=ln)
+    wposes = [sg.make_pose(v, p, Ww, Hw, pixel_error=TAU, slot=0) for v, p in poses]
+    wmine = [wposes[(rank + world * i) % NPOSES] for i in range(NPOSES)]
+
+    def warped_step(i):
+        sg.sg_select_lod(vol, mine[i % NPOSES], stream=stream)
+        sg.sg_render(vol, wmine[i % NPOSES], prm_w, warped, stream=stream)
+        sg.sg_unwarp(ln, warped, Ww, Hw, unwarped, W_EYE, H_EYE, stream=stream)
+
+    for i in range(3):
+        warped_step(i)
+    nw = min(args.steps, 32)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a0.record(stream)
+    for i in range(nw):
+        warped_step(args.warmup + i)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    warped_fps = nw / (a0.elapsed_time(a1) / 1e3)
+    ones = [torch.ones((Hw, Ww, 4), dtype=torch.float32, device=dev) for _ in range(2)]
+    cover = [torch.empty((H_EYE, W_EYE, 4), dtype=torch.float32, device=dev) for _ in range(2)]
+    sg.sg_unwarp(ln, ones, Ww, Hw, cover, W_EYE, H_EYE, stream=stream)
+    psnr = []
+    for i in range(4):
+        p = mine[(args.warmup + i) % NPOSES]
+        warped_step(args.warmup + i)
+        sg.sg_render(vol, p, prm, outs, stream=stream)
+        torch.cuda.synchronize()
+        for e in range(2):
+            m = cover[e][..., 3] > 0.999
+            mse = float(((unwarped[e] - outs[e])[m] ** 2).mean())
+            psnr.append(10 * np.log10(1.0 / mse) if mse > 0 else 1000.0)
+    warped_line = {"fps": round(warped_fps, 2), "steps": nw, "warped_eye": [Ww, Hw],
+                   "rays_fraction": round(Ww * Hw / (W_EYE * H_EYE), 4), "lens": {"k1": lens_k1, "k2": lens_k2},
+                   "psnr_db_vs_plain": {"mean": round(float(np.mean(psnr)), 2), "min": round(float(np.min(psnr)), 2)},
+                   "covered_fraction": round(float((cover[0][..., 3] > 0.999).float().mean()), 4)}
+    del ones, cover
+
     # end to end through the public C ABI with host buffers: pose in, both images out
     host = [torch.empty((H_EYE, W_EYE, 4), dtype=torch.float32, pin_memory=True) for _ in range(2)]
     e2e_steps = max(4, min(args.steps, 16))
@@ -634,7 +683,8 @@ def run_ours(args, rank, world, local_rank):
                         "h2d_bytes_per_step": int(np.dtype(np.uint8).itemsize * len(bytes(mine[0]))),
                         "d2h_bytes_per_step": out_bytes},
                 "select_stats_last": sel_stats,
-                "optical_models": modes}
+                "optical_models": modes,
+                "lens_warped": warped_line}
         if cpu:
             line["cpu_baseline"] = cpu
         if batched:

@@ -154,6 +154,23 @@ sg_status sg_set_brick_ranges(sg_volume* vol, int t, int c, int level, int n, co
 sg_status sg_set_transfer_function(sg_volume* vol, int c, const float* rgba, int n, float lo, float hi,
                                    float ref_step, void* stream);
 
+/* What a channel's table reads and where its colour comes from
+ * ("Visualization Enhancements"). input SG_INPUT_VALUE: the voxel value (the
+ * default); SG_INPUT_GRADIENT: the gradient magnitude |grad f| in value units
+ * per level-0 voxel, from central differences of the trilinear field at
+ * +-1/2 voxel of the sample's level along each axis (the window of
+ * sg_set_transfer_function then applies to gradient magnitudes; a block's
+ * gradient lies in [0, sqrt(3) (max - min)], which decides its
+ * transparency). m > 0: the colour comes from palette_rgb (m RGB entries in
+ * [0, 1]) at the sample's world distance d from the eye, x = clamp((d - near)
+ * / (far - near), 0, 1), linear between entries floor(x (m-1)) and the next
+ * (MIP: the distance of the first sample that reaches the maximum); the
+ * table keeps deciding opacity. m = 0: the table's colour. Marks earlier
+ * selections stale. Errors: INVALID_ARG, CUDA. */
+enum { SG_INPUT_VALUE = 0, SG_INPUT_GRADIENT = 1 };
+sg_status sg_set_channel_shading(sg_volume* vol, int c, int input, const float* palette_rgb, int m, float near,
+                                 float far, void* stream);
+
 /* One head pose: the two eyes' view and projection matrices, the per-eye image
  * size, the LOD tolerance in pixels (tau, 1.0 = a voxel may cover one pixel),
  * the time point, and the selection slot that sg_select_lod fills and

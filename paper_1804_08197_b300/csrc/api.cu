@@ -79,6 +79,7 @@ void free_volume(sg_volume* v) {
   cudaFree(v->d_subdist);
   cudaFree(v->d_nodeflags);
   cudaFree(v->d_tf_raw);
+  cudaFree(v->d_palette);
   cudaFree(v->d_lut);
   cudaFree(v->d_stage);
   cudaFree(v->d_err);
@@ -386,6 +387,7 @@ sg_status sg_volume_create(const sg_volume_desc* d, sg_volume** out) {
       (e = dalloc(&v->d_subdist, (size_t)v->pool_slots * ns3)) != cudaSuccess ||
       (e = dalloc(&v->d_nodeflags, tn)) != cudaSuccess ||
       (e = dalloc(&v->d_tf_raw, (size_t)v->nch * kMaxTF * 4)) != cudaSuccess ||
+      (e = dalloc(&v->d_palette, (size_t)v->nch * kMaxTF)) != cudaSuccess ||
       (e = dalloc(&v->d_lut, (size_t)2 * v->nch * v->levels * kMaxTF)) != cudaSuccess ||
       (e = dalloc(&v->d_err, 4)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&v->ev_select, cudaEventDisableTiming)) != cudaSuccess) {
@@ -523,6 +525,31 @@ sg_status sg_set_transfer_function(sg_volume* v, int c, const float* rgba, int n
   v->lut_step = -1.0f;
   v->lut_mode = -1;
   ++v->tf_version;
+  return refresh_flags(v, s);
+}
+
+sg_status sg_set_channel_shading(sg_volume* v, int c, int input, const float* palette_rgb, int m, float near,
+                                 float far, void* stream) {
+  SG_CHECK_ARG(v && c >= 0 && c < v->nch, "volume NULL or channel out of range");
+  SG_CHECK_ARG(input == SG_INPUT_VALUE || input == SG_INPUT_GRADIENT, "input must be SG_INPUT_VALUE or _GRADIENT");
+  SG_CHECK_ARG(m == 0 || (palette_rgb && m >= 1 && m <= kMaxTF && far > near), "palette: 1..4096 entries, far > near");
+  for (int i = 0; i < 3 * m; ++i)
+    SG_CHECK_ARG(palette_rgb[i] >= 0.0f && palette_rgb[i] <= 1.0f, "palette entries must be in [0, 1]");
+  cudaStream_t s = (cudaStream_t)stream;
+  TFHost& t = v->tf[c];
+  t.gradient = input == SG_INPUT_GRADIENT;
+  t.pal_m = m;
+  t.pal_near = near;
+  t.pal_far = far;
+  if (m > 0) {
+    std::vector<float4> pal(m);
+    for (int i = 0; i < m; ++i) pal[i] = make_float4(palette_rgb[3 * i], palette_rgb[3 * i + 1], palette_rgb[3 * i + 2], 0.f);
+    SG_CUDA(cudaMemcpyAsync(v->d_palette + (size_t)c * kMaxTF, pal.data(), sizeof(float4) * m, cudaMemcpyHostToDevice,
+                            s),
+            "palette upload");
+    SG_CUDA(cudaStreamSynchronize(s), "palette upload");
+  }
+  ++v->tf_version;  // transparency follows the table's input
   return refresh_flags(v, s);
 }
 

@@ -66,6 +66,9 @@ struct TFHost {
   // alpha is 0 exactly on a run of entries starting at entry 0 and positive
   // after it (so every transparent value lies below every visible one)
   bool low_end_transparent = false;
+  int gradient = 0;                 // the table reads the gradient magnitude
+  int pal_m = 0;                    // depth palette entries (0: the table's colour)
+  float pal_near = 0.0f, pal_far = 1.0f;
 };
 
 }  // namespace sg
@@ -99,6 +102,7 @@ struct sg_volume {
   // transfer functions
   sg::TFHost tf[sg::kMaxCh];
   float* d_tf_raw = nullptr;       // [nch][kMaxTF][4]
+  float4* d_palette = nullptr;     // [nch][kMaxTF] depth palette RGB (w unused)
   float4* d_lut = nullptr;         // [nch][levels][kMaxTF][2] opacity-corrected (entry, delta to next)
   float lut_step = -1.0f;
   int lut_mode = -1;

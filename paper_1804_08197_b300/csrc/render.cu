@@ -33,7 +33,7 @@ __device__ unsigned long long g_events[8];
 // Register budget of the brick-edge specialised one-ray-per-thread kernels:
 // 64 per thread, i.e. 32 resident warps per SM (on the 1024^3 bench 64
 // registers without spills beat 72 registers at 28 warps; 48 registers spill
-// and lose). The generic and two-rays-per-thread kernels would spill under
+// and lose). The generic, two-rays-per-thread and EXT kernels would spill under
 // it and keep the compiler's choice.
 constexpr int kWarpsPerSM = 32;
 // Lattice points a sample iteration may take (the first after a sub-block
@@ -44,8 +44,8 @@ constexpr int kWarpsPerSM = 32;
 #define SG_SAMPLES_PER_ITER 2
 #endif
 constexpr int kSamplesPerIter = SG_SAMPLES_PER_ITER;
-__host__ __device__ constexpr int min_blocks(int threads, int rpt, int bk) {
-  return (rpt == 1 && bk != 0) ? kWarpsPerSM * 32 / threads : 1;
+__host__ __device__ constexpr int min_blocks(int threads, int rpt, int bk, bool ext = false) {
+  return (rpt == 1 && bk != 0 && !ext) ? kWarpsPerSM * 32 / threads : 1;
 }
 
 
@@ -88,6 +88,12 @@ struct Args {
   int empty_skip;
   int mip_skip;        // MIP may skip transparent space (every table transparent only at its low end)
   float inv_voxel;     // level-0 voxels per world unit (the model's uniform scale, inverted)
+  float voxel;         // world units per level-0 voxel
+  // "Visualization Enhancements" (kernels instantiated with EXT only)
+  int grad[kMaxCh];    // the table reads the gradient magnitude
+  int pal_m[kMaxCh];   // depth palette entries (0: the table's colour)
+  float pal_near[kMaxCh], pal_inv[kMaxCh];
+  const float4* palette;  // [nch][kMaxTF]
   unsigned long long* total_samples;
 };
 
@@ -148,17 +154,70 @@ __device__ __forceinline__ float4 classify(const Args& a, int c, int L, float v)
   return make_float4(fmaf(f, de.x, e0.x), fmaf(f, de.y, e0.y), fmaf(f, de.z, e0.z), fmaf(f, de.w, e0.w));
 }
 
+// Gradient magnitude per level-0 voxel: central differences of the
+// trilinear field at +-1/2 level-L voxel along each axis (the taps stay
+// within the brick's apron), times 2^-L.
+template <typename T, int BK>
+__device__ __forceinline__ float grad_input(const T* __restrict__ br, int B, float lx, float ly, float lz, float sL) {
+  const float gx = tri<T, BK>(br, B, lx + 0.5f, ly, lz) - tri<T, BK>(br, B, lx - 0.5f, ly, lz);
+  const float gy = tri<T, BK>(br, B, lx, ly + 0.5f, lz) - tri<T, BK>(br, B, lx, ly - 0.5f, lz);
+  const float gz = tri<T, BK>(br, B, lx, ly, lz + 0.5f) - tri<T, BK>(br, B, lx, ly, lz - 0.5f);
+  return sqrtf(gx * gx + gy * gy + gz * gz) * sL;
+}
+
+// the table's input for channel c: the trilinear value, or (EXT kernels,
+// gradient tables) the gradient magnitude
+template <typename T, int BK, bool EXT>
+__device__ __forceinline__ float table_input(const Args& a, const T* __restrict__ br, int c, float lx, float ly, float lz,
+                                             float sL) {
+  if (EXT && a.grad[c]) return grad_input<T, BK>(br, a.B, lx, ly, lz, sL);
+  return tri<T, BK>(br, a.B, lx, ly, lz);
+}
+
+// depth palette colour of channel c at world distance d from the eye
+__device__ __forceinline__ float3 palette_at(const Args& a, int c, float d) {
+  const int m = a.pal_m[c];
+  const float4* p = a.palette + (size_t)c * kMaxTF;
+  if (m == 1) {
+    const float4 e = __ldg(p);
+    return make_float3(e.x, e.y, e.z);
+  }
+  const float x = fminf(fmaxf((d - a.pal_near[c]) * a.pal_inv[c], 0.0f), 1.0f);
+  const float q = x * (float)(m - 1);
+  const float fl = fminf(floorf(q), (float)(m - 2));
+  const int i = (int)fl;
+  const float f = q - fl;
+  const float4 e0 = __ldg(p + i), e1 = __ldg(p + i + 1);
+  return make_float3(fmaf(f, e1.x - e0.x, e0.x), fmaf(f, e1.y - e0.y, e0.y), fmaf(f, e1.z - e0.z, e0.z));
+}
+
+// classified sample of channel c (colour from the depth palette in EXT
+// kernels when the channel has one); t = the sample's distance from the eye
+// in level-0 voxels
+template <typename T, int BK, bool EXT>
+__device__ __forceinline__ float4 classify_sample(const Args& a, const T* __restrict__ br, int c, int L, float lx,
+                                                  float ly, float lz, float sL, float t) {
+  float4 e = classify(a, c, L, table_input<T, BK, EXT>(a, br, c, lx, ly, lz, sL));
+  if (EXT && a.pal_m[c] > 0) {
+    const float3 p = palette_at(a, c, t * a.voxel);
+    e.x = p.x;
+    e.y = p.y;
+    e.z = p.z;
+  }
+  return e;
+}
+
 // Trilinear value + classification + front-to-back compositing of one sample
 // at brick-local coordinate l (all channels, additive blend). Returns true
 // when the ray is opaque enough to stop.
-template <typename T, int BK>
+template <typename T, int BK, bool EXT>
 __device__ __forceinline__ bool composite_sample(const Args& a, const T* __restrict__ brick0, int L, float lx, float ly,
-                                                 float lz, float4& acc) {
+                                                 float lz, float sL, float t, float4& acc) {
   float sa, sr, sg, sb;
   if (a.nch == 1) {
     // one channel: alpha is an interpolation of table entries in [0, 1], so
     // the additive blend below never saturates
-    const float4 e = classify(a, 0, L, tri<T, BK>(brick0, a.B, lx, ly, lz));
+    const float4 e = classify_sample<T, BK, EXT>(a, brick0, 0, L, lx, ly, lz, sL, t);
     sa = e.w;
     sr = e.w * e.x;
     sg = e.w * e.y;
@@ -167,7 +226,7 @@ __device__ __forceinline__ bool composite_sample(const Args& a, const T* __restr
     sa = 0.0f; sr = 0.0f; sg = 0.0f; sb = 0.0f;
     for (int c = 0; c < a.nch; ++c) {
       const T* br = reinterpret_cast<const T*>(reinterpret_cast<const uint8_t*>(brick0) + (size_t)c * a.brick_bytes);
-      const float4 e = classify(a, c, L, tri<T, BK>(br, a.B, lx, ly, lz));
+      const float4 e = classify_sample<T, BK, EXT>(a, br, c, L, lx, ly, lz, sL, t);
       sa += e.w;
       sr = fmaf(e.w, e.x, sr);
       sg = fmaf(e.w, e.y, sg);
@@ -190,12 +249,12 @@ __device__ __forceinline__ bool composite_sample(const Args& a, const T* __restr
 // Emission-only sample: every channel adds its table colour times its
 // emission weight (the table's alpha for this level is alpha * step 2^L /
 // ref_step); no absorption, the ray never stops early.
-template <typename T, int BK>
+template <typename T, int BK, bool EXT>
 __device__ __forceinline__ void emission_sample(const Args& a, const T* __restrict__ brick0, int L, float lx, float ly,
-                                                float lz, float4& acc) {
+                                                float lz, float sL, float t, float4& acc) {
   for (int c = 0; c < a.nch; ++c) {
     const T* br = reinterpret_cast<const T*>(reinterpret_cast<const uint8_t*>(brick0) + (size_t)c * a.brick_bytes);
-    const float4 e = classify(a, c, L, tri<T, BK>(br, a.B, lx, ly, lz));
+    const float4 e = classify_sample<T, BK, EXT>(a, br, c, L, lx, ly, lz, sL, t);
     acc.x = fmaf(e.w, e.x, acc.x);
     acc.y = fmaf(e.w, e.y, acc.y);
     acc.z = fmaf(e.w, e.z, acc.z);
@@ -203,15 +262,19 @@ __device__ __forceinline__ void emission_sample(const Args& a, const T* __restri
 }
 
 // Maximum intensity projection sample: the running maximum of each
-// channel's trilinear value.
-template <typename T, int BK>
+// channel's table input, with the distance of the first sample reaching it.
+template <typename T, int BK, bool EXT>
 __device__ __forceinline__ void mip_sample(const Args& a, const T* __restrict__ brick0, float lx, float ly, float lz,
-                                           float (&vmax)[kMaxCh]) {
+                                           float sL, float t, float (&vmax)[kMaxCh], float (&tat)[kMaxCh]) {
 #pragma unroll
   for (int c = 0; c < kMaxCh; ++c) {
     if (c >= a.nch) break;
     const T* br = reinterpret_cast<const T*>(reinterpret_cast<const uint8_t*>(brick0) + (size_t)c * a.brick_bytes);
-    vmax[c] = fmaxf(vmax[c], tri<T, BK>(br, a.B, lx, ly, lz));
+    const float v = table_input<T, BK, EXT>(a, br, c, lx, ly, lz, sL);
+    if (v > vmax[c]) {
+      vmax[c] = v;
+      tat[c] = t;
+    }
   }
 }
 
@@ -230,7 +293,7 @@ __device__ inline int cell_of(float p, float invB, int lo, int hi) {
 // iteration (take a sample, jump over transparent sub-blocks, or move to
 // the next block), so the lanes of a warp stay in one loop instead of
 // diverging across nested ones.
-template <typename T, int BK, int MODE>
+template <typename T, int BK, int MODE, bool EXT>
 __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int px, int py, bool active, float4& acc,
                                           uint32_t& cnt) {
   acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -276,9 +339,12 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
   if (!hit) return;
   // transparent space may be skipped unless a MIP maximum could lie there
   const bool skip = a.empty_skip && (MODE != SG_MODE_MIP || a.mip_skip);
-  float vmax[kMaxCh];
+  float vmax[kMaxCh], tat[kMaxCh];
 #pragma unroll
-  for (int c = 0; c < kMaxCh; ++c) vmax[c] = -INFINITY;
+  for (int c = 0; c < kMaxCh; ++c) {
+    vmax[c] = -INFINITY;
+    tat[c] = 0.0f;
+  }
 #ifdef SG_RENDER_EVENT_STATS
   unsigned long long ev[8] = {0, 0, 0, 0, 0, 0, 1, 0};
 #endif
@@ -395,15 +461,15 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
     if (MODE == SG_MODE_EMISSION_ABSORPTION) {
 #ifdef SG_RENDER_EVENT_STATS
       const float w_before = acc.w;
-      stop = composite_sample<T, BK>(a, brick0, L, lx, ly, lz, acc);
+      stop = composite_sample<T, BK, EXT>(a, brick0, L, lx, ly, lz, sL, t, acc);
       SG_EV(7, acc.w != w_before ? 1 : 0);
 #else
-      stop = composite_sample<T, BK>(a, brick0, L, lx, ly, lz, acc);
+      stop = composite_sample<T, BK, EXT>(a, brick0, L, lx, ly, lz, sL, t, acc);
 #endif
     } else if (MODE == SG_MODE_EMISSION) {
-      emission_sample<T, BK>(a, brick0, L, lx, ly, lz, acc);
+      emission_sample<T, BK, EXT>(a, brick0, L, lx, ly, lz, sL, t, acc);
     } else {
-      mip_sample<T, BK>(a, brick0, lx, ly, lz, vmax);
+      mip_sample<T, BK, EXT>(a, brick0, lx, ly, lz, sL, t, vmax, tat);
     }
     if (stop) break;
     k += kstep;
@@ -419,11 +485,11 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
       ++cnt;
       SG_EV(0, 1);
       if (MODE == SG_MODE_EMISSION_ABSORPTION)
-        stop = composite_sample<T, BK>(a, brick0, L, mx, my, mz, acc);
+        stop = composite_sample<T, BK, EXT>(a, brick0, L, mx, my, mz, sL, t2, acc);
       else if (MODE == SG_MODE_EMISSION)
-        emission_sample<T, BK>(a, brick0, L, mx, my, mz, acc);
+        emission_sample<T, BK, EXT>(a, brick0, L, mx, my, mz, sL, t2, acc);
       else
-        mip_sample<T, BK>(a, brick0, mx, my, mz, vmax);
+        mip_sample<T, BK, EXT>(a, brick0, mx, my, mz, sL, t2, vmax, tat);
       if (stop) break;
       k += kstep;
     }
@@ -437,7 +503,13 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
 #pragma unroll
     for (int c = 0; c < kMaxCh; ++c) {
       if (c >= a.nch) break;
-      const float4 e = classify(a, c, 0, vmax[c]);
+      float4 e = classify(a, c, 0, vmax[c]);
+      if (EXT && a.pal_m[c] > 0) {
+        const float3 p = palette_at(a, c, tat[c] * a.voxel);
+        e.x = p.x;
+        e.y = p.y;
+        e.z = p.z;
+      }
       sa += e.w;
       sr = fmaf(e.w, e.x, sr);
       sg = fmaf(e.w, e.y, sg);
@@ -456,8 +528,8 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
 #endif
 }
 
-template <typename T, int MAXI, int BK, int MODE>
-__global__ void __launch_bounds__(kThreads, min_blocks(kThreads, 1, BK)) k_render(Args a, Jobs<MAXI> jobs) {
+template <typename T, int MAXI, int BK, int MODE, bool EXT>
+__global__ void __launch_bounds__(kThreads, min_blocks(kThreads, 1, BK, EXT)) k_render(Args a, Jobs<MAXI> jobs) {
   const int tile = blockIdx.x;
   int im = 0;
   while (im + 1 < jobs.n && tile >= jobs.img[im + 1].tile_begin) ++im;
@@ -471,7 +543,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(kThreads, 1, BK)) k_rende
 
   float4 acc;
   uint32_t cnt;
-  trace_ray<T, BK, MODE>(a, J, px, py, active, acc, cnt);
+  trace_ray<T, BK, MODE, EXT>(a, J, px, py, active, acc, cnt);
   if (active) {
     const size_t pix = (size_t)py * J.W + px;
     J.out[pix] = acc;
@@ -521,7 +593,7 @@ __global__ void __launch_bounds__(TW * TH / RPT, min_blocks(TW * TH / RPT, RPT, 
       const bool active = px < J.W && py < J.H;
       float4 acc;
       uint32_t cnt;
-      trace_ray<T, BK, SG_MODE_EMISSION_ABSORPTION>(a, J, px, py, active, acc, cnt);
+      trace_ray<T, BK, SG_MODE_EMISSION_ABSORPTION, false>(a, J, px, py, active, acc, cnt);
       if (active) {
         const size_t pix = (size_t)py * J.W + px;
         J.out[pix] = acc;
@@ -634,8 +706,17 @@ Args make_args(const sg_volume* v, const sg_render_params* prm) {
   // its first column is the voxel size
   const float* m = v->desc.model;
   a.inv_voxel = (float)(1.0 / sqrt((double)m[0] * m[0] + (double)m[1] * m[1] + (double)m[2] * m[2]));
+  a.voxel = (float)sqrt((double)m[0] * m[0] + (double)m[1] * m[1] + (double)m[2] * m[2]);
   a.mip_skip = 1;
   for (int c = 0; c < v->nch; ++c) a.mip_skip &= v->tf[c].low_end_transparent ? 1 : 0;
+  a.palette = v->d_palette;
+  for (int c = 0; c < kMaxCh; ++c) {
+    const bool on = c < v->nch;
+    a.grad[c] = on ? v->tf[c].gradient : 0;
+    a.pal_m[c] = on ? v->tf[c].pal_m : 0;
+    a.pal_near[c] = on ? v->tf[c].pal_near : 0.0f;
+    a.pal_inv[c] = on && v->tf[c].pal_m > 0 ? (float)(1.0 / ((double)v->tf[c].pal_far - v->tf[c].pal_near)) : 0.0f;
+  }
   return a;
 }
 
@@ -712,16 +793,16 @@ cudaError_t dispatch_tiles(sg_volume* v, const Args& a, const sg_pose* poses, in
   return cudaErrorInvalidValue;
 }
 
-template <int MAXI, int BK, int MODE>
+template <int MAXI, int BK, int MODE, bool EXT = false>
 cudaError_t launch_impl(sg_volume* v, const sg_pose* poses, int n, const sg_render_params* prm, float* const* outs,
                         cudaStream_t s) {
   Args a = make_args(v, prm);
   Jobs<MAXI> jobs;
   if (!make_jobs<MAXI>(v, poses, n, prm, outs, kTileW, kTileH, &jobs)) return cudaErrorInvalidValue;
   if (v->esize == 1)
-    k_render<uint8_t, MAXI, BK, MODE><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
+    k_render<uint8_t, MAXI, BK, MODE, EXT><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
   else
-    k_render<uint16_t, MAXI, BK, MODE><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
+    k_render<uint16_t, MAXI, BK, MODE, EXT><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
   return cudaGetLastError();
 }
 
@@ -730,6 +811,14 @@ cudaError_t launch_impl(sg_volume* v, const sg_pose* poses, int n, const sg_rend
 template <int BK>
 cudaError_t launch_b(sg_volume* v, const sg_pose* poses, int n, const sg_render_params* prm, float* const* outs,
                      cudaStream_t s) {
+  // gradient tables or depth palettes: the EXT kernels (one CTA per 16x8 tile)
+  bool ext = false;
+  for (int c = 0; c < v->nch; ++c) ext |= v->tf[c].gradient || v->tf[c].pal_m > 0;
+  if (ext) {
+    if (prm->mode == SG_MODE_EMISSION) return launch_impl<128, BK, SG_MODE_EMISSION, true>(v, poses, n, prm, outs, s);
+    if (prm->mode == SG_MODE_MIP) return launch_impl<128, BK, SG_MODE_MIP, true>(v, poses, n, prm, outs, s);
+    return launch_impl<128, BK, SG_MODE_EMISSION_ABSORPTION, true>(v, poses, n, prm, outs, s);
+  }
   // emission-only and MIP run the one-CTA-per-16x8-tile kernel (the launch
   // shapes and the autotuner serve the emission-absorption model)
   if (prm->mode == SG_MODE_EMISSION) return launch_impl<128, BK, SG_MODE_EMISSION>(v, poses, n, prm, outs, s);

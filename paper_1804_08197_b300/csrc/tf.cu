@@ -12,6 +12,7 @@ namespace {
 struct TFParams {
   int nch;
   int n[kMaxCh];
+  int grad[kMaxCh];  // the table reads the gradient magnitude
   float lo[kMaxCh], hi[kMaxCh];
   const float* raw;  // [nch][kMaxTF][4]
 };
@@ -25,9 +26,18 @@ struct TFParams {
 __device__ bool range_empty(const TFParams& p, int c, uint32_t vmin, uint32_t vmax) {
   if (vmin > vmax) return false;
   const int n = p.n[c];
+  // the table's input over the range: the values, or for gradient input
+  // [0, sqrt(3) (vmax - vmin)] (each central difference of the trilinear
+  // field spans at most vmax - vmin, and level-L gradients are divided by
+  // 2^L >= 1)
+  float in0 = __uint2float_rn(vmin), in1 = __uint2float_rn(vmax);
+  if (p.grad[c]) {
+    in0 = 0.0f;
+    in1 = __fmul_rn(1.7320508f, __uint2float_rn(vmax - vmin));
+  }
   const float width = __fsub_rn(p.hi[c], p.lo[c]);
-  float x0 = __fdiv_rn(__fsub_rn(__uint2float_rn(vmin), p.lo[c]), width);
-  float x1 = __fdiv_rn(__fsub_rn(__uint2float_rn(vmax), p.lo[c]), width);
+  float x0 = __fdiv_rn(__fsub_rn(in0, p.lo[c]), width);
+  float x1 = __fdiv_rn(__fsub_rn(in1, p.lo[c]), width);
   x0 = fminf(fmaxf(x0, 0.0f), 1.0f);
   x1 = fminf(fmaxf(x1, 0.0f), 1.0f);
   int ilo = (int)floorf(__fmul_rn(x0, (float)(n - 1))) - 1;
@@ -195,6 +205,7 @@ TFParams make_params(const sg_volume* v) {
     p.n[c] = c < v->nch ? v->tf[c].n : 2;
     p.lo[c] = c < v->nch ? v->tf[c].lo : 0.0f;
     p.hi[c] = c < v->nch ? v->tf[c].hi : 1.0f;
+    p.grad[c] = c < v->nch ? v->tf[c].gradient : 0;
   }
   p.raw = v->d_tf_raw;
   return p;

@@ -16,6 +16,7 @@ LIB_PATH = os.environ.get("SG_LIBRARY") or os.path.join(HERE, "libsg.so")
 SG_OK, SG_ERR_INVALID_ARG, SG_ERR_OOM, SG_ERR_CUDA, SG_ERR_NOT_RESIDENT, SG_ERR_TIMEOUT, SG_ERR_STATE = range(7)
 SG_U8, SG_U16 = 1, 2
 SG_MODE_EMISSION_ABSORPTION, SG_MODE_EMISSION, SG_MODE_MIP = 0, 1, 2
+SG_INPUT_VALUE, SG_INPUT_GRADIENT = 0, 1
 STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_OOM", 3: "SG_ERR_CUDA", 4: "SG_ERR_NOT_RESIDENT",
                 5: "SG_ERR_TIMEOUT", 6: "SG_ERR_STATE"}
 
@@ -24,7 +25,7 @@ EXPORTS = ["sg_volume_create", "sg_volume_destroy", "sg_upload_volume_device", "
            "sg_render", "sg_render_host", "sg_render_batch", "sg_set_render_config", "sg_get_render_config",
            "sg_autotune_render", "sg_select_lod_noalloc", "sg_read_residency", "sg_set_brick_ranges", "sg_unet_create", "sg_unet_destroy",
            "sg_unet_param_count", "sg_unet_get_params", "sg_unet_set_params", "sg_unet_forward", "sg_unet_backward",
-           "sg_unet_adam_step", "sg_unet_set_tensor_path", "sg_unet_check", "sg_psnr", "sg_read_ranges", "sg_upload_brick_list", "sg_unwarp",
+           "sg_unet_adam_step", "sg_unet_set_tensor_path", "sg_unet_check", "sg_psnr", "sg_read_ranges", "sg_upload_brick_list", "sg_unwarp", "sg_set_channel_shading",
            "sg_last_error",
            "sg_version"]
 
@@ -96,6 +97,7 @@ def _load():
         "sg_upload_bricks": [vp, i32, i32, i32, i32, vp, vp, vp],
         "sg_upload_brick_list": [vp, i32, i32, i32, vp, vp, P(ctypes.c_int32), vp],
         "sg_unwarp": [P(sg_lens), P(vp), i32, i32, P(vp), i32, i32, vp],
+        "sg_set_channel_shading": [vp, i32, i32, vp, i32, f32, f32, vp],
         "sg_set_transfer_function": [vp, i32, vp, i32, f32, f32, f32, vp],
         "sg_select_lod": [vp, P(sg_pose), P(sg_select_stats), vp],
         "sg_select_lod_batch": [vp, P(sg_pose), i32, vp],
@@ -215,6 +217,16 @@ def sg_set_transfer_function(vol, c, rgba, lo, hi, ref_step=0.5, stream=None):
     import numpy as np
     tab = np.ascontiguousarray(rgba, np.float32).reshape(-1, 4)
     _check(lib.sg_set_transfer_function(vol, c, _ptr(tab), len(tab), lo, hi, ref_step, _stream(stream)))
+
+
+def sg_set_channel_shading(vol, c, gradient=False, palette=None, near=0.0, far=1.0, stream=None):
+    """Channel c's table reads the gradient magnitude (gradient=True) or the
+    value; palette: optional (m, 3) RGB in [0, 1] indexed by world distance
+    from the eye over [near, far]."""
+    import numpy as np
+    pal = None if palette is None else np.ascontiguousarray(palette, np.float32).reshape(-1, 3)
+    _check(lib.sg_set_channel_shading(vol, c, SG_INPUT_GRADIENT if gradient else SG_INPUT_VALUE, _ptr(pal),
+                                      0 if pal is None else len(pal), near, far, _stream(stream)))
 
 
 def make_pose(views, projs, width, height, pixel_error=1.0, t=0, slot=0):

@@ -1,0 +1,63 @@
+"""Gradient-magnitude tables and depth palettes ("Visualization
+Enhancements") against the oracle, in every optical model, with selection
+(gradient transparency) bit-exact and empty-space skipping exact."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity_util import GpuCase, compare_image, compare_selection
+
+pytestmark = pytest.mark.gpu
+
+PALETTE = np.array([[1.0, 0.2, 0.0], [0.9, 0.9, 0.1], [0.1, 0.8, 0.9], [0.3, 0.0, 1.0]], np.float32)
+
+
+def _case(gradient, palette, seed=1002):
+    v = synth.filaments_u16((256, 256, 256), seed=seed, ntubes=40)
+    case = GpuCase([v], 32, 4, model=synth.volume_model(256, 0.5))
+    table = synth.tf_piecewise(2002, zero_alpha_points=2)
+    window = (50.0, 20000.0) if gradient else (300.0, 60000.0)
+    case.set_tfs([table], [window])
+    near, far = 0.4, 1.1
+    case.sg.sg_set_channel_shading(case.vol, 0, gradient=gradient, palette=palette, near=near, far=far)
+    case.otfs = [oracle.make_tf(table, *window, gradient=gradient, palette=palette, near=near, far=far)]
+    return case
+
+
+@pytest.mark.parametrize("gradient,palette,mode", [
+    (True, None, oracle.MODE_EA),
+    (False, PALETTE, oracle.MODE_EA),
+    (True, PALETTE, oracle.MODE_EMISSION),
+    (True, PALETTE, oracle.MODE_MIP),
+])
+def test_gradient_tables_and_depth_palettes_match_the_oracle(gradient, palette, mode):
+    case = _case(gradient, palette)
+    try:
+        W, H = 224, 240
+        (views, projs), = synth.head_poses(1, seed=3800, extent_m=0.5, width=W, height=H)
+        pose, _, gsel, ref = case.select(views, projs, W, H, tau=0.25)
+        compare_selection(gsel, ref)
+        imgs, cnts = case.render(pose, empty_skip=0, mode=mode)
+        for e in range(2):
+            oref = case.oracle_render(ref["leaf"], views[e], projs[e], W, H, mode=mode)
+            compare_image(imgs[e], oref, cnts[e])
+        assert max(float(i[:, :3].max()) for i in imgs) > 0.05
+        skip, _ = case.render(pose, empty_skip=1, mode=mode)
+        assert np.array_equal(skip[0], imgs[0]) and np.array_equal(skip[1], imgs[1])
+    finally:
+        case.close()
+
+
+def test_shading_arguments_are_checked():
+    from paper_1804_08197_b300 import sg
+    case = _case(False, None)
+    try:
+        with pytest.raises(sg.SGError):
+            sg.sg_set_channel_shading(case.vol, 0, palette=PALETTE, near=1.0, far=1.0)
+        with pytest.raises(sg.SGError):
+            sg.sg_set_channel_shading(case.vol, 1)
+        with pytest.raises(sg.SGError):
+            sg.sg_set_channel_shading(case.vol, 0, palette=PALETTE * 2.0, near=0.0, far=1.0)
+    finally:
+        case.close()
