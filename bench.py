@@ -350,6 +350,110 @@ def streaming_flythrough(sg, torch, dev, full=None, count=256, budget_bytes=256 
             "uploaded_bricks": int(up_bricks), "generate_s": round(gen_s, 1), "ingest_and_store_s": round(ingest_s, 1)}
 
 
+def container_streaming(sg, torch, dev, n_vox=1024, brick=64, levels=4, count=128, budget_bytes=128 << 20):
+    """The storage path end to end ("Volumetric Data Storage" + "Cashing"):
+    the cell-body volume converted into an LZ4 brick container on local disk,
+    then a fly-through served by sg_stream_requests from a host cache of half
+    the bricks (misses read + decompressed on 16 host threads) into a GPU
+    cache of a quarter of them; renders pipelined on a compute stream.
+    Reports conversion throughput, compression ratio, frame time p50/p99 and
+    where the bricks came from."""
+    import shutil
+    import tempfile
+    import synth
+    extent = n_vox / 4096.0
+    model = synth.volume_model(n_vox, extent)
+    d = torch.empty((n_vox,) * 3, dtype=torch.uint8, device=dev)
+    synth.cells_u8_device(n_vox, d.data_ptr(), seed=1004, cell=64)
+    src = sg.sg_volume_create((n_vox,) * 3, sg.SG_U8, brick, levels, model=model)
+    sg.sg_upload_volume_device(src, 0, 0, d.data_ptr())
+    torch.cuda.synchronize()
+    del d
+    geo = []
+    for L in range(levels):
+        nb = -(-(-(-n_vox // (1 << L))) // brick)
+        geo += [(L, x, y, z) for z in range(nb) for y in range(nb) for x in range(nb)]
+    nodes = len(geo)
+    R3 = (brick + 2) ** 3
+    ranges = sg.sg_read_ranges(src, 0, nodes)
+    tmp = tempfile.mkdtemp(prefix="sgc_")
+    path = os.path.join(tmp, "cells.sgc")
+    t0 = time.perf_counter()
+    k = sg.sg_container_create(path, sg.volume_desc((n_vox,) * 3, sg.SG_U8, brick, levels, model=model))
+    # conversion on 16 host threads (the library calls release the GIL)
+    from concurrent.futures import ThreadPoolExecutor
+
+    def convert(part):
+        buf = np.empty(R3, np.uint8)
+        for i in part:
+            L, x, y, z = geo[i]
+            sg.sg_read_brick(src, 0, 0, L, x, y, z, buf)
+            sg.sg_container_append(k, 0, 0, L, x, y, z, buf, *ranges[i, 0])
+
+    with ThreadPoolExecutor(16) as ex:
+        list(ex.map(convert, [range(j, nodes, 16) for j in range(16)]))
+    sg.sg_container_finish(k)
+    convert_s = time.perf_counter() - t0
+    info = sg.sg_container_get_info(k)
+    sg.sg_container_close(k)
+    sg.sg_volume_destroy(src)
+    k = sg.sg_container_open(path)
+    slot_bytes = (R3 + 255) // 256 * 256
+    vol = sg.sg_volume_create((n_vox,) * 3, sg.SG_U8, brick, levels, model=model,
+                              device_pool_bytes=(nodes // 4) * slot_bytes)
+    hc = sg.sg_host_cache_create(k, (nodes // 2) * R3, pinned=True, threads=16)
+    try:
+        sg.sg_set_transfer_function(vol, 0, synth.tf_piecewise(2004, zero_alpha_points=2, zero_span=(60, 80)),
+                                    0.0, 255.0)
+        off = 0
+        for L in range(levels):
+            nl = sum(1 for g in geo if g[0] == L)
+            sg.sg_set_brick_ranges(vol, 0, 0, L, np.array([g[1:] for g in geo[off:off + nl]]),
+                                   ranges[off:off + nl, 0, :])
+            off += nl
+        top = [i for i, g in enumerate(geo) if g[0] == levels - 1]
+        ptrs = [sg.sg_host_cache_fetch(hc, 0, 0, n)[0] for n in top]
+        sg.sg_upload_brick_list(vol, 0, 0, top, ptrs)
+        poses = synth.flythrough_poses(count, seed=3004, extent_m=extent, width=W_EYE, height=H_EYE)
+        outs = [torch.empty((H_EYE, W_EYE, 4), dtype=torch.float32, device=dev) for _ in range(2)]
+        prm = sg.render_params(step=STEP, term_alpha=TERM)
+        comp, copy = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        frame_ms, tot = [], dict(served=0, host_hits=0, disk_reads=0, disk_bytes=0, upload_bytes=0)
+        stream_ms = []
+        torch.cuda.synchronize()
+        for views, projs in poses:
+            t0 = time.perf_counter()
+            pose = sg.make_pose(views, projs, W_EYE, H_EYE, pixel_error=TAU)
+            st = sg.sg_select_lod(vol, pose, stats=True, stream=comp)
+            sg.sg_render(vol, pose, prm, outs, stream=comp)
+            ts = time.perf_counter()
+            if st["requested"]:
+                s = sg.sg_stream_requests(vol, 0, hc, budget_bytes, stream=copy)
+                for key in tot:
+                    tot[key] += s[key]
+            stream_ms.append((time.perf_counter() - ts) * 1e3)
+            comp.synchronize()
+            frame_ms.append((time.perf_counter() - t0) * 1e3)
+    finally:
+        sg.sg_host_cache_destroy(hc)
+        sg.sg_volume_destroy(vol)
+        sg.sg_container_close(k)
+        shutil.rmtree(tmp, ignore_errors=True)
+    fm, sm = np.array(frame_ms), np.array(stream_ms)
+    return {"workload": f"brick container + host cache: {n_vox}^3 u8 cell bodies, {brick}^3 bricks, {levels} levels, "
+                        f"{nodes} LZ4 chunks on local disk; host cache {nodes // 2} bricks (pinned, 16 decode "
+                        f"threads), GPU cache {nodes // 4} bricks; {count}-pose fly-through, 2x{W_EYE}x{H_EYE}, "
+                        f"<= {budget_bytes >> 20} MiB per frame",
+            "convert_s": round(convert_s, 2), "convert_gbs": round(info["raw_bytes"] / convert_s / 1e9, 3),
+            "compression_ratio": round(info["raw_bytes"] / max(info["compressed_bytes"], 1), 3),
+            "frame_ms_p50": round(float(np.percentile(fm, 50)), 3),
+            "frame_ms_p99": round(float(np.percentile(fm, 99)), 3),
+            "stream_ms_p99": round(float(np.percentile(sm, 99)), 3),
+            "bricks_served": int(tot["served"]), "host_hits": int(tot["host_hits"]),
+            "disk_reads": int(tot["disk_reads"]),
+            "disk_read_gbs": round(tot["disk_bytes"] / max(sm.sum() / 1e3, 1e-9) / 1e9, 3)}
+
+
 def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=4000, steps_per_pair=4, eval_poses=16,
                   threshold_db=40.0):
     """Learned reconstruction vs the plain path on the same GPU: training on
@@ -650,10 +754,11 @@ def run_ours(args, rank, world, local_rank):
         sg.sg_render_host(vol, p, prm, host, stream=stream)
     e2e_s = time.perf_counter() - t0
 
-    batched = learned = streaming = None
+    batched = learned = streaming = container = None
     if rank == 0 and not args.no_extra and n_vox == N_VOX:
         batched = batched_4d(sg, torch, dev)
         streaming = streaming_flythrough(sg, torch, dev)
+        container = container_streaming(sg, torch, dev)
         learned = learned_recon(sg, torch, dev, vol, tf_table, model, pairs=args.learned_pairs)
 
     cpu = None
@@ -693,6 +798,8 @@ def run_ours(args, rank, world, local_rank):
             line["learned"] = learned
         if streaming:
             line["streaming"] = streaming
+        if container:
+            line["container_streaming"] = container
         print(json.dumps(line), flush=True)
     sg.sg_volume_destroy(vol)
 
@@ -711,7 +818,7 @@ def main():
                     help="empty-space skipping cell edge in voxels (0 = the library's default)")
     ap.add_argument("--streaming-size", choices=["auto", "full", "scaled"], default="auto",
                     help="large-volume fly-through at 4096^3 (full), at 1024^3 (scaled), or full when it fits")
-    ap.add_argument("--only", choices=["net", "streaming"], default=None,
+    ap.add_argument("--only", choices=["net", "streaming", "container"], default=None,
                     help="net: only U-Net forwards at 2x720x800 (a small case for profiling the convolutions); "
                          "streaming: only the large-volume fly-through")
     ap.add_argument("--volume", type=int, default=N_VOX, help="volume edge (default 1024; smaller for profiling)")
@@ -736,6 +843,11 @@ def main():
         torch.cuda.set_device(local_rank)
         full = {"auto": None, "full": True, "scaled": False}[args.streaming_size]
         print(json.dumps(streaming_flythrough(sg, torch, torch.device("cuda"), full=full)), flush=True)
+    elif args.only == "container":
+        import torch
+        from paper_1804_08197_b300 import sg
+        torch.cuda.set_device(local_rank)
+        print(json.dumps(container_streaming(sg, torch, torch.device("cuda"))), flush=True)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:

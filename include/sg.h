@@ -49,7 +49,8 @@ typedef enum {
   SG_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error string) */
   SG_ERR_NOT_RESIDENT = 4,/* a brick the call needs is not in the device cache */
   SG_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
-  SG_ERR_STATE = 6        /* calls out of order (e.g. render before select, TF missing) */
+  SG_ERR_STATE = 6,       /* calls out of order (e.g. render before select, TF missing) */
+  SG_ERR_IO = 7           /* a container file could not be read or written, or holds a corrupt chunk */
 } sg_status;
 
 typedef enum { SG_U8 = 1, SG_U16 = 2 } sg_dtype;
@@ -129,6 +130,95 @@ sg_status sg_upload_bricks(sg_volume* vol, int t, int c, int level, int n, const
  * memory), CUDA. */
 sg_status sg_upload_brick_list(sg_volume* vol, int t, int c, int n, const int32_t* nodes, const void* const* host,
                                int32_t* n_done, void* stream);
+
+/* ---- Brick container and host cache ("Volumetric Data Storage",
+ * "Volumetric Data Cashing") ----------------------------------------------
+ * A container is one file of LZ4-compressed chunks, one per brick with its
+ * apron ((B+2)^3 voxels of the layout's dtype, x fastest) of any (t, c,
+ * level). Chunks are appended (a chunk has a header and a checksum, so a
+ * conversion that stopped part way resumes after its last complete chunk);
+ * sg_container_finish writes the index table of chunk offsets and a footer.
+ * The host cache keeps decompressed bricks in (optionally page-locked) host
+ * memory, least recently used out first, in front of a volume's GPU cache.
+ * Container and cache calls are host-only: no GPU is needed except for a
+ * page-locked cache and sg_stream_requests. */
+typedef struct sg_container sg_container;   /* opaque */
+typedef struct sg_host_cache sg_host_cache; /* opaque */
+
+typedef struct {
+  sg_volume_desc desc;        /* the layout (device_pool_bytes and model as written) */
+  int64_t chunks;             /* chunks present */
+  int64_t nodes;              /* blocks per (t, c) */
+  uint64_t raw_bytes;         /* total decompressed bytes of the chunks */
+  uint64_t compressed_bytes;  /* total chunk payload bytes */
+  int32_t complete;           /* 1: finished (indexed, read only); 0: appendable */
+  int32_t reserved;
+} sg_container_info;
+
+/* Creates (truncates) path as an empty container for the layout desc.
+ * Errors: INVALID_ARG, OOM, IO. */
+sg_status sg_container_create(const char* path, const sg_volume_desc* desc, sg_container** out);
+
+/* Opens a container. A finished one is read through its index (read only);
+ * an unfinished one is scanned chunk by chunk, a torn last chunk is cut off,
+ * and appending resumes after the last complete chunk. Errors: INVALID_ARG,
+ * OOM, IO (missing file, bad header). */
+sg_status sg_container_open(const char* path, sg_container** out);
+
+/* Compresses and appends the brick (t, c, level, bx, by, bz) with its value
+ * range [vmin, vmax] (over the brick and its apron, as the index of
+ * sg_set_brick_ranges). A brick appended twice keeps its last chunk. Safe
+ * to call from several threads at once (compression runs in parallel, the
+ * writes are serialised). Errors: INVALID_ARG, STATE (finished container),
+ * IO. */
+sg_status sg_container_append(sg_container* k, int t, int c, int level, int bx, int by, int bz, const void* brick,
+                              uint32_t vmin, uint32_t vmax);
+
+/* Writes the index table and the footer; the container becomes read only.
+ * Errors: INVALID_ARG, IO. */
+sg_status sg_container_finish(sg_container* k);
+
+sg_status sg_container_get_info(sg_container* k, sg_container_info* info);
+
+/* Reads and decompresses the brick of (t, c, node id) into out ((B+2)^3
+ * voxels); minmax (optional) receives its stored range. Errors: INVALID_ARG,
+ * NOT_RESIDENT (no chunk for it), IO (corrupt chunk). */
+sg_status sg_container_read(sg_container* k, int t, int c, int64_t node, void* out, uint32_t* minmax);
+
+sg_status sg_container_close(sg_container* k);
+
+/* A host cache of floor(bytes / brick bytes) decompressed bricks of
+ * container k (which must outlive it); pinned != 0 page-locks it for full
+ * upload bandwidth; threads decompress misses in parallel. Errors:
+ * INVALID_ARG, OOM. */
+sg_status sg_host_cache_create(sg_container* k, uint64_t bytes, int pinned, int threads, sg_host_cache** out);
+sg_status sg_host_cache_destroy(sg_host_cache* hc);
+
+/* The cached brick of (t, c, node), read and decompressed on a miss (*hit
+ * = 0) into an entry that stays valid until the next cache call. Errors:
+ * INVALID_ARG, NOT_RESIDENT, OOM, IO. */
+sg_status sg_host_cache_fetch(sg_host_cache* hc, int t, int c, int64_t node, const void** brick, int* hit);
+
+typedef struct {
+  int32_t requested;     /* requests of the selection */
+  int32_t served;        /* bricks placed in the GPU cache by this call */
+  int32_t host_hits;     /* brick-channels found in the host cache */
+  int32_t disk_reads;    /* brick-channels read and decompressed from the container */
+  int32_t missing;       /* requests without a chunk in the container (skipped) */
+  int32_t reserved;
+  uint64_t disk_bytes;   /* compressed bytes read */
+  uint64_t upload_bytes; /* bytes copied to the GPU cache */
+} sg_stream_stats;
+
+/* Serves the requests of selection slot `slot` of vol from container-backed
+ * host cache hc: coarse levels first (then node id), at most max_bytes of
+ * bricks (all channels); each from the host cache or read + decompressed
+ * (hc's threads), then placed in the GPU cache (sg_upload_brick_list per
+ * channel, on stream; complete on return). Stops early, without error, when
+ * either cache holds only bricks of the current frame. Errors: INVALID_ARG
+ * (layouts differ), STATE, IO, OOM, CUDA. */
+sg_status sg_stream_requests(sg_volume* vol, int slot, sg_host_cache* hc, uint64_t max_bytes, sg_stream_stats* stats,
+                             void* stream);
 
 /* Value ranges of bricks known without their data, as a container's index
  * table would hold them ("Volumetric Data Storage": chunks with an index):

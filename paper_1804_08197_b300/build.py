@@ -9,7 +9,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsg.so")
-SOURCES = ["api.cu", "ingest.cu", "tf.cu", "select.cu", "render.cu", "lens.cu", "unet.cu"]
+SOURCES = ["api.cu", "ingest.cu", "tf.cu", "select.cu", "render.cu", "lens.cu", "unet.cu", "lz4.cpp", "container.cpp",
+           "stream.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -627,6 +627,8 @@ sg_status sg_read_selection(sg_volume* v, int slot, int32_t* cell_node, int64_t 
   SG_CHECK_ARG(!cell_node || ncell >= v->ncell, "cell_node buffer too small");
   SG_CHECK_ARG(!node_state || nnode >= v->nodes, "node_state buffer too small");
   uint32_t c[8];
+  // the selection may have been launched on another stream
+  SG_CUDA(cudaStreamWaitEvent(s, v->ev_select, 0), "read selection");
   SG_CUDA(cudaMemcpyAsync(c, sl.d_counters, sizeof c, cudaMemcpyDeviceToHost, s), "read selection");
   if (cell_node)
     SG_CUDA(cudaMemcpyAsync(cell_node, sl.d_cell_node, v->ncell * sizeof(int32_t), cudaMemcpyDeviceToHost, s),

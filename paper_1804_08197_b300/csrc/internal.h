@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/sg.h"
@@ -155,4 +156,19 @@ cudaError_t launch_render(sg_volume* v, const sg_pose* poses, int n, const sg_re
 bool render_config_supported(const sg_render_config* c);
 int render_config_candidates(sg_render_config* out, int cap);
 
+}  // namespace sg
+
+// Container and host cache (host code shared by container.cpp and stream.cpp)
+namespace sg {
+size_t lz4_bound(size_t n);
+size_t lz4_compress(const uint8_t* src, size_t n, uint8_t* dst);
+bool lz4_decompress(const uint8_t* src, size_t csize, uint8_t* dst, size_t n);
+sg_status container_read_chunk(sg_container* k, uint64_t off, void* out, uint32_t* minmax, uint32_t* comp_bytes);
+const sg_volume_desc& container_desc(const sg_container* k);
+uint64_t container_chunk_offset(const sg_container* k, int t, int c, int64_t node, bool* found);
+size_t container_brick_bytes(const sg_container* k);
+int64_t container_nodes(const sg_container* k);
+sg_status host_cache_lookup(sg_host_cache* hc, int t, int c, int64_t node, int64_t* entry, int* hit,
+                            std::vector<std::pair<int64_t, int64_t>>* todo);
+void host_cache_drop(sg_host_cache* hc, int64_t e);
 }  // namespace sg

@@ -1,0 +1,293 @@
+// Host-memory brick cache between a container and a volume's GPU brick cache
+// ("Volumetric Data Cashing": a CPU cache and a GPU cache, each keeping as
+// many chunks as fit and dropping the least recently used, by timestamp).
+// sg_stream_requests serves one selection's requests: coarse levels first,
+// each brick from the host cache or, on a miss, read from the container and
+// LZ4-decompressed by a pool of threads, then placed in the GPU cache by one
+// list upload per channel.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <map>
+#include <new>
+#include <set>
+#include <thread>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+using namespace sg;
+
+struct sg_host_cache {
+  sg_container* k = nullptr;
+  uint8_t* arena = nullptr;
+  bool pinned = false;
+  size_t entry_bytes = 0;
+  int64_t entries = 0;
+  int threads = 1;
+  uint64_t frame = 0;
+  std::map<int64_t, int64_t> where;           // key (t, c, node) -> entry
+  std::vector<int64_t> owner;                 // entry -> key or -1
+  std::vector<uint64_t> stamp;                // entry -> frame of last use
+  std::set<std::pair<uint64_t, int64_t>> lru;  // (stamp, entry) of occupied entries
+  std::vector<int64_t> free_list;
+};
+
+extern "C" {
+
+sg_status sg_host_cache_create(sg_container* k, uint64_t bytes, int pinned, int threads, sg_host_cache** out) {
+  if (!k || !out) {
+    set_error("container and out must not be NULL");
+    return SG_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  const size_t eb = container_brick_bytes(k);
+  if (bytes < eb || threads < 1 || threads > 256) {
+    set_error("host cache: at least one brick of bytes, 1..256 threads");
+    return SG_ERR_INVALID_ARG;
+  }
+  sg_host_cache* hc = new (std::nothrow) sg_host_cache();
+  if (!hc) {
+    set_error("host allocation failed");
+    return SG_ERR_OOM;
+  }
+  hc->k = k;
+  hc->entry_bytes = eb;
+  hc->entries = (int64_t)(bytes / eb);
+  hc->threads = threads;
+  const size_t total = (size_t)hc->entries * eb;
+  if (pinned) {
+    if (cudaHostAlloc(reinterpret_cast<void**>(&hc->arena), total, cudaHostAllocDefault) != cudaSuccess) {
+      delete hc;
+      set_error("host cache: page-locked allocation failed");
+      return SG_ERR_OOM;
+    }
+    hc->pinned = true;
+  } else {
+    hc->arena = static_cast<uint8_t*>(malloc(total));
+    if (!hc->arena) {
+      delete hc;
+      set_error("host cache: allocation failed");
+      return SG_ERR_OOM;
+    }
+  }
+  hc->owner.assign(hc->entries, -1);
+  hc->stamp.assign(hc->entries, 0);
+  for (int64_t i = hc->entries - 1; i >= 0; --i) hc->free_list.push_back(i);
+  *out = hc;
+  return SG_OK;
+}
+
+sg_status sg_host_cache_destroy(sg_host_cache* hc) {
+  if (!hc) return SG_OK;
+  if (hc->pinned)
+    cudaFreeHost(hc->arena);
+  else
+    free(hc->arena);
+  delete hc;
+  return SG_OK;
+}
+
+sg_status sg_host_cache_fetch(sg_host_cache* hc, int t, int c, int64_t node, const void** brick, int* hit) {
+  if (!hc || !brick) {
+    set_error("cache or output NULL");
+    return SG_ERR_INVALID_ARG;
+  }
+  ++hc->frame;
+  std::vector<std::pair<int64_t, int64_t>> todo;  // (entry, chunk offset)
+  int64_t entry = -1;
+  sg_status st = host_cache_lookup(hc, t, c, node, &entry, hit, &todo);
+  if (st != SG_OK) return st;
+  if (!todo.empty()) {
+    st = container_read_chunk(hc->k, (uint64_t)todo[0].second, hc->arena + (size_t)entry * hc->entry_bytes, nullptr,
+                              nullptr);
+    if (st != SG_OK) {
+      host_cache_drop(hc, entry);
+      return st;
+    }
+  }
+  *brick = hc->arena + (size_t)entry * hc->entry_bytes;
+  return SG_OK;
+}
+
+}  // extern "C"
+
+namespace sg {
+
+// Finds or places (t, c, node) in the host cache, stamping it with the
+// current frame. A new entry comes from the free list, else from the least
+// recently used entry not used this frame; its chunk offset is queued in
+// todo for loading. SG_ERR_NOT_RESIDENT: no chunk in the container;
+// SG_ERR_OOM: every entry is in use this frame.
+sg_status host_cache_lookup(sg_host_cache* hc, int t, int c, int64_t node, int64_t* entry, int* hit,
+                            std::vector<std::pair<int64_t, int64_t>>* todo) {
+  const sg_volume_desc& d = container_desc(hc->k);
+  const int64_t nodes = container_nodes(hc->k);
+  const int64_t key = ((int64_t)t * d.channels + c) * nodes + node;
+  auto it = hc->where.find(key);
+  if (it != hc->where.end()) {
+    const int64_t e = it->second;
+    hc->lru.erase({hc->stamp[e], e});
+    hc->stamp[e] = hc->frame;
+    hc->lru.insert({hc->frame, e});
+    *entry = e;
+    if (hit) *hit = 1;
+    return SG_OK;
+  }
+  bool found = false;
+  const uint64_t off = container_chunk_offset(hc->k, t, c, node, &found);
+  if (!found) {
+    set_error("host cache: the container has no chunk for this brick");
+    return SG_ERR_NOT_RESIDENT;
+  }
+  int64_t e;
+  if (!hc->free_list.empty()) {
+    e = hc->free_list.back();
+    hc->free_list.pop_back();
+  } else {
+    auto lo = hc->lru.begin();
+    if (lo == hc->lru.end() || lo->first >= hc->frame) {
+      set_error("host cache: full of bricks used by the current frame");
+      return SG_ERR_OOM;
+    }
+    e = lo->second;
+    hc->lru.erase(lo);
+    hc->where.erase(hc->owner[e]);
+  }
+  hc->owner[e] = key;
+  hc->where[key] = e;
+  hc->stamp[e] = hc->frame;
+  hc->lru.insert({hc->frame, e});
+  todo->push_back({e, (int64_t)off});
+  *entry = e;
+  if (hit) *hit = 0;
+  return SG_OK;
+}
+
+void host_cache_drop(sg_host_cache* hc, int64_t e) {
+  hc->lru.erase({hc->stamp[e], e});
+  hc->where.erase(hc->owner[e]);
+  hc->owner[e] = -1;
+  hc->free_list.push_back(e);
+}
+
+}  // namespace sg
+
+extern "C" sg_status sg_stream_requests(sg_volume* v, int slot, sg_host_cache* hc, uint64_t max_bytes,
+                                        sg_stream_stats* stats, void* stream) {
+  if (!v || !hc || slot < 0 || slot >= kMaxSlots) {
+    set_error("volume/cache NULL or slot out of range");
+    return SG_ERR_INVALID_ARG;
+  }
+  const sg_volume_desc& d = container_desc(hc->k);
+  if (d.dims[0] != v->desc.dims[0] || d.dims[1] != v->desc.dims[1] || d.dims[2] != v->desc.dims[2] ||
+      d.dtype != v->desc.dtype || d.brick_size != v->B || d.lod_levels != v->levels || d.channels != v->nch ||
+      d.timepoints > v->T) {
+    set_error("sg_stream_requests: the container's layout differs from the volume's");
+    return SG_ERR_INVALID_ARG;
+  }
+  sg_stream_stats s0;
+  memset(&s0, 0, sizeof s0);
+  const SelSlot& sl = v->sel[slot];
+  if (!sl.valid) {
+    set_error("sg_stream_requests: slot was never selected");
+    return SG_ERR_STATE;
+  }
+  const int t = sl.t;
+  std::vector<int32_t> req((size_t)v->nodes);
+  int32_t nreq = 0;
+  sg_status st = sg_read_selection(v, slot, nullptr, 0, nullptr, 0, req.data(), (int32_t)req.size(), &nreq, stream);
+  if (st != SG_OK) return st;
+  req.resize((size_t)std::min<int64_t>(nreq, (int64_t)req.size()));
+  s0.requested = (int32_t)req.size();
+  // coarse levels first (a parent before its children), then node id
+  auto level_of = [&](int32_t n) {
+    int L = 0;
+    while (L + 1 < v->levels && n >= v->geom[L + 1].off) ++L;
+    return L;
+  };
+  std::stable_sort(req.begin(), req.end(), [&](int32_t a, int32_t b) {
+    const int la = level_of(a), lb = level_of(b);
+    return la != lb ? la > lb : a < b;
+  });
+  const uint64_t per_node = (uint64_t)hc->entry_bytes * v->nch;
+  const size_t budget = per_node ? (size_t)std::min<uint64_t>(max_bytes / per_node, req.size()) : 0;
+  ++hc->frame;
+  // place every (node, channel) of the budget in the host cache
+  std::vector<int32_t> nodes;
+  std::vector<std::vector<const void*>> ptrs(v->nch);
+  std::vector<std::pair<int64_t, int64_t>> todo;
+  for (size_t i = 0; i < budget; ++i) {
+    const int32_t node = req[i];
+    std::vector<int64_t> ent(v->nch);
+    bool ok = true;
+    size_t todo_mark = todo.size();
+    for (int c = 0; c < v->nch && ok; ++c) {
+      int hit = 0;
+      st = host_cache_lookup(hc, t, c, node, &ent[c], &hit, &todo);
+      if (st == SG_ERR_NOT_RESIDENT) {
+        ++s0.missing;
+        ok = false;
+      } else if (st == SG_ERR_OOM) {
+        ok = false;
+      } else if (st != SG_OK) {
+        return st;
+      } else if (hit) {
+        ++s0.host_hits;
+      }
+    }
+    if (!ok) {
+      // undo the entries queued for this node; stop at a full cache
+      while (todo.size() > todo_mark) {
+        host_cache_drop(hc, todo.back().first);
+        todo.pop_back();
+      }
+      if (st == SG_ERR_OOM) break;
+      continue;
+    }
+    nodes.push_back(node);
+    for (int c = 0; c < v->nch; ++c) ptrs[c].push_back(hc->arena + (size_t)ent[c] * hc->entry_bytes);
+  }
+  // read + decompress the misses on a pool of threads
+  std::atomic<size_t> next(0);
+  std::atomic<int> failed(0);
+  std::atomic<uint64_t> disk_bytes(0);
+  auto work = [&]() {
+    for (;;) {
+      const size_t i = next.fetch_add(1);
+      if (i >= todo.size()) return;
+      uint32_t comp = 0;
+      if (container_read_chunk(hc->k, (uint64_t)todo[i].second, hc->arena + (size_t)todo[i].first * hc->entry_bytes,
+                               nullptr, &comp) != SG_OK)
+        failed.fetch_add(1);
+      disk_bytes.fetch_add(comp);
+    }
+  };
+  const int nt = (int)std::min<size_t>((size_t)hc->threads, todo.size());
+  std::vector<std::thread> pool;
+  for (int i = 1; i < nt; ++i) pool.emplace_back(work);
+  if (nt >= 1) work();
+  for (auto& th : pool) th.join();
+  if (failed.load()) {
+    for (auto& e : todo) host_cache_drop(hc, e.first);
+    set_error("sg_stream_requests: a chunk failed to read or decompress");
+    return SG_ERR_IO;
+  }
+  s0.disk_reads = (int32_t)todo.size();
+  s0.disk_bytes = disk_bytes.load();
+  // one list upload per channel (the first places the slots)
+  int32_t placed = (int32_t)nodes.size();
+  for (int c = 0; c < v->nch && !nodes.empty(); ++c) {
+    int32_t done = 0;
+    st = sg_upload_brick_list(v, t, c, placed, nodes.data(), ptrs[c].data(), &done, stream);
+    if (st != SG_OK) return st;
+    placed = std::min(placed, done);
+  }
+  s0.served = placed;
+  s0.upload_bytes = (uint64_t)placed * per_node;
+  if (stats) *stats = s0;
+  return SG_OK;
+}

@@ -13,12 +13,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # SG_LIBRARY may point at another build of the same library (e.g. a tuning variant)
 LIB_PATH = os.environ.get("SG_LIBRARY") or os.path.join(HERE, "libsg.so")
 
-SG_OK, SG_ERR_INVALID_ARG, SG_ERR_OOM, SG_ERR_CUDA, SG_ERR_NOT_RESIDENT, SG_ERR_TIMEOUT, SG_ERR_STATE = range(7)
+SG_OK, SG_ERR_INVALID_ARG, SG_ERR_OOM, SG_ERR_CUDA, SG_ERR_NOT_RESIDENT, SG_ERR_TIMEOUT, SG_ERR_STATE, SG_ERR_IO = range(8)
 SG_U8, SG_U16 = 1, 2
 SG_MODE_EMISSION_ABSORPTION, SG_MODE_EMISSION, SG_MODE_MIP = 0, 1, 2
 SG_INPUT_VALUE, SG_INPUT_GRADIENT = 0, 1
 STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_OOM", 3: "SG_ERR_CUDA", 4: "SG_ERR_NOT_RESIDENT",
-                5: "SG_ERR_TIMEOUT", 6: "SG_ERR_STATE"}
+                5: "SG_ERR_TIMEOUT", 6: "SG_ERR_STATE", 7: "SG_ERR_IO"}
 
 EXPORTS = ["sg_volume_create", "sg_volume_destroy", "sg_upload_volume_device", "sg_upload_bricks",
            "sg_set_transfer_function", "sg_select_lod", "sg_select_lod_batch", "sg_read_selection", "sg_read_brick",
@@ -26,6 +26,9 @@ EXPORTS = ["sg_volume_create", "sg_volume_destroy", "sg_upload_volume_device", "
            "sg_autotune_render", "sg_select_lod_noalloc", "sg_read_residency", "sg_set_brick_ranges", "sg_unet_create", "sg_unet_destroy",
            "sg_unet_param_count", "sg_unet_get_params", "sg_unet_set_params", "sg_unet_forward", "sg_unet_backward",
            "sg_unet_adam_step", "sg_unet_set_tensor_path", "sg_unet_check", "sg_psnr", "sg_read_ranges", "sg_upload_brick_list", "sg_unwarp", "sg_set_channel_shading",
+           "sg_container_create", "sg_container_open", "sg_container_append", "sg_container_finish",
+           "sg_container_get_info", "sg_container_read", "sg_container_close", "sg_host_cache_create",
+           "sg_host_cache_destroy", "sg_host_cache_fetch", "sg_stream_requests",
            "sg_last_error",
            "sg_version"]
 
@@ -53,6 +56,18 @@ class sg_select_stats(ctypes.Structure):
     _fields_ = [("selected", ctypes.c_uint32), ("culled", ctypes.c_uint32), ("empty", ctypes.c_uint32),
                 ("requested", ctypes.c_uint32), ("fallback", ctypes.c_uint32), ("nonempty", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32 * 2)]
+
+
+class sg_container_info(ctypes.Structure):
+    _fields_ = [("desc", sg_volume_desc), ("chunks", ctypes.c_int64), ("nodes", ctypes.c_int64),
+                ("raw_bytes", ctypes.c_uint64), ("compressed_bytes", ctypes.c_uint64), ("complete", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class sg_stream_stats(ctypes.Structure):
+    _fields_ = [("requested", ctypes.c_int32), ("served", ctypes.c_int32), ("host_hits", ctypes.c_int32),
+                ("disk_reads", ctypes.c_int32), ("missing", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("disk_bytes", ctypes.c_uint64), ("upload_bytes", ctypes.c_uint64)]
 
 
 class sg_lens(ctypes.Structure):
@@ -98,6 +113,17 @@ def _load():
         "sg_upload_brick_list": [vp, i32, i32, i32, vp, vp, P(ctypes.c_int32), vp],
         "sg_unwarp": [P(sg_lens), P(vp), i32, i32, P(vp), i32, i32, vp],
         "sg_set_channel_shading": [vp, i32, i32, vp, i32, f32, f32, vp],
+        "sg_container_create": [ctypes.c_char_p, P(sg_volume_desc), P(vp)],
+        "sg_container_open": [ctypes.c_char_p, P(vp)],
+        "sg_container_append": [vp, i32, i32, i32, i32, i32, i32, vp, ctypes.c_uint32, ctypes.c_uint32],
+        "sg_container_finish": [vp],
+        "sg_container_get_info": [vp, P(sg_container_info)],
+        "sg_container_read": [vp, i32, i32, i64, vp, vp],
+        "sg_container_close": [vp],
+        "sg_host_cache_create": [vp, ctypes.c_uint64, i32, i32, P(vp)],
+        "sg_host_cache_destroy": [vp],
+        "sg_host_cache_fetch": [vp, i32, i32, i64, P(vp), P(ctypes.c_int)],
+        "sg_stream_requests": [vp, i32, vp, ctypes.c_uint64, P(sg_stream_stats), vp],
         "sg_set_transfer_function": [vp, i32, vp, i32, f32, f32, f32, vp],
         "sg_select_lod": [vp, P(sg_pose), P(sg_select_stats), vp],
         "sg_select_lod_batch": [vp, P(sg_pose), i32, vp],
@@ -217,6 +243,75 @@ def sg_set_transfer_function(vol, c, rgba, lo, hi, ref_step=0.5, stream=None):
     import numpy as np
     tab = np.ascontiguousarray(rgba, np.float32).reshape(-1, 4)
     _check(lib.sg_set_transfer_function(vol, c, _ptr(tab), len(tab), lo, hi, ref_step, _stream(stream)))
+
+
+def volume_desc(dims, dtype, brick_size, lod_levels, channels=1, timepoints=1, model=None):
+    d = sg_volume_desc()
+    d.dims[:] = [int(x) for x in dims]
+    d.dtype, d.channels, d.timepoints, d.brick_size, d.apron, d.lod_levels = dtype, channels, timepoints, brick_size, 1, lod_levels
+    m = [1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1] if model is None else [float(x) for x in model]
+    d.model[:] = m
+    return d
+
+
+def sg_container_create(path, desc):
+    h = ctypes.c_void_p()
+    _check(lib.sg_container_create(str(path).encode(), ctypes.byref(desc), ctypes.byref(h)))
+    return h
+
+
+def sg_container_open(path):
+    h = ctypes.c_void_p()
+    _check(lib.sg_container_open(str(path).encode(), ctypes.byref(h)))
+    return h
+
+
+def sg_container_append(k, t, c, level, bx, by, bz, brick, vmin, vmax):
+    _check(lib.sg_container_append(k, t, c, level, bx, by, bz, _ptr(brick), int(vmin), int(vmax)))
+
+
+def sg_container_finish(k):
+    _check(lib.sg_container_finish(k))
+
+
+def sg_container_get_info(k):
+    info = sg_container_info()
+    _check(lib.sg_container_get_info(k, ctypes.byref(info)))
+    return dict(chunks=info.chunks, nodes=info.nodes, raw_bytes=info.raw_bytes,
+                compressed_bytes=info.compressed_bytes, complete=bool(info.complete))
+
+
+def sg_container_read(k, t, c, node, out):
+    mm = (ctypes.c_uint32 * 2)()
+    _check(lib.sg_container_read(k, t, c, node, _ptr(out), mm))
+    return int(mm[0]), int(mm[1])
+
+
+def sg_container_close(k):
+    _check(lib.sg_container_close(k))
+
+
+def sg_host_cache_create(k, nbytes, pinned=False, threads=8):
+    h = ctypes.c_void_p()
+    _check(lib.sg_host_cache_create(k, int(nbytes), int(bool(pinned)), int(threads), ctypes.byref(h)))
+    return h
+
+
+def sg_host_cache_destroy(hc):
+    _check(lib.sg_host_cache_destroy(hc))
+
+
+def sg_host_cache_fetch(hc, t, c, node):
+    """(address of the cached brick, hit)"""
+    p, hit = ctypes.c_void_p(), ctypes.c_int(0)
+    _check(lib.sg_host_cache_fetch(hc, t, c, node, ctypes.byref(p), ctypes.byref(hit)))
+    return p.value, bool(hit.value)
+
+
+def sg_stream_requests(vol, slot, hc, max_bytes, stream=None):
+    st = sg_stream_stats()
+    _check(lib.sg_stream_requests(vol, slot, hc, int(max_bytes), ctypes.byref(st), _stream(stream)))
+    return {f[0]: getattr(st, f[0]) for f in sg_stream_stats._fields_ if f[0] != "reserved"}
 
 
 def sg_set_channel_shading(vol, c, gradient=False, palette=None, near=0.0, far=1.0, stream=None):

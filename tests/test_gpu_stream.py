@@ -214,3 +214,72 @@ def test_upload_list_cut_short_leaves_a_consistent_cache():
         assert cut, "the cache should have been too small for one frame's requests"
     finally:
         sg.sg_volume_destroy(vol)
+
+
+def test_streaming_from_a_container_through_the_host_cache(tmp_path):
+    """The full storage path: every brick LZ4-compressed in a container,
+    a host cache smaller than the volume, sg_stream_requests per frame
+    (coarse first, misses decompressed on host threads, one list upload).
+    Every frame's selection equals the oracle's for that residency; the
+    converged frame renders like the oracle."""
+    import torch
+    from paper_1804_08197_b300 import sg
+    a = synth.filaments_u16(DIMS, seed=33, ntubes=18)
+    model = synth.volume_model(128, 0.5)
+    ovol = oracle.Volume([oracle.pyramid(a, LEVELS)], B, model=model)
+    full = ovol.block_ranges()
+    table = synth.tf_piecewise(2002, zero_alpha_points=2)
+    otf = oracle.make_tf(table, 300.0, 60000.0)
+    path = tmp_path / "vol.sgc"
+    desc = sg.volume_desc(DIMS, sg.SG_U16, B, LEVELS, model=model)
+    k = sg.sg_container_create(path, desc)
+    for n in range(ovol.node_count):
+        L, b = ovol.node_coords(n)
+        sg.sg_container_append(k, 0, 0, L, *b, _brick(ovol, L, *b), *full[n, 0])
+    sg.sg_container_finish(k)
+    sg.sg_container_close(k)
+    k = sg.sg_container_open(path)
+    brick_bytes = ((B + 2) ** 3 * 2 + 255) // 256 * 256
+    W, H, tau = 192, 208, 0.3
+    views, projs = _stereo((-0.3, 0.05, 0.2), (-0.1, 0.0, 0.0), W, H)
+    st_full = ovol.select([otf], views, projs, H, tau=tau)["state"]
+    need = int(np.isin(st_full, [oracle.ST_SELECTED, oracle.ST_FALLBACK, oracle.ST_REFINED]).sum())
+    # the GPU cache holds the working set; the host cache only half of it
+    vol = sg.sg_volume_create(DIMS, sg.SG_U16, B, LEVELS, device_pool_bytes=(need + 8) * brick_bytes, model=model)
+    hc = sg.sg_host_cache_create(k, max(need // 2, 48) * (B + 2) ** 3 * 2, pinned=True, threads=4)
+    try:
+        sg.sg_set_transfer_function(vol, 0, table, 300.0, 60000.0)
+        for L in range(LEVELS):
+            nbx, nby, nbz = ovol.blocks_per_axis(L)
+            xyz = np.array([(x, y, z) for z in range(nbz) for y in range(nby) for x in range(nbx)])
+            lo, hi = ovol.level_offsets[L], ovol.level_offsets[L + 1]
+            sg.sg_set_brick_ranges(vol, 0, 0, L, xyz, full[lo:hi, 0, :])
+        root = int(ovol.level_offsets[LEVELS - 1])
+        ptr, _ = sg.sg_host_cache_fetch(hc, 0, 0, root)
+        assert sg.sg_upload_brick_list(vol, 0, 0, [root], [ptr]) == 1
+        pose = sg.make_pose(views, projs, W, H, pixel_error=tau)
+        total = dict(disk_reads=0, host_hits=0, served=0)
+        for frame in range(40):
+            stats = sg.sg_select_lod(vol, pose, stats=True)
+            res = sg.sg_read_residency(vol, 0, ovol.node_count) >= 0
+            ref = ovol.select([otf], views, projs, H, tau=tau, resident=res.astype(np.uint8), ranges=full)
+            compare_selection(sg.sg_read_selection(vol, 0, len(ref["leaf"]), ovol.node_count), ref)
+            if stats["requested"] == 0:
+                break
+            st = sg.sg_stream_requests(vol, 0, hc, 24 * (B + 2) ** 3 * 2)
+            assert st["requested"] == stats["requested"] and 0 < st["served"] <= 24 and st["missing"] == 0, (
+                frame, st, stats, sg.lib.sg_last_error().decode())
+            for key in total:
+                total[key] += st[key]
+        assert stats["requested"] == 0 and stats["fallback"] == 0
+        assert total["disk_reads"] > 0 and total["served"] > 0
+        outs = [torch.empty((H, W, 4), device="cuda") for _ in range(2)]
+        sg.sg_render(vol, pose, sg.render_params(), outs)
+        torch.cuda.synchronize()
+        ref = ovol.select([otf], views, projs, H, tau=tau)
+        for e in range(2):
+            compare_image(outs[e].cpu().numpy().reshape(-1, 4), ovol.render([otf], ref["leaf"], views[e], projs[e], W, H))
+    finally:
+        sg.sg_host_cache_destroy(hc)
+        sg.sg_volume_destroy(vol)
+        sg.sg_container_close(k)
