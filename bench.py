@@ -47,6 +47,22 @@ def workload_config(extra=None):
     return c
 
 
+def rank_poses(seq, rank, world):
+    """This rank's pose order for weak scaling: rank r takes r, r + world,
+    r + 2 world, ... (cyclically), so the first k steps of all ranks render
+    k * world different poses while there are enough."""
+    return [seq[(rank + world * i) % len(seq)] for i in range(len(seq))]
+
+
+def max_over_ranks(ms, world, device):
+    """The job's time: the slowest rank's (all-reduce MAX; a no-op on one rank)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_inputs(n_vox=N_VOX):
     import synth
     vol = synth.filaments_u16((n_vox,) * 3, seed=SEEDS["volume"], ntubes=max(1, 200 * n_vox // N_VOX))
@@ -618,7 +634,7 @@ def run_ours(args, rank, world, local_rank):
     outs = [torch.empty((H_EYE, W_EYE, 4), dtype=torch.float32, device=dev) for _ in range(2)]
     total = torch.zeros(1, dtype=torch.int64, device=dev)
     pose_objs = [sg.make_pose(v, p, W_EYE, H_EYE, pixel_error=TAU, slot=0) for v, p in poses]
-    mine = [pose_objs[(rank + world * i) % NPOSES] for i in range(NPOSES)]
+    mine = rank_poses(pose_objs, rank, world)
     prm = sg.render_params(step=STEP, term_alpha=TERM, empty_skip=1, sample_total=total)
     # the project's autotuner picks tile shape / persistence on the first pose (untimed setup)
     sg.sg_select_lod(vol, mine[0], stream=stream)
@@ -657,10 +673,7 @@ def run_ours(args, rank, world, local_rank):
     render_ms = [a.elapsed_time(b) for a, b, _ in rev]
     frame_ms = np.array([c.elapsed_time(b) for _, b, c in rev])  # select + render of one pose
     samples = int(total.item())
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
 
     # algorithmic bytes of the render launches (outside the timed region):
     # distinct non-transparent selected bricks + the two output images
@@ -706,7 +719,7 @@ def run_ours(args, rank, world, local_rank):
     unwarped = [torch.empty((H_EYE, W_EYE, 4), dtype=torch.float32, device=dev) for _ in range(2)]
     prm_w = sg.render_params(step=STEP, term_alpha=TERM, empty_skip=1, lens=ln)
     wposes = [sg.make_pose(v, p, Ww, Hw, pixel_error=TAU, slot=0) for v, p in poses]
-    wmine = [wposes[(rank + world * i) % NPOSES] for i in range(NPOSES)]
+    wmine = rank_poses(wposes, rank, world)
 
     def warped_step(i):
         sg.sg_select_lod(vol, mine[i % NPOSES], stream=stream)
