@@ -470,7 +470,7 @@ def container_streaming(sg, torch, dev, n_vox=1024, brick=64, levels=4, count=12
             "disk_read_gbs": round(tot["disk_bytes"] / max(sm.sum() / 1e3, 1e-9) / 1e9, 3)}
 
 
-def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=4000, steps_per_pair=4, eval_poses=16,
+def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=20000, steps_per_pair=4, eval_poses=16,
                   threshold_db=40.0):
     """Learned reconstruction vs the plain path on the same GPU: training on
     `pairs` seeded (pose, full-rate render, half-res render) pairs of the
@@ -768,7 +768,9 @@ def run_ours(args, rank, world, local_rank):
     e2e_s = time.perf_counter() - t0
 
     batched = learned = streaming = container = None
-    if rank == 0 and not args.no_extra and n_vox == N_VOX:
+    # the single-GPU measurements run on one-GPU runs only, so a multi-GPU
+    # run does not hold every GPU while one rank works alone
+    if rank == 0 and world == 1 and not args.no_extra and n_vox == N_VOX:
         batched = batched_4d(sg, torch, dev)
         streaming = streaming_flythrough(sg, torch, dev)
         container = container_streaming(sg, torch, dev)
@@ -825,8 +827,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched 4D and learned measurements")
-    ap.add_argument("--learned-pairs", type=int, default=4000,
-                    help="training pairs for the learned path (20000 = the full budget, ~4 min)")
+    ap.add_argument("--learned-pairs", type=int, default=20000,
+                    help="training pairs for the learned path (the configuration's 20000, about 3 min)")
     ap.add_argument("--skip-block", type=int, default=0,
                     help="empty-space skipping cell edge in voxels (0 = the library's default)")
     ap.add_argument("--streaming-size", choices=["auto", "full", "scaled"], default="auto",
