@@ -280,7 +280,10 @@ template <int BN, int R, int CC>
 cudaError_t conv_halo(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
   // two stages only where two CTAs still fit on an SM
   constexpr int kOne = halo_stage_bytes<BN, R, CC>();
-  const int stages = (a.Cin / CC > 1 && 2 * kOne <= 110 * 1024) ? 2 : 1;
+#ifndef SG_HALO_STAGE2_LIMIT
+#define SG_HALO_STAGE2_LIMIT (110 * 1024)
+#endif
+  const int stages = (a.Cin / CC > 1 && 2 * kOne <= SG_HALO_STAGE2_LIMIT) ? 2 : 1;
   const int smem = stages * kOne;
   static bool configured = false;  // per template instance, set once on first use
   if (!configured) {
@@ -296,7 +299,9 @@ cudaError_t conv_halo(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
 
 template <int BN>
 cudaError_t conv_halo_cc(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
+#ifndef SG_HALO_CC16_ONLY
   if (a.Cin % 32 == 0) return conv_halo<BN, SG_HALO_ROWS, 32>(a, err, s);
+#endif
   return conv_halo<BN, SG_HALO_ROWS, 16>(a, err, s);
 }
 

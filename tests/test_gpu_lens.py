@@ -90,3 +90,28 @@ def test_lens_arguments_are_checked():
             sg.sg_unwarp(sg.make_lens(0.1, 0.0), outs, 0, 32, outs, 32, 32)
     finally:
         case.close()
+
+
+def test_odd_sizes_and_off_centre_lens():
+    """Ragged warped and output sizes, an off-centre lens with its own scale
+    and aspect: warped render and unwarp against the oracle."""
+    case = _case()
+    try:
+        sg, torch = case.sg, case.torch
+        W, H, Ww, Hw = 173, 151, 119, 107
+        pose, wpose, views, projs, ref = _poses(case, W, H, Ww, Hw, seed=3710)
+        centres = ((0.11, -0.07), (-0.09, 0.05))
+        ln = sg.make_lens(0.3, 0.1, 0.7, 1.2, centres)
+        warped = [torch.empty((Hw, Ww, 4), device="cuda") for _ in range(2)]
+        sg.sg_render(case.vol, wpose, sg.render_params(lens=ln), warped)
+        out = [torch.empty((H, W, 4), device="cuda") for _ in range(2)]
+        sg.sg_unwarp(ln, warped, Ww, Hw, out, W, H)
+        torch.cuda.synchronize()
+        for e in range(2):
+            oln = oracle.lens(0.3, 0.1, 0.7, 1.2, *centres[e])
+            got = warped[e].cpu().numpy()
+            compare_image(got.reshape(-1, 4),
+                          case.ovol.render(case.otfs, ref["leaf"], views[e], projs[e], Ww, Hw, lens=oln))
+            assert np.abs(out[e].cpu().numpy() - oracle.unwarp(oln, got, W, H)).max() < 1e-4
+    finally:
+        case.close()

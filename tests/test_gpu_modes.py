@@ -108,3 +108,45 @@ def test_depth_buffers_are_rejected_by_the_batch_entry_point():
             sg.sg_render(case.vol, pose, sg.render_params(mode=7), outs)
     finally:
         case.close()
+
+
+@pytest.mark.parametrize("mode", [oracle.MODE_EMISSION, oracle.MODE_MIP])
+def test_two_channel_u8_models_match_the_oracle(mode):
+    """Two u8 channels blended additively, ragged volume and image sizes."""
+    a = synth.gaussians_u8(80, seed=41, count=6)
+    b = synth.gaussians_u8(80, seed=42, count=5)
+    a, b = np.ascontiguousarray(a[:72, :80, :76]), np.ascontiguousarray(b[:72, :80, :76])
+    case = GpuCase([a, b], 16, 3, model=synth.volume_model(80, 0.5))
+    try:
+        case.set_tfs([synth.tf_piecewise(2011, zero_alpha_points=2, colour=(0.1, 0.9, 0.2)),
+                      synth.tf_piecewise(2012, zero_alpha_points=2, colour=(0.9, 0.1, 0.8))],
+                     [(0.0, 255.0), (0.0, 255.0)])
+        W, H = 131, 97
+        (views, projs), = synth.head_poses(1, seed=3630, extent_m=0.5, width=W, height=H)
+        pose, _, gsel, ref = case.select(views, projs, W, H, tau=0.5)
+        compare_selection(gsel, ref)
+        imgs, cnts = case.render(pose, empty_skip=0, mode=mode)
+        for e in range(2):
+            compare_image(imgs[e], case.oracle_render(ref["leaf"], views[e], projs[e], W, H, mode=mode), cnts[e])
+        skip, _ = case.render(pose, empty_skip=1, mode=mode)
+        assert np.array_equal(skip[0], imgs[0]) and np.array_equal(skip[1], imgs[1])
+    finally:
+        case.close()
+
+
+def test_degenerate_depth_values():
+    """Depth 0, negative, NaN and +inf: no surface in front of the eye means
+    an empty pixel (0, negative), NaN is ignored like +inf (no surface)."""
+    case = _case(dims=(96, 96, 96), brick=16, levels=3, ntubes=10)
+    try:
+        pose, views, projs, ref = _pose(case, W=64, H=48, seed=3640, tau=0.5)
+        full, _ = case.render(pose, empty_skip=0, counts=False)
+        for value, expect_full in [(0.0, False), (-1.0, False), (np.nan, True), (np.inf, True)]:
+            depth = [np.full((48, 64), value, np.float32)] * 2
+            imgs, _ = case.render(pose, empty_skip=0, counts=False, depth=depth)
+            if expect_full:
+                assert np.array_equal(imgs[0], full[0]) and np.array_equal(imgs[1], full[1]), value
+            else:
+                assert not imgs[0].any() and not imgs[1].any(), value
+    finally:
+        case.close()

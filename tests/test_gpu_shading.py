@@ -61,3 +61,27 @@ def test_shading_arguments_are_checked():
             sg.sg_set_channel_shading(case.vol, 0, palette=PALETTE * 2.0, near=0.0, far=1.0)
     finally:
         case.close()
+
+
+def test_single_entry_palette_and_u8_gradient():
+    """A one-entry palette paints every sample one colour; gradient input on
+    u8 data (two levels), both against the oracle."""
+    a = synth.gaussians_u8(96, seed=51, count=7)
+    case = GpuCase([a], 32, 2, model=synth.volume_model(96, 0.5))
+    try:
+        table = synth.tf_piecewise(2013, zero_alpha_points=2)
+        case.set_tfs([table], [(2.0, 40.0)])
+        pal = np.array([[0.2, 0.6, 1.0]], np.float32)
+        case.sg.sg_set_channel_shading(case.vol, 0, gradient=True, palette=pal, near=0.1, far=2.0)
+        case.otfs = [oracle.make_tf(table, 2.0, 40.0, gradient=True, palette=pal, near=0.1, far=2.0)]
+        W, H = 112, 120
+        (views, projs), = synth.head_poses(1, seed=3810, extent_m=0.5, width=W, height=H)
+        pose, _, gsel, ref = case.select(views, projs, W, H, tau=0.5)
+        compare_selection(gsel, ref)
+        imgs, cnts = case.render(pose, empty_skip=0)
+        for e in range(2):
+            compare_image(imgs[e], case.oracle_render(ref["leaf"], views[e], projs[e], W, H), cnts[e])
+        img = imgs[0][imgs[0][:, 3] > 0.05]
+        assert len(img) and np.allclose(img[:, :3] / img[:, 3:4], pal[0], atol=1e-5)
+    finally:
+        case.close()
