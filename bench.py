@@ -555,6 +555,8 @@ def run_net_only(args):
     from paper_1804_08197_b300 import sg
     torch.cuda.set_device(0)
     net = sg.sg_unet_create(2, H_EYE // 2, W_EYE // 2, seed=1)
+    if args.tensor_path >= 0:
+        sg.sg_unet_set_tensor_path(net, args.tensor_path)
     x = [torch.rand((H_EYE // 2, W_EYE // 2, 4), device="cuda") for _ in range(2)]
     o = [torch.empty((H_EYE, W_EYE, 4), device="cuda") for _ in range(2)]
     for _ in range(args.warmup):
@@ -829,6 +831,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the batched 4D and learned measurements")
     ap.add_argument("--learned-pairs", type=int, default=20000,
                     help="training pairs for the learned path (the configuration's 20000, about 3 min)")
+    ap.add_argument("--tensor-path", type=int, default=-1,
+                    help="U-Net convolution path (0 mma.sync, 1 tcgen05, 2 halo, 3 halo + TMA; -1 the default)")
     ap.add_argument("--skip-block", type=int, default=0,
                     help="empty-space skipping cell edge in voxels (0 = the library's default)")
     ap.add_argument("--streaming-size", choices=["auto", "full", "scaled"], default="auto",

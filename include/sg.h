@@ -513,7 +513,9 @@ sg_status sg_unet_backward(sg_unet* net, const float* const* target, int64_t tar
 /* Selects the tensor-core path of the convolutions (all: BF16 products, FP32
  * sums): 2 (default) = tcgen05 with TMEM accumulators, each CTA computing two
  * output rows from input row segments loaded once per 32 channels (halo
- * reuse); 1 = tcgen05 implicit GEMM gathering every tap; 0 = mma.sync. */
+ * reuse); 3 = the same with the input row segments staged by TMA tensor
+ * copies (identical results); 1 = tcgen05 implicit GEMM gathering every
+ * tap; 0 = mma.sync. */
 sg_status sg_unet_set_tensor_path(sg_unet* net, int tcgen05);
 
 /* Reports (and clears) a timed-out bounded wait in a tcgen05 convolution since

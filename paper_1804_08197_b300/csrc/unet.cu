@@ -276,7 +276,42 @@ cudaError_t conv_tc(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
 #define SG_HALO_ROWS 4
 #endif
 
-template <int BN, int R, int CC>
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); looked up once
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// Tensor map of a convolution input (NHWC BF16, in_stride channels per
+// pixel): boxes of 8 channels x 130 pixels of one row of one image.
+cudaError_t input_tensor_map(const ConvArgs& a, CUtensorMap* m) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return cudaErrorNotSupported;
+  if ((reinterpret_cast<uintptr_t>(a.in) & 15) || (a.in_stride % 8) || (a.in_off % 8)) return cudaErrorInvalidValue;
+  const cuuint64_t dims[4] = {(cuuint64_t)a.in_stride, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.N};
+  const cuuint64_t strides[3] = {(cuuint64_t)a.in_stride * 2, (cuuint64_t)a.W * a.in_stride * 2,
+                                 (cuuint64_t)a.H * a.W * a.in_stride * 2};
+  const cuuint32_t box[4] = {8, 130, 1, 1}, estr[4] = {1, 1, 1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(a.in), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int BN, int R, int CC, bool TMA = false>
 cudaError_t conv_halo(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
   // two stages only where two CTAs still fit on an SM
   constexpr int kOne = halo_stage_bytes<BN, R, CC>();
@@ -287,30 +322,42 @@ cudaError_t conv_halo(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
   const int smem = stages * kOne;
   static bool configured = false;  // per template instance, set once on first use
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_halo<BN, R, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         2 * kOne);
+    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_halo<BN, R, CC, TMA>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kOne);
     if (e != cudaSuccess) return e;
     configured = true;
   }
+  CUtensorMap tmap;
+  memset(&tmap, 0, sizeof tmap);
+  if (TMA) {
+    cudaError_t e = input_tensor_map(a, &tmap);
+    if (e != cudaSuccess) return e;
+  }
   dim3 grid((a.W + 127) / 128, a.N * ((a.H + R - 1) / R), a.Cout / BN);
-  k_conv3x3_halo<BN, R, CC><<<grid, 128, smem, s>>>(a, stages, err);
+  k_conv3x3_halo<BN, R, CC, TMA><<<grid, 128, smem, s>>>(a, stages, err, tmap);
   return cudaGetLastError();
 }
 
-template <int BN>
+template <int BN, bool TMA>
 cudaError_t conv_halo_cc(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
 #ifndef SG_HALO_CC16_ONLY
-  if (a.Cin % 32 == 0) return conv_halo<BN, SG_HALO_ROWS, 32>(a, err, s);
+  if (a.Cin % 32 == 0) return conv_halo<BN, SG_HALO_ROWS, 32, TMA>(a, err, s);
 #endif
-  return conv_halo<BN, SG_HALO_ROWS, 16>(a, err, s);
+  return conv_halo<BN, SG_HALO_ROWS, 16, TMA>(a, err, s);
 }
 
-// mode: 0 mma.sync, 1 tcgen05 implicit GEMM, 2 tcgen05 with halo reuse
+// mode: 0 mma.sync, 1 tcgen05 implicit GEMM, 2 tcgen05 with halo reuse,
+// 3 the same with the input row segments staged by TMA
 cudaError_t conv(const ConvArgs& a, cudaStream_t s, uint32_t* tc_err = nullptr, int mode = 2) {
-  if (tc_err && mode == 2 && a.Cin % 16 == 0) {
-    if (a.Cout % 64 == 0) return conv_halo_cc<64>(a, tc_err, s);
-    if (a.Cout % 32 == 0) return conv_halo_cc<32>(a, tc_err, s);
-    return conv_halo_cc<16>(a, tc_err, s);
+  if (tc_err && mode == 3 && a.Cin % 16 == 0) {
+    if (a.Cout % 64 == 0) return conv_halo_cc<64, true>(a, tc_err, s);
+    if (a.Cout % 32 == 0) return conv_halo_cc<32, true>(a, tc_err, s);
+    return conv_halo_cc<16, true>(a, tc_err, s);
+  }
+  if (tc_err && mode >= 2 && a.Cin % 16 == 0) {
+    if (a.Cout % 64 == 0) return conv_halo_cc<64, false>(a, tc_err, s);
+    if (a.Cout % 32 == 0) return conv_halo_cc<32, false>(a, tc_err, s);
+    return conv_halo_cc<16, false>(a, tc_err, s);
   }
   if (tc_err) {
     if (a.Cout % 128 == 0) return conv_tc<128>(a, tc_err, s);
@@ -723,8 +770,8 @@ sg_status sg_unet_create(int max_batch, int max_h, int max_w, uint64_t seed, sg_
 }
 
 sg_status sg_unet_set_tensor_path(sg_unet* u, int tcgen05) {
-  if (!u || tcgen05 < 0 || tcgen05 > 2) {
-    set_error("sg_unet_set_tensor_path: NULL or mode not 0/1/2");
+  if (!u || tcgen05 < 0 || tcgen05 > 3) {
+    set_error("sg_unet_set_tensor_path: NULL or mode not 0/1/2/3");
     return SG_ERR_INVALID_ARG;
   }
   u->tc = tcgen05;

@@ -12,6 +12,7 @@
 // stage's mbarrier when its MMAs are done. Every wait is bounded: on timeout
 // the CTA raises an error word and leaves (after freeing its TMEM).
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -21,7 +22,9 @@ namespace sg {
 namespace nn {
 
 constexpr int kTcBM = 128, kTcBK = 64, kTcStages = 3;
-constexpr uint32_t kTcSpinLimit = 1u << 26;
+// Bounded waits: non-blocking polls, backing off with a short sleep after
+// the first few, so the bound is also a time bound (about 1-2 s).
+constexpr uint32_t kTcSpinLimit = 1u << 24;
 
 __device__ __forceinline__ uint64_t tc_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   // start address, leading / stride byte offsets (all >> 4), descriptor
@@ -40,12 +43,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
+    if (i >= 32) __nanosleep(64);
   }
   return false;
 }
@@ -268,13 +272,22 @@ __host__ __device__ constexpr int halo_stage_bytes() {
   return (R + 2) * halo_seg_bytes<CC>() + 9 * BN * CC * 2;
 }
 
-template <int BN, int R, int CC>
-__global__ void __launch_bounds__(128) k_conv3x3_halo(ConvArgs a, int stages, uint32_t* err) {
+// TMA: the input row segments arrive as tensor copies (one per segment and
+// 8-channel group: a box of 8 channels x 130 pixels of the NHWC input, which
+// lands as that group's [pixel][16 B] plane; pixels and rows outside the
+// image read as zero), issued by one thread and completed on a per-stage
+// mbarrier; the weights still come by cp.async. Without TMA every thread
+// gathers both with cp.async.
+template <int BN, int R, int CC, bool TMA>
+__global__ void __launch_bounds__(128) k_conv3x3_halo(ConvArgs a, int stages, uint32_t* err,
+                                                     const __grid_constant__ CUtensorMap tmap) {
   constexpr int kCols = R * BN < 32 ? 32 : (R * BN <= 64 ? 64 : (R * BN <= 128 ? 128 : 256));
   constexpr int kHaloSeg = halo_seg_bytes<CC>(), KC = CC / 8;
   constexpr int kA = (R + 2) * kHaloSeg, kStage = halo_stage_bytes<BN, R, CC>();
+  constexpr uint32_t kTmaBytes = (R + 2) * KC * 130 * 16;  // bytes the copies of one chunk deliver
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ uint64_t bars[2];
+  __shared__ uint64_t tbars[2];
   __shared__ uint32_t tmem_base_s;
   __shared__ volatile int abort_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -283,10 +296,18 @@ __global__ void __launch_bounds__(128) k_conv3x3_halo(ConvArgs a, int stages, ui
   const int n = blockIdx.y / bands, y0 = (blockIdx.y % bands) * R;
   const int n0 = blockIdx.z * BN;
   const int K = 9 * a.Cin, nch = a.Cin / CC;
+  // an earlier CTA gave up on a wait: the outputs are invalid anyway, leave
+  // before allocating anything (one read, shared by the whole CTA)
+  __shared__ int skip_s;
+  if (tid == 0) skip_s = *reinterpret_cast<volatile uint32_t*>(err) != 0;
+  __syncthreads();
+  if (skip_s) return;
 
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[0])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[1])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&tbars[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&tbars[1])));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     abort_s = 0;
   }
@@ -302,8 +323,24 @@ __global__ void __launch_bounds__(128) k_conv3x3_halo(ConvArgs a, int stages, ui
 
   auto gather = [&](int ch, int st) {
     const uint32_t base = smem_u32(smem + st * kStage);
+    if (TMA) {
+      if (tid == 0) {
+        const uint32_t tb = smem_u32(&tbars[st]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(tb), "r"(kTmaBytes) : "memory");
+#pragma unroll
+        for (int seg = 0; seg < R + 2; ++seg)
+#pragma unroll
+          for (int kc = 0; kc < KC; ++kc)
+            asm volatile(
+                "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+                "[%6];\n" ::"r"(base + seg * kHaloSeg + kc * (kHaloPx * 16)),
+                "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(a.in_off + ch * CC + kc * 8), "r"(x0 - 1), "r"(y0 + seg - 1),
+                "r"(n), "r"(tb)
+                : "memory");
+      }
+    }
     // input segments: (R + 2) rows x 130 pixels x KC chunks of 8 channels
-    constexpr int kItemsA = (R + 2) * 130 * KC;
+    constexpr int kItemsA = TMA ? 0 : (R + 2) * 130 * KC;
     for (int it = tid; it < kItemsA; it += 128) {
       const int seg = it / (130 * KC), rem = it - seg * (130 * KC), px = rem / KC, kc = rem % KC;
       const int yy = y0 + seg - 1, xx = x0 + px - 1;
@@ -334,6 +371,11 @@ __global__ void __launch_bounds__(128) k_conv3x3_halo(ConvArgs a, int stages, ui
   for (int ch = 0; ch < nch; ++ch) {
     const int st = stages > 1 ? (ch & 1) : 0;
     cp_async_wait<0>();
+    if (TMA && abort_s == 0) {
+      // this chunk's tensor copies (the stage's use count gives the phase)
+      const int use = stages > 1 ? ch >> 1 : ch;
+      if (!mbar_wait(smem_u32(&tbars[st]), use & 1)) abort_s = 1;
+    }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
     const bool aborted = abort_s != 0;
