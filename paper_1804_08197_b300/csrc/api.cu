@@ -384,7 +384,7 @@ sg_status sg_volume_create(const sg_volume_desc* d, sg_volume** out) {
       (e = dalloc(&v->d_slot, tn)) != cudaSuccess || (e = dalloc(&v->d_range, tn * v->nch * 2)) != cudaSuccess ||
       (e = dalloc(&v->d_subrange, (size_t)v->pool_slots * ns3 * v->nch * 2)) != cudaSuccess ||
       (e = dalloc(&v->d_subempty, (size_t)v->pool_slots * v->sub_words)) != cudaSuccess ||
-      (e = dalloc(&v->d_subdist, (size_t)v->pool_slots * ns3)) != cudaSuccess ||
+      (e = dalloc(&v->d_subdist, (size_t)v->pool_slots * 8 * ns3)) != cudaSuccess ||
       (e = dalloc(&v->d_nodeflags, tn)) != cudaSuccess ||
       (e = dalloc(&v->d_tf_raw, (size_t)v->nch * kMaxTF * 4)) != cudaSuccess ||
       (e = dalloc(&v->d_palette, (size_t)v->nch * kMaxTF)) != cudaSuccess ||
@@ -404,7 +404,7 @@ sg_status sg_volume_create(const sg_volume_desc* d, sg_volume** out) {
       (e = cudaMemset(v->d_range, 0, tn * v->nch * 2 * sizeof(uint32_t))) != cudaSuccess ||
       (e = cudaMemset2D(v->d_range, 8, 0xff, 4, tn * v->nch)) != cudaSuccess ||
       (e = cudaMemset(v->d_subempty, 0, (size_t)v->pool_slots * v->sub_words * 8)) != cudaSuccess ||
-      (e = cudaMemset(v->d_subdist, 0, (size_t)v->pool_slots * ns3)) != cudaSuccess ||
+      (e = cudaMemset(v->d_subdist, 0, (size_t)v->pool_slots * 8 * ns3)) != cudaSuccess ||
       (e = cudaMemset(v->d_nodeflags, 0, tn)) != cudaSuccess ||
       (e = cudaMemset(v->d_tf_raw, 0, (size_t)v->nch * kMaxTF * 16)) != cudaSuccess) {
     free_volume(v);

@@ -96,7 +96,7 @@ struct sg_volume {
   uint32_t* d_range = nullptr;     // [T][nodes][nch][2]
   uint16_t* d_subrange = nullptr;  // [slots][nsub^3][nch][2]
   uint64_t* d_subempty = nullptr;  // [slots][sub_words]
-  uint8_t* d_subdist = nullptr;    // [slots][nsub^3] Chebyshev distance to a non-transparent sub-block
+  uint8_t* d_subdist = nullptr;    // [slots][8 octants][nsub^3] sub-blocks ahead that are all transparent
   uint8_t* d_nodeflags = nullptr;  // [T][nodes]
   std::vector<uint8_t> has_data;   // [T][nch]
 

@@ -77,7 +77,7 @@ struct Jobs {
 struct Args {
   const uint8_t* pool;
   size_t brick_bytes;
-  const uint8_t* subdist;   // [slot][nsub^3] distance to a non-transparent sub-block
+  const uint8_t* subdist;   // [slot][8 octants][nsub^3] transparent sub-blocks ahead
   const float4* lut;   // [nch][levels][kMaxTF]
   int nch, levels, B, nsub, sub_words, sub, sub_shift;
   int nb0[3];
@@ -362,7 +362,8 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
   float texit = -1.0f;  // unclipped exit
   uint32_t slot = 0;
   const T* brick0 = nullptr;               // the current block's brick (channel 0)
-  const uint8_t* subd = nullptr;           // its sub-block distance map
+  const uint8_t* subd = nullptr;           // its sub-block distance map for this ray's octant
+  const int oct = (d.x < 0.0f ? 1 : 0) | (d.y < 0.0f ? 2 : 0) | (d.z < 0.0f ? 4 : 0);
   const int nsub3 = a.nsub * a.nsub * a.nsub;
   float3 lo = make_float3(0.f, 0.f, 0.f);  // block origin, level-0 voxels
   float sL = 1.0f;                         // 2^-L
@@ -422,7 +423,7 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
       k = (k + kstep - 1) & ~(kstep - 1);
       slot = (e & ~kLeafNone) >> 5;
       brick0 = reinterpret_cast<const T*>(a.pool + (size_t)slot * a.nch * a.brick_bytes);
-      subd = a.subdist + (size_t)slot * nsub3;
+      subd = a.subdist + ((size_t)slot * 8 + oct) * nsub3;
       sL = __int_as_float((127 - L) << 23);
       continue;
     }
@@ -437,9 +438,9 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
       const int sid = (sz * a.nsub + sy) * a.nsub + sx;
       const int D = __ldg(subd + sid);
       if (D > 0) {
-        // every sub-block within D - 1 steps is transparent: jump to the exit
-        // of that cube (clipped to the brick); the lattice points skipped
-        // have alpha exactly 0
+        // the box of D sub-blocks ahead of this one in the ray's octant is
+        // transparent: jump to its exit through a far face (clipped to the
+        // brick); the lattice points skipped have alpha exactly 0
         const float S = u2f(a.sub << L);
         const int ex_i = d.x > 0.0f ? min(sx + D, a.nsub) : max(sx - D + 1, 0);
         const int ey_i = d.y > 0.0f ? min(sy + D, a.nsub) : max(sy - D + 1, 0);

@@ -100,16 +100,22 @@ __global__ void k_sub_empty(TFParams p, const uint16_t* __restrict__ subrange, i
   }
 }
 
-// Chebyshev (L-infinity) distance, in sub-blocks, from every sub-block of a
-// brick to the nearest non-transparent one of the same brick: 0 = not
-// transparent, D > 0 = every sub-block within D - 1 steps (26-neighbourhood)
-// is transparent, so a ray may cross that whole cube without a sample; 255 =
-// no non-transparent sub-block in the brick (the ray's jump is clipped to the
-// brick). Exact, by the separable transform: a 1-D distance along x (two
-// scans per row), then along y and z the max-plus erosion
-// g'(i) = min_j max(|i - j|, g(j)), one column per thread in registers.
+// Directional distance maps, one per octant of ray directions (signs of
+// the direction's x, y, z; a zero component counts as positive): for
+// sub-block c and octant s, D = the largest k such that the box of k
+// sub-blocks ahead of c in the octant's directions (c itself included, k
+// along each axis) holds only transparent sub-blocks, that is
+// min over non-transparent q in the octant of max_axis (q - c) s. D = 0: c is
+// not transparent; 255: nothing non-transparent ahead in this brick (the jump
+// is clipped to the brick). A ray moving into that octant from inside c stays
+// in the box until it leaves through one of its far faces, so it may cross
+// the box without a sample; ignoring what lies behind the ray gives longer
+// jumps than one symmetric distance. Exact, by the separable transform per
+// octant: a one-sided 1-D distance along x, then along y and z the one-sided
+// max-plus erosion g'(i) = min over j on the octant's side of i of
+// max(|i - j|, g(j)), one column per thread in registers.
 constexpr int kDistInf = 255;
-__device__ __forceinline__ void erode_column(uint8_t* __restrict__ base, int stride, int n) {
+__device__ __forceinline__ void erode_column(uint8_t* __restrict__ base, int stride, int n, int sgn) {
   uint8_t g[kMaxSubPerEdge];
 #pragma unroll
   for (int j = 0; j < kMaxSubPerEdge; ++j)
@@ -117,8 +123,10 @@ __device__ __forceinline__ void erode_column(uint8_t* __restrict__ base, int str
   for (int i = 0; i < n; ++i) {
     int best = kDistInf;
 #pragma unroll
-    for (int j = 0; j < kMaxSubPerEdge; ++j)
-      if (j < n) best = min(best, max(abs(i - j), (int)g[j]));
+    for (int j = 0; j < kMaxSubPerEdge; ++j) {
+      const int dj = (j - i) * sgn;
+      if (j < n && dj >= 0) best = min(best, max(dj, (int)g[j]));
+    }
     base[i * stride] = (uint8_t)best;
   }
 }
@@ -129,29 +137,30 @@ __global__ void k_sub_dist(const uint64_t* __restrict__ bits, int nsub, int word
   const int64_t slot = slot_list ? slot_list[blockIdx.x] : blockIdx.x;
   const int n = nsub, n2 = nsub * nsub, ns3 = n2 * nsub;
   const uint64_t* w = bits + slot * words;
-  // x: distance to the nearest non-transparent sub-block of the same row
-  for (int r = threadIdx.x; r < n2; r += blockDim.x) {
-    uint8_t* row = sd + r * n;
-    int last = -kDistInf;
-    for (int x = 0; x < n; ++x) {
-      const int i = r * n + x;
-      if (!((w[i >> 6] >> (i & 63)) & 1ull)) last = x;
-      row[x] = (uint8_t)min(x - last, kDistInf);
+  for (int oct = 0; oct < 8; ++oct) {
+    const int sx = (oct & 1) ? -1 : 1, sy = (oct & 2) ? -1 : 1, sz = (oct & 4) ? -1 : 1;
+    // x: distance to the nearest non-transparent sub-block ahead in the row
+    for (int r = threadIdx.x; r < n2; r += blockDim.x) {
+      uint8_t* row = sd + r * n;
+      int last = 2 * kDistInf * sx + (sx > 0 ? n : 0);
+      for (int k = 0; k < n; ++k) {
+        const int x = sx > 0 ? n - 1 - k : k;
+        const int i = r * n + x;
+        if (!((w[i >> 6] >> (i & 63)) & 1ull)) last = x;
+        row[x] = (uint8_t)min((last - x) * sx, kDistInf);
+      }
     }
-    last = kDistInf * 2;
-    for (int x = n - 1; x >= 0; --x) {
-      if (row[x] == 0) last = x;
-      row[x] = (uint8_t)min((int)row[x], min(last - x, kDistInf));
-    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n2; c += blockDim.x)  // y columns: (x, z) = (c % n, c / n)
+      erode_column(sd + (c / n) * n2 + (c % n), n, n, sy);
+    __syncthreads();
+    for (int c = threadIdx.x; c < n2; c += blockDim.x)  // z columns: (x, y) = (c % n, c / n)
+      erode_column(sd + c, n2, n, sz);
+    __syncthreads();
+    uint8_t* out = dist + (slot * 8 + oct) * ns3;
+    for (int i = threadIdx.x; i < ns3; i += blockDim.x) out[i] = sd[i];
+    __syncthreads();
   }
-  __syncthreads();
-  for (int c = threadIdx.x; c < n2; c += blockDim.x)  // y columns: (x, z) = (c % n, c / n)
-    erode_column(sd + (c / n) * n2 + (c % n), n, n);
-  __syncthreads();
-  for (int c = threadIdx.x; c < n2; c += blockDim.x)  // z columns: (x, y) = (c % n, c / n)
-    erode_column(sd + c, n2, n);
-  __syncthreads();
-  for (int i = threadIdx.x; i < ns3; i += blockDim.x) dist[slot * ns3 + i] = sd[i];
 }
 
 // Opacity correction per level: a level-L sample stands for step 2^L
