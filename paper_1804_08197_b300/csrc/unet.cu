@@ -13,6 +13,7 @@
 //   up, concat [up 64 | e1 32],  d1a 96->32,  d1b 32->32   at h x w
 //   head 32->16 (no ReLU, FP32) -> pixel shuffle -> 4 channels at 2h x 2w
 #include <math.h>
+#include <algorithm>
 #include <string.h>
 
 #include <string>
@@ -21,6 +22,7 @@
 #include "internal.h"
 #include "unet_gemm.cuh"
 #include "unet_tc.cuh"
+#include "unet_ws.cuh"
 
 using namespace sg;
 using namespace sg::nn;
@@ -296,19 +298,69 @@ EncodeTiledFn encode_tiled() {
 }
 
 // Tensor map of a convolution input (NHWC BF16, in_stride channels per
-// pixel): boxes of 8 channels x 130 pixels of one row of one image.
-cudaError_t input_tensor_map(const ConvArgs& a, CUtensorMap* m) {
+// pixel): boxes of 8 channels x 130 pixels x `rows` rows of one image.
+cudaError_t input_tensor_map(const ConvArgs& a, CUtensorMap* m, int rows = 1) {
   EncodeTiledFn fn = encode_tiled();
   if (!fn) return cudaErrorNotSupported;
   if ((reinterpret_cast<uintptr_t>(a.in) & 15) || (a.in_stride % 8) || (a.in_off % 8)) return cudaErrorInvalidValue;
   const cuuint64_t dims[4] = {(cuuint64_t)a.in_stride, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.N};
   const cuuint64_t strides[3] = {(cuuint64_t)a.in_stride * 2, (cuuint64_t)a.W * a.in_stride * 2,
                                  (cuuint64_t)a.H * a.W * a.in_stride * 2};
-  const cuuint32_t box[4] = {8, 130, 1, 1}, estr[4] = {1, 1, 1, 1};
+  const cuuint32_t box[4] = {8, 130, (cuuint32_t)rows, 1}, estr[4] = {1, 1, 1, 1};
   const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(a.in), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Tensor map of convolution weights ([Cout][9 Cin] BF16): boxes of 8 input
+// channels of one tap x bn output channels.
+cudaError_t weight_tensor_map(const ConvArgs& a, int bn, CUtensorMap* m) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return cudaErrorNotSupported;
+  if ((reinterpret_cast<uintptr_t>(a.wt) & 15) || (a.Cin % 8) || bn > 256) return cudaErrorInvalidValue;
+  const cuuint64_t dims[2] = {(cuuint64_t)9 * a.Cin, (cuuint64_t)a.Cout};
+  const cuuint64_t strides[1] = {(cuuint64_t)9 * a.Cin * 2};
+  const cuuint32_t box[2] = {8, (cuuint32_t)bn}, estr[2] = {1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(a.wt), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// streaming multiprocessors of the current device (queried once per device)
+int sm_count() {
+  static int n[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  if (!n[dev] && cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n[dev] = 0;
+  return n[dev] > 0 ? n[dev] : 1;
+}
+
+// persistent warp-specialised convolution: one CTA per SM, as many ring
+// stages as fit in about 220 KB of shared memory
+template <int BN, int R>
+cudaError_t conv_ws(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
+  constexpr int kStage = ws_stage_bytes<BN, R>();
+  const int stages = std::min(kWsMaxStages, (220 * 1024) / kStage);
+  const int smem = stages * kStage;
+  static bool configured = false;  // per template instance, set once on first use
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_ws<BN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  CUtensorMap tin, twt;
+  memset(&tin, 0, sizeof tin);
+  memset(&twt, 0, sizeof twt);
+  cudaError_t e = input_tensor_map(a, &tin, R + 2);
+  if (e == cudaSuccess) e = weight_tensor_map(a, BN, &twt);
+  if (e != cudaSuccess) return e;
+  const int64_t nt = (int64_t)a.N * ((a.H + R - 1) / R) * ((a.W + 127) / 128) * (a.Cout / BN);
+  const int grid = (int)std::min<int64_t>(nt, sm_count());
+  if (grid < 1) return cudaSuccess;
+  k_conv3x3_ws<BN, R><<<grid, 192, smem, s>>>(a, stages, err, tin, twt);
+  return cudaGetLastError();
 }
 
 template <int BN, int R, int CC, bool TMA = false>
@@ -347,8 +399,14 @@ cudaError_t conv_halo_cc(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
 }
 
 // mode: 0 mma.sync, 1 tcgen05 implicit GEMM, 2 tcgen05 with halo reuse,
-// 3 the same with the input row segments staged by TMA
+// 3 the same with the input row segments staged by TMA, 4 persistent
+// warp-specialised halo reuse (TMA ring, two TMEM accumulators)
 cudaError_t conv(const ConvArgs& a, cudaStream_t s, uint32_t* tc_err = nullptr, int mode = 2) {
+  if (tc_err && mode == 4 && a.Cin % 16 == 0 && a.Cout % 16 == 0) {
+    if (a.Cout % 64 == 0) return conv_ws<64, 4>(a, tc_err, s);
+    if (a.Cout % 32 == 0) return conv_ws<32, 8>(a, tc_err, s);
+    return conv_ws<16, 8>(a, tc_err, s);
+  }
   if (tc_err && mode == 3 && a.Cin % 16 == 0) {
     if (a.Cout % 64 == 0) return conv_halo_cc<64, true>(a, tc_err, s);
     if (a.Cout % 32 == 0) return conv_halo_cc<32, true>(a, tc_err, s);
@@ -770,8 +828,8 @@ sg_status sg_unet_create(int max_batch, int max_h, int max_w, uint64_t seed, sg_
 }
 
 sg_status sg_unet_set_tensor_path(sg_unet* u, int tcgen05) {
-  if (!u || tcgen05 < 0 || tcgen05 > 3) {
-    set_error("sg_unet_set_tensor_path: NULL or mode not 0/1/2/3");
+  if (!u || tcgen05 < 0 || tcgen05 > 4) {
+    set_error("sg_unet_set_tensor_path: NULL or mode not 0..4");
     return SG_ERR_INVALID_ARG;
   }
   u->tc = tcgen05;

@@ -1,0 +1,320 @@
+// Persistent, warp-specialised 3x3 convolution on tcgen05 (the halo-reuse
+// scheme of k_conv3x3_halo, pipelined across channel chunks and tiles).
+//
+// A tile is R output rows x 128 pixels x BN output channels of one image;
+// the grid holds one CTA per SM and each CTA walks tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... Three roles run side by side:
+//   warp 0 (one thread)   producer: per 16-channel chunk of a tile, TMA
+//                         tensor copies of the R + 2 input row segments
+//                         (130 pixels with the halo, zero outside the image)
+//                         and of the chunk's weights for all 9 taps into one
+//                         stage of a shared-memory ring;
+//   warp 1 (one thread)   MMA issuer: R x 9 tcgen05.mma (M = 128 pixels,
+//                         N = BN, K = 16) per chunk into one of two TMEM
+//                         accumulators; tcgen05.commit frees the stage and,
+//                         after a tile's last chunk, hands the accumulator to
+//   warps 2-5             epilogue: tcgen05.ld, bias, ReLU, BF16/FP32 stores,
+//                         then release the accumulator to the MMA issuer.
+// So the loads of chunk c + S - 1 overlap the MMAs of chunk c, and the
+// epilogue of one tile overlaps the MMAs of the next.
+//
+// Shared-memory stage: [2 planes of 8 channels][R + 2 rows][130 px][16 B]
+// (plane pitch rounded up to 128 B), then [9 taps][2 planes][BN rows][16 B].
+// Both operands are K-major without swizzle: A of tap (dy, dx), output row r
+// starts (r + dy + 1) rows and dx + 1 pixels into the planes (leading byte
+// offset = plane pitch, stride byte offset 128 = 8 pixels); B of a tap has
+// leading byte offset BN x 16 (next 8 channels) and stride byte offset 128.
+//
+// Every wait is bounded (about a second) and gives up early once another
+// role has given up; the CTA then drains its own copies and MMAs in flight
+// (again bounded), raises the error word and frees its TMEM.
+#pragma once
+#include <cuda.h>
+#include <stdint.h>
+
+#include "unet_tc.cuh"
+
+namespace sg {
+namespace nn {
+
+constexpr int kWsMaxStages = 6;
+constexpr int kWsRowBytes = 130 * 16;  // one row segment of 8 channels
+
+template <int R>
+__host__ __device__ constexpr int ws_plane_bytes() {
+  return ((R + 2) * kWsRowBytes + 127) / 128 * 128;
+}
+
+template <int BN, int R>
+__host__ __device__ constexpr int ws_stage_bytes() {
+  return 2 * ws_plane_bytes<R>() + 9 * 2 * BN * 16;
+}
+
+// bounded wait that also returns (false) once *abort is set
+__device__ __forceinline__ bool ws_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  for (uint32_t i = 0; i < kTcSpinLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (i >= 32) {
+      if (abort && *abort) return false;
+      __nanosleep(64);
+    }
+  }
+  return false;
+}
+
+template <int BN, int R>
+__global__ void __launch_bounds__(192, 1)
+    k_conv3x3_ws(ConvArgs a, int stages, uint32_t* err, const __grid_constant__ CUtensorMap tin,
+                 const __grid_constant__ CUtensorMap twt) {
+  constexpr int kPlane = ws_plane_bytes<R>();
+  constexpr int kA = 2 * kPlane;
+  constexpr int kTap = 2 * BN * 16;
+  constexpr int kStage = ws_stage_bytes<BN, R>();
+  constexpr uint32_t kTx = 2u * (R + 2) * kWsRowBytes + 9u * kTap;  // bytes the copies of one chunk deliver
+  constexpr int kAcc = R * BN;                                        // TMEM columns of one accumulator
+  constexpr int kCols =
+      2 * kAcc <= 32 ? 32 : (2 * kAcc <= 64 ? 64 : (2 * kAcc <= 128 ? 128 : (2 * kAcc <= 256 ? 256 : 512)));
+  static_assert(2 * kAcc <= 512, "two accumulators must fit in TMEM");
+  static_assert(BN % 16 == 0 && BN <= 256, "N of the MMA");
+  static_assert(kStage % 128 == 0 && kA % 128 == 0 && (BN * 16) % 128 == 0, "TMA destinations 128-byte aligned");
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint64_t full[kWsMaxStages], empty[kWsMaxStages], tfull[2], tempty[2], done_bar;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ volatile int abort_s;
+  __shared__ int skip_s, produced_s, consumed_s, issued_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // an earlier CTA gave up on a wait: the outputs are invalid anyway
+  if (tid == 0) skip_s = *reinterpret_cast<volatile uint32_t*>(err) != 0;
+  __syncthreads();
+  if (skip_s) return;
+
+  const int tiles_x = (a.W + 127) / 128, bands = (a.H + R - 1) / R, nz = a.Cout / BN;
+  const int nt = a.N * bands * tiles_x * nz, nch = a.Cin / 16;
+  if (tid == 0) {
+    for (int s = 0; s < stages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[s])));
+    }
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&tfull[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(smem_u32(&tempty[b])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&done_bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    abort_s = 0;
+    produced_s = consumed_s = issued_s = 0;
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base_s)),
+                 "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_base_s;
+
+  // tile t -> (image n, first row y0, first pixel x0, output-channel block z);
+  // the channel blocks of one pixel tile are neighbours (shared input in L2)
+  auto decode = [&](int t, int& n, int& y0, int& x0, int& z) {
+    z = t % nz;
+    int q = t / nz;
+    x0 = (q % tiles_x) * 128;
+    q /= tiles_x;
+    y0 = (q % bands) * R;
+    n = q / bands;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- producer
+      int f = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < nt && ok; t += gridDim.x) {
+        int n, y0, x0, z;
+        decode(t, n, y0, x0, z);
+        for (int ch = 0; ch < nch; ++ch) {
+          const int st = f % stages, use = f / stages;
+          if (use > 0 && !ws_wait(smem_u32(&empty[st]), (use - 1) & 1, &abort_s)) {
+            ok = false;
+            break;
+          }
+          const uint32_t base = smem_u32(smem + st * kStage), fb = smem_u32(&full[st]);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(kTx) : "memory");
+#pragma unroll
+          for (int kc = 0; kc < 2; ++kc)
+            asm volatile(
+                "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+                "%5}], [%6];\n" ::"r"(base + kc * kPlane),
+                "l"(reinterpret_cast<uint64_t>(&tin)), "r"(a.in_off + ch * 16 + kc * 8), "r"(x0 - 1), "r"(y0 - 1),
+                "r"(n), "r"(fb)
+                : "memory");
+#pragma unroll
+          for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+            for (int kc = 0; kc < 2; ++kc)
+              asm volatile(
+                  "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                  "[%4];\n" ::"r"(base + kA + tap * kTap + kc * (BN * 16)),
+                  "l"(reinterpret_cast<uint64_t>(&twt)), "r"(tap * a.Cin + ch * 16 + kc * 8), "r"(z * BN), "r"(fb)
+                  : "memory");
+          ++f;
+        }
+      }
+      produced_s = f;
+      if (!ok) abort_s = 1;
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      constexpr uint32_t idesc = tc_idesc(128, BN);
+      int f = 0, j = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < nt && ok; t += gridDim.x, ++j) {
+        const int b = j & 1, u = j >> 1;
+        if (u > 0 && !ws_wait(smem_u32(&tempty[b]), (u - 1) & 1, &abort_s)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        for (int ch = 0; ch < nch; ++ch) {
+          const int st = f % stages, use = f / stages;
+          if (!ws_wait(smem_u32(&full[st]), use & 1, &abort_s)) {
+            ok = false;
+            break;
+          }
+          ++f;
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint32_t base = smem_u32(smem + st * kStage);
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+              const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+              const uint64_t da = tc_smem_desc(base + (r + dy + 1) * kWsRowBytes + (dx + 1) * 16, kPlane, 128);
+              const uint64_t db = tc_smem_desc(base + kA + tap * kTap, BN * 16, 128);
+              const uint32_t accum = (ch > 0 || tap > 0) ? 1u : 0u;
+              asm volatile(
+                  "{\n\t.reg .pred p;\n\t"
+                  "setp.ne.b32 p, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + b * kAcc + r * BN),
+                  "l"(da), "l"(db), "r"(idesc), "r"(accum));
+            }
+          issued_s = 1;
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                           smem_u32(&empty[st]))
+                       : "memory");
+        }
+        if (!ok) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         smem_u32(&tfull[b]))
+                     : "memory");
+      }
+      consumed_s = f;
+      if (!ok) abort_s = 1;
+    }
+  } else {
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
+    const int eq = warp & 3;
+    int j = 0;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x, ++j) {
+      const int b = j & 1, u = j >> 1;
+      const bool ok = __all_sync(0xffffffffu, ws_wait(smem_u32(&tfull[b]), u & 1, &abort_s));
+      if (!ok) {
+        if (lane == 0) abort_s = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      int n, y0, x0, z;
+      decode(t, n, y0, x0, z);
+      const int x = x0 + eq * 32 + lane, n0 = z * BN;
+#pragma unroll 1
+      for (int r = 0; r < R; ++r) {
+        const int y = y0 + r;
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          uint32_t v32[16];
+          const uint32_t taddr = tmem + ((uint32_t)(eq * 32) << 16) + b * kAcc + r * BN + c0;
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+              : "=r"(v32[0]), "=r"(v32[1]), "=r"(v32[2]), "=r"(v32[3]), "=r"(v32[4]), "=r"(v32[5]), "=r"(v32[6]),
+                "=r"(v32[7]), "=r"(v32[8]), "=r"(v32[9]), "=r"(v32[10]), "=r"(v32[11]), "=r"(v32[12]), "=r"(v32[13]),
+                "=r"(v32[14]), "=r"(v32[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+          if (x < a.W && y < a.H) {
+            const int64_t pr = ((int64_t)n * a.H + y) * a.W + x;
+            float v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              v[i] = __uint_as_float(v32[i]);
+              if (a.bias) v[i] += __ldg(a.bias + n0 + c0 + i);
+              if (a.relu) v[i] = fmaxf(v[i], 0.f);
+            }
+            if (a.out) {
+              uint32_t packed[8];
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+                packed[i] = *reinterpret_cast<uint32_t*>(&h2);
+              }
+              uint4* o = reinterpret_cast<uint4*>(a.out + pr * a.out_stride + a.out_off + n0 + c0);
+              o[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+              o[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+            }
+            if (a.out_f32) {
+              float4* o = reinterpret_cast<float4*>(a.out_f32 + pr * a.f32_stride + a.f32_off + n0 + c0);
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                float4 q = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                if (a.f32_accumulate) {
+                  const float4 o0 = o[i];
+                  q.x += o0.x; q.y += o0.y; q.z += o0.z; q.w += o0.w;
+                }
+                o[i] = q;
+              }
+            }
+          }
+        }
+      }
+      // the accumulator is read: hand it back to the MMA issuer
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&tempty[b])) : "memory");
+    }
+  }
+  __syncthreads();
+  // after a give-up: wait (bounded) for this CTA's own copies and MMAs in flight
+  if (abort_s) {
+    if (warp == 0 && lane == 0) {
+      const int p = produced_s;
+      for (int g = consumed_s > p - stages ? consumed_s : p - stages; g < p; ++g)
+        ws_wait(smem_u32(&full[g % stages]), (g / stages) & 1, nullptr);
+    }
+    if (warp == 1 && lane == 0 && issued_s) {
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       smem_u32(&done_bar))
+                   : "memory");
+      ws_wait(smem_u32(&done_bar), 0, nullptr);
+    }
+    if (tid == 0) atomicExch(err, 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols));
+  }
+}
+
+}  // namespace nn
+}  // namespace sg

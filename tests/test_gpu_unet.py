@@ -90,7 +90,7 @@ def test_tcgen05_and_mma_sync_paths_agree():
         x = rng.uniform(0, 1, (2, 24, 140, 4))
         t = rng.uniform(0, 1, (2, 48, 280, 4))
         res = {}
-        for path in (0, 1, 2, 3):
+        for path in (0, 1, 2, 3, 4):
             sg.sg_unet_set_tensor_path(net, path)
             out, loss = _run(net, x, t)
             sg.sg_unet_check(net)
@@ -102,7 +102,7 @@ def test_tcgen05_and_mma_sync_paths_agree():
         assert res[3][1] == pytest.approx(res[2][1], rel=1e-6)
         assert np.allclose(res[3][2], res[2][2], rtol=1e-5, atol=1e-7)
         base = ou.bilinear2x(x)
-        for path in (1, 2):
+        for path in (1, 2, 4):
             r0, r1 = res[0][0] - base, res[path][0] - base
             # shared BF16 rounding points, different FP32 summation order
             assert np.linalg.norm(r1 - r0) <= 5e-3 * np.linalg.norm(r0), path
@@ -111,6 +111,43 @@ def test_tcgen05_and_mma_sync_paths_agree():
                 for sl in (ws, bs):
                     g0, g1 = res[0][2][sl], res[path][2][sl]
                     assert np.linalg.norm(g1 - g0) <= 2e-2 * np.linalg.norm(g0) + 1e-12, path
+    finally:
+        sg.sg_unet_destroy(net)
+
+
+def test_persistent_convolution_over_many_tiles():
+    """The persistent warp-specialised convolution walks several tiles per
+    CTA (two TMEM accumulators in turn, the shared-memory ring wrapping
+    within and across tiles); ragged rows and columns at every level: 404 x
+    300 per image is 51 bands of 8 rows x 3 column segments (the last 44
+    pixels wide) at full size, over 2 x 148 tiles in all. Outputs, loss and
+    gradients agree with the mma.sync path to summation order."""
+    from paper_1804_08197_b300 import sg
+    net = sg.sg_unet_create(2, 404, 300, seed=21)
+    try:
+        p = _random_params(22, sg.sg_unet_param_count(net))
+        sg.sg_unet_set_params(net, p)
+        rng = np.random.default_rng(23)
+        x = rng.uniform(0, 1, (2, 404, 300, 4))
+        t = rng.uniform(0, 1, (2, 808, 600, 4))
+        res = {}
+        for path in (0, 4, 4):
+            sg.sg_unet_set_tensor_path(net, path)
+            out, loss = _run(net, x, t)
+            sg.sg_unet_check(net)
+            g = sg.sg_unet_get_params(net, which=1).astype(np.float64)
+            if path in res:
+                # a second run on the same inputs: the same products and sums
+                assert np.array_equal(out, res[path][0])
+            res[path] = (out, loss, g)
+        base = ou.bilinear2x(x)
+        r0, r1 = res[0][0] - base, res[4][0] - base
+        assert np.linalg.norm(r1 - r0) <= 5e-3 * np.linalg.norm(r0)
+        assert res[4][1] == pytest.approx(res[0][1], rel=1e-4)
+        for ws, bs in ou.layer_slices():
+            for sl in (ws, bs):
+                g0, g1 = res[0][2][sl], res[4][2][sl]
+                assert np.linalg.norm(g1 - g0) <= 2e-2 * np.linalg.norm(g0) + 1e-12
     finally:
         sg.sg_unet_destroy(net)
 
