@@ -298,32 +298,34 @@ EncodeTiledFn encode_tiled() {
 }
 
 // Tensor map of a convolution input (NHWC BF16, in_stride channels per
-// pixel): boxes of 8 channels x 130 pixels x `rows` rows of one image.
-cudaError_t input_tensor_map(const ConvArgs& a, CUtensorMap* m, int rows = 1) {
+// pixel): boxes of cw channels x 130 pixels x `rows` rows of one image,
+// written to shared memory with the given swizzle.
+cudaError_t input_tensor_map(const ConvArgs& a, CUtensorMap* m, int rows = 1, int cw = 8,
+                             CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_NONE) {
   EncodeTiledFn fn = encode_tiled();
   if (!fn) return cudaErrorNotSupported;
   if ((reinterpret_cast<uintptr_t>(a.in) & 15) || (a.in_stride % 8) || (a.in_off % 8)) return cudaErrorInvalidValue;
   const cuuint64_t dims[4] = {(cuuint64_t)a.in_stride, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.N};
   const cuuint64_t strides[3] = {(cuuint64_t)a.in_stride * 2, (cuuint64_t)a.W * a.in_stride * 2,
                                  (cuuint64_t)a.H * a.W * a.in_stride * 2};
-  const cuuint32_t box[4] = {8, 130, (cuuint32_t)rows, 1}, estr[4] = {1, 1, 1, 1};
+  const cuuint32_t box[4] = {(cuuint32_t)cw, 130, (cuuint32_t)rows, 1}, estr[4] = {1, 1, 1, 1};
   const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(a.in), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// Tensor map of convolution weights ([Cout][9 Cin] BF16): boxes of 8 input
-// channels of one tap x bn output channels.
-cudaError_t weight_tensor_map(const ConvArgs& a, int bn, CUtensorMap* m) {
+// Tensor map of convolution weights ([Cout][9 Cin] BF16): boxes of cw input
+// channels of one tap x bn output channels, written with the given swizzle.
+cudaError_t weight_tensor_map(const ConvArgs& a, int bn, int cw, CUtensorMapSwizzle swz, CUtensorMap* m) {
   EncodeTiledFn fn = encode_tiled();
   if (!fn) return cudaErrorNotSupported;
   if ((reinterpret_cast<uintptr_t>(a.wt) & 15) || (a.Cin % 8) || bn > 256) return cudaErrorInvalidValue;
   const cuuint64_t dims[2] = {(cuuint64_t)9 * a.Cin, (cuuint64_t)a.Cout};
   const cuuint64_t strides[1] = {(cuuint64_t)9 * a.Cin * 2};
-  const cuuint32_t box[2] = {8, (cuuint32_t)bn}, estr[2] = {1, 1};
+  const cuuint32_t box[2] = {(cuuint32_t)cw, (cuuint32_t)bn}, estr[2] = {1, 1};
   const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(a.wt), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -339,27 +341,28 @@ int sm_count() {
 
 // persistent warp-specialised convolution: one CTA per SM, as many ring
 // stages as fit in about 220 KB of shared memory
-template <int BN, int R>
+template <int BN, int R, int CW>
 cudaError_t conv_ws(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
-  constexpr int kStage = ws_stage_bytes<BN, R>();
-  const int stages = std::min(kWsMaxStages, (220 * 1024) / kStage);
-  const int smem = stages * kStage;
-  static bool configured = false;  // per template instance, set once on first use
+  using S = WsShape<BN, R, CW>;
+  const int stages = std::min(kWsMaxStages, (220 * 1024 - 1024) / S::kStage);
+  const int smem = stages * S::kStage + 1024;  // + room to align the ring to 1024 bytes
+  static bool configured = false;              // per template instance, set once on first use
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_ws<BN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_ws<BN, R, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
+  const CUtensorMapSwizzle swz = CW == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
   CUtensorMap tin, twt;
   memset(&tin, 0, sizeof tin);
   memset(&twt, 0, sizeof twt);
-  cudaError_t e = input_tensor_map(a, &tin, R + 2);
-  if (e == cudaSuccess) e = weight_tensor_map(a, BN, &twt);
+  cudaError_t e = input_tensor_map(a, &tin, R + 2, CW, swz);
+  if (e == cudaSuccess) e = weight_tensor_map(a, BN, CW, swz, &twt);
   if (e != cudaSuccess) return e;
   const int64_t nt = (int64_t)a.N * ((a.H + R - 1) / R) * ((a.W + 127) / 128) * (a.Cout / BN);
   const int grid = (int)std::min<int64_t>(nt, sm_count());
   if (grid < 1) return cudaSuccess;
-  k_conv3x3_ws<BN, R><<<grid, 192, smem, s>>>(a, stages, err, tin, twt);
+  k_conv3x3_ws<BN, R, CW><<<grid, 192, smem, s>>>(a, stages, err, tin, twt);
   return cudaGetLastError();
 }
 
@@ -403,9 +406,14 @@ cudaError_t conv_halo_cc(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
 // warp-specialised halo reuse (TMA ring, two TMEM accumulators)
 cudaError_t conv(const ConvArgs& a, cudaStream_t s, uint32_t* tc_err = nullptr, int mode = 2) {
   if (tc_err && mode == 4 && a.Cin % 16 == 0 && a.Cout % 16 == 0) {
-    if (a.Cout % 64 == 0) return conv_ws<64, 4>(a, tc_err, s);
-    if (a.Cout % 32 == 0) return conv_ws<32, 8>(a, tc_err, s);
-    return conv_ws<16, 8>(a, tc_err, s);
+    if (a.Cin % 32 == 0) {
+      if (a.Cout % 64 == 0) return conv_ws<64, 4, 32>(a, tc_err, s);
+      if (a.Cout % 32 == 0) return conv_ws<32, 8, 32>(a, tc_err, s);
+      return conv_ws<16, 8, 32>(a, tc_err, s);
+    }
+    if (a.Cout % 64 == 0) return conv_ws<64, 4, 16>(a, tc_err, s);
+    if (a.Cout % 32 == 0) return conv_ws<32, 8, 16>(a, tc_err, s);
+    return conv_ws<16, 8, 16>(a, tc_err, s);
   }
   if (tc_err && mode == 3 && a.Cin % 16 == 0) {
     if (a.Cout % 64 == 0) return conv_halo_cc<64, true>(a, tc_err, s);

@@ -4,26 +4,42 @@
 // A tile is R output rows x 128 pixels x BN output channels of one image;
 // the grid holds one CTA per SM and each CTA walks tiles t = blockIdx.x,
 // blockIdx.x + gridDim.x, ... Three roles run side by side:
-//   warp 0 (one thread)   producer: per 16-channel chunk of a tile, TMA
-//                         tensor copies of the R + 2 input row segments
-//                         (130 pixels with the halo, zero outside the image)
-//                         and of the chunk's weights for all 9 taps into one
-//                         stage of a shared-memory ring;
-//   warp 1 (one thread)   MMA issuer: R x 9 tcgen05.mma (M = 128 pixels,
-//                         N = BN, K = 16) per chunk into one of two TMEM
-//                         accumulators; tcgen05.commit frees the stage and,
-//                         after a tile's last chunk, hands the accumulator to
+//   warp 0 (one thread)   producer: per CW-channel chunk of a tile, one TMA
+//                         tensor copy of the R + 2 input row segments (130
+//                         pixels with the halo, zero outside the image) and
+//                         one per tap of the chunk's weights, into one stage
+//                         of a shared-memory ring;
+//   warp 1 (one thread)   MMA issuer: 3 (R + 2) CW / 16 tcgen05.mma
+//                         (M = 128 pixels, K = 16) per chunk into one of two
+//                         TMEM accumulators; tcgen05.commit frees the stage
+//                         and, after a tile's last chunk, hands the
+//                         accumulator to
 //   warps 2-5             epilogue: tcgen05.ld, bias, ReLU, BF16/FP32 stores,
-//                         then release the accumulator to the MMA issuer.
-// So the loads of chunk c + S - 1 overlap the MMAs of chunk c, and the
-// epilogue of one tile overlaps the MMAs of the next.
+//                         zeroing of what was read (tcgen05.st), then release
+//                         of the accumulator to the MMA issuer.
+// So the loads of chunk c + 1 overlap the MMAs of chunk c, and the epilogue
+// of one tile overlaps the MMAs of the next.
 //
-// Shared-memory stage: [2 planes of 8 channels][R + 2 rows][130 px][16 B]
-// (plane pitch rounded up to 128 B), then [9 taps][2 planes][BN rows][16 B].
-// Both operands are K-major without swizzle: A of tap (dy, dx), output row r
-// starts (r + dy + 1) rows and dx + 1 pixels into the planes (leading byte
-// offset = plane pitch, stride byte offset 128 = 8 pixels); B of a tap has
-// leading byte offset BN x 16 (next 8 channels) and stride byte offset 128.
+// Copies: a pixel's CW channels are one 2 CW-byte row of the TMA box (64 B
+// for CW = 32), and the operands use the matching swizzled K-major layout
+// (64-byte swizzle for CW = 32, 32-byte for CW = 16): a TMA box row of 16
+// bytes costs about as much as one of 64, so wide rows move a chunk with a
+// quarter of the requests of one 8-channel plane per copy.
+//
+// One MMA per input row i, horizontal shift dx and 16-channel step serves
+// the (up to) three output rows that row feeds: its B operand is the
+// weights of taps dy = +1, 0, -1 side by side (N = 3 BN; 2 BN or BN at the
+// band's edge rows) and its D the accumulators of output rows i - 2, i - 1,
+// i, side by side in TMEM. So the tensor core fetches each input row segment
+// 3 times per chunk instead of 9. Such an MMA adds to rows that earlier MMAs
+// already hold and to rows not yet touched, so the accumulators start at
+// zero instead of being overwritten by a first MMA.
+//
+// Shared-memory stage (1024-byte aligned): the input [R + 2 rows][130 px]
+// [2 CW bytes], then the weights [3 dx][3 dy: +1, 0, -1][BN rows][2 CW
+// bytes], both swizzled by the TMA. A of input row i, shift dx starts
+// (130 i + dx) rows in; B of shift dx starts at its weights; both advance 32
+// bytes per 16-channel step; 8-row groups are 16 CW bytes apart.
 //
 // Every wait is bounded (about a second) and gives up early once another
 // role has given up; the CTA then drains its own copies and MMAs in flight
@@ -38,17 +54,17 @@ namespace sg {
 namespace nn {
 
 constexpr int kWsMaxStages = 6;
-constexpr int kWsRowBytes = 130 * 16;  // one row segment of 8 channels
 
-template <int R>
-__host__ __device__ constexpr int ws_plane_bytes() {
-  return ((R + 2) * kWsRowBytes + 127) / 128 * 128;
-}
-
-template <int BN, int R>
-__host__ __device__ constexpr int ws_stage_bytes() {
-  return 2 * ws_plane_bytes<R>() + 9 * 2 * BN * 16;
-}
+template <int BN, int R, int CW>
+struct WsShape {
+  static constexpr int kRowPitch = 2 * CW;                                  // bytes of one pixel's chunk
+  static constexpr int kRow = 130 * kRowPitch;                              // one input row segment
+  static constexpr int kA = ((R + 2) * kRow + 1023) / 1024 * 1024;          // input part of a stage
+  static constexpr int kBlk = BN * kRowPitch;                               // one tap's weights
+  static constexpr int kDx = 3 * kBlk;                                      // the weights of one dx
+  static constexpr int kStage = (kA + 9 * kBlk + 1023) / 1024 * 1024;
+  static constexpr uint32_t kTx = (uint32_t)((R + 2) * kRow + 9 * kBlk);  // bytes one chunk's copies deliver
+};
 
 // bounded wait that also returns (false) once *abort is set
 __device__ __forceinline__ bool ws_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
@@ -70,27 +86,48 @@ __device__ __forceinline__ bool ws_wait(uint32_t bar, uint32_t parity, volatile 
   return false;
 }
 
-template <int BN, int R>
+// zeroes 16 TMEM columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};\n" ::"r"(taddr),
+      "r"(0u)
+      : "memory");
+}
+
+// Shared-memory descriptor of a swizzled K-major operand: start address,
+// stride byte offset between 8-row groups and the swizzle mode (bits 61-63:
+// 4 = 64-byte, 6 = 32-byte); the leading byte offset is unused (one MMA's 16
+// channels lie inside one swizzled row). The swizzle follows the address
+// bits, like the TMA's, so an operand may start any number of rows into a
+// pattern with base offset 0 (a start shifted by dx pixels reads what the
+// copy wrote there; parity against the unswizzled paths checks this).
+__device__ __forceinline__ uint64_t ws_desc(uint32_t addr, uint32_t sbo, uint32_t mode) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) |
+         (1ull << 46) | ((uint64_t)mode << 61);
+}
+
+template <int BN, int R, int CW>
 __global__ void __launch_bounds__(192, 1)
     k_conv3x3_ws(ConvArgs a, int stages, uint32_t* err, const __grid_constant__ CUtensorMap tin,
                  const __grid_constant__ CUtensorMap twt) {
-  constexpr int kPlane = ws_plane_bytes<R>();
-  constexpr int kA = 2 * kPlane;
-  constexpr int kTap = 2 * BN * 16;
-  constexpr int kStage = ws_stage_bytes<BN, R>();
-  constexpr uint32_t kTx = 2u * (R + 2) * kWsRowBytes + 9u * kTap;  // bytes the copies of one chunk deliver
-  constexpr int kAcc = R * BN;                                        // TMEM columns of one accumulator
+  using S = WsShape<BN, R, CW>;
+  constexpr int kAcc = R * BN;  // TMEM columns of one accumulator
   constexpr int kCols =
       2 * kAcc <= 32 ? 32 : (2 * kAcc <= 64 ? 64 : (2 * kAcc <= 128 ? 128 : (2 * kAcc <= 256 ? 256 : 512)));
+  constexpr uint32_t kMode = CW == 32 ? 4u : 6u;  // 64-byte / 32-byte swizzle
+  constexpr uint32_t kSbo = 8 * S::kRowPitch;
   static_assert(2 * kAcc <= 512, "two accumulators must fit in TMEM");
-  static_assert(BN % 16 == 0 && BN <= 256, "N of the MMA");
-  static_assert(kStage % 128 == 0 && kA % 128 == 0 && (BN * 16) % 128 == 0, "TMA destinations 128-byte aligned");
-  extern __shared__ __align__(1024) uint8_t smem[];
+  static_assert(BN % 16 == 0 && 3 * BN <= 256 && R >= 2, "N of the MMA, rows per tile");
+  static_assert(CW == 16 || CW == 32, "chunk width");
+  static_assert(S::kBlk % 512 == 0, "weight blocks aligned to the swizzle pattern");
+  extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t full[kWsMaxStages], empty[kWsMaxStages], tfull[2], tempty[2], done_bar;
   __shared__ uint32_t tmem_base_s;
   __shared__ volatile int abort_s;
   __shared__ int skip_s, produced_s, consumed_s, issued_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // the swizzle patterns repeat every 256 / 512 bytes: stages start on 1024
+  const uint32_t smem0 = (smem_u32(smem_raw) + 1023u) & ~1023u;
 
   // an earlier CTA gave up on a wait: the outputs are invalid anyway
   if (tid == 0) skip_s = *reinterpret_cast<volatile uint32_t*>(err) != 0;
@@ -98,7 +135,7 @@ __global__ void __launch_bounds__(192, 1)
   if (skip_s) return;
 
   const int tiles_x = (a.W + 127) / 128, bands = (a.H + R - 1) / R, nz = a.Cout / BN;
-  const int nt = a.N * bands * tiles_x * nz, nch = a.Cin / 16;
+  const int nt = a.N * bands * tiles_x * nz, nch = a.Cin / CW;
   if (tid == 0) {
     for (int s = 0; s < stages; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[s])));
@@ -148,25 +185,21 @@ __global__ void __launch_bounds__(192, 1)
             ok = false;
             break;
           }
-          const uint32_t base = smem_u32(smem + st * kStage), fb = smem_u32(&full[st]);
-          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(kTx) : "memory");
-#pragma unroll
-          for (int kc = 0; kc < 2; ++kc)
-            asm volatile(
-                "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-                "%5}], [%6];\n" ::"r"(base + kc * kPlane),
-                "l"(reinterpret_cast<uint64_t>(&tin)), "r"(a.in_off + ch * 16 + kc * 8), "r"(x0 - 1), "r"(y0 - 1),
-                "r"(n), "r"(fb)
-                : "memory");
+          const uint32_t base = smem0 + st * S::kStage, fb = smem_u32(&full[st]);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(S::kTx) : "memory");
+          asm volatile(
+              "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+              "%5}], [%6];\n" ::"r"(base),
+              "l"(reinterpret_cast<uint64_t>(&tin)), "r"(a.in_off + ch * CW), "r"(x0 - 1), "r"(y0 - 1), "r"(n),
+              "r"(fb)
+              : "memory");
 #pragma unroll
           for (int tap = 0; tap < 9; ++tap)
-#pragma unroll
-            for (int kc = 0; kc < 2; ++kc)
-              asm volatile(
-                  "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-                  "[%4];\n" ::"r"(base + kA + tap * kTap + kc * (BN * 16)),
-                  "l"(reinterpret_cast<uint64_t>(&twt)), "r"(tap * a.Cin + ch * 16 + kc * 8), "r"(z * BN), "r"(fb)
-                  : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                "[%4];\n" ::"r"(base + S::kA + (tap % 3) * S::kDx + (2 - tap / 3) * S::kBlk),
+                "l"(reinterpret_cast<uint64_t>(&twt)), "r"(tap * a.Cin + ch * CW), "r"(z * BN), "r"(fb)
+                : "memory");
           ++f;
         }
       }
@@ -176,12 +209,13 @@ __global__ void __launch_bounds__(192, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer
-      constexpr uint32_t idesc = tc_idesc(128, BN);
+      constexpr uint32_t id1 = tc_idesc(128, BN), id2 = tc_idesc(128, 2 * BN), id3 = tc_idesc(128, 3 * BN);
       int f = 0, j = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < nt && ok; t += gridDim.x, ++j) {
         const int b = j & 1, u = j >> 1;
-        if (u > 0 && !ws_wait(smem_u32(&tempty[b]), (u - 1) & 1, &abort_s)) {
+        // phase u of tempty[b]: the accumulator is zero (set up, or read and cleared)
+        if (!ws_wait(smem_u32(&tempty[b]), u & 1, &abort_s)) {
           ok = false;
           break;
         }
@@ -194,21 +228,27 @@ __global__ void __launch_bounds__(192, 1)
           }
           ++f;
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-          const uint32_t base = smem_u32(smem + st * kStage);
+          const uint32_t base = smem0 + st * S::kStage;
 #pragma unroll
-          for (int r = 0; r < R; ++r)
+          for (int i = 0; i < R + 2; ++i) {
+            // output rows r_lo .. r_hi take input row i (through dy = i - 1 - r)
+            const int r_lo = i - 2 > 0 ? i - 2 : 0, r_hi = i < R - 1 ? i : R - 1;
+            const int nb = r_hi - r_lo + 1, blk0 = r_lo - i + 2;
+            const uint32_t idesc = nb == 1 ? id1 : (nb == 2 ? id2 : id3);
 #pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-              const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-              const uint64_t da = tc_smem_desc(base + (r + dy + 1) * kWsRowBytes + (dx + 1) * 16, kPlane, 128);
-              const uint64_t db = tc_smem_desc(base + kA + tap * kTap, BN * 16, 128);
-              const uint32_t accum = (ch > 0 || tap > 0) ? 1u : 0u;
-              asm volatile(
-                  "{\n\t.reg .pred p;\n\t"
-                  "setp.ne.b32 p, %4, 0;\n\t"
-                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + b * kAcc + r * BN),
-                  "l"(da), "l"(db), "r"(idesc), "r"(accum));
-            }
+            for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+              for (int kk = 0; kk < CW / 16; ++kk) {
+                const uint32_t aaddr = base + (i * 130 + dx) * S::kRowPitch + kk * 32;
+                const uint64_t da = ws_desc(aaddr, kSbo, kMode);
+                const uint64_t db = ws_desc(base + S::kA + dx * S::kDx + blk0 * S::kBlk + kk * 32, kSbo, kMode);
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + b * kAcc + r_lo * BN),
+                    "l"(da), "l"(db), "r"(idesc), "r"(1u));
+              }
+          }
           issued_s = 1;
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                            smem_u32(&empty[st]))
@@ -225,6 +265,17 @@ __global__ void __launch_bounds__(192, 1)
   } else {
     // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
     const int eq = warp & 3;
+    const uint32_t lane_base = tmem + ((uint32_t)(eq * 32) << 16);
+    // both accumulators start at zero (phase 0 of tempty)
+#pragma unroll 1
+    for (int c = 0; c < 2 * kAcc; c += 16) tmem_zero16(lane_base + c);
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncwarp();
+    if (lane == 0) {
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&tempty[0])) : "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&tempty[1])) : "memory");
+    }
     int j = 0;
     for (int t = blockIdx.x; t < nt; t += gridDim.x, ++j) {
       const int b = j & 1, u = j >> 1;
@@ -243,7 +294,7 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
         for (int c0 = 0; c0 < BN; c0 += 16) {
           uint32_t v32[16];
-          const uint32_t taddr = tmem + ((uint32_t)(eq * 32) << 16) + b * kAcc + r * BN + c0;
+          const uint32_t taddr = lane_base + b * kAcc + r * BN + c0;
           asm volatile(
               "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
               : "=r"(v32[0]), "=r"(v32[1]), "=r"(v32[2]), "=r"(v32[3]), "=r"(v32[4]), "=r"(v32[5]), "=r"(v32[6]),
@@ -251,6 +302,7 @@ __global__ void __launch_bounds__(192, 1)
                 "=r"(v32[14]), "=r"(v32[15])
               : "r"(taddr));
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+          tmem_zero16(taddr);  // ready for the tile after next
           if (x < a.W && y < a.H) {
             const int64_t pr = ((int64_t)n * a.H + y) * a.W + x;
             float v[16];
@@ -286,7 +338,8 @@ __global__ void __launch_bounds__(192, 1)
           }
         }
       }
-      // the accumulator is read: hand it back to the MMA issuer
+      // the accumulator is read and zero again: hand it back to the MMA issuer
+      asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&tempty[b])) : "memory");
