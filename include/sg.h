@@ -511,13 +511,13 @@ sg_status sg_unet_backward(sg_unet* net, const float* const* target, int64_t tar
                            int64_t out_pitch, float* loss, void* stream);
 
 /* Selects the tensor-core path of the convolutions (all: BF16 products, FP32
- * sums): 2 (default) = tcgen05 with TMEM accumulators, each CTA computing two
- * output rows from input row segments loaded once per 32 channels (halo
- * reuse); 3 = the same with the input row segments staged by TMA tensor
- * copies (identical results); 4 = persistent warp-specialised halo reuse:
+ * sums): 2 = tcgen05 with TMEM accumulators, each CTA computing four output
+ * rows from input row segments loaded once per 32 channels (halo reuse); 3 = the same with the input row segments staged by TMA tensor
+ * copies (identical results); 4 (default) = persistent warp-specialised halo reuse:
  * one CTA per SM walking tiles, a TMA producer, one MMA-issuing thread and
- * four epilogue warps, a ring of 16-channel stages and two TMEM
- * accumulators, so loads, MMAs and stores of successive tiles overlap;
+ * eight epilogue warps, a ring of 32-channel stages (16 for 16-channel
+ * inputs) copied as swizzled 64-byte pixel rows, and two TMEM accumulators,
+ * so loads, MMAs and stores of successive tiles overlap;
  * 1 = tcgen05 implicit GEMM gathering every tap; 0 = mma.sync. */
 sg_status sg_unet_set_tensor_path(sg_unet* net, int tcgen05);
 

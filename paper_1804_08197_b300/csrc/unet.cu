@@ -206,7 +206,7 @@ cudaError_t pool_bwd(const float* src, int sstride, float* dst, int dstride, int
 
 struct sg_unet {
   int max_n = 0, max_h = 0, max_w = 0;
-  int tc = 2;                 // convolutions: 2 tcgen05 halo reuse, 1 tcgen05 implicit GEMM, 0 mma.sync
+  int tc = 4;                 // convolutions: 4 persistent tcgen05, 3/2 tcgen05 halo reuse, 1 implicit GEMM, 0 mma.sync
   uint32_t* d_err = nullptr;  // set by a tcgen05 kernel whose bounded wait gave up
   int n = 0, h = 0, w = 0;  // shape of the last forward
   int64_t nparam = 0;
@@ -362,7 +362,7 @@ cudaError_t conv_ws(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
   const int64_t nt = (int64_t)a.N * ((a.H + R - 1) / R) * ((a.W + 127) / 128) * (a.Cout / BN);
   const int grid = (int)std::min<int64_t>(nt, sm_count());
   if (grid < 1) return cudaSuccess;
-  k_conv3x3_ws<BN, R, CW><<<grid, 192, smem, s>>>(a, stages, err, tin, twt);
+  k_conv3x3_ws<BN, R, CW><<<grid, kWsThreads, smem, s>>>(a, stages, err, tin, twt);
   return cudaGetLastError();
 }
 

@@ -14,9 +14,11 @@
 //                         TMEM accumulators; tcgen05.commit frees the stage
 //                         and, after a tile's last chunk, hands the
 //                         accumulator to
-//   warps 2-5             epilogue: tcgen05.ld, bias, ReLU, BF16/FP32 stores,
+//   warps 2-9             epilogue: tcgen05.ld, bias, ReLU, BF16/FP32 stores,
 //                         zeroing of what was read (tcgen05.st), then release
-//                         of the accumulator to the MMA issuer.
+//                         of the accumulator to the MMA issuer; two warps per
+//                         TMEM lane quarter (32 pixels), each taking every
+//                         other output row.
 // So the loads of chunk c + 1 overlap the MMAs of chunk c, and the epilogue
 // of one tile overlaps the MMAs of the next.
 //
@@ -54,6 +56,7 @@ namespace sg {
 namespace nn {
 
 constexpr int kWsMaxStages = 6;
+constexpr int kWsThreads = 320;  // producer warp, MMA warp, 8 epilogue warps
 
 template <int BN, int R, int CW>
 struct WsShape {
@@ -107,7 +110,7 @@ __device__ __forceinline__ uint64_t ws_desc(uint32_t addr, uint32_t sbo, uint32_
 }
 
 template <int BN, int R, int CW>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kWsThreads, 1)
     k_conv3x3_ws(ConvArgs a, int stages, uint32_t* err, const __grid_constant__ CUtensorMap tin,
                  const __grid_constant__ CUtensorMap twt) {
   using S = WsShape<BN, R, CW>;
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int b = 0; b < 2; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&tfull[b])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(smem_u32(&tempty[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;\n" ::"r"(smem_u32(&tempty[b])));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&done_bar)));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -263,12 +266,16 @@ __global__ void __launch_bounds__(192, 1)
       if (!ok) abort_s = 1;
     }
   } else {
-    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
-    const int eq = warp & 3;
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, rows eh, eh + 2, ...
+    const int eq = warp & 3, eh = (warp - 2) >> 2;
     const uint32_t lane_base = tmem + ((uint32_t)(eq * 32) << 16);
     // both accumulators start at zero (phase 0 of tempty)
 #pragma unroll 1
-    for (int c = 0; c < 2 * kAcc; c += 16) tmem_zero16(lane_base + c);
+    for (int bb = 0; bb < 2; ++bb)
+#pragma unroll 1
+      for (int r = eh; r < R; r += 2)
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 16) tmem_zero16(lane_base + bb * kAcc + r * BN + c0);
     asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncwarp();
@@ -288,11 +295,14 @@ __global__ void __launch_bounds__(192, 1)
       int n, y0, x0, z;
       decode(t, n, y0, x0, z);
       const int x = x0 + eq * 32 + lane, n0 = z * BN;
-#pragma unroll 1
-      for (int r = 0; r < R; ++r) {
-        const int y = y0 + r;
 #pragma unroll
-        for (int c0 = 0; c0 < BN; c0 += 16) {
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float bias[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) bias[i] = a.bias ? __ldg(a.bias + n0 + c0 + i) : 0.f;
+#pragma unroll 1
+        for (int r = eh; r < R; r += 2) {
+          const int y = y0 + r;
           uint32_t v32[16];
           const uint32_t taddr = lane_base + b * kAcc + r * BN + c0;
           asm volatile(
@@ -308,8 +318,7 @@ __global__ void __launch_bounds__(192, 1)
             float v[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-              v[i] = __uint_as_float(v32[i]);
-              if (a.bias) v[i] += __ldg(a.bias + n0 + c0 + i);
+              v[i] = __uint_as_float(v32[i]) + bias[i];
               if (a.relu) v[i] = fmaxf(v[i], 0.f);
             }
             if (a.out) {
