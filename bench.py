@@ -505,6 +505,8 @@ def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=20000, steps_per_p
     train_s = time.perf_counter() - t0
     sg.sg_unet_check(rec.net)
     rec.vol = vol2
+    # launch shapes of both render rates tuned on a pose outside the evaluation set
+    rec.tune(*synth.head_poses(1, seed=9400, width=W_EYE, height=H_EYE)[0], stream=stream)
     for v, p in held[:2]:  # warm-up
         rec.evaluate(v, p)
     ev_ = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -546,6 +548,7 @@ def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=20000, steps_per_p
             "net_ms": round(float(np.mean(t_net)), 3),
             "net_tflops": round(net_flop / (float(np.mean(t_net)) / 1e3) / 1e12, 1),
             "half_render_ms": round(float(np.mean(np.array(t_learned) - np.array(t_net))), 3),
+            "render_config": {"full": rec.cfg_full, "half": rec.cfg_half},
             "train_s": round(train_s, 1), "train_pairs": pairs, "steps_per_pair": steps_per_pair}
 
 
@@ -572,6 +575,29 @@ def run_net_only(args):
     ms = a.elapsed_time(b) / args.steps
     print(json.dumps({"net_forward_ms": round(ms, 4), "tflops": round(268e9 / (ms / 1e3) / 1e12, 1)}), flush=True)
     sg.sg_unet_destroy(net)
+
+
+def run_learned_only(args):
+    """The learned-reconstruction measurement alone (training + held-out
+    evaluation), on the bench volume with its autotuned launch shape."""
+    import torch
+    from paper_1804_08197_b300 import sg
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    vol_host, tf_table, poses, model = make_inputs(args.volume)
+    vol = sg.sg_volume_create((args.volume,) * 3, sg.SG_U16, BRICK, LEVELS, model=model)
+    d0 = torch.from_numpy(vol_host.view(np.int16)).to(dev)
+    sg.sg_upload_volume_device(vol, 0, 0, d0.data_ptr())
+    torch.cuda.synchronize()
+    del d0
+    sg.sg_set_transfer_function(vol, 0, tf_table, *WINDOW)
+    stream = torch.cuda.current_stream()
+    outs = [torch.empty((H_EYE, W_EYE, 4), dtype=torch.float32, device=dev) for _ in range(2)]
+    p0 = sg.make_pose(*poses[0], W_EYE, H_EYE, pixel_error=TAU, slot=0)
+    sg.sg_select_lod(vol, p0, stream=stream)
+    sg.sg_autotune_render(vol, [p0], sg.render_params(step=STEP), outs, reps=3, stream=stream)
+    print(json.dumps(learned_recon(sg, torch, dev, vol, tf_table, model, pairs=args.learned_pairs)), flush=True)
+    sg.sg_volume_destroy(vol)
 
 
 def run_reference(args, rank, world):
@@ -837,7 +863,7 @@ def main():
                     help="empty-space skipping cell edge in voxels (0 = the library's default)")
     ap.add_argument("--streaming-size", choices=["auto", "full", "scaled"], default="auto",
                     help="large-volume fly-through at 4096^3 (full), at 1024^3 (scaled), or full when it fits")
-    ap.add_argument("--only", choices=["net", "streaming", "container"], default=None,
+    ap.add_argument("--only", choices=["net", "learned", "streaming", "container"], default=None,
                     help="net: only U-Net forwards at 2x720x800 (a small case for profiling the convolutions); "
                          "streaming: only the large-volume fly-through")
     ap.add_argument("--volume", type=int, default=N_VOX, help="volume edge (default 1024; smaller for profiling)")
@@ -856,6 +882,8 @@ def main():
         dist.init_process_group(backend)
     if args.only == "net":
         run_net_only(args)
+    elif args.only == "learned":
+        run_learned_only(args)
     elif args.only == "streaming":
         import torch
         from paper_1804_08197_b300 import sg

@@ -37,6 +37,9 @@ class Learned:
         self.loss = torch.zeros(1, dtype=f32, device=dev)
         self.psnr_buf = torch.zeros(2, dtype=f32, device=dev)
         self.rng = np.random.default_rng(seed)
+        # launch shapes (sg_render_config dicts) for full- and half-rate renders;
+        # None keeps the volume's own
+        self.cfg_full = self.cfg_half = None
 
     def close(self):
         sg.sg_unet_destroy(self.net)
@@ -53,12 +56,28 @@ class Learned:
     def render_full(self, views, projs, outs=None, stream=None):
         p = self.pose_full(views, projs)
         sg.sg_select_lod(self.vol, p, stream=stream)
+        if self.cfg_full is not None:
+            sg.sg_set_render_config(self.vol, **self.cfg_full)
         sg.sg_render(self.vol, p, sg.render_params(step=self.step), outs or self.full, stream=stream)
 
     def render_half(self, views, projs, stream=None):
         p = self.pose_half(views, projs)
         sg.sg_select_lod(self.vol, p, stream=stream)
+        if self.cfg_half is not None:
+            sg.sg_set_render_config(self.vol, **self.cfg_half)
         sg.sg_render(self.vol, p, sg.render_params(step=2 * self.step), self.half, stream=stream)
+
+    def tune(self, views, projs, stream=None):
+        """Autotunes the launch shape of the full- and the half-rate render on
+        one pose of the current volume (outputs overwritten)."""
+        p = self.pose_full(views, projs)
+        sg.sg_select_lod(self.vol, p, stream=stream)
+        self.cfg_full, _ = sg.sg_autotune_render(self.vol, [p], sg.render_params(step=self.step), self.full,
+                                                 reps=2, stream=stream)
+        p = self.pose_half(views, projs)
+        sg.sg_select_lod(self.vol, p, stream=stream)
+        self.cfg_half, _ = sg.sg_autotune_render(self.vol, [p], sg.render_params(step=2 * self.step), self.half,
+                                                 reps=2, stream=stream)
 
     # ------------------------------------------------------------------ training
     def _crops(self, n):
