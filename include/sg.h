@@ -427,6 +427,21 @@ sg_status sg_render(sg_volume* vol, const sg_pose* pose, const sg_render_params*
 sg_status sg_render_host(sg_volume* vol, const sg_pose* pose, const sg_render_params* params,
                          float* host_rgba[2], void* stream);
 
+/* Pipelined sg_render_host for a stream of frames: renders on `stream` into
+ * one of two library-owned device staging pairs (alternating per call), then
+ * copies both images to the caller's HOST buffers on a library-owned copy
+ * stream, and returns without waiting. So the copy of one frame overlaps
+ * the selection and render of the next. A render waits on the GPU (not the
+ * host) until the pair it reuses, two calls back, has been copied out. The
+ * images of a call are complete once sg_render_host_wait has covered it:
+ * all = 0 waits for the older of the (at most two) frames in flight, all != 0
+ * for both. Host buffers must stay valid and unread until then; pinned
+ * memory is needed for the copies to run asynchronously. Errors: as
+ * sg_render_host. */
+sg_status sg_render_host_async(sg_volume* vol, const sg_pose* pose, const sg_render_params* params,
+                               float* host_rgba[2], void* stream);
+sg_status sg_render_host_wait(sg_volume* vol, int all);
+
 /* Renders n selected poses (2n images of possibly different sizes) in one
  * persistent launch over a queue of ray tiles ("3D Movies": time points;
  * several viewers). outs[2i + e] is pose i's eye e (device, W*H*4 floats). */

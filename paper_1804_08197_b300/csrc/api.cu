@@ -82,6 +82,12 @@ void free_volume(sg_volume* v) {
   cudaFree(v->d_palette);
   cudaFree(v->d_lut);
   cudaFree(v->d_stage);
+  cudaFree(v->d_pipe);
+  for (int k = 0; k < 2; ++k) {
+    if (v->ev_rendered[k]) cudaEventDestroy(v->ev_rendered[k]);
+    if (v->ev_copied[k]) cudaEventDestroy(v->ev_copied[k]);
+  }
+  if (v->copy_stream) cudaStreamDestroy(v->copy_stream);
   cudaFree(v->d_err);
   cudaFree(v->d_stamp);
   if (v->ev_select) cudaEventDestroy(v->ev_select);
@@ -730,6 +736,63 @@ sg_status sg_render_host(sg_volume* v, const sg_pose* p, const sg_render_params*
   SG_CUDA(cudaMemcpyAsync(host_rgba[0], dev[0], per, cudaMemcpyDeviceToHost, s), "image download");
   SG_CUDA(cudaMemcpyAsync(host_rgba[1], dev[1], per, cudaMemcpyDeviceToHost, s), "image download");
   SG_CUDA(cudaStreamSynchronize(s), "image download");
+  return SG_OK;
+}
+
+sg_status sg_render_host_wait(sg_volume* v, int all) {
+  SG_CHECK_ARG(v, "volume NULL");
+  // pipe_next is the pair of the older frame in flight
+  const int order[2] = {v->pipe_next, v->pipe_next ^ 1};
+  for (int i = 0; i < (all ? 2 : 1); ++i) {
+    const int k = order[i];
+    if (!v->copy_pending[k]) continue;
+    SG_CUDA(cudaEventSynchronize(v->ev_copied[k]), "image download");
+    v->copy_pending[k] = false;
+  }
+  return SG_OK;
+}
+
+sg_status sg_render_host_async(sg_volume* v, const sg_pose* p, const sg_render_params* prm, float* host_rgba[2],
+                               void* stream) {
+  SG_CHECK_ARG(v && host_rgba && host_rgba[0] && host_rgba[1], "volume or outputs NULL");
+  sg_status st = check_pose(v, p);
+  if (st != SG_OK) return st;
+  const size_t per = (size_t)p->width * p->height * 4 * sizeof(float);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!v->copy_stream) {
+    SG_CUDA(cudaStreamCreateWithFlags(&v->copy_stream, cudaStreamNonBlocking), "copy stream");
+    for (int k = 0; k < 2; ++k) {
+      SG_CUDA(cudaEventCreateWithFlags(&v->ev_rendered[k], cudaEventDisableTiming), "pipeline events");
+      SG_CUDA(cudaEventCreateWithFlags(&v->ev_copied[k], cudaEventDisableTiming), "pipeline events");
+    }
+  }
+  if (v->pipe_bytes < 2 * per) {
+    // larger images: the copies in flight still read the old staging
+    if ((st = sg_render_host_wait(v, 1)) != SG_OK) return st;
+    cudaFree(v->d_pipe);
+    v->d_pipe = nullptr;
+    v->pipe_bytes = 0;
+    cudaError_t e = cudaMalloc(&v->d_pipe, 4 * per);
+    if (e != cudaSuccess) {
+      set_error(std::string("staging allocation: ") + cudaGetErrorString(e));
+      return SG_ERR_OOM;
+    }
+    v->pipe_bytes = 2 * per;
+  }
+  const int k = v->pipe_next;
+  float* dev[2] = {reinterpret_cast<float*>(v->d_pipe + k * v->pipe_bytes),
+                   reinterpret_cast<float*>(v->d_pipe + k * v->pipe_bytes + per)};
+  // the pair's previous frame must be copied out before this render overwrites it
+  if (v->copy_pending[k]) SG_CUDA(cudaStreamWaitEvent(s, v->ev_copied[k], 0), "pipeline order");
+  st = sg_render(v, p, prm, dev, stream);
+  if (st != SG_OK) return st;
+  SG_CUDA(cudaEventRecord(v->ev_rendered[k], s), "pipeline order");
+  SG_CUDA(cudaStreamWaitEvent(v->copy_stream, v->ev_rendered[k], 0), "pipeline order");
+  SG_CUDA(cudaMemcpyAsync(host_rgba[0], dev[0], per, cudaMemcpyDeviceToHost, v->copy_stream), "image download");
+  SG_CUDA(cudaMemcpyAsync(host_rgba[1], dev[1], per, cudaMemcpyDeviceToHost, v->copy_stream), "image download");
+  SG_CUDA(cudaEventRecord(v->ev_copied[k], v->copy_stream), "pipeline order");
+  v->copy_pending[k] = true;
+  v->pipe_next = k ^ 1;
   return SG_OK;
 }
 

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_OOM", 3: "SG_ERR
 
 EXPORTS = ["sg_volume_create", "sg_volume_destroy", "sg_upload_volume_device", "sg_upload_bricks",
            "sg_set_transfer_function", "sg_select_lod", "sg_select_lod_batch", "sg_read_selection", "sg_read_brick",
-           "sg_render", "sg_render_host", "sg_render_batch", "sg_set_render_config", "sg_get_render_config",
+           "sg_render", "sg_render_host", "sg_render_host_async", "sg_render_host_wait", "sg_render_batch", "sg_set_render_config", "sg_get_render_config",
            "sg_autotune_render", "sg_select_lod_noalloc", "sg_read_residency", "sg_set_brick_ranges", "sg_unet_create", "sg_unet_destroy",
            "sg_unet_param_count", "sg_unet_get_params", "sg_unet_set_params", "sg_unet_forward", "sg_unet_backward",
            "sg_unet_adam_step", "sg_unet_set_tensor_path", "sg_unet_check", "sg_psnr", "sg_read_ranges", "sg_upload_brick_list", "sg_unwarp", "sg_set_channel_shading",
@@ -145,6 +145,8 @@ def _load():
         "sg_unet_check": [vp],
         "sg_render": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
         "sg_render_host": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
+        "sg_render_host_async": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
+        "sg_render_host_wait": [vp, i32],
         "sg_render_batch": [vp, P(sg_pose), i32, P(sg_render_params), P(vp), vp],
         "sg_select_lod_noalloc": [vp, P(sg_pose), vp, vp, vp, vp, vp, vp],
         "sg_set_render_config": [vp, P(sg_render_config)],
@@ -400,6 +402,16 @@ def sg_render(vol, pose, params, outs, stream=None):
 def sg_render_host(vol, pose, params, host_outs, stream=None):
     arr = (ctypes.c_void_p * 2)(_ptr(host_outs[0]).value, _ptr(host_outs[1]).value)
     _check(lib.sg_render_host(vol, ctypes.byref(pose), ctypes.byref(params), arr, _stream(stream)))
+
+
+def sg_render_host_async(vol, pose, params, host_outs, stream=None):
+    """Pipelined host render (see include/sg.h): returns before the images land."""
+    arr = (ctypes.c_void_p * 2)(_ptr(host_outs[0]).value, _ptr(host_outs[1]).value)
+    _check(lib.sg_render_host_async(vol, ctypes.byref(pose), ctypes.byref(params), arr, _stream(stream)))
+
+
+def sg_render_host_wait(vol, all=True):
+    _check(lib.sg_render_host_wait(vol, 1 if all else 0))
 
 
 def sg_render_batch(vol, poses, params, outs, stream=None):

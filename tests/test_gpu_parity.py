@@ -192,6 +192,44 @@ def test_render_host_matches_device_render():
         case.close()
 
 
+def test_pipelined_host_render_matches_device_render():
+    """sg_render_host_async keeps two frames in flight (each frame's copy to
+    host overlaps the next frame's selection and render); every frame's host
+    images equal the device render of its pose, across staging growth (a
+    larger image size midway) and the reuse of both staging pairs."""
+    import torch
+    from paper_1804_08197_b300 import sg
+    case = _c1_case()
+    try:
+        sizes = [(96, 80)] * 3 + [(128, 112)] * 3
+        frames = []
+        for i, (w, h) in enumerate(sizes):
+            view, proj = synth.orbit_camera(128, seed=3100 + i, width=w, height=h)
+            frames.append(([view, view], [proj, proj], w, h))
+        refs = []
+        for views, projs, w, h in frames:
+            pose, _, _, _ = case.select(views, projs, w, h)
+            dev, _ = case.render(pose, counts=False)
+            refs.append(dev)
+        hosts = [[torch.empty((h, w, 4), dtype=torch.float32, pin_memory=True) for _ in range(2)]
+                 for _, _, w, h in frames]
+
+        def check(i):
+            for e in range(2):
+                assert np.array_equal(hosts[i][e].numpy().reshape(-1, 4), refs[i][e]), (i, e)
+
+        for i, (views, projs, w, h) in enumerate(frames):
+            pose, _, _, _ = case.select(views, projs, w, h)
+            sg.sg_render_host_async(case.vol, pose, sg.render_params(), hosts[i])
+            if i >= 1:
+                sg.sg_render_host_wait(case.vol, all=False)  # the older frame in flight is complete
+                check(i - 1)
+        sg.sg_render_host_wait(case.vol, all=True)
+        check(len(frames) - 1)
+    finally:
+        case.close()
+
+
 @pytest.mark.parametrize("brick,levels,kind", [(64, 3, "u16"), (128, 2, "u8")])
 def test_specialised_brick_edges_match_oracle_in_every_launch_shape(brick, levels, kind):
     """Brick edges 32, 64 and 128 run kernels specialised on the edge (the
