@@ -131,6 +131,23 @@ def measured_peak_hbm():
         return 6400.0, "fallback"
 
 
+def measured_peak_bf16():
+    """Dense BF16 tensor peak (TFLOP/s): the burst figure, for kernels timed in
+    sub-millisecond bursts like the U-Net forward."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (burst)"
+    except Exception:
+        return 1800.0, "fallback"
+
+
+def tensor_roofline(tflops):
+    peak, kind = measured_peak_bf16()
+    return {"bound": "tensor", "achieved": round(tflops, 1), "peak": peak, "unit": "TFLOP/s",
+            "frac": round(tflops / peak, 4), "peak_source": kind,
+            "scope": "3x3 convolution FLOPs over the whole forward, elementwise kernels included"}
+
+
 def profiled_traffic(alg_bytes):
     """DRAM bytes per render launch from the committed ncu summary, scaled to
     this run's algorithmic bytes; None if the kernel changed since."""
@@ -547,6 +564,7 @@ def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=20000, steps_per_p
             "fallback_rate": round(float(fall.mean()), 3), "threshold_db": threshold_db,
             "net_ms": round(float(np.mean(t_net)), 3),
             "net_tflops": round(net_flop / (float(np.mean(t_net)) / 1e3) / 1e12, 1),
+            "net_roofline": tensor_roofline(net_flop / (float(np.mean(t_net)) / 1e3) / 1e12),
             "half_render_ms": round(float(np.mean(np.array(t_learned) - np.array(t_net))), 3),
             "render_config": {"full": rec.cfg_full, "half": rec.cfg_half},
             "train_s": round(train_s, 1), "train_pairs": pairs, "steps_per_pair": steps_per_pair}
@@ -573,7 +591,9 @@ def run_net_only(args):
     torch.cuda.synchronize()
     sg.sg_unet_check(net)
     ms = a.elapsed_time(b) / args.steps
-    print(json.dumps({"net_forward_ms": round(ms, 4), "tflops": round(268e9 / (ms / 1e3) / 1e12, 1)}), flush=True)
+    tf = 268e9 / (ms / 1e3) / 1e12
+    print(json.dumps({"net_forward_ms": round(ms, 4), "tflops": round(tf, 1), "roofline": tensor_roofline(tf)}),
+          flush=True)
     sg.sg_unet_destroy(net)
 
 
