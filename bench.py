@@ -546,11 +546,20 @@ def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=20000, steps_per_p
         t_learned.append(a.elapsed_time(b))
         t_net.append(c.elapsed_time(dd))
         t_plain.append(e.elapsed_time(f))
+    # the same frames with two in flight: the half-rate render of frame i + 1
+    # overlaps the network on frame i (a second stream); a frame that falls
+    # back still adds its plain render
+    rs, ns = torch.cuda.Stream(), torch.cuda.Stream()
+    rec.run_pipelined(held, rs, ns)  # warm-up
+    pipe_ms = min(rec.run_pipelined(held, rs, ns) for _ in range(3)) / len(held)
     sg.sg_volume_destroy(vol2)
     rec.close()
     psnrs = np.array(psnrs)
     fall = psnrs < threshold_db
-    learned_ms = float(np.mean(np.array(t_learned) + np.where(fall, t_plain, 0.0)))
+    serial_ms = float(np.mean(np.array(t_learned) + np.where(fall, t_plain, 0.0)))
+    pipelined_ms = pipe_ms + float(np.mean(np.where(fall, t_plain, 0.0)))
+    # the headline takes the faster of the two schedules (both reported)
+    learned_ms = min(serial_ms, pipelined_ms)
     plain_ms = float(np.mean(t_plain))
     net_flop = 2 * 268.0e9 / 2  # ~134 GFLOP per eye (3x3 convs), both eyes
     return {"workload": "learned reconstruction: 2x720x800 at step 1.0 -> U-Net (32/64/128, BF16) -> 2x1440x1600; "
@@ -558,6 +567,9 @@ def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=20000, steps_per_p
                         f"seed and {eval_poses} held-out poses",
             "learned_fps": round(1e3 / learned_ms, 2), "plain_fps": round(1e3 / plain_ms, 2),
             "learned_over_plain": round(plain_ms / learned_ms, 3),
+            "learned_mode": "two frames in flight" if pipelined_ms < serial_ms else "one frame at a time",
+            "learned_fps_serial": round(1e3 / serial_ms, 2),
+            "learned_fps_two_in_flight": round(1e3 / pipelined_ms, 2),
             "psnr_db": {"mean": round(float(psnrs.mean()), 2), "min": round(float(psnrs.min()), 2),
                         "median": round(float(np.median(psnrs)), 2)},
             "bilinear_psnr_db": {"mean": round(float(bilinear.mean()), 2), "min": round(float(bilinear.min()), 2)},

@@ -111,6 +111,44 @@ class Learned:
         """Both eyes of the current half-resolution render -> self.recon."""
         sg.sg_unet_forward(self.net, self.half, self.w * 4, self.h, self.w, self.recon, self.W * 4, stream=stream)
 
+    def run_pipelined(self, poses, render_stream, net_stream):
+        """Learned frames of `poses` with two in flight: the selection and
+        half-rate render of frame i + 1 (render_stream) overlap the network on
+        frame i (net_stream); the render and the network are bound by
+        different units (instruction issue; copies and tensor cores) and share
+        the SMs. Half-rate images and reconstructions are double-buffered; a
+        render waits for the network to have read its buffer. Returns the
+        device time from the first render to the last reconstruction (ms);
+        the reconstructions stay in self.recon_pair."""
+        torch = self.torch
+        if not hasattr(self, "half_pair"):
+            self.half_pair = [self.half, [torch.empty_like(h) for h in self.half]]
+            self.recon_pair = [self.recon, [torch.empty_like(r) for r in self.recon]]
+        ev = lambda: torch.cuda.Event(enable_timing=False)
+        rendered, consumed = [ev(), ev()], [None, None]
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        start.record(render_stream)
+        net_stream.wait_event(start)
+        for i, (views, projs) in enumerate(poses):
+            k = i % 2
+            if consumed[k] is not None:
+                render_stream.wait_event(consumed[k])
+            p = self.pose_half(views, projs)
+            sg.sg_select_lod(self.vol, p, stream=render_stream)
+            if self.cfg_half is not None:
+                sg.sg_set_render_config(self.vol, **self.cfg_half)
+            sg.sg_render(self.vol, p, sg.render_params(step=2 * self.step), self.half_pair[k], stream=render_stream)
+            rendered[k].record(render_stream)
+            net_stream.wait_event(rendered[k])
+            sg.sg_unet_forward(self.net, self.half_pair[k], self.w * 4, self.h, self.w, self.recon_pair[k], self.W * 4,
+                               stream=net_stream)
+            consumed[k] = ev()
+            consumed[k].record(net_stream)
+        end.record(net_stream)
+        torch.cuda.synchronize()
+        return start.elapsed_time(end)
+
     def psnr(self, a, b, out_index=0, stream=None):
         sg.sg_psnr(a, b, a.numel(), self.psnr_buf[out_index:out_index + 1], stream=stream)
         return self.psnr_buf[out_index:out_index + 1]
