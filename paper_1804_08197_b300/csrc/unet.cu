@@ -3,7 +3,7 @@
 // turns a half-resolution, coarser-step render into a full-resolution image:
 // out = bilinear_2x(in) + pixel_shuffle_2x(head(unet(in))). Trained on the
 // GPU with the project's own forward and backward kernels (Adam, MSE), used
-// with the plain full-rate render as fallback and judge (PSNR).
+// with the plain full-rate render as fallback and yardstick (PSNR).
 //
 // Layers (h x w = half-resolution size, multiple of 4):
 //   c1a 16->32, c1b 32->32 (= e1)               at h x w      (input: RGBA + 12 zero channels)

@@ -7,7 +7,7 @@ copies). A pair is the plain full-rate render of a pose (W x H per eye,
 step s) and the reduced render of the same pose at half resolution and twice
 the step (W/2 x H/2, step 2s, at the level of detail of the full-resolution
 image); the network maps the reduced render to the full-rate one. The full-rate render
-is also the fallback and the judge: a frame whose PSNR against it falls below
+is also the fallback and the yardstick: a frame whose PSNR against it falls below
 the threshold is replaced by it.
 """
 import numpy as np
