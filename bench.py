@@ -487,7 +487,7 @@ def container_streaming(sg, torch, dev, n_vox=1024, brick=64, levels=4, count=12
             "disk_read_gbs": round(tot["disk_bytes"] / max(sm.sum() / 1e3, 1e-9) / 1e9, 3)}
 
 
-def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=20000, steps_per_pair=4, eval_poses=16,
+def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=20000, steps_per_pair=4, eval_poses=16, tau_half=None,
                   threshold_db=40.0):
     """Learned reconstruction vs the plain path on the same GPU: training on
     `pairs` seeded (pose, full-rate render, half-res render) pairs of the
@@ -498,7 +498,7 @@ def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=20000, steps_per_p
     import synth
     from paper_1804_08197_b300.learned import Learned
     stream = torch.cuda.current_stream()
-    rec = Learned(vol, W_EYE, H_EYE, step=STEP, tau=TAU, max_batch=16, crop=64, seed=7)
+    rec = Learned(vol, W_EYE, H_EYE, step=STEP, tau=TAU, max_batch=16, crop=64, seed=7, tau_half=tau_half)
     # held-out volume (different seed) and poses
     ev = synth.filaments_u16((N_VOX,) * 3, seed=9001)
     vol2 = sg.sg_volume_create((N_VOX,) * 3, sg.SG_U16, BRICK, LEVELS, model=model)
@@ -578,7 +578,7 @@ def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=20000, steps_per_p
             "net_tflops": round(net_flop / (float(np.mean(t_net)) / 1e3) / 1e12, 1),
             "net_roofline": tensor_roofline(net_flop / (float(np.mean(t_net)) / 1e3) / 1e12),
             "half_render_ms": round(float(np.mean(np.array(t_learned) - np.array(t_net))), 3),
-            "render_config": {"full": rec.cfg_full, "half": rec.cfg_half},
+            "render_config": {"full": rec.cfg_full, "half": rec.cfg_half}, "half_tau_px": rec.tau_half,
             "train_s": round(train_s, 1), "train_pairs": pairs, "steps_per_pair": steps_per_pair}
 
 
@@ -628,7 +628,8 @@ def run_learned_only(args):
     p0 = sg.make_pose(*poses[0], W_EYE, H_EYE, pixel_error=TAU, slot=0)
     sg.sg_select_lod(vol, p0, stream=stream)
     sg.sg_autotune_render(vol, [p0], sg.render_params(step=STEP), outs, reps=3, stream=stream)
-    print(json.dumps(learned_recon(sg, torch, dev, vol, tf_table, model, pairs=args.learned_pairs)), flush=True)
+    print(json.dumps(learned_recon(sg, torch, dev, vol, tf_table, model, pairs=args.learned_pairs,
+                                   tau_half=args.learned_half_tau)), flush=True)
     sg.sg_volume_destroy(vol)
 
 
@@ -908,6 +909,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched 4D and learned measurements")
+    ap.add_argument("--learned-half-tau", type=float, default=None,
+                    help="pixel error bound of the reduced render (default: half of tau, the full image's LOD)")
     ap.add_argument("--learned-pairs", type=int, default=20000,
                     help="training pairs for the learned path (the configuration's 20000, about 3 min)")
     ap.add_argument("--tensor-path", type=int, default=-1,

@@ -17,7 +17,7 @@ from . import sg
 
 class Learned:
     def __init__(self, vol, width, height, step=0.5, tau=1.0, max_batch=16, crop=64, seed=1, device="cuda",
-                 slot_full=200, slot_half=201):
+                 slot_full=200, slot_half=201, tau_half=None):
         import torch
         self.torch = torch
         self.vol = vol
@@ -25,6 +25,9 @@ class Learned:
         self.w, self.h = width // 2, height // 2
         assert self.h % 4 == 0 and self.w % 4 == 0
         self.step, self.tau = step, tau
+        # the reduced render's pixel error bound: tau / 2 keeps the level of
+        # detail of the full-resolution image (its pixels are twice as large)
+        self.tau_half = 0.5 * tau if tau_half is None else tau_half
         self.crop = crop
         self.slot_full, self.slot_half = slot_full, slot_half
         self.net = sg.sg_unet_create(max(max_batch, 2), max(self.h, crop), max(self.w, crop), seed)
@@ -49,9 +52,7 @@ class Learned:
         return sg.make_pose(views, projs, self.W, self.H, pixel_error=self.tau, t=t, slot=self.slot_full)
 
     def pose_half(self, views, projs, t=0):
-        # the reduced render keeps the level of detail of the full-resolution
-        # image: tau is halved because its pixels are twice as large
-        return sg.make_pose(views, projs, self.w, self.h, pixel_error=0.5 * self.tau, t=t, slot=self.slot_half)
+        return sg.make_pose(views, projs, self.w, self.h, pixel_error=self.tau_half, t=t, slot=self.slot_half)
 
     def render_full(self, views, projs, outs=None, stream=None):
         p = self.pose_full(views, projs)
