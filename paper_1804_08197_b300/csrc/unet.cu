@@ -23,6 +23,7 @@
 #include "unet_gemm.cuh"
 #include "unet_tc.cuh"
 #include "unet_ws.cuh"
+#include "unet_wgrad_tc.cuh"
 
 using namespace sg;
 using namespace sg::nn;
@@ -33,7 +34,8 @@ constexpr int kLayers = 11;
 enum { C1A, C1B, C2A, C2B, C3A, C3B, D2A, D2B, D1A, D1B, HEAD };
 const int kCin[kLayers] = {16, 32, 32, 64, 64, 128, 192, 64, 96, 32, 32};
 const int kCout[kLayers] = {32, 32, 64, 64, 128, 128, 64, 64, 32, 32, 16};
-constexpr int kWgradSplits = 32;
+constexpr int kWgradSplits = 32;      // pixel splits of the mma.sync weight gradient
+constexpr int kWgradMaxSplits = 128;  // pixel splits of the tcgen05 one (partials permitting)
 
 // ------------------------------------------------------------------ elementwise kernels
 
@@ -226,8 +228,12 @@ struct sg_unet {
         *g_a3 = nullptr, *g_b3 = nullptr, *g_a4 = nullptr, *g_d2 = nullptr, *g_a5 = nullptr, *g_d1 = nullptr,
         *g_head = nullptr;
   bf16* dz = nullptr;         // masked gradient staging (largest layer)
-  float* dw_part = nullptr;   // [S][9][128][192]
-  float* db_part = nullptr;   // [S][128]
+  float* dw_part = nullptr;   // [S][9][Cout][Cin], room for kWgradSplits x 9 x 128 x 192
+  float* db_part = nullptr;   // [S][Cout], room for kWgradMaxSplits x 128
+  // tcgen05 weight gradients: transposed operands, grown on demand
+  uint16_t* wg_dzT = nullptr;
+  uint16_t* wg_xT3 = nullptr;
+  size_t wg_dzT_bytes = 0, wg_xT3_bytes = 0;
   float* d_loss = nullptr;    // [2]
   Crops in_crops;
   std::vector<void*> allocs;
@@ -243,6 +249,8 @@ cudaError_t alloc(sg_unet* u, void** p, size_t bytes) {
 
 void free_unet(sg_unet* u) {
   for (void* p : u->allocs) cudaFree(p);
+  cudaFree(u->wg_dzT);
+  cudaFree(u->wg_xT3);
   delete u;
 }
 
@@ -437,6 +445,143 @@ cudaError_t conv(const ConvArgs& a, cudaStream_t s, uint32_t* tc_err = nullptr, 
   return conv_bn<16>(a, s);
 }
 
+// dW[co][tap][ci] += sum over the S splits of part[k][tap][co][ci] (elements
+// e < 9 Cout Cin, e = (co 9 + tap) Cin + ci), db[co] += sum of bpart[k][co]
+// (the next Cout elements). Thread (x, y) of a block sums the splits k = y,
+// y + 8, ... of element 32 blockIdx + x in order; the eight partial sums are
+// then added in order of y: a fixed order, the same on every run.
+__global__ void k_wgrad_reduce(const float* __restrict__ part, const float* __restrict__ bpart, int S, int Cout,
+                               int Cin, float* __restrict__ gw, float* __restrict__ gb) {
+  __shared__ float sum[8][33];
+  const int nw = 9 * Cout * Cin;
+  const int e = blockIdx.x * 32 + threadIdx.x, g = threadIdx.y;
+  float acc = 0.f;
+  if (e < nw) {
+    const int ci = e % Cin, tap = (e / Cin) % 9, co = e / (9 * Cin);
+    const size_t base = ((size_t)tap * Cout + co) * Cin + ci, stride = (size_t)nw;
+#pragma unroll 4
+    for (int k = g; k < S; k += 8) acc += part[k * stride + base];
+  } else if (e < nw + Cout) {
+#pragma unroll 4
+    for (int k = g; k < S; k += 8) acc += bpart[(size_t)k * Cout + (e - nw)];
+  }
+  sum[g][threadIdx.x] = acc;
+  __syncthreads();
+  if (g == 0) {
+    float t = sum[0][threadIdx.x];
+#pragma unroll
+    for (int i = 1; i < 8; ++i) t += sum[i][threadIdx.x];
+    if (e < nw)
+      gw[e] += t;
+    else if (e < nw + Cout)
+      gb[e - nw] += t;
+  }
+}
+
+// scratch of at least `bytes` (contents not kept when it grows)
+cudaError_t grow(uint16_t** p, size_t* have, size_t bytes) {
+  if (*have >= bytes) return cudaSuccess;
+  cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) *have = bytes;
+  return e;
+}
+
+template <int NB>
+cudaError_t wgrad_tc_launch(const WgradTcArgs& a, int S, uint32_t* err, const CUtensorMap& tA,
+                            const CUtensorMap& tB, cudaStream_t s) {
+  using Sh = WgradTcShape<NB>;
+  const int stages = Sh::kMaxStages;
+  const int smem = stages * Sh::kStage + 2048;  // + the ones tile and room to align to 1024
+  static bool configured = false;                // per template instance, set once on first use
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  k_wgrad_tc<NB><<<dim3(a.Cin / NB, S), 128, smem, s>>>(a, stages, err, tA, tB);
+  return cudaGetLastError();
+}
+
+// tcgen05 weight gradient into dw_part / db_part; returns the number of
+// splits, 0 when the shape needs the mma.sync kernel instead
+int wgrad_tc(sg_unet* u, int L, const bf16* dz, int dz_stride, const bf16* in, int in_stride, int in_off, int N,
+             int H, int W, cudaStream_t s, cudaError_t* err) {
+  const int Cin = kCin[L], Cout = kCout[L];
+  *err = cudaSuccess;
+  if (u->tc != 4 || W % 8 || (H * W) % 32 || Cin % 16 || Cout % 16 || Cout > 128 || dz_stride != Cout) return 0;
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn || (reinterpret_cast<uintptr_t>(in) & 15)) return 0;
+  const int64_t P = (int64_t)N * H * W, plane = (int64_t)N * (H + 2) * W;
+  cudaError_t e = grow(&u->wg_dzT, &u->wg_dzT_bytes, (size_t)Cout * P * 2);
+  if (e == cudaSuccess) e = grow(&u->wg_xT3, &u->wg_xT3_bytes, (size_t)3 * Cin * plane * 2);
+  if (e != cudaSuccess) {
+    *err = e;
+    return 0;
+  }
+  k_transpose_dz<<<dim3((unsigned)((P + 63) / 64), (Cout + 31) / 32), dim3(32, 8), 0, s>>>(
+      reinterpret_cast<const uint16_t*>(dz), dz_stride, Cout, P, u->wg_dzT);
+  k_shift_transpose<<<dim3((W + 63) / 64, H + 2, N * ((Cin + 31) / 32)), dim3(32, 8), 0, s>>>(
+      reinterpret_cast<const uint16_t*>(in), in_stride, in_off, Cin, N, H, W, u->wg_xT3);
+  if ((e = cudaGetLastError()) != cudaSuccess) {
+    *err = e;
+    return 0;
+  }
+  const int NB = Cin % 32 == 0 ? 32 : 16;
+  CUtensorMap tA, tB;
+  memset(&tA, 0, sizeof tA);
+  memset(&tB, 0, sizeof tB);
+  const cuuint32_t one[4] = {1, 1, 1, 1};
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)P, (cuuint64_t)Cout};
+    const cuuint64_t strides[1] = {(cuuint64_t)P * 2};
+    const cuuint32_t box[2] = {32, (cuuint32_t)Cout};
+    if (fn(&tA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, u->wg_dzT, dims, strides, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+      *err = cudaErrorInvalidValue;
+      return 0;
+    }
+  }
+  {
+    const cuuint64_t dims[4] = {(cuuint64_t)(H + 2) * W, (cuuint64_t)N, (cuuint64_t)Cin, 3};
+    const cuuint64_t strides[3] = {(cuuint64_t)(H + 2) * W * 2, (cuuint64_t)plane * 2, (cuuint64_t)Cin * plane * 2};
+    const cuuint32_t box[4] = {32, 1, (cuuint32_t)NB, 1};
+    if (fn(&tB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, u->wg_xT3, dims, strides, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+      *err = cudaErrorInvalidValue;
+      return 0;
+    }
+  }
+  // splits: about two CTAs per SM, within the partial buffers and the chunks
+  const int64_t chunks = P / 32;
+  const int nci = Cin / NB;
+  int64_t S = (2 * sm_count() + nci - 1) / nci;
+  S = std::min<int64_t>(S, kWgradMaxSplits);
+  S = std::min<int64_t>(S, (int64_t)kWgradSplits * 9 * 128 * 192 / (9 * Cout * Cin));
+  S = std::max<int64_t>(1, std::min<int64_t>(S, chunks));
+  WgradTcArgs a;
+  a.Cin = Cin;
+  a.Cout = Cout;
+  a.N = N;
+  a.H = H;
+  a.W = W;
+  a.chunks = chunks;
+  a.per = (chunks + S - 1) / S;
+  S = (chunks + a.per - 1) / a.per;  // no split without pixels
+  a.dw_part = u->dw_part;
+  a.db_part = u->db_part;
+  e = NB == 32 ? wgrad_tc_launch<32>(a, (int)S, u->d_err, tA, tB, s) : wgrad_tc_launch<16>(a, (int)S, u->d_err, tA, tB, s);
+  if (e != cudaSuccess) {
+    *err = e;
+    return 0;
+  }
+  return (int)S;
+}
+
 cudaError_t wgrad(sg_unet* u, int L, const bf16* dz, int dz_stride, const bf16* in, int in_stride, int in_off,
                   int N, int H, int W, cudaStream_t s) {
   WgradArgs a;
@@ -453,33 +598,25 @@ cudaError_t wgrad(sg_unet* u, int L, const bf16* dz, int dz_stride, const bf16* 
   a.W = W;
   a.Cin = kCin[L];
   a.Cout = kCout[L];
-  a.S = kWgradSplits;
-  const int TM = a.Cout % 32 == 0 ? 32 : 16, TN = a.Cin % 32 == 0 ? 32 : 16;
-  dim3 grid(a.Cout / TM, a.Cin / TN, 9 * a.S);
-  if (TM == 32 && TN == 32) k_wgrad<32, 32><<<grid, 128, 0, s>>>(a);
-  else if (TM == 32) k_wgrad<32, 16><<<grid, 128, 0, s>>>(a);
-  else if (TN == 32) k_wgrad<16, 32><<<grid, 128, 0, s>>>(a);
-  else k_wgrad<16, 16><<<grid, 128, 0, s>>>(a);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  int S = wgrad_tc(u, L, dz, dz_stride, in, in_stride, in_off, N, H, W, s, &e);
   if (e != cudaSuccess) return e;
+  if (S == 0) {
+    S = a.S = kWgradSplits;
+    const int TM = a.Cout % 32 == 0 ? 32 : 16, TN = a.Cin % 32 == 0 ? 32 : 16;
+    dim3 grid(a.Cout / TM, a.Cin / TN, 9 * a.S);
+    if (TM == 32 && TN == 32) k_wgrad<32, 32><<<grid, 128, 0, s>>>(a);
+    else if (TM == 32) k_wgrad<32, 16><<<grid, 128, 0, s>>>(a);
+    else if (TN == 32) k_wgrad<16, 32><<<grid, 128, 0, s>>>(a);
+    else k_wgrad<16, 16><<<grid, 128, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   // sum the splits into the gradient: dW[co][tap][ci] (+=), db[co] (+=)
-  const int Cin = a.Cin, Cout = a.Cout;
-  float* gw = u->d_grad + u->woff[L];
-  float* gb = u->d_grad + u->boff[L];
-  const float* part = u->dw_part;
-  const float* bpart = u->db_part;
-  e = each((int64_t)Cout * 9 * Cin, s, [=] __device__(int64_t i) {
-    const int ci = (int)(i % Cin), tap = (int)((i / Cin) % 9), co = (int)(i / (9 * Cin));
-    float acc = 0.f;
-    for (int k = 0; k < kWgradSplits; ++k) acc += part[(((size_t)k * 9 + tap) * Cout + co) * Cin + ci];
-    gw[i] += acc;
-  });
-  if (e != cudaSuccess) return e;
-  return each(Cout, s, [=] __device__(int64_t co) {
-    float acc = 0.f;
-    for (int k = 0; k < kWgradSplits; ++k) acc += bpart[(size_t)k * Cout + co];
-    gb[co] += acc;
-  });
+  const int nw = 9 * a.Cout * a.Cin;
+  k_wgrad_reduce<<<(nw + a.Cout + 31) / 32, dim3(32, 8), 0, s>>>(u->dw_part, u->db_part, S, a.Cout, a.Cin,
+                                                                 u->d_grad + u->woff[L], u->d_grad + u->boff[L]);
+  return cudaGetLastError();
 }
 
 ConvArgs conv_args(sg_unet* u, int L, const bf16* in, int in_stride, int in_off, int N, int H, int W) {
@@ -797,7 +934,7 @@ sg_status sg_unet_create(int max_batch, int max_h, int max_w, uint64_t seed, sg_
   A_(u->g_cat2, P2 * 192 * f) A_(u->g_p2, P3 * 64 * f) A_(u->g_a3, P3 * 128 * f) A_(u->g_b3, P3 * 128 * f)
   A_(u->g_a4, P2 * 64 * f) A_(u->g_d2, P2 * 64 * f) A_(u->g_a5, P1 * 32 * f) A_(u->g_d1, P1 * 32 * f)
   A_(u->g_head, P1 * 16 * f) A_(u->dz, P1 * 32 * b)
-  A_(u->dw_part, (size_t)kWgradSplits * 9 * 128 * 192 * f) A_(u->db_part, (size_t)kWgradSplits * 128 * f)
+  A_(u->dw_part, (size_t)kWgradSplits * 9 * 128 * 192 * f) A_(u->db_part, (size_t)kWgradMaxSplits * 128 * f)
   A_(u->d_loss, 2 * f)
   A_(u->d_err, 16)
 #undef A_

@@ -152,6 +152,38 @@ def test_persistent_convolution_over_many_tiles():
         sg.sg_unet_destroy(net)
 
 
+def test_tensor_core_weight_gradients_agree_with_mma_sync():
+    """With widths that are multiples of 8 at every level (32 x 64, 16 x 32,
+    8 x 16) the weight and bias gradients run on tcgen05 (pixels as the
+    contraction over transposed, row-padded operands, one TMEM accumulator
+    per tap, pixel splits summed in a fixed order); they agree with the
+    mma.sync path to summation order, and repeat exactly on a second run."""
+    from paper_1804_08197_b300 import sg
+    net = sg.sg_unet_create(3, 32, 64, seed=31)
+    try:
+        p = _random_params(32, sg.sg_unet_param_count(net))
+        sg.sg_unet_set_params(net, p)
+        rng = np.random.default_rng(33)
+        x = rng.uniform(0, 1, (3, 32, 64, 4))
+        t = rng.uniform(0, 1, (3, 64, 128, 4))
+        res = {}
+        for path in (0, 4, 4):
+            sg.sg_unet_set_tensor_path(net, path)
+            out, loss = _run(net, x, t)
+            sg.sg_unet_check(net)
+            g = sg.sg_unet_get_params(net, which=1).astype(np.float64)
+            if path in res:
+                assert np.array_equal(g, res[path][1])
+            res[path] = (loss, g)
+        assert res[4][0] == pytest.approx(res[0][0], rel=1e-4)
+        for L, (ws, bs) in enumerate(ou.layer_slices()):
+            for sl in (ws, bs):
+                g0, g1 = res[0][1][sl], res[4][1][sl]
+                assert np.linalg.norm(g1 - g0) <= 2e-2 * np.linalg.norm(g0) + 1e-12, (ou.NAMES[L], sl)
+    finally:
+        sg.sg_unet_destroy(net)
+
+
 def test_untrained_network_is_exactly_bilinear_upsampling():
     from paper_1804_08197_b300 import sg
     net = sg.sg_unet_create(3, 12, 20, seed=9)
