@@ -633,6 +633,44 @@ def run_learned_only(args):
     sg.sg_volume_destroy(vol)
 
 
+def run_train_only(args):
+    """Training steps alone (16 random 64x64 crops of one rendered pair:
+    forward, loss, backward, Adam), timed with CUDA events after warm-up."""
+    import torch
+    from paper_1804_08197_b300 import sg
+    from paper_1804_08197_b300.learned import Learned
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    vol_host, tf_table, poses, model = make_inputs(args.volume)
+    vol = sg.sg_volume_create((args.volume,) * 3, sg.SG_U16, BRICK, LEVELS, model=model)
+    d0 = torch.from_numpy(vol_host.view(np.int16)).to(dev)
+    sg.sg_upload_volume_device(vol, 0, 0, d0.data_ptr())
+    torch.cuda.synchronize()
+    del d0
+    sg.sg_set_transfer_function(vol, 0, tf_table, *WINDOW)
+    rec = Learned(vol, W_EYE, H_EYE, step=STEP, tau=TAU, max_batch=16, crop=64, seed=7)
+    rec.train_on_pair(*poses[0], steps=args.warmup)  # renders the pair, then the warm-up steps
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c = rec.crop
+    outs = [rec.crop_out[i].data_ptr() for i in range(16)]
+    a.record()
+    for _ in range(args.steps):
+        ins, tgts = rec._crops(16)
+        sg.sg_unet_forward(rec.net, ins, rec.w * 4, c, c, outs, 2 * c * 4)
+        sg.sg_unet_backward(rec.net, tgts, rec.W * 4, outs, 2 * c * 4, loss=rec.loss)
+        sg.sg_unet_adam_step(rec.net, 1e-4)
+    b.record()
+    torch.cuda.synchronize()
+    sg.sg_unet_check(rec.net)
+    ms = a.elapsed_time(b) / args.steps
+    flop = 3 * 268e9 * (16 * 64 * 64) / (2 * (H_EYE // 2) * (W_EYE // 2))  # forward, input and weight gradients
+    print(json.dumps({"train_step_ms": round(ms, 4), "crops": "16 x 64 x 64 (half-rate) -> 128 x 128",
+                      "tflops": round(flop / (ms / 1e3) / 1e12, 1)}), flush=True)
+    rec.close()
+    sg.sg_volume_destroy(vol)
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle on the host cores, bounded sample per step."""
     if rank != 0:
@@ -919,7 +957,7 @@ def main():
                     help="empty-space skipping cell edge in voxels (0 = the library's default)")
     ap.add_argument("--streaming-size", choices=["auto", "full", "scaled"], default="auto",
                     help="large-volume fly-through at 4096^3 (full), at 1024^3 (scaled), or full when it fits")
-    ap.add_argument("--only", choices=["net", "learned", "streaming", "container"], default=None,
+    ap.add_argument("--only", choices=["net", "learned", "train", "streaming", "container"], default=None,
                     help="net: only U-Net forwards at 2x720x800 (a small case for profiling the convolutions); "
                          "streaming: only the large-volume fly-through")
     ap.add_argument("--volume", type=int, default=N_VOX, help="volume edge (default 1024; smaller for profiling)")
@@ -940,6 +978,8 @@ def main():
         run_net_only(args)
     elif args.only == "learned":
         run_learned_only(args)
+    elif args.only == "train":
+        run_train_only(args)
     elif args.only == "streaming":
         import torch
         from paper_1804_08197_b300 import sg
