@@ -232,6 +232,7 @@ struct sg_unet {
   float* db_part = nullptr;   // [S][Cout], room for kWgradMaxSplits x 128
   // tcgen05 weight gradients: transposed operands, grown on demand
   uint16_t* wg_dzT = nullptr;
+  bool dzT_ready = false;  // wg_dzT holds the current layer's masked gradient
   uint16_t* wg_xT3 = nullptr;
   size_t wg_dzT_bytes = 0, wg_xT3_bytes = 0;
   float* d_loss = nullptr;    // [2]
@@ -478,6 +479,14 @@ __global__ void k_wgrad_reduce(const float* __restrict__ part, const float* __re
   }
 }
 
+// the shapes the tcgen05 weight gradient takes (others: mma.sync)
+bool wgrad_tc_shape(const sg_unet* u, int L, int N, int H, int W) {
+  const int Cin = kCin[L], Cout = kCout[L];
+  (void)N;
+  return u->tc == 4 && W % 8 == 0 && (H * W) % 32 == 0 && Cin % 16 == 0 && Cout % 16 == 0 && Cout <= 128 &&
+         encode_tiled() != nullptr;
+}
+
 // scratch of at least `bytes` (contents not kept when it grows)
 cudaError_t grow(uint16_t** p, size_t* have, size_t bytes) {
   if (*have >= bytes) return cudaSuccess;
@@ -511,9 +520,10 @@ int wgrad_tc(sg_unet* u, int L, const bf16* dz, int dz_stride, const bf16* in, i
              int H, int W, cudaStream_t s, cudaError_t* err) {
   const int Cin = kCin[L], Cout = kCout[L];
   *err = cudaSuccess;
-  if (u->tc != 4 || W % 8 || (H * W) % 32 || Cin % 16 || Cout % 16 || Cout > 128 || dz_stride != Cout) return 0;
+  const bool dzT_ready = u->dzT_ready;
+  u->dzT_ready = false;
+  if (!wgrad_tc_shape(u, L, N, H, W) || dz_stride != Cout || (reinterpret_cast<uintptr_t>(in) & 15)) return 0;
   EncodeTiledFn fn = encode_tiled();
-  if (!fn || (reinterpret_cast<uintptr_t>(in) & 15)) return 0;
   const int64_t P = (int64_t)N * H * W, plane = (int64_t)N * (H + 2) * W;
   cudaError_t e = grow(&u->wg_dzT, &u->wg_dzT_bytes, (size_t)Cout * P * 2);
   if (e == cudaSuccess) e = grow(&u->wg_xT3, &u->wg_xT3_bytes, (size_t)3 * Cin * plane * 2);
@@ -521,8 +531,9 @@ int wgrad_tc(sg_unet* u, int L, const bf16* dz, int dz_stride, const bf16* in, i
     *err = e;
     return 0;
   }
-  k_transpose_dz<<<dim3((unsigned)((P + 63) / 64), (Cout + 31) / 32), dim3(32, 8), 0, s>>>(
-      reinterpret_cast<const uint16_t*>(dz), dz_stride, Cout, P, u->wg_dzT);
+  if (!dzT_ready)
+    k_transpose_dz<<<dim3((unsigned)((P + 63) / 64), (Cout + 31) / 32), dim3(32, 8), 0, s>>>(
+        reinterpret_cast<const uint16_t*>(dz), dz_stride, Cout, P, u->wg_dzT);
   k_shift_transpose<<<dim3((W + 63) / 64, H + 2, N * ((Cin + 31) / 32)), dim3(32, 8), 0, s>>>(
       reinterpret_cast<const uint16_t*>(in), in_stride, in_off, Cin, N, H, W, u->wg_xT3);
   if ((e = cudaGetLastError()) != cudaSuccess) {
@@ -654,6 +665,24 @@ cudaError_t relu_bwd(const float* dy, int dy_stride, int dy_off, const bf16* y, 
     }
     *reinterpret_cast<uint4*>(dz + (size_t)p * C + c) = f_to_bf8(f);
   });
+}
+
+// the masked output gradient of layer L (as relu_bwd), written transposed as
+// well when the layer's weight gradient runs on tcgen05
+cudaError_t masked_grad(sg_unet* u, int L, const float* dy, int dy_stride, int dy_off, const bf16* y, int y_stride,
+                        int y_off, int N, int H, int W, bf16* dz, cudaStream_t s) {
+  const int C = kCout[L];
+  const int64_t P = (int64_t)N * H * W;
+  u->dzT_ready = false;
+  if (!wgrad_tc_shape(u, L, N, H, W)) return relu_bwd(dy, dy_stride, dy_off, y, y_stride, y_off, C, P, dz, s);
+  cudaError_t e = grow(&u->wg_dzT, &u->wg_dzT_bytes, (size_t)C * P * 2);
+  if (e != cudaSuccess) return e;
+  k_relu_bwd_t<<<dim3((unsigned)((P + 63) / 64), (C + 31) / 32), dim3(32, 8), 0, s>>>(
+      dy, dy_stride, dy_off, reinterpret_cast<const uint16_t*>(y), y_stride, y_off, C, P,
+      reinterpret_cast<uint16_t*>(dz), u->wg_dzT);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  u->dzT_ready = true;
+  return cudaSuccess;
 }
 
 // input gradient of a conv: dx[:, off..off+Cin) += conv(dz, flipped weights)
@@ -839,52 +868,52 @@ cudaError_t backward(sg_unet* u, const Crops& tgt, const float* out, int64_t out
   }
   bf16* dz = u->dz;
   // head (no ReLU)
-  if ((e = relu_bwd(u->g_head, 16, 0, nullptr, 0, 0, 16, P1, dz, s))) return e;
+  if ((e = masked_grad(u, HEAD, u->g_head, 16, 0, nullptr, 0, 0, N, h, w, dz, s))) return e;
   if ((e = wgrad(u, HEAD, dz, 16, u->d1, 32, 0, N, h, w, s))) return e;
   if ((e = dgrad(u, HEAD, dz, u->g_d1, 32, 0, N, h, w, s))) return e;
   // d1b: y = d1, x = a5
-  if ((e = relu_bwd(u->g_d1, 32, 0, u->d1, 32, 0, 32, P1, dz, s))) return e;
+  if ((e = masked_grad(u, D1B, u->g_d1, 32, 0, u->d1, 32, 0, N, h, w, dz, s))) return e;
   if ((e = wgrad(u, D1B, dz, 32, u->a5, 32, 0, N, h, w, s))) return e;
   if ((e = dgrad(u, D1B, dz, u->g_a5, 32, 0, N, h, w, s))) return e;
   // d1a: y = a5, x = cat1 (96)
-  if ((e = relu_bwd(u->g_a5, 32, 0, u->a5, 32, 0, 32, P1, dz, s))) return e;
+  if ((e = masked_grad(u, D1A, u->g_a5, 32, 0, u->a5, 32, 0, N, h, w, dz, s))) return e;
   if ((e = wgrad(u, D1A, dz, 32, u->cat1, 96, 0, N, h, w, s))) return e;
   if ((e = dgrad(u, D1A, dz, u->g_cat1, 96, 0, N, h, w, s))) return e;
   if ((e = up_bwd(u->g_cat1, 96, u->g_d2, 64, 64, N, h2, w2, s))) return e;  // up: g_d2 += children
   // d2b: y = d2, x = a4
-  if ((e = relu_bwd(u->g_d2, 64, 0, u->d2, 64, 0, 64, P2, dz, s))) return e;
+  if ((e = masked_grad(u, D2B, u->g_d2, 64, 0, u->d2, 64, 0, N, h2, w2, dz, s))) return e;
   if ((e = wgrad(u, D2B, dz, 64, u->a4, 64, 0, N, h2, w2, s))) return e;
   if ((e = dgrad(u, D2B, dz, u->g_a4, 64, 0, N, h2, w2, s))) return e;
   // d2a: y = a4, x = cat2 (192)
-  if ((e = relu_bwd(u->g_a4, 64, 0, u->a4, 64, 0, 64, P2, dz, s))) return e;
+  if ((e = masked_grad(u, D2A, u->g_a4, 64, 0, u->a4, 64, 0, N, h2, w2, dz, s))) return e;
   if ((e = wgrad(u, D2A, dz, 64, u->cat2, 192, 0, N, h2, w2, s))) return e;
   if ((e = dgrad(u, D2A, dz, u->g_cat2, 192, 0, N, h2, w2, s))) return e;
   if ((e = up_bwd(u->g_cat2, 192, u->g_b3, 128, 128, N, h4, w4, s))) return e;  // up: g_b3 += children
   // c3b: y = b3, x = a3
-  if ((e = relu_bwd(u->g_b3, 128, 0, u->b3, 128, 0, 128, P3, dz, s))) return e;
+  if ((e = masked_grad(u, C3B, u->g_b3, 128, 0, u->b3, 128, 0, N, h4, w4, dz, s))) return e;
   if ((e = wgrad(u, C3B, dz, 128, u->a3, 128, 0, N, h4, w4, s))) return e;
   if ((e = dgrad(u, C3B, dz, u->g_a3, 128, 0, N, h4, w4, s))) return e;
   // c3a: y = a3, x = p2
-  if ((e = relu_bwd(u->g_a3, 128, 0, u->a3, 128, 0, 128, P3, dz, s))) return e;
+  if ((e = masked_grad(u, C3A, u->g_a3, 128, 0, u->a3, 128, 0, N, h4, w4, dz, s))) return e;
   if ((e = wgrad(u, C3A, dz, 128, u->p2, 64, 0, N, h4, w4, s))) return e;
   if ((e = dgrad(u, C3A, dz, u->g_p2, 64, 0, N, h4, w4, s))) return e;
   // pool: g_cat2[:, 128..192) += g_p2 / 4 (e2's gradient lives at its place in cat2)
   if ((e = pool_bwd(u->g_p2, 64, u->g_cat2, 192, 128, 64, N, h4, w4, s))) return e;
   // c2b: y = e2 = cat2[:, 128..), x = a2
-  if ((e = relu_bwd(u->g_cat2, 192, 128, u->cat2, 192, 128, 64, P2, dz, s))) return e;
+  if ((e = masked_grad(u, C2B, u->g_cat2, 192, 128, u->cat2, 192, 128, N, h2, w2, dz, s))) return e;
   if ((e = wgrad(u, C2B, dz, 64, u->a2, 64, 0, N, h2, w2, s))) return e;
   if ((e = dgrad(u, C2B, dz, u->g_a2, 64, 0, N, h2, w2, s))) return e;
   // c2a: y = a2, x = p1
-  if ((e = relu_bwd(u->g_a2, 64, 0, u->a2, 64, 0, 64, P2, dz, s))) return e;
+  if ((e = masked_grad(u, C2A, u->g_a2, 64, 0, u->a2, 64, 0, N, h2, w2, dz, s))) return e;
   if ((e = wgrad(u, C2A, dz, 64, u->p1, 32, 0, N, h2, w2, s))) return e;
   if ((e = dgrad(u, C2A, dz, u->g_p1, 32, 0, N, h2, w2, s))) return e;
   if ((e = pool_bwd(u->g_p1, 32, u->g_cat1, 96, 64, 32, N, h2, w2, s))) return e;  // pool: e1's gradient
   // c1b: y = e1 = cat1[:, 64..), x = a1
-  if ((e = relu_bwd(u->g_cat1, 96, 64, u->cat1, 96, 64, 32, P1, dz, s))) return e;
+  if ((e = masked_grad(u, C1B, u->g_cat1, 96, 64, u->cat1, 96, 64, N, h, w, dz, s))) return e;
   if ((e = wgrad(u, C1B, dz, 32, u->a1, 32, 0, N, h, w, s))) return e;
   if ((e = dgrad(u, C1B, dz, u->g_a1, 32, 0, N, h, w, s))) return e;
   // c1a: y = a1, x = in16 (no input gradient)
-  if ((e = relu_bwd(u->g_a1, 32, 0, u->a1, 32, 0, 32, P1, dz, s))) return e;
+  if ((e = masked_grad(u, C1A, u->g_a1, 32, 0, u->a1, 32, 0, N, h, w, dz, s))) return e;
   if ((e = wgrad(u, C1A, dz, 32, u->in16, 16, 0, N, h, w, s))) return e;
   return cudaSuccess;
 }

@@ -61,6 +61,37 @@ __global__ void k_transpose_dz(const uint16_t* __restrict__ dz, int stride, int 
   }
 }
 
+// The masked output gradient of a layer, in both layouts the backward pass
+// uses: dz[p][c] = bf16(dy[p][c] if y[p][c] > 0 (or no y) else 0) for the
+// input gradient, and dzT[c][p] for the weight gradient; tiles of 64 pixels x
+// 32 channels, the transpose through shared memory
+__global__ void k_relu_bwd_t(const float* __restrict__ dy, int dy_stride, int dy_off, const uint16_t* __restrict__ y,
+                             int y_stride, int y_off, int C, int64_t P, uint16_t* __restrict__ dz,
+                             uint16_t* __restrict__ dzT) {
+  __shared__ uint16_t t[32][66];
+  const int64_t p0 = (int64_t)blockIdx.x * 64;
+  const int c0 = blockIdx.y * 32, tx = threadIdx.x;
+  for (int r = threadIdx.y; r < 64; r += 8) {
+    const int64_t p = p0 + r;
+    const int c = c0 + tx;
+    uint16_t v = 0;
+    if (p < P && c < C) {
+      float f = dy[p * dy_stride + dy_off + c];
+      if (y && !(__bfloat162float(__ushort_as_bfloat16(y[p * y_stride + y_off + c])) > 0.f)) f = 0.f;
+      v = __bfloat16_as_ushort(__float2bfloat16_rn(f));
+      dz[p * C + c] = v;
+    }
+    t[tx][r] = v;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int c = c0 + r;
+    const int64_t p = p0 + 2 * tx;
+    if (c < C && p < P)
+      *reinterpret_cast<uint32_t*>(dzT + (int64_t)c * P + p) = (uint32_t)t[r][2 * tx] | ((uint32_t)t[r][2 * tx + 1] << 16);
+  }
+}
+
 // xT3[d][c][n][yp][x] = x[n][yp - 1][x + d - 1][c] (zero outside the image),
 // yp in [0, H + 2); block: 64 pixels of one padded row x 32 channels, written
 // as pixel pairs (W is even)
