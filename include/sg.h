@@ -302,7 +302,11 @@ typedef struct {
  * transfer function or no data for t), CUDA. */
 sg_status sg_select_lod(sg_volume* vol, const sg_pose* pose, sg_select_stats* stats, void* stream);
 
-/* Selection for n poses in one launch (batched frames); no stats. */
+/* Selection for n poses in one launch (batched frames); no stats.
+ * Selections may be captured into a CUDA graph (stats = NULL). A captured
+ * selection is not tracked for other streams: after replaying the graph,
+ * order reads (sg_read_selection) and uploads after the replay through the
+ * caller's streams, e.g. by synchronising. */
 sg_status sg_select_lod_batch(sg_volume* vol, const sg_pose* poses, int n, void* stream);
 
 /* Allocation-free selection. The paper has no counterpart: this entry point

@@ -610,8 +610,14 @@ sg_status sg_select_lod_batch(sg_volume* v, const sg_pose* poses, int n, void* s
   cudaStream_t s = (cudaStream_t)stream;
   ++v->frame;
   SG_CUDA(launch_select(v, poses, n, s), "selection");
-  // uploads on other streams read the stamps this launch writes
-  SG_CUDA(cudaEventRecord(v->ev_select, s), "selection");
+  // uploads and reads on other streams wait for the stamps and results this
+  // launch writes. A launch captured into a CUDA graph is not recorded: an
+  // event recorded during capture cannot be waited on outside it, so the
+  // event keeps the last selection launched directly, and a caller replaying
+  // the graph orders what follows through its own streams.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  SG_CUDA(cudaStreamIsCapturing(s, &cap), "selection");
+  if (cap == cudaStreamCaptureStatusNone) SG_CUDA(cudaEventRecord(v->ev_select, s), "selection");
   for (int i = 0; i < n; ++i) {
     SelSlot& sl = v->sel[poses[i].slot];
     sl.valid = true;
