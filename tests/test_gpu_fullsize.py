@@ -122,3 +122,52 @@ def test_full_size_batched_4d_on_sampled_pixels():
                     compare_image(img[pix], oref)
     finally:
         sg.sg_volume_destroy(vol)
+
+
+def test_full_size_learned_forward_on_sampled_crops():
+    """The learned reconstruction's network at the bench's size (both eyes of
+    720 x 800 -> 1440 x 1600, the persistent tcgen05 convolution over 1200
+    tiles per layer) against the FP64 network oracle on sampled crops. The
+    network is local: an output farther than its receptive radius (under 28
+    input pixels: 3x3 convolutions at three levels, two 2x2 pools, two 2x
+    upsamplings) from a crop's edge is the same computed on the crop or on
+    the whole image, when the crop keeps the pooling grid (origin a multiple
+    of 4). The oracle runs 96 x 96 crops; their centres (and, for a corner
+    crop, the region along the image edges) are compared at BF16 tolerance."""
+    import torch
+    import oracle.unet as ou
+    from paper_1804_08197_b300 import sg
+    h, w, R, C = 800, 720, 28, 96
+    net = sg.sg_unet_create(2, h, w, seed=41)
+    try:
+        rng = np.random.default_rng(42)
+        p = np.zeros(ou.param_count(), np.float32)
+        for (ws, bs), ci in zip(ou.layer_slices(), ou.CIN):
+            p[ws] = rng.normal(0, np.sqrt(2.0 / (9 * ci)), ws.stop - ws.start)
+            p[bs] = rng.normal(0, 0.05, bs.stop - bs.start)
+        ws0, _ = ou.layer_slices()[0]
+        p[ws0].reshape(32, 9, 16)[:, :, 4:] = 0  # padding input channels
+        sg.sg_unet_set_params(net, p)
+        x = rng.uniform(0, 1, (2, h, w, 4)).astype(np.float32)
+        xin = [torch.from_numpy(np.ascontiguousarray(x[i])).cuda() for i in range(2)]
+        out = [torch.zeros((2 * h, 2 * w, 4), device="cuda") for _ in range(2)]
+        sg.sg_unet_forward(net, xin, w * 4, h, w, out, 2 * w * 4)
+        torch.cuda.synchronize()
+        sg.sg_unet_check(net)
+        gpu = np.stack([o.cpu().numpy() for o in out]).astype(np.float64)
+        q = p.astype(np.float64).copy()
+        for ws, _ in ou.layer_slices():
+            q[ws] = torch.from_numpy(p[ws]).to(torch.bfloat16).to(torch.float64).numpy()
+        # (image, crop origin y, x, valid rows / columns of the crop in input pixels)
+        crops = [(0, 352, 312, (R, C - R), (R, C - R)), (1, 100, 600, (R, C - R), (R, C - R)),
+                 (1, 704, 204, (R, C - R), (R, C - R)), (0, 0, 0, (0, C - R), (0, C - R))]
+        for n, y0, x0, (ya, yb), (xa, xb) in crops:
+            xc = x[n:n + 1, y0:y0 + C, x0:x0 + C].astype(np.float64)
+            ref = ou.forward(q, xc)[0]
+            base = ou.bilinear2x(xc)[0]
+            sl = (slice(2 * ya, 2 * yb), slice(2 * xa, 2 * xb))
+            g = gpu[n, 2 * y0:2 * y0 + 2 * C, 2 * x0:2 * x0 + 2 * C][sl]
+            r_gpu, r_ref = g - base[sl], ref[sl] - base[sl]
+            assert np.linalg.norm(r_gpu - r_ref) <= 2e-2 * np.linalg.norm(r_ref), (n, y0, x0)
+    finally:
+        sg.sg_unet_destroy(net)
