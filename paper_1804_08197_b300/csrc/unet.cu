@@ -351,7 +351,7 @@ int sm_count() {
 // persistent warp-specialised convolution: one CTA per SM, as many ring
 // stages as fit in about 220 KB of shared memory
 template <int BN, int R, int CW>
-cudaError_t conv_ws(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
+cudaError_t conv_ws(const ConvArgs& a, uint32_t* err, cudaStream_t s, const HeadOut* head_out = nullptr) {
   using S = WsShape<BN, R, CW>;
   const int stages = std::min(kWsMaxStages, (220 * 1024 - 1024) / S::kStage);
   const int smem = stages * S::kStage + 1024;  // + room to align the ring to 1024 bytes
@@ -371,7 +371,10 @@ cudaError_t conv_ws(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
   const int64_t nt = (int64_t)a.N * ((a.H + R - 1) / R) * ((a.W + 127) / 128) * (a.Cout / BN);
   const int grid = (int)std::min<int64_t>(nt, sm_count());
   if (grid < 1) return cudaSuccess;
-  k_conv3x3_ws<BN, R, CW><<<grid, kWsThreads, smem, s>>>(a, stages, err, tin, twt);
+  HeadOut ho;
+  memset(&ho, 0, sizeof ho);
+  if (head_out) ho = *head_out;
+  k_conv3x3_ws<BN, R, CW><<<grid, kWsThreads, smem, s>>>(a, stages, err, tin, twt, ho);
   return cudaGetLastError();
 }
 
@@ -413,7 +416,13 @@ cudaError_t conv_halo_cc(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
 // mode: 0 mma.sync, 1 tcgen05 implicit GEMM, 2 tcgen05 with halo reuse,
 // 3 the same with the input row segments staged by TMA, 4 persistent
 // warp-specialised halo reuse (TMA ring, two TMEM accumulators)
-cudaError_t conv(const ConvArgs& a, cudaStream_t s, uint32_t* tc_err = nullptr, int mode = 2) {
+cudaError_t conv(const ConvArgs& a, cudaStream_t s, uint32_t* tc_err = nullptr, int mode = 2,
+                 const HeadOut* head_out = nullptr) {
+  if (head_out) {
+    // the network's output from the head's epilogue: persistent path, 16 channels
+    if (!tc_err || mode != 4 || a.Cout != 16 || a.Cin % 16 || a.out || a.out_f32) return cudaErrorInvalidValue;
+    return a.Cin % 32 == 0 ? conv_ws<16, 8, 32>(a, tc_err, s, head_out) : conv_ws<16, 8, 16>(a, tc_err, s, head_out);
+  }
   if (tc_err && mode == 4 && a.Cin % 16 == 0 && a.Cout % 16 == 0) {
     if (a.Cin % 32 == 0) {
       if (a.Cout % 64 == 0) return conv_ws<64, 4, 32>(a, tc_err, s);
@@ -779,10 +788,25 @@ cudaError_t forward(sg_unet* u, const Crops& c, int N, int h, int w, float* out,
   if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
   a = conv_args(u, D1B, u->a5, 32, 0, N, h, w); a.out = u->d1; a.out_stride = 32; a.out_off = 0;
   if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
-  a = conv_args(u, HEAD, u->d1, 32, 0, N, h, w); a.out_f32 = u->head; a.f32_stride = 16; a.f32_off = 0;
-  if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
+  a = conv_args(u, HEAD, u->d1, 32, 0, N, h, w);
+  if (u->tc == 4) {
+    // the persistent path writes the output from the head's epilogue
+    HeadOut ho;
+    memset(&ho, 0, sizeof ho);
+    for (int n = 0; n < N; ++n) {
+      ho.in[n] = c.ptr[n];
+      ho.out[n] = out_ptrs ? out_ptrs[n] : out + (size_t)n * 2 * h * out_pitch;
+    }
+    ho.in_pitch = c.pitch;
+    ho.out_pitch = out_pitch;
+    ho.on = 1;
+    if ((e = conv(a, s, u->d_err, 4, &ho))) return e;
+  } else {
+    a.out_f32 = u->head; a.f32_stride = 16; a.f32_off = 0;
+    if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
+  }
   // out = bilinear 2x (half-pixel centres, clamp) of the input + pixel shuffle of the head
-  {
+  if (u->tc != 4) {
     const float* head = u->head;
     const int H2 = 2 * h, W2 = 2 * w;
     OutPtrs op;

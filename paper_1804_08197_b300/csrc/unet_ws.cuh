@@ -109,10 +109,53 @@ __device__ __forceinline__ uint64_t ws_desc(uint32_t addr, uint32_t sbo, uint32_
          (1ull << 46) | ((uint64_t)mode << 61);
 }
 
+// The network's output written by the head convolution's epilogue (its 16
+// channels per half-rate pixel): out = bilinear 2x upsampling of the RGBA
+// input (half-pixel centres, edges clamped) + pixel shuffle of the head.
+struct HeadOut {
+  const float* in[64];          // per image: RGBA input rows, in_pitch floats apart
+  float* out[64];               // per image: RGBA output rows (2H x 2W), out_pitch floats apart
+  int64_t in_pitch, out_pitch;
+  int on;                       // 0: the convolution writes out / out_f32 as usual
+};
+
+// output pixels (2y + sy, 2x + sx) of image n from the head's 16 values v
+__device__ __forceinline__ void ws_head_out(const HeadOut& ho, int n, int y, int x, int H, int W, const float* v) {
+  const float* src = ho.in[n];
+  float4 nb[3][3];  // the clamped 3 x 3 neighbourhood of the input pixel
+#pragma unroll
+  for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) {
+      const int yy = min(max(y + dy - 1, 0), H - 1), xx = min(max(x + dx - 1, 0), W - 1);
+      nb[dy][dx] = *reinterpret_cast<const float4*>(src + (int64_t)yy * ho.in_pitch + xx * 4);
+    }
+#pragma unroll
+  for (int sy = 0; sy < 2; ++sy)
+#pragma unroll
+    for (int sx = 0; sx < 2; ++sx) {
+      const int Y = 2 * y + sy, X = 2 * x + sx;
+      const float ux = 0.5f * X - 0.25f, uy = 0.5f * Y - 0.25f;
+      const float fx0 = floorf(ux), fy0 = floorf(uy);
+      const float fx = ux - fx0, fy = uy - fy0;
+      const int x0 = min(max((int)fx0, 0), W - 1) - x + 1, x1 = min(max((int)fx0 + 1, 0), W - 1) - x + 1;
+      const int y0 = min(max((int)fy0, 0), H - 1) - y + 1, y1 = min(max((int)fy0 + 1, 0), H - 1) - y + 1;
+      const float4 v00 = nb[y0][x0], v01 = nb[y0][x1], v10 = nb[y1][x0], v11 = nb[y1][x1];
+      const float a00 = (1.f - fy) * (1.f - fx), a01 = (1.f - fy) * fx, a10 = fy * (1.f - fx), a11 = fy * fx;
+      const int sh = sy * 2 + sx;
+      float4 o;
+      o.x = a00 * v00.x + a01 * v01.x + a10 * v10.x + a11 * v11.x + v[sh];
+      o.y = a00 * v00.y + a01 * v01.y + a10 * v10.y + a11 * v11.y + v[sh + 4];
+      o.z = a00 * v00.z + a01 * v01.z + a10 * v10.z + a11 * v11.z + v[sh + 8];
+      o.w = a00 * v00.w + a01 * v01.w + a10 * v10.w + a11 * v11.w + v[sh + 12];
+      *reinterpret_cast<float4*>(ho.out[n] + (int64_t)Y * ho.out_pitch + X * 4) = o;
+    }
+}
+
 template <int BN, int R, int CW>
 __global__ void __launch_bounds__(kWsThreads, 1)
     k_conv3x3_ws(ConvArgs a, int stages, uint32_t* err, const __grid_constant__ CUtensorMap tin,
-                 const __grid_constant__ CUtensorMap twt) {
+                 const __grid_constant__ CUtensorMap twt, const __grid_constant__ HeadOut ho) {
   using S = WsShape<BN, R, CW>;
   constexpr int kAcc = R * BN;  // TMEM columns of one accumulator
   constexpr int kCols =
@@ -332,6 +375,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
               o[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
               o[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
             }
+            if (BN == 16 && ho.on) ws_head_out(ho, n, y, x, a.H, a.W, v);
             if (a.out_f32) {
               float4* o = reinterpret_cast<float4*>(a.out_f32 + pr * a.f32_stride + a.f32_off + n0 + c0);
 #pragma unroll
