@@ -115,28 +115,40 @@ __global__ void k_sub_empty(TFParams p, const uint16_t* __restrict__ subrange, i
 // max-plus erosion g'(i) = min over j on the octant's side of i of
 // max(|i - j|, g(j)), one column per thread in registers.
 constexpr int kDistInf = 255;
+// One column, in place in shared memory, entries taken in the scan order so
+// that every read sees an input value. The scan of entry i stops once the
+// distance |j - i| reaches the best value so far (no farther entry can lower
+// it), and a column holding only "nothing ahead" (kDistInf) stays as it is:
+// the same result as the full min over the side, at a fraction of the work.
 __device__ __forceinline__ void erode_column(uint8_t* __restrict__ base, int stride, int n, int sgn) {
-  uint8_t g[kMaxSubPerEdge];
-#pragma unroll
-  for (int j = 0; j < kMaxSubPerEdge; ++j)
-    if (j < n) g[j] = base[j * stride];
-  for (int i = 0; i < n; ++i) {
-    int best = kDistInf;
-#pragma unroll
-    for (int j = 0; j < kMaxSubPerEdge; ++j) {
-      const int dj = (j - i) * sgn;
-      if (j < n && dj >= 0) best = min(best, max(dj, (int)g[j]));
+  bool all_inf = true;
+  for (int j = 0; j < n && all_inf; ++j) all_inf = base[j * stride] == kDistInf;
+  if (all_inf) return;
+  if (sgn > 0) {
+    for (int i = 0; i < n; ++i) {
+      int best = kDistInf;
+      for (int j = i; j < n && j - i < best; ++j) best = min(best, max(j - i, (int)base[j * stride]));
+      base[i * stride] = (uint8_t)best;
     }
-    base[i * stride] = (uint8_t)best;
+  } else {
+    for (int i = n - 1; i >= 0; --i) {
+      int best = kDistInf;
+      for (int j = i; j >= 0 && i - j < best; --j) best = min(best, max(i - j, (int)base[j * stride]));
+      base[i * stride] = (uint8_t)best;
+    }
   }
 }
 
 __global__ void k_sub_dist(const uint64_t* __restrict__ bits, int nsub, int words, uint8_t* __restrict__ dist,
                            const int32_t* __restrict__ slot_list) {
-  extern __shared__ uint8_t sd[];
+  extern __shared__ uint64_t sdw[];
   const int64_t slot = slot_list ? slot_list[blockIdx.x] : blockIdx.x;
   const int n = nsub, n2 = nsub * nsub, ns3 = n2 * nsub;
-  const uint64_t* w = bits + slot * words;
+  // the brick's transparency bits, then the distance map being built
+  uint64_t* w = sdw;
+  uint8_t* sd = reinterpret_cast<uint8_t*>(sdw + words);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) w[i] = bits[slot * words + i];
+  __syncthreads();
   for (int oct = 0; oct < 8; ++oct) {
     const int sx = (oct & 1) ? -1 : 1, sy = (oct & 2) ? -1 : 1, sz = (oct & 4) ? -1 : 1;
     // x: distance to the nearest non-transparent sub-block ahead in the row
@@ -250,7 +262,8 @@ cudaError_t launch_tf_flags(sg_volume* v, cudaStream_t s, const int32_t* d_slots
   const int64_t words = nsl * v->sub_words;
   k_sub_empty<<<grid_for(words, 128), 128, 0, s>>>(p, v->d_subrange, nsl, ns3, v->sub_words, v->d_subempty, d_slots);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_sub_dist<<<(unsigned)nsl, 256, ns3, s>>>(v->d_subempty, v->nsub, v->sub_words, v->d_subdist, d_slots);
+  k_sub_dist<<<(unsigned)nsl, 256, ns3 + v->sub_words * sizeof(uint64_t), s>>>(v->d_subempty, v->nsub, v->sub_words,
+                                                                               v->d_subdist, d_slots);
   return cudaGetLastError();
 }
 
