@@ -729,6 +729,15 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     del d0
     sg.sg_set_transfer_function(vol, 0, tf_table, *WINDOW)
+    # a transfer-function edit: tables, node flags, sub-block flags and the
+    # directional distance maps of every brick, until the GPU is done
+    tf_ms = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sg.sg_set_transfer_function(vol, 0, tf_table, *WINDOW)
+        torch.cuda.synchronize()
+        tf_ms.append((time.perf_counter() - t0) * 1e3)
     stream = torch.cuda.current_stream()
     outs = [torch.empty((H_EYE, W_EYE, 4), dtype=torch.float32, device=dev) for _ in range(2)]
     total = torch.zeros(1, dtype=torch.int64, device=dev)
@@ -923,6 +932,7 @@ def run_ours(args, rank, world, local_rank):
                         "mode": "sg_render_host_async, two frames in flight",
                         "serial_value": round(e2e_serial_s and e2e_steps / e2e_serial_s, 3)},
                 "select_stats_last": sel_stats,
+                "tf_edit_ms": round(min(tf_ms), 3),
                 "optical_models": modes,
                 "lens_warped": warped_line}
         if cpu:
