@@ -149,7 +149,8 @@ __global__ void k_sub_dist(const uint64_t* __restrict__ bits, int nsub, int word
   uint8_t* sd = reinterpret_cast<uint8_t*>(sdw + words);
   for (int i = threadIdx.x; i < words; i += blockDim.x) w[i] = bits[slot * words + i];
   __syncthreads();
-  for (int oct = 0; oct < 8; ++oct) {
+  {
+    const int oct = blockIdx.y;  // one octant of ray directions per CTA
     const int sx = (oct & 1) ? -1 : 1, sy = (oct & 2) ? -1 : 1, sz = (oct & 4) ? -1 : 1;
     // x: distance to the nearest non-transparent sub-block ahead in the row
     for (int r = threadIdx.x; r < n2; r += blockDim.x) {
@@ -262,8 +263,8 @@ cudaError_t launch_tf_flags(sg_volume* v, cudaStream_t s, const int32_t* d_slots
   const int64_t words = nsl * v->sub_words;
   k_sub_empty<<<grid_for(words, 128), 128, 0, s>>>(p, v->d_subrange, nsl, ns3, v->sub_words, v->d_subempty, d_slots);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_sub_dist<<<(unsigned)nsl, 256, ns3 + v->sub_words * sizeof(uint64_t), s>>>(v->d_subempty, v->nsub, v->sub_words,
-                                                                               v->d_subdist, d_slots);
+  k_sub_dist<<<dim3((unsigned)nsl, 8), 256, ns3 + v->sub_words * sizeof(uint64_t), s>>>(
+      v->d_subempty, v->nsub, v->sub_words, v->d_subdist, d_slots);
   return cudaGetLastError();
 }
 
