@@ -28,7 +28,12 @@ MAX_LEVELS = 16
 MAX_CH = 4
 
 ST_UNSEEN, ST_CULLED, ST_EMPTY, ST_SELECTED, ST_FALLBACK, ST_REFINED = range(6)
-FL_FACE, FL_TEDGE, FL_TERM, FL_COUNT = 1, 2, 4, 8
+# pixel flags of Volume.render: FL_FACE / FL_TEDGE mark pixels with lattice
+# points within eps of a face between differently sampled cells / of the
+# ray's end (resolved: every legitimate assignment is enumerated), FL_TERM a
+# termination decision within term_tol, FL_ENTRY an eye within eps of a
+# volume face and FL_MANY more assignments than the cap (both unresolved)
+FL_FACE, FL_TEDGE, FL_TERM, FL_ENTRY, FL_MANY = 1, 2, 4, 8, 16
 MODE_EA, MODE_EMISSION, MODE_MIP = 0, 1, 2
 
 
@@ -72,6 +77,9 @@ def _load():
         L.or_classify.argtypes = [vp, vp, dbl, vp]
         L.or_render.argtypes = [vp, vp, vp, vp, vp, i32, i32, dbl, dbl, dbl, dbl, vp, i64,
                                 vp, vp, vp, vp, vp, i32, i32, vp, vp]
+        L.or_render_variants.argtypes = [vp, vp, vp, vp, vp, i32, i32, dbl, dbl, dbl, dbl, vp, i64, i32,
+                                         vp, vp, vp, vp, vp, i32, i32, vp, vp]
+        L.or_render_variants.restype = i32
         L.or_lens_unwarp_point.argtypes = [vp, dbl, dbl, vp, vp]
         L.or_unwarp.argtypes = [vp, vp, i32, i32, vp, i32, i32]
         L.or_render.restype = i32
@@ -239,34 +247,79 @@ class Volume:
         return _load().or_sample(ctypes.byref(self._s), int(L), int(c), _p(pp))
 
     def render(self, tfs, leaf, view, proj, W, H, step=0.5, term=0.99, term_tol=1e-4, eps=1e-3,
-               pixels=None, nthreads=0, mode=MODE_EA, depth=None, lens=None):
+               pixels=None, nthreads=0, mode=MODE_EA, depth=None, lens=None, variants=True, var_cap=256):
         """Cast rays for `pixels` (flat ids j*W+i; None = all). Returns dict
-        with early/late RGBA (n,4) FP64, sample counts and flags.
+        with early/late RGBA (n,4) FP64, sample counts and flags, all for the
+        exact assignment of lattice points to cells.
 
         mode: MODE_EA (emission-absorption), MODE_EMISSION (emission only),
         MODE_MIP (maximum intensity projection). depth: optional (H, W)
         distances in world units from the eye along each pixel's ray to an
         opaque surface that ends the ray (inf = none); converted to level-0
         voxels with the model's uniform scale. lens: a Lens for rays through
-        the warped image (W x H is then the warped image's size)."""
+        the warped image (W x H is then the warped image's size).
+
+        variants: for every pixel flagged FL_FACE or FL_TEDGE, also every
+        legitimate result (one per assignment of its ambiguous lattice
+        points, at most var_cap): var_idx (positions of those pixels in this
+        result) and var_groups, a list of dicts with idx (positions), n
+        (results per pixel: 0 = more than the group's cap, -1 = in a later
+        group), early / late (m, k, 4) and count_early / count_late (m, k)."""
         pix = None if pixels is None else np.ascontiguousarray(pixels, np.int64)
-        tmax = None
-        if depth is not None:
-            m = np.asarray(self.model, np.float64).reshape(4, 4).T  # column-major -> row-major
-            voxel = np.linalg.norm(m[:3, 0])
-            tmax = np.ascontiguousarray(np.asarray(depth, np.float64).reshape(-1) / voxel)
+        tmax = self._tmax(depth)
         n = W * H if pix is None else len(pix)
         e = np.zeros((n, 4)); l = np.zeros((n, 4))
         ce = np.zeros(n, np.uint32); cl = np.zeros(n, np.uint32); fl = np.zeros(n, np.uint8)
         v = np.ascontiguousarray(np.asarray(view, np.float64).reshape(16))
         p = np.ascontiguousarray(np.asarray(proj, np.float64).reshape(16))
-        ok = _load().or_render(ctypes.byref(self._s), _tf_array(tfs), _p(np.ascontiguousarray(leaf, np.int32)),
-                               _p(v), _p(p), W, H, step, term, term_tol, eps, _p(pix), n,
-                               _p(e), _p(l), _p(ce), _p(cl), _p(fl), int(nthreads), int(mode), _p(tmax),
+        lf = np.ascontiguousarray(leaf, np.int32)
+        tfa = _tf_array(tfs)
+        ok = _load().or_render(ctypes.byref(self._s), tfa, _p(lf), _p(v), _p(p), W, H, step, term, term_tol, eps,
+                               _p(pix), n, _p(e), _p(l), _p(ce), _p(cl), _p(fl), int(nthreads), int(mode), _p(tmax),
                                ctypes.byref(lens) if lens is not None else None)
         if not ok:
             raise ValueError("singular view/projection/model matrix")
-        return dict(early=e, late=l, count_early=ce, count_late=cl, flags=fl)
+        out = dict(early=e, late=l, count_early=ce, count_late=cl, flags=fl)
+        if variants:
+            idx = np.flatnonzero(fl & (FL_FACE | FL_TEDGE))
+            ids = np.ascontiguousarray(idx if pix is None else pix[idx], np.int64)
+            args = (tfa, lf, v, p, W, H, step, term, term_tol, eps, nthreads, mode, tmax, lens)
+            groups = []
+            first = self._variants(args, ids, 32)
+            over = first["n"] == 0
+            first["idx"] = idx
+            groups.append(first)
+            if over.any():
+                # the few pixels with many assignments, with a larger cap
+                second = self._variants(args, ids[over], var_cap)
+                second["idx"] = idx[over]
+                first["n"][over] = -1  # handled by the second group
+                groups.append(second)
+            out["var_groups"] = groups
+            out["var_idx"] = idx
+        return out
+
+    def _variants(self, args, ids, cap):
+        tfa, lf, v, p, W, H, step, term, term_tol, eps, nthreads, mode, tmax, lens = args
+        m = len(ids)
+        ve = np.zeros((m, cap, 4)); vl = np.zeros((m, cap, 4))
+        vce = np.zeros((m, cap), np.uint32); vcl = np.zeros((m, cap), np.uint32)
+        vn = np.zeros(m, np.int32)
+        if m:
+            _load().or_render_variants(ctypes.byref(self._s), tfa, _p(lf), _p(v), _p(p), W, H, step, term, term_tol,
+                                       eps, _p(np.ascontiguousarray(ids, np.int64)), m, int(cap), _p(ve), _p(vl),
+                                       _p(vce), _p(vcl), _p(vn), int(nthreads), int(mode), _p(tmax),
+                                       ctypes.byref(lens) if lens is not None else None)
+        k = max(int(vn.max()) if m else 1, 1)
+        return dict(n=vn, early=ve[:, :k].copy(), late=vl[:, :k].copy(), count_early=vce[:, :k].copy(),
+                    count_late=vcl[:, :k].copy())
+
+    def _tmax(self, depth):
+        if depth is None:
+            return None
+        m = np.asarray(self.model, np.float64).reshape(4, 4).T  # column-major -> row-major
+        voxel = np.linalg.norm(m[:3, 0])
+        return np.ascontiguousarray(np.asarray(depth, np.float64).reshape(-1) / voxel)
 
 
 def tf_table(tf, spacing):

@@ -565,7 +565,16 @@ static void palette_rgb(const or_tf* tf, double d, double* rgb) {
 /* ------------------------------------------------------------------------ */
 /* ray casting                                                               */
 
-enum { FL_FACE = 1, FL_TEDGE = 2, FL_TERM = 4, FL_COUNT = 8 };
+/* Pixel flags. FL_FACE: a lattice point lies within eps of a face between
+ * cells whose sampling differs (two levels, or a dropped cell next to a
+ * rendered one); FL_TEDGE: a lattice point lies within eps of where the ray
+ * ends (the volume's exit face or a depth-buffer surface). Both are resolved
+ * by enumerating the legitimate assignments (or_render_variants). FL_TERM:
+ * the termination threshold test is within term_tol. FL_ENTRY: the eye lies
+ * within eps of a volume face, so the lattice anchor itself is uncertain;
+ * FL_MANY: more assignments than the enumeration's cap. These two are not
+ * resolved. */
+enum { FL_FACE = 1, FL_TEDGE = 2, FL_TERM = 4, FL_ENTRY = 8, FL_MANY = 16 };
 
 /* Optical models ("DVR Techniques"): emission-absorption (front-to-back
  * compositing with early termination), emission-only (the integral of the
@@ -687,217 +696,426 @@ static void cell_of(const ray_t* r, const double* p, double shift, const int* di
   }
 }
 
-/* One ray, FP64. Two compositing results bracket the termination decision:
- * "early" stops after the first sample with A >= term - term_tol, "late"
- * after the first with A >= term + term_tol (they differ only when a sample
- * lands within term_tol of the threshold). Flags mark pixels where an FP32
- * implementation may legitimately assign a sample differently: a sample
- * within eps of a face between cells rendered at different levels (FL_FACE),
- * a sample within eps of the volume exit (FL_TEDGE), or a differing
- * termination (FL_TERM). */
-static void cast(const ray_t* r, int64_t pix, double* early, double* late, uint32_t* ne, uint32_t* nl,
-                 uint8_t* flag) {
+/* ---- one ray: the lattice walk ------------------------------------------
+ *
+ * The ray takes the lattice points t0 + k step (k >= 0) in order; the point
+ * belongs to the level-0 cell containing it, and the selected block rendering
+ * that cell (level L) takes it iff k is a multiple of 2^L, sampling level L
+ * there. The ray ends at the first point at or beyond t1 (volume exit or
+ * depth-buffer surface), or after the sample that makes A >= term.
+ *
+ * Where exact arithmetic puts a point within eps of a face between cells
+ * that would treat it differently, or within eps of the ray's end, a
+ * floating-point implementation may legitimately assign it either way. Each
+ * such point is a branch point with its candidate behaviours (sample at
+ * level L, skip, or end the ray). The exact walk takes the exact assignment
+ * everywhere; the enumeration walks every combination, with one constraint
+ * that follows from the geometry: along a run of consecutive points near
+ * one face (a ray grazing it) the ray crosses that face once, so once a
+ * point of the run is given the far side, the later ones are too. */
+
+enum { BEH_SKIP = -1, BEH_END = -2 };
+
+typedef struct {
+  double o[3], d[3];
+  double t0, t1box, tsurf;
+  uint8_t entry_flag;
+} geom_t;
+
+typedef struct {
+  int64_t k;
+  double C[3], A, Ce[3], Ae;
+  uint32_t cnt, cnte;
+  int early_done;
+  double vmax[OR_MAX_CH], tat[OR_MAX_CH];
+  int any;
+  int run_ax;      /* face run in progress: axis, -1 for none */
+  double run_face; /* its plane, level-0 voxels */
+  int run_far;     /* the walk has given a point of the run the far side */
+} walk_t;
+
+typedef struct {
+  int cap, n, overflow;
+  double* early; /* [cap][4] */
+  double* late;  /* [cap][4] */
+  uint32_t* ce;  /* [cap] */
+  uint32_t* cl;  /* [cap] */
+  uint8_t flags;
+} leaves_t;
+
+#define OR_MAX_CAND 10
+
+typedef struct {
+  int n;
+  int beh[OR_MAX_CAND];
+  int far[OR_MAX_CAND]; /* 1: this candidate is the far side of the current run's face */
+  int exact;            /* index of the exact assignment */
+  uint8_t kind;         /* FL_FACE and/or FL_TEDGE when n > 1 */
+} cand_t;
+
+static int geom_setup(const ray_t* r, int64_t pix, geom_t* g) {
   int i = (int)(pix % r->W), j = (int)(pix / r->W);
   double x = 2.0 * (i + 0.5) / r->W - 1.0, y = 1.0 - 2.0 * (j + 0.5) / r->H;
   if (r->lens) lens_warp_to_undistorted(r->lens, x, y, &x, &y);
   double pn[4] = {x, y, -1.0, 1.0}, pf[4] = {x, y, 1.0, 1.0}, a[4], b[4];
   mat_apply(r->inv, pn, a);
   mat_apply(r->inv, pf, b);
-  double d[3], dn = 0.0;
-  for (int k = 0; k < 3; ++k) { d[k] = b[k] / b[3] - a[k] / a[3]; dn += d[k] * d[k]; }
+  double dn = 0.0;
+  for (int k = 0; k < 3; ++k) { g->d[k] = b[k] / b[3] - a[k] / a[3]; dn += g->d[k] * g->d[k]; }
   dn = sqrt(dn);
-  for (int k = 0; k < 3; ++k) d[k] /= dn;
-  const double* o = r->eye;
+  for (int k = 0; k < 3; ++k) { g->d[k] /= dn; g->o[k] = r->eye[k]; }
   double tn = -INFINITY, tf = INFINITY;
-  uint8_t fl = 0;
   for (int k = 0; k < 3; ++k) {
     double N = (double)r->v->dims[0][k];
-    if (d[k] == 0.0) {
-      if (o[k] < 0.0 || o[k] > N) { tf = -INFINITY; break; }
+    if (g->d[k] == 0.0) {
+      if (g->o[k] < 0.0 || g->o[k] > N) { tf = -INFINITY; break; }
       continue;
     }
-    double t1 = (0.0 - o[k]) / d[k], t2 = (N - o[k]) / d[k];
+    double t1 = (0.0 - g->o[k]) / g->d[k], t2 = (N - g->o[k]) / g->d[k];
     if (t1 > t2) { double t = t1; t1 = t2; t2 = t; }
     if (t1 > tn) tn = t1;
     if (t2 < tf) tf = t2;
   }
-  double t0 = tn > 0.0 ? tn : 0.0, t1 = tf;
+  g->t0 = tn > 0.0 ? tn : 0.0;
+  g->t1box = tf;
   /* depth-buffer termination: an opaque surface at tmax ends the ray
    * ("Volumetric and Mesh Data Compositing") */
-  const double tsurf = r->tmax ? r->tmax[pix] : INFINITY;
-  if (tsurf < t1) t1 = tsurf;
-  double vmax[OR_MAX_CH], tat[OR_MAX_CH];
-  int any = 0;
-  for (int c = 0; c < OR_MAX_CH; ++c) { vmax[c] = -INFINITY; tat[c] = 0.0; }
-  double C[3] = {0, 0, 0}, A = 0.0, Ce[3] = {0, 0, 0}, Ae = 0.0;
-  uint32_t cnt = 0, cnte = 0;
-  int early_done = 0;
-  if (t1 > t0) {
-    if (fabs(tn) < r->eps) fl |= FL_TEDGE;
-    int nch = r->v->nch;
-    for (int64_t k = 0;; ++k) {
-      double t = t0 + (double)k * r->step;
-      if (t >= t1) {
-        if (t - t1 < r->eps) fl |= FL_TEDGE;
-        break;
-      }
-      if (t1 - t < r->eps) fl |= FL_TEDGE;
-      double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
-      int zero[3] = {0, 0, 0};
-      int64_t cell[3];
-      cell_of(r, p, 0.0, zero, cell);
-      int32_t id = cell_at(r, cell);
-      int L = node_level(r, id);
-      /* face proximity: the cells within eps of p, all sign combinations.
-       * Two rendered levels that differ, or a dropped (transparent) cell next
-       * to a block of level > 0, can change the value (FL_FACE). A dropped
-       * cell next to a level-0 block cannot: the dropped subtree's level-0
-       * ranges include the one-voxel apron, so the sample's alpha is exactly
-       * 0 wherever it is assigned; only the sample count may differ
-       * (FL_COUNT). */
-      if (!(fl & FL_FACE)) {
-        int near_ax[3], nnear = 0;
-        for (int ax = 0; ax < 3; ++ax) {
-          double fr = p[ax] / (double)r->v->brick;
-          double dist = fabs(fr - floor(fr + 0.5)) * (double)r->v->brick;
-          near_ax[ax] = dist < r->eps;
-          nnear += near_ax[ax];
-        }
-        if (nnear) {
-          int used = (L >= 0 && (k & (((int64_t)1 << L) - 1)) == 0);
-          int value = 0, count = 0;
-          for (int m = 0; m < 8; ++m) {
-            int dirs[3];
-            int skip = 0;
-            for (int ax = 0; ax < 3; ++ax) {
-              dirs[ax] = (m >> ax) & 1 ? 1 : -1;
-              if (!near_ax[ax] && ((m >> ax) & 1)) skip = 1;
-              if (!near_ax[ax]) dirs[ax] = 0;
-            }
-            if (skip) continue;
-            int64_t c2[3];
-            cell_of(r, p, r->eps, dirs, c2);
-            int32_t id2 = cell_at(r, c2);
-            int L2 = node_level(r, id2);
-            if (L2 != L) {
-              if ((L >= 0 && L2 >= 0) || L > 0 || L2 > 0) value = 1;
-              else count = 1;
-            }
-            if (L2 >= 0 && (k & (((int64_t)1 << L2) - 1)) == 0) used = 1;
-          }
-          if (used && value) fl |= FL_FACE;
-          if (used && count) fl |= FL_COUNT;
-        }
-      }
-      if (L < 0 || (k & (((int64_t)1 << L) - 1)) != 0) continue;
-      if (r->mode == OR_MODE_MIP) {
-        /* the maximum table input per channel (the first sample that
-         * reaches it keeps its distance), classified after the loop */
-        for (int c = 0; c < nch; ++c) {
-          double val = tf_input(r, L, c, p);
-          if (val > vmax[c]) { vmax[c] = val; tat[c] = t; }
-        }
-        any = 1;
-        ++cnt;
-        continue;
-      }
-      if (r->mode == OR_MODE_EMISSION) {
-        /* emitted intensity per level-0 voxel of path: the table's colour
-         * times its opacity for one reference step, over that step; a
-         * level-L sample stands for step * 2^L of path */
-        for (int c = 0; c < nch; ++c) {
-          double val = tf_input(r, L, c, p), rgba[4];
-          or_classify(&r->tf[c], r->raw[c], val, rgba);
-          if (r->tf[c].m > 0) palette_rgb(&r->tf[c], t * r->voxel, rgba);
-          double w = rgba[3] * (r->step * (double)((int64_t)1 << L)) / (double)r->tf[c].ref_step;
-          for (int q = 0; q < 3; ++q) C[q] += w * rgba[q];
-        }
-        ++cnt;
-        continue;
-      }
-      /* classify every channel, blend additively (alpha capped at 1) */
-      double sa = 0.0, sc[3] = {0, 0, 0};
-      for (int c = 0; c < nch; ++c) {
-        double val = tf_input(r, L, c, p), rgba[4];
-        or_classify(&r->tf[c], r->table[L][c], val, rgba);
-        if (r->tf[c].m > 0) palette_rgb(&r->tf[c], t * r->voxel, rgba);
-        sa += rgba[3];
-        for (int q = 0; q < 3; ++q) sc[q] += rgba[3] * rgba[q];
-      }
-      double as = sa < 1.0 ? sa : 1.0;
-      double scale = sa > 0.0 ? as / (sa > as ? sa : as) : 0.0;
-      for (int q = 0; q < 3; ++q) C[q] += (1.0 - A) * sc[q] * scale;
-      A += (1.0 - A) * as;
-      ++cnt;
-      if (!early_done && A >= r->term - r->term_tol) {
-        early_done = 1;
-        memcpy(Ce, C, sizeof C);
-        Ae = A;
-        cnte = cnt;
-      }
-      if (A >= r->term + r->term_tol) break;
+  g->tsurf = r->tmax ? r->tmax[pix] : INFINITY;
+  g->entry_flag = (tf > g->t0 && fabs(tn) < r->eps) ? FL_ENTRY : 0;
+  double t1 = tf < g->tsurf ? tf : g->tsurf;
+  return t1 > g->t0;
+}
+
+/* behaviour of the cell holding node id at lattice point k */
+static int cell_behaviour(const ray_t* r, int32_t id, int64_t k) {
+  int L = node_level(r, id);
+  if (L < 0) return BEH_SKIP;
+  return (k & (((int64_t)1 << L) - 1)) == 0 ? L : BEH_SKIP;
+}
+
+static void cand_add(cand_t* c, int beh, int far) {
+  for (int i = 0; i < c->n; ++i)
+    if (c->beh[i] == beh) {
+      if (!far) c->far[i] = 0; /* reachable without crossing */
+      return;
+    }
+  if (c->n < OR_MAX_CAND) {
+    c->beh[c->n] = beh;
+    c->far[c->n] = far;
+    ++c->n;
+  }
+}
+
+/* Candidate behaviours of lattice point k at distance t, position p. Updates
+ * the walk's face run. */
+static void candidates(const ray_t* r, const geom_t* g, walk_t* s, double t, const double* p, cand_t* c) {
+  const double B = (double)r->v->brick;
+  c->n = 0;
+  c->exact = 0;
+  c->kind = 0;
+  /* where the ray ends: out_dist = how far p lies outside the volume box,
+   * exit_dist = its distance to the nearest face the ray leaves through */
+  double out_dist = 0.0, exit_dist = INFINITY;
+  for (int a = 0; a < 3; ++a) {
+    const double N = (double)r->v->dims[0][a];
+    const double o = p[a] - N > -p[a] ? p[a] - N : -p[a];
+    if (o > out_dist) out_dist = o;
+    if (g->d[a] != 0.0) {
+      const double e = fabs(p[a] - (g->d[a] > 0.0 ? N : 0.0));
+      if (e < exit_dist) exit_dist = e;
     }
   }
-  if (r->mode == OR_MODE_MIP && any) {
+  const int inside = t < g->t1box && t < g->tsurf;
+  const int beyond = (t >= g->t1box && out_dist >= r->eps) || t >= g->tsurf + r->eps;
+  if (beyond) {
+    c->n = 1;
+    c->beh[0] = BEH_END;
+    c->far[0] = 0;
+    s->run_ax = -1;
+    return;
+  }
+  /* not beyond but not inside: within eps past the end */
+  const int end_amb = (t < g->t1box ? exit_dist < r->eps : out_dist < r->eps) || fabs(t - g->tsurf) < r->eps;
+  /* the cells around p: faces within eps on each axis (interior faces only) */
+  int zero[3] = {0, 0, 0};
+  int64_t ce[3];
+  cell_of(r, p, 0.0, zero, ce);
+  const int exact_beh = cell_behaviour(r, cell_at(r, ce), s->k);
+  int near_ax[3], nnear = 0, lone = -1;
+  double face[3];
+  for (int a = 0; a < 3; ++a) {
+    double f = floor(p[a] / B + 0.5) * B;
+    int64_t fi = (int64_t)floor(p[a] / B + 0.5);
+    near_ax[a] = fabs(p[a] - f) < r->eps && fi >= 1 && fi <= r->nb0[a] - 1;
+    face[a] = f;
+    if (near_ax[a]) { ++nnear; lone = a; }
+  }
+  if (nnear == 1) {
+    const int a = lone;
+    if (s->run_ax != a || s->run_face != face[a]) {
+      s->run_ax = a;
+      s->run_face = face[a];
+      s->run_far = 0;
+    }
+    int64_t lo[3] = {ce[0], ce[1], ce[2]}, hi[3] = {ce[0], ce[1], ce[2]};
+    lo[a] = (int64_t)(face[a] / B) - 1;
+    hi[a] = (int64_t)(face[a] / B);
+    const int blo = cell_behaviour(r, cell_at(r, lo), s->k), bhi = cell_behaviour(r, cell_at(r, hi), s->k);
+    /* near side: the one the ray comes from (for a ray in the face's plane,
+     * the exact one) */
+    int lo_near = g->d[a] > 0.0 ? 1 : (g->d[a] < 0.0 ? 0 : ce[a] == lo[a]);
+    const int bnear = lo_near ? blo : bhi, bfar = lo_near ? bhi : blo;
+    if (!s->run_far) cand_add(c, bnear, 0);
+    cand_add(c, bfar, 1);
+    if (c->n > 1) c->kind |= FL_FACE;
+  } else if (nnear > 1) {
+    s->run_ax = -1;
+    for (int m = 0; m < 8; ++m) {
+      int64_t cc[3];
+      int skip = 0;
+      for (int a = 0; a < 3; ++a) {
+        int side = (m >> a) & 1;
+        if (!near_ax[a]) {
+          if (side) skip = 1;
+          cc[a] = ce[a];
+        } else {
+          cc[a] = (int64_t)(face[a] / B) - 1 + side;
+        }
+      }
+      if (skip) continue;
+      cand_add(c, cell_behaviour(r, cell_at(r, cc), s->k), 0);
+    }
+    if (c->n > 1) c->kind |= FL_FACE;
+  } else {
+    s->run_ax = -1;
+    cand_add(c, exact_beh, 0);
+  }
+  if (end_amb) {
+    cand_add(c, BEH_END, 0);
+    if (c->n > 1) c->kind |= FL_TEDGE;
+  }
+  /* index of the exact assignment */
+  const int want = inside ? exact_beh : BEH_END;
+  for (int i = 0; i < c->n; ++i)
+    if (c->beh[i] == want) c->exact = i;
+}
+
+/* Takes the sample of lattice point s->k at level L. Returns 1 when the ray
+ * stops (A >= term + term_tol). */
+static int take_sample(const ray_t* r, walk_t* s, int L, double t, const double* p) {
+  const int nch = r->v->nch;
+  if (r->mode == OR_MODE_MIP) {
+    /* the maximum table input per channel (the first sample that reaches it
+     * keeps its distance), classified when the ray ends */
+    for (int c = 0; c < nch; ++c) {
+      double val = tf_input(r, L, c, p);
+      if (val > s->vmax[c]) { s->vmax[c] = val; s->tat[c] = t; }
+    }
+    s->any = 1;
+    ++s->cnt;
+    return 0;
+  }
+  if (r->mode == OR_MODE_EMISSION) {
+    /* emitted intensity per level-0 voxel of path: the table's colour times
+     * its opacity for one reference step, over that step; a level-L sample
+     * stands for step * 2^L of path */
+    for (int c = 0; c < nch; ++c) {
+      double val = tf_input(r, L, c, p), rgba[4];
+      or_classify(&r->tf[c], r->raw[c], val, rgba);
+      if (r->tf[c].m > 0) palette_rgb(&r->tf[c], t * r->voxel, rgba);
+      double w = rgba[3] * (r->step * (double)((int64_t)1 << L)) / (double)r->tf[c].ref_step;
+      for (int q = 0; q < 3; ++q) s->C[q] += w * rgba[q];
+    }
+    ++s->cnt;
+    return 0;
+  }
+  /* classify every channel, blend additively (alpha capped at 1) */
+  double sa = 0.0, sc[3] = {0, 0, 0};
+  for (int c = 0; c < nch; ++c) {
+    double val = tf_input(r, L, c, p), rgba[4];
+    or_classify(&r->tf[c], r->table[L][c], val, rgba);
+    if (r->tf[c].m > 0) palette_rgb(&r->tf[c], t * r->voxel, rgba);
+    sa += rgba[3];
+    for (int q = 0; q < 3; ++q) sc[q] += rgba[3] * rgba[q];
+  }
+  double as = sa < 1.0 ? sa : 1.0;
+  double scale = sa > 0.0 ? as / (sa > as ? sa : as) : 0.0;
+  for (int q = 0; q < 3; ++q) s->C[q] += (1.0 - s->A) * sc[q] * scale;
+  s->A += (1.0 - s->A) * as;
+  ++s->cnt;
+  if (!s->early_done && s->A >= r->term - r->term_tol) {
+    s->early_done = 1;
+    memcpy(s->Ce, s->C, sizeof s->C);
+    s->Ae = s->A;
+    s->cnte = s->cnt;
+  }
+  return s->A >= r->term + r->term_tol;
+}
+
+/* The ray has ended: finish MIP, record early/late results. */
+static void leaf(const ray_t* r, walk_t* s, leaves_t* out) {
+  if (r->mode == OR_MODE_MIP && s->any) {
     /* classify each channel's maximum with its table for one reference
      * step, blend the channels additively (alpha capped at 1), premultiply */
     double sa = 0.0, sc[3] = {0, 0, 0};
     for (int c = 0; c < r->v->nch; ++c) {
       double rgba[4];
-      or_classify(&r->tf[c], r->raw[c], vmax[c], rgba);
-      if (r->tf[c].m > 0) palette_rgb(&r->tf[c], tat[c] * r->voxel, rgba);
+      or_classify(&r->tf[c], r->raw[c], s->vmax[c], rgba);
+      if (r->tf[c].m > 0) palette_rgb(&r->tf[c], s->tat[c] * r->voxel, rgba);
       sa += rgba[3];
       for (int q = 0; q < 3; ++q) sc[q] += rgba[3] * rgba[q];
     }
     double as = sa < 1.0 ? sa : 1.0;
     double scale = sa > 0.0 ? as / (sa > as ? sa : as) : 0.0;
-    for (int q = 0; q < 3; ++q) C[q] = sc[q] * scale;
-    A = as;
+    for (int q = 0; q < 3; ++q) s->C[q] = sc[q] * scale;
+    s->A = as;
   }
-  if (!early_done) { memcpy(Ce, C, sizeof C); Ae = A; cnte = cnt; }
-  if (cnte != cnt) fl |= FL_TERM;
-  for (int q = 0; q < 3; ++q) { early[q] = Ce[q]; late[q] = C[q]; }
-  early[3] = Ae;
-  late[3] = A;
-  *ne = cnte;
-  *nl = cnt;
-  *flag = fl;
+  if (!s->early_done) {
+    memcpy(s->Ce, s->C, sizeof s->C);
+    s->Ae = s->A;
+    s->cnte = s->cnt;
+  }
+  if (s->cnte != s->cnt) out->flags |= FL_TERM;
+  if (out->n >= out->cap) {
+    out->overflow = 1;
+    return;
+  }
+  double* e = out->early + 4 * out->n;
+  double* l = out->late + 4 * out->n;
+  for (int q = 0; q < 3; ++q) { e[q] = s->Ce[q]; l[q] = s->C[q]; }
+  e[3] = s->Ae;
+  l[3] = s->A;
+  out->ce[out->n] = s->cnte;
+  out->cl[out->n] = s->cnt;
+  ++out->n;
+}
+
+/* Applies behaviour b at the walk's point. Returns 1 when the ray has ended. */
+static int apply(const ray_t* r, walk_t* s, int b, double t, const double* p) {
+  if (b == BEH_END) return 1;
+  if (b == BEH_SKIP) return 0;
+  return take_sample(r, s, b, t, p);
+}
+
+/* Walks the ray from s.k on. explore = 0: the exact assignment at every
+ * point (one leaf); explore = 1: every candidate at every branch point,
+ * depth-first (depth = branch points taken so far on this path). */
+#define OR_MAX_BRANCH_DEPTH 400
+
+static void walk(const ray_t* r, const geom_t* g, walk_t s, int explore, int depth, leaves_t* out) {
+  if (depth > OR_MAX_BRANCH_DEPTH) {
+    out->overflow = 1;
+    return;
+  }
+  for (;; ++s.k) {
+    if (out->overflow) return;
+    const double t = g->t0 + (double)s.k * r->step;
+    const double p[3] = {g->o[0] + t * g->d[0], g->o[1] + t * g->d[1], g->o[2] + t * g->d[2]};
+    cand_t c;
+    candidates(r, g, &s, t, p, &c);
+    if (c.n > 1) out->flags |= c.kind;
+    if (!explore || c.n == 1) {
+      const int i = explore ? 0 : c.exact;
+      if (c.far[i]) s.run_far = 1;
+      if (apply(r, &s, c.beh[i], t, p)) {
+        leaf(r, &s, out);
+        return;
+      }
+      continue;
+    }
+    for (int i = 0; i < c.n && !out->overflow; ++i) {
+      walk_t s2 = s;
+      if (c.far[i]) s2.run_far = 1;
+      if (apply(r, &s2, c.beh[i], t, p)) {
+        leaf(r, &s2, out);
+        continue;
+      }
+      s2.k += 1;
+      walk(r, g, s2, 1, depth + 1, out);
+    }
+    return;
+  }
+}
+
+static void walk_init(walk_t* s) {
+  memset(s, 0, sizeof *s);
+  for (int c = 0; c < OR_MAX_CH; ++c) s->vmax[c] = -INFINITY;
+  s->run_ax = -1;
+}
+
+/* One ray, FP64, exact assignment. Two compositing results bracket the
+ * termination decision: "early" stops after the first sample with
+ * A >= term - term_tol, "late" after the first with A >= term + term_tol
+ * (they differ only when a sample lands within term_tol of the threshold). */
+static void cast(const ray_t* r, int64_t pix, double* early, double* late, uint32_t* ne, uint32_t* nl,
+                 uint8_t* flag) {
+  geom_t g;
+  leaves_t out;
+  memset(&out, 0, sizeof out);
+  out.cap = 1;
+  out.early = early;
+  out.late = late;
+  out.ce = ne;
+  out.cl = nl;
+  walk_t s;
+  walk_init(&s);
+  if (!geom_setup(r, pix, &g)) {
+    for (int q = 0; q < 4; ++q) early[q] = late[q] = 0.0;
+    *ne = *nl = 0;
+    *flag = 0;
+    return;
+  }
+  walk(r, &g, s, 0, 0, &out);
+  *flag = out.flags | g.entry_flag;
+}
+
+static int ray_init(ray_t* r, const or_volume* v, const or_tf* tfs, const int32_t* leaf, const double* view,
+                    const double* proj, int W, int H, double step, double term, double term_tol, double eps, int mode,
+                    const double* tmax, const or_lens* lens) {
+  memset(r, 0, sizeof *r);
+  r->v = v; r->tf = tfs; r->leaf = leaf; r->W = W; r->H = H;
+  r->step = step; r->term = term; r->term_tol = term_tol; r->eps = eps;
+  r->mode = mode; r->tmax = tmax; r->lens = lens;
+  r->voxel = sqrt(v->model[0] * v->model[0] + v->model[1] * v->model[1] + v->model[2] * v->model[2]);
+  or_node_count(v, r->off);
+  level_blocks(v, 0, r->nb0);
+  double vm[16], pvm[16], vminv[16];
+  mat_mul(view, v->model, vm);
+  mat_mul(proj, vm, pvm);
+  if (!mat_inv(pvm, r->inv) || !mat_inv(vm, vminv)) return 0;
+  double o[4] = {0, 0, 0, 1}, e[4];
+  mat_apply(vminv, o, e);
+  for (int k = 0; k < 3; ++k) r->eye[k] = e[k] / e[3];
+  for (int c = 0; c < v->nch; ++c) {
+    r->raw[c] = (double*)malloc(sizeof(double) * 4 * tfs[c].n);
+    for (int i = 0; i < 4 * tfs[c].n; ++i) r->raw[c][i] = (double)tfs[c].rgba[i];
+  }
+  for (int L = 0; L < v->levels; ++L)
+    for (int c = 0; c < v->nch; ++c) {
+      r->table[L][c] = (double*)malloc(sizeof(double) * 4 * tfs[c].n);
+      or_tf_table(&tfs[c], step * (double)((int64_t)1 << L), r->table[L][c]);
+    }
+  return 1;
+}
+
+static void ray_free(ray_t* r) {
+  for (int L = 0; L < r->v->levels; ++L)
+    for (int c = 0; c < r->v->nch; ++c) free(r->table[L][c]);
+  for (int c = 0; c < r->v->nch; ++c) free(r->raw[c]);
 }
 
 /* Render the pixels pix[0..npix) (row-major ids j*W+i, row 0 = top; NULL
- * means every pixel) of one eye. leaf comes from or_select. step is the
- * level-0 sample spacing; level L samples every 2^L-th lattice point
- * t0 + k step, k >= 0, anchored at the volume entry t0. Returns 0 on a
- * singular matrix. nthreads <= 0 uses every core. */
+ * means every pixel) of one eye with the exact assignment. leaf comes from
+ * or_select. step is the level-0 sample spacing; level L samples every
+ * 2^L-th lattice point t0 + k step, k >= 0, anchored at the volume entry t0.
+ * Returns 0 on a singular matrix. nthreads <= 0 uses every core. */
 int or_render(const or_volume* v, const or_tf* tfs, const int32_t* leaf, const double* view,
               const double* proj, int W, int H, double step, double term, double term_tol, double eps,
               const int64_t* pix, int64_t npix, double* rgba_early, double* rgba_late, uint32_t* cnt_early,
               uint32_t* cnt_late, uint8_t* flags, int nthreads, int mode, const double* tmax,
               const or_lens* lens) {
   ray_t r;
-  memset(&r, 0, sizeof r);
-  r.v = v; r.tf = tfs; r.leaf = leaf; r.W = W; r.H = H;
-  r.step = step; r.term = term; r.term_tol = term_tol; r.eps = eps;
-  r.mode = mode; r.tmax = tmax; r.lens = lens;
-  r.voxel = sqrt(v->model[0] * v->model[0] + v->model[1] * v->model[1] + v->model[2] * v->model[2]);
-  or_node_count(v, r.off);
-  level_blocks(v, 0, r.nb0);
-  double vm[16], pvm[16], vminv[16];
-  mat_mul(view, v->model, vm);
-  mat_mul(proj, vm, pvm);
-  if (!mat_inv(pvm, r.inv) || !mat_inv(vm, vminv)) return 0;
-  double o[4] = {0, 0, 0, 1}, e[4];
-  mat_apply(vminv, o, e);
-  for (int k = 0; k < 3; ++k) r.eye[k] = e[k] / e[3];
-  for (int c = 0; c < v->nch; ++c) {
-    r.raw[c] = (double*)malloc(sizeof(double) * 4 * tfs[c].n);
-    for (int i = 0; i < 4 * tfs[c].n; ++i) r.raw[c][i] = (double)tfs[c].rgba[i];
-  }
-  for (int L = 0; L < v->levels; ++L)
-    for (int c = 0; c < v->nch; ++c) {
-      r.table[L][c] = (double*)malloc(sizeof(double) * 4 * tfs[c].n);
-      or_tf_table(&tfs[c], step * (double)((int64_t)1 << L), r.table[L][c]);
-    }
+  if (!ray_init(&r, v, tfs, leaf, view, proj, W, H, step, term, term_tol, eps, mode, tmax, lens)) return 0;
   int64_t n = pix ? npix : (int64_t)W * H;
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 64)
@@ -905,9 +1123,45 @@ int or_render(const or_volume* v, const or_tf* tfs, const int32_t* leaf, const d
     int64_t id = pix ? pix[q] : q;
     cast(&r, id, rgba_early + 4 * q, rgba_late + 4 * q, cnt_early + q, cnt_late + q, flags + q);
   }
-  for (int L = 0; L < v->levels; ++L)
-    for (int c = 0; c < v->nch; ++c) free(r.table[L][c]);
-  for (int c = 0; c < v->nch; ++c) free(r.raw[c]);
+  ray_free(&r);
+  return 1;
+}
+
+/* Every legitimate result of the pixels pix[0..npix): one per combination of
+ * candidate assignments at the ray's branch points (see the lattice walk
+ * above), at most cap per pixel, each with its early/late bracket. nvar[q]
+ * is the number written, 0 when the combinations exceed cap. Output layout:
+ * [npix][cap][4] RGBA and [npix][cap] counts. */
+int or_render_variants(const or_volume* v, const or_tf* tfs, const int32_t* leaf, const double* view,
+                       const double* proj, int W, int H, double step, double term, double term_tol, double eps,
+                       const int64_t* pix, int64_t npix, int cap, double* rgba_early, double* rgba_late,
+                       uint32_t* cnt_early, uint32_t* cnt_late, int32_t* nvar, int nthreads, int mode,
+                       const double* tmax, const or_lens* lens) {
+  ray_t r;
+  if (!ray_init(&r, v, tfs, leaf, view, proj, W, H, step, term, term_tol, eps, mode, tmax, lens)) return 0;
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t q = 0; q < npix; ++q) {
+    geom_t g;
+    leaves_t out;
+    memset(&out, 0, sizeof out);
+    out.cap = cap;
+    out.early = rgba_early + (size_t)4 * cap * q;
+    out.late = rgba_late + (size_t)4 * cap * q;
+    out.ce = cnt_early + (size_t)cap * q;
+    out.cl = cnt_late + (size_t)cap * q;
+    walk_t s;
+    walk_init(&s);
+    if (!geom_setup(&r, pix[q], &g)) {
+      for (int k = 0; k < 4; ++k) out.early[k] = out.late[k] = 0.0;
+      out.ce[0] = out.cl[0] = 0;
+      nvar[q] = 1;
+      continue;
+    }
+    walk(&r, &g, s, 1, 0, &out);
+    nvar[q] = out.overflow ? 0 : out.n;
+  }
+  ray_free(&r);
   return 1;
 }
 

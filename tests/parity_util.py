@@ -1,17 +1,18 @@
 """Shared helpers of the GPU parity tests: run one case through the C ABI
 (libsg.so) and through the FP64 oracle on the same seeded inputs, then compare.
 
-Image bar (tolerance 1e-3 per RGBA channel): for every pixel the oracle does
-not flag, the GPU value must lie within [min(early, late) - 1e-3,
-max(early, late) + 1e-3] per channel, where early/late are the oracle's
-results with the termination threshold moved by -/+1e-4 (equal unless a
-sample lands within 1e-4 of the threshold). Pixels with a sample within
-1e-3 voxel of a face between blocks of different levels, or of the volume
-exit, may legitimately differ by one sample's assignment; they are counted
-and must stay rare. Where a transparent (dropped) cell meets a level-0 block
-only the sample count can differ (the sample's alpha is exactly 0 either
-way), so those pixels keep the value check and skip the count check.
-Selections must match bit for bit."""
+Image bar (tolerance 1e-3 per RGBA channel). For a pixel whose ray has no
+ambiguous lattice point, the GPU value must lie within [min(early, late) -
+1e-3, max(early, late) + 1e-3] per channel, where early/late are the
+oracle's results with the termination threshold moved by -/+1e-4 (equal
+unless a sample lands within 1e-4 of the threshold), and its sample count
+within [count_early, count_late]. A pixel whose ray has lattice points within
+1e-3 voxel of a face between differently sampled cells, or of where the ray
+ends, may legitimately take them either way: the oracle enumerates every
+such assignment, and the GPU pixel must match one of them on all four
+channels and on the count. Pixels the oracle cannot resolve (an eye on a
+volume face, more assignments than the enumeration's cap) are counted and
+must not occur. Selections must match bit for bit."""
 import numpy as np
 
 import oracle
@@ -98,21 +99,57 @@ def compare_selection(gpu, ref):
     assert np.array_equal(np.sort(req), ref["requests"])
 
 
-def compare_image(img, ref, counts=None, max_flagged=0.01, tol=TOL):
-    """img: (n,4) GPU pixels matching ref's pixel order. Returns stats."""
+def compare_image(img, ref, counts=None, tol=TOL, max_unresolved=0):
+    """img: (n,4) GPU pixels matching ref's pixel order (ref from
+    oracle.Volume.render). Returns dict(max_err, max_err_ambiguous,
+    ambiguous, unresolved, n): the largest |gpu - oracle| over unambiguous
+    pixels, the largest distance to the best-matching variant over ambiguous
+    ones, the fraction of ambiguous pixels and the count of unresolved ones."""
     fl = ref["flags"]
-    strict = (fl & (oracle.FL_FACE | oracle.FL_TEDGE)) == 0
+    n = len(img)
+    amb = np.zeros(n, bool)
+    amb[ref["var_idx"]] = True
+    unres = (fl & (oracle.FL_ENTRY | oracle.FL_MANY)) != 0
+    for grp in ref["var_groups"]:
+        unres[grp["idx"][grp["n"] == 0]] = True
+    strict = ~amb & ~unres
     lo = np.minimum(ref["early"], ref["late"]) - tol
     hi = np.maximum(ref["early"], ref["late"]) + tol
     bad = strict[:, None] & ((img < lo) | (img > hi))
     err = np.where(strict[:, None], np.abs(img - ref["late"]), 0.0)
-    worst = np.unravel_index(np.argmax(err), err.shape)
+    worst = np.unravel_index(np.argmax(err), err.shape) if n else (0, 0)
     assert not bad.any(), (f"{np.count_nonzero(bad.any(1))} pixels outside tolerance; worst {err.max():.3g} at "
                            f"{worst}: gpu {img[worst[0]]} oracle {ref['late'][worst[0]]} flags {fl[worst[0]]}")
-    frac = 1.0 - strict.mean()
-    assert frac <= max_flagged, f"{frac:.4f} of pixels flagged"
     if counts is not None:
-        cstrict = strict & ((fl & oracle.FL_COUNT) == 0)
         ok = (counts >= ref["count_early"]) & (counts <= ref["count_late"])
-        assert ok[cstrict].all(), f"{np.count_nonzero(~ok[cstrict])} sample-count mismatches"
-    return dict(max_err=float(err.max()), flagged=float(frac), n=len(img))
+        assert ok[strict].all(), f"{np.count_nonzero(~ok[strict])} sample-count mismatches"
+    # ambiguous pixels: some enumerated assignment matches on every channel
+    # (and on the count)
+    amb_err = 0.0
+    for grp in ref["var_groups"]:
+        sel = grp["n"] > 0
+        idx = grp["idx"][sel]
+        if not len(idx):
+            continue
+        nv = grp["n"][sel]
+        ve, vl = grp["early"][sel], grp["late"][sel]
+        live = np.arange(ve.shape[1])[None, :] < nv[:, None]
+        g = img[idx][:, None, :]
+        vlo, vhi = np.minimum(ve, vl) - tol, np.maximum(ve, vl) + tol
+        match = ((g >= vlo) & (g <= vhi)).all(axis=2) & live
+        if counts is not None:
+            c = counts[idx][:, None]
+            match &= (c >= grp["count_early"][sel]) & (c <= grp["count_late"][sel])
+        dist = np.where(live, np.abs(g - vl).max(axis=2), np.inf)
+        amb_err = max(amb_err, float(dist.min(axis=1).max()))
+        miss = ~match.any(axis=1)
+        if miss.any():
+            i = int(np.flatnonzero(miss)[0])
+            j = int(np.argmin(dist[i]))
+            raise AssertionError(f"{int(miss.sum())} ambiguous pixels match none of their assignments; pixel "
+                                 f"{idx[i]}: gpu {img[idx[i]]} (count {None if counts is None else counts[idx[i]]}) "
+                                 f"nearest variant {vl[i, j]} of {nv[i]} flags {fl[idx[i]]}")
+    nunres = int(unres.sum())
+    assert nunres <= max_unresolved, f"{nunres} pixels the oracle cannot resolve (flags {np.unique(fl[unres])})"
+    return dict(max_err=float(err.max()) if n else 0.0, max_err_ambiguous=amb_err,
+                ambiguous=float(amb.mean()) if n else 0.0, unresolved=nunres, n=n)

@@ -124,9 +124,10 @@ def test_streaming_frames_match_the_oracle_and_evict_lru(mode, index_ranges=True
                     upload(gsel[2])
                     comp.synchronize()
                     # early frames mix levels (fallbacks next to refined
-                    # blocks), so more pixels sit near a face between levels
+                    # blocks): more pixels have points near a face between
+                    # levels, each resolved by the oracle's assignments
                     compare_image(outs[0].cpu().numpy().reshape(-1, 4),
-                                  ovol.render([otf], ref["leaf"], views[0], projs[0], W, H), max_flagged=0.05)
+                                  ovol.render([otf], ref["leaf"], views[0], projs[0], W, H))
                     continue
                 upload(gsel[2])
             assert stats["requested"] == 0 and stats["fallback"] == 0

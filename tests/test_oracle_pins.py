@@ -404,3 +404,147 @@ def test_depth_palette_colours_by_distance():
     s1 = q * (1 - m * q ** (m - 1) + (m - 1) * q ** m) / (1 - q) ** 2
     d = 0.3 / 16.0
     assert r["late"][0] == pytest.approx([ap * (s0 - d * s1), 0.0, ap * d * s1, 1 - q ** m], abs=1e-12)
+
+
+# ---------------------------------------------------------------- the multi-level sample lattice (Octree Representation)
+
+def _x_ray(eye_x, nx, levels, brick=8, a=0.01):
+    """Constant volume nx x 8 x 8 (value 100 at every level), a constant
+    table of opacity a per reference step 0.5, and a camera on the axis
+    y = z = 4 looking along +x (the centre pixel of a 9 x 9 image)."""
+    lv = [np.full((8, 8, nx), 100, np.uint8)]
+    for _ in range(1, levels):
+        s = lv[-1].shape
+        lv.append(np.full(((s[0] + 1) // 2, (s[1] + 1) // 2, (s[2] + 1) // 2), 100, np.uint8))
+    vol = oracle.Volume([lv], brick)
+    tf = _const_tf((0.25, 0.5, 1.0), float(np.float32(a)))
+    view = synth.colmajor(synth.look_at([eye_x, 4.0, 4.0], [eye_x + 1.0, 4.0, 4.0], [0.0, 0.0, 1.0]))
+    proj = synth.colmajor(synth.perspective(90.0, 1.0, 0.1, 1000.0))
+    return vol, tf, view, proj
+
+
+def _leaf_of_levels(vol, cell_levels):
+    """Leaf map of a row of level-0 cells along x: cell i is rendered by the
+    block of level cell_levels[i] that contains it."""
+    leaf = []
+    for i, L in enumerate(cell_levels):
+        nbx = vol.blocks_per_axis(L)[0]
+        bx = i >> L
+        assert bx < nbx
+        leaf.append(int(vol.level_offsets[L]) + bx)
+    return np.array(leaf, np.int32)
+
+
+def _lattice_count(x0, step, lo, hi, stride):
+    """Brute force with exact rationals: lattice indices k >= 0 with
+    x0 + k step in [lo, hi) and k a multiple of stride."""
+    from fractions import Fraction as F
+    x0, step = F(x0), F(step)
+    n = 0
+    k = 0
+    while x0 + k * step < hi:
+        if x0 + k * step >= lo and k % stride == 0:
+            n += 1
+        k += 1
+    return n
+
+
+@pytest.mark.parametrize("eye_x,levels_of_cells,nlev,step", [
+    (-10.0, [1, 1, 0, 0], 2, "0.3"),    # entry at x = 0; a level-1 block, then two level-0 blocks
+    (-10.0, [0, 0, 1, 1], 2, "0.3"),    # the reverse
+    ("1.15", [1, 1, 0, 0], 2, "0.3"),   # eye inside the volume: the lattice starts at the eye
+    ("-7.3", [2, 2, 2, 2, 0, 0, 1, 1], 3, "0.35"),
+    ("2.9", [0, 0, 2, 2, 2, 2, 1, 1], 3, "0.35"),
+])
+def test_each_level_takes_every_2L_th_point_of_one_global_lattice(eye_x, levels_of_cells, nlev, step):
+    """A3: samples lie on one lattice t0 + k step anchored at the volume
+    entry; a block of level L takes the points k = 0 mod 2^L inside it and
+    corrects opacity for the spacing step 2^L. Along an axial ray through a
+    constant medium the count per block is the brute-force count of such
+    points, and A = 1 - (1 - a)^(sum over samples of step 2^L / 0.5). A
+    lattice anchored at each block's entry instead gives other counts on
+    these layouts."""
+    from fractions import Fraction as F
+    nx = 8 * len(levels_of_cells)
+    vol, tf, view, proj = _x_ray(float(eye_x), nx, nlev)
+    leaf = _leaf_of_levels(vol, levels_of_cells)
+    r = vol.render([tf], leaf, view, proj, 9, 9, step=float(step), pixels=[40])
+    x0 = max(F(eye_x), F(0))
+    count, expo = 0, F(0)
+    i = 0
+    while i < len(levels_of_cells):
+        L = levels_of_cells[i]
+        j = i
+        while j < len(levels_of_cells) and levels_of_cells[j] == L and (j >> L) == (i >> L):
+            j += 1
+        n = _lattice_count(x0, F(step), 8 * i, 8 * j, 2 ** L)
+        count += n
+        expo += n * F(step) * 2 ** L / F("0.5")
+        i = j
+    a = float(np.float32(0.01))
+    A = 1.0 - (1.0 - a) ** float(expo)
+    assert r["flags"][0] == 0
+    assert r["count_late"][0] == count
+    assert r["late"][0] == pytest.approx([0.25 * A, 0.5 * A, 1.0 * A, A], abs=1e-12)
+    # the block-entry anchoring this pins against
+    if eye_x == -10.0 and levels_of_cells[0] == 1:
+        entry_anchor = _lattice_count(0, F(step), 0, 16, 2) + _lattice_count(16, F(step), 16, 32, 1)
+        assert entry_anchor != count
+
+
+def test_a_point_on_a_face_between_levels_has_both_assignments():
+    """A16: with step 0.5 the lattice point k = 32 lies exactly on the face
+    x = 16 between two level-0 blocks and a level-1 block. Assigned to the
+    level-1 block (the exact cell), it is one of that block's samples at
+    spacing 1.0; assigned to the level-0 block before the face, it is a
+    level-0 sample at spacing 0.5 and the level-1 block starts at k = 34.
+    The oracle flags the pixel and enumerates exactly these two results:
+    exponents (32 + 16 * 2) and (33 + 15 * 2) reference steps."""
+    vol, tf, view, proj = _x_ray(-10.0, 32, 2)
+    leaf = _leaf_of_levels(vol, [0, 0, 1, 1])
+    r = vol.render([tf], leaf, view, proj, 9, 9, step=0.5, pixels=[40])
+    assert r["flags"][0] & oracle.FL_FACE and r["flags"][0] & oracle.FL_TEDGE
+    a = float(np.float32(0.01))
+    g = r["var_groups"][0]
+    n = g["n"][0]
+    got = sorted((int(g["count_late"][0][i]), g["late"][0][i][3]) for i in range(n))
+    # k = 64 lies on the exit face x = 32 as well: a ray that ends there takes
+    # no sample, one that ends a rounding later takes a last level-1 sample
+    # (two more reference steps); both are legitimate
+    want = sorted((c + extra, 1.0 - (1.0 - a) ** (e + 2 * extra))
+                  for c, e in [(32 + 16, 64), (33 + 15, 63)] for extra in (0, 1))
+    assert [c for c, _ in got] == [c for c, _ in want]
+    for (c, A), (_, Aw) in zip(got, want):
+        assert A == pytest.approx(Aw, abs=1e-12)
+    # the exact result (the face point in the level-1 block, the exit point
+    # not taken) is one of them
+    assert int(r["count_late"][0]) == 48
+    assert r["late"][0][3] == pytest.approx(1.0 - (1.0 - a) ** 64, abs=1e-12)
+
+
+def test_a_ray_grazing_a_face_has_one_crossing_per_variant():
+    """A ray nearly parallel to the face x = 16 between a level-0 and a
+    level-1 block keeps many lattice points within eps of it. A
+    floating-point ray crosses that face once, so the legitimate results are
+    the m + 1 crossing positions among the m points whose assignment
+    matters, not 2^m: the enumeration stays small and every variant's sample
+    count lies between the all-before and all-after assignments."""
+    vol, tf, view, proj = _x_ray(-10.0, 32, 2)
+    leaf = _leaf_of_levels(vol, [0, 0, 1, 1])
+    # the centre ray runs along +y, rising 1e-5 voxel in x per voxel of y,
+    # from x = 15.99994 where it enters at y = 0; step 0.3: points
+    # y_k = 0.3 k, k = 0..26 (the exit y = 8 is not a lattice point), all
+    # within 1e-3 of x = 16 (the ray crosses it near k = 20)
+    eye = np.array([15.9999, -6.0, 4.0])
+    view = synth.colmajor(synth.look_at(eye, eye + np.array([1e-5, 1.0, 0.0]), [0.0, 0.0, 1.0]))
+    r = vol.render([tf], leaf, view, proj, 9, 9, step=0.3, pixels=[40])
+    assert r["flags"][0] & oracle.FL_FACE and not r["flags"][0] & (oracle.FL_MANY | oracle.FL_TEDGE)
+    g = r["var_groups"][-1]
+    n = int(g["n"][0])
+    # every point's assignment matters (level 0 samples it; level 1 samples
+    # even k at level 1 and skips odd k): 27 + 1 crossing positions
+    assert n == 28
+    cl = np.sort(g["count_late"][0][:n])
+    # all before the face: 27 level-0 samples; all after: the 14 even k
+    assert cl[0] == 14 and cl[-1] == 27
+    assert int(r["count_late"][0]) in cl
