@@ -323,7 +323,13 @@ sg_status sg_select_lod_batch(sg_volume* vol, const sg_pose* poses, int n, void*
  * sg_read_selection, req[nodes] requested node ids in no particular order,
  * counters[8] = requested, selected, culled, empty, fallback, nonempty.
  * The first call on a device looks up the fixed array's device address (no
- * allocation); make that first call before any stream capture. Every call
+ * allocation); make that first call before any stream capture. The address
+ * is kept for the life of the process: after cudaDeviceReset on a device
+ * this entry point must not be called on it again. Brick uploads issued
+ * later on other streams wait for the call when it was not captured (as
+ * they do for sg_select_lod); after a captured call, and for
+ * transfer-function changes in every case, order them after the call
+ * yourself (one stream, or events). Every call
  * shares the array and it keeps the last call's contents (each call writes
  * before it reads, nothing needs clearing): calls whose work overlaps on the
  * GPU race, so order them (one stream, or events). pose.slot is ignored and
@@ -544,6 +550,16 @@ sg_status sg_unet_set_tensor_path(sg_unet* net, int tcgen05);
  * the last check: SG_ERR_TIMEOUT means the affected outputs are invalid.
  * Synchronous. */
 sg_status sg_unet_check(sg_unet* net);
+
+/* Failure-detection self-test of the bounded waits (the paper has no
+ * counterpart). Launches one small kernel on stream that waits, with the
+ * tensor-core kernels' own bounded poll limited to `polls` polls (1 to
+ * 2^24), on a shared-memory barrier that nothing ever arrives at; no copy,
+ * MMA or tensor-memory allocation is in flight. The wait gives up and the
+ * kernel raises the network's error word exactly as a stalled convolution
+ * would, so the next sg_unet_check returns SG_ERR_TIMEOUT (and clears it).
+ * Errors: INVALID_ARG, CUDA. */
+sg_status sg_unet_wait_selftest(sg_unet* net, uint32_t polls, void* stream);
 
 /* One Adam step on the FP32 master parameters with the last gradients
  * (bias-corrected moments), then refreshes the BF16 copies. */

@@ -68,7 +68,9 @@ def _load():
         L.or_node_count.argtypes = [vp, vp]
         L.or_node_count.restype = i64
         L.or_block_ranges.argtypes = [vp, vp]
-        L.or_select.argtypes = [vp, vp, vp, vp, vp, i32, dbl, vp, vp, vp, vp, i32, vp]
+        L.or_select.argtypes = [vp, vp, vp, vp, vp, i32, dbl, vp, vp, vp, vp, i32, vp, vp]
+        L.or_cache_place.argtypes = [vp, i64, ctypes.c_uint64, vp, vp, vp, i32, vp, vp]
+        L.or_cache_place.restype = i32
         L.or_select.restype = i32
         L.or_select_inputs.argtypes = [vp, vp, vp, i32, dbl, vp, vp, vp]
         L.or_sample.argtypes = [vp, i32, i32, vp]
@@ -216,12 +218,15 @@ class Volume:
 
     def select(self, tfs, views, projs, height, tau=1.0, resident=None, ranges=None, req_cap=1 << 20):
         """LOD + residency selection for a stereo pose (pass the same view
-        twice for a single view). Returns dict(leaf, state, requests, selected)."""
+        twice for a single view). Returns dict(leaf, state, requests,
+        selected, used); used marks the blocks whose cache stamps this
+        traversal renews."""
         if ranges is None:
             ranges = self.block_ranges()
         nb0 = self.blocks_per_axis(0)
         leaf = np.empty(nb0[2] * nb0[1] * nb0[0], np.int32)
         state = np.zeros(self.node_count, np.uint8)
+        used = np.zeros(self.node_count, np.uint8)
         req = np.zeros(req_cap, np.int32)
         nreq = ctypes.c_int(0)
         v = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64).reshape(16) for x in views]))
@@ -229,8 +234,8 @@ class Volume:
         res = None if resident is None else np.ascontiguousarray(resident, np.uint8)
         nsel = _load().or_select(ctypes.byref(self._s), _tf_array(tfs), _p(np.ascontiguousarray(ranges)),
                                  _p(v), _p(p), int(height), float(tau), _p(res), _p(leaf), _p(state),
-                                 _p(req), req_cap, ctypes.byref(nreq))
-        return dict(leaf=leaf, state=state, requests=req[: nreq.value].copy(), selected=nsel)
+                                 _p(req), req_cap, ctypes.byref(nreq), _p(used))
+        return dict(leaf=leaf, state=state, requests=req[: nreq.value].copy(), selected=nsel, used=used.astype(bool))
 
     def select_inputs(self, views, projs, height, tau=1.0):
         eyes = np.zeros(6, np.int64)
@@ -247,7 +252,7 @@ class Volume:
         return _load().or_sample(ctypes.byref(self._s), int(L), int(c), _p(pp))
 
     def render(self, tfs, leaf, view, proj, W, H, step=0.5, term=0.99, term_tol=1e-4, eps=1e-3,
-               pixels=None, nthreads=0, mode=MODE_EA, depth=None, lens=None, variants=True, var_cap=256):
+               pixels=None, nthreads=0, mode=MODE_EA, depth=None, lens=None, variants=True, var_cap=1024):
         """Cast rays for `pixels` (flat ids j*W+i; None = all). Returns dict
         with early/late RGBA (n,4) FP64, sample counts and flags, all for the
         exact assignment of lattice points to cells.
@@ -320,6 +325,35 @@ class Volume:
         m = np.asarray(self.model, np.float64).reshape(4, 4).T  # column-major -> row-major
         voxel = np.linalg.norm(m[:3, 0])
         return np.ascontiguousarray(np.asarray(depth, np.float64).reshape(-1) / voxel)
+
+
+class Cache:
+    """The GPU brick cache as the oracle sees it ("Volumetric Data Cashing"):
+    at most `slots` resident blocks, each with the frame of its last use.
+    Mirror every selection with select(...) (frames count selections, as the
+    library's do) and every placement with place(...)."""
+
+    def __init__(self, volume, slots):
+        self.vol = volume
+        self.slots = int(slots)
+        self.resident = np.zeros(volume.node_count, np.uint8)
+        self.stamp = np.zeros(volume.node_count, np.uint64)
+        self.frame = 0
+
+    def select(self, tfs, views, projs, height, tau=1.0, ranges=None):
+        self.frame += 1
+        ref = self.vol.select(tfs, views, projs, height, tau=tau, resident=self.resident, ranges=ranges)
+        self.stamp[ref["used"] & (self.resident != 0)] = self.frame
+        return ref
+
+    def place(self, req):
+        """Places req in order; returns (requests processed, evicted ids)."""
+        r = np.ascontiguousarray(req, np.int32)
+        ev = np.zeros(max(len(r), 1), np.int32)
+        nev = ctypes.c_int(0)
+        m = _load().or_cache_place(ctypes.byref(self.vol._s), self.slots, ctypes.c_uint64(self.frame),
+                                   _p(self.resident), _p(self.stamp), _p(r), len(r), _p(ev), ctypes.byref(nev))
+        return m, ev[: nev.value].copy()
 
 
 def tf_table(tf, spacing):

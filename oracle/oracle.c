@@ -259,6 +259,7 @@ typedef struct {
   int32_t* leaf;
   int32_t* req;
   int req_cap, nreq;
+  uint8_t* used;
 } sel_t;
 
 enum { ST_UNSEEN = 0, ST_CULLED = 1, ST_EMPTY = 2, ST_SELECTED = 3, ST_FALLBACK = 4, ST_REFINED = 5 };
@@ -347,6 +348,7 @@ static void visit(sel_t* s, int L, const int64_t* b) {
     for (int i = 0; i < nneed; ++i) {
       int64_t cid = node_id(s, L - 1, need[i]);
       if (!s->resident[cid] && s->nreq < s->req_cap) s->req[s->nreq++] = (int32_t)cid;
+      if (s->resident[cid] && s->used) s->used[cid] = 1;
     }
     s->state[id] = ST_FALLBACK;
     fill_leaf(s, L, b, (int32_t)id);
@@ -397,10 +399,15 @@ static void eye_inputs(const double* model, const double* view, const double* pr
 /* view/proj: [2][16] column major (FP64 copies of FP32 inputs).
  * leaf: one int32 per level-0 block cell, -1 where nothing is rendered.
  * state: one byte per node (see ST_*). req: requested node ids, ascending.
+ * used (optional, one byte per node): the blocks this traversal used, whose
+ * cache time stamps it renews ("Volumetric Data Cashing"): every block
+ * rendered, rendered in place of its children, or refined, and the resident
+ * children a fallback block needs (evicting those to make room for the
+ * missing ones would keep the block from ever refining).
  * Returns the number of selected nodes. */
 int or_select(const or_volume* v, const or_tf* tfs, const uint32_t* ranges, const double* view,
               const double* proj, int height, double tau, const uint8_t* resident, int32_t* leaf,
-              uint8_t* state, int32_t* req, int req_cap, int* nreq) {
+              uint8_t* state, int32_t* req, int req_cap, int* nreq, uint8_t* used) {
   sel_t s;
   memset(&s, 0, sizeof s);
   s.v = v; s.tf = tfs; s.ranges = ranges; s.resident = resident;
@@ -444,6 +451,8 @@ int or_select(const or_volume* v, const or_tf* tfs, const uint32_t* ranges, cons
   int64_t ncell = s.nb[0][0] * s.nb[0][1] * s.nb[0][2];
   for (int64_t i = 0; i < ncell; ++i) leaf[i] = -1;
   s.leaf = leaf; s.req = req; s.req_cap = req_cap; s.nreq = 0;
+  s.used = used;
+  if (used) memset(used, 0, nn);
   int top = v->levels - 1;
   for (int64_t bz = 0; bz < s.nb[top][2]; ++bz)
     for (int64_t by = 0; by < s.nb[top][1]; ++by)
@@ -454,10 +463,64 @@ int or_select(const or_volume* v, const or_tf* tfs, const uint32_t* ranges, cons
   qsort(req, s.nreq, sizeof(int32_t), cmp_i32);
   *nreq = s.nreq;
   int nsel = 0;
-  for (int64_t id = 0; id < nn; ++id) nsel += (state[id] == ST_SELECTED || state[id] == ST_FALLBACK);
+  for (int64_t id = 0; id < nn; ++id) {
+    nsel += (state[id] == ST_SELECTED || state[id] == ST_FALLBACK);
+    if (used && (state[id] == ST_SELECTED || state[id] == ST_FALLBACK || state[id] == ST_REFINED)) used[id] = 1;
+  }
   free(s.own_empty);
   free(s.sub_empty);
   return nsel;
+}
+
+/* ------------------------------------------------------------------------ */
+/* brick cache ("Volumetric Data Cashing")                                   */
+
+/* The GPU cache holds at most `slots` blocks. Each resident block carries
+ * the time stamp of the last frame whose traversal used it (see or_select's
+ * `used`). Blocks of the coarsest level are pinned: they are never evicted.
+ * Requests are placed in the order given. A request already resident is
+ * left as it is. Otherwise it takes a free slot if there is one, else the
+ * slot of the resident block with the smallest stamp that is older than the
+ * current frame, ties going to the coarser block and then to the lower node
+ * id; the placed block is stamped with the current frame. Placement stops
+ * at the first request that finds no such block (every unpinned block in
+ * use this frame). Returns the number of requests processed, a prefix of
+ * the list; evicted[0..*nevicted) lists the blocks evicted, in order. */
+int or_cache_place(const or_volume* v, int64_t slots, uint64_t frame, uint8_t* resident, uint64_t* stamp,
+                   const int32_t* req, int nreq, int32_t* evicted, int* nevicted) {
+  int64_t off[OR_MAX_LEVELS + 1];
+  int64_t nn = or_node_count(v, off);
+  int64_t nres = 0;
+  for (int64_t i = 0; i < nn; ++i) nres += resident[i] != 0;
+  *nevicted = 0;
+  int m = 0;
+  for (; m < nreq; ++m) {
+    int64_t id = req[m];
+    if (resident[id]) continue;
+    if (nres >= slots) {
+      int64_t victim = -1;
+      int vlevel = 0;
+      for (int64_t j = 0; j < nn; ++j) {
+        if (!resident[j] || j >= off[v->levels - 1] || stamp[j] >= frame) continue;
+        int L = 0;
+        while (L + 1 < v->levels && j >= off[L + 1]) ++L;
+        /* smallest stamp, then the larger level, then the lower id (j
+         * ascends, so a later j only wins on a strictly better key) */
+        if (victim < 0 || stamp[j] < stamp[victim] || (stamp[j] == stamp[victim] && L > vlevel)) {
+          victim = j;
+          vlevel = L;
+        }
+      }
+      if (victim < 0) break;
+      resident[victim] = 0;
+      evicted[(*nevicted)++] = (int32_t)victim;
+      --nres;
+    }
+    resident[id] = 1;
+    stamp[id] = frame;
+    ++nres;
+  }
+  return m;
 }
 
 /* The integers the selection decides with, exposed for pins. */
@@ -1117,8 +1180,8 @@ int or_render(const or_volume* v, const or_tf* tfs, const int32_t* leaf, const d
   ray_t r;
   if (!ray_init(&r, v, tfs, leaf, view, proj, W, H, step, term, term_tol, eps, mode, tmax, lens)) return 0;
   int64_t n = pix ? npix : (int64_t)W * H;
-  if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 64)
+  const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nt)
   for (int64_t q = 0; q < n; ++q) {
     int64_t id = pix ? pix[q] : q;
     cast(&r, id, rgba_early + 4 * q, rgba_late + 4 * q, cnt_early + q, cnt_late + q, flags + q);
@@ -1139,8 +1202,8 @@ int or_render_variants(const or_volume* v, const or_tf* tfs, const int32_t* leaf
                        const double* tmax, const or_lens* lens) {
   ray_t r;
   if (!ray_init(&r, v, tfs, leaf, view, proj, W, H, step, term, term_tol, eps, mode, tmax, lens)) return 0;
-  if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 1)
+  const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
   for (int64_t q = 0; q < npix; ++q) {
     geom_t g;
     leaves_t out;

@@ -8,6 +8,7 @@
 #include <new>
 #include <set>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -22,6 +23,19 @@ void set_error(const std::string& msg) { g_err = msg; }
 sg_status cuda_fail(cudaError_t e, const char* what) {
   g_err = std::string(what) + ": " + cudaGetErrorString(e);
   return SG_ERR_CUDA;
+}
+
+sg_status check_pose_fields(const sg_volume* v, const sg_pose* p) {
+  auto bad = [](const char* msg) {
+    set_error(msg);
+    return SG_ERR_INVALID_ARG;
+  };
+  if (!p) return bad("pose is NULL");
+  if (!(p->t >= 0 && p->t < v->T)) return bad("pose.t out of range");
+  if (!(p->width > 0 && p->height > 0 && p->width <= 32768 && p->height <= 32768)) return bad("pose image size");
+  if (!(p->pixel_error > 0.0f)) return bad("pose.pixel_error must be > 0");
+  if (p->proj[0][5] == 0.0f) return bad("projection has P11 == 0");
+  return SG_OK;
 }
 
 }  // namespace sg
@@ -44,8 +58,13 @@ using namespace sg;
 
 namespace {
 
+// LRU order of occupied, unpinned slots: (stamp, tie, slot). The eviction
+// victim is the first: the smallest stamp, ties going to the coarser block,
+// then to the lower (time point, node) key.
+using LruKey = std::tuple<uint64_t, int64_t, int64_t>;
+
 struct VolumeExtra {
-  std::set<std::pair<uint64_t, int64_t>> lru;  // (stamp, slot) of occupied, unpinned slots
+  std::set<LruKey> lru;
   std::vector<int64_t> free_slots;
   int32_t* d_scratch = nullptr;                // upload bookkeeping
   size_t scratch_n = 0;
@@ -60,6 +79,15 @@ VolumeExtra* extra_of(sg_volume* v) {
   for (auto& p : extras())
     if (p.first == v) return p.second;
   return nullptr;
+}
+
+// tie rank of the block with page-table key `key`: coarser levels first,
+// then ascending key
+int64_t lru_tie(const sg_volume* v, int64_t key) {
+  const int64_t node = key % v->nodes;
+  int level = 0;
+  while (level + 1 < v->levels && node >= v->geom[level + 1].off) ++level;
+  return (int64_t)(v->levels - 1 - level) * ((int64_t)v->T * v->nodes) + key;
 }
 
 template <typename T>
@@ -146,11 +174,15 @@ sg_status upload_list(sg_volume* v, int t, int c, int n, const int32_t* nodes, c
     SG_CUDA(cudaMemcpyAsync(st.data(), v->d_stamp, v->pool_slots * sizeof(uint64_t), cudaMemcpyDeviceToHost, s),
             "stamps");
     SG_CUDA(cudaStreamSynchronize(s), "upload");
+    // a slot's stamp only moves forward: the device array holds the stamps
+    // selections wrote, so a slot placed since the last selection still
+    // carries its previous occupant's (older) stamp there
     for (int64_t sl = 0; sl < v->pool_slots; ++sl)
-      if (v->slot_owner[sl] >= 0 && !v->slot_pinned[sl] && st[sl] != v->slot_stamp[sl]) {
-        x->lru.erase({v->slot_stamp[sl], sl});
+      if (v->slot_owner[sl] >= 0 && !v->slot_pinned[sl] && st[sl] > v->slot_stamp[sl]) {
+        const int64_t tie = lru_tie(v, v->slot_owner[sl]);
+        x->lru.erase(LruKey{v->slot_stamp[sl], tie, sl});
         v->slot_stamp[sl] = st[sl];
-        x->lru.insert({st[sl], sl});
+        x->lru.insert(LruKey{st[sl], tie, sl});
       }
   }
   std::vector<int32_t> lists(2 * (size_t)n);  // [nodes placed][their slots]
@@ -168,8 +200,8 @@ sg_status upload_list(sg_volume* v, int t, int c, int n, const int32_t* nodes, c
       } else {
         // least recently used slot not used by the current frame
         auto it = x->lru.begin();
-        if (it == x->lru.end() || it->first >= v->frame) break;
-        sl = it->second;
+        if (it == x->lru.end() || std::get<0>(*it) >= v->frame) break;
+        sl = std::get<2>(*it);
         x->lru.erase(it);
         const int64_t old = v->slot_owner[sl];
         v->h_slot[old] = -1;
@@ -185,7 +217,7 @@ sg_status upload_list(sg_volume* v, int t, int c, int n, const int32_t* nodes, c
         v->slot_pinned[sl] = 1;
       } else {
         v->slot_stamp[sl] = v->frame;
-        x->lru.insert({v->frame, sl});
+        x->lru.insert(LruKey{v->frame, lru_tie(v, key), sl});
       }
     }
     lists[m] = node;
@@ -256,11 +288,7 @@ sg_status ensure_selection(sg_volume* v, int slot) {
 sg_status check_pose(const sg_volume* v, const sg_pose* p) {
   SG_CHECK_ARG(p, "pose is NULL");
   SG_CHECK_ARG(p->slot >= 0 && p->slot < kMaxSlots, "pose.slot out of range [0, 255]");
-  SG_CHECK_ARG(p->t >= 0 && p->t < v->T, "pose.t out of range");
-  SG_CHECK_ARG(p->width > 0 && p->height > 0 && p->width <= 32768 && p->height <= 32768, "pose image size");
-  SG_CHECK_ARG(p->pixel_error > 0.0f, "pose.pixel_error must be > 0");
-  SG_CHECK_ARG(p->proj[0][5] != 0.0f, "projection has P11 == 0");
-  return SG_OK;
+  return check_pose_fields(v, p);
 }
 
 sg_status check_render_params(const sg_render_params* r) {

@@ -137,6 +137,9 @@ namespace sg {
 
 void set_error(const std::string& msg);
 sg_status cuda_fail(cudaError_t e, const char* what);
+// the checks of a pose that do not involve its selection slot (time point,
+// image size, pixel error, projection)
+sg_status check_pose_fields(const sg_volume* v, const sg_pose* p);
 
 // ingest.cu
 cudaError_t launch_pyramid(const void* src, const int64_t* sdims, void* dst, const int64_t* ddims, int esize,

@@ -401,11 +401,8 @@ extern "C" sg_status sg_select_lod_noalloc(sg_volume* v, const sg_pose* p, uint3
     set_error("sg_select_lod_noalloc: volume, pose and every output must be non-NULL");
     return SG_ERR_INVALID_ARG;
   }
-  if (p->t < 0 || p->t >= v->T || p->width <= 0 || p->height <= 0 || !(p->pixel_error > 0.0f) ||
-      p->proj[0][5] == 0.0f) {
-    set_error("sg_select_lod_noalloc: pose out of range (t, image size, pixel_error or P11)");
-    return SG_ERR_INVALID_ARG;
-  }
+  sg_status pst = check_pose_fields(v, p);
+  if (pst != SG_OK) return pst;
   if (v->max_level_nodes > kStaticFrontierNodes) {
     set_error("sg_select_lod_noalloc: the volume has more than 65536 blocks on one level; its fixed scratch "
               "holds at most 65536 (use sg_select_lod)");
@@ -469,8 +466,19 @@ extern "C" sg_status sg_select_lod_noalloc(sg_volume* v, const sg_pose* p, uint3
   J.req = req;
   J.counters = counters;
   J.frontier = frontier;
-  k_select<<<1, kSelThreads, 0, (cudaStream_t)stream>>>(jobs, g);
+  const cudaStream_t s = (cudaStream_t)stream;
+  k_select<<<1, kSelThreads, 0, s>>>(jobs, g);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "sg_select_lod_noalloc: launch");
+  // an upload on another stream rewrites the page table and node flags this
+  // launch reads: uploads wait on the selection event, so record it here too
+  // (not during capture, where a recorded event cannot be waited on later)
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return cuda_fail(e, "sg_select_lod_noalloc: capture status");
+  if (cap == cudaStreamCaptureStatusNone) {
+    e = cudaEventRecord(v->ev_select, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sg_select_lod_noalloc: event");
+  }
   return SG_OK;
 }

@@ -952,6 +952,24 @@ sg_status check_shape(const sg_unet* u, int n, int h, int w) {
 
 }  // namespace
 
+namespace sg {
+namespace nn {
+// Failure-detection self-test: the bounded wait of the tensor-core kernels
+// on an mbarrier that expects one arrival which never comes. No copy, MMA
+// or TMEM allocation is in flight; after `limit` polls the wait gives up and
+// the kernel raises the error word as a stalled convolution would.
+__global__ void k_wait_selftest(uint32_t* err, uint32_t limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_limit(smem_u32(&bar), 0, limit)) atomicExch(err, 1u);
+}
+}  // namespace nn
+}  // namespace sg
+
 extern "C" {
 
 sg_status sg_unet_create(int max_batch, int max_h, int max_w, uint64_t seed, sg_unet** out) {
@@ -1047,6 +1065,17 @@ sg_status sg_unet_check(sg_unet* u) {
     set_error("sg_unet: a tensor-core wait timed out (results of the affected launches are invalid)");
     return SG_ERR_TIMEOUT;
   }
+  return SG_OK;
+}
+
+sg_status sg_unet_wait_selftest(sg_unet* u, uint32_t polls, void* stream) {
+  if (!u || polls == 0 || polls > kTcSpinLimit) {
+    set_error("sg_unet_wait_selftest: NULL network or polls outside [1, 2^24]");
+    return SG_ERR_INVALID_ARG;
+  }
+  nn::k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>(u->d_err, polls);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "sg_unet_wait_selftest");
   return SG_OK;
 }
 

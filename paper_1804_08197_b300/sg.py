@@ -25,7 +25,7 @@ EXPORTS = ["sg_volume_create", "sg_volume_destroy", "sg_upload_volume_device", "
            "sg_render", "sg_render_host", "sg_render_host_async", "sg_render_host_wait", "sg_render_batch", "sg_set_render_config", "sg_get_render_config",
            "sg_autotune_render", "sg_select_lod_noalloc", "sg_read_residency", "sg_set_brick_ranges", "sg_unet_create", "sg_unet_destroy",
            "sg_unet_param_count", "sg_unet_get_params", "sg_unet_set_params", "sg_unet_forward", "sg_unet_backward",
-           "sg_unet_adam_step", "sg_unet_set_tensor_path", "sg_unet_check", "sg_psnr", "sg_read_ranges", "sg_upload_brick_list", "sg_unwarp", "sg_set_channel_shading",
+           "sg_unet_adam_step", "sg_unet_set_tensor_path", "sg_unet_check", "sg_unet_wait_selftest", "sg_psnr", "sg_read_ranges", "sg_upload_brick_list", "sg_unwarp", "sg_set_channel_shading",
            "sg_container_create", "sg_container_open", "sg_container_append", "sg_container_finish",
            "sg_container_get_info", "sg_container_read", "sg_container_close", "sg_host_cache_create",
            "sg_host_cache_destroy", "sg_host_cache_fetch", "sg_stream_requests",
@@ -143,6 +143,7 @@ def _load():
         "sg_psnr": [vp, vp, i64, vp, vp],
         "sg_unet_set_tensor_path": [vp, i32],
         "sg_unet_check": [vp],
+        "sg_unet_wait_selftest": [vp, ctypes.c_uint32, vp],
         "sg_render": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
         "sg_render_host": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
         "sg_render_host_async": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
@@ -524,6 +525,12 @@ def sg_unet_set_tensor_path(net, tcgen05=1):
 
 def sg_unet_check(net):
     _check(lib.sg_unet_check(net))
+
+
+def sg_unet_wait_selftest(net, polls, stream=None):
+    """Failure-detection self-test: a bounded wait that nothing satisfies
+    gives up after `polls` polls and raises the network's error word."""
+    _check(lib.sg_unet_wait_selftest(net, int(polls), _stream(stream)))
 
 
 def sg_read_ranges(vol, t, nnode, channels=1):

@@ -289,5 +289,13 @@ def test_every_skip_block_size_leaves_the_image_unchanged(skip_block):
             imgs[skip] = [o.cpu().numpy() for o in outs]
         assert np.array_equal(imgs[0][0], imgs[1][0]) and np.array_equal(imgs[0][1], imgs[1][1])
         assert imgs[1][0][..., 3].max() > 0.2
+        # and the skipping render matches the oracle, both eyes
+        ovol = oracle.Volume([oracle.pyramid(v, 3)], 32, model=model)
+        otf = oracle.make_tf(synth.tf_piecewise(2002, zero_alpha_points=2), 300.0, 60000.0)
+        ref = ovol.select([otf], views, projs, H, tau=0.3)
+        cells, _, _ = sg.sg_read_selection(vol, 0, len(ref["leaf"]), ovol.node_count)
+        assert np.array_equal(cells, ref["leaf"])
+        for e in range(2):
+            compare_image(imgs[1][e].reshape(-1, 4), ovol.render([otf], ref["leaf"], views[e], projs[e], W, H))
     finally:
         sg.sg_volume_destroy(vol)

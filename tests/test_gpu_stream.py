@@ -2,9 +2,10 @@
 volume starts with only its coarsest level; each frame selects (falling back
 one level and requesting missing children, "Octree Representation"), then
 uploads the requested bricks, evicting the least recently used ones when the
-cache is full. Every frame's selection must equal the oracle's for the same
-residency and the same known value ranges, bit for bit; the converged frame
-must render like the oracle."""
+cache is full. The oracle runs its own cache beside the GPU's (oracle.Cache:
+its own stamps from its own selections, its own evictions): the resident set
+must be the same after every upload, every frame's selection must equal the
+oracle's bit for bit, and the rendered frames must match the oracle."""
 import numpy as np
 import pytest
 
@@ -73,8 +74,18 @@ def test_streaming_frames_match_the_oracle_and_evict_lru(mode, index_ranges=True
 
         comp = torch.cuda.Stream() if mode == "pipelined" else None
         copy = torch.cuda.Stream() if mode == "pipelined" else None
+        cache = oracle.Cache(ovol, cap)
+        nevicted = 0
+
+        def same_residency():
+            res = sg.sg_read_residency(vol, 0, ovol.node_count) >= 0
+            assert np.array_equal(res, cache.resident != 0), (
+                f"GPU-only {np.flatnonzero(res & (cache.resident == 0))}, "
+                f"oracle-only {np.flatnonzero(~res & (cache.resident != 0))}")
+            return res
 
         def upload(ids):
+            nonlocal nevicted
             if mode in ("list", "pipelined"):
                 # one call per frame, by node id, coarse levels first
                 ids = sorted((int(i) for i in ids), key=lambda n: (-ovol.node_coords(n)[0], n))
@@ -83,36 +94,36 @@ def test_streaming_frames_match_the_oracle_and_evict_lru(mode, index_ranges=True
                     L, b = ovol.node_coords(n)
                     host.append(_brick(ovol, L, *b))
                 done = sg.sg_upload_brick_list(vol, 0, 0, ids, host, stream=copy)
-                assert 0 < done <= len(ids)
-                res = sg.sg_read_residency(vol, 0, ovol.node_count)
-                assert (res[ids[:done]] >= 0).all()
+                m, ev = cache.place(ids)
+                assert 0 < done <= len(ids) and done == m
+                nevicted += len(ev)
+                same_residency()
                 known[np.array(ids[:done], dtype=np.int64)] = True
                 return
             by_level = {}
             for i in ids:
                 L, b = ovol.node_coords(int(i))
-                by_level.setdefault(L, []).append(b)
-            for L, bs in by_level.items():
-                host = np.stack([_brick(ovol, L, *b) for b in bs])
-                sg.sg_upload_bricks(vol, 0, 0, L, np.array(bs), host)
+                by_level.setdefault(L, []).append((int(i), b))
+            for L, nb in by_level.items():
+                host = np.stack([_brick(ovol, L, *b) for _, b in nb])
+                sg.sg_upload_bricks(vol, 0, 0, L, np.array([b for _, b in nb]), host)
+                m, ev = cache.place([n for n, _ in nb])
+                assert m == len(nb)
+                nevicted += len(ev)
+            same_residency()
             known[np.array(list(ids), dtype=np.int64)] = True
 
         upload([ovol.level_offsets[LEVELS - 1]])  # the root
-        ever_resident = set()
-        evicted = False
         for views, projs in poses:
             pose = sg.make_pose(views, projs, W, H, pixel_error=tau)
             for frame in range(24):  # overlap bricks evicted early come back a few frames later
                 stats = sg.sg_select_lod(vol, pose, stats=True)
                 gsel = sg.sg_read_selection(vol, 0, len(ovol.select([otf], views, projs, H)["leaf"]), ovol.node_count)
-                res = sg.sg_read_residency(vol, 0, ovol.node_count) >= 0
-                now = set(np.flatnonzero(res))
-                evicted |= bool(ever_resident - now)
-                ever_resident |= now
+                same_residency()
                 ranges = full.copy()
                 ranges[~known, 0, 0] = 0xFFFFFFFF
                 ranges[~known, 0, 1] = 0
-                ref = ovol.select([otf], views, projs, H, tau=tau, resident=res.astype(np.uint8), ranges=ranges)
+                ref = cache.select([otf], views, projs, H, tau=tau, ranges=ranges)
                 compare_selection(gsel, ref)
                 if stats["requested"] == 0:
                     break
@@ -131,7 +142,7 @@ def test_streaming_frames_match_the_oracle_and_evict_lru(mode, index_ranges=True
                     continue
                 upload(gsel[2])
             assert stats["requested"] == 0 and stats["fallback"] == 0
-        assert evicted, "the second view should have evicted bricks of the first"
+        assert nevicted > 0, "the second view should have evicted bricks of the first"
         # the converged second view renders like the oracle
         views, projs = poses[1]
         pose = sg.make_pose(views, projs, W, H, pixel_error=tau)
@@ -180,21 +191,26 @@ def test_upload_list_cut_short_leaves_a_consistent_cache():
                 out.append(_brick(ovol, L, *b))
             return out
 
+        cache = oracle.Cache(ovol, cap)
         root = [int(ovol.level_offsets[LEVELS - 1])]
         assert sg.sg_upload_brick_list(vol, 0, 0, root, bricks(root)) == 1
+        cache.place(root)
         pose = sg.make_pose(views, projs, W, H, pixel_error=tau)
         cut = False
         for frame in range(6):
             sg.sg_select_lod(vol, pose)
+            cache.select([otf], views, projs, H, tau=tau, ranges=full)
             req = sg.sg_read_requests(vol, 0)
             if len(req) == 0:
                 break
             ids = sorted((int(n) for n in req), key=lambda n: (-ovol.node_coords(n)[0], n))
             host = bricks(ids)
             done = sg.sg_upload_brick_list(vol, 0, 0, ids, host)
+            m, _ = cache.place(ids)
+            assert done == m
             cut |= done < len(ids)
             res = sg.sg_read_residency(vol, 0, ovol.node_count)
-            assert (res[ids[:done]] >= 0).all()
+            assert np.array_equal(res >= 0, cache.resident != 0)
             assert len(set(res[res >= 0].tolist())) == np.count_nonzero(res >= 0) <= cap
             # every resident brick holds its own data
             for n in np.flatnonzero(res >= 0)[:6]:
@@ -204,8 +220,7 @@ def test_upload_list_cut_short_leaves_a_consistent_cache():
                 assert np.array_equal(got, _brick(ovol, L, *b).reshape(-1))
             # selection and image for exactly this residency
             sg.sg_select_lod(vol, pose)
-            resident = (res >= 0).astype(np.uint8)
-            ref = ovol.select([otf], views, projs, H, tau=tau, resident=resident, ranges=full)
+            ref = cache.select([otf], views, projs, H, tau=tau, ranges=full)
             gsel = sg.sg_read_selection(vol, 0, len(ref["leaf"]), ovol.node_count)
             compare_selection(gsel, ref)
             outs = [torch.empty((H, W, 4), device="cuda") for _ in range(2)]
@@ -221,8 +236,9 @@ def test_streaming_from_a_container_through_the_host_cache(tmp_path):
     """The full storage path: every brick LZ4-compressed in a container,
     a host cache smaller than the volume, sg_stream_requests per frame
     (coarse first, misses decompressed on host threads, one list upload).
-    Every frame's selection equals the oracle's for that residency; the
-    converged frame renders like the oracle."""
+    The GPU cache's residency equals the oracle cache's after every frame,
+    every frame's selection equals the oracle's, and the converged frame
+    renders like the oracle."""
     import torch
     from paper_1804_08197_b300 import sg
     a = synth.filaments_u16(DIMS, seed=33, ntubes=18)
@@ -258,18 +274,25 @@ def test_streaming_from_a_container_through_the_host_cache(tmp_path):
         root = int(ovol.level_offsets[LEVELS - 1])
         ptr, _ = sg.sg_host_cache_fetch(hc, 0, 0, root)
         assert sg.sg_upload_brick_list(vol, 0, 0, [root], [ptr]) == 1
+        cache = oracle.Cache(ovol, need + 8)
+        cache.place([root])
         pose = sg.make_pose(views, projs, W, H, pixel_error=tau)
         total = dict(disk_reads=0, host_hits=0, served=0)
         for frame in range(40):
             stats = sg.sg_select_lod(vol, pose, stats=True)
             res = sg.sg_read_residency(vol, 0, ovol.node_count) >= 0
-            ref = ovol.select([otf], views, projs, H, tau=tau, resident=res.astype(np.uint8), ranges=full)
+            assert np.array_equal(res, cache.resident != 0)
+            ref = cache.select([otf], views, projs, H, tau=tau, ranges=full)
             compare_selection(sg.sg_read_selection(vol, 0, len(ref["leaf"]), ovol.node_count), ref)
             if stats["requested"] == 0:
                 break
             st = sg.sg_stream_requests(vol, 0, hc, 24 * (B + 2) ** 3 * 2)
             assert st["requested"] == stats["requested"] and 0 < st["served"] <= 24 and st["missing"] == 0, (
                 frame, st, stats, sg.lib.sg_last_error().decode())
+            # served coarse levels first, then by node id, 24 bricks at most
+            order = sorted((int(n) for n in ref["requests"]), key=lambda n: (-ovol.node_coords(n)[0], n))
+            m, _ = cache.place(order[:24])
+            assert m == st["served"]
             for key in total:
                 total[key] += st[key]
         assert stats["requested"] == 0 and stats["fallback"] == 0

@@ -234,3 +234,29 @@ def test_training_beats_the_method_without_the_network():
             rec.close()
     finally:
         sg.sg_volume_destroy(vol)
+
+
+def test_a_bounded_wait_that_runs_out_is_reported_and_the_context_survives():
+    """Failure detection without a GPU fault: a wait on a barrier nothing
+    arrives at gives up after its poll limit, raises the error word, and
+    sg_unet_check reports SG_ERR_TIMEOUT once (then clears it). The CUDA
+    context stays usable: a forward pass afterwards runs and checks clean."""
+    import torch
+    from paper_1804_08197_b300 import sg
+    net = sg.sg_unet_create(1, 16, 32, seed=3)
+    try:
+        sg.sg_unet_check(net)  # clean to start with
+        sg.sg_unet_wait_selftest(net, 4096)
+        torch.cuda.synchronize()
+        with pytest.raises(sg.SGError) as ei:
+            sg.sg_unet_check(net)
+        assert ei.value.status == sg.SG_ERR_TIMEOUT
+        sg.sg_unet_check(net)  # reported once, then cleared
+        x = [torch.rand((16, 32, 4), device="cuda")]
+        out = [torch.zeros((32, 64, 4), device="cuda")]
+        sg.sg_unet_forward(net, x, 32 * 4, 16, 32, out, 64 * 4)
+        torch.cuda.synchronize()
+        sg.sg_unet_check(net)
+        assert torch.isfinite(out[0]).all()
+    finally:
+        sg.sg_unet_destroy(net)
