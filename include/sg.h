@@ -199,13 +199,17 @@ sg_status sg_host_cache_destroy(sg_host_cache* hc);
  * INVALID_ARG, NOT_RESIDENT, OOM, IO. */
 sg_status sg_host_cache_fetch(sg_host_cache* hc, int t, int c, int64_t node, const void** brick, int* hit);
 
+/* Forgets the chunks sg_stream_requests found unreadable, so the next calls
+ * try them again (after a transient read error, say). Errors: INVALID_ARG. */
+sg_status sg_host_cache_clear_failures(sg_host_cache* hc);
+
 typedef struct {
   int32_t requested;     /* requests of the selection */
   int32_t served;        /* bricks placed in the GPU cache by this call */
   int32_t host_hits;     /* brick-channels found in the host cache */
   int32_t disk_reads;    /* brick-channels read and decompressed from the container */
   int32_t missing;       /* requests without a chunk in the container (skipped) */
-  int32_t reserved;
+  int32_t failed;        /* requests skipped: a chunk failed to read or decompress (now or earlier) */
   uint64_t disk_bytes;   /* compressed bytes read */
   uint64_t upload_bytes; /* bytes copied to the GPU cache */
 } sg_stream_stats;
@@ -215,8 +219,14 @@ typedef struct {
  * bricks (all channels); each from the host cache or read + decompressed
  * (hc's threads), then placed in the GPU cache (sg_upload_brick_list per
  * channel, on stream; complete on return). Stops early, without error, when
- * either cache holds only bricks of the current frame. Errors: INVALID_ARG
- * (layouts differ), STATE, IO, OOM, CUDA. */
+ * either cache holds only bricks of the current frame. A brick whose chunk
+ * fails to read or decompress (any channel) is left out: it stays
+ * non-resident, so the next selections render its parent in its place
+ * ("Octree Representation"), and hc remembers the chunk, so later calls
+ * skip it without spending budget (sg_host_cache_clear_failures forgets).
+ * The other bricks are served; the call then returns SG_ERR_IO with *stats
+ * filled (stats->failed counts the skipped requests). Errors: INVALID_ARG
+ * (layouts differ), STATE, IO (see above), OOM, CUDA. */
 sg_status sg_stream_requests(sg_volume* vol, int slot, sg_host_cache* hc, uint64_t max_bytes, sg_stream_stats* stats,
                              void* stream);
 

@@ -349,11 +349,16 @@ static double round_var(double v, double s, double* r) {
   return pu * hu * hu + pd * hd * hd;
 }
 
-/* mean square of (s + d)_+ for s <= 0, d ~ N(0, sg^2) */
+/* mean square of (s + d)_+ for s <= 0, d ~ N(0, sg^2): (s^2 + sg^2) Phi(z)
+ * + s sg phi(z), z = s / sg. The two terms cancel as z falls; below z = -8
+ * the value (under 1e-15 sg^2) is taken as 0, and rounding never makes it
+ * negative. */
 static double relu_clamped_ms(double s, double sg) {
   if (sg == 0.0) return 0.0;
   double z = s / sg;
-  return (s * s + sg * sg) * Phi(z) + s * sg * exp(-0.5 * z * z) / sqrt(2.0 * M_PI);
+  if (z < -8.0) return 0.0;
+  double v = (s * s + sg * sg) * Phi(z) + s * sg * exp(-0.5 * z * z) / sqrt(2.0 * M_PI);
+  return v > 0.0 ? v : 0.0;
 }
 
 #define U23 (1.0 / 8388608.0)  /* 2^-23: one FP32 operation, truncating or not */

@@ -13,6 +13,7 @@
 #include <map>
 #include <new>
 #include <set>
+#include <string>
 #include <thread>
 #include <utility>
 #include <vector>
@@ -34,6 +35,7 @@ struct sg_host_cache {
   std::vector<uint64_t> stamp;                // entry -> frame of last use
   std::set<std::pair<uint64_t, int64_t>> lru;  // (stamp, entry) of occupied entries
   std::vector<int64_t> free_list;
+  std::set<int64_t> failed;                    // keys whose chunk failed to read or decompress
 };
 
 extern "C" {
@@ -88,6 +90,15 @@ sg_status sg_host_cache_destroy(sg_host_cache* hc) {
   else
     free(hc->arena);
   delete hc;
+  return SG_OK;
+}
+
+sg_status sg_host_cache_clear_failures(sg_host_cache* hc) {
+  if (!hc) {
+    set_error("cache NULL");
+    return SG_ERR_INVALID_ARG;
+  }
+  hc->failed.clear();
   return SG_OK;
 }
 
@@ -216,12 +227,23 @@ extern "C" sg_status sg_stream_requests(sg_volume* v, int slot, sg_host_cache* h
   const uint64_t per_node = (uint64_t)hc->entry_bytes * v->nch;
   const size_t budget = per_node ? (size_t)std::min<uint64_t>(max_bytes / per_node, req.size()) : 0;
   ++hc->frame;
-  // place every (node, channel) of the budget in the host cache
+  const sg_volume_desc& kd = container_desc(hc->k);
+  const int64_t knodes = container_nodes(hc->k);
+  auto key_of = [&](int c, int32_t node) { return ((int64_t)t * kd.channels + c) * knodes + node; };
+  // place every (node, channel) of the budget in the host cache; a brick
+  // whose chunk failed before is skipped without spending budget
   std::vector<int32_t> nodes;
   std::vector<std::vector<const void*>> ptrs(v->nch);
   std::vector<std::pair<int64_t, int64_t>> todo;
-  for (size_t i = 0; i < budget; ++i) {
+  std::vector<size_t> todo_node;  // index into nodes of each queued read
+  for (size_t i = 0; i < req.size() && nodes.size() < budget; ++i) {
     const int32_t node = req[i];
+    bool bad = false;
+    for (int c = 0; c < v->nch && !bad; ++c) bad = hc->failed.count(key_of(c, node)) > 0;
+    if (bad) {
+      ++s0.failed;
+      continue;
+    }
     std::vector<int64_t> ent(v->nch);
     bool ok = true;
     size_t todo_mark = todo.size();
@@ -248,12 +270,13 @@ extern "C" sg_status sg_stream_requests(sg_volume* v, int slot, sg_host_cache* h
       if (st == SG_ERR_OOM) break;
       continue;
     }
+    while (todo_node.size() < todo.size()) todo_node.push_back(nodes.size());
     nodes.push_back(node);
     for (int c = 0; c < v->nch; ++c) ptrs[c].push_back(hc->arena + (size_t)ent[c] * hc->entry_bytes);
   }
   // read + decompress the misses on a pool of threads
   std::atomic<size_t> next(0);
-  std::atomic<int> failed(0);
+  std::vector<uint8_t> fail(todo.size(), 0);
   std::atomic<uint64_t> disk_bytes(0);
   auto work = [&]() {
     for (;;) {
@@ -262,7 +285,7 @@ extern "C" sg_status sg_stream_requests(sg_volume* v, int slot, sg_host_cache* h
       uint32_t comp = 0;
       if (container_read_chunk(hc->k, (uint64_t)todo[i].second, hc->arena + (size_t)todo[i].first * hc->entry_bytes,
                                nullptr, &comp) != SG_OK)
-        failed.fetch_add(1);
+        fail[i] = 1;
       disk_bytes.fetch_add(comp);
     }
   };
@@ -271,12 +294,34 @@ extern "C" sg_status sg_stream_requests(sg_volume* v, int slot, sg_host_cache* h
   for (int i = 1; i < nt; ++i) pool.emplace_back(work);
   if (nt >= 1) work();
   for (auto& th : pool) th.join();
-  if (failed.load()) {
-    for (auto& e : todo) host_cache_drop(hc, e.first);
-    set_error("sg_stream_requests: a chunk failed to read or decompress");
-    return SG_ERR_IO;
+  // a failed chunk: its entry is dropped, its key remembered, and its brick
+  // (every channel) left out of the upload, so it stays non-resident and
+  // its parent keeps rendering; the other bricks are served
+  int32_t nfail = 0;
+  std::vector<uint8_t> drop(nodes.size(), 0);
+  for (size_t i = 0; i < todo.size(); ++i)
+    if (fail[i]) {
+      const int64_t key = hc->owner[todo[i].first];
+      hc->failed.insert(key);
+      host_cache_drop(hc, todo[i].first);
+      drop[todo_node[i]] = 1;
+      ++nfail;
+    }
+  if (nfail) {
+    size_t w = 0;
+    for (size_t i = 0; i < nodes.size(); ++i) {
+      if (drop[i]) {
+        ++s0.failed;
+        continue;
+      }
+      nodes[w] = nodes[i];
+      for (int c = 0; c < v->nch; ++c) ptrs[c][w] = ptrs[c][i];
+      ++w;
+    }
+    nodes.resize(w);
+    for (int c = 0; c < v->nch; ++c) ptrs[c].resize(w);
   }
-  s0.disk_reads = (int32_t)todo.size();
+  s0.disk_reads = (int32_t)todo.size() - nfail;
   s0.disk_bytes = disk_bytes.load();
   // one list upload per channel (the first places the slots)
   int32_t placed = (int32_t)nodes.size();
@@ -289,5 +334,10 @@ extern "C" sg_status sg_stream_requests(sg_volume* v, int slot, sg_host_cache* h
   s0.served = placed;
   s0.upload_bytes = (uint64_t)placed * per_node;
   if (stats) *stats = s0;
+  if (s0.failed) {
+    set_error("sg_stream_requests: " + std::to_string(s0.failed) +
+              " requested bricks have a chunk that failed to read or decompress; the others were served");
+    return SG_ERR_IO;
+  }
   return SG_OK;
 }

@@ -28,7 +28,7 @@ EXPORTS = ["sg_volume_create", "sg_volume_destroy", "sg_upload_volume_device", "
            "sg_unet_adam_step", "sg_unet_set_tensor_path", "sg_unet_check", "sg_unet_wait_selftest", "sg_psnr", "sg_read_ranges", "sg_upload_brick_list", "sg_unwarp", "sg_set_channel_shading",
            "sg_container_create", "sg_container_open", "sg_container_append", "sg_container_finish",
            "sg_container_get_info", "sg_container_read", "sg_container_close", "sg_host_cache_create",
-           "sg_host_cache_destroy", "sg_host_cache_fetch", "sg_stream_requests",
+           "sg_host_cache_destroy", "sg_host_cache_fetch", "sg_host_cache_clear_failures", "sg_stream_requests",
            "sg_last_error",
            "sg_version"]
 
@@ -66,7 +66,7 @@ class sg_container_info(ctypes.Structure):
 
 class sg_stream_stats(ctypes.Structure):
     _fields_ = [("requested", ctypes.c_int32), ("served", ctypes.c_int32), ("host_hits", ctypes.c_int32),
-                ("disk_reads", ctypes.c_int32), ("missing", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("disk_reads", ctypes.c_int32), ("missing", ctypes.c_int32), ("failed", ctypes.c_int32),
                 ("disk_bytes", ctypes.c_uint64), ("upload_bytes", ctypes.c_uint64)]
 
 
@@ -123,6 +123,7 @@ def _load():
         "sg_host_cache_create": [vp, ctypes.c_uint64, i32, i32, P(vp)],
         "sg_host_cache_destroy": [vp],
         "sg_host_cache_fetch": [vp, i32, i32, i64, P(vp), P(ctypes.c_int)],
+        "sg_host_cache_clear_failures": [vp],
         "sg_stream_requests": [vp, i32, vp, ctypes.c_uint64, P(sg_stream_stats), vp],
         "sg_set_transfer_function": [vp, i32, vp, i32, f32, f32, f32, vp],
         "sg_select_lod": [vp, P(sg_pose), P(sg_select_stats), vp],
@@ -312,9 +313,21 @@ def sg_host_cache_fetch(hc, t, c, node):
 
 
 def sg_stream_requests(vol, slot, hc, max_bytes, stream=None):
+    """Serves a selection's requests; returns the stats as a dict. A call in
+    which some chunks failed (SG_ERR_IO) still served the others: it returns
+    the stats (failed > 0) instead of raising."""
     st = sg_stream_stats()
-    _check(lib.sg_stream_requests(vol, slot, hc, int(max_bytes), ctypes.byref(st), _stream(stream)))
-    return {f[0]: getattr(st, f[0]) for f in sg_stream_stats._fields_ if f[0] != "reserved"}
+    status = lib.sg_stream_requests(vol, slot, hc, int(max_bytes), ctypes.byref(st), _stream(stream))
+    if status != SG_ERR_IO:
+        _check(status)
+    out = {f[0]: getattr(st, f[0]) for f in sg_stream_stats._fields_}
+    if status == SG_ERR_IO and out["failed"] == 0:
+        _check(status)  # an I/O error that left no stats
+    return out
+
+
+def sg_host_cache_clear_failures(hc):
+    _check(lib.sg_host_cache_clear_failures(hc))
 
 
 def sg_set_channel_shading(vol, c, gradient=False, palette=None, near=0.0, far=1.0, stream=None):

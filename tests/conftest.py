@@ -1,3 +1,4 @@
+import json
 import os
 import sys
 
@@ -6,6 +7,10 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+
+# achieved errors per output, written at the end of the session to the JSON
+# file named by SG_PARITY_RECORD (nothing is written without it)
+_RECORD = {}
 
 
 def pytest_configure(config):
@@ -24,3 +29,20 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture
+def record_error(request):
+    """record_error(output_name, **figures): keeps the achieved error figures
+    of one compared output under the test's name."""
+    def rec(name, **figures):
+        clean = {k: (float(v) if hasattr(v, "__float__") else v) for k, v in figures.items()}
+        _RECORD.setdefault(request.node.nodeid, {})[name] = clean
+    return rec
+
+
+def pytest_sessionfinish(session, exitstatus):
+    path = os.environ.get("SG_PARITY_RECORD")
+    if path and _RECORD:
+        with open(path, "w") as f:
+            json.dump(_RECORD, f, indent=1, sort_keys=True)

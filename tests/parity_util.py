@@ -151,5 +151,13 @@ def compare_image(img, ref, counts=None, tol=TOL, max_unresolved=0):
                                  f"nearest variant {vl[i, j]} of {nv[i]} flags {fl[idx[i]]}")
     nunres = int(unres.sum())
     assert nunres <= max_unresolved, f"{nunres} pixels the oracle cannot resolve (flags {np.unique(fl[unres])})"
-    return dict(max_err=float(err.max()) if n else 0.0, max_err_ambiguous=amb_err,
-                ambiguous=float(amb.mean()) if n else 0.0, unresolved=nunres, n=n)
+    # achieved errors: |gpu - oracle| where the termination decision is not
+    # in question (early == late), else the distance to the [early, late]
+    # bracket
+    tie = (fl & oracle.FL_TERM) != 0
+    plain = strict & ~tie
+    e_plain = float(np.abs(img - ref["late"])[plain].max()) if plain.any() else 0.0
+    d_br = np.maximum(np.minimum(ref["early"], ref["late"]) - img, img - np.maximum(ref["early"], ref["late"]))
+    e_tie = float(np.maximum(d_br, 0.0)[strict & tie].max()) if (strict & tie).any() else 0.0
+    return dict(max_err=e_plain, max_err_termination_bracket=e_tie, max_err_ambiguous=amb_err,
+                ambiguous=float(amb.mean()) if n else 0.0, termination_ties=int(tie.sum()), unresolved=nunres, n=n)

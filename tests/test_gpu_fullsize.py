@@ -10,6 +10,7 @@ bit."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from parity_util import GpuCase, compare_image, compare_selection
 
@@ -31,7 +32,7 @@ def bench_case():
 
 
 @pytest.mark.parametrize("pose_index", [0, 37])
-def test_full_size_stereo_frame_on_sampled_pixels(bench_case, pose_index):
+def test_full_size_stereo_frame_on_sampled_pixels(bench_case, pose_index, record_error):
     import torch
     from paper_1804_08197_b300 import sg
     case = bench_case
@@ -55,9 +56,19 @@ def test_full_size_stereo_frame_on_sampled_pixels(bench_case, pose_index):
         st = compare_image(imgs[e][pix], oref)
         assert st["n"] == len(pix)
         compare_image(plain[e][pix], oref, cnts[e][pix])
+        # max |gpu - oracle| per RGBA channel over the sampled pixels with no
+        # ambiguous lattice point and no termination tie
+        keep = np.ones(len(pix), bool)
+        keep[oref["var_idx"]] = False
+        keep &= (oref["flags"] & oracle.FL_TERM) == 0
+        ch = np.abs(imgs[e][pix][keep] - oref["late"][keep]).max(axis=0)
+        record_error(f"eye {e} image", max_abs_err_rgba=[float(v) for v in ch],
+                     max_err_termination_bracket=st["max_err_termination_bracket"],
+                     max_abs_err_ambiguous=st["max_err_ambiguous"], ambiguous_fraction=st["ambiguous"],
+                     termination_ties=st["termination_ties"], pixels=st["n"])
 
 
-def test_full_size_batched_4d_on_sampled_pixels():
+def test_full_size_batched_4d_on_sampled_pixels(record_error):
     """The batched 4D workload at full size, as bench.py times it: 16 time
     points of 512 x 512 x 256 u16 with 2 channels (blob seed 1003, tables 2003
     / 2004 over [200, 40000], additive blend), 3 stereo viewers at 1440 x
@@ -107,6 +118,7 @@ def test_full_size_batched_4d_on_sampled_pixels():
             g.replay()
         torch.cuda.synchronize()
         otfs = [oracle.make_tf(tb, 200.0, 40000.0) for tb in tabs]
+        worst, amb = 0.0, []
         for t in (0, 9, 15):
             ovol = oracle.Volume([oracle.pyramid(data[(t, c)], LEVELS) for c in range(2)], BRICK, model=model)
             ranges = ovol.block_ranges()
@@ -119,12 +131,16 @@ def test_full_size_batched_4d_on_sampled_pixels():
                     pix = np.arange(7 * e + t + i, w * h, 211)
                     oref = ovol.render(otfs, ref["leaf"], views[e], projs[e], w, h, step=0.5, pixels=pix)
                     img = outs[2 * (t * 3 + i) + e].cpu().numpy().reshape(-1, 4)
-                    compare_image(img[pix], oref)
+                    st = compare_image(img[pix], oref)
+                    worst = max(worst, st["max_err"])
+                    amb.append(st["ambiguous"])
+        record_error("96 images (time points 0, 9, 15 sampled)", max_abs_err=worst,
+                     ambiguous_fraction_mean=float(np.mean(amb)))
     finally:
         sg.sg_volume_destroy(vol)
 
 
-def test_full_size_learned_forward_on_sampled_crops():
+def test_full_size_learned_forward_on_sampled_crops(record_error):
     """The learned reconstruction's network at the bench's size (both eyes of
     720 x 800 -> 1440 x 1600, the persistent tcgen05 convolution over 1200
     tiles per layer) against the FP64 network oracle on sampled crops. The
@@ -132,8 +148,10 @@ def test_full_size_learned_forward_on_sampled_crops():
     input pixels: 3x3 convolutions at three levels, two 2x2 pools, two 2x
     upsamplings) from a crop's edge is the same computed on the crop or on
     the whole image, when the crop keeps the pooling grid (origin a multiple
-    of 4). The oracle runs 96 x 96 crops; their centres (and, for a corner
-    crop, the region along the image edges) are compared at BF16 tolerance."""
+    of 4). The oracle runs its BF16 network on 96 x 96 crops; their centres
+    (and, for a corner crop, the region along the image edges) must match
+    element by element within 8 sigma (the per-element spread of an
+    FP32-accumulating implementation, from the oracle)."""
     import torch
     import oracle.unet as ou
     from paper_1804_08197_b300 import sg
@@ -161,13 +179,17 @@ def test_full_size_learned_forward_on_sampled_crops():
         # (image, crop origin y, x, valid rows / columns of the crop in input pixels)
         crops = [(0, 352, 312, (R, C - R), (R, C - R)), (1, 100, 600, (R, C - R), (R, C - R)),
                  (1, 704, 204, (R, C - R), (R, C - R)), (0, 0, 0, (0, C - R), (0, C - R))]
+        worst = dict(max_abs_err=0.0, max_sigma_ratio=0.0, n=0)
         for n, y0, x0, (ya, yb), (xa, xb) in crops:
             xc = x[n:n + 1, y0:y0 + C, x0:x0 + C].astype(np.float64)
-            ref = ou.forward(q, xc)[0]
-            base = ou.bilinear2x(xc)[0]
+            ref, sig = ou.bf16_forward(q, xc)
             sl = (slice(2 * ya, 2 * yb), slice(2 * xa, 2 * xb))
             g = gpu[n, 2 * y0:2 * y0 + 2 * C, 2 * x0:2 * x0 + 2 * C][sl]
-            r_gpu, r_ref = g - base[sl], ref[sl] - base[sl]
-            assert np.linalg.norm(r_gpu - r_ref) <= 2e-2 * np.linalg.norm(r_ref), (n, y0, x0)
+            err = np.abs(g - ref[0][sl])
+            ratio = err / sig[0][sl]
+            assert (ratio <= 8.0).all(), ((n, y0, x0), int((ratio > 8.0).sum()), ratio.max())
+            worst = dict(max_abs_err=max(worst["max_abs_err"], err.max()),
+                         max_sigma_ratio=max(worst["max_sigma_ratio"], ratio.max()), n=worst["n"] + err.size)
+        record_error("output (4 crops of 2 x 720 x 800)", **worst)
     finally:
         sg.sg_unet_destroy(net)

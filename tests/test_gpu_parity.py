@@ -18,7 +18,7 @@ def _c1_case():
     return case
 
 
-def test_plain_ray_cast_single_view_matches_oracle():
+def test_plain_ray_cast_single_view_matches_oracle(record_error):
     """128^3 uint8 Gaussians, one 256x256 view, step 0.5 (the plain single-view case)."""
     case = _c1_case()
     try:
@@ -27,7 +27,8 @@ def test_plain_ray_cast_single_view_matches_oracle():
         compare_selection(gsel, ref)
         imgs, cnts = case.render(pose, empty_skip=0)
         oref = case.oracle_render(ref["leaf"], view, proj, 256, 256)
-        compare_image(imgs[0], oref, cnts[0])
+        st = compare_image(imgs[0], oref, cnts[0])
+        record_error("image 256 x 256", **st)
         assert np.array_equal(imgs[0], imgs[1])  # both eyes share the view
         assert oref["late"][:, 3].max() > 0.5
         skip, _ = case.render(pose, empty_skip=1)
@@ -45,7 +46,7 @@ def _filament_case(dims=(256, 256, 256), brick=32, levels=4, seed=1002, ntubes=4
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_multilod_stereo_pair_matches_oracle(seed):
+def test_multilod_stereo_pair_matches_oracle(seed, record_error):
     case = _filament_case()
     try:
         W, H = 360, 400
@@ -58,7 +59,8 @@ def test_multilod_stereo_pair_matches_oracle(seed):
         imgs, cnts = case.render(pose, empty_skip=0)
         for e in range(2):
             oref = case.oracle_render(ref["leaf"], views[e], projs[e], W, H)
-            compare_image(imgs[e], oref, cnts[e])
+            st = compare_image(imgs[e], oref, cnts[e])
+            record_error(f"eye {e} image", **st)
         skip, _ = case.render(pose, empty_skip=1)
         assert np.array_equal(skip[0], imgs[0]) and np.array_equal(skip[1], imgs[1])
         assert len(levels) >= 1

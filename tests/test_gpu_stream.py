@@ -307,3 +307,115 @@ def test_streaming_from_a_container_through_the_host_cache(tmp_path):
         sg.sg_host_cache_destroy(hc)
         sg.sg_volume_destroy(vol)
         sg.sg_container_close(k)
+
+
+def _corrupt_chunk(path, node, nbytes=16):
+    """Overwrites part of the payload of node's chunk (time point 0, channel
+    0) in a finished container: footer -> index -> chunk header (48 bytes) ->
+    payload. The chunk's checksum no longer matches."""
+    import struct
+    data = bytearray(open(path, "rb").read())
+    magic, version, index_off, chunks = struct.unpack_from("<IIQQ", data, len(data) - 24)
+    for i in range(chunks):
+        key, off = struct.unpack_from("<qQ", data, index_off + 16 * i)
+        if key == node:
+            p = off + 48 + 8
+            data[p:p + nbytes] = bytes((b ^ 0x5A) for b in data[p:p + nbytes])
+            open(path, "wb").write(bytes(data))
+            return
+    raise AssertionError(f"no chunk for node {node}")
+
+
+def test_streaming_survives_unreadable_chunks(tmp_path):
+    """Failure injected on the host: two level-0 chunks of the container are
+    overwritten on disk after conversion. sg_stream_requests serves every
+    other request, reports the two (SG_ERR_IO with stats, `failed`), and
+    skips them in later frames without spending budget, so streaming keeps
+    making progress. Their parents keep rendering in their place ("Octree
+    Representation"): frame by frame the GPU cache equals the oracle's and
+    the selection equals the oracle's for that residency, the view converges
+    with only the two bricks still requested, and the image matches the
+    oracle's."""
+    import torch
+    from paper_1804_08197_b300 import sg
+    a = synth.filaments_u16(DIMS, seed=33, ntubes=18)
+    model = synth.volume_model(128, 0.5)
+    ovol = oracle.Volume([oracle.pyramid(a, LEVELS)], B, model=model)
+    full = ovol.block_ranges()
+    table = synth.tf_piecewise(2002, zero_alpha_points=2)
+    otf = oracle.make_tf(table, 300.0, 60000.0)
+    path = tmp_path / "vol.sgc"
+    desc = sg.volume_desc(DIMS, sg.SG_U16, B, LEVELS, model=model)
+    k = sg.sg_container_create(path, desc)
+    for n in range(ovol.node_count):
+        L, b = ovol.node_coords(n)
+        sg.sg_container_append(k, 0, 0, L, *b, _brick(ovol, L, *b), *full[n, 0])
+    sg.sg_container_finish(k)
+    sg.sg_container_close(k)
+    W, H, tau = 192, 208, 0.3
+    views, projs = _stereo((-0.3, 0.05, 0.2), (-0.1, 0.0, 0.0), W, H)
+    st_full = ovol.select([otf], views, projs, H, tau=tau)["state"]
+    lvl0 = [n for n in np.flatnonzero(st_full == oracle.ST_SELECTED) if ovol.node_coords(int(n))[0] == 0]
+    bad = {int(lvl0[len(lvl0) // 3]), int(lvl0[2 * len(lvl0) // 3])}
+    for n in bad:
+        _corrupt_chunk(path, n)
+    k = sg.sg_container_open(path)
+    need = int(np.isin(st_full, [oracle.ST_SELECTED, oracle.ST_FALLBACK, oracle.ST_REFINED]).sum())
+    brick_bytes = ((B + 2) ** 3 * 2 + 255) // 256 * 256
+    vol = sg.sg_volume_create(DIMS, sg.SG_U16, B, LEVELS, device_pool_bytes=(need + 8) * brick_bytes, model=model)
+    hc = sg.sg_host_cache_create(k, (need + 8) * (B + 2) ** 3 * 2, pinned=True, threads=4)
+    try:
+        sg.sg_set_transfer_function(vol, 0, table, 300.0, 60000.0)
+        for L in range(LEVELS):
+            nbx, nby, nbz = ovol.blocks_per_axis(L)
+            xyz = np.array([(x, y, z) for z in range(nbz) for y in range(nby) for x in range(nbx)])
+            lo, hi = ovol.level_offsets[L], ovol.level_offsets[L + 1]
+            sg.sg_set_brick_ranges(vol, 0, 0, L, xyz, full[lo:hi, 0, :])
+        root = int(ovol.level_offsets[LEVELS - 1])
+        ptr, _ = sg.sg_host_cache_fetch(hc, 0, 0, root)
+        assert sg.sg_upload_brick_list(vol, 0, 0, [root], [ptr]) == 1
+        cache = oracle.Cache(ovol, need + 8)
+        cache.place([root])
+        pose = sg.make_pose(views, projs, W, H, pixel_error=tau)
+        failed, known_bad = 0, set()
+        for frame in range(40):
+            stats = sg.sg_select_lod(vol, pose, stats=True)
+            res = sg.sg_read_residency(vol, 0, ovol.node_count) >= 0
+            assert np.array_equal(res, cache.resident != 0)
+            ref = cache.select([otf], views, projs, H, tau=tau, ranges=full)
+            compare_selection(sg.sg_read_selection(vol, 0, len(ref["leaf"]), ovol.node_count), ref)
+            if set(int(n) for n in ref["requests"]) <= bad:
+                break
+            st = sg.sg_stream_requests(vol, 0, hc, 24 * (B + 2) ** 3 * 2)
+            failed += st["failed"]
+            # a bad brick met for the first time is read (and fails) within
+            # the budget; once known it is skipped without spending any
+            order = sorted((int(n) for n in ref["requests"]), key=lambda n: (-ovol.node_coords(n)[0], n))
+            taken = [n for n in order if n not in known_bad][:24]
+            assert st["failed"] == len(known_bad & set(order)) + len(bad & set(taken))
+            known_bad |= bad & set(taken)
+            m, _ = cache.place([n for n in taken if n not in bad])
+            assert m == st["served"] and st["missing"] == 0
+        else:
+            raise AssertionError("streaming made no progress past the unreadable chunks")
+        # both bad bricks were requested, reported, never placed; their
+        # parents render as fallbacks
+        assert known_bad == bad and failed >= len(bad)
+        assert not res[list(bad)].any() and stats["fallback"] > 0
+        assert set(int(n) for n in ref["requests"]) == bad
+        outs = [torch.empty((H, W, 4), device="cuda") for _ in range(2)]
+        sg.sg_render(vol, pose, sg.render_params(), outs)
+        torch.cuda.synchronize()
+        for e in range(2):
+            compare_image(outs[e].cpu().numpy().reshape(-1, 4),
+                          ovol.render([otf], ref["leaf"], views[e], projs[e], W, H))
+        # after clearing the failures the chunks are tried (and fail) again
+        sg.sg_host_cache_clear_failures(hc)
+        sg.sg_select_lod(vol, pose)
+        cache.select([otf], views, projs, H, tau=tau, ranges=full)
+        st = sg.sg_stream_requests(vol, 0, hc, 24 * (B + 2) ** 3 * 2)
+        assert st["failed"] == len(bad) and st["served"] == 0
+    finally:
+        sg.sg_host_cache_destroy(hc)
+        sg.sg_volume_destroy(vol)
+        sg.sg_container_close(k)

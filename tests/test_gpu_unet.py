@@ -1,7 +1,10 @@
-"""Learned reconstruction on the GPU against the FP64 network oracle:
-forward outputs and gradients at BF16 tolerance, the untrained (zero-head)
-network as exact bilinear upsampling, the PSNR kernel's closed form, and a
-short training run that must beat the method without the network."""
+"""Learned reconstruction on the GPU against the network oracle: every
+output value and every weight and bias gradient of every convolution path
+within 8 sigma of the BF16 network (sigma: the per-element spread of an
+FP32-accumulating implementation, propagated by the oracle from the BF16
+rounding points), the untrained (zero-head) network as exact bilinear
+upsampling, the PSNR kernel's closed form, and a short training run that
+must beat the method without the network."""
 import numpy as np
 import pytest
 
@@ -46,7 +49,48 @@ def _run(net, x, t=None):
     return np.stack([o.cpu().numpy() for o in out]).astype(np.float64), loss
 
 
-def test_forward_and_gradients_match_the_oracle_at_bf16_tolerance():
+K = 8.0  # |gpu - oracle| <= K sigma, element by element
+
+
+def _oracle_params(p):
+    """the parameters as the tensor cores see them: BF16 weights, FP32 biases"""
+    q = p.astype(np.float64).copy()
+    for ws, _ in ou.layer_slices():
+        q[ws] = _bf16(p[ws])
+    return q
+
+
+def check_elementwise(name, got, ref, sigma, record=None):
+    """every element within K sigma; returns the achieved figures"""
+    err = np.abs(np.asarray(got, np.float64) - ref)
+    ratio = err / np.maximum(sigma, 1e-300)
+    bad = ratio > K
+    assert not bad.any(), (f"{name}: {int(bad.sum())} of {bad.size} elements beyond {K} sigma; worst "
+                           f"{ratio.max():.2f} sigma (|err| {err.reshape(-1)[np.argmax(ratio)]:.3g})")
+    fig = dict(max_abs_err=err.max(), max_sigma_ratio=ratio.max(), max_abs_ref=np.abs(ref).max(), n=err.size)
+    if record:
+        record(name, **fig)
+    return fig
+
+
+def check_network(gpu_out, gpu_loss, g_gpu, p, x, t, record=None, tag=""):
+    """outputs, loss and every gradient against the BF16 network oracle"""
+    q = _oracle_params(p)
+    x32 = x.astype(np.float32).astype(np.float64)
+    t32 = t.astype(np.float32).astype(np.float64)
+    loss, g, sg, out, so = ou.bf16_loss_grad(q, x32, t32)
+    check_elementwise(tag + "output", gpu_out, out, so, record)
+    cnt = out.size
+    sl = np.sqrt(np.sum((2.0 * (out - t32) * so / cnt) ** 2)) + 2.0 ** -23 * np.sqrt(cnt) * loss
+    assert abs(gpu_loss - loss) <= K * sl, (gpu_loss, loss, sl)
+    if record:
+        record(tag + "loss", abs_err=abs(gpu_loss - loss), sigma=sl)
+    for L, (ws, bs) in enumerate(ou.layer_slices()):
+        check_elementwise(f"{tag}{ou.NAMES[L]}.dW", g_gpu[ws], g[ws], sg[ws], record)
+        check_elementwise(f"{tag}{ou.NAMES[L]}.db", g_gpu[bs], g[bs], sg[bs], record)
+
+
+def test_forward_and_gradients_match_the_oracle_element_by_element(record_error):
     from paper_1804_08197_b300 import sg
     net = sg.sg_unet_create(2, 16, 24, seed=3)
     try:
@@ -58,31 +102,21 @@ def test_forward_and_gradients_match_the_oracle_at_bf16_tolerance():
         x = rng.uniform(0, 1, (2, 16, 24, 4))
         t = rng.uniform(0, 1, (2, 32, 48, 4))
         gpu_out, gpu_loss = _run(net, x, t)
+        sg.sg_unet_check(net)
         g_gpu = sg.sg_unet_get_params(net, which=1).astype(np.float64)
-        # the oracle sees the BF16-rounded weights the tensor cores use (biases stay FP32)
-        q = p.astype(np.float64).copy()
-        for ws, _ in ou.layer_slices():
-            q[ws] = _bf16(p[ws])
-        loss, g_ref, out_ref = ou.loss_grad(q, x, t)
-        base = ou.bilinear2x(x)
-        r_gpu, r_ref = gpu_out - base, out_ref - base
-        assert np.linalg.norm(r_gpu - r_ref) <= 2e-2 * np.linalg.norm(r_ref)
-        assert gpu_loss == pytest.approx(loss, rel=1e-2)
-        for L, (ws, bs) in enumerate(ou.layer_slices()):
-            for sl in (ws, bs):
-                ref = g_ref[sl]
-                err = np.linalg.norm(g_gpu[sl] - ref)
-                assert err <= 5e-2 * np.linalg.norm(ref) + 1e-12, (ou.NAMES[L], err / np.linalg.norm(ref))
+        check_network(gpu_out, gpu_loss, g_gpu, p, x, t, record_error)
     finally:
         sg.sg_unet_destroy(net)
 
 
-def test_tcgen05_and_mma_sync_paths_agree():
-    """The tcgen05 (TMEM; implicit GEMM and halo reuse) and mma.sync
-    convolutions compute the same BF16 products with FP32 sums: outputs and
-    gradients agree to summation order."""
+def test_every_convolution_path_matches_the_oracle_element_by_element(record_error):
+    """The tcgen05 paths (TMEM; implicit GEMM, halo reuse with cp.async or
+    TMA row segments, the persistent warp-specialised kernel) and the
+    mma.sync path compute the same BF16 products with FP32 sums in different
+    orders: each is within 8 sigma of the BF16 network on every output and
+    gradient. Two row segments of 128 pixels per row (140 columns)."""
     from paper_1804_08197_b300 import sg
-    net = sg.sg_unet_create(2, 24, 140, seed=11)  # 140 columns: two 128-pixel segments per row
+    net = sg.sg_unet_create(2, 24, 140, seed=11)
     try:
         p = _random_params(12, sg.sg_unet_param_count(net))
         sg.sg_unet_set_params(net, p)
@@ -95,22 +129,10 @@ def test_tcgen05_and_mma_sync_paths_agree():
             out, loss = _run(net, x, t)
             sg.sg_unet_check(net)
             res[path] = (out, loss, sg.sg_unet_get_params(net, which=1).astype(np.float64))
+            check_network(out, loss, res[path][2], p, x, t, record_error if path == 4 else None, f"path{path}.")
         # TMA staging of the row segments moves the same bytes to the same
-        # places: identical outputs to the cp.async halo path (the loss and
-        # gradient reductions may sum in another order from run to run)
+        # places: identical outputs to the cp.async halo path
         assert np.array_equal(res[3][0], res[2][0])
-        assert res[3][1] == pytest.approx(res[2][1], rel=1e-6)
-        assert np.allclose(res[3][2], res[2][2], rtol=1e-5, atol=1e-7)
-        base = ou.bilinear2x(x)
-        for path in (1, 2, 4):
-            r0, r1 = res[0][0] - base, res[path][0] - base
-            # shared BF16 rounding points, different FP32 summation order
-            assert np.linalg.norm(r1 - r0) <= 5e-3 * np.linalg.norm(r0), path
-            assert res[path][1] == pytest.approx(res[0][1], rel=1e-4)
-            for ws, bs in ou.layer_slices():
-                for sl in (ws, bs):
-                    g0, g1 = res[0][2][sl], res[path][2][sl]
-                    assert np.linalg.norm(g1 - g0) <= 2e-2 * np.linalg.norm(g0) + 1e-12, path
     finally:
         sg.sg_unet_destroy(net)
 
@@ -152,12 +174,13 @@ def test_persistent_convolution_over_many_tiles():
         sg.sg_unet_destroy(net)
 
 
-def test_tensor_core_weight_gradients_agree_with_mma_sync():
+def test_tensor_core_weight_gradients_match_the_oracle_element_by_element(record_error):
     """With widths that are multiples of 8 at every level (32 x 64, 16 x 32,
     8 x 16) the weight and bias gradients run on tcgen05 (pixels as the
     contraction over transposed, row-padded operands, one TMEM accumulator
-    per tap, pixel splits summed in a fixed order); they agree with the
-    mma.sync path to summation order, and repeat exactly on a second run."""
+    per tap, pixel splits summed in a fixed order): every gradient is within
+    8 sigma of the BF16 network's, for the tcgen05 and the mma.sync weight
+    gradients alike, and repeats exactly on a second run."""
     from paper_1804_08197_b300 import sg
     net = sg.sg_unet_create(3, 32, 64, seed=31)
     try:
@@ -174,12 +197,9 @@ def test_tensor_core_weight_gradients_agree_with_mma_sync():
             g = sg.sg_unet_get_params(net, which=1).astype(np.float64)
             if path in res:
                 assert np.array_equal(g, res[path][1])
+                continue
             res[path] = (loss, g)
-        assert res[4][0] == pytest.approx(res[0][0], rel=1e-4)
-        for L, (ws, bs) in enumerate(ou.layer_slices()):
-            for sl in (ws, bs):
-                g0, g1 = res[0][1][sl], res[4][1][sl]
-                assert np.linalg.norm(g1 - g0) <= 2e-2 * np.linalg.norm(g0) + 1e-12, (ou.NAMES[L], sl)
+            check_network(out, loss, g, p, x, t, record_error if path == 4 else None, f"wgrad_path{path}.")
     finally:
         sg.sg_unet_destroy(net)
 
