@@ -496,6 +496,15 @@ typedef struct {
 sg_status sg_set_render_config(sg_volume* vol, const sg_render_config* cfg);
 sg_status sg_get_render_config(sg_volume* vol, sg_render_config* cfg);
 
+/* The autotuner's picks, kept across runs in a text file of lines
+ * "<key> TAB <persistent> <tile_w> <tile_h> <rays_per_thread>" (the key names
+ * the GPU and workload; a later line for a key replaces an earlier one).
+ * store appends one; lookup sets *found and, when found, *cfg (a missing
+ * file is an empty cache). Errors: INVALID_ARG (NULL, key with a tab or
+ * newline, unsupported configuration), IO. */
+sg_status sg_render_config_store(const char* path, const char* key, const sg_render_config* cfg);
+sg_status sg_render_config_lookup(const char* path, const char* key, sg_render_config* cfg, int* found);
+
 /* Autotuner: renders the n selected poses with every supported configuration
  * (one warm-up launch, then reps timed launches each, CUDA events on the
  * stream), keeps the fastest as the volume's configuration and returns it
@@ -578,6 +587,43 @@ sg_status sg_unet_adam_step(sg_unet* net, float lr, float beta1, float beta2, fl
 /* PSNR of a against b over count floats in [0, 1]: 10 log10(1 / MSE), into
  * the device float out_db (1000 when identical). */
 sg_status sg_psnr(const float* a, const float* b, int64_t count, float* out_db, void* stream);
+
+/* Saves the network's training state to a file: the FP32 parameters, both
+ * Adam moments and the step count (a checkpoint to resume training from, or
+ * to serve a trained network without retraining). Synchronous. Errors:
+ * INVALID_ARG, IO, CUDA. */
+sg_status sg_unet_save(sg_unet* net, const char* path);
+/* Restores a checkpoint written by sg_unet_save for this network (same
+ * parameter count) and refreshes the BF16 weights. Synchronous. Errors:
+ * INVALID_ARG, IO (missing, truncated or another network's file), CUDA. */
+sg_status sg_unet_load(sg_unet* net, const char* path);
+
+/* One learned frame (the method's reconstruction path, not in the paper). */
+typedef struct {
+  float step;               /* full-rate sample spacing, level-0 voxels; the reduced render uses 2 step */
+  float term_alpha;         /* early termination (0 = 0.99) */
+  float pixel_error_half;   /* tau of the reduced render (0 = pose->pixel_error / 2: the full image's detail) */
+  float threshold_db;       /* judging: fall back to the full-rate render below this stereo PSNR */
+  int32_t judge;            /* 1: also render the full-rate frame, compute the PSNR, fall back */
+  int32_t half_slot;        /* selection slot of the reduced pose (0..255, not pose->slot) */
+  int32_t reserved[2];
+  sg_render_config half_config, full_config; /* launch shapes (all zero: the volume's own) */
+} sg_learned_params;
+
+/* A learned stereo frame, all on the device, asynchronous on stream (no
+ * host synchronisation): selects and renders the pose at half resolution
+ * (width/2 x height/2 per eye, multiples of 4) and twice the step, then
+ * reconstructs both eyes with the network into out_rgba[2] (caller-owned
+ * device FP32, width x height x 4 each). With prm->judge it also selects
+ * and renders the plain full-rate frame (the yardstick), writes psnr_db[0..2]
+ * (device: eye 0, eye 1, and the stereo PSNR 10 log10(1 / mean of the two
+ * eyes' MSE)) and *fell_back (device int32); a frame below
+ * prm->threshold_db gets the full-rate render in out_rgba instead. The
+ * reduced and full-rate images live in buffers of the network, grown on
+ * first use. The pose's own selection slot takes the full-rate selection.
+ * Errors: INVALID_ARG, STATE, OOM, CUDA. */
+sg_status sg_render_learned(sg_volume* vol, sg_unet* net, const sg_pose* pose, const sg_learned_params* prm,
+                            float* out_rgba[2], float* psnr_db, int32_t* fell_back, void* stream);
 
 /* Thread-local message of the last failure on this thread ("" if none). */
 const char* sg_last_error(void);

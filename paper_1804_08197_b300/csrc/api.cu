@@ -498,6 +498,51 @@ sg_status sg_upload_volume_device(sg_volume* v, int t, int c, const void* dev_le
   return refresh_flags(v, s);
 }
 
+// ---------------------------------------------------------------- autotuner cache
+//
+// A text file of lines "<key>\t<persistent> <tile_w> <tile_h> <rays_per_thread>";
+// a later line for a key replaces an earlier one.
+
+sg_status sg_render_config_store(const char* path, const char* key, const sg_render_config* cfg) {
+  SG_CHECK_ARG(path && key && cfg, "path, key and cfg must not be NULL");
+  SG_CHECK_ARG(key[0] && !strpbrk(key, "\t\n") && strlen(key) < 1024, "key: 1..1023 characters, no tab or newline");
+  SG_CHECK_ARG(render_config_supported(cfg), "unsupported render configuration");
+  FILE* f = fopen(path, "a");
+  if (!f) {
+    set_error(std::string("sg_render_config_store: cannot open ") + path);
+    return SG_ERR_IO;
+  }
+  const int n = fprintf(f, "%s\t%d %d %d %d\n", key, cfg->persistent, cfg->tile_w, cfg->tile_h, cfg->rays_per_thread);
+  if (fclose(f) != 0 || n < 0) {
+    set_error(std::string("sg_render_config_store: write failed: ") + path);
+    return SG_ERR_IO;
+  }
+  return SG_OK;
+}
+
+sg_status sg_render_config_lookup(const char* path, const char* key, sg_render_config* cfg, int* found) {
+  SG_CHECK_ARG(path && key && cfg && found, "path, key, cfg and found must not be NULL");
+  *found = 0;
+  FILE* f = fopen(path, "r");
+  if (!f) return SG_OK;  // no cache yet
+  char line[1200];
+  while (fgets(line, sizeof line, f)) {
+    char* tab = strchr(line, '\t');
+    if (!tab) continue;
+    *tab = 0;
+    if (strcmp(line, key) != 0) continue;
+    sg_render_config c;
+    memset(&c, 0, sizeof c);
+    if (sscanf(tab + 1, "%d %d %d %d", &c.persistent, &c.tile_w, &c.tile_h, &c.rays_per_thread) == 4 &&
+        render_config_supported(&c)) {
+      *cfg = c;
+      *found = 1;
+    }
+  }
+  fclose(f);
+  return SG_OK;
+}
+
 sg_status sg_set_brick_ranges(sg_volume* v, int t, int c, int level, int n, const int32_t* xyz,
                               const uint32_t* minmax, void* stream) {
   SG_CHECK_ARG(v && xyz && minmax && n >= 1, "volume/brick_xyz/minmax NULL or n < 1");

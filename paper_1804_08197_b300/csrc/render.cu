@@ -44,15 +44,6 @@ constexpr int kWarpsPerSM = 32;
 #define SG_SAMPLES_PER_ITER 2
 #endif
 constexpr int kSamplesPerIter = SG_SAMPLES_PER_ITER;
-// Loop structure of the ray march: 0 = one event per lane per trip; 1 = an
-// in-block event, then up to kBlockStepsPerTrip block steps, per trip.
-#ifndef SG_LOOP_ORDER
-#define SG_LOOP_ORDER 0
-#endif
-#ifndef SG_BLOCK_STEPS_PER_TRIP
-#define SG_BLOCK_STEPS_PER_TRIP 1
-#endif
-constexpr int kBlockStepsPerTrip = SG_BLOCK_STEPS_PER_TRIP;
 __host__ __device__ constexpr int min_blocks(int threads, int rpt, int bk, bool ext = false) {
   return (rpt == 1 && bk != 0 && !ext) ? kWarpsPerSM * 32 / threads : 1;
 }
@@ -379,7 +370,6 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
   bool render = false;
   const int nsm = a.nsub - 1;
 
-#if SG_LOOP_ORDER == 0
   for (int guard = 0; guard < (1 << 25); ++guard) {
 #ifdef SG_RENDER_EVENT_STATS
     {
@@ -506,155 +496,6 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
     }
     if (stop) break;
   }
-#else
-  bool ended = false;
-  // Each trip: first the lane's event inside its current block (a jump
-  // over transparent sub-blocks, or samples), then, if the lattice point
-  // now lies beyond the block (or no block is entered yet), the step into
-  // the next block. A warp runs the union of the paths its lanes take in a
-  // trip, so letting one lane take an in-block event and a block step in
-  // the same trip consumes more events per trip at the same cost.
-  float t = lattice_t(k, t0, a);
-  for (int guard = 0; guard < (1 << 25); ++guard) {
-#ifdef SG_RENDER_EVENT_STATS
-    {
-      const unsigned am = __activemask();
-      if ((am & ((1u << (threadIdx.x & 31)) - 1u)) == 0u) ++ev[4];
-      ++ev[5];
-    }
-#endif
-    if (render && t < tend) {
-      // ---- lattice point k lies in a rendered block of level L
-      const float px0 = fmaf(t, d.x, o.x), py0 = fmaf(t, d.y, o.y), pz0 = fmaf(t, d.z, o.z);
-      // brick-local coordinate: level-L position - block origin + 1 (apron) - 0.5 (voxel centre)
-      const float lx = fmaf(px0 - lo.x, sL, 0.5f), ly = fmaf(py0 - lo.y, sL, 0.5f), lz = fmaf(pz0 - lo.z, sL, 0.5f);
-      int D = 0;
-      int sx = 0, sy = 0, sz = 0;
-      if (skip) {
-        sx = min(max(floor_i(lx - 0.5f) >> a.sub_shift, 0), nsm);
-        sy = min(max(floor_i(ly - 0.5f) >> a.sub_shift, 0), nsm);
-        sz = min(max(floor_i(lz - 0.5f) >> a.sub_shift, 0), nsm);
-        D = __ldg(subd + (sz * a.nsub + sy) * a.nsub + sx);
-      }
-      if (D > 0) {
-        // the box of D sub-blocks ahead of this one in the ray's octant is
-        // transparent: jump to its exit through a far face (clipped to the
-        // brick); the lattice points skipped have alpha exactly 0
-        const float S = u2f(a.sub << L);
-        const int ex_i = d.x > 0.0f ? min(sx + D, a.nsub) : max(sx - D + 1, 0);
-        const int ey_i = d.y > 0.0f ? min(sy + D, a.nsub) : max(sy - D + 1, 0);
-        const int ez_i = d.z > 0.0f ? min(sz + D, a.nsub) : max(sz - D + 1, 0);
-        const float ts = fminf(fminf(exit_through(o.x, d.x, inv.x, fmaf(u2f(ex_i), S, lo.x)),
-                                     exit_through(o.y, d.y, inv.y, fmaf(u2f(ey_i), S, lo.y))),
-                               fminf(exit_through(o.z, d.z, inv.z, fmaf(u2f(ez_i), S, lo.z)), tend));
-        // a rounded-up target may skip a point lying within rounding of the
-        // exit: it is inside the cube's footprint margin, alpha 0, exact
-        k = max(ceil_i((ts - t0) * a.inv_step), k + 1);
-        k = (k + kstep - 1) & ~(kstep - 1);
-        SG_EV(1, 1);
-      } else {
-        ++cnt;
-        SG_EV(0, 1);
-        bool stop = false;
-        if (MODE == SG_MODE_EMISSION_ABSORPTION) {
-#ifdef SG_RENDER_EVENT_STATS
-          const float w_before = acc.w;
-          stop = composite_sample<T, BK, EXT>(a, brick0, L, lx, ly, lz, sL, t, acc);
-          SG_EV(7, acc.w != w_before ? 1 : 0);
-#else
-          stop = composite_sample<T, BK, EXT>(a, brick0, L, lx, ly, lz, sL, t, acc);
-#endif
-        } else if (MODE == SG_MODE_EMISSION) {
-          emission_sample<T, BK, EXT>(a, brick0, L, lx, ly, lz, sL, t, acc);
-        } else {
-          mip_sample<T, BK, EXT>(a, brick0, lx, ly, lz, sL, t, vmax, tat);
-        }
-        if (stop) break;
-        k += kstep;
-        // the next lattice points of the same block, taken without a
-        // sub-block lookup: a sample in a transparent sub-block adds exactly
-        // nothing (and cannot raise a MIP maximum that matters), so taking
-        // it is always exact
-#pragma unroll
-        for (int u = 1; u < kSamplesPerIter; ++u) {
-          const float t2 = lattice_t(k, t0, a);
-          if (!(t2 < tend)) break;
-          const float qx = fmaf(t2, d.x, o.x), qy = fmaf(t2, d.y, o.y), qz = fmaf(t2, d.z, o.z);
-          const float mx = fmaf(qx - lo.x, sL, 0.5f), my = fmaf(qy - lo.y, sL, 0.5f), mz = fmaf(qz - lo.z, sL, 0.5f);
-          ++cnt;
-          SG_EV(0, 1);
-          if (MODE == SG_MODE_EMISSION_ABSORPTION)
-            stop = composite_sample<T, BK, EXT>(a, brick0, L, mx, my, mz, sL, t2, acc);
-          else if (MODE == SG_MODE_EMISSION)
-            emission_sample<T, BK, EXT>(a, brick0, L, mx, my, mz, sL, t2, acc);
-          else
-            mip_sample<T, BK, EXT>(a, brick0, mx, my, mz, sL, t2, vmax, tat);
-          if (stop) break;
-          k += kstep;
-        }
-        if (stop) break;
-      }
-      t = lattice_t(k, t0, a);
-    }
-#pragma unroll 1
-    for (int b = 0; b < kBlockStepsPerTrip && !(render && t < tend); ++b) {
-      // ---- leave the current block and enter the next one
-      if (ax >= 0) {
-        if (texit >= t1) {
-          ended = true;
-          break;
-        }
-        const int nl_x = (cx >> L) << L, nl_y = (cy >> L) << L, nl_z = (cz >> L) << L;
-        const int nh_x = min(nl_x + (1 << L), a.nb0[0]), nh_y = min(nl_y + (1 << L), a.nb0[1]),
-                  nh_z = min(nl_z + (1 << L), a.nb0[2]);
-        // the neighbour across the exit face along axis ax; on the other two
-        // axes the cell of the exit point, clamped to the block just left
-        // (all three formed, the exit axis then replaced: no 3-way branch)
-        const int c_ax = ax == 0 ? (d.x > 0.0f ? nh_x : nl_x - 1)
-                                 : (ax == 1 ? (d.y > 0.0f ? nh_y : nl_y - 1) : (d.z > 0.0f ? nh_z : nl_z - 1));
-        const int n_ax = ax == 0 ? a.nb0[0] : (ax == 1 ? a.nb0[1] : a.nb0[2]);
-        if (c_ax < 0 || c_ax >= n_ax) {
-          ended = true;
-          break;
-        }
-        const int ncx = cell_of(fmaf(texit, d.x, o.x), invB, nl_x, nh_x - 1);
-        const int ncy = cell_of(fmaf(texit, d.y, o.y), invB, nl_y, nh_y - 1);
-        const int ncz = cell_of(fmaf(texit, d.z, o.z), invB, nl_z, nh_z - 1);
-        cx = ax == 0 ? c_ax : ncx;
-        cy = ax == 1 ? c_ax : ncy;
-        cz = ax == 2 ? c_ax : ncz;
-        // lattice points before the exit belong to the block just left
-        k = first_k_at(tend, t0, a, kb);
-      }
-      const uint32_t e = __ldg(J.leaf + ((size_t)cz * a.nb0[1] + cy) * a.nb0[0] + cx);
-      L = e & 15;
-      const int nl_x = (cx >> L) << L, nl_y = (cy >> L) << L, nl_z = (cz >> L) << L;
-      lo = make_float3(u2f(nl_x) * Bf, u2f(nl_y) * Bf, u2f(nl_z) * Bf);
-      const float span = u2f(B << L);
-      const float ex = exit_through(o.x, d.x, inv.x, d.x > 0.0f ? fminf(lo.x + span, a.dims0[0]) : lo.x);
-      const float ey = exit_through(o.y, d.y, inv.y, d.y > 0.0f ? fminf(lo.y + span, a.dims0[1]) : lo.y);
-      const float ez = exit_through(o.z, d.z, inv.z, d.z > 0.0f ? fminf(lo.z + span, a.dims0[2]) : lo.z);
-      ax = 0;
-      texit = ex;
-      if (ey < texit) { texit = ey; ax = 1; }
-      if (ez < texit) { texit = ez; ax = 2; }
-      tend = fminf(texit, t1);
-      kb = k;
-      render = !(e & kLeafNone) && !(skip && (e & 16u));
-      SG_EV(render ? 2 : 3, 1);
-      if (render) {
-        kstep = 1 << L;
-        k = (k + kstep - 1) & ~(kstep - 1);
-        slot = (e & ~kLeafNone) >> 5;
-        brick0 = reinterpret_cast<const T*>(a.pool + (size_t)slot * a.nch * a.brick_bytes);
-        subd = a.subdist + ((size_t)slot * 8 + oct) * nsub3;
-        sL = __int_as_float((127 - L) << 23);
-      }
-      t = lattice_t(k, t0, a);
-    }
-    if (ended) break;
-  }
-#endif
   if (MODE == SG_MODE_MIP && cnt > 0) {
     // classify each channel's maximum (the MIP tables hold the transfer
     // functions as given, the same for every level), blend the channels

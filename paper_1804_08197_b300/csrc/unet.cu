@@ -236,6 +236,12 @@ struct sg_unet {
   uint16_t* wg_xT3 = nullptr;
   size_t wg_dzT_bytes = 0, wg_xT3_bytes = 0;
   float* d_loss = nullptr;    // [2]
+  // sg_render_learned: the reduced render of both eyes and (judging) the
+  // full-rate render, grown on demand; squared-error sums of the judge
+  float* lrn_half = nullptr;
+  float* lrn_full = nullptr;
+  size_t lrn_half_bytes = 0, lrn_full_bytes = 0;
+  float* lrn_acc = nullptr;   // [2]
   Crops in_crops;
   std::vector<void*> allocs;
 };
@@ -252,6 +258,9 @@ void free_unet(sg_unet* u) {
   for (void* p : u->allocs) cudaFree(p);
   cudaFree(u->wg_dzT);
   cudaFree(u->wg_xT3);
+  cudaFree(u->lrn_half);
+  cudaFree(u->lrn_full);
+  cudaFree(u->lrn_acc);
   delete u;
 }
 
@@ -1198,6 +1207,192 @@ sg_status sg_psnr(const float* a, const float* b, int64_t count, float* out_db, 
       acc[0] = mse > 0.f ? 10.0f * log10f(1.0f / mse) : 1000.0f;
     });
   return e == cudaSuccess ? SG_OK : cuda_fail(e, "sg_psnr");
+}
+
+// ---------------------------------------------------------------- checkpoints
+
+namespace {
+constexpr uint32_t kCkptMagic = 0x4e554753u;  // "SGUN"
+constexpr uint32_t kCkptVersion = 1;
+struct CkptHeader {
+  uint32_t magic, version;
+  int64_t nparam, step;
+};
+}  // namespace
+
+sg_status sg_unet_save(sg_unet* u, const char* path) {
+  if (!u || !path) {
+    set_error("sg_unet_save: NULL argument");
+    return SG_ERR_INVALID_ARG;
+  }
+  std::vector<float> host((size_t)u->nparam * 3);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(host.data(), u->d_param, u->nparam * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(host.data() + u->nparam, u->d_m, u->nparam * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(host.data() + 2 * u->nparam, u->d_v, u->nparam * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "sg_unet_save");
+  FILE* f = fopen(path, "wb");
+  if (!f) {
+    set_error(std::string("sg_unet_save: cannot open ") + path);
+    return SG_ERR_IO;
+  }
+  const CkptHeader h{kCkptMagic, kCkptVersion, u->nparam, u->step};
+  const bool ok = fwrite(&h, sizeof h, 1, f) == 1 && fwrite(host.data(), sizeof(float), host.size(), f) == host.size();
+  if (fclose(f) != 0 || !ok) {
+    set_error(std::string("sg_unet_save: write failed: ") + path);
+    return SG_ERR_IO;
+  }
+  return SG_OK;
+}
+
+sg_status sg_unet_load(sg_unet* u, const char* path) {
+  if (!u || !path) {
+    set_error("sg_unet_load: NULL argument");
+    return SG_ERR_INVALID_ARG;
+  }
+  FILE* f = fopen(path, "rb");
+  if (!f) {
+    set_error(std::string("sg_unet_load: cannot open ") + path);
+    return SG_ERR_IO;
+  }
+  CkptHeader h;
+  std::vector<float> host((size_t)u->nparam * 3);
+  const bool ok = fread(&h, sizeof h, 1, f) == 1 && h.magic == kCkptMagic && h.version == kCkptVersion &&
+                  h.nparam == u->nparam && h.step >= 0 &&
+                  fread(host.data(), sizeof(float), host.size(), f) == host.size();
+  fclose(f);
+  if (!ok) {
+    set_error(std::string("sg_unet_load: not a checkpoint of this network (or truncated): ") + path);
+    return SG_ERR_IO;
+  }
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(u->d_param, host.data(), u->nparam * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(u->d_m, host.data() + u->nparam, u->nparam * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(u->d_v, host.data() + 2 * u->nparam, u->nparam * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = refresh_bf16(u, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "sg_unet_load");
+  u->step = h.step;
+  return SG_OK;
+}
+
+// ---------------------------------------------------------------- a learned frame
+
+sg_status sg_render_learned(sg_volume* vol, sg_unet* u, const sg_pose* pose, const sg_learned_params* prm,
+                            float* out_rgba[2], float* psnr_db, int32_t* fell_back, void* stream) {
+  if (!vol || !u || !pose || !prm || !out_rgba || !out_rgba[0] || !out_rgba[1]) {
+    set_error("sg_render_learned: NULL argument");
+    return SG_ERR_INVALID_ARG;
+  }
+  const int W = pose->width, H = pose->height, w = W / 2, h = H / 2;
+  if (W % 8 || H % 8 || W < 8 || H < 8 || (int64_t)h * w > (int64_t)u->max_h * u->max_w || u->max_n < 2) {
+    set_error("sg_render_learned: width and height must be multiples of 8, the half-resolution image within the "
+              "network's max_h x max_w pixels, and the network must take batches of 2");
+    return SG_ERR_INVALID_ARG;
+  }
+  if (prm->judge && (!psnr_db || !fell_back)) {
+    set_error("sg_render_learned: judging needs psnr_db and fell_back");
+    return SG_ERR_INVALID_ARG;
+  }
+  if (prm->half_slot < 0 || prm->half_slot >= 256 || prm->half_slot == pose->slot || !(prm->step > 0.0f)) {
+    set_error("sg_render_learned: half_slot in [0, 255] other than pose->slot, and step > 0");
+    return SG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  auto grow = [](float** p, size_t* have, size_t bytes) {
+    if (*have >= bytes) return cudaSuccess;
+    cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) *have = bytes;
+    return e;
+  };
+  const size_t half_px = (size_t)w * h, full_px = (size_t)W * H;
+  cudaError_t e = grow(&u->lrn_half, &u->lrn_half_bytes, 2 * half_px * 4 * sizeof(float));
+  if (e == cudaSuccess && prm->judge) e = grow(&u->lrn_full, &u->lrn_full_bytes, 2 * full_px * 4 * sizeof(float));
+  if (e == cudaSuccess && !u->lrn_acc) e = cudaMalloc(&u->lrn_acc, 2 * sizeof(float));
+  if (e != cudaSuccess) {
+    set_error(std::string("sg_render_learned: buffers: ") + cudaGetErrorString(e));
+    return SG_ERR_OOM;
+  }
+  // the reduced render: half resolution, twice the step, at the level of
+  // detail of the full-resolution image (its pixels are twice as large)
+  sg_pose hp = *pose;
+  hp.width = w;
+  hp.height = h;
+  hp.pixel_error = prm->pixel_error_half > 0.0f ? prm->pixel_error_half : 0.5f * pose->pixel_error;
+  hp.slot = prm->half_slot;
+  sg_render_config keep;
+  sg_status st = sg_get_render_config(vol, &keep);
+  if (st != SG_OK) return st;
+  auto render = [&](const sg_pose* p, float step, const sg_render_config& cfg, float* outs[2]) -> sg_status {
+    sg_status r = sg_select_lod_batch(vol, p, 1, stream);
+    if (r != SG_OK) return r;
+    if (cfg.tile_w || cfg.persistent) {
+      r = sg_set_render_config(vol, &cfg);
+      if (r != SG_OK) return r;
+    }
+    sg_render_params rp;
+    memset(&rp, 0, sizeof rp);
+    rp.step = step;
+    rp.term_alpha = prm->term_alpha > 0.0f ? prm->term_alpha : 0.99f;
+    rp.empty_skip = 1;
+    rp.mode = SG_MODE_EMISSION_ABSORPTION;
+    r = sg_render(vol, p, &rp, outs, stream);
+    sg_set_render_config(vol, &keep);
+    return r;
+  };
+  float* half[2] = {u->lrn_half, u->lrn_half + half_px * 4};
+  if ((st = render(&hp, 2.0f * prm->step, prm->half_config, half)) != SG_OK) return st;
+  const float* hin[2] = {half[0], half[1]};
+  if ((st = sg_unet_forward(u, hin, (int64_t)w * 4, 2, h, w, out_rgba, (int64_t)W * 4, stream)) != SG_OK) return st;
+  if (!prm->judge) return SG_OK;
+  // the yardstick: the plain full-rate render, the stereo PSNR
+  // 10 log10(1 / mean of the eyes' MSE) on the device, and the fallback
+  float* full[2] = {u->lrn_full, u->lrn_full + full_px * 4};
+  if ((st = render(pose, prm->step, prm->full_config, full)) != SG_OK) return st;
+  float* acc = u->lrn_acc;
+  const int64_t cnt = (int64_t)full_px * 4;
+  const float* o0 = out_rgba[0];
+  const float* o1 = out_rgba[1];
+  const float* f0 = full[0];
+  const float* f1 = full[1];
+  e = cudaMemsetAsync(acc, 0, 2 * sizeof(float), s);
+  if (e == cudaSuccess)
+    e = sum(cnt, acc, s, [=] __device__(int64_t i) {
+      const float d = o0[i] - f0[i];
+      return d * d;
+    });
+  if (e == cudaSuccess)
+    e = sum(cnt, acc + 1, s, [=] __device__(int64_t i) {
+      const float d = o1[i] - f1[i];
+      return d * d;
+    });
+  const float thr = prm->threshold_db;
+  if (e == cudaSuccess)
+    e = each(1, s, [=] __device__(int64_t) {
+      const float m0 = acc[0] / (float)cnt, m1 = acc[1] / (float)cnt, m = 0.5f * (m0 + m1);
+      psnr_db[0] = m0 > 0.f ? 10.0f * log10f(1.0f / m0) : 1000.0f;
+      psnr_db[1] = m1 > 0.f ? 10.0f * log10f(1.0f / m1) : 1000.0f;
+      psnr_db[2] = m > 0.f ? 10.0f * log10f(1.0f / m) : 1000.0f;
+      *fell_back = psnr_db[2] < thr ? 1 : 0;
+    });
+  // a frame below the threshold shows the full-rate render
+  float* d0 = out_rgba[0];
+  float* d1 = out_rgba[1];
+  const int32_t* fb = fell_back;
+  if (e == cudaSuccess)
+    e = each(cnt / 4, s, [=] __device__(int64_t i) {
+      if (!*fb) return;
+      reinterpret_cast<float4*>(d0)[i] = reinterpret_cast<const float4*>(f0)[i];
+      reinterpret_cast<float4*>(d1)[i] = reinterpret_cast<const float4*>(f1)[i];
+    });
+  return e == cudaSuccess ? SG_OK : cuda_fail(e, "sg_render_learned");
 }
 
 }  // extern "C"

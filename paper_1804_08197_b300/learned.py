@@ -8,7 +8,9 @@ step s) and the reduced render of the same pose at half resolution and twice
 the step (W/2 x H/2, step 2s, at the level of detail of the full-resolution
 image); the network maps the reduced render to the full-rate one. The full-rate render
 is also the fallback and the yardstick: a frame whose PSNR against it falls below
-the threshold is replaced by it.
+the threshold is replaced by it. A learned frame (reduced render, network,
+and when judged the full-rate render, the stereo PSNR and the fallback) is
+one sg_render_learned call, all on the device.
 """
 import numpy as np
 
@@ -39,6 +41,10 @@ class Learned:
         self.crop_out = torch.empty((max_batch, 2 * crop, 2 * crop, 4), dtype=f32, device=dev)
         self.loss = torch.zeros(1, dtype=f32, device=dev)
         self.psnr_buf = torch.zeros(2, dtype=f32, device=dev)
+        # per judged frame: PSNR of eye 0, eye 1, the stereo pair; fallback flag
+        self.max_frames = 256
+        self.psnr_frames = torch.zeros((self.max_frames, 3), dtype=f32, device=dev)
+        self.fell_back = torch.zeros(self.max_frames, dtype=torch.int32, device=dev)
         self.rng = np.random.default_rng(seed)
         # launch shapes (sg_render_config dicts) for full- and half-rate renders;
         # None keeps the volume's own
@@ -154,18 +160,24 @@ class Learned:
         sg.sg_psnr(a, b, a.numel(), self.psnr_buf[out_index:out_index + 1], stream=stream)
         return self.psnr_buf[out_index:out_index + 1]
 
-    def frame_psnr(self, stream=None):
-        """PSNR (dB) of the current reconstruction against the current full-rate
-        render over both eyes: 10 log10(1 / mean of the two eyes' MSE)."""
-        for e in range(2):
-            self.psnr(self.recon[e], self.full[e], out_index=e, stream=stream)
-        db = self.psnr_buf.cpu().numpy().astype(np.float64)
-        mse = np.mean([10.0 ** (-d / 10.0) for d in db])
-        return 10.0 * np.log10(1.0 / mse) if mse > 0 else 1000.0
+    def learned_params(self, judge=False, threshold_db=40.0):
+        return sg.learned_params(step=self.step, pixel_error_half=self.tau_half, threshold_db=threshold_db,
+                                 judge=judge, half_slot=self.slot_half, half_config=self.cfg_half,
+                                 full_config=self.cfg_full)
 
-    def evaluate(self, views, projs, stream=None):
-        """Renders one pose both ways, reconstructs, returns the PSNR (dB)."""
-        self.render_full(views, projs, stream=stream)
-        self.render_half(views, projs, stream=stream)
-        self.reconstruct(stream=stream)
-        return self.frame_psnr(stream=stream)
+    def frame(self, views, projs, judge=False, threshold_db=40.0, index=0, stream=None):
+        """One learned stereo frame (sg_render_learned) into self.recon. Judged,
+        it also renders the full-rate frame into the network's buffer and
+        writes the PSNRs of the pair to psnr_frames[index] and the fallback
+        flag to fell_back[index] (device; nothing waits)."""
+        pose = self.pose_full(views, projs)
+        prm = self.learned_params(judge, threshold_db)
+        sg.sg_render_learned(self.vol, self.net, pose, prm, self.recon,
+                             self.psnr_frames[index] if judge else None, self.fell_back[index:index + 1] if judge else None,
+                             stream=stream)
+
+    def evaluate(self, views, projs, index=0, stream=None):
+        """Judges one pose's learned frame; returns its stereo PSNR (dB), reading
+        the device value (the one host wait of this call)."""
+        self.frame(views, projs, judge=True, index=index, stream=stream)
+        return float(self.psnr_frames[index, 2].item())

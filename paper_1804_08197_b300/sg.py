@@ -23,9 +23,9 @@ STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_OOM", 3: "SG_ERR
 EXPORTS = ["sg_volume_create", "sg_volume_destroy", "sg_upload_volume_device", "sg_upload_bricks",
            "sg_set_transfer_function", "sg_select_lod", "sg_select_lod_batch", "sg_read_selection", "sg_read_brick",
            "sg_render", "sg_render_host", "sg_render_host_async", "sg_render_host_wait", "sg_render_batch", "sg_set_render_config", "sg_get_render_config",
-           "sg_autotune_render", "sg_select_lod_noalloc", "sg_read_residency", "sg_set_brick_ranges", "sg_unet_create", "sg_unet_destroy",
+           "sg_autotune_render", "sg_render_config_store", "sg_render_config_lookup", "sg_select_lod_noalloc", "sg_read_residency", "sg_set_brick_ranges", "sg_unet_create", "sg_unet_destroy",
            "sg_unet_param_count", "sg_unet_get_params", "sg_unet_set_params", "sg_unet_forward", "sg_unet_backward",
-           "sg_unet_adam_step", "sg_unet_set_tensor_path", "sg_unet_check", "sg_unet_wait_selftest", "sg_psnr", "sg_read_ranges", "sg_upload_brick_list", "sg_unwarp", "sg_set_channel_shading",
+           "sg_unet_adam_step", "sg_unet_set_tensor_path", "sg_unet_check", "sg_unet_wait_selftest", "sg_unet_save", "sg_unet_load", "sg_render_learned", "sg_psnr", "sg_read_ranges", "sg_upload_brick_list", "sg_unwarp", "sg_set_channel_shading",
            "sg_container_create", "sg_container_open", "sg_container_append", "sg_container_finish",
            "sg_container_get_info", "sg_container_read", "sg_container_close", "sg_host_cache_create",
            "sg_host_cache_destroy", "sg_host_cache_fetch", "sg_host_cache_clear_failures", "sg_stream_requests",
@@ -99,6 +99,13 @@ class sg_render_config(ctypes.Structure):
                     rays_per_thread=self.rays_per_thread)
 
 
+class sg_learned_params(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_float), ("term_alpha", ctypes.c_float), ("pixel_error_half", ctypes.c_float),
+                ("threshold_db", ctypes.c_float), ("judge", ctypes.c_int32), ("half_slot", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2), ("half_config", sg_render_config),
+                ("full_config", sg_render_config)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libsg.so not built at {LIB_PATH}: run python -m paper_1804_08197_b300.build")
@@ -145,6 +152,9 @@ def _load():
         "sg_unet_set_tensor_path": [vp, i32],
         "sg_unet_check": [vp],
         "sg_unet_wait_selftest": [vp, ctypes.c_uint32, vp],
+        "sg_unet_save": [vp, ctypes.c_char_p],
+        "sg_unet_load": [vp, ctypes.c_char_p],
+        "sg_render_learned": [vp, vp, P(sg_pose), P(sg_learned_params), P(vp), vp, vp, vp],
         "sg_render": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
         "sg_render_host": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
         "sg_render_host_async": [vp, P(sg_pose), P(sg_render_params), P(vp), vp],
@@ -153,6 +163,8 @@ def _load():
         "sg_select_lod_noalloc": [vp, P(sg_pose), vp, vp, vp, vp, vp, vp],
         "sg_set_render_config": [vp, P(sg_render_config)],
         "sg_get_render_config": [vp, P(sg_render_config)],
+        "sg_render_config_store": [ctypes.c_char_p, ctypes.c_char_p, P(sg_render_config)],
+        "sg_render_config_lookup": [ctypes.c_char_p, ctypes.c_char_p, P(sg_render_config), P(ctypes.c_int)],
         "sg_autotune_render": [vp, P(sg_pose), i32, P(sg_render_params), P(vp), i32, P(sg_render_config),
                                P(ctypes.c_float), vp],
     }
@@ -540,6 +552,34 @@ def sg_unet_check(net):
     _check(lib.sg_unet_check(net))
 
 
+def sg_unet_save(net, path):
+    _check(lib.sg_unet_save(net, os.fsencode(str(path))))
+
+
+def sg_unet_load(net, path):
+    _check(lib.sg_unet_load(net, os.fsencode(str(path))))
+
+
+def learned_params(step=0.5, term_alpha=0.99, pixel_error_half=0.0, threshold_db=40.0, judge=False, half_slot=201,
+                   half_config=None, full_config=None):
+    p = sg_learned_params()
+    p.step, p.term_alpha, p.pixel_error_half, p.threshold_db = step, term_alpha, pixel_error_half, threshold_db
+    p.judge, p.half_slot = int(bool(judge)), half_slot
+    for name, cfg in (("half_config", half_config), ("full_config", full_config)):
+        if cfg:
+            c = getattr(p, name)
+            c.persistent, c.tile_w, c.tile_h, c.rays_per_thread = (cfg["persistent"], cfg["tile_w"], cfg["tile_h"],
+                                                                   cfg["rays_per_thread"])
+    return p
+
+
+def sg_render_learned(vol, net, pose, params, outs, psnr_db=None, fell_back=None, stream=None):
+    """A learned stereo frame into outs (two device buffers); psnr_db (3
+    floats) and fell_back (one int32) are device buffers, needed when judging."""
+    _check(lib.sg_render_learned(vol, net, ctypes.byref(pose), ctypes.byref(params), _ptr_array(outs), _ptr(psnr_db),
+                                 _ptr(fell_back), _stream(stream)))
+
+
 def sg_unet_wait_selftest(net, polls, stream=None):
     """Failure-detection self-test: a bounded wait that nothing satisfies
     gives up after `polls` polls and raises the network's error word."""
@@ -560,3 +600,19 @@ def sg_read_requests(vol, slot, cap=1 << 16, stream=None):
     nreq = ctypes.c_int32(0)
     _check(lib.sg_read_selection(vol, slot, None, 0, None, 0, _ptr(req), cap, ctypes.byref(nreq), _stream(stream)))
     return req[: min(nreq.value, cap)].copy()
+
+
+def sg_render_config_store(path, key, cfg):
+    """Appends the autotuner's pick (a dict as sg_autotune_render returns) for key."""
+    c = sg_render_config()
+    c.persistent, c.tile_w, c.tile_h, c.rays_per_thread = (cfg["persistent"], cfg["tile_w"], cfg["tile_h"],
+                                                           cfg["rays_per_thread"])
+    _check(lib.sg_render_config_store(os.fsencode(str(path)), key.encode(), ctypes.byref(c)))
+
+
+def sg_render_config_lookup(path, key):
+    """The stored pick for key as a dict, or None."""
+    c = sg_render_config()
+    found = ctypes.c_int(0)
+    _check(lib.sg_render_config_lookup(os.fsencode(str(path)), key.encode(), ctypes.byref(c), ctypes.byref(found)))
+    return c.as_dict() if found.value else None

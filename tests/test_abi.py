@@ -63,3 +63,24 @@ def test_no_cpu_fallback_when_the_library_is_missing(tmp_path, monkeypatch):
     monkeypatch.setattr(os.path, "exists", lambda p: False if p.endswith("libsg.so") else os.path.isfile(p))
     with pytest.raises(ImportError):
         spec.loader.exec_module(mod)
+
+
+def test_autotuner_cache_round_trip(tmp_path):
+    """The autotuner's pick survives the process: store appends, lookup finds
+    the latest line for a key, other keys and a missing file give nothing,
+    unsupported shapes and bad keys are refused (host only, no GPU)."""
+    from paper_1804_08197_b300 import sg
+    path = tmp_path / "tuned.txt"
+    assert sg.sg_render_config_lookup(path, "B300 bench") is None
+    a = dict(persistent=1, tile_w=8, tile_h=8, rays_per_thread=1)
+    b = dict(persistent=0, tile_w=16, tile_h=16, rays_per_thread=2)
+    sg.sg_render_config_store(path, "B300 bench", a)
+    sg.sg_render_config_store(path, "B300 other", b)
+    assert sg.sg_render_config_lookup(path, "B300 bench") == a
+    sg.sg_render_config_store(path, "B300 bench", b)
+    assert sg.sg_render_config_lookup(path, "B300 bench") == b
+    assert sg.sg_render_config_lookup(path, "B200 bench") is None
+    with pytest.raises(sg.SGError):
+        sg.sg_render_config_store(path, "bad", dict(persistent=0, tile_w=7, tile_h=8, rays_per_thread=1))
+    with pytest.raises(sg.SGError):
+        sg.sg_render_config_store(path, "tab\there", a)

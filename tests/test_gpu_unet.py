@@ -280,3 +280,99 @@ def test_a_bounded_wait_that_runs_out_is_reported_and_the_context_survives():
         assert torch.isfinite(out[0]).all()
     finally:
         sg.sg_unet_destroy(net)
+
+
+def _learned_case(sg, torch, seed=41):
+    dims = (192, 192, 192)
+    a = synth.filaments_u16(dims, seed=seed, ntubes=30)
+    vol = sg.sg_volume_create(dims, sg.SG_U16, 32, 3, model=synth.volume_model(192, 0.5))
+    d = torch.from_numpy(a.view(np.int16)).cuda()
+    sg.sg_upload_volume_device(vol, 0, 0, d.data_ptr())
+    sg.sg_set_transfer_function(vol, 0, synth.tf_piecewise(2002, zero_alpha_points=2), 300.0, 60000.0)
+    torch.cuda.synchronize()
+    return vol
+
+
+def test_learned_frame_is_the_reduced_render_through_the_network_and_judges_on_the_device():
+    """sg_render_learned = select + render at half resolution and twice the
+    step, then the network: identical to those calls made one by one. Judged,
+    it writes the stereo PSNR 10 log10(1 / mean of the eyes' MSE) against the
+    full-rate render (checked here from the downloaded images) and falls back
+    to that render exactly when the PSNR is below the threshold."""
+    import torch
+    from paper_1804_08197_b300 import sg
+    from paper_1804_08197_b300.learned import Learned
+    vol = _learned_case(sg, torch)
+    try:
+        W, H = 256, 288
+        rec = Learned(vol, W, H, max_batch=8, crop=32, seed=5)
+        try:
+            train = synth.head_poses(8, seed=9100, width=W, height=H, dist=(0.35, 0.8))
+            for i in range(12):
+                rec.train_on_pair(*train[i % 8], steps=2, batch=8, lr=1e-3)
+            views, projs = synth.head_poses(1, seed=9200, width=W, height=H, dist=(0.35, 0.8))[0]
+            # one by one
+            rec.render_half(views, projs)
+            rec.reconstruct()
+            ref = [r.clone() for r in rec.recon]
+            rec.render_full(views, projs)
+            full = [f.clone() for f in rec.full]
+            # one call, not judged: the same images
+            for r in rec.recon:
+                r.fill_(-1.0)
+            rec.frame(views, projs)
+            torch.cuda.synchronize()
+            for e in range(2):
+                assert torch.equal(rec.recon[e], ref[e])
+            # judged: PSNR from the images, fallback both ways
+            mse = [float(((ref[e].double() - full[e].double()) ** 2).mean()) for e in range(2)]
+            want = 10 * np.log10(1.0 / np.mean(mse))
+            for thr, falls in ((want - 1.0, False), (want + 1.0, True)):
+                rec.frame(views, projs, judge=True, threshold_db=thr, index=3)
+                torch.cuda.synchronize()
+                got = rec.psnr_frames[3].cpu().numpy()
+                assert got[2] == pytest.approx(want, abs=2e-3)
+                assert got[0] == pytest.approx(10 * np.log10(1 / mse[0]), abs=2e-3)
+                assert bool(rec.fell_back[3].item()) == falls
+                for e in range(2):
+                    assert torch.equal(rec.recon[e], full[e] if falls else ref[e])
+        finally:
+            rec.close()
+    finally:
+        sg.sg_volume_destroy(vol)
+
+
+def test_checkpoint_resumes_training_exactly(tmp_path):
+    """sg_unet_save / sg_unet_load carry the parameters, both Adam moments and
+    the step: a network loaded from a checkpoint gives bit-identical outputs
+    and, after one more identical training step, bit-identical parameters."""
+    import torch
+    from paper_1804_08197_b300 import sg
+    a = sg.sg_unet_create(2, 16, 24, seed=3)
+    b = sg.sg_unet_create(2, 16, 24, seed=99)
+    try:
+        rng = np.random.default_rng(7)
+        x = rng.uniform(0, 1, (2, 16, 24, 4))
+        t = rng.uniform(0, 1, (2, 32, 48, 4))
+        for _ in range(3):
+            _run(a, x, t)
+            sg.sg_unet_adam_step(a, 1e-3)
+        path = tmp_path / "net.ckpt"
+        sg.sg_unet_save(a, path)
+        sg.sg_unet_load(b, path)
+        oa, la = _run(a, x, t)
+        ob, lb = _run(b, x, t)
+        assert np.array_equal(oa, ob) and lb == pytest.approx(la, rel=1e-6)  # the loss sums with atomics
+        sg.sg_unet_adam_step(a, 1e-3)
+        sg.sg_unet_adam_step(b, 1e-3)
+        torch.cuda.synchronize()
+        pa = sg.sg_unet_get_params(a, which=0)
+        pb = sg.sg_unet_get_params(b, which=0)
+        assert np.array_equal(pa, pb)
+        # a file of another shape or a truncated one is refused
+        open(tmp_path / "short.ckpt", "wb").write(open(path, "rb").read()[:1000])
+        with pytest.raises(sg.SGError):
+            sg.sg_unet_load(b, tmp_path / "short.ckpt")
+    finally:
+        sg.sg_unet_destroy(a)
+        sg.sg_unet_destroy(b)
