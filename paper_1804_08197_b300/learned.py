@@ -144,7 +144,9 @@ class Learned:
             p = self.pose_half(views, projs)
             sg.sg_select_lod(self.vol, p, stream=render_stream)
             if self.cfg_half is not None:
-                sg.sg_set_render_config(self.vol, **self.cfg_half)
+                # one CTA per tile: a persistent grid holds every SM until its
+                # queue drains and would not share them with the network
+                sg.sg_set_render_config(self.vol, **dict(self.cfg_half, persistent=0))
             sg.sg_render(self.vol, p, sg.render_params(step=2 * self.step), self.half_pair[k], stream=render_stream)
             rendered[k].record(render_stream)
             net_stream.wait_event(rendered[k])
