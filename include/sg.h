@@ -424,6 +424,11 @@ typedef struct {
                              surface. sg_render / sg_render_host only. */
   const sg_lens* lens;    /* optional: rays through the lens-warped image (the pose's width/height are the
                              warped image's); sg_render / sg_render_host only */
+  uint8_t* touched;       /* optional device buffer, one byte per cache slot: set to 1 for every brick a ray
+                             took a sample from (the slot of node n at time point t is t * nodes + n for a
+                             volume without a device_pool_bytes budget). A diagnostic of the bricks the frame
+                             reads: sg_render and sg_render_host, emission-absorption without gradient or palette tables, the
+                             default launch shape. */
 } sg_render_params;
 
 /* Ray casts both eyes of a selected pose ("DVR Techniques"). For pixel (i,j)

@@ -95,6 +95,7 @@ struct Args {
   float pal_near[kMaxCh], pal_inv[kMaxCh];
   const float4* palette;  // [nch][kMaxTF]
   unsigned long long* total_samples;
+  uint8_t* touched;    // diagnostic kernels only: per slot, a sample was taken from the brick
 };
 
 // Exact integer <-> float conversions on the FMA/ALU pipes (the conversion
@@ -293,7 +294,7 @@ __device__ inline int cell_of(float p, float invB, int lo, int hi) {
 // iteration (take a sample, jump over transparent sub-blocks, or move to
 // the next block), so the lanes of a warp stay in one loop instead of
 // diverging across nested ones.
-template <typename T, int BK, int MODE, bool EXT>
+template <typename T, int BK, int MODE, bool EXT, bool TOUCH = false>
 __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int px, int py, bool active, float4& acc,
                                           uint32_t& cnt) {
   acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -458,6 +459,7 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
     }
     ++cnt;
     SG_EV(0, 1);
+    if (TOUCH) a.touched[slot] = 1;
     bool stop = false;
     if (MODE == SG_MODE_EMISSION_ABSORPTION) {
 #ifdef SG_RENDER_EVENT_STATS
@@ -529,7 +531,7 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
 #endif
 }
 
-template <typename T, int MAXI, int BK, int MODE, bool EXT>
+template <typename T, int MAXI, int BK, int MODE, bool EXT, bool TOUCH = false>
 __global__ void __launch_bounds__(kThreads, min_blocks(kThreads, 1, BK, EXT)) k_render(Args a, Jobs<MAXI> jobs) {
   const int tile = blockIdx.x;
   int im = 0;
@@ -544,7 +546,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(kThreads, 1, BK, EXT)) k_
 
   float4 acc;
   uint32_t cnt;
-  trace_ray<T, BK, MODE, EXT>(a, J, px, py, active, acc, cnt);
+  trace_ray<T, BK, MODE, EXT, TOUCH>(a, J, px, py, active, acc, cnt);
   if (active) {
     const size_t pix = (size_t)py * J.W + px;
     J.out[pix] = acc;
@@ -703,6 +705,7 @@ Args make_args(const sg_volume* v, const sg_render_params* prm) {
   a.term = prm->term_alpha > 0.0f ? prm->term_alpha : 0.99f;
   a.empty_skip = prm->empty_skip;
   a.total_samples = prm->sample_total;
+  a.touched = prm->touched;
   // voxels per world unit: the model's scale is uniform, so the length of
   // its first column is the voxel size
   const float* m = v->desc.model;
@@ -794,16 +797,16 @@ cudaError_t dispatch_tiles(sg_volume* v, const Args& a, const sg_pose* poses, in
   return cudaErrorInvalidValue;
 }
 
-template <int MAXI, int BK, int MODE, bool EXT = false>
+template <int MAXI, int BK, int MODE, bool EXT = false, bool TOUCH = false>
 cudaError_t launch_impl(sg_volume* v, const sg_pose* poses, int n, const sg_render_params* prm, float* const* outs,
                         cudaStream_t s) {
   Args a = make_args(v, prm);
   Jobs<MAXI> jobs;
   if (!make_jobs<MAXI>(v, poses, n, prm, outs, kTileW, kTileH, &jobs)) return cudaErrorInvalidValue;
   if (v->esize == 1)
-    k_render<uint8_t, MAXI, BK, MODE, EXT><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
+    k_render<uint8_t, MAXI, BK, MODE, EXT, TOUCH><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
   else
-    k_render<uint16_t, MAXI, BK, MODE, EXT><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
+    k_render<uint16_t, MAXI, BK, MODE, EXT, TOUCH><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
   return cudaGetLastError();
 }
 
@@ -815,6 +818,12 @@ cudaError_t launch_b(sg_volume* v, const sg_pose* poses, int n, const sg_render_
   // gradient tables or depth palettes: the EXT kernels (one CTA per 16x8 tile)
   bool ext = false;
   for (int c = 0; c < v->nch; ++c) ext |= v->tf[c].gradient || v->tf[c].pal_m > 0;
+  if (prm->touched) {
+    // the diagnostic of the bricks a frame reads: the default kernel with a
+    // flag store per sample
+    if (ext || prm->mode != SG_MODE_EMISSION_ABSORPTION || n != 1) return cudaErrorInvalidValue;
+    return launch_impl<2, BK, SG_MODE_EMISSION_ABSORPTION, false, true>(v, poses, n, prm, outs, s);
+  }
   if (ext) {
     if (prm->mode == SG_MODE_EMISSION) return launch_impl<128, BK, SG_MODE_EMISSION, true>(v, poses, n, prm, outs, s);
     if (prm->mode == SG_MODE_MIP) return launch_impl<128, BK, SG_MODE_MIP, true>(v, poses, n, prm, outs, s);

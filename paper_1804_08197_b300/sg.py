@@ -87,7 +87,7 @@ class sg_render_params(ctypes.Structure):
     _fields_ = [("step", ctypes.c_float), ("term_alpha", ctypes.c_float), ("mode", ctypes.c_int32),
                 ("empty_skip", ctypes.c_int32), ("sample_count", ctypes.c_void_p * 2),
                 ("sample_total", ctypes.c_void_p), ("depth", ctypes.c_void_p * 2),
-                ("lens", ctypes.POINTER(sg_lens))]
+                ("lens", ctypes.POINTER(sg_lens)), ("touched", ctypes.c_void_p)]
 
 
 class sg_render_config(ctypes.Structure):
@@ -393,12 +393,16 @@ def sg_read_brick(vol, t, c, level, bx, by, bz, host_out, stream=None):
 
 
 def render_params(step=0.5, term_alpha=0.99, empty_skip=1, sample_count=None, sample_total=None,
-                  mode=SG_MODE_EMISSION_ABSORPTION, depth=None, lens=None):
+                  mode=SG_MODE_EMISSION_ABSORPTION, depth=None, lens=None, touched=None):
     """depth: optional pair of device float buffers (H, W) per eye, the world
     distance along each pixel's ray to an opaque surface (inf = none).
     lens: optional sg_lens (make_lens) for rays through the warped image; the
-    structure must stay alive while the parameters are used."""
+    structure must stay alive while the parameters are used. touched:
+    optional device uint8 buffer, one byte per cache slot, set for every
+    brick a sample was taken from (a diagnostic render)."""
     r = sg_render_params()
+    if touched is not None:
+        r.touched = _ptr(touched).value
     if lens is not None:
         r.lens = ctypes.pointer(lens)
     if sample_total is not None:

@@ -266,6 +266,38 @@ def test_specialised_brick_edges_match_oracle_in_every_launch_shape(brick, level
         case.close()
 
 
+def test_touched_bricks_are_leaves_of_the_selection():
+    """The diagnostic render (a flag per brick a sample came from) draws the
+    same image as the timed kernel, and every flagged brick is a leaf of the
+    selection ("Octree Representation": rays sample only the selected cut)."""
+    case = _filament_case()
+    try:
+        W, H = 360, 400
+        (views, projs), = synth.head_poses(1, seed=3105, extent_m=0.5, width=W, height=H)
+        pose, _, gsel, ref = case.select(views, projs, W, H, tau=0.25)
+        compare_selection(gsel, ref)
+        imgs, cnts = case.render(pose, empty_skip=1)
+        torch, sg = case.torch, case.sg
+        touched = torch.zeros(case.ovol.node_count, dtype=torch.uint8, device="cuda")
+        outs = [torch.empty((H, W, 4), dtype=torch.float32, device="cuda") for _ in range(2)]
+        sg.sg_render(case.vol, pose, sg.render_params(step=0.5, term_alpha=0.99, empty_skip=1, touched=touched), outs)
+        torch.cuda.synchronize()
+        for e in range(2):
+            assert np.array_equal(outs[e].cpu().numpy().reshape(-1, 4), imgs[e])
+        t = np.flatnonzero(touched.cpu().numpy())
+        leaves = set(np.unique(ref["leaf"][ref["leaf"] >= 0]).tolist())
+        assert len(t) > 0 and (cnts[0].sum() + cnts[1].sum()) > 0
+        assert set(t.tolist()) <= leaves
+        assert np.all(ref["state"][t] == oracle.ST_SELECTED)
+        # the flags are a diagnostic of the default kernel only
+        two = sg.render_params(step=0.5, term_alpha=0.99, empty_skip=1, touched=touched,
+                               mode=sg.SG_MODE_MIP)
+        with pytest.raises(sg.SGError):
+            sg.sg_render(case.vol, pose, two, outs)
+    finally:
+        case.close()
+
+
 @pytest.mark.parametrize("skip_block", [2, 4, 8, 16])
 def test_every_skip_block_size_leaves_the_image_unchanged(skip_block):
     """Empty-space skipping at any cell size is exact: the image equals the
