@@ -362,13 +362,25 @@ int sm_count() {
 template <int BN, int R, int CW>
 cudaError_t conv_ws(const ConvArgs& a, uint32_t* err, cudaStream_t s, const HeadOut* head_out = nullptr) {
   using S = WsShape<BN, R, CW>;
-  const int stages = std::min(kWsMaxStages, (220 * 1024 - 1024) / S::kStage);
-  const int smem = stages * S::kStage + 1024;  // + room to align the ring to 1024 bytes
-  static bool configured = false;              // per template instance, set once on first use
-  if (!configured) {
+  // pooling needs whole 2 x 2 windows in every row pair a warp takes
+  if (a.pool_out && (R % 4 || a.H % 2 || a.W % 2)) return cudaErrorInvalidValue;
+  if (a.Cout > kWsMaxCout) return cudaErrorInvalidValue;
+  // shared memory: the ring of stages, [the resident weights,] the eight
+  // epilogue warps' staging rows, and room to align the ring to 1024 bytes.
+  // With one output-channel block every tile multiplies the same weights:
+  // they stay resident when the ring still gets two input stages.
+  const int avail = 220 * 1024 - 1024 - 8 * S::kOut;
+  const int wbytes = (a.Cin / CW * 9 * S::kBlk + 1023) / 1024 * 1024;
+  const int wres = (a.Cout == BN && (avail - wbytes) / S::kA >= 2) ? 1 : 0;
+  const int stages = wres ? std::min(kWsMaxStages, (avail - wbytes) / S::kA) : std::min(kWsMaxStages, avail / S::kStage);
+  const int smem = (wres ? stages * S::kA + wbytes : stages * S::kStage) + 8 * S::kOut + 1024;
+  // (the kernel's static shared memory, the bias, barriers and flags, takes the last 2 KB)
+  if (stages < 1 || smem > 225 * 1024) return cudaErrorInvalidValue;
+  static int configured = 0;  // per template instance: the largest dynamic size allowed so far
+  if (smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(k_conv3x3_ws<BN, R, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    configured = true;
+    configured = smem;
   }
   const CUtensorMapSwizzle swz = CW == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
   CUtensorMap tin, twt;
@@ -383,7 +395,7 @@ cudaError_t conv_ws(const ConvArgs& a, uint32_t* err, cudaStream_t s, const Head
   HeadOut ho;
   memset(&ho, 0, sizeof ho);
   if (head_out) ho = *head_out;
-  k_conv3x3_ws<BN, R, CW><<<grid, kWsThreads, smem, s>>>(a, stages, err, tin, twt, ho);
+  k_conv3x3_ws<BN, R, CW><<<grid, kWsThreads, smem, s>>>(a, stages, wres, err, tin, twt, ho);
   return cudaGetLastError();
 }
 
@@ -427,6 +439,9 @@ cudaError_t conv_halo_cc(const ConvArgs& a, uint32_t* err, cudaStream_t s) {
 // warp-specialised halo reuse (TMA ring, two TMEM accumulators)
 cudaError_t conv(const ConvArgs& a, cudaStream_t s, uint32_t* tc_err = nullptr, int mode = 2,
                  const HeadOut* head_out = nullptr) {
+  // pooled and upsampled copies come from the persistent kernel's epilogue only
+  if ((a.pool_out || a.up_out) && !(tc_err && mode == 4 && a.Cin % 16 == 0 && a.Cout % 16 == 0 && !head_out))
+    return cudaErrorInvalidValue;
   if (head_out) {
     // the network's output from the head's epilogue: persistent path, 16 channels
     if (!tc_err || mode != 4 || a.Cout != 16 || a.Cin % 16 || a.out || a.out_f32) return cudaErrorInvalidValue;
@@ -775,24 +790,31 @@ cudaError_t forward(sg_unet* u, const Crops& c, int N, int h, int w, float* out,
   a = conv_args(u, C1A, u->in16, 16, 0, N, h, w); a.out = u->a1; a.out_stride = 32; a.out_off = 0;
   if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
   // e1 lives in cat1 at channel offset 64 (after the 64 upsampled channels)
+  // the persistent path writes the pooled and upsampled copies from the
+  // producing convolution's epilogue; the others run them as separate passes
+  const bool fused = u->tc == 4;
   a = conv_args(u, C1B, u->a1, 32, 0, N, h, w); a.out = u->cat1; a.out_stride = 96; a.out_off = 64;
+  if (fused) { a.pool_out = u->p1; a.pool_stride = 32; a.pool_off = 0; }  // pool e1 -> p1
   if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
-  if ((e = pool_fwd(u->cat1, 96, 64, u->p1, 32, 0, 32, N, h, w, s))) return e;  // pool e1 -> p1
+  if (!fused && (e = pool_fwd(u->cat1, 96, 64, u->p1, 32, 0, 32, N, h, w, s))) return e;
   a = conv_args(u, C2A, u->p1, 32, 0, N, h2, w2); a.out = u->a2; a.out_stride = 64; a.out_off = 0;
   if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
   a = conv_args(u, C2B, u->a2, 64, 0, N, h2, w2); a.out = u->cat2; a.out_stride = 192; a.out_off = 128;
+  if (fused) { a.pool_out = u->p2; a.pool_stride = 64; a.pool_off = 0; }  // pool e2 -> p2
   if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
-  if ((e = pool_fwd(u->cat2, 192, 128, u->p2, 64, 0, 64, N, h2, w2, s))) return e;  // pool e2 -> p2
+  if (!fused && (e = pool_fwd(u->cat2, 192, 128, u->p2, 64, 0, 64, N, h2, w2, s))) return e;
   a = conv_args(u, C3A, u->p2, 64, 0, N, h4, w4); a.out = u->a3; a.out_stride = 128; a.out_off = 0;
   if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
   a = conv_args(u, C3B, u->a3, 128, 0, N, h4, w4); a.out = u->b3; a.out_stride = 128; a.out_off = 0;
+  if (fused) { a.up_out = u->cat2; a.up_stride = 192; a.up_off = 0; }  // up b3 -> cat2[:, 0..128)
   if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
-  if ((e = up_fwd(u->b3, 128, u->cat2, 192, 0, 128, N, h4, w4, s))) return e;  // up b3 -> cat2[:, 0..128)
+  if (!fused && (e = up_fwd(u->b3, 128, u->cat2, 192, 0, 128, N, h4, w4, s))) return e;
   a = conv_args(u, D2A, u->cat2, 192, 0, N, h2, w2); a.out = u->a4; a.out_stride = 64; a.out_off = 0;
   if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
   a = conv_args(u, D2B, u->a4, 64, 0, N, h2, w2); a.out = u->d2; a.out_stride = 64; a.out_off = 0;
+  if (fused) { a.up_out = u->cat1; a.up_stride = 96; a.up_off = 0; }  // up d2 -> cat1[:, 0..64)
   if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
-  if ((e = up_fwd(u->d2, 64, u->cat1, 96, 0, 64, N, h2, w2, s))) return e;  // up d2 -> cat1[:, 0..64)
+  if (!fused && (e = up_fwd(u->d2, 64, u->cat1, 96, 0, 64, N, h2, w2, s))) return e;
   a = conv_args(u, D1A, u->cat1, 96, 0, N, h, w); a.out = u->a5; a.out_stride = 32; a.out_off = 0;
   if ((e = conv(a, s, u->tc ? u->d_err : nullptr, u->tc))) return e;
   a = conv_args(u, D1B, u->a5, 32, 0, N, h, w); a.out = u->d1; a.out_stride = 32; a.out_off = 0;

@@ -64,6 +64,13 @@ struct ConvArgs {
   int f32_accumulate;      // 1: out_f32 += result
   int N, H, W, Cin, Cout;
   int relu;
+  // persistent tcgen05 kernel only (the others reject them): the BF16 output
+  // also written 2x2-mean pooled (H/2 x W/2 grid) and nearest-2x upsampled
+  // (2H x 2W grid), each at its own pixel stride and channel offset
+  bf16* pool_out;
+  int pool_stride, pool_off;
+  bf16* up_out;
+  int up_stride, up_off;
 };
 
 constexpr int kConvBM = 128;
