@@ -189,7 +189,9 @@ sg_status sg_container_close(sg_container* k);
 
 /* A host cache of floor(bytes / brick bytes) decompressed bricks of
  * container k (which must outlive it); pinned != 0 page-locks it for full
- * upload bandwidth; threads decompress misses in parallel. Errors:
+ * upload bandwidth; threads decompress misses in parallel (and, once
+ * sg_stream_requests_async or sg_host_cache_prefetch is first called, as
+ * many background loader threads run until sg_host_cache_destroy). Errors:
  * INVALID_ARG, OOM. */
 sg_status sg_host_cache_create(sg_container* k, uint64_t bytes, int pinned, int threads, sg_host_cache** out);
 sg_status sg_host_cache_destroy(sg_host_cache* hc);
@@ -212,6 +214,8 @@ typedef struct {
   int32_t failed;        /* requests skipped: a chunk failed to read or decompress (now or earlier) */
   uint64_t disk_bytes;   /* compressed bytes read */
   uint64_t upload_bytes; /* bytes copied to the GPU cache */
+  int32_t queued;        /* sg_stream_requests_async: brick-channels handed to the loaders by this call */
+  int32_t in_flight;     /* sg_stream_requests_async: brick-channels being loaded after this call */
 } sg_stream_stats;
 
 /* Serves the requests of selection slot `slot` of vol from container-backed
@@ -229,6 +233,35 @@ typedef struct {
  * (layouts differ), STATE, IO (see above), OOM, CUDA. */
 sg_status sg_stream_requests(sg_volume* vol, int slot, sg_host_cache* hc, uint64_t max_bytes, sg_stream_stats* stats,
                              void* stream);
+
+/* The same requests served without waiting for the disk ("Volumetric Data
+ * Cashing" with "Octree Representation"'s coarser stand-ins): the bricks
+ * whose every channel the host cache holds are placed in the GPU cache (at
+ * most max_bytes, coarse levels first; complete on return); the others are
+ * handed to hc's background loader threads (at most max_bytes of new loads
+ * per call) and placed by a later call once loaded. Until then the next
+ * selections render their resident ancestors, so a frame never waits on a
+ * read. stats->disk_reads / disk_bytes count the loads finished since the
+ * previous call, stats->queued the loads this call started, stats->in_flight
+ * those still running. A chunk that fails to load is remembered and skipped
+ * as in sg_stream_requests (the call that learns of it returns SG_ERR_IO
+ * with *stats filled). A host cache may serve both calls; sg_stream_requests
+ * and sg_host_cache_fetch first wait for every load in flight. Errors: as
+ * sg_stream_requests. */
+sg_status sg_stream_requests_async(sg_volume* vol, int slot, sg_host_cache* hc, uint64_t max_bytes,
+                                   sg_stream_stats* stats, void* stream);
+
+/* Queues background loads of the bricks (t, c, nodes[0..n)) that hc does not
+ * hold (bricks without a chunk, or whose chunk failed before, are skipped);
+ * *queued (optional) receives how many were queued. Host only. Errors:
+ * INVALID_ARG, OOM (every entry is in use this call or being loaded: the
+ * bricks before are queued). */
+sg_status sg_host_cache_prefetch(sg_host_cache* hc, int t, int c, const int64_t* nodes, int32_t n, int32_t* queued);
+
+/* Waits for every background load of hc and takes the results in: loaded
+ * bricks become hits, failed chunks are remembered (*failed, optional,
+ * receives how many failed). Host only. Errors: INVALID_ARG. */
+sg_status sg_host_cache_wait(sg_host_cache* hc, int32_t* failed);
 
 /* Value ranges of bricks known without their data, as a container's index
  * table would hold them ("Volumetric Data Storage": chunks with an index):

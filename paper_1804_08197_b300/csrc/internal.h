@@ -182,4 +182,6 @@ int64_t container_nodes(const sg_container* k);
 sg_status host_cache_lookup(sg_host_cache* hc, int t, int c, int64_t node, int64_t* entry, int* hit,
                             std::vector<std::pair<int64_t, int64_t>>* todo);
 void host_cache_drop(sg_host_cache* hc, int64_t e);
+void host_cache_collect(sg_host_cache* hc, bool wait, int32_t* reads, uint64_t* bytes, int32_t* failed);
+void host_cache_drain(sg_host_cache* hc);
 }  // namespace sg

@@ -29,6 +29,7 @@ EXPORTS = ["sg_volume_create", "sg_volume_destroy", "sg_upload_volume_device", "
            "sg_container_create", "sg_container_open", "sg_container_append", "sg_container_finish",
            "sg_container_get_info", "sg_container_read", "sg_container_close", "sg_host_cache_create",
            "sg_host_cache_destroy", "sg_host_cache_fetch", "sg_host_cache_clear_failures", "sg_stream_requests",
+           "sg_stream_requests_async", "sg_host_cache_prefetch", "sg_host_cache_wait",
            "sg_last_error",
            "sg_version"]
 
@@ -67,7 +68,8 @@ class sg_container_info(ctypes.Structure):
 class sg_stream_stats(ctypes.Structure):
     _fields_ = [("requested", ctypes.c_int32), ("served", ctypes.c_int32), ("host_hits", ctypes.c_int32),
                 ("disk_reads", ctypes.c_int32), ("missing", ctypes.c_int32), ("failed", ctypes.c_int32),
-                ("disk_bytes", ctypes.c_uint64), ("upload_bytes", ctypes.c_uint64)]
+                ("disk_bytes", ctypes.c_uint64), ("upload_bytes", ctypes.c_uint64), ("queued", ctypes.c_int32),
+                ("in_flight", ctypes.c_int32)]
 
 
 class sg_lens(ctypes.Structure):
@@ -132,6 +134,9 @@ def _load():
         "sg_host_cache_fetch": [vp, i32, i32, i64, P(vp), P(ctypes.c_int)],
         "sg_host_cache_clear_failures": [vp],
         "sg_stream_requests": [vp, i32, vp, ctypes.c_uint64, P(sg_stream_stats), vp],
+        "sg_stream_requests_async": [vp, i32, vp, ctypes.c_uint64, P(sg_stream_stats), vp],
+        "sg_host_cache_prefetch": [vp, i32, i32, P(ctypes.c_int64), i32, P(i32)],
+        "sg_host_cache_wait": [vp, P(i32)],
         "sg_set_transfer_function": [vp, i32, vp, i32, f32, f32, f32, vp],
         "sg_select_lod": [vp, P(sg_pose), P(sg_select_stats), vp],
         "sg_select_lod_batch": [vp, P(sg_pose), i32, vp],
@@ -324,12 +329,14 @@ def sg_host_cache_fetch(hc, t, c, node):
     return p.value, bool(hit.value)
 
 
-def sg_stream_requests(vol, slot, hc, max_bytes, stream=None):
+def sg_stream_requests(vol, slot, hc, max_bytes, stream=None, asynchronous=False):
     """Serves a selection's requests; returns the stats as a dict. A call in
     which some chunks failed (SG_ERR_IO) still served the others: it returns
-    the stats (failed > 0) instead of raising."""
+    the stats (failed > 0) instead of raising. asynchronous=True: the
+    non-blocking form (sg_stream_requests_async)."""
     st = sg_stream_stats()
-    status = lib.sg_stream_requests(vol, slot, hc, int(max_bytes), ctypes.byref(st), _stream(stream))
+    fn = lib.sg_stream_requests_async if asynchronous else lib.sg_stream_requests
+    status = fn(vol, slot, hc, int(max_bytes), ctypes.byref(st), _stream(stream))
     if status != SG_ERR_IO:
         _check(status)
     out = {f[0]: getattr(st, f[0]) for f in sg_stream_stats._fields_}
@@ -340,6 +347,23 @@ def sg_stream_requests(vol, slot, hc, max_bytes, stream=None):
 
 def sg_host_cache_clear_failures(hc):
     _check(lib.sg_host_cache_clear_failures(hc))
+
+
+def sg_host_cache_prefetch(hc, t, c, nodes):
+    """Queues background loads of the listed bricks; returns how many were queued."""
+    import numpy as np
+    arr = np.ascontiguousarray(nodes, np.int64)
+    q = ctypes.c_int32(0)
+    _check(lib.sg_host_cache_prefetch(hc, t, c, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(arr),
+                                      ctypes.byref(q)))
+    return q.value
+
+
+def sg_host_cache_wait(hc):
+    """Waits for the background loads; returns how many failed."""
+    f = ctypes.c_int32(0)
+    _check(lib.sg_host_cache_wait(hc, ctypes.byref(f)))
+    return f.value
 
 
 def sg_set_channel_shading(vol, c, gradient=False, palette=None, near=0.0, far=1.0, stream=None):

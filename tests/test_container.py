@@ -235,3 +235,74 @@ def test_container_arguments_are_checked(tmp_path):
             sg.sg_container_read(k, 0, 0, 0, np.zeros(R3, np.uint8))
     finally:
         sg.sg_container_close(k)
+
+
+def _chunk_offsets(path, desc_size):
+    """file offset of each chunk's payload, by (level, bx, by, bz)."""
+    data = open(path, "rb").read()
+    off = 8 + desc_size
+    out = {}
+    while off + 48 <= len(data) and data[off:off + 4] == b"CHNK":
+        fields = struct.unpack_from("<4s6i5I", data, off)
+        out[tuple(fields[3:7])] = off + 48
+        off += 48 + fields[8]
+    return out
+
+
+def test_background_loads_land_in_the_host_cache(tmp_path):
+    """sg_host_cache_prefetch hands misses to loader threads; after
+    sg_host_cache_wait every good brick is a hit holding its data, and a
+    chunk made unreadable on disk is reported, remembered and skipped until
+    the failures are cleared ("Volumetric Data Cashing")."""
+    sg = _sg()
+    desc = _desc()
+    path = tmp_path / "v.sgc"
+    bricks = _bricks()
+    k = sg.sg_container_create(path, desc)
+    for (L, bx, by, bz), b in bricks.items():
+        sg.sg_container_append(k, 0, 0, L, bx, by, bz, b, 0, 255)
+    sg.sg_container_finish(k)
+    sg.sg_container_close(k)
+    bad = (0, 0, 1, 0)  # level 0, brick (0, 1, 0): node 2
+    off = _chunk_offsets(path, ctypes.sizeof(desc))[bad]
+    with open(path, "r+b") as f:
+        f.seek(off)
+        f.write(b"\xff" * 8)
+    k = sg.sg_container_open(path)
+    hc = sg.sg_host_cache_create(k, 5 * R3 + 10, pinned=False, threads=3)
+    try:
+        nodes = [_node(*kk) for kk in bricks]
+        assert sg.sg_host_cache_prefetch(hc, 0, 0, nodes) == len(nodes)
+        assert sg.sg_host_cache_wait(hc) == 1
+        for kk, b in bricks.items():
+            if kk == bad:
+                continue
+            ptr, hit = sg.sg_host_cache_fetch(hc, 0, 0, _node(*kk))
+            assert hit
+            got = np.ctypeslib.as_array((ctypes.c_uint8 * R3).from_address(ptr))
+            assert np.array_equal(got, b.reshape(-1))
+        # the bad chunk is skipped, read again once the failures are cleared
+        assert sg.sg_host_cache_prefetch(hc, 0, 0, [_node(*bad)]) == 0
+        sg.sg_host_cache_clear_failures(hc)
+        assert sg.sg_host_cache_prefetch(hc, 0, 0, [_node(*bad)]) == 1
+        assert sg.sg_host_cache_wait(hc) == 1
+        with pytest.raises(sg.SGError):
+            sg.sg_host_cache_fetch(hc, 0, 0, _node(*bad))
+        with pytest.raises(sg.SGError):
+            sg.sg_host_cache_prefetch(hc, 0, 0, [99])
+    finally:
+        sg.sg_host_cache_destroy(hc)
+    # a cache of two entries: the third load of one call finds none free
+    hc = sg.sg_host_cache_create(k, 2 * R3 + 10, pinned=False, threads=2)
+    try:
+        with pytest.raises(sg.SGError):
+            sg.sg_host_cache_prefetch(hc, 0, 0, [0, 1, 3])
+        assert sg.sg_host_cache_wait(hc) == 0
+        assert sg.sg_host_cache_fetch(hc, 0, 0, 1)[1]
+    finally:
+        sg.sg_host_cache_destroy(hc)
+    # destroyed with loads still queued: the loaders stop and are joined
+    hc = sg.sg_host_cache_create(k, 5 * R3 + 10, pinned=False, threads=1)
+    sg.sg_host_cache_prefetch(hc, 0, 0, [0, 1, 3, 4])
+    sg.sg_host_cache_destroy(hc)
+    sg.sg_container_close(k)

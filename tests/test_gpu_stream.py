@@ -419,3 +419,90 @@ def test_streaming_survives_unreadable_chunks(tmp_path):
         sg.sg_host_cache_destroy(hc)
         sg.sg_volume_destroy(vol)
         sg.sg_container_close(k)
+
+
+def test_async_streaming_never_waits_and_converges(tmp_path):
+    """sg_stream_requests_async: misses go to the host cache's loader
+    threads and the call returns at once (the first, cold call serves
+    nothing and queues the budget), later calls place what has arrived. The
+    residency then depends on timing, so each frame is checked against the
+    oracle's selection for the GPU's actual residency. One chunk made
+    unreadable on disk is reported by the call that learns of it and
+    skipped afterwards; the view converges with only that brick requested
+    (its parent renders in its place), and the image matches the oracle."""
+    import time
+    import torch
+    from paper_1804_08197_b300 import sg
+    a = synth.filaments_u16(DIMS, seed=33, ntubes=18)
+    model = synth.volume_model(128, 0.5)
+    ovol = oracle.Volume([oracle.pyramid(a, LEVELS)], B, model=model)
+    full = ovol.block_ranges()
+    table = synth.tf_piecewise(2002, zero_alpha_points=2)
+    otf = oracle.make_tf(table, 300.0, 60000.0)
+    path = tmp_path / "vol.sgc"
+    desc = sg.volume_desc(DIMS, sg.SG_U16, B, LEVELS, model=model)
+    k = sg.sg_container_create(path, desc)
+    for n in range(ovol.node_count):
+        L, b = ovol.node_coords(n)
+        sg.sg_container_append(k, 0, 0, L, *b, _brick(ovol, L, *b), *full[n, 0])
+    sg.sg_container_finish(k)
+    sg.sg_container_close(k)
+    W, H, tau = 192, 208, 0.3
+    views, projs = _stereo((-0.3, 0.05, 0.2), (-0.1, 0.0, 0.0), W, H)
+    st_full = ovol.select([otf], views, projs, H, tau=tau)["state"]
+    lvl0 = [n for n in np.flatnonzero(st_full == oracle.ST_SELECTED) if ovol.node_coords(int(n))[0] == 0]
+    bad = int(lvl0[len(lvl0) // 2])
+    _corrupt_chunk(path, bad)
+    k = sg.sg_container_open(path)
+    need = int(np.isin(st_full, [oracle.ST_SELECTED, oracle.ST_FALLBACK, oracle.ST_REFINED]).sum())
+    brick_bytes = ((B + 2) ** 3 * 2 + 255) // 256 * 256
+    vol = sg.sg_volume_create(DIMS, sg.SG_U16, B, LEVELS, device_pool_bytes=(need + 8) * brick_bytes, model=model)
+    hc = sg.sg_host_cache_create(k, (need + 8) * (B + 2) ** 3 * 2, pinned=True, threads=4)
+    budget = 24 * (B + 2) ** 3 * 2
+    try:
+        sg.sg_set_transfer_function(vol, 0, table, 300.0, 60000.0)
+        for L in range(LEVELS):
+            nbx, nby, nbz = ovol.blocks_per_axis(L)
+            xyz = np.array([(x, y, z) for z in range(nbz) for y in range(nby) for x in range(nbx)])
+            lo, hi = ovol.level_offsets[L], ovol.level_offsets[L + 1]
+            sg.sg_set_brick_ranges(vol, 0, 0, L, xyz, full[lo:hi, 0, :])
+        root = int(ovol.level_offsets[LEVELS - 1])
+        ptr, _ = sg.sg_host_cache_fetch(hc, 0, 0, root)
+        assert sg.sg_upload_brick_list(vol, 0, 0, [root], [ptr]) == 1
+        pose = sg.make_pose(views, projs, W, H, pixel_error=tau)
+        failed, served, reads = 0, 0, 0
+        for frame in range(2000):
+            stats = sg.sg_select_lod(vol, pose, stats=True)
+            res = sg.sg_read_residency(vol, 0, ovol.node_count) >= 0
+            ref = ovol.select([otf], views, projs, H, tau=tau, resident=res.astype(np.uint8), ranges=full)
+            compare_selection(sg.sg_read_selection(vol, 0, len(ref["leaf"]), ovol.node_count), ref)
+            reqs = set(int(n) for n in ref["requests"])
+            if reqs <= {bad} and failed:
+                break
+            st = sg.sg_stream_requests(vol, 0, hc, budget, asynchronous=True)
+            assert st["missing"] == 0 and st["served"] <= 24 and st["requested"] == stats["requested"]
+            if frame == 0:
+                # a cold host cache: nothing to place yet, a full budget of loads queued
+                assert st["served"] == 0 and st["queued"] == min(24, len(reqs)) and st["in_flight"] > 0
+            failed += st["failed"]
+            served += st["served"]
+            reads += st["disk_reads"]
+            if st["served"] == 0:
+                time.sleep(0.002)  # nothing arrived yet: let the loaders work
+        else:
+            raise AssertionError("asynchronous streaming did not converge")
+        assert failed >= 1 and served > 0 and reads >= served
+        assert not res[bad] and stats["fallback"] > 0
+        outs = [torch.empty((H, W, 4), device="cuda") for _ in range(2)]
+        sg.sg_render(vol, pose, sg.render_params(), outs)
+        torch.cuda.synchronize()
+        for e in range(2):
+            compare_image(outs[e].cpu().numpy().reshape(-1, 4),
+                          ovol.render([otf], ref["leaf"], views[e], projs[e], W, H))
+        # the blocking call on the same cache waits for nothing and places nothing new
+        st = sg.sg_stream_requests(vol, 0, hc, budget)
+        assert st["served"] == 0 and st["failed"] == 1
+    finally:
+        sg.sg_host_cache_destroy(hc)
+        sg.sg_volume_destroy(vol)
+        sg.sg_container_close(k)
