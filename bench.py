@@ -166,16 +166,17 @@ def profiled_traffic(alg_bytes):
         return None
 
 
-def cpu_baseline(vol, tf_table, poses, model, npose=16, stride=32, npose_1core=4, stride_1core=512):
+def cpu_baseline(vol, tf_table, poses, model, pose_ids, stride=32, npose_1core=4, stride_1core=512):
     """The FP64 oracle, as it stands, on bounded pixel samples of the bench poses.
 
     Block value ranges are an ingest quantity: computed once, untimed. A
     frame is one selection plus every pixel of both eyes; the sample times
     each pose's selection and every `stride`-th pixel, extrapolates only the
-    per-pixel work, and reports frames / total time over `npose` poses (the
-    cost varies a lot from pose to pose; the reference arm averages over its
-    steps' poses the same way). Also timed: the same on one core and the
-    full 256 x 256 view of the plain 128^3 u8 ray-cast workload."""
+    per-pixel work, and reports frames / total time over the poses pose_ids:
+    the GPU arm's timed poses, which the reference arm run with the same
+    --steps / --warmup steps through too (the cost varies a lot from pose to
+    pose). Also timed: the same on one core and the full 256 x 256 view of
+    the plain 128^3 u8 ray-cast workload."""
     import oracle
     import synth
     t_setup = time.perf_counter()
@@ -185,9 +186,9 @@ def cpu_baseline(vol, tf_table, poses, model, npose=16, stride=32, npose_1core=4
     setup_s = time.perf_counter() - t_setup
     npix = W_EYE * H_EYE
 
-    def frames(npose, stride, nthreads):
+    def frames(ids, stride, nthreads):
         total_s, samples, busy = 0.0, 0, 0.0
-        for i in range(npose):
+        for i in ids:
             views, projs = poses[i % len(poses)]
             t0 = time.perf_counter()
             sel = ovol.select([otf], views, projs, H_EYE, tau=TAU, ranges=ranges)
@@ -205,8 +206,10 @@ def cpu_baseline(vol, tf_table, poses, model, npose=16, stride=32, npose_1core=4
         return total_s, samples, busy
 
     cores = oracle.max_threads()
-    frame_s, samples, busy = frames(npose, stride, 0)
-    frame1_s, samples1, busy1 = frames(npose_1core, stride_1core, 1)
+    npose = len(pose_ids)
+    frame_s, samples, busy = frames(pose_ids, stride, 0)
+    frame1_s, samples1, busy1 = frames(pose_ids[:npose_1core], stride_1core, 1)
+    npose_1core = min(npose_1core, npose)
     # the plain single-view workload: 128^3 u8 Gaussians, one 256 x 256 view
     a = synth.gaussians_u8(128, seed=1001)
     v1 = oracle.Volume([[a]], 128)
@@ -217,13 +220,15 @@ def cpu_baseline(vol, tf_table, poses, model, npose=16, stride=32, npose_1core=4
     r1 = v1.render([tf1], sel1["leaf"], view1, proj1, 256, 256, step=0.5, variants=False)
     c1_s = time.perf_counter() - t0
     return {"value": round(npose / frame_s, 6), "unit": "stereo frames/s", "cores": cores, "kind": "oracle",
-            "sample": f"poses 0-{npose - 1}, each with its selection and every {stride}th pixel of both eyes "
+            "sample": f"{npose} poses (ids {pose_ids[0]}..{pose_ids[-1]} mod {len(poses)}: the GPU arm's timed poses), "
+                      f"each with its selection and every {stride}th pixel of both eyes "
                       f"({busy:.1f} s timed), per-pixel time extrapolated to full 2 x {W_EYE} x {H_EYE} frames "
                       f"({frame_s:.1f} s for {npose}); block ranges computed once at ingest (untimed)",
             "msamples_per_s": round(samples / frame_s / 1e6, 3), "setup_s": round(setup_s, 2),
             "one_core": {"value": round(npose_1core / frame1_s, 6), "unit": "stereo frames/s", "cores": 1,
                          "msamples_per_s": round(samples1 / frame1_s / 1e6, 3),
-                         "sample": f"poses 0-{npose_1core - 1}, every {stride_1core}th pixel, {busy1:.1f} s"},
+                         "sample": f"the first {min(npose_1core, npose)} of those poses, every {stride_1core}th pixel, "
+                                   f"{busy1:.1f} s"},
             "plain_256": {"value": round(1.0 / c1_s, 4), "unit": "images/s", "cores": cores,
                           "msamples_per_s": round(int(r1["count_late"].sum()) / c1_s / 1e6, 3),
                           "sample": "the full 256 x 256 view of 128^3 u8 Gaussians with its selection"}}
@@ -750,8 +755,9 @@ def run_train_only(args):
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle on the host cores, bounded sample per
     step. Block ranges are computed once at ingest (untimed); a step is the
-    pose's selection plus every 128th pixel of both eyes, and a frame's time
-    extrapolates only the per-pixel part."""
+    pose's selection plus every 32nd pixel of both eyes (the sample
+    cpu_baseline takes of the same poses), and a frame's time extrapolates
+    only the per-pixel part."""
     if rank != 0:
         return
     import oracle
@@ -759,7 +765,7 @@ def run_reference(args, rank, world):
     ovol = oracle.Volume([oracle.pyramid(vol, LEVELS)], BRICK, model=model)
     otf = oracle.make_tf(tf_table, *WINDOW)
     ranges = ovol.block_ranges()
-    stride = 128
+    stride = 32
     npix = W_EYE * H_EYE
 
     def step(i):
@@ -1010,7 +1016,9 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and n_vox == N_VOX:
-        cpu = cpu_baseline(vol_host, tf_table, poses, model)
+        # the GPU arm's timed poses (at most 32, so the sample stays within ~15 s)
+        ids = [(args.warmup + i) % NPOSES for i in range(min(args.steps, 32))]
+        cpu = cpu_baseline(vol_host, tf_table, poses, model, ids)
 
     if rank == 0:
         fps = args.steps * world / (ms_max / 1e3)
