@@ -35,7 +35,10 @@ __device__ unsigned long long g_events[8];
 // registers without spills beat 72 registers at 28 warps; 48 registers spill
 // and lose). The generic, two-rays-per-thread and EXT kernels would spill under
 // it and keep the compiler's choice.
-constexpr int kWarpsPerSM = 32;
+#ifndef SG_RENDER_WARPS_PER_SM
+#define SG_RENDER_WARPS_PER_SM 32
+#endif
+constexpr int kWarpsPerSM = SG_RENDER_WARPS_PER_SM;
 // Lattice points a sample iteration may take (the first after a sub-block
 // lookup, the others without one while they stay in the block): fewer loop
 // trips per sample and fewer iterations in which the warp also runs the jump
