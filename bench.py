@@ -558,7 +558,7 @@ def container_streaming(sg, torch, dev, n_vox=1024, brick=64, levels=4, count=12
 
 
 def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=20000, steps_per_pair=4, eval_poses=16, tau_half=None,
-                  threshold_db=40.0):
+                  threshold_db=40.0, frame_log=None):
     """Learned reconstruction vs the plain path on the same GPU: training on
     `pairs` seeded (pose, full-rate render, half-res render) pairs of the
     bench volume, evaluation on a held-out volume seed and held-out poses.
@@ -625,6 +625,14 @@ def learned_recon(sg, torch, dev, vol, tf_table, model, pairs=20000, steps_per_p
         t_plain.append(e.elapsed_time(f))
     psnrs = rec.psnr_frames[:len(held), 2].cpu().numpy().astype(np.float64)
     fell = rec.fell_back[:len(held)].cpu().numpy().astype(bool)
+    if frame_log:
+        # per held-out frame, appended to the render leg's lines
+        with open(frame_log, "a") as f:
+            for i in range(len(held)):
+                f.write(json.dumps({"leg": "learned", "frame": i, "psnr_db": round(float(psnrs[i]), 3),
+                                    "fell_back": bool(fell[i]), "learned_ms": round(t_learned[i], 4),
+                                    "net_ms": round(t_net[i], 4), "half_render_ms": round(t_learned[i] - t_net[i], 4),
+                                    "plain_ms": round(t_plain[i], 4)}) + "\n")
     # the same frames with two in flight: the half-rate render of frame i + 1
     # overlaps the network on frame i (a second stream); a frame that falls
     # back still adds its plain render
@@ -890,19 +898,38 @@ def run_ours(args, rank, world, local_rank):
     out_bytes = 2 * W_EYE * H_EYE * 16
     nodes = sum(-(-(-(-n_vox // 2 ** L)) // BRICK) ** 3 for L in range(LEVELS))
     touched = torch.zeros(nodes, dtype=torch.uint8, device=dev)
-    prm_touch = sg.render_params(step=STEP, term_alpha=TERM, empty_skip=1, touched=touched)
+    frame_samples = torch.zeros(1, dtype=torch.int64, device=dev)
+    prm_touch = sg.render_params(step=STEP, term_alpha=TERM, empty_skip=1, touched=touched,
+                                 sample_total=frame_samples)
     saved_cfg = sg.sg_get_render_config(vol)
     sg.sg_set_render_config(vol)
-    alg, alg_selected = [], []
+    alg, alg_selected, frame_records = [], [], []
     for i in range(args.steps):
         p = mine[(args.warmup + i) % NPOSES]
         st = sg.sg_select_lod(vol, p, stats=True, stream=stream)
         touched.zero_()
+        frame_samples.zero_()
         sg.sg_render(vol, p, prm_touch, outs, stream=stream)
-        alg.append(int(touched.sum().item()) * brick_bytes + out_bytes)
+        nt = int(touched.sum().item())
+        alg.append(nt * brick_bytes + out_bytes)
         alg_selected.append(st["nonempty"] * brick_bytes + out_bytes)
+        if args.frame_log:
+            ns = int(frame_samples.item())
+            frame_records.append({"leg": "render", "frame": i, "pose": (args.warmup + i) % NPOSES, "rank": rank,
+                                  "frame_ms": round(float(frame_ms[i]), 4), "render_ms": round(render_ms[i], 4),
+                                  "fps": round(1e3 / float(frame_ms[i]), 2), "samples": ns,
+                                  "gsamples_per_s": round(ns / render_ms[i] / 1e6, 3),
+                                  "bricks_selected": st["selected"], "bricks_nonempty": st["nonempty"],
+                                  "bricks_touched": nt, "requested": st["requested"], "fallback": st["fallback"],
+                                  "culled": st["culled"], "empty": st["empty"]})
     sg.sg_set_render_config(vol, **saved_cfg)
     sel_stats = st
+    if args.frame_log:
+        # one JSON object per timed frame (rank r writes PATH.r on multi-GPU runs)
+        path = args.frame_log if world == 1 else f"{args.frame_log}.{rank}"
+        with open(path, "w") as f:
+            for r in frame_records:
+                f.write(json.dumps(r) + "\n")
     peak, peak_kind = measured_peak_hbm()
     avg_render_s = sum(render_ms) / len(render_ms) / 1e3
     achieved = (sum(alg) / len(alg)) / avg_render_s / 1e9
@@ -1012,7 +1039,8 @@ def run_ours(args, rank, world, local_rank):
         batched = batched_4d(sg, torch, dev)
         streaming = streaming_flythrough(sg, torch, dev)
         container = container_streaming(sg, torch, dev)
-        learned = learned_recon(sg, torch, dev, vol, tf_table, model, pairs=args.learned_pairs)
+        learned = learned_recon(sg, torch, dev, vol, tf_table, model, pairs=args.learned_pairs,
+                                frame_log=args.frame_log)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and n_vox == N_VOX:
@@ -1075,6 +1103,9 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the batched 4D and learned measurements")
     ap.add_argument("--learned-half-tau", type=float, default=None,
                     help="pixel error bound of the reduced render (default: half of tau, the full image's LOD)")
+    ap.add_argument("--frame-log", default=None, metavar="PATH",
+                    help="write per-frame metrics of the timed frames as JSON lines (untimed replay of each pose: "
+                         "samples, bricks selected / touched / requested, fallback; times from the timed region)")
     ap.add_argument("--learned-pairs", type=int, default=20000,
                     help="training pairs for the learned path (the configuration's 20000, about 3 min)")
     ap.add_argument("--tensor-path", type=int, default=-1,

@@ -471,6 +471,7 @@ sg_status sg_volume_destroy(sg_volume* v) {
 }
 
 sg_status sg_upload_volume_device(sg_volume* v, int t, int c, const void* dev_level0, void* stream) {
+  sg::NvtxRange nvtx_range("sg_upload_volume_device");
   SG_CHECK_ARG(v && dev_level0, "volume and dev_level0 must not be NULL");
   SG_CHECK_ARG(t >= 0 && t < v->T && c >= 0 && c < v->nch, "t or c out of range");
   if (v->pooled) {
@@ -573,6 +574,7 @@ sg_status sg_set_brick_ranges(sg_volume* v, int t, int c, int level, int n, cons
 
 sg_status sg_set_transfer_function(sg_volume* v, int c, const float* rgba, int n, float lo, float hi, float ref_step,
                                    void* stream) {
+  sg::NvtxRange nvtx_range("sg_set_transfer_function");
   SG_CHECK_ARG(v && rgba, "volume and rgba must not be NULL");
   SG_CHECK_ARG(c >= 0 && c < v->nch, "channel out of range");
   SG_CHECK_ARG(n >= 2 && n <= kMaxTF, "table size must be 2..4096");
@@ -633,6 +635,7 @@ sg_status sg_set_channel_shading(sg_volume* v, int c, int input, const float* pa
 }
 
 sg_status sg_select_lod(sg_volume* v, const sg_pose* p, sg_select_stats* stats, void* stream) {
+  sg::NvtxRange nvtx_range("sg_select_lod");
   SG_CHECK_ARG(v, "volume is NULL");
   sg_status st = check_pose(v, p);
   if (st != SG_OK) return st;
@@ -778,6 +781,7 @@ sg_status sg_read_brick(sg_volume* v, int t, int c, int level, int bx, int by, i
 }
 
 sg_status sg_render(sg_volume* v, const sg_pose* p, const sg_render_params* prm, float* out_rgba[2], void* stream) {
+  sg::NvtxRange nvtx_range("sg_render");
   SG_CHECK_ARG(v && out_rgba && out_rgba[0] && out_rgba[1], "volume or outputs NULL");
   SG_CHECK_ARG(((uintptr_t)out_rgba[0] % 16) == 0 && ((uintptr_t)out_rgba[1] % 16) == 0,
                "output buffers must be 16-byte aligned");
@@ -793,6 +797,7 @@ sg_status sg_render(sg_volume* v, const sg_pose* p, const sg_render_params* prm,
 
 sg_status sg_render_host(sg_volume* v, const sg_pose* p, const sg_render_params* prm, float* host_rgba[2],
                          void* stream) {
+  sg::NvtxRange nvtx_range("sg_render_host");
   SG_CHECK_ARG(v && host_rgba && host_rgba[0] && host_rgba[1], "volume or outputs NULL");
   sg_status st = check_pose(v, p);
   if (st != SG_OK) return st;
@@ -877,6 +882,7 @@ sg_status sg_render_host_async(sg_volume* v, const sg_pose* p, const sg_render_p
 
 sg_status sg_render_batch(sg_volume* v, const sg_pose* poses, int n, const sg_render_params* prm, float** outs,
                           void* stream) {
+  sg::NvtxRange nvtx_range("sg_render_batch");
   SG_CHECK_ARG(v && poses && outs && n >= 1 && n <= 64, "volume/poses/outs NULL or n not in 1..64");
   sg_status st = check_render_params(prm);
   if (st != SG_OK) return st;
@@ -993,6 +999,7 @@ sg_status sg_upload_bricks(sg_volume* v, int t, int c, int level, int n, const i
 
 sg_status sg_upload_brick_list(sg_volume* v, int t, int c, int n, const int32_t* nodes, const void* const* host,
                                int32_t* n_done, void* stream) {
+  sg::NvtxRange nvtx_range("sg_upload_brick_list");
   SG_CHECK_ARG(v && n_done && n >= 0 && (n == 0 || (nodes && host)), "volume/nodes/host/n_done NULL or n < 0");
   SG_CHECK_ARG(t >= 0 && t < v->T && c >= 0 && c < v->nch, "t or c out of range");
   *n_done = 0;

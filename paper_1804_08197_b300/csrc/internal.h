@@ -8,8 +8,19 @@
 #include <vector>
 
 #include "../../include/sg.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace sg {
+
+// A named NVTX range over the C-ABI call it is declared in, so a profiler
+// that reads NVTX (ncu --nvtx) can pick a stage's kernels; without an
+// attached tool a push or pop is a test of an unset function pointer.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int kMaxLevels = 16;
 constexpr int kMaxCh = 4;

@@ -292,6 +292,7 @@ namespace {
 
 sg_status stream_impl(sg_volume* v, int slot, sg_host_cache* hc, uint64_t max_bytes, sg_stream_stats* stats,
                       void* stream, bool async, const char* name) {
+  NvtxRange nvtx_range(name);
   if (!v || !hc || slot < 0 || slot >= kMaxSlots) {
     set_error("volume/cache NULL or slot out of range");
     return SG_ERR_INVALID_ARG;

@@ -1148,6 +1148,7 @@ sg_status sg_unet_set_params(sg_unet* u, const float* host, int64_t n) {
 
 sg_status sg_unet_forward(sg_unet* u, const float* const* in, int64_t in_pitch, int n, int h, int w, float* const* out,
                           int64_t out_pitch, void* stream) {
+  sg::NvtxRange nvtx_range("sg_unet_forward");
   if (!u || !in || !out) {
     set_error("sg_unet_forward: NULL argument");
     return SG_ERR_INVALID_ARG;
@@ -1173,6 +1174,7 @@ sg_status sg_unet_forward(sg_unet* u, const float* const* in, int64_t in_pitch, 
 
 sg_status sg_unet_backward(sg_unet* u, const float* const* target, int64_t target_pitch, const float* const* out,
                            int64_t out_pitch, float* loss, void* stream) {
+  sg::NvtxRange nvtx_range("sg_unet_backward");
   if (!u || !target || !out || u->n == 0) {
     set_error("sg_unet_backward: NULL argument or no forward pass before");
     return SG_ERR_INVALID_ARG;
@@ -1306,6 +1308,7 @@ sg_status sg_unet_load(sg_unet* u, const char* path) {
 
 sg_status sg_render_learned(sg_volume* vol, sg_unet* u, const sg_pose* pose, const sg_learned_params* prm,
                             float* out_rgba[2], float* psnr_db, int32_t* fell_back, void* stream) {
+  sg::NvtxRange nvtx_range("sg_render_learned");
   if (!vol || !u || !pose || !prm || !out_rgba || !out_rgba[0] || !out_rgba[1]) {
     set_error("sg_render_learned: NULL argument");
     return SG_ERR_INVALID_ARG;
