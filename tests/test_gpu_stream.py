@@ -483,7 +483,8 @@ def test_async_streaming_never_waits_and_converges(tmp_path):
             assert st["missing"] == 0 and st["served"] <= 24 and st["requested"] == stats["requested"]
             if frame == 0:
                 # a cold host cache: nothing to place yet, a full budget of loads queued
-                assert st["served"] == 0 and st["queued"] == min(24, len(reqs)) and st["in_flight"] > 0
+                assert st["served"] == 0 and st["queued"] == min(24, len(reqs))
+                assert 0 <= st["in_flight"] <= st["queued"]  # the loaders may already have finished some
             failed += st["failed"]
             served += st["served"]
             reads += st["disk_reads"]
