@@ -6,7 +6,7 @@ the autotuner picks (as bench.py times it). The selection is compared bit
 for bit over the whole octree; the image on every 97th pixel of both eyes
 (about 47 500 rays); the sample counts on the same pixels of the render
 without empty-space skipping, which must equal the skipping one bit for
-bit."""
+bit. Then all 64 poses: selections bit for bit and every 16th pixel."""
 import numpy as np
 import pytest
 
@@ -66,6 +66,39 @@ def test_full_size_stereo_frame_on_sampled_pixels(bench_case, pose_index, record
                      max_err_termination_bracket=st["max_err_termination_bracket"],
                      max_abs_err_ambiguous=st["max_err_ambiguous"], ambiguous_fraction=st["ambiguous"],
                      termination_ties=st["termination_ties"], pixels=st["n"])
+
+
+def test_every_bench_pose_on_a_sixteenth_of_the_pixels(bench_case, record_error):
+    """All 64 bench poses: each pose's selection bit for bit over the whole
+    octree, and every 16th pixel of both eyes (a different offset per pose
+    and eye, 288 000 rays per eye) against the oracle's ray casting, in the
+    launch shape the autotuner picks on the first pose."""
+    import torch
+    from paper_1804_08197_b300 import sg
+    case = bench_case
+    poses = synth.head_poses(64, seed=3002, width=W_EYE, height=H_EYE)
+    outs = [torch.empty((H_EYE, W_EYE, 4), dtype=torch.float32, device="cuda") for _ in range(2)]
+    npix = W_EYE * H_EYE
+    worst = dict(max_err=0.0, max_err_termination_bracket=0.0, max_err_ambiguous=0.0)
+    amb, ties, n = 0.0, 0, 0
+    for i, (views, projs) in enumerate(poses):
+        pose, stats, gsel, ref = case.select(views, projs, W_EYE, H_EYE, tau=1.0)
+        compare_selection(gsel, ref)
+        if i == 0:
+            sg.sg_autotune_render(case.vol, [pose], sg.render_params(step=0.5), outs, reps=1)
+        imgs, _ = case.render(pose, step=0.5, counts=False)
+        for e in range(2):
+            pix = np.arange((5 * i + 3 * e) % 16, npix, 16)
+            oref = case.ovol.render(case.otfs, ref["leaf"], views[e], projs[e], W_EYE, H_EYE, step=0.5, pixels=pix)
+            st = compare_image(imgs[e][pix], oref)
+            assert st["n"] == len(pix)
+            for k in worst:
+                worst[k] = max(worst[k], st[k])
+            amb = max(amb, st["ambiguous"])
+            ties += st["termination_ties"]
+            n += st["n"]
+    record_error("64 poses x 2 eyes, every 16th pixel", **worst, ambiguous_fraction_max=amb,
+                 termination_ties=ties, pixels=n)
 
 
 def test_full_size_batched_4d_on_sampled_pixels(record_error):
