@@ -187,11 +187,37 @@ class Volume:
         s = _Vol()
         s.dtype = 1 if self.channels[0][0].dtype == np.uint8 else 2
         s.levels, s.brick, s.nch = self.levels, self.brick, self.nch
+        self.level_dims = []
         for L in range(self.levels):
             a = self.channels[0][L]
             s.dims[L][0], s.dims[L][1], s.dims[L][2] = a.shape[2], a.shape[1], a.shape[0]
+            self.level_dims.append((a.shape[2], a.shape[1], a.shape[0]))
             for c in range(self.nch):
                 s.data[L][c] = self.channels[c][L].ctypes.data
+        self._finish(s, model)
+
+    @classmethod
+    def layout(cls, dims, brick, levels, model=None, dtype=np.uint8, nch=1):
+        """A volume of the given layout (level-0 dims (x, y, z); each level
+        halves every axis, rounding up, as pyramid() does) with no voxel
+        data: for the selection only, which reads the geometry, the block
+        ranges (pass them to select) and the residency, never a voxel."""
+        self = cls.__new__(cls)
+        self.channels = None
+        self.levels, self.brick, self.nch = int(levels), int(brick), int(nch)
+        s = _Vol()
+        s.dtype = 1 if np.dtype(dtype) == np.uint8 else 2
+        s.levels, s.brick, s.nch = self.levels, self.brick, self.nch
+        self.level_dims = []
+        d = [int(x) for x in dims]
+        for L in range(self.levels):
+            s.dims[L][0], s.dims[L][1], s.dims[L][2] = d
+            self.level_dims.append(tuple(d))
+            d = [(x + 1) // 2 for x in d]
+        self._finish(s, model)
+        return self
+
+    def _finish(self, s, model):
         m = np.eye(4).T.reshape(16) if model is None else np.asarray(model, np.float64)
         self.model = np.asarray(m, np.float64).reshape(16).copy()
         for i in range(16):
@@ -202,8 +228,7 @@ class Volume:
         self.level_offsets = offs[: self.levels + 1].copy()
 
     def blocks_per_axis(self, L):
-        a = self.channels[0][L]
-        return tuple((d + self.brick - 1) // self.brick for d in (a.shape[2], a.shape[1], a.shape[0]))
+        return tuple((d + self.brick - 1) // self.brick for d in self.level_dims[L])
 
     def node_coords(self, node_id):
         L = int(np.searchsorted(self.level_offsets, node_id, side="right") - 1)
@@ -221,6 +246,8 @@ class Volume:
         twice for a single view). Returns dict(leaf, state, requests,
         selected, used); used marks the blocks whose cache stamps this
         traversal renews."""
+        if ranges is None and self.channels is None:
+            raise ValueError("a layout-only volume needs the block ranges")
         if ranges is None:
             ranges = self.block_ranges()
         nb0 = self.blocks_per_axis(0)

@@ -507,3 +507,66 @@ def test_async_streaming_never_waits_and_converges(tmp_path):
         sg.sg_host_cache_destroy(hc)
         sg.sg_volume_destroy(vol)
         sg.sg_container_close(k)
+
+
+def test_full_size_large_volume_selection_and_cache_match_the_oracle():
+    """The large-volume configuration's layout at full size: 4096^3 u8 over
+    1 m, 128^3 bricks, 6 levels (37 449 blocks), along a 48-pose seeded
+    fly-through (seed 3004) at 2 x 1440 x 1600, tau 1 px, a 2000-brick device
+    cache and 64 bricks uploaded per frame (coarse first). The transfer
+    function has non-zero alpha everywhere, so no block is transparent
+    whatever its values and the selection depends only on the geometry and
+    the residency: uploads can be zero bricks, and the oracle needs no voxel
+    data (a layout-only volume with every range [0, 255]). Every frame the
+    GPU cache's residency equals the oracle cache's and the selection (leaf
+    map, node states, requests) equals the oracle's bit for bit."""
+    import torch
+    from paper_1804_08197_b300 import sg
+    N, BB, LV, slots, per_frame = 4096, 128, 6, 2000, 64
+    model = synth.volume_model(N, 1.0)
+    ovol = oracle.Volume.layout((N, N, N), BB, LV, model=model, dtype=np.uint8)
+    assert ovol.node_count == 37449
+    ranges = np.zeros((ovol.node_count, 1, 2), np.uint32)
+    ranges[:, 0, 1] = 255
+    table = synth.tf_piecewise(2004).copy()
+    table[:, 3] = np.maximum(table[:, 3], 0.05)  # opaque enough everywhere: nothing is transparent
+    otf = oracle.make_tf(table, 0.0, 255.0)
+    R = BB + 2
+    brick_bytes = (R ** 3 + 255) // 256 * 256
+    vol = sg.sg_volume_create((N, N, N), sg.SG_U8, BB, LV, model=model, device_pool_bytes=slots * brick_bytes)
+    zero = torch.zeros(R ** 3, dtype=torch.uint8).pin_memory()
+    try:
+        sg.sg_set_transfer_function(vol, 0, table, 0.0, 255.0)
+        for L in range(LV):
+            nbx, nby, nbz = ovol.blocks_per_axis(L)
+            xyz = np.array([(x, y, z) for z in range(nbz) for y in range(nby) for x in range(nbx)])
+            lo, hi = ovol.level_offsets[L], ovol.level_offsets[L + 1]
+            sg.sg_set_brick_ranges(vol, 0, 0, L, xyz, ranges[lo:hi, 0, :])
+        root = int(ovol.level_offsets[LV - 1])
+        assert sg.sg_upload_brick_list(vol, 0, 0, [root], [zero.data_ptr()]) == 1
+        cache = oracle.Cache(ovol, slots)
+        cache.place([root])
+        W, H = 1440, 1600
+        poses = synth.flythrough_poses(48, seed=3004, extent_m=1.0, width=W, height=H)
+        nb0 = ovol.blocks_per_axis(0)
+        ncell = nb0[0] * nb0[1] * nb0[2]
+        evicted, requested, fallback = 0, 0, 0
+        for views, projs in poses:
+            pose = sg.make_pose(views, projs, W, H, pixel_error=1.0)
+            stats = sg.sg_select_lod(vol, pose, stats=True)
+            res = sg.sg_read_residency(vol, 0, ovol.node_count) >= 0
+            assert np.array_equal(res, cache.resident != 0)
+            ref = cache.select([otf], views, projs, H, tau=1.0, ranges=ranges)
+            compare_selection(sg.sg_read_selection(vol, 0, ncell, ovol.node_count), ref)
+            assert stats["selected"] == ref["selected"] and stats["empty"] == 0
+            requested += stats["requested"]
+            fallback += stats["fallback"]
+            order = sorted((int(n) for n in ref["requests"]), key=lambda n: (-ovol.node_coords(n)[0], n))[:per_frame]
+            if order:
+                done = sg.sg_upload_brick_list(vol, 0, 0, order, [zero.data_ptr()] * len(order))
+                m, ev = cache.place(order)
+                assert m == done
+                evicted += len(ev)
+        assert requested > 0 and fallback > 0 and evicted > 0
+    finally:
+        sg.sg_volume_destroy(vol)

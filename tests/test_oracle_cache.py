@@ -111,3 +111,32 @@ def test_invariants_over_random_histories():
                 st[r] = frame
             assert not evs
             assert np.array_equal(res, c.resident)
+
+
+def test_layout_only_volume_selects_like_the_volume_with_data():
+    """Volume.layout (geometry without voxels) gives the same level offsets,
+    blocks and selection as the volume built from data, given the same block
+    ranges and residency; it refuses to select without ranges."""
+    import pytest
+    import synth
+    a = synth.filaments_u16((77, 50, 39), seed=11, ntubes=6)  # ragged on every axis
+    model = synth.volume_model(77, 0.5)
+    full = oracle.Volume([oracle.pyramid(a, 4)], 8, model=model)
+    bare = oracle.Volume.layout((77, 50, 39), 8, 4, model=model, dtype=np.uint16)
+    assert bare.node_count == full.node_count and list(bare.level_offsets) == list(full.level_offsets)
+    for L in range(4):
+        assert bare.blocks_per_axis(L) == full.blocks_per_axis(L)
+    ranges = full.block_ranges()
+    tf = oracle.make_tf(synth.tf_piecewise(2002, zero_alpha_points=2), 300.0, 60000.0)
+    rng = np.random.default_rng(3)
+    resident = (rng.random(full.node_count) < 0.7).astype(np.uint8)
+    resident[full.level_offsets[3]:] = 1
+    (views, projs), = synth.head_poses(1, seed=3101, extent_m=0.5, width=96, height=80)
+    for res in (None, resident):
+        r1 = full.select([tf], views, projs, 80, tau=0.5, resident=res, ranges=ranges)
+        r2 = bare.select([tf], views, projs, 80, tau=0.5, resident=res, ranges=ranges)
+        for k in ("leaf", "state", "requests", "used"):
+            assert np.array_equal(r1[k], r2[k]), k
+        assert r1["selected"] == r2["selected"]
+    with pytest.raises(ValueError):
+        bare.select([tf], views, projs, 80)
