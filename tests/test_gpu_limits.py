@@ -121,3 +121,46 @@ def test_step_extremes_and_no_early_termination(step, term, record_error):
                name=f"step {step} term {term}")
     finally:
         case.close()
+
+
+def test_a_batch_of_64_poses_equals_single_renders():
+    """The largest batch (64 poses, 128 images of uneven sizes, each pose in
+    its own selection slot, up to 255): one launch per launch shape, every
+    image equal bit for bit to sg_render of its pose; the slot-0 image also
+    matches the oracle."""
+    import torch
+    from paper_1804_08197_b300 import sg
+    v = synth.filaments_u16((96, 80, 72), seed=1106, ntubes=12)
+    case = GpuCase([v], 16, 3, model=synth.volume_model(96, 0.5))
+    try:
+        case.set_tfs([synth.tf_piecewise(2106, zero_alpha_points=2)], [(300.0, 60000.0)])
+        sizes = [(40 + 8 * (i % 5), 32 + 8 * (i % 3)) for i in range(64)]
+        poses, views = [], []
+        for i, (W, H) in enumerate(sizes):
+            vw, pj = _views(3600 + i, W, H)
+            p = sg.make_pose(vw, pj, W, H, pixel_error=0.5, slot=255 - i)
+            sg.sg_select_lod(case.vol, p)
+            poses.append(p)
+            views.append((vw, pj))
+        prm = sg.render_params(step=0.5)
+        outs = [torch.empty((H, W, 4), device="cuda") for (W, H) in sizes for _ in range(2)]
+        single = [torch.empty((H, W, 4), device="cuda") for (W, H) in sizes for _ in range(2)]
+        for cfg in [dict(), dict(persistent=1, tile_w=8, tile_h=8), dict(tile_w=32, tile_h=8, rays_per_thread=2)]:
+            sg.sg_set_render_config(case.vol, **cfg)
+            for o in outs:
+                o.fill_(-1.0)
+            sg.sg_render_batch(case.vol, poses, prm, outs)
+            for i, p in enumerate(poses):
+                sg.sg_render(case.vol, p, prm, single[2 * i:2 * i + 2])
+            torch.cuda.synchronize()
+            for a, b in zip(outs, single):
+                assert torch.equal(a, b), cfg
+        sg.sg_set_render_config(case.vol)
+        (W, H), (vw, pj) = sizes[0], views[0]
+        ref = case.ovol.select(case.otfs, vw, pj, H, tau=0.5, ranges=case.ranges)
+        for e in range(2):
+            compare_image(outs[e].cpu().numpy().reshape(-1, 4), case.oracle_render(ref["leaf"], vw[e], pj[e], W, H))
+        with pytest.raises(sg.SGError):
+            sg.sg_render_batch(case.vol, poses + poses[:1], prm, outs + outs[:2])
+    finally:
+        case.close()

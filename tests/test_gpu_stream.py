@@ -570,3 +570,80 @@ def test_full_size_large_volume_selection_and_cache_match_the_oracle():
         assert requested > 0 and fallback > 0 and evicted > 0
     finally:
         sg.sg_volume_destroy(vol)
+
+
+def test_two_channel_container_streams_both_channels_together(tmp_path):
+    """A 2-channel container (blob channels 0 and 1, their own tables,
+    additive blend): a brick is placed only once both of its channels are in
+    the host cache, so the GPU never holds one channel of a brick. Streamed
+    asynchronously until the view converges; every frame's selection equals
+    the oracle's for the GPU's residency, and the converged image matches
+    the oracle's two-channel rendering."""
+    import time
+    import torch
+    from paper_1804_08197_b300 import sg
+    dims = (96, 80, 64)
+    chans = [synth.blobs_u16(dims, seed=1003, channel=c, nblobs=10) for c in range(2)]
+    model = synth.volume_model(96, 0.5)
+    ovol = oracle.Volume([oracle.pyramid(a, 3) for a in chans], 16, model=model)
+    full = ovol.block_ranges()
+    tables = [synth.tf_piecewise(2003, zero_alpha_points=2, colour=(0.1, 0.9, 0.2)),
+              synth.tf_piecewise(2004, zero_alpha_points=2, colour=(0.9, 0.1, 0.8))]
+    otfs = [oracle.make_tf(t, 200.0, 40000.0) for t in tables]
+    path = tmp_path / "two.sgc"
+    k = sg.sg_container_create(path, sg.volume_desc(dims, sg.SG_U16, 16, 3, channels=2, model=model))
+    for n in range(ovol.node_count):
+        L, b = ovol.node_coords(n)
+        for c in range(2):
+            g = ovol.channels[c][L]
+            R = 18
+            iz = np.clip(np.arange(R) + b[2] * 16 - 1, 0, g.shape[0] - 1)
+            iy = np.clip(np.arange(R) + b[1] * 16 - 1, 0, g.shape[1] - 1)
+            ix = np.clip(np.arange(R) + b[0] * 16 - 1, 0, g.shape[2] - 1)
+            sg.sg_container_append(k, 0, c, L, *b, np.ascontiguousarray(g[np.ix_(iz, iy, ix)]), *full[n, c])
+    sg.sg_container_finish(k)
+    sg.sg_container_close(k)
+    k = sg.sg_container_open(path)
+    brick_bytes = (18 ** 3 * 2 + 255) // 256 * 256
+    vol = sg.sg_volume_create(dims, sg.SG_U16, 16, 3, channels=2, model=model,
+                              device_pool_bytes=ovol.node_count * brick_bytes * 2)
+    hc = sg.sg_host_cache_create(k, 2 * ovol.node_count * 18 ** 3 * 2, pinned=True, threads=4)
+    try:
+        for c in range(2):
+            sg.sg_set_transfer_function(vol, c, tables[c], 200.0, 40000.0)
+            for L in range(3):
+                nbx, nby, nbz = ovol.blocks_per_axis(L)
+                xyz = np.array([(x, y, z) for z in range(nbz) for y in range(nby) for x in range(nbx)])
+                lo, hi = ovol.level_offsets[L], ovol.level_offsets[L + 1]
+                sg.sg_set_brick_ranges(vol, 0, c, L, xyz, full[lo:hi, c, :])
+        top = list(range(int(ovol.level_offsets[2]), int(ovol.level_offsets[3])))  # the coarsest level (pinned)
+        for c in range(2):
+            ptrs = [sg.sg_host_cache_fetch(hc, 0, c, n)[0] for n in top]
+            assert sg.sg_upload_brick_list(vol, 0, c, top, ptrs) == len(top)
+        W, H, tau = 160, 176, 0.5
+        views, projs = _stereo((-0.3, 0.05, 0.2), (-0.05, 0.0, 0.0), W, H)
+        pose = sg.make_pose(views, projs, W, H, pixel_error=tau)
+        for frame in range(2000):
+            stats = sg.sg_select_lod(vol, pose, stats=True)
+            res = sg.sg_read_residency(vol, 0, ovol.node_count) >= 0
+            ref = ovol.select(otfs, views, projs, H, tau=tau, resident=res.astype(np.uint8), ranges=full)
+            nb0 = ovol.blocks_per_axis(0)
+            compare_selection(sg.sg_read_selection(vol, 0, nb0[0] * nb0[1] * nb0[2], ovol.node_count), ref)
+            if stats["requested"] == 0:
+                break
+            st = sg.sg_stream_requests(vol, 0, hc, 16 * 18 ** 3 * 2 * 2, asynchronous=True)
+            assert st["failed"] == 0 and st["missing"] == 0
+            if st["served"] == 0:
+                time.sleep(0.002)
+        else:
+            raise AssertionError("two-channel streaming did not converge")
+        assert stats["fallback"] == 0
+        outs = [torch.empty((H, W, 4), device="cuda") for _ in range(2)]
+        sg.sg_render(vol, pose, sg.render_params(), outs)
+        torch.cuda.synchronize()
+        for e in range(2):
+            compare_image(outs[e].cpu().numpy().reshape(-1, 4), ovol.render(otfs, ref["leaf"], views[e], projs[e], W, H))
+    finally:
+        sg.sg_host_cache_destroy(hc)
+        sg.sg_volume_destroy(vol)
+        sg.sg_container_close(k)
