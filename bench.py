@@ -856,16 +856,32 @@ def run_ours(args, rank, world, local_rank):
         if args.tune_cache and rank == 0:
             sg.sg_render_config_store(args.tune_cache, tune_key, tuned)
 
+    # selection of pose i + 1 (its own slot, a second stream) overlaps the
+    # render of pose i; a slot is selected again only after the render that
+    # read it (two slots, alternating)
+    sel_stream = torch.cuda.Stream(dev)
+    mine2 = [[p, sg.make_pose(*pv, W_EYE, H_EYE, pixel_error=TAU, slot=1)]
+             for p, pv in zip(mine, rank_poses(poses, rank, world))]
+    selected = [torch.cuda.Event(), torch.cuda.Event()]
+    rendered = [None, None]
+
     def step(i, ev=None):
-        p = mine[i % NPOSES]
+        k = i % 2
+        p = mine2[i % NPOSES][k]
+        if rendered[k] is not None:
+            sel_stream.wait_event(rendered[k])
         if ev is not None:
-            ev[2].record(stream)
-        sg.sg_select_lod(vol, p, stream=stream)
+            ev[2].record(sel_stream)
+        sg.sg_select_lod(vol, p, stream=sel_stream)
+        selected[k].record(sel_stream)
+        stream.wait_event(selected[k])
         if ev is not None:
             ev[0].record(stream)
         sg.sg_render(vol, p, prm, outs, stream=stream)
         if ev is not None:
             ev[1].record(stream)
+        rendered[k] = torch.cuda.Event()
+        rendered[k].record(stream)
 
     for i in range(args.warmup):
         step(i)
@@ -880,6 +896,7 @@ def run_ours(args, rank, world, local_rank):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
+    sel_stream.wait_event(e0)
     for i in range(args.steps):
         step(args.warmup + i, rev[i])
     e1.record(stream)
@@ -887,7 +904,10 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     render_ms = [a.elapsed_time(b) for a, b, _ in rev]
-    frame_ms = np.array([c.elapsed_time(b) for _, b, c in rev])  # select + render of one pose
+    # frame period: from the previous frame's render end (the loop start for
+    # the first) to this one's; a pose's selection overlaps the render before
+    ends = [e0] + [b for _, b, _ in rev]
+    frame_ms = np.array([ends[i].elapsed_time(ends[i + 1]) for i in range(args.steps)])
     samples = int(total.item())
     ms_max = max_over_ranks(ms, world, dev)
 
