@@ -252,7 +252,32 @@ void host_cache_enqueue(sg_host_cache* hc, const std::vector<std::pair<int64_t, 
     for (auto& j : todo) hc->jobs.push_back(j);
     hc->in_flight += (int64_t)todo.size();
   }
-  while ((int)hc->loaders.size() < hc->threads) hc->loaders.emplace_back(loader_main, hc);
+  while ((int)hc->loaders.size() < hc->threads) {
+    try {
+      hc->loaders.emplace_back(loader_main, hc);
+    } catch (...) {  // no thread to be had: fewer loaders (or none, below)
+      break;
+    }
+  }
+  if (hc->loaders.empty()) {
+    // no loader could start: read the queue here, so that no wait can hang
+    for (;;) {
+      std::pair<int64_t, int64_t> job;
+      {
+        std::lock_guard<std::mutex> g(hc->mu);
+        if (hc->jobs.empty()) break;
+        job = hc->jobs.front();
+        hc->jobs.pop_front();
+      }
+      uint32_t comp = 0;
+      const sg_status st = container_read_chunk(hc->k, (uint64_t)job.second,
+                                                hc->arena + (size_t)job.first * hc->entry_bytes, nullptr, &comp);
+      std::lock_guard<std::mutex> g(hc->mu);
+      hc->done.push_back({job.first, st == SG_OK ? std::max<uint32_t>(comp, 1u) : 0u});
+      --hc->in_flight;
+    }
+    return;
+  }
   hc->cv_job.notify_all();
 }
 
@@ -460,7 +485,13 @@ sg_status stream_impl(sg_volume* v, int slot, sg_host_cache* hc, uint64_t max_by
     };
     const int nt = (int)std::min<size_t>((size_t)hc->threads, todo.size());
     std::vector<std::thread> pool;
-    for (int i = 1; i < nt; ++i) pool.emplace_back(work);
+    for (int i = 1; i < nt; ++i) {
+      try {
+        pool.emplace_back(work);
+      } catch (...) {  // no more threads: the calling thread reads the rest
+        break;
+      }
+    }
     if (nt >= 1) work();
     for (auto& th : pool) th.join();
     // a failed chunk: its entry is dropped, its key remembered, and its brick
