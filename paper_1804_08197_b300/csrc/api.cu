@@ -337,130 +337,132 @@ const char* sg_last_error(void) { return g_err.c_str(); }
 const char* sg_version(void) { return "sg-b300 0.1 (sm_103a)"; }
 
 sg_status sg_volume_create(const sg_volume_desc* d, sg_volume** out) {
-  SG_CHECK_ARG(d && out, "desc and out must not be NULL");
-  *out = nullptr;
-  SG_CHECK_ARG(d->dims[0] >= 1 && d->dims[1] >= 1 && d->dims[2] >= 1, "dims must be >= 1");
-  SG_CHECK_ARG(d->dtype == SG_U8 || d->dtype == SG_U16, "dtype must be SG_U8 or SG_U16");
-  SG_CHECK_ARG(d->channels >= 1 && d->channels <= kMaxCh, "channels must be 1..4");
-  SG_CHECK_ARG(d->timepoints >= 1 && d->timepoints <= 4096, "timepoints must be 1..4096");
-  SG_CHECK_ARG(d->brick_size >= 8 && d->brick_size <= 256 && d->brick_size % 8 == 0,
-               "brick_size must be a multiple of 8 in [8, 256]");
-  SG_CHECK_ARG(d->apron == 1, "apron must be 1");
-  SG_CHECK_ARG(d->lod_levels >= 1 && d->lod_levels <= kMaxLevels, "lod_levels must be 1..16");
-  // default: the finest cell that keeps at most kMaxSubPerEdge cells per brick edge
-  const int sub = d->skip_block ? d->skip_block : (d->brick_size <= 64 ? 2 : (d->brick_size <= 128 ? 4 : 8));
-  SG_CHECK_ARG((sub == 2 || sub == 4 || sub == 8 || sub == 16) && d->brick_size % sub == 0 &&
-                   d->brick_size / sub <= kMaxSubPerEdge,
-               "skip_block must be 0 or 2/4/8/16 dividing brick_size, at most 32 cells per brick edge");
+  return sg::guarded("sg_volume_create", [&]() -> sg_status {
+    SG_CHECK_ARG(d && out, "desc and out must not be NULL");
+    *out = nullptr;
+    SG_CHECK_ARG(d->dims[0] >= 1 && d->dims[1] >= 1 && d->dims[2] >= 1, "dims must be >= 1");
+    SG_CHECK_ARG(d->dtype == SG_U8 || d->dtype == SG_U16, "dtype must be SG_U8 or SG_U16");
+    SG_CHECK_ARG(d->channels >= 1 && d->channels <= kMaxCh, "channels must be 1..4");
+    SG_CHECK_ARG(d->timepoints >= 1 && d->timepoints <= 4096, "timepoints must be 1..4096");
+    SG_CHECK_ARG(d->brick_size >= 8 && d->brick_size <= 256 && d->brick_size % 8 == 0,
+                 "brick_size must be a multiple of 8 in [8, 256]");
+    SG_CHECK_ARG(d->apron == 1, "apron must be 1");
+    SG_CHECK_ARG(d->lod_levels >= 1 && d->lod_levels <= kMaxLevels, "lod_levels must be 1..16");
+    // default: the finest cell that keeps at most kMaxSubPerEdge cells per brick edge
+    const int sub = d->skip_block ? d->skip_block : (d->brick_size <= 64 ? 2 : (d->brick_size <= 128 ? 4 : 8));
+    SG_CHECK_ARG((sub == 2 || sub == 4 || sub == 8 || sub == 16) && d->brick_size % sub == 0 &&
+                     d->brick_size / sub <= kMaxSubPerEdge,
+                 "skip_block must be 0 or 2/4/8/16 dividing brick_size, at most 32 cells per brick edge");
 
-  sg_volume* v = new (std::nothrow) sg_volume();
-  if (!v) {
-    set_error("host allocation failed");
-    return SG_ERR_OOM;
-  }
-  v->desc = *d;
-  v->levels = d->lod_levels;
-  v->B = d->brick_size;
-  v->nch = d->channels;
-  v->T = d->timepoints;
-  v->esize = d->dtype == SG_U8 ? 1 : 2;
-  int64_t off = 0;
-  int64_t dims[3] = {d->dims[0], d->dims[1], d->dims[2]};
-  for (int L = 0; L < v->levels; ++L) {
-    LevelGeom& g = v->geom[L];
-    for (int a = 0; a < 3; ++a) {
-      g.dims[a] = dims[a];
-      g.nb[a] = (int32_t)((dims[a] + v->B - 1) / v->B);
-      dims[a] = (dims[a] + 1) / 2;
-    }
-    g.off = off;
-    int64_t n = (int64_t)g.nb[0] * g.nb[1] * g.nb[2];
-    off += n;
-    v->max_level_nodes = std::max(v->max_level_nodes, n);
-  }
-  v->nodes = off;
-  v->ncell = (int64_t)v->geom[0].nb[0] * v->geom[0].nb[1] * v->geom[0].nb[2];
-  if (v->ncell > (1 << 24) || v->nodes * v->T > ((int64_t)1 << 30)) {
-    delete v;
-    set_error("volume has too many blocks (use a larger brick_size)");
-    return SG_ERR_INVALID_ARG;
-  }
-  const int R = v->B + 2;
-  v->brick_bytes = ((size_t)R * R * R * v->esize + 255) / 256 * 256;
-  v->sub = sub;
-  v->sub_shift = sub == 2 ? 1 : (sub == 4 ? 2 : (sub == 8 ? 3 : 4));
-  v->nsub = v->B / sub;
-  const int ns3 = v->nsub * v->nsub * v->nsub;
-  v->sub_words = (ns3 + 63) / 64;
-  const int top = v->levels - 1;
-  const int64_t top_nodes = (int64_t)v->geom[top].nb[0] * v->geom[top].nb[1] * v->geom[top].nb[2];
-  if (d->device_pool_bytes == 0) {
-    v->pool_slots = v->nodes * v->T;
-  } else {
-    v->pooled = true;
-    v->pool_slots = (int64_t)(d->device_pool_bytes / (v->brick_bytes * v->nch));
-    if (v->pool_slots < top_nodes * v->T) {
-      delete v;
-      set_error("device_pool_bytes cannot hold the coarsest level of every time point");
-      return SG_ERR_INVALID_ARG;
-    }
-    v->pool_slots = std::min(v->pool_slots, v->nodes * v->T);
-  }
-  if (v->pool_slots >= (1 << 26)) {
-    delete v;
-    set_error("brick pool has too many slots");
-    return SG_ERR_INVALID_ARG;
-  }
-
-  cudaError_t e = cudaSuccess;
-  const int64_t tn = v->nodes * v->T;
-  if ((e = dalloc(&v->d_pool, (size_t)v->pool_slots * v->nch * v->brick_bytes)) != cudaSuccess ||
-      (e = dalloc(&v->d_slot, tn)) != cudaSuccess || (e = dalloc(&v->d_range, tn * v->nch * 2)) != cudaSuccess ||
-      (e = dalloc(&v->d_subrange, (size_t)v->pool_slots * ns3 * v->nch * 2)) != cudaSuccess ||
-      (e = dalloc(&v->d_subempty, (size_t)v->pool_slots * v->sub_words)) != cudaSuccess ||
-      (e = dalloc(&v->d_subdist, (size_t)v->pool_slots * 8 * ns3)) != cudaSuccess ||
-      (e = dalloc(&v->d_nodeflags, tn)) != cudaSuccess ||
-      (e = dalloc(&v->d_tf_raw, (size_t)v->nch * kMaxTF * 4)) != cudaSuccess ||
-      (e = dalloc(&v->d_palette, (size_t)v->nch * kMaxTF)) != cudaSuccess ||
-      (e = dalloc(&v->d_lut, (size_t)2 * v->nch * v->levels * kMaxTF)) != cudaSuccess ||
-      (e = dalloc(&v->d_err, 4)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&v->ev_select, cudaEventDisableTiming)) != cudaSuccess) {
-    free_volume(v);
-    set_error(std::string("device allocation: ") + cudaGetErrorString(e));
-    return SG_ERR_OOM;
-  }
-  // page table: resident volumes map (t, node) -> t * nodes + node
-  v->h_slot.assign(tn, -1);
-  if (!v->pooled)
-    for (int64_t i = 0; i < tn; ++i) v->h_slot[i] = (int32_t)i;
-  // value ranges start unknown (min > max), which is never transparent
-  if ((e = cudaMemcpy(v->d_slot, v->h_slot.data(), tn * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemset(v->d_range, 0, tn * v->nch * 2 * sizeof(uint32_t))) != cudaSuccess ||
-      (e = cudaMemset2D(v->d_range, 8, 0xff, 4, tn * v->nch)) != cudaSuccess ||
-      (e = cudaMemset(v->d_subempty, 0, (size_t)v->pool_slots * v->sub_words * 8)) != cudaSuccess ||
-      (e = cudaMemset(v->d_subdist, 0, (size_t)v->pool_slots * 8 * ns3)) != cudaSuccess ||
-      (e = cudaMemset(v->d_nodeflags, 0, tn)) != cudaSuccess ||
-      (e = cudaMemset(v->d_tf_raw, 0, (size_t)v->nch * kMaxTF * 16)) != cudaSuccess) {
-    free_volume(v);
-    return cuda_fail(e, "volume initialisation");
-  }
-  v->has_data.assign((size_t)v->T * v->nch, 0);
-  VolumeExtra* x = new VolumeExtra();
-  extras().push_back({v, x});
-  if (v->pooled) {
-    v->slot_owner.assign(v->pool_slots, -1);
-    v->slot_stamp.assign(v->pool_slots, 0);
-    v->slot_pinned.assign(v->pool_slots, 0);
-    for (int64_t s = v->pool_slots - 1; s >= 0; --s) x->free_slots.push_back(s);
-    if ((e = dalloc(&v->d_stamp, v->pool_slots)) != cudaSuccess ||
-        (e = cudaMemset(v->d_stamp, 0, v->pool_slots * sizeof(uint64_t))) != cudaSuccess) {
-      free_volume(v);
-      set_error(std::string("stamp table: ") + cudaGetErrorString(e));
+    sg_volume* v = new (std::nothrow) sg_volume();
+    if (!v) {
+      set_error("host allocation failed");
       return SG_ERR_OOM;
     }
-  }
-  *out = v;
-  return SG_OK;
+    v->desc = *d;
+    v->levels = d->lod_levels;
+    v->B = d->brick_size;
+    v->nch = d->channels;
+    v->T = d->timepoints;
+    v->esize = d->dtype == SG_U8 ? 1 : 2;
+    int64_t off = 0;
+    int64_t dims[3] = {d->dims[0], d->dims[1], d->dims[2]};
+    for (int L = 0; L < v->levels; ++L) {
+      LevelGeom& g = v->geom[L];
+      for (int a = 0; a < 3; ++a) {
+        g.dims[a] = dims[a];
+        g.nb[a] = (int32_t)((dims[a] + v->B - 1) / v->B);
+        dims[a] = (dims[a] + 1) / 2;
+      }
+      g.off = off;
+      int64_t n = (int64_t)g.nb[0] * g.nb[1] * g.nb[2];
+      off += n;
+      v->max_level_nodes = std::max(v->max_level_nodes, n);
+    }
+    v->nodes = off;
+    v->ncell = (int64_t)v->geom[0].nb[0] * v->geom[0].nb[1] * v->geom[0].nb[2];
+    if (v->ncell > (1 << 24) || v->nodes * v->T > ((int64_t)1 << 30)) {
+      delete v;
+      set_error("volume has too many blocks (use a larger brick_size)");
+      return SG_ERR_INVALID_ARG;
+    }
+    const int R = v->B + 2;
+    v->brick_bytes = ((size_t)R * R * R * v->esize + 255) / 256 * 256;
+    v->sub = sub;
+    v->sub_shift = sub == 2 ? 1 : (sub == 4 ? 2 : (sub == 8 ? 3 : 4));
+    v->nsub = v->B / sub;
+    const int ns3 = v->nsub * v->nsub * v->nsub;
+    v->sub_words = (ns3 + 63) / 64;
+    const int top = v->levels - 1;
+    const int64_t top_nodes = (int64_t)v->geom[top].nb[0] * v->geom[top].nb[1] * v->geom[top].nb[2];
+    if (d->device_pool_bytes == 0) {
+      v->pool_slots = v->nodes * v->T;
+    } else {
+      v->pooled = true;
+      v->pool_slots = (int64_t)(d->device_pool_bytes / (v->brick_bytes * v->nch));
+      if (v->pool_slots < top_nodes * v->T) {
+        delete v;
+        set_error("device_pool_bytes cannot hold the coarsest level of every time point");
+        return SG_ERR_INVALID_ARG;
+      }
+      v->pool_slots = std::min(v->pool_slots, v->nodes * v->T);
+    }
+    if (v->pool_slots >= (1 << 26)) {
+      delete v;
+      set_error("brick pool has too many slots");
+      return SG_ERR_INVALID_ARG;
+    }
+
+    cudaError_t e = cudaSuccess;
+    const int64_t tn = v->nodes * v->T;
+    if ((e = dalloc(&v->d_pool, (size_t)v->pool_slots * v->nch * v->brick_bytes)) != cudaSuccess ||
+        (e = dalloc(&v->d_slot, tn)) != cudaSuccess || (e = dalloc(&v->d_range, tn * v->nch * 2)) != cudaSuccess ||
+        (e = dalloc(&v->d_subrange, (size_t)v->pool_slots * ns3 * v->nch * 2)) != cudaSuccess ||
+        (e = dalloc(&v->d_subempty, (size_t)v->pool_slots * v->sub_words)) != cudaSuccess ||
+        (e = dalloc(&v->d_subdist, (size_t)v->pool_slots * 8 * ns3)) != cudaSuccess ||
+        (e = dalloc(&v->d_nodeflags, tn)) != cudaSuccess ||
+        (e = dalloc(&v->d_tf_raw, (size_t)v->nch * kMaxTF * 4)) != cudaSuccess ||
+        (e = dalloc(&v->d_palette, (size_t)v->nch * kMaxTF)) != cudaSuccess ||
+        (e = dalloc(&v->d_lut, (size_t)2 * v->nch * v->levels * kMaxTF)) != cudaSuccess ||
+        (e = dalloc(&v->d_err, 4)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&v->ev_select, cudaEventDisableTiming)) != cudaSuccess) {
+      free_volume(v);
+      set_error(std::string("device allocation: ") + cudaGetErrorString(e));
+      return SG_ERR_OOM;
+    }
+    // page table: resident volumes map (t, node) -> t * nodes + node
+    v->h_slot.assign(tn, -1);
+    if (!v->pooled)
+      for (int64_t i = 0; i < tn; ++i) v->h_slot[i] = (int32_t)i;
+    // value ranges start unknown (min > max), which is never transparent
+    if ((e = cudaMemcpy(v->d_slot, v->h_slot.data(), tn * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(v->d_range, 0, tn * v->nch * 2 * sizeof(uint32_t))) != cudaSuccess ||
+        (e = cudaMemset2D(v->d_range, 8, 0xff, 4, tn * v->nch)) != cudaSuccess ||
+        (e = cudaMemset(v->d_subempty, 0, (size_t)v->pool_slots * v->sub_words * 8)) != cudaSuccess ||
+        (e = cudaMemset(v->d_subdist, 0, (size_t)v->pool_slots * 8 * ns3)) != cudaSuccess ||
+        (e = cudaMemset(v->d_nodeflags, 0, tn)) != cudaSuccess ||
+        (e = cudaMemset(v->d_tf_raw, 0, (size_t)v->nch * kMaxTF * 16)) != cudaSuccess) {
+      free_volume(v);
+      return cuda_fail(e, "volume initialisation");
+    }
+    v->has_data.assign((size_t)v->T * v->nch, 0);
+    VolumeExtra* x = new VolumeExtra();
+    extras().push_back({v, x});
+    if (v->pooled) {
+      v->slot_owner.assign(v->pool_slots, -1);
+      v->slot_stamp.assign(v->pool_slots, 0);
+      v->slot_pinned.assign(v->pool_slots, 0);
+      for (int64_t s = v->pool_slots - 1; s >= 0; --s) x->free_slots.push_back(s);
+      if ((e = dalloc(&v->d_stamp, v->pool_slots)) != cudaSuccess ||
+          (e = cudaMemset(v->d_stamp, 0, v->pool_slots * sizeof(uint64_t))) != cudaSuccess) {
+        free_volume(v);
+        set_error(std::string("stamp table: ") + cudaGetErrorString(e));
+        return SG_ERR_OOM;
+      }
+    }
+    *out = v;
+    return SG_OK;
+  });
 }
 
 sg_status sg_volume_destroy(sg_volume* v) {
@@ -505,71 +507,77 @@ sg_status sg_upload_volume_device(sg_volume* v, int t, int c, const void* dev_le
 // a later line for a key replaces an earlier one.
 
 sg_status sg_render_config_store(const char* path, const char* key, const sg_render_config* cfg) {
-  SG_CHECK_ARG(path && key && cfg, "path, key and cfg must not be NULL");
-  SG_CHECK_ARG(key[0] && !strpbrk(key, "\t\n") && strlen(key) < 1024, "key: 1..1023 characters, no tab or newline");
-  SG_CHECK_ARG(render_config_supported(cfg), "unsupported render configuration");
-  FILE* f = fopen(path, "a");
-  if (!f) {
-    set_error(std::string("sg_render_config_store: cannot open ") + path);
-    return SG_ERR_IO;
-  }
-  const int n = fprintf(f, "%s\t%d %d %d %d\n", key, cfg->persistent, cfg->tile_w, cfg->tile_h, cfg->rays_per_thread);
-  if (fclose(f) != 0 || n < 0) {
-    set_error(std::string("sg_render_config_store: write failed: ") + path);
-    return SG_ERR_IO;
-  }
-  return SG_OK;
+  return sg::guarded("sg_render_config_store", [&]() -> sg_status {
+    SG_CHECK_ARG(path && key && cfg, "path, key and cfg must not be NULL");
+    SG_CHECK_ARG(key[0] && !strpbrk(key, "\t\n") && strlen(key) < 1024, "key: 1..1023 characters, no tab or newline");
+    SG_CHECK_ARG(render_config_supported(cfg), "unsupported render configuration");
+    FILE* f = fopen(path, "a");
+    if (!f) {
+      set_error(std::string("sg_render_config_store: cannot open ") + path);
+      return SG_ERR_IO;
+    }
+    const int n = fprintf(f, "%s\t%d %d %d %d\n", key, cfg->persistent, cfg->tile_w, cfg->tile_h, cfg->rays_per_thread);
+    if (fclose(f) != 0 || n < 0) {
+      set_error(std::string("sg_render_config_store: write failed: ") + path);
+      return SG_ERR_IO;
+    }
+    return SG_OK;
+  });
 }
 
 sg_status sg_render_config_lookup(const char* path, const char* key, sg_render_config* cfg, int* found) {
-  SG_CHECK_ARG(path && key && cfg && found, "path, key, cfg and found must not be NULL");
-  *found = 0;
-  FILE* f = fopen(path, "r");
-  if (!f) return SG_OK;  // no cache yet
-  char line[1200];
-  while (fgets(line, sizeof line, f)) {
-    char* tab = strchr(line, '\t');
-    if (!tab) continue;
-    *tab = 0;
-    if (strcmp(line, key) != 0) continue;
-    sg_render_config c;
-    memset(&c, 0, sizeof c);
-    if (sscanf(tab + 1, "%d %d %d %d", &c.persistent, &c.tile_w, &c.tile_h, &c.rays_per_thread) == 4 &&
-        render_config_supported(&c)) {
-      *cfg = c;
-      *found = 1;
+  return sg::guarded("sg_render_config_lookup", [&]() -> sg_status {
+    SG_CHECK_ARG(path && key && cfg && found, "path, key, cfg and found must not be NULL");
+    *found = 0;
+    FILE* f = fopen(path, "r");
+    if (!f) return SG_OK;  // no cache yet
+    char line[1200];
+    while (fgets(line, sizeof line, f)) {
+      char* tab = strchr(line, '\t');
+      if (!tab) continue;
+      *tab = 0;
+      if (strcmp(line, key) != 0) continue;
+      sg_render_config c;
+      memset(&c, 0, sizeof c);
+      if (sscanf(tab + 1, "%d %d %d %d", &c.persistent, &c.tile_w, &c.tile_h, &c.rays_per_thread) == 4 &&
+          render_config_supported(&c)) {
+        *cfg = c;
+        *found = 1;
+      }
     }
-  }
-  fclose(f);
-  return SG_OK;
+    fclose(f);
+    return SG_OK;
+  });
 }
 
 sg_status sg_set_brick_ranges(sg_volume* v, int t, int c, int level, int n, const int32_t* xyz,
                               const uint32_t* minmax, void* stream) {
-  SG_CHECK_ARG(v && xyz && minmax && n >= 1, "volume/brick_xyz/minmax NULL or n < 1");
-  SG_CHECK_ARG(t >= 0 && t < v->T && c >= 0 && c < v->nch && level >= 0 && level < v->levels,
-               "t, c or level out of range");
-  const LevelGeom& g = v->geom[level];
-  cudaStream_t s = (cudaStream_t)stream;
-  // host-side scatter into a copy of the level's range table, one upload
-  const int64_t nlev = (int64_t)g.nb[0] * g.nb[1] * g.nb[2];
-  std::vector<uint32_t> tab((size_t)nlev * v->nch * 2);
-  uint32_t* dst = v->d_range + ((int64_t)t * v->nodes + g.off) * v->nch * 2;
-  SG_CUDA(cudaMemcpyAsync(tab.data(), dst, tab.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "ranges");
-  SG_CUDA(cudaStreamSynchronize(s), "ranges");
-  for (int i = 0; i < n; ++i) {
-    SG_CHECK_ARG(xyz[3 * i] >= 0 && xyz[3 * i] < g.nb[0] && xyz[3 * i + 1] >= 0 && xyz[3 * i + 1] < g.nb[1] &&
-                     xyz[3 * i + 2] >= 0 && xyz[3 * i + 2] < g.nb[2],
-                 "brick coordinates out of range");
-    SG_CHECK_ARG(minmax[2 * i] <= minmax[2 * i + 1], "range with min > max");
-    int64_t b = ((int64_t)xyz[3 * i + 2] * g.nb[1] + xyz[3 * i + 1]) * g.nb[0] + xyz[3 * i];
-    tab[(b * v->nch + c) * 2] = minmax[2 * i];
-    tab[(b * v->nch + c) * 2 + 1] = minmax[2 * i + 1];
-  }
-  SG_CUDA(cudaMemcpyAsync(dst, tab.data(), tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s), "ranges");
-  SG_CUDA(cudaStreamSynchronize(s), "ranges");
-  ++v->tf_version;
-  return refresh_flags(v, s);
+  return sg::guarded("sg_set_brick_ranges", [&]() -> sg_status {
+    SG_CHECK_ARG(v && xyz && minmax && n >= 1, "volume/brick_xyz/minmax NULL or n < 1");
+    SG_CHECK_ARG(t >= 0 && t < v->T && c >= 0 && c < v->nch && level >= 0 && level < v->levels,
+                 "t, c or level out of range");
+    const LevelGeom& g = v->geom[level];
+    cudaStream_t s = (cudaStream_t)stream;
+    // host-side scatter into a copy of the level's range table, one upload
+    const int64_t nlev = (int64_t)g.nb[0] * g.nb[1] * g.nb[2];
+    std::vector<uint32_t> tab((size_t)nlev * v->nch * 2);
+    uint32_t* dst = v->d_range + ((int64_t)t * v->nodes + g.off) * v->nch * 2;
+    SG_CUDA(cudaMemcpyAsync(tab.data(), dst, tab.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "ranges");
+    SG_CUDA(cudaStreamSynchronize(s), "ranges");
+    for (int i = 0; i < n; ++i) {
+      SG_CHECK_ARG(xyz[3 * i] >= 0 && xyz[3 * i] < g.nb[0] && xyz[3 * i + 1] >= 0 && xyz[3 * i + 1] < g.nb[1] &&
+                       xyz[3 * i + 2] >= 0 && xyz[3 * i + 2] < g.nb[2],
+                   "brick coordinates out of range");
+      SG_CHECK_ARG(minmax[2 * i] <= minmax[2 * i + 1], "range with min > max");
+      int64_t b = ((int64_t)xyz[3 * i + 2] * g.nb[1] + xyz[3 * i + 1]) * g.nb[0] + xyz[3 * i];
+      tab[(b * v->nch + c) * 2] = minmax[2 * i];
+      tab[(b * v->nch + c) * 2 + 1] = minmax[2 * i + 1];
+    }
+    SG_CUDA(cudaMemcpyAsync(dst, tab.data(), tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s), "ranges");
+    SG_CUDA(cudaStreamSynchronize(s), "ranges");
+    ++v->tf_version;
+    return refresh_flags(v, s);
+  });
 }
 
 sg_status sg_set_transfer_function(sg_volume* v, int c, const float* rgba, int n, float lo, float hi, float ref_step,
@@ -705,37 +713,39 @@ sg_status sg_select_lod_batch(sg_volume* v, const sg_pose* poses, int n, void* s
 
 sg_status sg_read_selection(sg_volume* v, int slot, int32_t* cell_node, int64_t ncell, uint8_t* node_state,
                             int64_t nnode, int32_t* req, int32_t req_cap, int32_t* nreq, void* stream) {
-  SG_CHECK_ARG(v && slot >= 0 && slot < kMaxSlots, "volume NULL or slot out of range");
-  const SelSlot& sl = v->sel[slot];
-  if (!sl.valid) {
-    set_error("sg_read_selection: slot was never selected");
-    return SG_ERR_STATE;
-  }
-  cudaStream_t s = (cudaStream_t)stream;
-  SG_CHECK_ARG(!cell_node || ncell >= v->ncell, "cell_node buffer too small");
-  SG_CHECK_ARG(!node_state || nnode >= v->nodes, "node_state buffer too small");
-  uint32_t c[8];
-  // the selection may have been launched on another stream
-  SG_CUDA(cudaStreamWaitEvent(s, v->ev_select, 0), "read selection");
-  SG_CUDA(cudaMemcpyAsync(c, sl.d_counters, sizeof c, cudaMemcpyDeviceToHost, s), "read selection");
-  if (cell_node)
-    SG_CUDA(cudaMemcpyAsync(cell_node, sl.d_cell_node, v->ncell * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
-            "read selection");
-  if (node_state)
-    SG_CUDA(cudaMemcpyAsync(node_state, sl.d_state, v->nodes, cudaMemcpyDeviceToHost, s), "read selection");
-  SG_CUDA(cudaStreamSynchronize(s), "read selection");
-  if (nreq) *nreq = (int32_t)c[0];
-  if (req && req_cap > 0) {
-    std::vector<int32_t> r(c[0]);
-    if (c[0]) {
-      SG_CUDA(cudaMemcpyAsync(r.data(), sl.d_req, c[0] * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
-              "read requests");
-      SG_CUDA(cudaStreamSynchronize(s), "read requests");
+  return sg::guarded("sg_read_selection", [&]() -> sg_status {
+    SG_CHECK_ARG(v && slot >= 0 && slot < kMaxSlots, "volume NULL or slot out of range");
+    const SelSlot& sl = v->sel[slot];
+    if (!sl.valid) {
+      set_error("sg_read_selection: slot was never selected");
+      return SG_ERR_STATE;
     }
-    std::sort(r.begin(), r.end());
-    for (int32_t i = 0; i < req_cap && i < (int32_t)r.size(); ++i) req[i] = r[i];
-  }
-  return SG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    SG_CHECK_ARG(!cell_node || ncell >= v->ncell, "cell_node buffer too small");
+    SG_CHECK_ARG(!node_state || nnode >= v->nodes, "node_state buffer too small");
+    uint32_t c[8];
+    // the selection may have been launched on another stream
+    SG_CUDA(cudaStreamWaitEvent(s, v->ev_select, 0), "read selection");
+    SG_CUDA(cudaMemcpyAsync(c, sl.d_counters, sizeof c, cudaMemcpyDeviceToHost, s), "read selection");
+    if (cell_node)
+      SG_CUDA(cudaMemcpyAsync(cell_node, sl.d_cell_node, v->ncell * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+              "read selection");
+    if (node_state)
+      SG_CUDA(cudaMemcpyAsync(node_state, sl.d_state, v->nodes, cudaMemcpyDeviceToHost, s), "read selection");
+    SG_CUDA(cudaStreamSynchronize(s), "read selection");
+    if (nreq) *nreq = (int32_t)c[0];
+    if (req && req_cap > 0) {
+      std::vector<int32_t> r(c[0]);
+      if (c[0]) {
+        SG_CUDA(cudaMemcpyAsync(r.data(), sl.d_req, c[0] * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+                "read requests");
+        SG_CUDA(cudaStreamSynchronize(s), "read requests");
+      }
+      std::sort(r.begin(), r.end());
+      for (int32_t i = 0; i < req_cap && i < (int32_t)r.size(); ++i) req[i] = r[i];
+    }
+    return SG_OK;
+  });
 }
 
 sg_status sg_read_ranges(sg_volume* v, int t, uint32_t* minmax, int64_t nnode) {
@@ -931,87 +941,93 @@ sg_status sg_get_render_config(sg_volume* v, sg_render_config* cfg) {
 
 sg_status sg_autotune_render(sg_volume* v, const sg_pose* poses, int n, const sg_render_params* prm, float** outs,
                              int reps, sg_render_config* best, float* best_ms, void* stream) {
-  SG_CHECK_ARG(v && reps >= 1 && reps <= 1000, "volume NULL or reps not in 1..1000");
-  cudaStream_t s = (cudaStream_t)stream;
-  sg_render_config cand[32];
-  int nc = render_config_candidates(cand, 32);
-  cudaEvent_t e0, e1;
-  SG_CUDA(cudaEventCreate(&e0), "autotune events");
-  SG_CUDA(cudaEventCreate(&e1), "autotune events");
-  const sg_render_config keep = v->render_cfg;
-  float best_t = 1e30f;
-  sg_render_config best_c = keep;
-  sg_status st = SG_OK;
-  for (int i = 0; i < nc && st == SG_OK; ++i) {
-    v->render_cfg = cand[i];
-    st = sg_render_batch(v, poses, n, prm, outs, stream);  // warm-up, also validates the arguments
-    if (st != SG_OK) break;
-    cudaEventRecord(e0, s);
-    for (int r = 0; r < reps && st == SG_OK; ++r) st = sg_render_batch(v, poses, n, prm, outs, stream);
-    cudaEventRecord(e1, s);
-    cudaError_t ce = cudaEventSynchronize(e1);
-    if (ce != cudaSuccess) {
-      st = cuda_fail(ce, "autotune");
-      break;
+  return sg::guarded("sg_autotune_render", [&]() -> sg_status {
+    SG_CHECK_ARG(v && reps >= 1 && reps <= 1000, "volume NULL or reps not in 1..1000");
+    cudaStream_t s = (cudaStream_t)stream;
+    sg_render_config cand[32];
+    int nc = render_config_candidates(cand, 32);
+    cudaEvent_t e0, e1;
+    SG_CUDA(cudaEventCreate(&e0), "autotune events");
+    SG_CUDA(cudaEventCreate(&e1), "autotune events");
+    const sg_render_config keep = v->render_cfg;
+    float best_t = 1e30f;
+    sg_render_config best_c = keep;
+    sg_status st = SG_OK;
+    for (int i = 0; i < nc && st == SG_OK; ++i) {
+      v->render_cfg = cand[i];
+      st = sg_render_batch(v, poses, n, prm, outs, stream);  // warm-up, also validates the arguments
+      if (st != SG_OK) break;
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps && st == SG_OK; ++r) st = sg_render_batch(v, poses, n, prm, outs, stream);
+      cudaEventRecord(e1, s);
+      cudaError_t ce = cudaEventSynchronize(e1);
+      if (ce != cudaSuccess) {
+        st = cuda_fail(ce, "autotune");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= reps;
+      if (ms < best_t) {
+        best_t = ms;
+        best_c = cand[i];
+      }
     }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    ms /= reps;
-    if (ms < best_t) {
-      best_t = ms;
-      best_c = cand[i];
-    }
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  v->render_cfg = st == SG_OK ? best_c : keep;
-  if (st != SG_OK) return st;
-  if (best) *best = best_c;
-  if (best_ms) *best_ms = best_t;
-  return SG_OK;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    v->render_cfg = st == SG_OK ? best_c : keep;
+    if (st != SG_OK) return st;
+    if (best) *best = best_c;
+    if (best_ms) *best_ms = best_t;
+    return SG_OK;
+  });
 }
 
 sg_status sg_upload_bricks(sg_volume* v, int t, int c, int level, int n, const int32_t* xyz, const void* host,
                            void* stream) {
-  SG_CHECK_ARG(v && xyz && host && n >= 1, "volume/brick_xyz/host NULL or n < 1");
-  SG_CHECK_ARG(t >= 0 && t < v->T && c >= 0 && c < v->nch, "t or c out of range");
-  SG_CHECK_ARG(level >= 0 && level < v->levels, "level out of range");
-  const LevelGeom& g = v->geom[level];
-  for (int i = 0; i < n; ++i)
-    SG_CHECK_ARG(xyz[3 * i] >= 0 && xyz[3 * i] < g.nb[0] && xyz[3 * i + 1] >= 0 && xyz[3 * i + 1] < g.nb[1] &&
-                     xyz[3 * i + 2] >= 0 && xyz[3 * i + 2] < g.nb[2],
-                 "brick coordinates out of range");
-  const size_t raw = (size_t)(v->B + 2) * (v->B + 2) * (v->B + 2) * v->esize;
-  std::vector<int32_t> nodes(n);
-  std::vector<const void*> ptrs(n);
-  for (int i = 0; i < n; ++i) {
-    nodes[i] = (int32_t)(g.off + ((int64_t)xyz[3 * i + 2] * g.nb[1] + xyz[3 * i + 1]) * g.nb[0] + xyz[3 * i]);
-    ptrs[i] = static_cast<const uint8_t*>(host) + raw * i;
-  }
-  int done = 0;
-  sg_status st = upload_list(v, t, c, n, nodes.data(), ptrs.data(), &done, (cudaStream_t)stream);
-  if (st == SG_OK && done < n) {
-    set_error("sg_upload_bricks: brick cache full of bricks used by the current frame");
-    return SG_ERR_OOM;
-  }
-  return st;
+  return sg::guarded("sg_upload_bricks", [&]() -> sg_status {
+    SG_CHECK_ARG(v && xyz && host && n >= 1, "volume/brick_xyz/host NULL or n < 1");
+    SG_CHECK_ARG(t >= 0 && t < v->T && c >= 0 && c < v->nch, "t or c out of range");
+    SG_CHECK_ARG(level >= 0 && level < v->levels, "level out of range");
+    const LevelGeom& g = v->geom[level];
+    for (int i = 0; i < n; ++i)
+      SG_CHECK_ARG(xyz[3 * i] >= 0 && xyz[3 * i] < g.nb[0] && xyz[3 * i + 1] >= 0 && xyz[3 * i + 1] < g.nb[1] &&
+                       xyz[3 * i + 2] >= 0 && xyz[3 * i + 2] < g.nb[2],
+                   "brick coordinates out of range");
+    const size_t raw = (size_t)(v->B + 2) * (v->B + 2) * (v->B + 2) * v->esize;
+    std::vector<int32_t> nodes(n);
+    std::vector<const void*> ptrs(n);
+    for (int i = 0; i < n; ++i) {
+      nodes[i] = (int32_t)(g.off + ((int64_t)xyz[3 * i + 2] * g.nb[1] + xyz[3 * i + 1]) * g.nb[0] + xyz[3 * i]);
+      ptrs[i] = static_cast<const uint8_t*>(host) + raw * i;
+    }
+    int done = 0;
+    sg_status st = upload_list(v, t, c, n, nodes.data(), ptrs.data(), &done, (cudaStream_t)stream);
+    if (st == SG_OK && done < n) {
+      set_error("sg_upload_bricks: brick cache full of bricks used by the current frame");
+      return SG_ERR_OOM;
+    }
+    return st;
+  });
 }
 
 sg_status sg_upload_brick_list(sg_volume* v, int t, int c, int n, const int32_t* nodes, const void* const* host,
                                int32_t* n_done, void* stream) {
-  sg::NvtxRange nvtx_range("sg_upload_brick_list");
-  SG_CHECK_ARG(v && n_done && n >= 0 && (n == 0 || (nodes && host)), "volume/nodes/host/n_done NULL or n < 0");
-  SG_CHECK_ARG(t >= 0 && t < v->T && c >= 0 && c < v->nch, "t or c out of range");
-  *n_done = 0;
-  for (int i = 0; i < n; ++i) {
-    SG_CHECK_ARG(nodes[i] >= 0 && nodes[i] < v->nodes, "node id out of range");
-    SG_CHECK_ARG(host[i], "host pointer NULL");
-  }
-  if (n == 0) return SG_OK;
-  int done = 0;
-  sg_status st = upload_list(v, t, c, n, nodes, host, &done, (cudaStream_t)stream);
-  *n_done = done;
-  return st;
+  return sg::guarded("sg_upload_brick_list", [&]() -> sg_status {
+    sg::NvtxRange nvtx_range("sg_upload_brick_list");
+    SG_CHECK_ARG(v && n_done && n >= 0 && (n == 0 || (nodes && host)), "volume/nodes/host/n_done NULL or n < 0");
+    SG_CHECK_ARG(t >= 0 && t < v->T && c >= 0 && c < v->nch, "t or c out of range");
+    *n_done = 0;
+    for (int i = 0; i < n; ++i) {
+      SG_CHECK_ARG(nodes[i] >= 0 && nodes[i] < v->nodes, "node id out of range");
+      SG_CHECK_ARG(host[i], "host pointer NULL");
+    }
+    if (n == 0) return SG_OK;
+    int done = 0;
+    sg_status st = upload_list(v, t, c, n, nodes, host, &done, (cudaStream_t)stream);
+    *n_done = done;
+    return st;
+  });
 }
 
 }  // extern "C"

@@ -150,160 +150,168 @@ uint64_t scan_chunks(sg_container* k, uint64_t file_size) {
 extern "C" {
 
 sg_status sg_container_create(const char* path, const sg_volume_desc* desc, sg_container** out) {
-  if (!path || !desc || !out) {
-    set_error("path, desc and out must not be NULL");
-    return SG_ERR_INVALID_ARG;
-  }
-  *out = nullptr;
-  if (!check_desc(*desc)) {
-    set_error("invalid volume layout");
-    return SG_ERR_INVALID_ARG;
-  }
-  sg_container* k = new (std::nothrow) sg_container();
-  if (!k) {
-    set_error("host allocation failed");
-    return SG_ERR_OOM;
-  }
-  k->path = path;
-  k->desc = *desc;
-  k->g = geometry_of(*desc);
-  k->f = fopen(path, "w+b");
-  if (!k->f) {
-    delete k;
-    return fail_io(std::string("cannot create ") + path);
-  }
-  FileHeader h{kFileMagic, kVersion, *desc};
-  if (fwrite(&h, sizeof h, 1, k->f) != 1 || fflush(k->f) != 0) {
-    fclose(k->f);
-    delete k;
-    return fail_io("cannot write the container header");
-  }
-  k->writable = true;
-  k->end = sizeof h;
-  *out = k;
-  return SG_OK;
+  return sg::guarded("sg_container_create", [&]() -> sg_status {
+    if (!path || !desc || !out) {
+      set_error("path, desc and out must not be NULL");
+      return SG_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (!check_desc(*desc)) {
+      set_error("invalid volume layout");
+      return SG_ERR_INVALID_ARG;
+    }
+    sg_container* k = new (std::nothrow) sg_container();
+    if (!k) {
+      set_error("host allocation failed");
+      return SG_ERR_OOM;
+    }
+    k->path = path;
+    k->desc = *desc;
+    k->g = geometry_of(*desc);
+    k->f = fopen(path, "w+b");
+    if (!k->f) {
+      delete k;
+      return fail_io(std::string("cannot create ") + path);
+    }
+    FileHeader h{kFileMagic, kVersion, *desc};
+    if (fwrite(&h, sizeof h, 1, k->f) != 1 || fflush(k->f) != 0) {
+      fclose(k->f);
+      delete k;
+      return fail_io("cannot write the container header");
+    }
+    k->writable = true;
+    k->end = sizeof h;
+    *out = k;
+    return SG_OK;
+  });
 }
 
 sg_status sg_container_open(const char* path, sg_container** out) {
-  if (!path || !out) {
-    set_error("path and out must not be NULL");
-    return SG_ERR_INVALID_ARG;
-  }
-  *out = nullptr;
-  sg_container* k = new (std::nothrow) sg_container();
-  if (!k) {
-    set_error("host allocation failed");
-    return SG_ERR_OOM;
-  }
-  k->path = path;
-  k->f = fopen(path, "r+b");
-  if (!k->f) k->f = fopen(path, "rb");
-  if (!k->f) {
-    delete k;
-    return fail_io(std::string("cannot open ") + path);
-  }
-  FileHeader h;
-  if (!read_at(k->f, 0, &h, sizeof h) || h.magic != kFileMagic || h.version != kVersion || !check_desc(h.desc)) {
-    fclose(k->f);
-    delete k;
-    return fail_io("not a brick container (bad header)");
-  }
-  k->desc = h.desc;
-  k->g = geometry_of(h.desc);
-  fseeko(k->f, 0, SEEK_END);
-  const uint64_t size = (uint64_t)ftello(k->f);
-  Footer ft;
-  bool indexed = false;
-  if (size >= sizeof(FileHeader) + sizeof ft && read_at(k->f, size - sizeof ft, &ft, sizeof ft) &&
-      ft.magic == kIndexMagic && ft.version == kVersion && ft.index_offset + ft.chunks * 16 + sizeof ft == size) {
-    std::vector<int64_t> rec(2 * ft.chunks);
-    if (ft.chunks == 0 || read_at(k->f, ft.index_offset, rec.data(), rec.size() * sizeof(int64_t))) {
-      for (uint64_t i = 0; i < ft.chunks; ++i) k->index[rec[2 * i]] = (uint64_t)rec[2 * i + 1];
-      for (auto& e : k->index) {
-        ChunkHeader ch;
-        if (read_at(k->f, e.second, &ch, sizeof ch)) {
-          k->raw_total += ch.raw_bytes;
-          k->comp_total += ch.comp_bytes;
-        }
-      }
-      k->complete = true;
-      k->end = ft.index_offset;
-      indexed = true;
+  return sg::guarded("sg_container_open", [&]() -> sg_status {
+    if (!path || !out) {
+      set_error("path and out must not be NULL");
+      return SG_ERR_INVALID_ARG;
     }
-  }
-  if (!indexed) {
-    // an interrupted conversion: keep every complete chunk, cut off a torn
-    // one, resume appending after them
-    k->end = scan_chunks(k, size);
-    fflush(k->f);
-    if (k->end < size && ftruncate(fileno(k->f), (off_t)k->end) != 0) {
+    *out = nullptr;
+    sg_container* k = new (std::nothrow) sg_container();
+    if (!k) {
+      set_error("host allocation failed");
+      return SG_ERR_OOM;
+    }
+    k->path = path;
+    k->f = fopen(path, "r+b");
+    if (!k->f) k->f = fopen(path, "rb");
+    if (!k->f) {
+      delete k;
+      return fail_io(std::string("cannot open ") + path);
+    }
+    FileHeader h;
+    if (!read_at(k->f, 0, &h, sizeof h) || h.magic != kFileMagic || h.version != kVersion || !check_desc(h.desc)) {
       fclose(k->f);
       delete k;
-      return fail_io("cannot cut the torn chunk off the container");
+      return fail_io("not a brick container (bad header)");
     }
-    k->writable = true;
-  }
-  *out = k;
-  return SG_OK;
+    k->desc = h.desc;
+    k->g = geometry_of(h.desc);
+    fseeko(k->f, 0, SEEK_END);
+    const uint64_t size = (uint64_t)ftello(k->f);
+    Footer ft;
+    bool indexed = false;
+    if (size >= sizeof(FileHeader) + sizeof ft && read_at(k->f, size - sizeof ft, &ft, sizeof ft) &&
+        ft.magic == kIndexMagic && ft.version == kVersion && ft.index_offset + ft.chunks * 16 + sizeof ft == size) {
+      std::vector<int64_t> rec(2 * ft.chunks);
+      if (ft.chunks == 0 || read_at(k->f, ft.index_offset, rec.data(), rec.size() * sizeof(int64_t))) {
+        for (uint64_t i = 0; i < ft.chunks; ++i) k->index[rec[2 * i]] = (uint64_t)rec[2 * i + 1];
+        for (auto& e : k->index) {
+          ChunkHeader ch;
+          if (read_at(k->f, e.second, &ch, sizeof ch)) {
+            k->raw_total += ch.raw_bytes;
+            k->comp_total += ch.comp_bytes;
+          }
+        }
+        k->complete = true;
+        k->end = ft.index_offset;
+        indexed = true;
+      }
+    }
+    if (!indexed) {
+      // an interrupted conversion: keep every complete chunk, cut off a torn
+      // one, resume appending after them
+      k->end = scan_chunks(k, size);
+      fflush(k->f);
+      if (k->end < size && ftruncate(fileno(k->f), (off_t)k->end) != 0) {
+        fclose(k->f);
+        delete k;
+        return fail_io("cannot cut the torn chunk off the container");
+      }
+      k->writable = true;
+    }
+    *out = k;
+    return SG_OK;
+  });
 }
 
 sg_status sg_container_append(sg_container* k, int t, int c, int level, int bx, int by, int bz, const void* brick,
                               uint32_t vmin, uint32_t vmax) {
-  if (!k || !brick) {
-    set_error("container or brick NULL");
-    return SG_ERR_INVALID_ARG;
-  }
-  if (!k->writable || k->complete) {
-    set_error("sg_container_append: the container is finished (read only)");
-    return SG_ERR_STATE;
-  }
-  if (t < 0 || t >= k->g.T || c < 0 || c >= k->g.nch || level < 0 || level >= k->g.levels || bx < 0 || by < 0 ||
-      bz < 0 || bx >= k->g.nb[level][0] || by >= k->g.nb[level][1] || bz >= k->g.nb[level][2]) {
-    set_error("sg_container_append: brick coordinates out of range");
-    return SG_ERR_INVALID_ARG;
-  }
-  // compression runs outside the lock, so appends from several threads
-  // compress in parallel and only the write is serialised
-  std::vector<uint8_t> comp(lz4_bound(k->g.raw_bytes));
-  const size_t cs = lz4_compress(static_cast<const uint8_t*>(brick), k->g.raw_bytes, comp.data());
-  ChunkHeader h{kChunkMagic, t, c, level, bx, by, bz, (uint32_t)k->g.raw_bytes, (uint32_t)cs, vmin, vmax,
-                checksum(comp.data(), cs)};
-  std::lock_guard<std::mutex> lock(k->m);
-  if (k->complete) {
-    set_error("sg_container_append: the container is finished (read only)");
-    return SG_ERR_STATE;
-  }
-  if (fseeko(k->f, (off_t)k->end, SEEK_SET) != 0 || fwrite(&h, sizeof h, 1, k->f) != 1 ||
-      fwrite(comp.data(), 1, cs, k->f) != cs || fflush(k->f) != 0)
-    return fail_io("sg_container_append: write failed");
-  const int64_t node = k->g.off[level] + ((int64_t)bz * k->g.nb[level][1] + by) * k->g.nb[level][0] + bx;
-  k->index[k->key(t, c, node)] = k->end;
-  k->end += sizeof h + cs;
-  k->raw_total += k->g.raw_bytes;
-  k->comp_total += cs;
-  return SG_OK;
+  return sg::guarded("sg_container_append", [&]() -> sg_status {
+    if (!k || !brick) {
+      set_error("container or brick NULL");
+      return SG_ERR_INVALID_ARG;
+    }
+    if (!k->writable || k->complete) {
+      set_error("sg_container_append: the container is finished (read only)");
+      return SG_ERR_STATE;
+    }
+    if (t < 0 || t >= k->g.T || c < 0 || c >= k->g.nch || level < 0 || level >= k->g.levels || bx < 0 || by < 0 ||
+        bz < 0 || bx >= k->g.nb[level][0] || by >= k->g.nb[level][1] || bz >= k->g.nb[level][2]) {
+      set_error("sg_container_append: brick coordinates out of range");
+      return SG_ERR_INVALID_ARG;
+    }
+    // compression runs outside the lock, so appends from several threads
+    // compress in parallel and only the write is serialised
+    std::vector<uint8_t> comp(lz4_bound(k->g.raw_bytes));
+    const size_t cs = lz4_compress(static_cast<const uint8_t*>(brick), k->g.raw_bytes, comp.data());
+    ChunkHeader h{kChunkMagic, t, c, level, bx, by, bz, (uint32_t)k->g.raw_bytes, (uint32_t)cs, vmin, vmax,
+                  checksum(comp.data(), cs)};
+    std::lock_guard<std::mutex> lock(k->m);
+    if (k->complete) {
+      set_error("sg_container_append: the container is finished (read only)");
+      return SG_ERR_STATE;
+    }
+    if (fseeko(k->f, (off_t)k->end, SEEK_SET) != 0 || fwrite(&h, sizeof h, 1, k->f) != 1 ||
+        fwrite(comp.data(), 1, cs, k->f) != cs || fflush(k->f) != 0)
+      return fail_io("sg_container_append: write failed");
+    const int64_t node = k->g.off[level] + ((int64_t)bz * k->g.nb[level][1] + by) * k->g.nb[level][0] + bx;
+    k->index[k->key(t, c, node)] = k->end;
+    k->end += sizeof h + cs;
+    k->raw_total += k->g.raw_bytes;
+    k->comp_total += cs;
+    return SG_OK;
+  });
 }
 
 sg_status sg_container_finish(sg_container* k) {
-  if (!k) {
-    set_error("container NULL");
-    return SG_ERR_INVALID_ARG;
-  }
-  std::lock_guard<std::mutex> lock(k->m);
-  if (k->complete) return SG_OK;
-  std::vector<int64_t> rec;
-  rec.reserve(2 * k->index.size());
-  for (auto& e : k->index) {
-    rec.push_back(e.first);
-    rec.push_back((int64_t)e.second);
-  }
-  Footer ft{kIndexMagic, kVersion, k->end, (uint64_t)k->index.size()};
-  if (fseeko(k->f, (off_t)k->end, SEEK_SET) != 0 ||
-      (!rec.empty() && fwrite(rec.data(), sizeof(int64_t), rec.size(), k->f) != rec.size()) ||
-      fwrite(&ft, sizeof ft, 1, k->f) != 1 || fflush(k->f) != 0)
-    return fail_io("sg_container_finish: write failed");
-  k->complete = true;
-  return SG_OK;
+  return sg::guarded("sg_container_finish", [&]() -> sg_status {
+    if (!k) {
+      set_error("container NULL");
+      return SG_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lock(k->m);
+    if (k->complete) return SG_OK;
+    std::vector<int64_t> rec;
+    rec.reserve(2 * k->index.size());
+    for (auto& e : k->index) {
+      rec.push_back(e.first);
+      rec.push_back((int64_t)e.second);
+    }
+    Footer ft{kIndexMagic, kVersion, k->end, (uint64_t)k->index.size()};
+    if (fseeko(k->f, (off_t)k->end, SEEK_SET) != 0 ||
+        (!rec.empty() && fwrite(rec.data(), sizeof(int64_t), rec.size(), k->f) != rec.size()) ||
+        fwrite(&ft, sizeof ft, 1, k->f) != 1 || fflush(k->f) != 0)
+      return fail_io("sg_container_finish: write failed");
+    k->complete = true;
+    return SG_OK;
+  });
 }
 
 sg_status sg_container_get_info(sg_container* k, sg_container_info* info) {
@@ -322,20 +330,22 @@ sg_status sg_container_get_info(sg_container* k, sg_container_info* info) {
 }
 
 sg_status sg_container_read(sg_container* k, int t, int c, int64_t node, void* out, uint32_t* minmax) {
-  if (!k || !out) {
-    set_error("container or output NULL");
-    return SG_ERR_INVALID_ARG;
-  }
-  if (t < 0 || t >= k->g.T || c < 0 || c >= k->g.nch || node < 0 || node >= k->g.nodes) {
-    set_error("sg_container_read: (t, c, node) out of range");
-    return SG_ERR_INVALID_ARG;
-  }
-  auto it = k->index.find(k->key(t, c, node));
-  if (it == k->index.end()) {
-    set_error("sg_container_read: no chunk for this brick");
-    return SG_ERR_NOT_RESIDENT;
-  }
-  return container_read_chunk(k, it->second, out, minmax, nullptr);
+  return sg::guarded("sg_container_read", [&]() -> sg_status {
+    if (!k || !out) {
+      set_error("container or output NULL");
+      return SG_ERR_INVALID_ARG;
+    }
+    if (t < 0 || t >= k->g.T || c < 0 || c >= k->g.nch || node < 0 || node >= k->g.nodes) {
+      set_error("sg_container_read: (t, c, node) out of range");
+      return SG_ERR_INVALID_ARG;
+    }
+    auto it = k->index.find(k->key(t, c, node));
+    if (it == k->index.end()) {
+      set_error("sg_container_read: no chunk for this brick");
+      return SG_ERR_NOT_RESIDENT;
+    }
+    return container_read_chunk(k, it->second, out, minmax, nullptr);
+  });
 }
 
 sg_status sg_container_close(sg_container* k) {

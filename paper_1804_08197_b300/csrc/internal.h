@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <exception>
 #include <string>
 #include <utility>
 #include <vector>
@@ -147,6 +148,21 @@ struct sg_volume {
 namespace sg {
 
 void set_error(const std::string& msg);
+
+// Runs an entry point's body; a C++ exception from host bookkeeping (a
+// container that could not grow, a thread that could not start) becomes
+// SG_ERR_OOM with a message, so that none crosses the C ABI.
+template <typename F>
+sg_status guarded(const char* name, F&& body) {
+  try {
+    return body();
+  } catch (const std::exception& e) {
+    set_error(std::string(name) + ": host resources exhausted (" + e.what() + ")");
+  } catch (...) {
+    set_error(std::string(name) + ": host resources exhausted");
+  }
+  return SG_ERR_OOM;
+}
 sg_status cuda_fail(cudaError_t e, const char* what);
 // the checks of a pose that do not involve its selection slot (time point,
 // image size, pixel error, projection)

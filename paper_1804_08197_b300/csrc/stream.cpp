@@ -58,47 +58,49 @@ struct sg_host_cache {
 extern "C" {
 
 sg_status sg_host_cache_create(sg_container* k, uint64_t bytes, int pinned, int threads, sg_host_cache** out) {
-  if (!k || !out) {
-    set_error("container and out must not be NULL");
-    return SG_ERR_INVALID_ARG;
-  }
-  *out = nullptr;
-  const size_t eb = container_brick_bytes(k);
-  if (bytes < eb || threads < 1 || threads > 256) {
-    set_error("host cache: at least one brick of bytes, 1..256 threads");
-    return SG_ERR_INVALID_ARG;
-  }
-  sg_host_cache* hc = new (std::nothrow) sg_host_cache();
-  if (!hc) {
-    set_error("host allocation failed");
-    return SG_ERR_OOM;
-  }
-  hc->k = k;
-  hc->entry_bytes = eb;
-  hc->entries = (int64_t)(bytes / eb);
-  hc->threads = threads;
-  const size_t total = (size_t)hc->entries * eb;
-  if (pinned) {
-    if (cudaHostAlloc(reinterpret_cast<void**>(&hc->arena), total, cudaHostAllocDefault) != cudaSuccess) {
-      delete hc;
-      set_error("host cache: page-locked allocation failed");
+  return sg::guarded("sg_host_cache_create", [&]() -> sg_status {
+    if (!k || !out) {
+      set_error("container and out must not be NULL");
+      return SG_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    const size_t eb = container_brick_bytes(k);
+    if (bytes < eb || threads < 1 || threads > 256) {
+      set_error("host cache: at least one brick of bytes, 1..256 threads");
+      return SG_ERR_INVALID_ARG;
+    }
+    sg_host_cache* hc = new (std::nothrow) sg_host_cache();
+    if (!hc) {
+      set_error("host allocation failed");
       return SG_ERR_OOM;
     }
-    hc->pinned = true;
-  } else {
-    hc->arena = static_cast<uint8_t*>(malloc(total));
-    if (!hc->arena) {
-      delete hc;
-      set_error("host cache: allocation failed");
-      return SG_ERR_OOM;
+    hc->k = k;
+    hc->entry_bytes = eb;
+    hc->entries = (int64_t)(bytes / eb);
+    hc->threads = threads;
+    const size_t total = (size_t)hc->entries * eb;
+    if (pinned) {
+      if (cudaHostAlloc(reinterpret_cast<void**>(&hc->arena), total, cudaHostAllocDefault) != cudaSuccess) {
+        delete hc;
+        set_error("host cache: page-locked allocation failed");
+        return SG_ERR_OOM;
+      }
+      hc->pinned = true;
+    } else {
+      hc->arena = static_cast<uint8_t*>(malloc(total));
+      if (!hc->arena) {
+        delete hc;
+        set_error("host cache: allocation failed");
+        return SG_ERR_OOM;
+      }
     }
-  }
-  hc->owner.assign(hc->entries, -1);
-  hc->stamp.assign(hc->entries, 0);
-  hc->loading.assign(hc->entries, 0);
-  for (int64_t i = hc->entries - 1; i >= 0; --i) hc->free_list.push_back(i);
-  *out = hc;
-  return SG_OK;
+    hc->owner.assign(hc->entries, -1);
+    hc->stamp.assign(hc->entries, 0);
+    hc->loading.assign(hc->entries, 0);
+    for (int64_t i = hc->entries - 1; i >= 0; --i) hc->free_list.push_back(i);
+    *out = hc;
+    return SG_OK;
+  });
 }
 
 sg_status sg_host_cache_destroy(sg_host_cache* hc) {
@@ -127,26 +129,28 @@ sg_status sg_host_cache_clear_failures(sg_host_cache* hc) {
 }
 
 sg_status sg_host_cache_fetch(sg_host_cache* hc, int t, int c, int64_t node, const void** brick, int* hit) {
-  if (!hc || !brick) {
-    set_error("cache or output NULL");
-    return SG_ERR_INVALID_ARG;
-  }
-  host_cache_drain(hc);
-  ++hc->frame;
-  std::vector<std::pair<int64_t, int64_t>> todo;  // (entry, chunk offset)
-  int64_t entry = -1;
-  sg_status st = host_cache_lookup(hc, t, c, node, &entry, hit, &todo);
-  if (st != SG_OK) return st;
-  if (!todo.empty()) {
-    st = container_read_chunk(hc->k, (uint64_t)todo[0].second, hc->arena + (size_t)entry * hc->entry_bytes, nullptr,
-                              nullptr);
-    if (st != SG_OK) {
-      host_cache_drop(hc, entry);
-      return st;
+  return sg::guarded("sg_host_cache_fetch", [&]() -> sg_status {
+    if (!hc || !brick) {
+      set_error("cache or output NULL");
+      return SG_ERR_INVALID_ARG;
     }
-  }
-  *brick = hc->arena + (size_t)entry * hc->entry_bytes;
-  return SG_OK;
+    host_cache_drain(hc);
+    ++hc->frame;
+    std::vector<std::pair<int64_t, int64_t>> todo;  // (entry, chunk offset)
+    int64_t entry = -1;
+    sg_status st = host_cache_lookup(hc, t, c, node, &entry, hit, &todo);
+    if (st != SG_OK) return st;
+    if (!todo.empty()) {
+      st = container_read_chunk(hc->k, (uint64_t)todo[0].second, hc->arena + (size_t)entry * hc->entry_bytes, nullptr,
+                                nullptr);
+      if (st != SG_OK) {
+        host_cache_drop(hc, entry);
+        return st;
+      }
+    }
+    *brick = hc->arena + (size_t)entry * hc->entry_bytes;
+    return SG_OK;
+  });
 }
 
 }  // extern "C"
@@ -549,48 +553,54 @@ extern "C" {
 
 sg_status sg_stream_requests(sg_volume* v, int slot, sg_host_cache* hc, uint64_t max_bytes, sg_stream_stats* stats,
                              void* stream) {
-  return stream_impl(v, slot, hc, max_bytes, stats, stream, false, "sg_stream_requests");
+  return sg::guarded("sg_stream_requests", [&]() -> sg_status {
+    return stream_impl(v, slot, hc, max_bytes, stats, stream, false, "sg_stream_requests");
+  });
 }
 
 sg_status sg_stream_requests_async(sg_volume* v, int slot, sg_host_cache* hc, uint64_t max_bytes,
                                    sg_stream_stats* stats, void* stream) {
-  return stream_impl(v, slot, hc, max_bytes, stats, stream, true, "sg_stream_requests_async");
+  return sg::guarded("sg_stream_requests_async", [&]() -> sg_status {
+    return stream_impl(v, slot, hc, max_bytes, stats, stream, true, "sg_stream_requests_async");
+  });
 }
 
 sg_status sg_host_cache_prefetch(sg_host_cache* hc, int t, int c, const int64_t* nodes, int32_t n, int32_t* queued) {
-  if (!hc || (n > 0 && !nodes) || n < 0) {
-    set_error("sg_host_cache_prefetch: cache or nodes NULL, or n < 0");
-    return SG_ERR_INVALID_ARG;
-  }
-  const sg_volume_desc& d = container_desc(hc->k);
-  if (t < 0 || t >= d.timepoints || c < 0 || c >= d.channels) {
-    set_error("sg_host_cache_prefetch: time point or channel out of range");
-    return SG_ERR_INVALID_ARG;
-  }
-  host_cache_collect(hc, false, nullptr, nullptr, nullptr);
-  ++hc->frame;
-  std::vector<std::pair<int64_t, int64_t>> todo;
-  sg_status st = SG_OK;
-  for (int32_t i = 0; i < n; ++i) {
-    if (nodes[i] < 0 || nodes[i] >= container_nodes(hc->k)) {
-      st = SG_ERR_INVALID_ARG;
-      set_error("sg_host_cache_prefetch: node id out of range");
-      break;
+  return sg::guarded("sg_host_cache_prefetch", [&]() -> sg_status {
+    if (!hc || (n > 0 && !nodes) || n < 0) {
+      set_error("sg_host_cache_prefetch: cache or nodes NULL, or n < 0");
+      return SG_ERR_INVALID_ARG;
     }
-    const int64_t key = ((int64_t)t * d.channels + c) * container_nodes(hc->k) + nodes[i];
-    if (hc->failed.count(key)) continue;
-    int64_t e = -1;
-    int hit = 0;
-    const sg_status s1 = host_cache_lookup(hc, t, c, nodes[i], &e, &hit, &todo);
-    if (s1 == SG_ERR_NOT_RESIDENT) continue;
-    if (s1 != SG_OK) {
-      st = s1;
-      break;
+    const sg_volume_desc& d = container_desc(hc->k);
+    if (t < 0 || t >= d.timepoints || c < 0 || c >= d.channels) {
+      set_error("sg_host_cache_prefetch: time point or channel out of range");
+      return SG_ERR_INVALID_ARG;
     }
-  }
-  host_cache_enqueue(hc, todo);
-  if (queued) *queued = (int32_t)todo.size();
-  return st;
+    host_cache_collect(hc, false, nullptr, nullptr, nullptr);
+    ++hc->frame;
+    std::vector<std::pair<int64_t, int64_t>> todo;
+    sg_status st = SG_OK;
+    for (int32_t i = 0; i < n; ++i) {
+      if (nodes[i] < 0 || nodes[i] >= container_nodes(hc->k)) {
+        st = SG_ERR_INVALID_ARG;
+        set_error("sg_host_cache_prefetch: node id out of range");
+        break;
+      }
+      const int64_t key = ((int64_t)t * d.channels + c) * container_nodes(hc->k) + nodes[i];
+      if (hc->failed.count(key)) continue;
+      int64_t e = -1;
+      int hit = 0;
+      const sg_status s1 = host_cache_lookup(hc, t, c, nodes[i], &e, &hit, &todo);
+      if (s1 == SG_ERR_NOT_RESIDENT) continue;
+      if (s1 != SG_OK) {
+        st = s1;
+        break;
+      }
+    }
+    host_cache_enqueue(hc, todo);
+    if (queued) *queued = (int32_t)todo.size();
+    return st;
+  });
 }
 
 sg_status sg_host_cache_wait(sg_host_cache* hc, int32_t* failed) {

@@ -1004,74 +1004,76 @@ __global__ void k_wait_selftest(uint32_t* err, uint32_t limit) {
 extern "C" {
 
 sg_status sg_unet_create(int max_batch, int max_h, int max_w, uint64_t seed, sg_unet** out) {
-  if (!out || max_batch < 1 || max_batch > 64 || max_h < 4 || max_w < 4 || max_h % 4 || max_w % 4) {
-    set_error("sg_unet_create: max_batch 1..64, max_h and max_w multiples of 4");
-    return SG_ERR_INVALID_ARG;
-  }
-  sg_unet* u = new sg_unet();
-  u->max_n = max_batch;
-  u->max_h = max_h;
-  u->max_w = max_w;
-  int64_t off = 0;
-  for (int L = 0; L < kLayers; ++L) {
-    u->woff[L] = off;
-    off += (int64_t)kCout[L] * 9 * kCin[L];
-    u->boff[L] = off;
-    off += kCout[L];
-  }
-  u->nparam = off;
-  const int64_t P1 = (int64_t)max_batch * max_h * max_w, P2 = P1 / 4, P3 = P1 / 16;
-  const size_t b = sizeof(bf16), f = sizeof(float);
-  cudaError_t e = cudaSuccess;
-  void** p;
-#define A_(ptr, bytes) \
-  if (e == cudaSuccess) { p = reinterpret_cast<void**>(&(ptr)); e = alloc(u, p, (bytes)); }
-  A_(u->d_param, off * f) A_(u->d_grad, off * f) A_(u->d_m, off * f) A_(u->d_v, off * f)
-  A_(u->d_w, off * b) A_(u->d_wt, off * b)
-  A_(u->in16, P1 * 16 * b) A_(u->a1, P1 * 32 * b) A_(u->cat1, P1 * 96 * b) A_(u->p1, P2 * 32 * b)
-  A_(u->a2, P2 * 64 * b) A_(u->cat2, P2 * 192 * b) A_(u->p2, P3 * 64 * b) A_(u->a3, P3 * 128 * b)
-  A_(u->b3, P3 * 128 * b) A_(u->a4, P2 * 64 * b) A_(u->d2, P2 * 64 * b) A_(u->a5, P1 * 32 * b) A_(u->d1, P1 * 32 * b)
-  A_(u->head, P1 * 16 * f)
-  A_(u->g_a1, P1 * 32 * f) A_(u->g_cat1, P1 * 96 * f) A_(u->g_p1, P2 * 32 * f) A_(u->g_a2, P2 * 64 * f)
-  A_(u->g_cat2, P2 * 192 * f) A_(u->g_p2, P3 * 64 * f) A_(u->g_a3, P3 * 128 * f) A_(u->g_b3, P3 * 128 * f)
-  A_(u->g_a4, P2 * 64 * f) A_(u->g_d2, P2 * 64 * f) A_(u->g_a5, P1 * 32 * f) A_(u->g_d1, P1 * 32 * f)
-  A_(u->g_head, P1 * 16 * f) A_(u->dz, P1 * 32 * b)
-  A_(u->dw_part, (size_t)kWgradSplits * 9 * 128 * 192 * f) A_(u->db_part, (size_t)kWgradMaxSplits * 128 * f)
-  A_(u->d_loss, 2 * f)
-  A_(u->d_err, 16)
-#undef A_
-  if (e != cudaSuccess) {
-    free_unet(u);
-    set_error(std::string("sg_unet_create: ") + cudaGetErrorString(e));
-    return SG_ERR_OOM;
-  }
-  // He-normal weights, zero biases; the head starts at zero so the untrained
-  // network is exactly the bilinear upsampling of its input
-  cudaMemset(u->d_param, 0, off * f);
-  cudaMemset(u->d_err, 0, 16);
-  cudaMemset(u->d_m, 0, off * f);
-  cudaMemset(u->d_v, 0, off * f);
-  for (int L = 0; L < HEAD; ++L) {
-    const int64_t n = (int64_t)kCout[L] * 9 * kCin[L];
-    const int fan_in = 9 * (L == C1A ? 4 : kCin[L]);
-    k_init<<<blocks_for(n), 256>>>(u->d_param + u->woff[L], n, sqrtf(2.0f / fan_in), seed, u->woff[L]);
-  }
-  e = cudaGetLastError();
-  if (e == cudaSuccess) {
-    // input channels 4..15 of c1a are padding: their weights stay zero
-    float* w = u->d_param + u->woff[C1A];
-    e = each((int64_t)kCout[C1A] * 9 * 16, 0, [=] __device__(int64_t i) {
-      if (i % 16 >= 4) w[i] = 0.f;
-    });
-  }
-  if (e == cudaSuccess) e = refresh_bf16(u, 0);
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  if (e != cudaSuccess) {
-    free_unet(u);
-    return cuda_fail(e, "sg_unet_create");
-  }
-  *out = u;
-  return SG_OK;
+  return sg::guarded("sg_unet_create", [&]() -> sg_status {
+    if (!out || max_batch < 1 || max_batch > 64 || max_h < 4 || max_w < 4 || max_h % 4 || max_w % 4) {
+      set_error("sg_unet_create: max_batch 1..64, max_h and max_w multiples of 4");
+      return SG_ERR_INVALID_ARG;
+    }
+    sg_unet* u = new sg_unet();
+    u->max_n = max_batch;
+    u->max_h = max_h;
+    u->max_w = max_w;
+    int64_t off = 0;
+    for (int L = 0; L < kLayers; ++L) {
+      u->woff[L] = off;
+      off += (int64_t)kCout[L] * 9 * kCin[L];
+      u->boff[L] = off;
+      off += kCout[L];
+    }
+    u->nparam = off;
+    const int64_t P1 = (int64_t)max_batch * max_h * max_w, P2 = P1 / 4, P3 = P1 / 16;
+    const size_t b = sizeof(bf16), f = sizeof(float);
+    cudaError_t e = cudaSuccess;
+    void** p;
+  #define A_(ptr, bytes) \
+    if (e == cudaSuccess) { p = reinterpret_cast<void**>(&(ptr)); e = alloc(u, p, (bytes)); }
+    A_(u->d_param, off * f) A_(u->d_grad, off * f) A_(u->d_m, off * f) A_(u->d_v, off * f)
+    A_(u->d_w, off * b) A_(u->d_wt, off * b)
+    A_(u->in16, P1 * 16 * b) A_(u->a1, P1 * 32 * b) A_(u->cat1, P1 * 96 * b) A_(u->p1, P2 * 32 * b)
+    A_(u->a2, P2 * 64 * b) A_(u->cat2, P2 * 192 * b) A_(u->p2, P3 * 64 * b) A_(u->a3, P3 * 128 * b)
+    A_(u->b3, P3 * 128 * b) A_(u->a4, P2 * 64 * b) A_(u->d2, P2 * 64 * b) A_(u->a5, P1 * 32 * b) A_(u->d1, P1 * 32 * b)
+    A_(u->head, P1 * 16 * f)
+    A_(u->g_a1, P1 * 32 * f) A_(u->g_cat1, P1 * 96 * f) A_(u->g_p1, P2 * 32 * f) A_(u->g_a2, P2 * 64 * f)
+    A_(u->g_cat2, P2 * 192 * f) A_(u->g_p2, P3 * 64 * f) A_(u->g_a3, P3 * 128 * f) A_(u->g_b3, P3 * 128 * f)
+    A_(u->g_a4, P2 * 64 * f) A_(u->g_d2, P2 * 64 * f) A_(u->g_a5, P1 * 32 * f) A_(u->g_d1, P1 * 32 * f)
+    A_(u->g_head, P1 * 16 * f) A_(u->dz, P1 * 32 * b)
+    A_(u->dw_part, (size_t)kWgradSplits * 9 * 128 * 192 * f) A_(u->db_part, (size_t)kWgradMaxSplits * 128 * f)
+    A_(u->d_loss, 2 * f)
+    A_(u->d_err, 16)
+  #undef A_
+    if (e != cudaSuccess) {
+      free_unet(u);
+      set_error(std::string("sg_unet_create: ") + cudaGetErrorString(e));
+      return SG_ERR_OOM;
+    }
+    // He-normal weights, zero biases; the head starts at zero so the untrained
+    // network is exactly the bilinear upsampling of its input
+    cudaMemset(u->d_param, 0, off * f);
+    cudaMemset(u->d_err, 0, 16);
+    cudaMemset(u->d_m, 0, off * f);
+    cudaMemset(u->d_v, 0, off * f);
+    for (int L = 0; L < HEAD; ++L) {
+      const int64_t n = (int64_t)kCout[L] * 9 * kCin[L];
+      const int fan_in = 9 * (L == C1A ? 4 : kCin[L]);
+      k_init<<<blocks_for(n), 256>>>(u->d_param + u->woff[L], n, sqrtf(2.0f / fan_in), seed, u->woff[L]);
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+      // input channels 4..15 of c1a are padding: their weights stay zero
+      float* w = u->d_param + u->woff[C1A];
+      e = each((int64_t)kCout[C1A] * 9 * 16, 0, [=] __device__(int64_t i) {
+        if (i % 16 >= 4) w[i] = 0.f;
+      });
+    }
+    if (e == cudaSuccess) e = refresh_bf16(u, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+      free_unet(u);
+      return cuda_fail(e, "sg_unet_create");
+    }
+    *out = u;
+    return SG_OK;
+  });
 }
 
 sg_status sg_unet_set_tensor_path(sg_unet* u, int tcgen05) {
@@ -1245,63 +1247,67 @@ struct CkptHeader {
 }  // namespace
 
 sg_status sg_unet_save(sg_unet* u, const char* path) {
-  if (!u || !path) {
-    set_error("sg_unet_save: NULL argument");
-    return SG_ERR_INVALID_ARG;
-  }
-  std::vector<float> host((size_t)u->nparam * 3);
-  cudaError_t e = cudaDeviceSynchronize();
-  if (e == cudaSuccess) e = cudaMemcpy(host.data(), u->d_param, u->nparam * sizeof(float), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(host.data() + u->nparam, u->d_m, u->nparam * sizeof(float), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(host.data() + 2 * u->nparam, u->d_v, u->nparam * sizeof(float), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_fail(e, "sg_unet_save");
-  FILE* f = fopen(path, "wb");
-  if (!f) {
-    set_error(std::string("sg_unet_save: cannot open ") + path);
-    return SG_ERR_IO;
-  }
-  const CkptHeader h{kCkptMagic, kCkptVersion, u->nparam, u->step};
-  const bool ok = fwrite(&h, sizeof h, 1, f) == 1 && fwrite(host.data(), sizeof(float), host.size(), f) == host.size();
-  if (fclose(f) != 0 || !ok) {
-    set_error(std::string("sg_unet_save: write failed: ") + path);
-    return SG_ERR_IO;
-  }
-  return SG_OK;
+  return sg::guarded("sg_unet_save", [&]() -> sg_status {
+    if (!u || !path) {
+      set_error("sg_unet_save: NULL argument");
+      return SG_ERR_INVALID_ARG;
+    }
+    std::vector<float> host((size_t)u->nparam * 3);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(host.data(), u->d_param, u->nparam * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(host.data() + u->nparam, u->d_m, u->nparam * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(host.data() + 2 * u->nparam, u->d_v, u->nparam * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "sg_unet_save");
+    FILE* f = fopen(path, "wb");
+    if (!f) {
+      set_error(std::string("sg_unet_save: cannot open ") + path);
+      return SG_ERR_IO;
+    }
+    const CkptHeader h{kCkptMagic, kCkptVersion, u->nparam, u->step};
+    const bool ok = fwrite(&h, sizeof h, 1, f) == 1 && fwrite(host.data(), sizeof(float), host.size(), f) == host.size();
+    if (fclose(f) != 0 || !ok) {
+      set_error(std::string("sg_unet_save: write failed: ") + path);
+      return SG_ERR_IO;
+    }
+    return SG_OK;
+  });
 }
 
 sg_status sg_unet_load(sg_unet* u, const char* path) {
-  if (!u || !path) {
-    set_error("sg_unet_load: NULL argument");
-    return SG_ERR_INVALID_ARG;
-  }
-  FILE* f = fopen(path, "rb");
-  if (!f) {
-    set_error(std::string("sg_unet_load: cannot open ") + path);
-    return SG_ERR_IO;
-  }
-  CkptHeader h;
-  std::vector<float> host((size_t)u->nparam * 3);
-  const bool ok = fread(&h, sizeof h, 1, f) == 1 && h.magic == kCkptMagic && h.version == kCkptVersion &&
-                  h.nparam == u->nparam && h.step >= 0 &&
-                  fread(host.data(), sizeof(float), host.size(), f) == host.size();
-  fclose(f);
-  if (!ok) {
-    set_error(std::string("sg_unet_load: not a checkpoint of this network (or truncated): ") + path);
-    return SG_ERR_IO;
-  }
-  cudaError_t e = cudaDeviceSynchronize();
-  if (e == cudaSuccess) e = cudaMemcpy(u->d_param, host.data(), u->nparam * sizeof(float), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(u->d_m, host.data() + u->nparam, u->nparam * sizeof(float), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(u->d_v, host.data() + 2 * u->nparam, u->nparam * sizeof(float), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = refresh_bf16(u, nullptr);
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  if (e != cudaSuccess) return cuda_fail(e, "sg_unet_load");
-  u->step = h.step;
-  return SG_OK;
+  return sg::guarded("sg_unet_load", [&]() -> sg_status {
+    if (!u || !path) {
+      set_error("sg_unet_load: NULL argument");
+      return SG_ERR_INVALID_ARG;
+    }
+    FILE* f = fopen(path, "rb");
+    if (!f) {
+      set_error(std::string("sg_unet_load: cannot open ") + path);
+      return SG_ERR_IO;
+    }
+    CkptHeader h;
+    std::vector<float> host((size_t)u->nparam * 3);
+    const bool ok = fread(&h, sizeof h, 1, f) == 1 && h.magic == kCkptMagic && h.version == kCkptVersion &&
+                    h.nparam == u->nparam && h.step >= 0 &&
+                    fread(host.data(), sizeof(float), host.size(), f) == host.size();
+    fclose(f);
+    if (!ok) {
+      set_error(std::string("sg_unet_load: not a checkpoint of this network (or truncated): ") + path);
+      return SG_ERR_IO;
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(u->d_param, host.data(), u->nparam * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(u->d_m, host.data() + u->nparam, u->nparam * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(u->d_v, host.data() + 2 * u->nparam, u->nparam * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = refresh_bf16(u, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "sg_unet_load");
+    u->step = h.step;
+    return SG_OK;
+  });
 }
 
 // ---------------------------------------------------------------- a learned frame
