@@ -749,6 +749,13 @@ __global__ void k_init(float* p, int64_t n, float stdv, uint64_t seed, int64_t b
   }
 }
 
+// per layer: the weights' offset in the parameter vector and the shape
+// (by value into the Adam kernel)
+struct LayerTable {
+  int64_t woff[kLayers];
+  int cin[kLayers], cout[kLayers];
+};
+
 cudaError_t refresh_bf16(sg_unet* u, cudaStream_t s) {
   // BF16 weights and the flipped/transposed copy used by the input gradient
   for (int L = 0; L < kLayers; ++L) {
@@ -1199,7 +1206,16 @@ sg_status sg_unet_adam_step(sg_unet* u, float lr, float beta1, float beta2, floa
   ++u->step;
   const float c1 = 1.0f - powf(beta1, (float)u->step), c2 = 1.0f - powf(beta2, (float)u->step);
   float *p = u->d_param, *g = u->d_grad, *m = u->d_m, *v = u->d_v;
+  bf16 *wb = u->d_w, *wt = u->d_wt;
   const int64_t pad_lo = u->woff[C1A], pad_n = (int64_t)kCout[C1A] * 9 * 16;
+  LayerTable lt;
+  for (int L = 0; L < kLayers; ++L) {
+    lt.woff[L] = u->woff[L];
+    lt.cin[L] = kCin[L];
+    lt.cout[L] = kCout[L];
+  }
+  // one pass: the update, then (for a weight) its BF16 copy and the
+  // flipped / transposed one the input gradient reads, as refresh_bf16 does
   cudaError_t e = each(u->nparam, s, [=] __device__(int64_t i) {
     // the padding input channels of the first layer stay zero
     if (i >= pad_lo && i < pad_lo + pad_n && (i - pad_lo) % 16 >= 4) return;
@@ -1207,9 +1223,19 @@ sg_status sg_unet_adam_step(sg_unet* u, float lr, float beta1, float beta2, floa
     const float mi = beta1 * m[i] + (1.f - beta1) * gi, vi = beta2 * v[i] + (1.f - beta2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
-    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    const float pn = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pn;
+    int L = kLayers - 1;
+    while (L > 0 && i < lt.woff[L]) --L;
+    const int64_t r = i - lt.woff[L];
+    const int Cin = lt.cin[L], Cout = lt.cout[L];
+    if (r < (int64_t)Cout * 9 * Cin) {
+      const int ci = (int)(r % Cin), tap = (int)((r / Cin) % 9), co = (int)(r / (9 * Cin));
+      const bf16 b16 = __float2bfloat16_rn(pn);
+      wb[i] = b16;
+      wt[lt.woff[L] + ((int64_t)ci * 9 + (8 - tap)) * Cout + co] = b16;
+    }
   });
-  if (e == cudaSuccess) e = refresh_bf16(u, s);
   return e == cudaSuccess ? SG_OK : cuda_fail(e, "sg_unet_adam_step");
 }
 
