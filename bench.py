@@ -769,7 +769,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
-    vol, tf_table, poses, model = make_inputs()
+    vol, tf_table, poses, model = make_inputs(args.volume)
     ovol = oracle.Volume([oracle.pyramid(vol, LEVELS)], BRICK, model=model)
     otf = oracle.make_tf(tf_table, *WINDOW)
     ranges = ovol.block_ranges()
@@ -803,7 +803,10 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(frames_s / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": workload_config({"sample": f"selection + every {stride}th pixel of both eyes per step"}),
+            "config": workload_config(dict(
+                {"sample": f"selection + every {stride}th pixel of both eyes per step", "volume": [args.volume] * 3},
+                **({} if args.volume == N_VOX else {
+                    "workload": WORKLOAD.replace(f"{N_VOX}^3", f"{args.volume}^3") + " (a smaller volume)"}))),
             "gsamples_per_s": round(samples / frames_s / 1e9, 6),
             "cpu_baseline": {"value": round(fps, 6), "unit": "stereo frames/s", "cores": oracle.max_threads(),
                              "kind": "oracle",
