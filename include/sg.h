@@ -237,7 +237,11 @@ sg_status sg_stream_requests(sg_volume* vol, int slot, sg_host_cache* hc, uint64
 /* The same requests served without waiting for the disk ("Volumetric Data
  * Cashing" with "Octree Representation"'s coarser stand-ins): the bricks
  * whose every channel the host cache holds are placed in the GPU cache (at
- * most max_bytes, coarse levels first; complete on return); the others are
+ * most max_bytes, coarse levels first): the page table is updated on return,
+ * the copies and the bricks' ranges and flags are queued on stream and not
+ * waited for; every later selection, transfer-function change or brick read
+ * waits for them on the device, and the host cache reuses none of those
+ * entries before they are done. The others are
  * handed to hc's background loader threads (at most max_bytes of new loads
  * per call) and placed by a later call once loaded. Until then the next
  * selections render their resident ancestors, so a frame never waits on a

@@ -68,6 +68,14 @@ struct VolumeExtra {
   std::vector<int64_t> free_slots;
   int32_t* d_scratch = nullptr;                // upload bookkeeping
   size_t scratch_n = 0;
+  // page-locked staging of an upload's lists when the call does not wait
+  // for its copies: a ring, each buffer reused once its event has passed
+  struct Stage {
+    int32_t* h = nullptr;
+    size_t n = 0;  // int32 words
+    cudaEvent_t ev = nullptr;
+  } stage[4];
+  int stage_next = 0;
 };
 
 std::vector<std::pair<sg_volume*, VolumeExtra*>>& extras() {
@@ -99,6 +107,7 @@ cudaError_t dalloc(T** p, size_t count) {
 
 void free_volume(sg_volume* v) {
   if (!v) return;
+  if (v->ev_upload) cudaEventSynchronize(v->ev_upload);  // no copy may still read or write freed memory
   cudaFree(v->d_pool);
   cudaFree(v->d_slot);
   cudaFree(v->d_range);
@@ -119,6 +128,7 @@ void free_volume(sg_volume* v) {
   cudaFree(v->d_err);
   cudaFree(v->d_stamp);
   if (v->ev_select) cudaEventDestroy(v->ev_select);
+  if (v->ev_upload) cudaEventDestroy(v->ev_upload);
   for (auto& s : v->sel) {
     cudaFree(s.d_leaf);
     cudaFree(s.d_cell_node);
@@ -131,6 +141,10 @@ void free_volume(sg_volume* v) {
   for (size_t i = 0; i < xs.size(); ++i)
     if (xs[i].first == v) {
       cudaFree(xs[i].second->d_scratch);
+      for (auto& g : xs[i].second->stage) {
+        if (g.ev) cudaEventDestroy(g.ev);
+        cudaFreeHost(g.h);
+      }
       delete xs[i].second;
       xs.erase(xs.begin() + i);
       break;
@@ -146,6 +160,8 @@ bool tfs_ready(const sg_volume* v) {
 
 sg_status refresh_flags(sg_volume* v, cudaStream_t s, const int32_t* d_slots = nullptr, int nslots = 0) {
   if (!tfs_ready(v)) return SG_OK;
+  // the flags read the ranges of bricks that queued uploads may still be writing
+  SG_CUDA(wait_uploads(v, s), "transfer-function flags");
   SG_CUDA(launch_tf_flags(v, s, d_slots, nslots), "transfer-function flags");
   return SG_OK;
 }
@@ -159,14 +175,17 @@ __global__ void k_page_update(int32_t* __restrict__ slot_of_key, const int64_t* 
 // brick i from host[i]; stops at the first brick that finds the cache full of
 // bricks used by the current frame (*done = bricks placed, a prefix of the
 // list). Page-table entries, value ranges and transparency flags of every
-// placed brick are consistent on return, whether or not the list was cut.
+// placed brick are consistent once the stream reaches v->ev_upload; with
+// wait the call returns only then, else as soon as everything is queued.
 sg_status upload_list(sg_volume* v, int t, int c, int n, const int32_t* nodes, const void* const* host, int* done,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool wait = true) {
   VolumeExtra* x = extra_of(v);
   const int R = v->B + 2;
   const size_t raw = (size_t)R * R * R * v->esize;
   *done = 0;
-  if (v->pooled) {
+  // after every earlier upload, on whatever stream (its scratch and page-table writes)
+  SG_CUDA(cudaStreamWaitEvent(s, v->ev_upload, 0), "upload");
+  if (v->pooled && v->stamps_read != v->frame) {
     // stamps of slots used by recent selections, read on this stream once
     // the last selection launch (on whatever stream) has written them
     std::vector<uint64_t> st(v->pool_slots);
@@ -184,6 +203,8 @@ sg_status upload_list(sg_volume* v, int t, int c, int n, const int32_t* nodes, c
         v->slot_stamp[sl] = st[sl];
         x->lru.insert(LruKey{st[sl], tie, sl});
       }
+    // only a selection moves the device stamps: once per frame is enough
+    v->stamps_read = v->frame;
   }
   std::vector<int32_t> lists(2 * (size_t)n);  // [nodes placed][their slots]
   std::vector<int64_t> touched;               // page-table keys whose entry changed
@@ -254,10 +275,38 @@ sg_status upload_list(sg_volume* v, int t, int c, int n, const int32_t* nodes, c
   int32_t* d_nodes = x->d_scratch;
   int32_t* d_slots = x->d_scratch + m;
   int64_t* d_upd = reinterpret_cast<int64_t*>(x->d_scratch + ((2 * (size_t)m + 1) & ~(size_t)1));
-  SG_CUDA(cudaMemcpyAsync(d_nodes, lists.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, s), "upload");
-  SG_CUDA(cudaMemcpyAsync(d_slots, lists.data() + n, m * sizeof(int32_t), cudaMemcpyHostToDevice, s), "upload");
+  // the lists' host side: the vectors above when the call waits; else a
+  // page-locked staging buffer that stays put until its copies are done
+  const int32_t* h_nodes = lists.data();
+  const int32_t* h_slots = lists.data() + n;
+  const int64_t* h_upd = upd.data();
+  VolumeExtra::Stage* g = nullptr;
+  if (!wait) {
+    g = &x->stage[x->stage_next];
+    x->stage_next = (x->stage_next + 1) % 4;
+    if (g->ev) SG_CUDA(cudaEventSynchronize(g->ev), "upload staging");
+    else SG_CUDA(cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming), "upload staging");
+    if (g->n < need + 2) {
+      cudaFreeHost(g->h);
+      g->h = nullptr;
+      g->n = 0;
+      SG_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&g->h), (need + 2) * sizeof(int32_t), cudaHostAllocDefault),
+              "upload staging");
+      g->n = need + 2;
+    }
+    int32_t* gl = g->h;
+    int64_t* gu = reinterpret_cast<int64_t*>(g->h + ((2 * (size_t)m + 1) & ~(size_t)1));
+    memcpy(gl, lists.data(), m * sizeof(int32_t));
+    memcpy(gl + m, lists.data() + n, m * sizeof(int32_t));
+    if (nupd) memcpy(gu, upd.data(), upd.size() * sizeof(int64_t));
+    h_nodes = gl;
+    h_slots = gl + m;
+    h_upd = gu;
+  }
+  SG_CUDA(cudaMemcpyAsync(d_nodes, h_nodes, m * sizeof(int32_t), cudaMemcpyHostToDevice, s), "upload");
+  SG_CUDA(cudaMemcpyAsync(d_slots, h_slots, m * sizeof(int32_t), cudaMemcpyHostToDevice, s), "upload");
   if (nupd) {
-    SG_CUDA(cudaMemcpyAsync(d_upd, upd.data(), upd.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s), "upload");
+    SG_CUDA(cudaMemcpyAsync(d_upd, h_upd, upd.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s), "upload");
     k_page_update<<<(unsigned)((nupd + 255) / 256), 256, 0, s>>>(v->d_slot, d_upd, (int)nupd);
     SG_CUDA(cudaGetLastError(), "page table update");
   }
@@ -266,6 +315,11 @@ sg_status upload_list(sg_volume* v, int t, int c, int n, const int32_t* nodes, c
   v->has_data[(size_t)t * v->nch + c] = 1;
   // node flags everywhere, sub-block flags of the uploaded slots only
   sg_status st = refresh_flags(v, s, d_slots, m);
+  SG_CUDA(cudaEventRecord(v->ev_upload, s), "upload");
+  if (g) {
+    SG_CUDA(cudaEventRecord(g->ev, s), "upload staging");
+    return st;
+  }
   // the host vectors above are consumed by the copies before they return
   SG_CUDA(cudaStreamSynchronize(s), "upload");
   return st;
@@ -329,6 +383,25 @@ sg_status prepare_lut(sg_volume* v, float step, int mode, cudaStream_t s) {
 }
 
 }  // namespace
+
+namespace sg {
+
+cudaError_t wait_uploads(sg_volume* v, cudaStream_t s) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess || cap != cudaStreamCaptureStatusNone) return e;
+  return cudaStreamWaitEvent(s, v->ev_upload, 0);
+}
+
+sg_status upload_list_nowait(sg_volume* v, int t, int c, int n, const int32_t* nodes, const void* const* host,
+                             int32_t* done, cudaStream_t s) {
+  int d = 0;
+  const sg_status st = upload_list(v, t, c, n, nodes, host, &d, s, false);
+  *done = d;
+  return st;
+}
+
+}  // namespace sg
 
 extern "C" {
 
@@ -425,7 +498,8 @@ sg_status sg_volume_create(const sg_volume_desc* d, sg_volume** out) {
         (e = dalloc(&v->d_palette, (size_t)v->nch * kMaxTF)) != cudaSuccess ||
         (e = dalloc(&v->d_lut, (size_t)2 * v->nch * v->levels * kMaxTF)) != cudaSuccess ||
         (e = dalloc(&v->d_err, 4)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&v->ev_select, cudaEventDisableTiming)) != cudaSuccess) {
+        (e = cudaEventCreateWithFlags(&v->ev_select, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&v->ev_upload, cudaEventDisableTiming)) != cudaSuccess) {
       free_volume(v);
       set_error(std::string("device allocation: ") + cudaGetErrorString(e));
       return SG_ERR_OOM;
@@ -692,6 +766,8 @@ sg_status sg_select_lod_batch(sg_volume* v, const sg_pose* poses, int n, void* s
     if (st != SG_OK) return st;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  // the page table, ranges and flags of every brick upload queued so far
+  SG_CUDA(wait_uploads(v, s), "selection");
   ++v->frame;
   SG_CUDA(launch_select(v, poses, n, s), "selection");
   // uploads and reads on other streams wait for the stamps and results this
@@ -783,6 +859,7 @@ sg_status sg_read_brick(sg_volume* v, int t, int c, int level, int bx, int by, i
   }
   const int R = v->B + 2;
   cudaStream_t s = (cudaStream_t)stream;
+  SG_CUDA(wait_uploads(v, s), "brick download");
   SG_CUDA(cudaMemcpyAsync(host_out, v->d_pool + ((size_t)slot * v->nch + c) * v->brick_bytes,
                           (size_t)R * R * R * v->esize, cudaMemcpyDeviceToHost, s),
           "brick download");

@@ -128,6 +128,8 @@ struct sg_volume {
   uint64_t frame = 0;
   uint64_t* d_stamp = nullptr;        // [slots] frame of last use, written by the selection kernel
   cudaEvent_t ev_select = nullptr;    // recorded after each stamping selection launch
+  cudaEvent_t ev_upload = nullptr;    // recorded after each brick upload's copies and kernels
+  uint64_t stamps_read = ~0ull;       // the frame whose device stamps the host LRU last took in
 
   sg::SelSlot sel[sg::kMaxSlots];
 
@@ -209,6 +211,15 @@ int64_t container_nodes(const sg_container* k);
 sg_status host_cache_lookup(sg_host_cache* hc, int t, int c, int64_t node, int64_t* entry, int* hit,
                             std::vector<std::pair<int64_t, int64_t>>* todo);
 void host_cache_drop(sg_host_cache* hc, int64_t e);
+// sg_upload_brick_list without the final wait: returns once the copies and
+// kernels are queued on s (the host bricks must stay untouched until
+// v->ev_upload has passed; later selections wait for it on the device)
+sg_status upload_list_nowait(sg_volume* v, int t, int c, int n, const int32_t* nodes, const void* const* host,
+                             int32_t* done, cudaStream_t s);
+// the stream waits (on the device) for every brick upload queued so far
+// (not while it is being captured into a graph)
+cudaError_t wait_uploads(sg_volume* v, cudaStream_t s);
 void host_cache_collect(sg_host_cache* hc, bool wait, int32_t* reads, uint64_t* bytes, int32_t* failed);
 void host_cache_drain(sg_host_cache* hc);
+void host_cache_quiesce(sg_host_cache* hc);
 }  // namespace sg

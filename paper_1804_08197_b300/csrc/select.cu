@@ -467,6 +467,9 @@ extern "C" sg_status sg_select_lod_noalloc(sg_volume* v, const sg_pose* p, uint3
   J.counters = counters;
   J.frontier = frontier;
   const cudaStream_t s = (cudaStream_t)stream;
+  // after the brick uploads queued so far (page table, flags)
+  e = wait_uploads(v, s);
+  if (e != cudaSuccess) return cuda_fail(e, "sg_select_lod_noalloc: upload order");
   k_select<<<1, kSelThreads, 0, s>>>(jobs, g);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "sg_select_lod_noalloc: launch");

@@ -53,6 +53,10 @@ struct sg_host_cache {
   int64_t in_flight = 0;                       // queued + being loaded
   bool stop = false;
   std::vector<std::thread> loaders;            // started on first use
+  // the copies of the last sg_stream_requests_async may still be reading
+  // entries: nothing reuses or frees an entry before this event has passed
+  cudaEvent_t ev_copies = nullptr;
+  bool copies_pending = false;
 };
 
 extern "C" {
@@ -111,6 +115,8 @@ sg_status sg_host_cache_destroy(sg_host_cache* hc) {
   }
   hc->cv_job.notify_all();
   for (auto& th : hc->loaders) th.join();
+  host_cache_quiesce(hc);
+  if (hc->ev_copies) cudaEventDestroy(hc->ev_copies);
   if (hc->pinned)
     cudaFreeHost(hc->arena);
   else
@@ -134,6 +140,7 @@ sg_status sg_host_cache_fetch(sg_host_cache* hc, int t, int c, int64_t node, con
       set_error("cache or output NULL");
       return SG_ERR_INVALID_ARG;
     }
+    host_cache_quiesce(hc);
     host_cache_drain(hc);
     ++hc->frame;
     std::vector<std::pair<int64_t, int64_t>> todo;  // (entry, chunk offset)
@@ -315,6 +322,13 @@ void host_cache_collect(sg_host_cache* hc, bool wait, int32_t* reads, uint64_t* 
 
 void host_cache_drain(sg_host_cache* hc) { host_cache_collect(hc, true, nullptr, nullptr, nullptr); }
 
+void host_cache_quiesce(sg_host_cache* hc) {
+  if (hc->copies_pending) {
+    cudaEventSynchronize(hc->ev_copies);
+    hc->copies_pending = false;
+  }
+}
+
 }  // namespace sg
 
 namespace {
@@ -341,6 +355,7 @@ sg_status stream_impl(sg_volume* v, int slot, sg_host_cache* hc, uint64_t max_by
     return SG_ERR_STATE;
   }
   const int t = sl.t;
+  host_cache_quiesce(hc);  // the previous call's copies are done reading their entries
   std::vector<int32_t> req((size_t)v->nodes);
   int32_t nreq = 0;
   sg_status st = sg_read_selection(v, slot, nullptr, 0, nullptr, 0, req.data(), (int32_t)req.size(), &nreq, stream);
@@ -532,9 +547,19 @@ sg_status stream_impl(sg_volume* v, int slot, sg_host_cache* hc, uint64_t max_by
   int32_t placed = (int32_t)nodes.size();
   for (int c = 0; c < v->nch && !nodes.empty(); ++c) {
     int32_t done = 0;
-    st = sg_upload_brick_list(v, t, c, placed, nodes.data(), ptrs[c].data(), &done, stream);
+    // asynchronous: queued, not waited for (later selections wait on the device)
+    st = async ? upload_list_nowait(v, t, c, placed, nodes.data(), ptrs[c].data(), &done, (cudaStream_t)stream)
+               : sg_upload_brick_list(v, t, c, placed, nodes.data(), ptrs[c].data(), &done, stream);
     if (st != SG_OK) return st;
     placed = std::min(placed, done);
+  }
+  if (async && !nodes.empty()) {
+    if (!hc->ev_copies && cudaEventCreateWithFlags(&hc->ev_copies, cudaEventDisableTiming) != cudaSuccess)
+      cudaStreamSynchronize((cudaStream_t)stream);  // no event to be had: wait here instead
+    else if (cudaEventRecord(hc->ev_copies, (cudaStream_t)stream) == cudaSuccess)
+      hc->copies_pending = true;
+    else
+      cudaStreamSynchronize((cudaStream_t)stream);
   }
   s0.served = placed;
   s0.upload_bytes = (uint64_t)placed * per_node;
@@ -576,6 +601,7 @@ sg_status sg_host_cache_prefetch(sg_host_cache* hc, int t, int c, const int64_t*
       set_error("sg_host_cache_prefetch: time point or channel out of range");
       return SG_ERR_INVALID_ARG;
     }
+    host_cache_quiesce(hc);
     host_cache_collect(hc, false, nullptr, nullptr, nullptr);
     ++hc->frame;
     std::vector<std::pair<int64_t, int64_t>> todo;
