@@ -344,9 +344,12 @@ typedef struct {
  * Otherwise, if a needed (not culled, not dropped) child is not resident,
  * those children are requested and the block itself is rendered; else the
  * needed children are visited. The result (which block renders each level-0
- * block cell, requests, counters) is kept in pose->slot. If stats is not NULL
- * the call waits for the stream and fills it. Errors: INVALID_ARG, STATE (no
- * transfer function or no data for t), CUDA. */
+ * block cell, requests, counters) is kept in pose->slot. The launch waits
+ * on the device for every brick upload queued before it, on any stream (an
+ * upload of sg_stream_requests_async may still be running); not while the
+ * stream is captured into a graph. If stats is not NULL the call waits for
+ * the stream and fills it. Errors: INVALID_ARG, STATE (no transfer function
+ * or no data for t), CUDA. */
 sg_status sg_select_lod(sg_volume* vol, const sg_pose* pose, sg_select_stats* stats, void* stream);
 
 /* Selection for n poses in one launch (batched frames); no stats.
