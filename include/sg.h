@@ -131,6 +131,16 @@ sg_status sg_upload_bricks(sg_volume* vol, int t, int c, int level, int n, const
 sg_status sg_upload_brick_list(sg_volume* vol, int t, int c, int n, const int32_t* nodes, const void* const* host,
                                int32_t* n_done, void* stream);
 
+/* sg_upload_brick_list without the wait: placement (page table, LRU state,
+ * *n_done) is decided on return, the copies and the placed bricks' ranges
+ * and flags are queued on stream. The caller keeps host[0..*n_done) unchanged
+ * (page-locked, for the copies to run asynchronously) until the stream has
+ * passed the upload. Later selections, transfer-function changes and brick
+ * reads, on any stream, wait for it on the device (not while their stream
+ * is captured into a graph). Errors: as sg_upload_brick_list. */
+sg_status sg_upload_brick_list_async(sg_volume* vol, int t, int c, int n, const int32_t* nodes,
+                                     const void* const* host, int32_t* n_done, void* stream);
+
 /* ---- Brick container and host cache ("Volumetric Data Storage",
  * "Volumetric Data Cashing") ----------------------------------------------
  * A container is one file of LZ4-compressed chunks, one per brick with its

@@ -1107,4 +1107,23 @@ sg_status sg_upload_brick_list(sg_volume* v, int t, int c, int n, const int32_t*
   });
 }
 
+sg_status sg_upload_brick_list_async(sg_volume* v, int t, int c, int n, const int32_t* nodes,
+                                     const void* const* host, int32_t* n_done, void* stream) {
+  return sg::guarded("sg_upload_brick_list_async", [&]() -> sg_status {
+    sg::NvtxRange nvtx_range("sg_upload_brick_list_async");
+    SG_CHECK_ARG(v && n_done && n >= 0 && (n == 0 || (nodes && host)), "volume/nodes/host/n_done NULL or n < 0");
+    SG_CHECK_ARG(t >= 0 && t < v->T && c >= 0 && c < v->nch, "t or c out of range");
+    *n_done = 0;
+    for (int i = 0; i < n; ++i) {
+      SG_CHECK_ARG(nodes[i] >= 0 && nodes[i] < v->nodes, "node id out of range");
+      SG_CHECK_ARG(host[i], "host pointer NULL");
+    }
+    if (n == 0) return SG_OK;
+    int done = 0;
+    sg_status st = upload_list(v, t, c, n, nodes, host, &done, (cudaStream_t)stream, false);
+    *n_done = done;
+    return st;
+  });
+}
+
 }  // extern "C"

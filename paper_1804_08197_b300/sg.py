@@ -29,7 +29,7 @@ EXPORTS = ["sg_volume_create", "sg_volume_destroy", "sg_upload_volume_device", "
            "sg_container_create", "sg_container_open", "sg_container_append", "sg_container_finish",
            "sg_container_get_info", "sg_container_read", "sg_container_close", "sg_host_cache_create",
            "sg_host_cache_destroy", "sg_host_cache_fetch", "sg_host_cache_clear_failures", "sg_stream_requests",
-           "sg_stream_requests_async", "sg_host_cache_prefetch", "sg_host_cache_wait",
+           "sg_stream_requests_async", "sg_host_cache_prefetch", "sg_host_cache_wait", "sg_upload_brick_list_async",
            "sg_last_error",
            "sg_version"]
 
@@ -120,6 +120,7 @@ def _load():
         "sg_upload_volume_device": [vp, i32, i32, vp, vp],
         "sg_upload_bricks": [vp, i32, i32, i32, i32, vp, vp, vp],
         "sg_upload_brick_list": [vp, i32, i32, i32, vp, vp, P(ctypes.c_int32), vp],
+        "sg_upload_brick_list_async": [vp, i32, i32, i32, vp, vp, P(ctypes.c_int32), vp],
         "sg_unwarp": [P(sg_lens), P(vp), i32, i32, P(vp), i32, i32, vp],
         "sg_set_channel_shading": [vp, i32, i32, vp, i32, f32, f32, vp],
         "sg_container_create": [ctypes.c_char_p, P(sg_volume_desc), P(vp)],
@@ -249,14 +250,17 @@ def sg_upload_bricks(vol, t, c, level, brick_xyz, host, stream=None):
     _check(lib.sg_upload_bricks(vol, t, c, level, len(xyz), _ptr(xyz), _ptr(host), _stream(stream)))
 
 
-def sg_upload_brick_list(vol, t, c, nodes, host_ptrs, stream=None):
+def sg_upload_brick_list(vol, t, c, nodes, host_ptrs, stream=None, asynchronous=False):
     """Uploads bricks by node id from per-brick host pointers (ints, numpy
-    arrays or tensors); returns how many (a prefix of the list) were cached."""
+    arrays or tensors); returns how many (a prefix of the list) were cached.
+    asynchronous=True: sg_upload_brick_list_async (copies queued; keep the
+    host bricks unchanged until the stream has passed them)."""
     import numpy as np
     ids = np.ascontiguousarray(nodes, np.int32).reshape(-1)
     ptrs = _ptr_array(host_ptrs) if len(ids) else None
     done = ctypes.c_int32(0)
-    _check(lib.sg_upload_brick_list(vol, t, c, len(ids), _ptr(ids), ptrs, ctypes.byref(done), _stream(stream)))
+    fn = lib.sg_upload_brick_list_async if asynchronous else lib.sg_upload_brick_list
+    _check(fn(vol, t, c, len(ids), _ptr(ids), ptrs, ctypes.byref(done), _stream(stream)))
     return done.value
 
 

@@ -39,7 +39,7 @@ def _stereo(head, target, W, H, fovy=40.0, ipd=0.064):
     return views, [proj, proj]
 
 
-@pytest.mark.parametrize("mode", ["bricks", "list", "pipelined"])
+@pytest.mark.parametrize("mode", ["bricks", "list", "pipelined", "list_async"])
 def test_streaming_frames_match_the_oracle_and_evict_lru(mode, index_ranges=True):
     import torch
     from paper_1804_08197_b300 import sg
@@ -73,7 +73,8 @@ def test_streaming_frames_match_the_oracle_and_evict_lru(mode, index_ranges=True
             known[:] = True
 
         comp = torch.cuda.Stream() if mode == "pipelined" else None
-        copy = torch.cuda.Stream() if mode == "pipelined" else None
+        copy = torch.cuda.Stream() if mode in ("pipelined", "list_async") else None
+        keep = []  # page-locked bricks of queued uploads stay alive until the end
         cache = oracle.Cache(ovol, cap)
         nevicted = 0
 
@@ -86,14 +87,19 @@ def test_streaming_frames_match_the_oracle_and_evict_lru(mode, index_ranges=True
 
         def upload(ids):
             nonlocal nevicted
-            if mode in ("list", "pipelined"):
+            if mode in ("list", "pipelined", "list_async"):
                 # one call per frame, by node id, coarse levels first
                 ids = sorted((int(i) for i in ids), key=lambda n: (-ovol.node_coords(n)[0], n))
                 host = []
                 for n in ids:
                     L, b = ovol.node_coords(n)
                     host.append(_brick(ovol, L, *b))
-                done = sg.sg_upload_brick_list(vol, 0, 0, ids, host, stream=copy)
+                if mode == "list_async":
+                    # queued on a copy stream, never waited for here: the next
+                    # selection (another stream) waits for it on the device
+                    host = [torch.from_numpy(h.view(np.int16)).pin_memory() for h in host]
+                    keep.extend(host)
+                done = sg.sg_upload_brick_list(vol, 0, 0, ids, host, stream=copy, asynchronous=mode == "list_async")
                 m, ev = cache.place(ids)
                 assert 0 < done <= len(ids) and done == m
                 nevicted += len(ev)
