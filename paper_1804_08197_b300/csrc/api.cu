@@ -76,6 +76,12 @@ struct VolumeExtra {
     cudaEvent_t ev = nullptr;
   } stage[4];
   int stage_next = 0;
+  // the host's reads of selection stamps and requests: a stream of their
+  // own, so that they wait for the last selection only and not for copies
+  // queued on the caller's stream (made at first use, as is the page-locked
+  // array of stamps)
+  cudaStream_t side_s = nullptr;
+  uint64_t* h_stamp = nullptr;
 };
 
 std::vector<std::pair<sg_volume*, VolumeExtra*>>& extras() {
@@ -145,6 +151,8 @@ void free_volume(sg_volume* v) {
         if (g.ev) cudaEventDestroy(g.ev);
         cudaFreeHost(g.h);
       }
+      if (xs[i].second->side_s) cudaStreamDestroy(xs[i].second->side_s);
+      cudaFreeHost(xs[i].second->h_stamp);
       delete xs[i].second;
       xs.erase(xs.begin() + i);
       break;
@@ -186,13 +194,22 @@ sg_status upload_list(sg_volume* v, int t, int c, int n, const int32_t* nodes, c
   // after every earlier upload, on whatever stream (its scratch and page-table writes)
   SG_CUDA(cudaStreamWaitEvent(s, v->ev_upload, 0), "upload");
   if (v->pooled && v->stamps_read != v->frame) {
-    // stamps of slots used by recent selections, read on this stream once
-    // the last selection launch (on whatever stream) has written them
-    std::vector<uint64_t> st(v->pool_slots);
-    SG_CUDA(cudaStreamWaitEvent(s, v->ev_select, 0), "upload");
-    SG_CUDA(cudaMemcpyAsync(st.data(), v->d_stamp, v->pool_slots * sizeof(uint64_t), cudaMemcpyDeviceToHost, s),
+    // stamps of slots used by recent selections, read once the last
+    // selection launch (on whatever stream) has written them
+    cudaStream_t rs = side_stream(v);
+    if (!rs) {
+      set_error("stamps: no stream could be made");
+      return SG_ERR_CUDA;
+    }
+    if (!x->h_stamp)
+      SG_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&x->h_stamp), v->pool_slots * sizeof(uint64_t),
+                            cudaHostAllocDefault),
+              "stamps");
+    const uint64_t* st = x->h_stamp;
+    SG_CUDA(cudaStreamWaitEvent(rs, v->ev_select, 0), "upload");
+    SG_CUDA(cudaMemcpyAsync(x->h_stamp, v->d_stamp, v->pool_slots * sizeof(uint64_t), cudaMemcpyDeviceToHost, rs),
             "stamps");
-    SG_CUDA(cudaStreamSynchronize(s), "upload");
+    SG_CUDA(cudaStreamSynchronize(rs), "upload");
     // a slot's stamp only moves forward: the device array holds the stamps
     // selections wrote, so a slot placed since the last selection still
     // carries its previous occupant's (older) stamp there
@@ -261,16 +278,20 @@ sg_status upload_list(sg_volume* v, int t, int c, int n, const int32_t* nodes, c
   }
   // device copies of the lists for the range kernels and the page update
   const size_t need = 2 * (size_t)m + 4 * nupd;  // int32 words: lists + int64 pairs
+  // sized at first use for a list of up to 65536 blocks (nupd <= 2 m, so
+  // 10 words a block): growing later frees and allocates, and both wait for
+  // the whole device, a render in flight included
+  const size_t cap = std::max(need + 2, 10 * (size_t)std::min<int64_t>(v->nodes * v->T, 1 << 16) + 2);
   if (x->scratch_n < need) {
     cudaFree(x->d_scratch);
     x->d_scratch = nullptr;
     x->scratch_n = 0;
-    cudaError_t e = dalloc(&x->d_scratch, need + 2);
+    cudaError_t e = dalloc(&x->d_scratch, cap);
     if (e != cudaSuccess) {
       set_error(std::string("upload scratch: ") + cudaGetErrorString(e));
       return SG_ERR_OOM;
     }
-    x->scratch_n = need;
+    x->scratch_n = cap - 2;
   }
   int32_t* d_nodes = x->d_scratch;
   int32_t* d_slots = x->d_scratch + m;
@@ -290,9 +311,9 @@ sg_status upload_list(sg_volume* v, int t, int c, int n, const int32_t* nodes, c
       cudaFreeHost(g->h);
       g->h = nullptr;
       g->n = 0;
-      SG_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&g->h), (need + 2) * sizeof(int32_t), cudaHostAllocDefault),
+      SG_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&g->h), cap * sizeof(int32_t), cudaHostAllocDefault),
               "upload staging");
-      g->n = need + 2;
+      g->n = cap;
     }
     int32_t* gl = g->h;
     int64_t* gu = reinterpret_cast<int64_t*>(g->h + ((2 * (size_t)m + 1) & ~(size_t)1));
@@ -385,6 +406,13 @@ sg_status prepare_lut(sg_volume* v, float step, int mode, cudaStream_t s) {
 }  // namespace
 
 namespace sg {
+
+cudaStream_t side_stream(sg_volume* v) {
+  VolumeExtra* x = extra_of(v);
+  if (!x) return nullptr;
+  if (!x->side_s && cudaStreamCreateWithFlags(&x->side_s, cudaStreamNonBlocking) != cudaSuccess) x->side_s = nullptr;
+  return x->side_s;
+}
 
 cudaError_t wait_uploads(sg_volume* v, cudaStream_t s) {
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;

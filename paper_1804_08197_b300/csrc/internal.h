@@ -222,4 +222,9 @@ cudaError_t wait_uploads(sg_volume* v, cudaStream_t s);
 void host_cache_collect(sg_host_cache* hc, bool wait, int32_t* reads, uint64_t* bytes, int32_t* failed);
 void host_cache_drain(sg_host_cache* hc);
 void host_cache_quiesce(sg_host_cache* hc);
+// clears the pending state of the copies once they are done, without waiting
+void host_cache_poll(sg_host_cache* hc);
+// a non-blocking stream of the volume for the host's reads of selection
+// results and stamps (made at first use; nullptr if none could be made)
+cudaStream_t side_stream(sg_volume* v);
 }  // namespace sg

@@ -53,10 +53,14 @@ struct sg_host_cache {
   int64_t in_flight = 0;                       // queued + being loaded
   bool stop = false;
   std::vector<std::thread> loaders;            // started on first use
-  // the copies of the last sg_stream_requests_async may still be reading
-  // entries: nothing reuses or frees an entry before this event has passed
+  // the copies of recent sg_stream_requests_async calls may still be
+  // reading entries, those stamped copies_frame or later: such an entry is
+  // neither reused nor freed before this event (recorded on copies_stream
+  // after the last of them) has passed
   cudaEvent_t ev_copies = nullptr;
   bool copies_pending = false;
+  uint64_t copies_frame = 0;
+  cudaStream_t copies_stream = nullptr;
 };
 
 extern "C" {
@@ -207,6 +211,8 @@ sg_status host_cache_lookup(sg_host_cache* hc, int t, int c, int64_t node, int64
       set_error("host cache: full of bricks used by the current frame");
       return SG_ERR_OOM;
     }
+    // the entry may be the source of a copy still in flight
+    if (hc->copies_pending && lo->first >= hc->copies_frame) host_cache_quiesce(hc);
     e = lo->second;
     hc->lru.erase(lo);
     hc->where.erase(hc->owner[e]);
@@ -329,6 +335,10 @@ void host_cache_quiesce(sg_host_cache* hc) {
   }
 }
 
+void host_cache_poll(sg_host_cache* hc) {
+  if (hc->copies_pending && cudaEventQuery(hc->ev_copies) == cudaSuccess) hc->copies_pending = false;
+}
+
 }  // namespace sg
 
 namespace {
@@ -355,10 +365,20 @@ sg_status stream_impl(sg_volume* v, int slot, sg_host_cache* hc, uint64_t max_by
     return SG_ERR_STATE;
   }
   const int t = sl.t;
-  host_cache_quiesce(hc);  // the previous call's copies are done reading their entries
+  // entries that earlier calls' copies may still read: the blocking path
+  // waits for those copies here, the asynchronous one only where it would
+  // reuse such an entry (in host_cache_lookup)
+  if (async)
+    host_cache_poll(hc);
+  else
+    host_cache_quiesce(hc);
   std::vector<int32_t> req((size_t)v->nodes);
   int32_t nreq = 0;
-  sg_status st = sg_read_selection(v, slot, nullptr, 0, nullptr, 0, req.data(), (int32_t)req.size(), &nreq, stream);
+  // read on a stream of its own, which waits for the selection alone and
+  // not for copies already queued on the caller's stream
+  cudaStream_t rs = side_stream(v);
+  sg_status st = sg_read_selection(v, slot, nullptr, 0, nullptr, 0, req.data(), (int32_t)req.size(), &nreq,
+                                   rs ? (void*)rs : stream);
   if (st != SG_OK) return st;
   req.resize((size_t)std::min<int64_t>(nreq, (int64_t)req.size()));
   s0.requested = (int32_t)req.size();
@@ -554,12 +574,19 @@ sg_status stream_impl(sg_volume* v, int slot, sg_host_cache* hc, uint64_t max_by
     placed = std::min(placed, done);
   }
   if (async && !nodes.empty()) {
-    if (!hc->ev_copies && cudaEventCreateWithFlags(&hc->ev_copies, cudaEventDisableTiming) != cudaSuccess)
+    // one event covers every pending call's copies only when all were
+    // queued on one stream: on a new stream the older copies are waited for
+    if (hc->copies_pending && hc->copies_stream != (cudaStream_t)stream) host_cache_quiesce(hc);
+    if (!hc->ev_copies && cudaEventCreateWithFlags(&hc->ev_copies, cudaEventDisableTiming) != cudaSuccess) {
       cudaStreamSynchronize((cudaStream_t)stream);  // no event to be had: wait here instead
-    else if (cudaEventRecord(hc->ev_copies, (cudaStream_t)stream) == cudaSuccess)
+    } else if (cudaEventRecord(hc->ev_copies, (cudaStream_t)stream) == cudaSuccess) {
+      if (!hc->copies_pending) hc->copies_frame = hc->frame;
       hc->copies_pending = true;
-    else
+      hc->copies_stream = (cudaStream_t)stream;
+    } else {
       cudaStreamSynchronize((cudaStream_t)stream);
+      hc->copies_pending = false;
+    }
   }
   s0.served = placed;
   s0.upload_bytes = (uint64_t)placed * per_node;
