@@ -263,7 +263,12 @@ void loader_main(sg_host_cache* hc) {
 // queues the reads of newly placed entries on the loader threads
 void host_cache_enqueue(sg_host_cache* hc, const std::vector<std::pair<int64_t, int64_t>>& todo) {
   if (todo.empty()) return;
-  for (auto& j : todo) hc->loading[j.first] = 1;
+  // out of the LRU set while loading (host_cache_lookup placed them there):
+  // nothing may evict an entry a loader is writing; collect puts it back
+  for (auto& j : todo) {
+    hc->lru.erase({hc->stamp[j.first], j.first});
+    hc->loading[j.first] = 1;
+  }
   {
     std::lock_guard<std::mutex> g(hc->mu);
     for (auto& j : todo) hc->jobs.push_back(j);

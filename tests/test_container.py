@@ -306,3 +306,49 @@ def test_background_loads_land_in_the_host_cache(tmp_path):
     sg.sg_host_cache_prefetch(hc, 0, 0, [0, 1, 3, 4])
     sg.sg_host_cache_destroy(hc)
     sg.sg_container_close(k)
+
+
+def test_loads_in_flight_are_never_evicted(tmp_path):
+    """A host cache of 8 entries fed faster than its 4 loader threads
+    finish: calls that find every entry either loading or used this frame
+    place nothing (SG_ERR_OOM) instead of evicting an entry a loader is
+    still writing. After every wait each cached brick holds its own chunk's
+    data, and the cache never holds more bricks than entries."""
+    sg = _sg()
+    desc = sg.volume_desc((64, 64, 64), sg.SG_U8, B, 3)
+    nodes = 8 ** 3 + 4 ** 3 + 2 ** 3
+    rng = np.random.default_rng(7)
+    bricks = {}
+    path = tmp_path / "v.sgc"
+    k = sg.sg_container_create(path, desc)
+    for n in range(nodes):
+        L = 0 if n < 512 else (1 if n < 576 else 2)
+        nb = 8 >> L
+        i = n - (0 if L == 0 else (512 if L == 1 else 576))
+        bx, by, bz = i % nb, (i // nb) % nb, i // (nb * nb)
+        b = rng.integers(0, 256, (B + 2,) * 3).astype(np.uint8)
+        b[0, 0, :2] = (n & 255, n >> 8)  # the brick's own id in its first voxels
+        bricks[n] = b
+        sg.sg_container_append(k, 0, 0, L, bx, by, bz, b, 0, 255)
+    sg.sg_container_finish(k)
+    sg.sg_container_close(k)
+    k = sg.sg_container_open(path)
+    hc = sg.sg_host_cache_create(k, 8 * R3, pinned=False, threads=4)
+    try:
+        full = 0
+        for rnd in range(300):
+            want = [int(x) for x in rng.choice(nodes, 8, replace=False)]
+            try:
+                sg.sg_host_cache_prefetch(hc, 0, 0, want)
+            except sg.SGError:
+                full += 1
+            if rnd % 10 == 9:
+                assert sg.sg_host_cache_wait(hc) == 0
+                for n in want:
+                    ptr, hit = sg.sg_host_cache_fetch(hc, 0, 0, n)
+                    got = np.ctypeslib.as_array((ctypes.c_uint8 * R3).from_address(ptr))
+                    assert np.array_equal(got, bricks[n].reshape(-1)), (rnd, n, hit)
+        assert full > 0  # the loaders were outpaced at least once
+    finally:
+        sg.sg_host_cache_destroy(hc)
+        sg.sg_container_close(k)

@@ -653,3 +653,88 @@ def test_two_channel_container_streams_both_channels_together(tmp_path):
         sg.sg_host_cache_destroy(hc)
         sg.sg_volume_destroy(vol)
         sg.sg_container_close(k)
+
+
+def test_async_streaming_through_a_small_host_cache_keeps_bricks_intact(tmp_path):
+    """sg_stream_requests_async with a host cache of 40 bricks, far fewer
+    than the views need: nearly every call evicts entries that the previous
+    call's queued copies read, on one stream or alternating between two. An
+    entry reused while a copy still reads it would leave a wrong brick on
+    the GPU, so after an eight-pose fly-through every resident brick is read
+    back and compared voxel for voxel with the oracle's pyramid, and the
+    last frame's selection and image match the oracle."""
+    import time
+    import torch
+    from paper_1804_08197_b300 import sg
+    a = synth.filaments_u16(DIMS, seed=35, ntubes=24)
+    model = synth.volume_model(128, 0.5)
+    ovol = oracle.Volume([oracle.pyramid(a, LEVELS)], B, model=model)
+    full = ovol.block_ranges()
+    table = synth.tf_piecewise(2004, zero_alpha_points=2)
+    otf = oracle.make_tf(table, 300.0, 60000.0)
+    path = tmp_path / "vol.sgc"
+    k = sg.sg_container_create(path, sg.volume_desc(DIMS, sg.SG_U16, B, LEVELS, model=model))
+    for n in range(ovol.node_count):
+        L, b = ovol.node_coords(n)
+        sg.sg_container_append(k, 0, 0, L, *b, _brick(ovol, L, *b), *full[n, 0])
+    sg.sg_container_finish(k)
+    sg.sg_container_close(k)
+    k = sg.sg_container_open(path)
+    R = B + 2
+    brick_bytes = (R ** 3 * 2 + 255) // 256 * 256
+    vol = sg.sg_volume_create(DIMS, sg.SG_U16, B, LEVELS, device_pool_bytes=ovol.node_count * brick_bytes, model=model)
+    hc = sg.sg_host_cache_create(k, 40 * R ** 3 * 2, pinned=True, threads=4)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    W, H, tau = 160, 176, 0.3
+    try:
+        sg.sg_set_transfer_function(vol, 0, table, 300.0, 60000.0)
+        for L in range(LEVELS):
+            nbx, nby, nbz = ovol.blocks_per_axis(L)
+            xyz = np.array([(x, y, z) for z in range(nbz) for y in range(nby) for x in range(nbx)])
+            lo, hi = ovol.level_offsets[L], ovol.level_offsets[L + 1]
+            sg.sg_set_brick_ranges(vol, 0, 0, L, xyz, full[lo:hi, 0, :])
+        root = int(ovol.level_offsets[LEVELS - 1])
+        ptr, _ = sg.sg_host_cache_fetch(hc, 0, 0, root)
+        assert sg.sg_upload_brick_list(vol, 0, 0, [root], [ptr]) == 1
+        reads, calls = 0, 0
+        for i in range(8):
+            ang = 2 * np.pi * i / 8
+            head = (0.45 * np.cos(ang), 0.45 * np.sin(ang), 0.05)
+            views, projs = _stereo(head, (0.0, 0.0, 0.0), W, H)
+            pose = sg.make_pose(views, projs, W, H, pixel_error=tau)
+            for frame in range(400):
+                stats = sg.sg_select_lod(vol, pose, stats=True)
+                if stats["requested"] == 0:
+                    break
+                s = streams[(calls // 3) % 2] if i % 2 else streams[0]
+                st = sg.sg_stream_requests(vol, 0, hc, 24 * R ** 3 * 2, stream=s, asynchronous=True)
+                assert st["failed"] == 0 and st["missing"] == 0
+                reads += st["disk_reads"]
+                calls += 1
+                if st["served"] == 0:
+                    time.sleep(0.002)
+            else:
+                raise AssertionError(f"pose {i}: streaming did not converge")
+        torch.cuda.synchronize()
+        assert reads > 3 * 40  # the host cache turned over several times
+        res = sg.sg_read_residency(vol, 0, ovol.node_count)
+        got = np.empty((R, R, R), np.uint16)
+        checked = 0
+        for n in np.flatnonzero(res >= 0):
+            L, b = ovol.node_coords(int(n))
+            sg.sg_read_brick(vol, 0, 0, L, *b, got)
+            assert np.array_equal(got, _brick(ovol, L, *b)), (int(n), L, b)
+            checked += 1
+        assert checked > 40
+        ref = ovol.select([otf], views, projs, H, tau=tau, resident=(res >= 0).astype(np.uint8), ranges=full)
+        compare_selection(sg.sg_read_selection(vol, 0, len(ref["leaf"]), ovol.node_count), ref)
+        assert len(ref["requests"]) == 0
+        outs = [torch.empty((H, W, 4), device="cuda") for _ in range(2)]
+        sg.sg_render(vol, pose, sg.render_params(), outs)
+        torch.cuda.synchronize()
+        for e in range(2):
+            compare_image(outs[e].cpu().numpy().reshape(-1, 4), ovol.render([otf], ref["leaf"], views[e], projs[e], W, H))
+    finally:
+        sg.sg_host_cache_destroy(hc)
+        sg.sg_volume_destroy(vol)
+        sg.sg_container_close(k)
