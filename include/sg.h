@@ -503,16 +503,18 @@ sg_status sg_render_host(sg_volume* vol, const sg_pose* pose, const sg_render_pa
                          float* host_rgba[2], void* stream);
 
 /* Pipelined sg_render_host for a stream of frames: renders on `stream` into
- * one of two library-owned device staging pairs (alternating per call), then
+ * one of three library-owned device staging pairs (taken in turn), then
  * copies both images to the caller's HOST buffers on a library-owned copy
  * stream, and returns without waiting. So the copy of one frame overlaps
- * the selection and render of the next. A render waits on the GPU (not the
- * host) until the pair it reuses, two calls back, has been copied out. The
- * images of a call are complete once sg_render_host_wait has covered it:
- * all = 0 waits for the older of the (at most two) frames in flight, all != 0
- * for both. Host buffers must stay valid and unread until then; pinned
- * memory is needed for the copies to run asynchronously. Errors: as
- * sg_render_host. */
+ * the renders of the next two: a caller that waits for frame i - 2 after
+ * queueing frame i keeps the GPU rendering while frame i - 1 is copied,
+ * even when a render is shorter than a copy. A render waits on the GPU (not
+ * the host) until the pair it reuses, three calls back, has been copied
+ * out. The images of a call are complete once sg_render_host_wait has
+ * covered it: all = 0 waits for the oldest of the (at most three) frames in
+ * flight, all != 0 for all of them. Host buffers must stay valid and unread
+ * until then; pinned memory is needed for the copies to run asynchronously.
+ * Errors: as sg_render_host. */
 sg_status sg_render_host_async(sg_volume* vol, const sg_pose* pose, const sg_render_params* params,
                                float* host_rgba[2], void* stream);
 sg_status sg_render_host_wait(sg_volume* vol, int all);

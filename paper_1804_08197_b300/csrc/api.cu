@@ -126,7 +126,7 @@ void free_volume(sg_volume* v) {
   cudaFree(v->d_lut);
   cudaFree(v->d_stage);
   cudaFree(v->d_pipe);
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < sg_volume::kPipeDepth; ++k) {
     if (v->ev_rendered[k]) cudaEventDestroy(v->ev_rendered[k]);
     if (v->ev_copied[k]) cudaEventDestroy(v->ev_copied[k]);
   }
@@ -940,13 +940,13 @@ sg_status sg_render_host(sg_volume* v, const sg_pose* p, const sg_render_params*
 
 sg_status sg_render_host_wait(sg_volume* v, int all) {
   SG_CHECK_ARG(v, "volume NULL");
-  // pipe_next is the pair of the older frame in flight
-  const int order[2] = {v->pipe_next, v->pipe_next ^ 1};
-  for (int i = 0; i < (all ? 2 : 1); ++i) {
-    const int k = order[i];
+  // from pipe_next (the pair of the oldest frame) on, oldest first
+  for (int i = 0; i < sg_volume::kPipeDepth; ++i) {
+    const int k = (v->pipe_next + i) % sg_volume::kPipeDepth;
     if (!v->copy_pending[k]) continue;
     SG_CUDA(cudaEventSynchronize(v->ev_copied[k]), "image download");
     v->copy_pending[k] = false;
+    if (!all) break;
   }
   return SG_OK;
 }
@@ -960,7 +960,7 @@ sg_status sg_render_host_async(sg_volume* v, const sg_pose* p, const sg_render_p
   cudaStream_t s = (cudaStream_t)stream;
   if (!v->copy_stream) {
     SG_CUDA(cudaStreamCreateWithFlags(&v->copy_stream, cudaStreamNonBlocking), "copy stream");
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < sg_volume::kPipeDepth; ++k) {
       SG_CUDA(cudaEventCreateWithFlags(&v->ev_rendered[k], cudaEventDisableTiming), "pipeline events");
       SG_CUDA(cudaEventCreateWithFlags(&v->ev_copied[k], cudaEventDisableTiming), "pipeline events");
     }
@@ -971,7 +971,7 @@ sg_status sg_render_host_async(sg_volume* v, const sg_pose* p, const sg_render_p
     cudaFree(v->d_pipe);
     v->d_pipe = nullptr;
     v->pipe_bytes = 0;
-    cudaError_t e = cudaMalloc(&v->d_pipe, 4 * per);
+    cudaError_t e = cudaMalloc(&v->d_pipe, 2 * sg_volume::kPipeDepth * per);
     if (e != cudaSuccess) {
       set_error(std::string("staging allocation: ") + cudaGetErrorString(e));
       return SG_ERR_OOM;
@@ -981,7 +981,9 @@ sg_status sg_render_host_async(sg_volume* v, const sg_pose* p, const sg_render_p
   const int k = v->pipe_next;
   float* dev[2] = {reinterpret_cast<float*>(v->d_pipe + k * v->pipe_bytes),
                    reinterpret_cast<float*>(v->d_pipe + k * v->pipe_bytes + per)};
-  // the pair's previous frame must be copied out before this render overwrites it
+  // the pair's previous frame (kPipeDepth calls back) must be copied out
+  // before this render overwrites it: a wait on the GPU, not the host (the
+  // copy stream's next event covers that frame's copy too)
   if (v->copy_pending[k]) SG_CUDA(cudaStreamWaitEvent(s, v->ev_copied[k], 0), "pipeline order");
   st = sg_render(v, p, prm, dev, stream);
   if (st != SG_OK) return st;
@@ -991,7 +993,7 @@ sg_status sg_render_host_async(sg_volume* v, const sg_pose* p, const sg_render_p
   SG_CUDA(cudaMemcpyAsync(host_rgba[1], dev[1], per, cudaMemcpyDeviceToHost, v->copy_stream), "image download");
   SG_CUDA(cudaEventRecord(v->ev_copied[k], v->copy_stream), "pipeline order");
   v->copy_pending[k] = true;
-  v->pipe_next = k ^ 1;
+  v->pipe_next = (k + 1) % sg_volume::kPipeDepth;
   return SG_OK;
 }
 

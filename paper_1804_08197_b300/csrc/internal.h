@@ -136,14 +136,15 @@ struct sg_volume {
   sg_render_config render_cfg = {};  // tile shape / persistence; zero = default
   float* d_stage = nullptr;  // sg_render_host staging
   size_t stage_bytes = 0;
-  // sg_render_host_async: two staging pairs (frames in flight), a copy stream,
-  // per-pair events; the pair of the next call alternates
+  // sg_render_host_async: kPipeDepth staging pairs (frames in flight), a copy
+  // stream, per-pair events; the calls take the pairs in turn
+  static constexpr int kPipeDepth = 3;
   uint8_t* d_pipe = nullptr;
   size_t pipe_bytes = 0;  // one pair (both eyes)
   cudaStream_t copy_stream = nullptr;
-  cudaEvent_t ev_rendered[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
-  bool copy_pending[2] = {false, false};
-  int pipe_next = 0;
+  cudaEvent_t ev_rendered[kPipeDepth] = {}, ev_copied[kPipeDepth] = {};
+  bool copy_pending[kPipeDepth] = {};
+  int pipe_next = 0;  // the pair of the next call: the oldest frame's
   uint32_t* d_err = nullptr; // device control block: [0] tile queue head of the persistent render
 };
 

@@ -195,10 +195,11 @@ def test_render_host_matches_device_render():
 
 
 def test_pipelined_host_render_matches_device_render():
-    """sg_render_host_async keeps two frames in flight (each frame's copy to
-    host overlaps the next frame's selection and render); every frame's host
-    images equal the device render of its pose, across staging growth (a
-    larger image size midway) and the reuse of both staging pairs."""
+    """sg_render_host_async keeps up to three frames in flight (each frame's
+    copy to host overlaps the next two renders); every frame's host images
+    equal the device render of its pose, across staging growth (a larger
+    image size midway) and the reuse of every staging pair. A caller that
+    waits one frame behind (two in flight) gets the same images."""
     import torch
     from paper_1804_08197_b300 import sg
     case = _c1_case()
@@ -220,14 +221,19 @@ def test_pipelined_host_render_matches_device_render():
             for e in range(2):
                 assert np.array_equal(hosts[i][e].numpy().reshape(-1, 4), refs[i][e]), (i, e)
 
-        for i, (views, projs, w, h) in enumerate(frames):
-            pose, _, _, _ = case.select(views, projs, w, h)
-            sg.sg_render_host_async(case.vol, pose, sg.render_params(), hosts[i])
-            if i >= 1:
-                sg.sg_render_host_wait(case.vol, all=False)  # the older frame in flight is complete
-                check(i - 1)
-        sg.sg_render_host_wait(case.vol, all=True)
-        check(len(frames) - 1)
+        for lag in (2, 1):
+            for hst in hosts:
+                for t in hst:
+                    t.fill_(-1.0)
+            for i, (views, projs, w, h) in enumerate(frames):
+                pose, _, _, _ = case.select(views, projs, w, h)
+                sg.sg_render_host_async(case.vol, pose, sg.render_params(), hosts[i])
+                if i >= lag:
+                    sg.sg_render_host_wait(case.vol, all=False)  # the oldest frame in flight is complete
+                    check(i - lag)
+            sg.sg_render_host_wait(case.vol, all=True)
+            for i in range(len(frames) - lag, len(frames)):
+                check(i)
     finally:
         case.close()
 
