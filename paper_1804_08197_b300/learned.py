@@ -158,6 +158,36 @@ class Learned:
         torch.cuda.synchronize()
         return start.elapsed_time(end)
 
+    def run_plain_pipelined(self, poses, render_stream, sel_stream, slots=(202, 203)):
+        """Plain full-rate frames of `poses` with the selection of frame i + 1
+        (sel_stream, its own slot of two) overlapping the render of frame i
+        (render_stream); a slot is selected again only after the render that
+        read it. Returns the device time from the first selection to the
+        last render (ms); the images stay in self.full."""
+        torch = self.torch
+        ev = lambda: torch.cuda.Event(enable_timing=False)
+        selected, read = [ev(), ev()], [None, None]
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        start.record(render_stream)
+        sel_stream.wait_event(start)
+        if self.cfg_full is not None:
+            sg.sg_set_render_config(self.vol, **self.cfg_full)
+        for i, (views, projs) in enumerate(poses):
+            k = i % 2
+            p = sg.make_pose(views, projs, self.W, self.H, pixel_error=self.tau, slot=slots[k])
+            if read[k] is not None:
+                sel_stream.wait_event(read[k])
+            sg.sg_select_lod(self.vol, p, stream=sel_stream)
+            selected[k].record(sel_stream)
+            render_stream.wait_event(selected[k])
+            sg.sg_render(self.vol, p, sg.render_params(step=self.step), self.full, stream=render_stream)
+            read[k] = ev()
+            read[k].record(render_stream)
+        end.record(render_stream)
+        torch.cuda.synchronize()
+        return start.elapsed_time(end)
+
     def psnr(self, a, b, out_index=0, stream=None):
         sg.sg_psnr(a, b, a.numel(), self.psnr_buf[out_index:out_index + 1], stream=stream)
         return self.psnr_buf[out_index:out_index + 1]
