@@ -549,6 +549,8 @@ def container_streaming(sg, torch, dev, n_vox=1024, brick=64, levels=4, count=12
                 "bricks_served": int(tot["served"]), "host_hits": int(tot["host_hits"]),
                 "disk_reads": int(tot["disk_reads"]),
                 "missed_deadlines": int((fm > period * 1e3).sum()),
+                "missed_frames": [int(i) for i in np.flatnonzero(fm > period * 1e3)][:16],
+                "frame_ms_max": round(float(fm.max()), 3),
                 "frames_with_requests": int(sum(1 for p in pending if p)),
                 "requests_per_frame_mean": round(float(np.mean(pending)), 1),
                 "disk_read_gbs": round(tot["disk_bytes"] / max(sm.sum() / 1e3, 1e-9) / 1e9, 3)}

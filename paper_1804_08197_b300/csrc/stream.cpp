@@ -55,12 +55,11 @@ struct sg_host_cache {
   std::vector<std::thread> loaders;            // started on first use
   // the copies of recent sg_stream_requests_async calls may still be
   // reading entries, those stamped copies_frame or later: such an entry is
-  // neither reused nor freed before this event (recorded on copies_stream
-  // after the last of them) has passed
+  // neither reused nor freed before this event (recorded after the last of
+  // them, and covering the earlier ones) has passed
   cudaEvent_t ev_copies = nullptr;
   bool copies_pending = false;
   uint64_t copies_frame = 0;
-  cudaStream_t copies_stream = nullptr;
 };
 
 extern "C" {
@@ -579,18 +578,19 @@ sg_status stream_impl(sg_volume* v, int slot, sg_host_cache* hc, uint64_t max_by
     placed = std::min(placed, done);
   }
   if (async && !nodes.empty()) {
-    // one event covers every pending call's copies only when all were
-    // queued on one stream: on a new stream the older copies are waited for
-    if (hc->copies_pending && hc->copies_stream != (cudaStream_t)stream) host_cache_quiesce(hc);
+    // the event, recorded after this call's copies, also covers copies of
+    // earlier calls still pending (on whatever stream): the stream waits
+    // for the previous event before the new one is recorded
+    cudaStream_t s = (cudaStream_t)stream;
     if (!hc->ev_copies && cudaEventCreateWithFlags(&hc->ev_copies, cudaEventDisableTiming) != cudaSuccess) {
-      cudaStreamSynchronize((cudaStream_t)stream);  // no event to be had: wait here instead
-    } else if (cudaEventRecord(hc->ev_copies, (cudaStream_t)stream) == cudaSuccess) {
+      cudaStreamSynchronize(s);  // no event to be had: wait here instead
+    } else if ((!hc->copies_pending || cudaStreamWaitEvent(s, hc->ev_copies, 0) == cudaSuccess) &&
+               cudaEventRecord(hc->ev_copies, s) == cudaSuccess) {
       if (!hc->copies_pending) hc->copies_frame = hc->frame;
       hc->copies_pending = true;
-      hc->copies_stream = (cudaStream_t)stream;
     } else {
-      cudaStreamSynchronize((cudaStream_t)stream);
-      hc->copies_pending = false;
+      cudaStreamSynchronize(s);
+      host_cache_quiesce(hc);
     }
   }
   s0.served = placed;
