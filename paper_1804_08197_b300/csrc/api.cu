@@ -706,6 +706,7 @@ sg_status sg_set_transfer_function(sg_volume* v, int c, const float* rgba, int n
     bool positive_after = true;
     for (int k = e; k < n; ++k) positive_after &= rgba[4 * k + 3] > 0.0f;
     t.low_end_transparent = positive_after;
+    t.zero_run = e;
   }
   SG_CUDA(cudaMemcpyAsync(v->d_tf_raw + (size_t)c * kMaxTF * 4, t.rgba.data(), sizeof(float) * 4 * n,
                           cudaMemcpyHostToDevice, s),

@@ -79,6 +79,7 @@ struct TFHost {
   // alpha is 0 exactly on a run of entries starting at entry 0 and positive
   // after it (so every transparent value lies below every visible one)
   bool low_end_transparent = false;
+  int zero_run = 0;                 // entries 0 .. zero_run - 1 have alpha exactly 0
   int gradient = 0;                 // the table reads the gradient magnitude
   int pal_m = 0;                    // depth palette entries (0: the table's colour)
   float pal_near = 0.0f, pal_far = 1.0f;

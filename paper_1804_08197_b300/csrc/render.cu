@@ -87,6 +87,12 @@ struct Args {
   float dims0[3];
   int n[kMaxCh];
   float lo[kMaxCh], inv_w[kMaxCh];
+  // a table input of channel c below vzero[c] reads two table entries of
+  // alpha exactly 0 (at every level and in every optical model but MIP),
+  // so the channel's sample adds exactly nothing; used by the plain
+  // emission-absorption kernels on one-channel volumes (where the check
+  // costs no registers the kernel does not have)
+  float vzero[kMaxCh];
   float step, inv_step, term;
   int empty_skip;
   int mip_skip;        // MIP may skip transparent space (every table transparent only at its low end)
@@ -221,7 +227,14 @@ __device__ __forceinline__ bool composite_sample(const Args& a, const T* __restr
   if (a.nch == 1) {
     // one channel: alpha is an interpolation of table entries in [0, 1], so
     // the additive blend below never saturates
-    const float4 e = classify_sample<T, BK, EXT>(a, brick0, 0, L, lx, ly, lz, sL, t);
+    float4 e;
+    if (!EXT) {
+      const float v = tri<T, BK>(brick0, a.B, lx, ly, lz);
+      if (v < a.vzero[0]) return false;  // alpha 0: acc unchanged (and below term, or the ray had stopped)
+      e = classify(a, 0, L, v);
+    } else {
+      e = classify_sample<T, BK, EXT>(a, brick0, 0, L, lx, ly, lz, sL, t);
+    }
     sa = e.w;
     sr = e.w * e.x;
     sg = e.w * e.y;
@@ -702,6 +715,35 @@ Args make_args(const sg_volume* v, const sg_render_params* prm) {
     a.n[c] = c < v->nch ? v->tf[c].n : 2;
     a.lo[c] = c < v->nch ? v->tf[c].lo : 0.f;
     a.inv_w[c] = c < v->nch ? 1.0f / (v->tf[c].hi - v->tf[c].lo) : 1.f;
+  }
+  for (int c = 0; c < kMaxCh; ++c) {
+    a.vzero[c] = -INFINITY;
+    if (c >= v->nch || v->tf[c].zero_run < 2) continue;
+    // the table index the kernel's classify takes for input x, in the same
+    // FP32 operations; monotone in x, so the inputs whose index is at most
+    // zero_run - 2 (entries i and i + 1 both of alpha 0) lie below the
+    // smallest input whose index reaches zero_run - 1, found by bisection
+    // over the non-negative floats (trilinear inputs are never negative)
+    const int n = a.n[c], need = v->tf[c].zero_run - 1;
+    const float lo = a.lo[c], iw = a.inv_w[c];
+    auto index_of = [&](float x) {
+      const float u = std::fmin(std::fmax((x - lo) * iw, 0.0f), 1.0f);
+      const float q = u * (float)(n - 1);
+      return (int)std::fmin(std::floor(q), (float)(n - 2));
+    };
+    auto bits_f = [](uint32_t b) {
+      float f;
+      memcpy(&f, &b, 4);
+      return f;
+    };
+    if (index_of(0.0f) < need) {
+      uint32_t lo_b = 0, hi_b = 0x7F800000u;  // index(0) < need <= index(+inf)
+      while (hi_b - lo_b > 1) {
+        const uint32_t mid = lo_b + (hi_b - lo_b) / 2;
+        if (index_of(bits_f(mid)) >= need) hi_b = mid; else lo_b = mid;
+      }
+      a.vzero[c] = bits_f(hi_b);
+    }
   }
   a.step = prm->step;
   a.inv_step = 1.0f / prm->step;

@@ -85,3 +85,40 @@ def test_single_entry_palette_and_u8_gradient():
         assert len(img) and np.allclose(img[:, :3] / img[:, 3:4], pal[0], atol=1e-5)
     finally:
         case.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_transparent_samples_skipped_by_the_plain_kernel_change_nothing(mode):
+    """The plain emission-absorption kernels skip the table lookup and the
+    blend of a one-channel sample whose table input falls below the table's
+    run of leading zero-alpha entries (it would add exactly 0). The shading
+    kernels never skip. With a constant table colour, a one-entry palette of
+    that colour makes the shading kernel compute the same arithmetic, so the
+    two images must be equal bit for bit. The same holds for the emission
+    model and for two channels (the second with a table of alpha 0
+    everywhere, read as a gradient in the shading kernel)."""
+    from paper_1804_08197_b300 import sg
+    colour = (0.75, 0.5, 0.25)
+    a = synth.filaments_u16((112, 96, 104), seed=1201, ntubes=14)
+    tf = synth.tf_piecewise(2201, zero_alpha_points=2, zero_span=(40, 60), alpha_max=0.4, colour=colour)
+    assert tf[0, 3] == 0 and tf[30, 3] == 0 and tf[-1, 3] > 0
+    views, projs = synth.orbit_camera(112, seed=3201, width=96, height=88)
+    for nch in (1, 2):
+        chans = [a] if nch == 1 else [a, synth.filaments_u16((112, 96, 104), seed=1202, ntubes=10)]
+        case = GpuCase(chans, 16, 3)
+        try:
+            tables = [tf] if nch == 1 else [tf, np.zeros_like(tf)]
+            case.set_tfs(tables, [(300.0, 60000.0)] * nch)
+            pose, _, _, _ = case.select([views, views], [projs, projs], 96, 88)
+            plain, _ = case.render(pose, counts=False, mode=mode)
+            if nch == 1:
+                sg.sg_set_channel_shading(case.vol, 0, palette=np.array([colour], np.float32))
+            else:
+                sg.sg_set_channel_shading(case.vol, 1, gradient=True)
+            pose, _, _, _ = case.select([views, views], [projs, projs], 96, 88)
+            shaded, _ = case.render(pose, counts=False, mode=mode)
+            assert plain[0][:, :3].max() > 0.05  # the channel shows
+            for e in range(2):
+                assert np.array_equal(plain[e], shaded[e]), (nch, mode, e)
+        finally:
+            case.close()
