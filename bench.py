@@ -87,7 +87,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             threading.Thread(target=self._read, daemon=True).start()
         except (OSError, FileNotFoundError):
@@ -95,9 +95,12 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self):
+    def stop(self, window=None):
+        """Median SM clock and the throttle reasons of the samples taken within
+        window (host perf_counter seconds: the timed region), or of all
+        samples if none fell within it."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -105,9 +108,10 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        inside = [ln for t, ln in self.lines if window and window[0] <= t <= window[1]]
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in inside or [ln for _, ln in self.lines]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -120,7 +124,8 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "samples_in_timed_region": len(inside),
+                "interval_ms": 50}
 
 
 def measured_peak_hbm():
@@ -922,13 +927,14 @@ def run_ours(args, rank, world, local_rank):
     rev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(args.steps)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    w0 = time.perf_counter()
     e0.record(stream)
     sel_stream.wait_event(e0)
     for i in range(args.steps):
         step(args.warmup + i, rev[i])
     e1.record(stream)
     torch.cuda.synchronize()
-    clk = clocks.stop()
+    clk = clocks.stop(window=(w0, time.perf_counter()))
     ms = e0.elapsed_time(e1)
     render_ms = [a.elapsed_time(b) for a, b, _ in rev]
     # frame period: from the previous frame's render end (the loop start for
