@@ -1180,7 +1180,7 @@ def main():
                     help="empty-space skipping cell edge in voxels (0 = the library's default)")
     ap.add_argument("--streaming-size", choices=["auto", "full", "scaled"], default="auto",
                     help="large-volume fly-through at 4096^3 (full), at 1024^3 (scaled), or full when it fits")
-    ap.add_argument("--only", choices=["net", "learned", "train", "streaming", "container"], default=None,
+    ap.add_argument("--only", choices=["net", "learned", "train", "streaming", "container", "batched"], default=None,
                     help="net: only U-Net forwards at 2x720x800 (a small case for profiling the convolutions); "
                          "streaming: only the large-volume fly-through")
     ap.add_argument("--volume", type=int, default=N_VOX, help="volume edge (default 1024; smaller for profiling)")
@@ -1216,6 +1216,11 @@ def main():
         from paper_1804_08197_b300 import sg
         torch.cuda.set_device(local_rank)
         print(json.dumps(container_streaming(sg, torch, torch.device("cuda"))), flush=True)
+    elif args.only == "batched":
+        import torch
+        from paper_1804_08197_b300 import sg
+        torch.cuda.set_device(local_rank)
+        print(json.dumps(batched_4d(sg, torch, torch.device("cuda"))), flush=True)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -89,9 +89,8 @@ struct Args {
   float lo[kMaxCh], inv_w[kMaxCh];
   // a table input of channel c below vzero[c] reads two table entries of
   // alpha exactly 0 (at every level and in every optical model but MIP),
-  // so the channel's sample adds exactly nothing; used by the plain
-  // emission-absorption kernels on one-channel volumes (where the check
-  // costs no registers the kernel does not have)
+  // so the channel's sample adds exactly nothing; the plain
+  // emission-absorption kernels skip such samples
   float vzero[kMaxCh];
   float step, inv_step, term;
   int empty_skip;
@@ -220,11 +219,11 @@ __device__ __forceinline__ float4 classify_sample(const Args& a, const T* __rest
 // Trilinear value + classification + front-to-back compositing of one sample
 // at brick-local coordinate l (all channels, additive blend). Returns true
 // when the ray is opaque enough to stop.
-template <typename T, int BK, bool EXT>
+template <typename T, int BK, bool EXT, int NC = 0>
 __device__ __forceinline__ bool composite_sample(const Args& a, const T* __restrict__ brick0, int L, float lx, float ly,
                                                  float lz, float sL, float t, float4& acc) {
   float sa, sr, sg, sb;
-  if (a.nch == 1) {
+  if (NC == 1 || a.nch == 1) {
     // one channel: alpha is an interpolation of table entries in [0, 1], so
     // the additive blend below never saturates
     float4 e;
@@ -243,7 +242,14 @@ __device__ __forceinline__ bool composite_sample(const Args& a, const T* __restr
     sa = 0.0f; sr = 0.0f; sg = 0.0f; sb = 0.0f;
     for (int c = 0; c < a.nch; ++c) {
       const T* br = reinterpret_cast<const T*>(reinterpret_cast<const uint8_t*>(brick0) + (size_t)c * a.brick_bytes);
-      const float4 e = classify_sample<T, BK, EXT>(a, br, c, L, lx, ly, lz, sL, t);
+      float4 e;
+      if (!EXT) {
+        const float v = tri<T, BK>(br, a.B, lx, ly, lz);
+        if (v < a.vzero[c]) continue;  // alpha 0: adds exactly nothing to the blend
+        e = classify(a, c, L, v);
+      } else {
+        e = classify_sample<T, BK, EXT>(a, br, c, L, lx, ly, lz, sL, t);
+      }
       sa += e.w;
       sr = fmaf(e.w, e.x, sr);
       sg = fmaf(e.w, e.y, sg);
@@ -310,7 +316,7 @@ __device__ inline int cell_of(float p, float invB, int lo, int hi) {
 // iteration (take a sample, jump over transparent sub-blocks, or move to
 // the next block), so the lanes of a warp stay in one loop instead of
 // diverging across nested ones.
-template <typename T, int BK, int MODE, bool EXT, bool TOUCH = false>
+template <typename T, int BK, int MODE, bool EXT, bool TOUCH = false, int NC = 0>
 __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int px, int py, bool active, float4& acc,
                                           uint32_t& cnt) {
   acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -480,10 +486,10 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
     if (MODE == SG_MODE_EMISSION_ABSORPTION) {
 #ifdef SG_RENDER_EVENT_STATS
       const float w_before = acc.w;
-      stop = composite_sample<T, BK, EXT>(a, brick0, L, lx, ly, lz, sL, t, acc);
+      stop = composite_sample<T, BK, EXT, NC>(a, brick0, L, lx, ly, lz, sL, t, acc);
       SG_EV(7, acc.w != w_before ? 1 : 0);
 #else
-      stop = composite_sample<T, BK, EXT>(a, brick0, L, lx, ly, lz, sL, t, acc);
+      stop = composite_sample<T, BK, EXT, NC>(a, brick0, L, lx, ly, lz, sL, t, acc);
 #endif
     } else if (MODE == SG_MODE_EMISSION) {
       emission_sample<T, BK, EXT>(a, brick0, L, lx, ly, lz, sL, t, acc);
@@ -504,7 +510,7 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
       ++cnt;
       SG_EV(0, 1);
       if (MODE == SG_MODE_EMISSION_ABSORPTION)
-        stop = composite_sample<T, BK, EXT>(a, brick0, L, mx, my, mz, sL, t2, acc);
+        stop = composite_sample<T, BK, EXT, NC>(a, brick0, L, mx, my, mz, sL, t2, acc);
       else if (MODE == SG_MODE_EMISSION)
         emission_sample<T, BK, EXT>(a, brick0, L, mx, my, mz, sL, t2, acc);
       else
@@ -547,7 +553,7 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
 #endif
 }
 
-template <typename T, int MAXI, int BK, int MODE, bool EXT, bool TOUCH = false>
+template <typename T, int MAXI, int BK, int MODE, bool EXT, bool TOUCH = false, int NC = 0>
 __global__ void __launch_bounds__(kThreads, min_blocks(kThreads, 1, BK, EXT)) k_render(Args a, Jobs<MAXI> jobs) {
   const int tile = blockIdx.x;
   int im = 0;
@@ -562,7 +568,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(kThreads, 1, BK, EXT)) k_
 
   float4 acc;
   uint32_t cnt;
-  trace_ray<T, BK, MODE, EXT, TOUCH>(a, J, px, py, active, acc, cnt);
+  trace_ray<T, BK, MODE, EXT, TOUCH, NC>(a, J, px, py, active, acc, cnt);
   if (active) {
     const size_t pix = (size_t)py * J.W + px;
     J.out[pix] = acc;
@@ -579,7 +585,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(kThreads, 1, BK, EXT)) k_
 // PERSIST: a grid sized to the machine pulls tiles from a global counter
 // (work queue over all images of the batch, whatever their sizes); else one
 // CTA per tile.
-template <typename T, int TW, int TH, int RPT, bool PERSIST, int BK>
+template <typename T, int TW, int TH, int RPT, bool PERSIST, int BK, int NC>
 __global__ void __launch_bounds__(TW * TH / RPT, min_blocks(TW * TH / RPT, RPT, BK))
     k_render_tiles(Args a, Jobs<128> jobs, int* __restrict__ counter) {
   constexpr int kN = TW * TH / RPT;
@@ -612,7 +618,7 @@ __global__ void __launch_bounds__(TW * TH / RPT, min_blocks(TW * TH / RPT, RPT, 
       const bool active = px < J.W && py < J.H;
       float4 acc;
       uint32_t cnt;
-      trace_ray<T, BK, SG_MODE_EMISSION_ABSORPTION, false>(a, J, px, py, active, acc, cnt);
+      trace_ray<T, BK, SG_MODE_EMISSION_ABSORPTION, false, false, NC>(a, J, px, py, active, acc, cnt);
       if (active) {
         const size_t pix = (size_t)py * J.W + px;
         J.out[pix] = acc;
@@ -801,28 +807,28 @@ bool make_jobs(const sg_volume* v, const sg_pose* poses, int n, const sg_render_
   return true;
 }
 
-template <typename T, int TW, int TH, int RPT, int BK>
+template <typename T, int TW, int TH, int RPT, int BK, int NC>
 cudaError_t launch_tiles(sg_volume* v, const Args& a, const Jobs<128>& jobs, bool persist, cudaStream_t s) {
   constexpr int kN = TW * TH / RPT;
   if (!persist) {
-    k_render_tiles<T, TW, TH, RPT, false, BK><<<jobs.total_tiles, kN, 0, s>>>(a, jobs, nullptr);
+    k_render_tiles<T, TW, TH, RPT, false, BK, NC><<<jobs.total_tiles, kN, 0, s>>>(a, jobs, nullptr);
     return cudaGetLastError();
   }
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_tiles<T, TW, TH, RPT, true, BK>, kN, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_tiles<T, TW, TH, RPT, true, BK, NC>, kN, 0);
   if (per_sm < 1) per_sm = 1;
   int grid = sms * per_sm;
   if (grid > jobs.total_tiles) grid = jobs.total_tiles;
   // word 0 of the volume's device control block is the tile queue head
   cudaError_t e = cudaMemsetAsync(v->d_err, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
-  k_render_tiles<T, TW, TH, RPT, true, BK><<<grid, kN, 0, s>>>(a, jobs, reinterpret_cast<int*>(v->d_err));
+  k_render_tiles<T, TW, TH, RPT, true, BK, NC><<<grid, kN, 0, s>>>(a, jobs, reinterpret_cast<int*>(v->d_err));
   return cudaGetLastError();
 }
 
-template <typename T, int BK>
+template <typename T, int BK, int NC>
 cudaError_t dispatch_tiles(sg_volume* v, const Args& a, const sg_pose* poses, int n, const sg_render_params* prm,
                            float* const* outs, const sg_render_config& c, cudaStream_t s) {
   Jobs<128> jobs;  // by-value kernel parameter block (about 13 KB)
@@ -830,7 +836,7 @@ cudaError_t dispatch_tiles(sg_volume* v, const Args& a, const sg_pose* poses, in
 #define SG_TILE(TW, TH, RPT)                                                              \
   if (c.tile_w == TW && c.tile_h == TH && c.rays_per_thread == RPT) {                     \
     if (!make_jobs<128>(v, poses, n, prm, outs, TW, TH, &jobs)) return cudaErrorInvalidValue; \
-    return launch_tiles<T, TW, TH, RPT, BK>(v, a, jobs, p, s);                            \
+    return launch_tiles<T, TW, TH, RPT, BK, NC>(v, a, jobs, p, s);                        \
   }
   SG_TILE(16, 8, 1)
   SG_TILE(8, 16, 1)
@@ -842,16 +848,16 @@ cudaError_t dispatch_tiles(sg_volume* v, const Args& a, const sg_pose* poses, in
   return cudaErrorInvalidValue;
 }
 
-template <int MAXI, int BK, int MODE, bool EXT = false, bool TOUCH = false>
+template <int MAXI, int BK, int MODE, bool EXT = false, bool TOUCH = false, int NC = 0>
 cudaError_t launch_impl(sg_volume* v, const sg_pose* poses, int n, const sg_render_params* prm, float* const* outs,
                         cudaStream_t s) {
   Args a = make_args(v, prm);
   Jobs<MAXI> jobs;
   if (!make_jobs<MAXI>(v, poses, n, prm, outs, kTileW, kTileH, &jobs)) return cudaErrorInvalidValue;
   if (v->esize == 1)
-    k_render<uint8_t, MAXI, BK, MODE, EXT, TOUCH><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
+    k_render<uint8_t, MAXI, BK, MODE, EXT, TOUCH, NC><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
   else
-    k_render<uint16_t, MAXI, BK, MODE, EXT, TOUCH><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
+    k_render<uint16_t, MAXI, BK, MODE, EXT, TOUCH, NC><<<jobs.total_tiles, kThreads, 0, s>>>(a, jobs);
   return cudaGetLastError();
 }
 
@@ -878,14 +884,23 @@ cudaError_t launch_b(sg_volume* v, const sg_pose* poses, int n, const sg_render_
   // shapes and the autotuner serve the emission-absorption model)
   if (prm->mode == SG_MODE_EMISSION) return launch_impl<128, BK, SG_MODE_EMISSION>(v, poses, n, prm, outs, s);
   if (prm->mode == SG_MODE_MIP) return launch_impl<128, BK, SG_MODE_MIP>(v, poses, n, prm, outs, s);
+  // the emission-absorption kernels come in two builds: one channel known at
+  // compile time (no blend loop in the code), and any channel count
   const sg_render_config& c = v->render_cfg;
+  const bool one = v->nch == 1;
   if (c.tile_w == 0) {  // default: one 16 x 8 CTA per tile
-    if (n == 1) return launch_impl<2, BK, SG_MODE_EMISSION_ABSORPTION>(v, poses, n, prm, outs, s);
-    return launch_impl<128, BK, SG_MODE_EMISSION_ABSORPTION>(v, poses, n, prm, outs, s);
+    if (n == 1)
+      return one ? launch_impl<2, BK, SG_MODE_EMISSION_ABSORPTION, false, false, 1>(v, poses, n, prm, outs, s)
+                 : launch_impl<2, BK, SG_MODE_EMISSION_ABSORPTION>(v, poses, n, prm, outs, s);
+    return one ? launch_impl<128, BK, SG_MODE_EMISSION_ABSORPTION, false, false, 1>(v, poses, n, prm, outs, s)
+               : launch_impl<128, BK, SG_MODE_EMISSION_ABSORPTION>(v, poses, n, prm, outs, s);
   }
   Args a = make_args(v, prm);
-  if (v->esize == 1) return dispatch_tiles<uint8_t, BK>(v, a, poses, n, prm, outs, c, s);
-  return dispatch_tiles<uint16_t, BK>(v, a, poses, n, prm, outs, c, s);
+  if (v->esize == 1)
+    return one ? dispatch_tiles<uint8_t, BK, 1>(v, a, poses, n, prm, outs, c, s)
+               : dispatch_tiles<uint8_t, BK, 0>(v, a, poses, n, prm, outs, c, s);
+  return one ? dispatch_tiles<uint16_t, BK, 1>(v, a, poses, n, prm, outs, c, s)
+             : dispatch_tiles<uint16_t, BK, 0>(v, a, poses, n, prm, outs, c, s);
 }
 
 }  // namespace
