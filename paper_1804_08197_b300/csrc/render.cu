@@ -42,9 +42,11 @@ constexpr int kWarpsPerSM = SG_RENDER_WARPS_PER_SM;
 // Lattice points a sample iteration may take (the first after a sub-block
 // lookup, the others without one while they stay in the block): fewer loop
 // trips per sample and fewer iterations in which the warp also runs the jump
-// and block-step paths for its other lanes.
+// and block-step paths for its other lanes. Three fit the one-channel
+// kernels' 64 registers without spills (on the 1024^3 bench: 2 / 3 / 4 ->
+// 482 / 494 / 481 stereo fps).
 #ifndef SG_SAMPLES_PER_ITER
-#define SG_SAMPLES_PER_ITER 2
+#define SG_SAMPLES_PER_ITER 3
 #endif
 constexpr int kSamplesPerIter = SG_SAMPLES_PER_ITER;
 __host__ __device__ constexpr int min_blocks(int threads, int rpt, int bk, bool ext = false) {
