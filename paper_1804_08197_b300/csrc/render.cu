@@ -274,10 +274,11 @@ __device__ __forceinline__ bool composite_sample(const Args& a, const T* __restr
 // Emission-only sample: every channel adds its table colour times its
 // emission weight (the table's alpha for this level is alpha * step 2^L /
 // ref_step); no absorption, the ray never stops early.
-template <typename T, int BK, bool EXT>
+template <typename T, int BK, bool EXT, int NC = 0>
 __device__ __forceinline__ void emission_sample(const Args& a, const T* __restrict__ brick0, int L, float lx, float ly,
                                                 float lz, float sL, float t, float4& acc) {
-  for (int c = 0; c < a.nch; ++c) {
+  const int nch = NC == 1 ? 1 : a.nch;
+  for (int c = 0; c < nch; ++c) {
     const T* br = reinterpret_cast<const T*>(reinterpret_cast<const uint8_t*>(brick0) + (size_t)c * a.brick_bytes);
     const float4 e = classify_sample<T, BK, EXT>(a, br, c, L, lx, ly, lz, sL, t);
     acc.x = fmaf(e.w, e.x, acc.x);
@@ -288,12 +289,12 @@ __device__ __forceinline__ void emission_sample(const Args& a, const T* __restri
 
 // Maximum intensity projection sample: the running maximum of each
 // channel's table input, with the distance of the first sample reaching it.
-template <typename T, int BK, bool EXT>
+template <typename T, int BK, bool EXT, int NC = 0>
 __device__ __forceinline__ void mip_sample(const Args& a, const T* __restrict__ brick0, float lx, float ly, float lz,
                                            float sL, float t, float (&vmax)[kMaxCh], float (&tat)[kMaxCh]) {
 #pragma unroll
   for (int c = 0; c < kMaxCh; ++c) {
-    if (c >= a.nch) break;
+    if (c >= (NC == 1 ? 1 : a.nch)) break;
     const T* br = reinterpret_cast<const T*>(reinterpret_cast<const uint8_t*>(brick0) + (size_t)c * a.brick_bytes);
     const float v = table_input<T, BK, EXT>(a, br, c, lx, ly, lz, sL);
     if (v > vmax[c]) {
@@ -494,9 +495,9 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
       stop = composite_sample<T, BK, EXT, NC>(a, brick0, L, lx, ly, lz, sL, t, acc);
 #endif
     } else if (MODE == SG_MODE_EMISSION) {
-      emission_sample<T, BK, EXT>(a, brick0, L, lx, ly, lz, sL, t, acc);
+      emission_sample<T, BK, EXT, NC>(a, brick0, L, lx, ly, lz, sL, t, acc);
     } else {
-      mip_sample<T, BK, EXT>(a, brick0, lx, ly, lz, sL, t, vmax, tat);
+      mip_sample<T, BK, EXT, NC>(a, brick0, lx, ly, lz, sL, t, vmax, tat);
     }
     if (stop) break;
     k += kstep;
@@ -514,9 +515,9 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
       if (MODE == SG_MODE_EMISSION_ABSORPTION)
         stop = composite_sample<T, BK, EXT, NC>(a, brick0, L, mx, my, mz, sL, t2, acc);
       else if (MODE == SG_MODE_EMISSION)
-        emission_sample<T, BK, EXT>(a, brick0, L, mx, my, mz, sL, t2, acc);
+        emission_sample<T, BK, EXT, NC>(a, brick0, L, mx, my, mz, sL, t2, acc);
       else
-        mip_sample<T, BK, EXT>(a, brick0, mx, my, mz, sL, t2, vmax, tat);
+        mip_sample<T, BK, EXT, NC>(a, brick0, mx, my, mz, sL, t2, vmax, tat);
       if (stop) break;
       k += kstep;
     }
@@ -529,7 +530,7 @@ __device__ __forceinline__ void trace_ray(const Args& a, const ImageJob& J, int 
     float sa = 0.0f, sr = 0.0f, sg = 0.0f, sb = 0.0f;
 #pragma unroll
     for (int c = 0; c < kMaxCh; ++c) {
-      if (c >= a.nch) break;
+      if (c >= (NC == 1 ? 1 : a.nch)) break;
       float4 e = classify(a, c, 0, vmax[c]);
       if (EXT && a.pal_m[c] > 0) {
         const float3 p = palette_at(a, c, tat[c] * a.voxel);
@@ -882,14 +883,18 @@ cudaError_t launch_b(sg_volume* v, const sg_pose* poses, int n, const sg_render_
     if (prm->mode == SG_MODE_MIP) return launch_impl<128, BK, SG_MODE_MIP, true>(v, poses, n, prm, outs, s);
     return launch_impl<128, BK, SG_MODE_EMISSION_ABSORPTION, true>(v, poses, n, prm, outs, s);
   }
-  // emission-only and MIP run the one-CTA-per-16x8-tile kernel (the launch
-  // shapes and the autotuner serve the emission-absorption model)
-  if (prm->mode == SG_MODE_EMISSION) return launch_impl<128, BK, SG_MODE_EMISSION>(v, poses, n, prm, outs, s);
-  if (prm->mode == SG_MODE_MIP) return launch_impl<128, BK, SG_MODE_MIP>(v, poses, n, prm, outs, s);
-  // the emission-absorption kernels come in two builds: one channel known at
-  // compile time (no blend loop in the code), and any channel count
-  const sg_render_config& c = v->render_cfg;
+  // every plain kernel comes in two builds: one channel known at compile
+  // time (no loop over channels in the code), and any channel count.
+  // Emission-only and MIP run the one-CTA-per-16x8-tile kernel (the launch
+  // shapes and the autotuner serve the emission-absorption model).
   const bool one = v->nch == 1;
+  if (prm->mode == SG_MODE_EMISSION)
+    return one ? launch_impl<128, BK, SG_MODE_EMISSION, false, false, 1>(v, poses, n, prm, outs, s)
+               : launch_impl<128, BK, SG_MODE_EMISSION>(v, poses, n, prm, outs, s);
+  if (prm->mode == SG_MODE_MIP)
+    return one ? launch_impl<128, BK, SG_MODE_MIP, false, false, 1>(v, poses, n, prm, outs, s)
+               : launch_impl<128, BK, SG_MODE_MIP>(v, poses, n, prm, outs, s);
+  const sg_render_config& c = v->render_cfg;
   if (c.tile_w == 0) {  // default: one 16 x 8 CTA per tile
     if (n == 1)
       return one ? launch_impl<2, BK, SG_MODE_EMISSION_ABSORPTION, false, false, 1>(v, poses, n, prm, outs, s)
