@@ -5,6 +5,8 @@
 import os
 import subprocess
 import sys
+import tempfile
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
@@ -31,17 +33,29 @@ def _stale():
 
 
 def build(force=False, verbose=False, out=None, defines=()):
-    """Compiles csrc/*.cu into `out` (default: the in-tree libsg.so)."""
+    """Compiles csrc/*.cu into `out` (default: the in-tree libsg.so): one
+    object per source, compiled in parallel, then linked."""
     out = out or LIB
     if out == LIB and not defines and not force and not _stale():
         return LIB
-    cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", "--extended-lambda", "-o", out + ".tmp"]
-    cmd += [f"-D{d}" for d in defines]
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+             "--expt-relaxed-constexpr", "--extended-lambda"]
+    flags += [f"-D{d}" for d in defines]
     if verbose:
-        cmd += ["-Xptxas", "-v"]
-    cmd += [os.path.join(CSRC, f) for f in SOURCES]
-    subprocess.check_call(cmd)
+        flags += ["-Xptxas", "-v"]
+    with tempfile.TemporaryDirectory(prefix="sg_build_") as tmp:
+        objs = [os.path.join(tmp, os.path.splitext(f)[0] + ".o") for f in SOURCES]
+
+        def compile_one(i):
+            subprocess.check_call([_nvcc(), *flags, "-c", os.path.join(CSRC, SOURCES[i]), "-o", objs[i]])
+
+        # the longest compile first
+        order = sorted(range(len(SOURCES)), key=lambda i: os.path.getsize(os.path.join(CSRC, SOURCES[i])),
+                       reverse=True)
+        with ThreadPoolExecutor(max_workers=max(1, min(len(SOURCES), os.cpu_count() or 1))) as ex:
+            for f in [ex.submit(compile_one, i) for i in order]:
+                f.result()
+        subprocess.check_call([_nvcc(), *ARCH, "-shared", "-o", out + ".tmp", *objs])
     os.replace(out + ".tmp", out)
     return out
 

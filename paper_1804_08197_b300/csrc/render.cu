@@ -225,7 +225,7 @@ template <typename T, int BK, bool EXT, int NC = 0>
 __device__ __forceinline__ bool composite_sample(const Args& a, const T* __restrict__ brick0, int L, float lx, float ly,
                                                  float lz, float sL, float t, float4& acc) {
   float sa, sr, sg, sb;
-  if (NC == 1 || a.nch == 1) {
+  if (NC == 1 || (NC == 0 && a.nch == 1)) {
     // one channel: alpha is an interpolation of table entries in [0, 1], so
     // the additive blend below never saturates
     float4 e;
@@ -242,12 +242,12 @@ __device__ __forceinline__ bool composite_sample(const Args& a, const T* __restr
     sb = e.w * e.z;
   } else {
     sa = 0.0f; sr = 0.0f; sg = 0.0f; sb = 0.0f;
-    for (int c = 0; c < a.nch; ++c) {
+    auto channel = [&](int c) {
       const T* br = reinterpret_cast<const T*>(reinterpret_cast<const uint8_t*>(brick0) + (size_t)c * a.brick_bytes);
       float4 e;
       if (!EXT) {
         const float v = tri<T, BK>(br, a.B, lx, ly, lz);
-        if (v < a.vzero[c]) continue;  // alpha 0: adds exactly nothing to the blend
+        if (v < a.vzero[c]) return;  // alpha 0: adds exactly nothing to the blend
         e = classify(a, c, L, v);
       } else {
         e = classify_sample<T, BK, EXT>(a, br, c, L, lx, ly, lz, sL, t);
@@ -256,6 +256,12 @@ __device__ __forceinline__ bool composite_sample(const Args& a, const T* __restr
       sr = fmaf(e.w, e.x, sr);
       sg = fmaf(e.w, e.y, sg);
       sb = fmaf(e.w, e.z, sb);
+    };
+    if (NC >= 2) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) channel(c);
+    } else {
+      for (int c = 0; c < a.nch; ++c) channel(c);
     }
     if (sa > 1.0f) {  // additive blend saturates: alpha 1, colour renormalised
       const float r = 1.0f / sa;
@@ -887,7 +893,7 @@ cudaError_t launch_b(sg_volume* v, const sg_pose* poses, int n, const sg_render_
   // time (no loop over channels in the code), and any channel count.
   // Emission-only and MIP run the one-CTA-per-16x8-tile kernel (the launch
   // shapes and the autotuner serve the emission-absorption model).
-  const bool one = v->nch == 1;
+  const bool one = v->nch == 1, two = v->nch == 2;
   if (prm->mode == SG_MODE_EMISSION)
     return one ? launch_impl<128, BK, SG_MODE_EMISSION, false, false, 1>(v, poses, n, prm, outs, s)
                : launch_impl<128, BK, SG_MODE_EMISSION>(v, poses, n, prm, outs, s);
@@ -895,18 +901,23 @@ cudaError_t launch_b(sg_volume* v, const sg_pose* poses, int n, const sg_render_
     return one ? launch_impl<128, BK, SG_MODE_MIP, false, false, 1>(v, poses, n, prm, outs, s)
                : launch_impl<128, BK, SG_MODE_MIP>(v, poses, n, prm, outs, s);
   const sg_render_config& c = v->render_cfg;
+  // (emission-absorption: one, two or any channels)
   if (c.tile_w == 0) {  // default: one 16 x 8 CTA per tile
     if (n == 1)
       return one ? launch_impl<2, BK, SG_MODE_EMISSION_ABSORPTION, false, false, 1>(v, poses, n, prm, outs, s)
+           : two ? launch_impl<2, BK, SG_MODE_EMISSION_ABSORPTION, false, false, 2>(v, poses, n, prm, outs, s)
                  : launch_impl<2, BK, SG_MODE_EMISSION_ABSORPTION>(v, poses, n, prm, outs, s);
     return one ? launch_impl<128, BK, SG_MODE_EMISSION_ABSORPTION, false, false, 1>(v, poses, n, prm, outs, s)
+         : two ? launch_impl<128, BK, SG_MODE_EMISSION_ABSORPTION, false, false, 2>(v, poses, n, prm, outs, s)
                : launch_impl<128, BK, SG_MODE_EMISSION_ABSORPTION>(v, poses, n, prm, outs, s);
   }
   Args a = make_args(v, prm);
   if (v->esize == 1)
     return one ? dispatch_tiles<uint8_t, BK, 1>(v, a, poses, n, prm, outs, c, s)
+         : two ? dispatch_tiles<uint8_t, BK, 2>(v, a, poses, n, prm, outs, c, s)
                : dispatch_tiles<uint8_t, BK, 0>(v, a, poses, n, prm, outs, c, s);
   return one ? dispatch_tiles<uint16_t, BK, 1>(v, a, poses, n, prm, outs, c, s)
+       : two ? dispatch_tiles<uint16_t, BK, 2>(v, a, poses, n, prm, outs, c, s)
              : dispatch_tiles<uint16_t, BK, 0>(v, a, poses, n, prm, outs, c, s);
 }
 
