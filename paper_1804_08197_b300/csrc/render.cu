@@ -286,7 +286,14 @@ __device__ __forceinline__ void emission_sample(const Args& a, const T* __restri
   const int nch = NC == 1 ? 1 : a.nch;
   for (int c = 0; c < nch; ++c) {
     const T* br = reinterpret_cast<const T*>(reinterpret_cast<const uint8_t*>(brick0) + (size_t)c * a.brick_bytes);
-    const float4 e = classify_sample<T, BK, EXT>(a, br, c, L, lx, ly, lz, sL, t);
+    float4 e;
+    if (!EXT) {
+      const float v = tri<T, BK>(br, a.B, lx, ly, lz);
+      if (v < a.vzero[c]) continue;  // emission weight 0: adds exactly nothing
+      e = classify(a, c, L, v);
+    } else {
+      e = classify_sample<T, BK, EXT>(a, br, c, L, lx, ly, lz, sL, t);
+    }
     acc.x = fmaf(e.w, e.x, acc.x);
     acc.y = fmaf(e.w, e.y, acc.y);
     acc.z = fmaf(e.w, e.z, acc.z);

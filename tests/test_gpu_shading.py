@@ -89,14 +89,15 @@ def test_single_entry_palette_and_u8_gradient():
 
 @pytest.mark.parametrize("mode", [0, 1])
 def test_transparent_samples_skipped_by_the_plain_kernel_change_nothing(mode):
-    """The plain emission-absorption kernels skip the table lookup and the
-    blend of a one-channel sample whose table input falls below the table's
-    run of leading zero-alpha entries (it would add exactly 0). The shading
-    kernels never skip. With a constant table colour, a one-entry palette of
-    that colour makes the shading kernel compute the same arithmetic, so the
-    two images must be equal bit for bit. The same holds for the emission
-    model and for two channels (the second with a table of alpha 0
-    everywhere, read as a gradient in the shading kernel)."""
+    """The plain emission-absorption and emission-only kernels skip the
+    table lookup and the blend of a channel's sample whose table input falls
+    below the table's run of leading zero-alpha entries (it would add
+    exactly 0). The shading kernels never skip. With a constant table
+    colour, a one-entry palette of that colour makes the shading kernel
+    compute the same arithmetic, so the two images must be equal bit for
+    bit: one channel (the one-channel build), then two (the second with a
+    table of alpha 0 everywhere, read as a gradient in the shading
+    kernel)."""
     from paper_1804_08197_b300 import sg
     colour = (0.75, 0.5, 0.25)
     a = synth.filaments_u16((112, 96, 104), seed=1201, ntubes=14)
