@@ -251,7 +251,9 @@ sg_status sg_stream_requests(sg_volume* vol, int slot, sg_host_cache* hc, uint64
  * the copies and the bricks' ranges and flags are queued on stream and not
  * waited for; every later selection, transfer-function change or brick read
  * waits for them on the device, and the host cache reuses none of those
- * entries before they are done. The others are
+ * entries before they are done (the call waits for earlier calls' copies
+ * only when it must reuse an entry they may still read; it reads the
+ * selection's requests on a stream of the volume's own). The others are
  * handed to hc's background loader threads (at most max_bytes of new loads
  * per call) and placed by a later call once loaded. Until then the next
  * selections render their resident ancestors, so a frame never waits on a
